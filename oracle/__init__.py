@@ -1,0 +1,211 @@
+"""Oracle for the correspondence search (Sec. IV-C) and fusion search (Sec. IV-D).
+
+TEST INFRASTRUCTURE ONLY.  A plain, slow, obviously-correct CPU definition (C, in
+`tm_oracle.c`) plus this ctypes wrapper.  Only the tests, the smoke check and the benchmark's
+CPU-baseline / reference arm load it; the library never does, and it shares no code with the
+CUDA path.
+
+Parity pins: see tests/test_oracle_pins.py (brute force, closed forms, planted geometry,
+hand-worked golden cases under tests/golden/).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force=False, src=_SRC, out=_LIB):
+    """Compile the oracle with gcc (no FMA contraction, IEEE float)."""
+    hdr = os.path.join(_HERE, "tm_oracle.h")
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
+            os.path.getmtime(src), os.path.getmtime(hdr)):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.run(["gcc", *CFLAGS, "-I", _HERE, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class _Keyframe(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32),
+                ("desc", ctypes.c_void_p), ("xy", ctypes.c_void_p),
+                ("angle", ctypes.c_void_p), ("level", ctypes.c_void_p),
+                ("node", ctypes.c_void_p), ("Tcw", ctypes.c_double * 12)]
+
+
+class _SearchParams(ctypes.Structure):
+    _fields_ = [("hamming_max", ctypes.c_int32), ("ratio_num", ctypes.c_int32),
+                ("ratio_den", ctypes.c_int32), ("epi_chi2", ctypes.c_float),
+                ("epipolar", ctypes.c_int32), ("resolve", ctypes.c_int32),
+                ("rot_filter", ctypes.c_int32)]
+
+
+class _FuseParams(ctypes.Structure):
+    _fields_ = [("chi2", ctypes.c_float), ("hamming_max", ctypes.c_int32),
+                ("radius_scale", ctypes.c_float)]
+
+
+@dataclass
+class SearchParams:
+    hamming_max: int = 50
+    ratio_num: int = 3
+    ratio_den: int = 5
+    epi_chi2: float = 3.84
+    epipolar: bool = True
+    resolve: bool = True
+    rot_filter: bool = True
+
+
+@dataclass
+class FuseParams:
+    chi2: float = 5.99
+    hamming_max: int = 50
+    radius_scale: float = 3.0
+
+
+_lib = None
+
+
+def use_library(path):
+    """Load the oracle from another build of tm_oracle.c (None: the default build).  Used by
+    the mutation test, which compiles deliberately broken copies of the source."""
+    global _lib
+    _lib = None
+    return lib(path)
+
+
+def lib(path=None):
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(path or build())
+        P = ctypes.c_void_p
+        L.orc_fundamental.argtypes = [ctypes.POINTER(_Camera), P, P, P]
+        L.orc_fundamental.restype = None
+        L.orc_search_pair.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Keyframe),
+                                      ctypes.POINTER(_Keyframe), P, P,
+                                      ctypes.POINTER(_SearchParams), P, P, P,
+                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        L.orc_search_pair.restype = ctypes.c_int64
+        L.orc_fuse.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Keyframe),
+                               ctypes.c_int32, P, P, P, P, P, P,
+                               ctypes.POINTER(_FuseParams), P, P, P, ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_int64)]
+        L.orc_fuse.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _cam(cam):
+    return _Camera(int(cam["width"]), int(cam["height"]), float(cam["fx"]), float(cam["fy"]),
+                   float(cam["cx"]), float(cam["cy"]))
+
+
+def _kf(kf, keep):
+    arrs = [np.ascontiguousarray(kf["desc"], np.uint8), np.ascontiguousarray(kf["xy"], np.float32),
+            np.ascontiguousarray(kf["angle"], np.float32), np.ascontiguousarray(kf["level"], np.uint8),
+            np.ascontiguousarray(kf["node"], np.uint32)]
+    keep.extend(arrs)
+    s = _Keyframe()
+    s.n = int(len(arrs[0]))
+    s.desc, s.xy, s.angle, s.level, s.node = (a.ctypes.data for a in arrs)
+    s.Tcw[:] = [float(x) for x in np.asarray(kf["Tcw"], np.float64).reshape(12)]
+    return s
+
+
+def fundamental(cam, tcw_q, tcw_t):
+    F = np.zeros(9, np.float32)
+    a = np.ascontiguousarray(tcw_q, np.float64).reshape(12)
+    b = np.ascontiguousarray(tcw_t, np.float64).reshape(12)
+    c = _cam(cam)
+    lib().orc_fundamental(ctypes.byref(c), a.ctypes.data, b.ctypes.data, F.ctypes.data)
+    return F.reshape(3, 3)
+
+
+def _mask(m):
+    return None if m is None else np.ascontiguousarray(m, np.uint8)
+
+
+def search_pair(cam, Q, T, free_q=None, free_t=None, params=None):
+    """Matches of one (Q, T) pair as an int32 array (k, 3) of (q_idx, t_idx, dist), sorted
+    by q_idx, and the number of descriptor comparisons."""
+    p = params or SearchParams()
+    keep = []
+    q, t = _kf(Q, keep), _kf(T, keep)
+    fq, ft = _mask(free_q), _mask(free_t)
+    sp = _SearchParams(p.hamming_max, p.ratio_num, p.ratio_den, p.epi_chi2, int(p.epipolar),
+                       int(p.resolve), int(p.rot_filter))
+    cap = max(1, min(q.n, t.n) if p.resolve else q.n)
+    out = np.zeros((3, cap), np.int32)
+    ncmp = ctypes.c_int64(0)
+    c = _cam(cam)
+    n = lib().orc_search_pair(ctypes.byref(c), ctypes.byref(q), ctypes.byref(t), _ptr(fq),
+                              _ptr(ft), ctypes.byref(sp), out[0].ctypes.data,
+                              out[1].ctypes.data, out[2].ctypes.data, cap, ctypes.byref(ncmp))
+    assert n <= cap
+    return np.ascontiguousarray(out[:, :n].T), int(ncmp.value)
+
+
+def fuse(cam, T, mps, params=None):
+    """Fusion candidates of a map-point batch into keyframe T as an int32 array (k, 3) of
+    (mp_idx, kp_idx, dist), sorted by mp_idx, and the number of window comparisons."""
+    p = params or FuseParams()
+    keep = []
+    t = _kf(T, keep)
+    n = int(mps["n"])
+    pos = np.ascontiguousarray(mps["pos"], np.float32)
+    nrm = np.ascontiguousarray(mps["normal"], np.float32)
+    desc = np.ascontiguousarray(mps["desc"], np.uint8)
+    mn = np.ascontiguousarray(mps["min_dist"], np.float32)
+    mx = np.ascontiguousarray(mps["max_dist"], np.float32)
+    skip = _mask(mps.get("skip"))
+    fp = _FuseParams(p.chi2, p.hamming_max, p.radius_scale)
+    cap = max(1, n)
+    out = np.zeros((3, cap), np.int32)
+    ncmp = ctypes.c_int64(0)
+    c = _cam(cam)
+    k = lib().orc_fuse(ctypes.byref(c), ctypes.byref(t), n, pos.ctypes.data, nrm.ctypes.data,
+                       desc.ctypes.data, mn.ctypes.data, mx.ctypes.data, _ptr(skip),
+                       ctypes.byref(fp), out[0].ctypes.data, out[1].ctypes.data,
+                       out[2].ctypes.data, cap, ctypes.byref(ncmp))
+    assert k <= cap
+    return np.ascontiguousarray(out[:, :k].T), int(ncmp.value)
+
+
+def search_step(cam, frames, step, params=None):
+    """All pairs of one local-mapping step, in neighbour order: list of match arrays and the
+    total number of comparisons."""
+    Q = frames[step["q"]]
+    res, ncmp = [], 0
+    for k, f in enumerate(step["nbrs"]):
+        ft = None if step.get("nbr_free") is None else step["nbr_free"][k]
+        m, c = search_pair(cam, Q, frames[f], step.get("q_free"), ft, params)
+        res.append(m)
+        ncmp += c
+    return res, ncmp
+
+
+def fuse_step(cam, frames, step, params=None):
+    if step.get("mps") is None:
+        return np.zeros((0, 3), np.int32), 0
+    return fuse(cam, frames[step["q"]], step["mps"], params)

@@ -1,0 +1,390 @@
+"""Pins for the oracle: each part is checked against something other than the oracle itself
+(library routines, brute force, closed forms, planted geometry, hand-worked cases).
+
+Runs on the CPU only."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+GATES_OFF = O.SearchParams(hamming_max=256, ratio_num=0, epipolar=False, resolve=False,
+                           rot_filter=False)
+
+
+def prefix_desc(bits):
+    """Descriptors whose first `bits[k]` bits are set: Hamming(a, b) = |bits_a - bits_b|."""
+    bits = np.asarray(bits, np.int64)
+    out = np.zeros((len(bits), 256), np.uint8)
+    for k, b in enumerate(bits):
+        out[k, :b] = 1
+    return np.packbits(out, axis=1)
+
+
+def kf_from(desc, node, xy=None, angle=None, level=None, tcw=None):
+    n = len(desc)
+    return W.make_keyframe(desc, np.zeros((n, 2), np.float32) if xy is None else xy,
+                           np.zeros(n, np.float32) if angle is None else angle,
+                           np.zeros(n, np.uint8) if level is None else level,
+                           np.asarray(node, np.uint32), np.eye(3, 4) if tcw is None else tcw,
+                           -np.ones(n, np.int64))
+
+
+def hamming_np(a, b):
+    """All-pairs Hamming distance with numpy's bit count (library routine)."""
+    x = np.bitwise_xor(a[:, None, :], b[None, :, :])
+    return np.bitwise_count(x).sum(axis=2).astype(np.int64)
+
+
+CAM = W.CAM_CFG0
+
+
+# --------------------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hamming_argmin_brute_force(seed):
+    """Gates off, one node: every query's match is numpy's argmin of the Hamming matrix."""
+    rng = np.random.default_rng(seed)
+    nq, nt = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    Q = W.random_keyframe(rng, nq, CAM, n_nodes=1)
+    T = W.random_keyframe(rng, nt, CAM, n_nodes=1)
+    m, ncmp = O.search_pair(CAM, Q, T, params=GATES_OFF)
+    D = hamming_np(Q["desc"], T["desc"])
+    exp = np.stack([np.arange(nq), D.argmin(axis=1), D.min(axis=1)], axis=1)
+    assert ncmp == nq * nt
+    np.testing.assert_array_equal(m, exp)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_node_buckets_brute_force(seed):
+    """Gates off, a few nodes, random masks: the match of each free query is the argmin over
+    free same-node targets; the comparison count is the size of that join."""
+    rng = np.random.default_rng(100 + seed)
+    nq, nt = int(rng.integers(0, 60)), int(rng.integers(0, 60))
+    Q = W.random_keyframe(rng, nq, CAM, n_nodes=4)
+    T = W.random_keyframe(rng, nt, CAM, n_nodes=4)
+    fq = (rng.random(nq) < 0.8).astype(np.uint8)
+    ft = (rng.random(nt) < 0.8).astype(np.uint8)
+    m, ncmp = O.search_pair(CAM, Q, T, fq, ft, GATES_OFF)
+    D = hamming_np(Q["desc"], T["desc"]) if nq and nt else np.zeros((nq, nt), np.int64)
+    ok = (Q["node"][:, None] == T["node"][None, :]) & (fq[:, None] > 0) & (ft[None, :] > 0)
+    assert ncmp == int(ok.sum())
+    Dm = np.where(ok, D, 10 ** 6)
+    rows = [(i, int(Dm[i].argmin()), int(Dm[i].min())) for i in range(nq) if ok[i].any()]
+    np.testing.assert_array_equal(m.reshape(-1, 3), np.array(rows, np.int64).reshape(-1, 3))
+
+
+# --------------------------------------------------------------------------- hand-worked cases
+
+def test_ratio_golden():
+    g = json.load(open(os.path.join(GOLD, "ratio_cases.json")))
+    p = O.SearchParams(epipolar=False, rot_filter=False)
+    for case in g["cases"]:
+        d = case["dists"]
+        Q = kf_from(prefix_desc([0]), [0])
+        T = kf_from(prefix_desc(d) if d else np.zeros((0, 32), np.uint8), [0] * len(d))
+        m, _ = O.search_pair(CAM, Q, T, params=p)
+        assert m.tolist() == case["expect"], case
+
+
+def test_resolve_golden():
+    g = json.load(open(os.path.join(GOLD, "resolve_cases.json")))
+    p = O.SearchParams(epipolar=False, rot_filter=False)
+    for case in g["cases"]:
+        Q = kf_from(prefix_desc(case["q_bits"]), case["q_node"])
+        T = kf_from(prefix_desc(case["t_bits"]), case["t_node"])
+        m, _ = O.search_pair(CAM, Q, T, params=p)
+        assert m.tolist() == case["expect"], case
+
+
+def test_rotation_golden():
+    g = json.load(open(os.path.join(GOLD, "rotation_cases.json")))
+    p = O.SearchParams(epipolar=False)
+    for case in g["cases"]:
+        n = len(case["q_angle"])
+        qa = np.asarray(case["q_angle"], np.float32)
+        ta = np.asarray(case.get("t_angle", [0.0] * n), np.float32)
+        Q = kf_from(prefix_desc([0] * n), np.arange(n), angle=qa)
+        T = kf_from(prefix_desc([0] * n), np.arange(n), angle=ta)
+        m, _ = O.search_pair(CAM, Q, T, params=p)
+        assert m[:, 0].tolist() == case["expect_q"], case
+        assert (m[:, 0] == m[:, 1]).all()
+
+
+def test_fuse_golden():
+    g = json.load(open(os.path.join(GOLD, "fuse_cases.json")))
+    cam = dict(g["camera"])
+    k = g["keypoints"]
+    T = kf_from(prefix_desc(k["bits"]), np.zeros(len(k["bits"])),
+                xy=np.asarray(k["xy"], np.float32), level=np.asarray(k["level"], np.uint8),
+                tcw=np.asarray(g["Tcw"], np.float64).reshape(3, 4))
+    mp = g["mappoints"]
+    n = len(mp["pos"])
+    mps = dict(n=n, pos=np.asarray(mp["pos"], np.float32), normal=np.asarray(mp["normal"], np.float32),
+               desc=prefix_desc(mp["bits"]), min_dist=np.asarray(mp["min_dist"], np.float32),
+               max_dist=np.asarray(mp["max_dist"], np.float32), skip=np.asarray(mp["skip"], np.uint8))
+    m, ncmp = O.fuse(cam, T, mps)
+    assert m.tolist() == g["expect"]
+    assert ncmp == g["expect_comparisons"]
+
+
+# --------------------------------------------------------------------------- closed forms
+
+def _pose_pair(rng):
+    ta = W.yaw_pose(rng.normal(0, 1, 3), rng.uniform(-30, 30))
+    tb = W.yaw_pose(rng.normal(0, 1, 3), rng.uniform(-30, 30))
+    # add pitch/roll so that no entry of R is structurally zero
+    def tilt(t, ax, ay):
+        cx, sx, cy, sy = np.cos(ax), np.sin(ax), np.cos(ay), np.sin(ay)
+        rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+        rz = np.array([[cy, -sy, 0], [sy, cy, 0], [0, 0, 1]])
+        r = rx @ rz @ t[:, :3]
+        c = W.camera_center(t)
+        return np.hstack([r, (-r @ c)[:, None]])
+    return tilt(ta, *rng.uniform(-0.3, 0.3, 2)), tilt(tb, *rng.uniform(-0.3, 0.3, 2))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_fundamental_epipolar_constraint(seed):
+    """Noise-free correspondences satisfy x_Q^T F x_T = 0; the transpose does not; the
+    8-point estimate (numpy SVD) of F agrees up to scale; F(T,Q) = F(Q,T)^T."""
+    rng = np.random.default_rng(seed)
+    tq, tt = _pose_pair(rng)
+    cam = W.CAM_EUROC
+    c = 0.5 * (W.camera_center(tq) + W.camera_center(tt))
+    pts = c + rng.normal(0, 1, (400, 3)) + np.array([0, 0, 8.0])
+    uq, vq, zq = W.project(tq, cam, pts)
+    ut, vt, zt = W.project(tt, cam, pts)
+    keep = (zq > 0) & (zt > 0)
+    xq = np.stack([uq, vq, np.ones_like(uq)], 1)[keep]
+    xt = np.stack([ut, vt, np.ones_like(ut)], 1)[keep]
+    F = O.fundamental(cam, tq, tt).astype(np.float64)
+    # residual as a distance to the epipolar line (pixels)
+    l = xq @ F
+    r = np.abs((l * xt).sum(1)) / np.hypot(l[:, 0], l[:, 1])
+    assert np.max(r) < 1e-2
+    lt = xq @ F.T
+    rt = np.abs((lt * xt).sum(1)) / np.hypot(lt[:, 0], lt[:, 1])
+    assert np.median(rt) > 1.0
+    A = np.stack([np.outer(a, b).ravel() for a, b in zip(xq, xt)])
+    f8 = np.linalg.svd(A)[2][-1].reshape(3, 3)
+    fn, f8n = F / np.linalg.norm(F), f8 / np.linalg.norm(f8)
+    if np.sum(fn * f8n) < 0:
+        f8n = -f8n
+    assert np.max(np.abs(fn - f8n)) < 1e-4
+    F2 = O.fundamental(cam, tt, tq).astype(np.float64)
+    np.testing.assert_allclose(F2, F.T, rtol=1e-5, atol=1e-7 * np.abs(F).max())
+
+
+def _line_distance_geometric(cam, tq, tt, xq, xt):
+    """Distance of x_T to the epipolar line of x_Q, built without F: project two points of
+    the viewing ray of x_Q (depths 1 and 1000) into T and measure point-to-line distance."""
+    a = W.backproject(tq, cam, xq[:, 0], xq[:, 1], np.full(len(xq), 1.0))
+    b = W.backproject(tq, cam, xq[:, 0], xq[:, 1], np.full(len(xq), 1000.0))
+    ua, va, _ = W.project(tt, cam, a)
+    ub, vb, _ = W.project(tt, cam, b)
+    dx, dy = ub - ua, vb - va
+    return np.abs(dx * (xt[:, 1] - va) - dy * (xt[:, 0] - ua)) / np.hypot(dx, dy)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_epipolar_gate_geometric(seed):
+    """One candidate per query: the oracle keeps exactly the candidates whose geometric
+    distance to the epipolar line is below sqrt(3.84)*1.2^level (ties within 1e-3 excused)."""
+    rng = np.random.default_rng(seed)
+    p = W.make_pair_cfg0(10 + seed, n_kp=600, n_planted=600)
+    cam, Q, T = p["cam"], p["Q"], p["T"]
+    iq, jt = p["planted"]
+    n = len(iq)
+    Qs = W.permute_keyframe(Q, iq)
+    Ts = W.permute_keyframe(T, jt)
+    Qs["node"] = np.arange(n, dtype=np.uint32)
+    Ts["node"] = np.arange(n, dtype=np.uint32)
+    # levels drawn independently in the two views, so that the sigma of the gate must come
+    # from the target keypoint
+    Qs["level"] = W.draw_levels(rng, n)
+    Ts["level"] = W.draw_levels(rng, n)
+    prm = O.SearchParams(hamming_max=256, ratio_num=0, resolve=False, rot_filter=False)
+    m, _ = O.search_pair(cam, Qs, Ts, params=prm)
+    passed = np.zeros(n, bool)
+    passed[m[:, 0]] = True
+    dist = _line_distance_geometric(cam, Q["Tcw"], T["Tcw"], Qs["xy"].astype(np.float64),
+                                    Ts["xy"].astype(np.float64))
+    thr = 3.84 * (1.2 ** (2 * Ts["level"].astype(np.float64)))
+    ratio = dist ** 2 / thr
+    expect = ratio < 1.0
+    near = np.abs(ratio - 1.0) < 1e-3
+    assert 0.2 < expect.mean() < 0.95
+    assert np.all(passed[~near] == expect[~near])
+
+
+# --------------------------------------------------------------------------- planted truth
+
+def _epi_pass_probability(p, rng, trials=400):
+    """Monte-Carlo P(epipolar pass) per planted pair from the generator's geometry with
+    fresh 2-px noise in both views (float64, no F)."""
+    cam, Q, T = p["cam"], p["Q"], p["T"]
+    iq, jt = p["planted"]
+    pts = p["points"][Q["wp"][iq]]
+    uq, vq, _ = W.project(Q["Tcw"], cam, pts)
+    ut, vt, _ = W.project(T["Tcw"], cam, pts)
+    lvl = T["level"][jt].astype(np.float64)
+    thr = 3.84 * 1.2 ** (2 * lvl)
+    hits = np.zeros(len(iq))
+    for _ in range(trials):
+        xq = np.stack([uq + rng.normal(0, 2, len(iq)), vq + rng.normal(0, 2, len(iq))], 1)
+        xt = np.stack([ut + rng.normal(0, 2, len(iq)), vt + rng.normal(0, 2, len(iq))], 1)
+        d = _line_distance_geometric(cam, Q["Tcw"], T["Tcw"], xq, xt)
+        hits += d ** 2 < thr
+    return hits / trials
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_planted_recovery(seed):
+    """cfg0: every accepted match is a planted pair (a random pair at Hamming <= 50 has
+    probability ~1e-22), and the number recovered agrees with 0.9 * P(epipolar pass)."""
+    p = W.make_pair_cfg0(seed)
+    m, ncmp = O.search_pair(p["cam"], p["Q"], p["T"])
+    iq, jt = p["planted"]
+    planted = set(zip(iq.tolist(), jt.tolist()))
+    assert all((int(a), int(b)) in planted for a, b, _ in m)
+    prob = 0.9 * _epi_pass_probability(p, np.random.default_rng(99 + seed))
+    mean, sd = prob.sum(), np.sqrt((prob * (1 - prob)).sum())
+    assert abs(len(m) - mean) < 4.5 * sd + 3, (len(m), mean, sd)
+    assert 300 < ncmp < 600  # ~ 0.9*200 + 500^2/1000
+
+
+def test_permutation_invariance():
+    """Relabelling the keypoints of either frame relabels the matches and nothing else."""
+    p = W.make_pair_cfg0(7)
+    cam, Q, T = p["cam"], p["Q"], p["T"]
+    m0, c0 = O.search_pair(cam, Q, T)
+    rng = np.random.default_rng(5)
+    pq, pt = rng.permutation(Q["n"]), rng.permutation(T["n"])
+    m1, c1 = O.search_pair(cam, W.permute_keyframe(Q, pq), W.permute_keyframe(T, pt))
+    back = sorted((int(pq[a]), int(pt[b]), int(d)) for a, b, d in m1)
+    assert back == sorted(map(tuple, m0.tolist()))
+    assert c0 == c1
+
+
+def test_step_invariants():
+    """cfg1: per pair each target at most once, d == numpy Hamming <= 50, same node, masks
+    respected, sorted by query, at most three rotation bins."""
+    w = W.make_cfg1()
+    st = w["steps"][0]
+    Q = w["frames"][st["q"]]
+    res, _ = O.search_step(w["cam"], w["frames"], st)
+    total = 0
+    for k, (f, m) in enumerate(zip(st["nbrs"], res)):
+        T = w["frames"][f]
+        total += len(m)
+        if not len(m):
+            continue
+        q, t, d = m.T
+        assert len(set(t.tolist())) == len(t) and np.all(np.diff(q) > 0)
+        assert np.all(d <= 50)
+        dd = np.bitwise_count(np.bitwise_xor(Q["desc"][q], T["desc"][t])).sum(1)
+        np.testing.assert_array_equal(dd, d)
+        assert np.all(Q["node"][q] == T["node"][t])
+        assert np.all(st["q_free"][q] == 1) and np.all(st["nbr_free"][k][t] == 1)
+        rot = np.mod(Q["angle"][q].astype(np.float64) - T["angle"][t], 360.0)
+        assert len(np.unique(np.floor(rot / 12.0) % 30)) <= 3
+        # planted truth: matches are the same world point
+        assert np.all(Q["wp"][q] == T["wp"][t]) and np.all(Q["wp"][q] >= 0)
+    assert total > 300
+
+
+# --------------------------------------------------------------------------- fusion
+
+def _fuse_geometry_f64(cam, T, mps):
+    """Projection gates and predicted level in float64, written from the pinhole model."""
+    R, t = T["Tcw"][:, :3], T["Tcw"][:, 3]
+    pos = mps["pos"].astype(np.float64)
+    pc = pos @ R.T + t
+    z = pc[:, 2]
+    with np.errstate(all="ignore"):
+        u = cam["fx"] * pc[:, 0] / z + cam["cx"]
+        v = cam["fy"] * pc[:, 1] / z + cam["cy"]
+    o = W.camera_center(T["Tcw"])
+    po = pos - o
+    dist = np.linalg.norm(po, axis=1)
+    cosv = (po * mps["normal"]).sum(1) / dist
+    ok = (z > 0) & (u >= 0) & (u < cam["width"]) & (v >= 0) & (v < cam["height"])
+    ok &= (dist >= mps["min_dist"]) & (dist <= mps["max_dist"]) & (cosv >= 0.5)
+    with np.errstate(all="ignore"):
+        pl = np.clip(np.ceil(np.log(mps["max_dist"] / dist) / np.log(1.2)), 0, 7).astype(int)
+    return ok, u, v, dist, cosv, pl
+
+
+def _random_mps(rng, T, cam, n):
+    o = W.camera_center(T["Tcw"])
+    R = T["Tcw"][:, :3]
+    d = rng.uniform(1, 12, n)
+    u = rng.uniform(-50, cam["width"] + 50, n)
+    v = rng.uniform(-50, cam["height"] + 50, n)
+    pos = W.backproject(T["Tcw"], cam, u, v, d * rng.choice([1, -1], n, p=[0.9, 0.1]))
+    view = pos - o
+    view /= np.linalg.norm(view, axis=1)[:, None]
+    nrm = view + rng.normal(0, 0.6, (n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    dist = np.linalg.norm(pos - o, axis=1)
+    mx = dist * 1.2 ** rng.uniform(-0.5, 7.5, n)
+    mn = mx / 1.2 ** 7 * rng.uniform(0.5, 1.5, n)
+    return dict(n=n, pos=pos.astype(np.float32), normal=nrm.astype(np.float32),
+                desc=W.random_desc(rng, n), min_dist=mn.astype(np.float32),
+                max_dist=mx.astype(np.float32), skip=(rng.random(n) < 0.1).astype(np.uint8))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fuse_gates_geometric(seed):
+    """With an unbounded window, chi2 and Hamming threshold, a map point yields a result
+    iff it passes the projection, distance and viewing-angle gates (float64 pinhole model;
+    cases within 1e-4 of a threshold excused), and the result is numpy's argmin of the
+    Hamming distance over keypoints at level pl-1 or pl."""
+    rng = np.random.default_rng(seed)
+    cam = W.CAM_EUROC
+    T = W.random_keyframe(rng, 400, cam, tcw=W.yaw_pose([0.2, 0.0, -0.1], 7.0))
+    mps = _random_mps(rng, T, cam, 3000)
+    m, ncmp = O.fuse(cam, T, mps, O.FuseParams(chi2=1e30, hamming_max=256, radius_scale=1e6))
+    ok, u, v, dist, cosv, pl = _fuse_geometry_f64(cam, T, mps)
+    ok &= mps["skip"] == 0
+    with np.errstate(all="ignore"):
+        lvl_f = np.log(mps["max_dist"] / dist) / np.log(1.2)
+    near = ((np.abs(u) < 1e-3) | (np.abs(u - cam["width"]) < 1e-3) |
+            (np.abs(v) < 1e-3) | (np.abs(v - cam["height"]) < 1e-3) |
+            (np.abs(dist / mps["min_dist"] - 1) < 1e-4) | (np.abs(dist / mps["max_dist"] - 1) < 1e-4) |
+            (np.abs(cosv - 0.5) < 1e-4) | (np.abs(lvl_f - np.round(lvl_f)) < 1e-4))
+    got = np.zeros(mps["n"], bool)
+    got[m[:, 0]] = True
+    assert np.all(got[~near] == ok[~near])
+    assert 0.1 < ok.mean() < 0.9
+    D = hamming_np(mps["desc"], T["desc"])
+    for mi, kj, d in m:
+        if near[mi]:
+            continue
+        allowed = (T["level"] == pl[mi]) | (T["level"] == pl[mi] - 1)
+        if not allowed.any():
+            continue
+        row = np.where(allowed, D[mi], 10 ** 6)
+        assert kj == int(row.argmin()) and d == int(row.min())
+
+
+def test_fuse_planted():
+    """cfg1: every fusion candidate joins a map point to a keypoint of the same world point
+    (a random descriptor pair at <= 50 is ~1e-22), and most fusable map points are found."""
+    w = W.make_cfg1()
+    st = w["steps"][0]
+    Q = w["frames"][st["q"]]
+    mps = st["mps"]
+    m, ncmp = O.fuse_step(w["cam"], w["frames"], st)
+    assert len(m) > 20
+    assert np.all(mps["wp"][m[:, 0]] == Q["wp"][m[:, 1]])
+    assert np.all(mps["skip"][m[:, 0]] == 0)
+    assert np.all(np.diff(m[:, 0]) > 0)
+    dd = np.bitwise_count(np.bitwise_xor(mps["desc"][m[:, 0]], Q["desc"][m[:, 1]])).sum(1)
+    np.testing.assert_array_equal(dd, m[:, 2])
