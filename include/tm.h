@@ -1,0 +1,277 @@
+/*
+ * tm -- GB300-native keypoint correspondence search and map-point fusion search for the
+ * local-mapping stage of visual SLAM (TurboMap, Hosseininejad et al., arXiv 2511.02036).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every function returns a tm_status; on failure
+ * tm_last_error() returns a thread-local message and no output is written, except where a
+ * function says otherwise (TM_ERR_CAPACITY reports the required size).
+ *
+ * Pointers marked "host or device" may point to pageable or pinned host memory or to device
+ * memory of the context's GPU (unified addressing decides).  `stream` is a cudaStream_t of the
+ * context's device, or NULL for the context's own stream.  Unless stated otherwise a call is
+ * synchronous: it returns after its results are in the caller's buffers, and inputs may be
+ * reused as soon as it returns.
+ *
+ * Units of work (Sec. IV):
+ *   keyframe store    Sec. IV-B: the immutable part of a keyframe (keypoints, descriptors,
+ *                     BoW nodes, pose) is copied to the GPU once, when the keyframe enters
+ *                     local mapping, and stays resident until it is removed.
+ *   search            Sec. IV-C: correspondence search of a new keyframe against each of its
+ *                     neighbours -- descriptor comparisons validated by the epipolar
+ *                     constraint, all neighbours in parallel, triangulation left to the caller.
+ *   fuse              Sec. IV-D: for each map point of a batch, the most similar keypoint of a
+ *                     keyframe within the projection window; merging is left to the caller.
+ *   batch / server    many local-mapping steps in one launch, and a continuous-batching loop.
+ *
+ * The matching rules (BoW buckets, Hamming <= 50, ratio 0.6, epipolar chi2 3.84 sigma^2,
+ * one match per target keypoint, 30-bin rotation histogram keeping the top three bins,
+ * window 3*scale with chi2 5.99 sigma^2) are not spelled out by the paper; they are the
+ * readings stated in the repository's design notes and are parameters below.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tm_status;
+#define TM_OK 0
+#define TM_ERR_INVALID_ARG 1 /* bad pointer, size or parameter                              */
+#define TM_ERR_NOT_FOUND 2   /* unknown keyframe id                                         */
+#define TM_ERR_EXISTS 3      /* keyframe id already stored                                  */
+#define TM_ERR_NO_MEMORY 4   /* store full (slots or memory budget) or device allocation    */
+#define TM_ERR_CAPACITY 5    /* output buffer too small; required sizes are reported        */
+#define TM_ERR_CUDA 6        /* CUDA runtime error (message in tm_last_error)               */
+#define TM_ERR_TIMEOUT 7     /* a bounded wait ran out                                      */
+#define TM_ERR_BUSY 8        /* keyframe referenced by a live plan; server queue full       */
+
+#define TM_DESC_BYTES 32       /* 256-bit binary descriptor                                 */
+#define TM_LEVELS 8            /* pyramid levels, scale factor 1.2                          */
+#define TM_MAX_KP_LIMIT 8192   /* largest per-keyframe keypoint capacity                    */
+
+typedef struct tm_ctx tm_ctx;
+typedef struct tm_plan tm_plan;
+typedef struct tm_server tm_server;
+
+/* Pinhole camera shared by all keyframes of a context. */
+typedef struct {
+    int32_t width, height; /* image size in pixels                                         */
+    double fx, fy, cx, cy; /* intrinsics in pixels                                         */
+} tm_camera;
+
+/* One keyframe's immutable data (Sec. IV-B), n keypoints in the caller's order.  Keypoint
+ * indices reported by every call refer to this order.  Arrays: host or device. */
+typedef struct {
+    int32_t n;              /* 0 .. max_kp of the context                                   */
+    const uint8_t *desc;    /* [n][32] descriptor bytes                                     */
+    const float *xy;        /* [n][2]  pixel coordinates                                    */
+    const float *angle;     /* [n]     orientation, degrees in [0, 360)                     */
+    const uint8_t *level;   /* [n]     pyramid level 0..7                                   */
+    const uint32_t *node;   /* [n]     BoW vocabulary node id                               */
+    double Tcw[12];         /* row-major 3x4 [R | t], world -> camera                       */
+} tm_keyframe_view;
+
+/* A batch of map points (Sec. IV-D: the map-point data a stage needs, gathered by the
+ * caller and transferred in one step).  Arrays: host or device. */
+typedef struct {
+    int32_t n;
+    const float *pos;       /* [n][3] world position                                        */
+    const float *normal;    /* [n][3] unit mean viewing direction                           */
+    const uint8_t *desc;    /* [n][32] representative descriptor                            */
+    const float *min_dist;  /* [n] scale-invariance distance range                          */
+    const float *max_dist;  /* [n]                                                          */
+    const uint8_t *skip;    /* [n] or NULL: 1 = already observed by the target keyframe     */
+} tm_mappoint_view;
+
+#define TM_MODE_FUSED 0      /* one CTA per pair, whole pipeline in shared memory (default) */
+#define TM_MODE_PER_PAIR 1   /* plain form: one pair at a time, one launch per stage        */
+
+typedef struct {
+    int32_t hamming_max;    /* accept best <= hamming_max (50)                              */
+    int32_t ratio_num;      /* accept ratio_den*best < ratio_num*second (3, 5);             */
+    int32_t ratio_den;      /*   ratio_num = 0 disables the ratio test                      */
+    float epi_chi2;         /* epipolar gate: dist^2 < epi_chi2 * 1.2^(2*level_T) (3.84)    */
+    int32_t epipolar;       /* 1 = apply the epipolar gate                                  */
+    int32_t resolve;        /* 1 = one match per target keypoint                            */
+    int32_t rot_filter;     /* 1 = 30-bin rotation-histogram filter                         */
+    int32_t mode;           /* TM_MODE_FUSED or TM_MODE_PER_PAIR                            */
+    int32_t lanes_per_query;/* 0 = autotuned; else 1, 2, 4, 8, 16 or 32                     */
+} tm_search_params;
+
+typedef struct {
+    float chi2;             /* reprojection gate e^2 <= chi2 * 1.2^(2*level) (5.99)         */
+    int32_t hamming_max;    /* (50)                                                         */
+    float radius_scale;     /* window half-width radius_scale * 1.2^predicted_level (3.0)   */
+} tm_fuse_params;
+
+/* A correspondence: keypoint q_idx of the new keyframe and t_idx of the neighbour. */
+typedef struct { int32_t q_idx, t_idx, dist; } tm_match;
+/* A fusion candidate: map point mp_idx (index within its batch) and keypoint kp_idx. */
+typedef struct { int32_t mp_idx, kp_idx, dist; } tm_fuse_match;
+
+typedef struct {
+    int32_t device, max_kp, slots_used, slots_free_in_budget;
+    size_t slot_bytes, bytes_reserved, budget_bytes;
+} tm_store_stats;
+
+/* Defaults: the readings of the design notes (50, 3/5, 3.84, all gates on, fused mode,
+ * autotuned lanes; 5.99, 50, 3.0). */
+void tm_search_params_default(tm_search_params *p);
+void tm_fuse_params_default(tm_fuse_params *p);
+
+/* ---------------------------------------------------------------------------- context
+ * Creates a context on `device` (made current for the calling thread).  max_kp (1 ..
+ * TM_MAX_KP_LIMIT) fixes the per-keyframe slot size.  mem_budget_bytes bounds the keyframe
+ * store; 0 = admit by the free device memory at the time of each allocation, keeping 1 GiB
+ * in reserve.  The context owns all device memory it allocates; destroy frees it. */
+tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max_kp,
+                        size_t mem_budget_bytes, tm_ctx **out);
+tm_status tm_ctx_destroy(tm_ctx *ctx);
+const char *tm_last_error(void);
+tm_status tm_store_get_stats(tm_ctx *ctx, tm_store_stats *out);
+
+/* ---------------------------------------------------------------------------- store (Sec. IV-B)
+ * Copies the keyframe into a device slot, then builds on the GPU its node-sorted keypoint
+ * order (BoW buckets) and its 64x48 projection-grid index.  TM_ERR_EXISTS if the id is
+ * stored, TM_ERR_NO_MEMORY if no slot fits the budget (nothing is stored then). */
+tm_status tm_store_add_keyframe(tm_ctx *ctx, uint64_t kf_id, const tm_keyframe_view *kf,
+                                void *stream);
+/* The same for n keyframes in one transfer and one launch; all or nothing. */
+tm_status tm_store_add_keyframes(tm_ctx *ctx, int32_t n, const uint64_t *kf_ids,
+                                 const tm_keyframe_view *kfs, void *stream);
+/* Frees the slot (Sec. IV-B: resident until removed).  TM_ERR_BUSY while a plan uses it. */
+tm_status tm_store_remove_keyframe(tm_ctx *ctx, uint64_t kf_id);
+/* Number of keypoints of a stored keyframe, or TM_ERR_NOT_FOUND. */
+tm_status tm_store_keyframe_size(tm_ctx *ctx, uint64_t kf_id, int32_t *n);
+
+/* ---------------------------------------------------------------------------- search (Sec. IV-C)
+ * Correspondence search of stored keyframe `kf` against stored neighbours nbrs[0..n_nbrs).
+ *   q_free    [n_Q] or NULL   1 = the keypoint has no map point yet (eligible)     host/device
+ *   nbr_free  [sum n_T] or NULL  the neighbours' masks concatenated in nbrs order  host/device
+ *   out       host buffer of cap matches; pair k occupies out[pair_offsets[k] ..
+ *             pair_offsets[k+1]), sorted by q_idx
+ *   pair_offsets  host [n_nbrs + 1]
+ *   n_comparisons host, optional: descriptor comparisons performed (same-node free pairs)
+ * On TM_ERR_CAPACITY *n_out holds the number of matches and nothing else is written. */
+tm_status tm_search_triangulation(tm_ctx *ctx, uint64_t kf, const uint64_t *nbrs,
+                                  int32_t n_nbrs, const tm_search_params *params,
+                                  const uint8_t *q_free, const uint8_t *nbr_free,
+                                  tm_match *out, size_t cap, size_t *n_out,
+                                  int32_t *pair_offsets, uint64_t *n_comparisons,
+                                  void *stream);
+
+/* ---------------------------------------------------------------------------- fuse (Sec. IV-D)
+ * Fusion search of the map points `mps` into stored keyframe `kf`: at most one candidate per
+ * map point, sorted by mp_idx.  Several map points may name the same keypoint; the caller's
+ * sequential merge decides.  n_comparisons counts (map point, keypoint) pairs inside the
+ * window at an admissible level. */
+tm_status tm_fuse(tm_ctx *ctx, uint64_t kf, const tm_mappoint_view *mps,
+                  const tm_fuse_params *params, tm_fuse_match *out, size_t cap,
+                  size_t *n_out, uint64_t *n_comparisons, void *stream);
+
+/* ---------------------------------------------------------------------------- batches
+ * Many local-mapping steps in one persistent launch.  Masks and map points of all steps are
+ * passed once, concatenated (one transfer each); a step names its ranges in them. */
+typedef struct {
+    uint64_t kf_id;          /* new keyframe (stored)                                       */
+    const uint64_t *nbr_ids; /* host [n_nbrs] stored neighbours                             */
+    int32_t n_nbrs;
+    int64_t q_free_off;      /* byte offset of the new keyframe's mask in masks, -1 = free  */
+    int64_t nbr_free_off;    /* byte offset of the neighbours' concatenated masks, -1 = free*/
+    int32_t mp_begin;        /* this step's map points are mps[mp_begin, mp_begin+mp_count) */
+    int32_t mp_count;        /*   fused into kf_id; 0 = no fusion                           */
+} tm_step;
+
+typedef struct {
+    const uint8_t *masks;    /* host or device, mask_bytes bytes (may be NULL if unused)    */
+    size_t mask_bytes;
+    tm_mappoint_view mps;    /* all steps' map points (n may be 0)                          */
+} tm_batch_inputs;
+
+/* Results, host buffers.  Search matches of all steps, step-major then neighbour order:
+ * pair p (counting pairs over all steps) is matches[pair_offsets[p] .. pair_offsets[p+1]).
+ * Fusion candidates of step s are fuse[fuse_offsets[s] .. fuse_offsets[s+1]), mp_idx
+ * relative to the step's mp_begin. */
+typedef struct {
+    tm_match *matches; size_t match_cap; size_t n_matches;
+    int32_t *pair_offsets;   /* [total pairs + 1]                                           */
+    tm_fuse_match *fuse; size_t fuse_cap; size_t n_fuse;
+    int32_t *fuse_offsets;   /* [n_steps + 1]                                               */
+    uint64_t n_comparisons_search, n_comparisons_fuse;
+} tm_batch_result;
+
+/* One-shot: upload, one persistent launch, download.  TM_ERR_CAPACITY sets n_matches and
+ * n_fuse to the required sizes and writes nothing else. */
+tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
+                       const tm_batch_inputs *in, const tm_search_params *sp,
+                       const tm_fuse_params *fp, tm_batch_result *res, void *stream);
+
+/* Prepared batch: uploads the inputs once and captures the launch in a CUDA graph; each
+ * tm_plan_run replays it (asynchronous on `stream`, results stay on the device until
+ * tm_plan_results).  The plan keeps its keyframes from being removed until destroyed. */
+tm_status tm_plan_create(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
+                         const tm_batch_inputs *in, const tm_search_params *sp,
+                         const tm_fuse_params *fp, tm_plan **out);
+tm_status tm_plan_run(tm_plan *plan, void *stream);
+tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
+/* Launch configuration the plan uses: threads per CTA, lanes per query, CTAs, kernels per run. */
+tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
+                       int32_t *kernels_per_run);
+tm_status tm_plan_destroy(tm_plan *plan);
+
+/* ---------------------------------------------------------------------------- serving
+ * Continuous batching.  A host thread admits submitted requests in arrival order as
+ * in-flight batch slots and store memory allow, ingests their keyframes, and launches
+ * each batch's search + fuse while earlier batches are still on the GPU (a ring of
+ * streams).  A request's neighbours must be stored or belong to earlier requests. */
+typedef struct {
+    int32_t max_batch_requests;   /* requests per launch (64)                               */
+    int32_t max_inflight_batches; /* batches on the GPU at once (3)                         */
+    int32_t queue_capacity;       /* pending requests before submit returns TM_ERR_BUSY     */
+    int32_t evict_after;          /* keep only the newest N keyframes of the stream, 0 = no */
+    tm_search_params search;
+    tm_fuse_params fuse;
+} tm_server_config;
+
+typedef struct {
+    uint64_t kf_id;
+    tm_keyframe_view kf;          /* copied at submit                                       */
+    const uint64_t *nbr_ids;      /* copied at submit                                       */
+    int32_t n_nbrs;
+    const uint8_t *q_free;        /* [n] or NULL, copied                                    */
+    const uint8_t *nbr_free;      /* [sum n_T] or NULL, copied                              */
+    tm_mappoint_view mps;         /* fused into kf_id; copied (host arrays)                 */
+} tm_request;
+
+typedef struct {
+    int32_t done;                 /* 1 when complete                                        */
+    tm_status status;
+    int32_t n_matches, n_fuse;
+    double t_submit, t_admit, t_done; /* seconds, monotonic clock                           */
+} tm_request_info;
+
+void tm_server_config_default(tm_server_config *c);
+tm_status tm_server_start(tm_ctx *ctx, const tm_server_config *cfg, tm_server **out);
+/* Host arrays only.  *ticket identifies the request. */
+tm_status tm_server_submit(tm_server *srv, const tm_request *req, uint64_t *ticket);
+/* Non-blocking status; timeout_s > 0 waits at most that long for completion. */
+tm_status tm_server_poll(tm_server *srv, uint64_t ticket, double timeout_s,
+                         tm_request_info *info);
+/* Copies a finished request's results (host buffers): matches [n_matches], pair_offsets
+ * [n_nbrs+1], fuse [n_fuse], then forgets the ticket. */
+tm_status tm_server_take(tm_server *srv, uint64_t ticket, tm_match *matches,
+                         int32_t *pair_offsets, tm_fuse_match *fuse);
+/* Drains the queue, stops the thread, frees the server. */
+tm_status tm_server_stop(tm_server *srv);
+
+/* Monotonic clock used by the server (seconds). */
+double tm_now(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,468 @@
+"""GB300-native correspondence search and map-point fusion search for visual-SLAM local
+mapping (TurboMap, arXiv 2511.02036, Sec. IV).
+
+Thin Python binding of the C ABI in include/tm.h: every `tm_*` name below is the C function
+itself (ctypes), and `Context` / `Plan` / `Server` only marshal numpy arrays or torch tensors
+into its structs.  All work runs in the CUDA library libtm.so; importing this package without
+it raises.  PyTorch is optional here: tensors are accepted for their device pointers and
+`torch.cuda.Stream.cuda_stream` for streams.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (TM_ERR_BUSY, TM_ERR_CAPACITY, TM_ERR_CUDA, TM_ERR_EXISTS,  # noqa: F401
+                   TM_ERR_INVALID_ARG, TM_ERR_NO_MEMORY, TM_ERR_NOT_FOUND, TM_ERR_TIMEOUT,
+                   TM_MODE_FUSED, TM_MODE_PER_PAIR, TM_OK, TM_MAX_KP_LIMIT)
+
+_clib = L.load()
+for _name in L.SIGNATURES:
+    globals()[_name] = getattr(_clib, _name)
+LIB_PATH = L.LIB_PATH
+
+
+class TMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tm status %d: %s" % (status, msg))
+        self.status = status
+
+
+def check(st):
+    if st != TM_OK:
+        raise TMError(st, _clib.tm_last_error().decode(errors="replace"))
+    return st
+
+
+# --------------------------------------------------------------------------- marshalling
+
+def _ptr(a):
+    """Address of a numpy array (host) or torch tensor (host or device); None stays None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _host(a, dtype):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def camera_struct(cam):
+    return L.tm_camera(int(cam["width"]), int(cam["height"]), float(cam["fx"]), float(cam["fy"]),
+                       float(cam["cx"]), float(cam["cy"]))
+
+
+def keyframe_view(kf, keep):
+    """tm_keyframe_view of a dict with desc, xy, angle, level, node (numpy or torch), Tcw."""
+    arrs = [_host(kf["desc"], np.uint8), _host(kf["xy"], np.float32), _host(kf["angle"], np.float32),
+            _host(kf["level"], np.uint8), _host(kf["node"], np.uint32)]
+    keep.extend(arrs)
+    v = L.tm_keyframe_view()
+    v.n = int(len(arrs[0]))
+    v.desc, v.xy, v.angle, v.level, v.node = (_ptr(a) for a in arrs)
+    v.Tcw[:] = [float(x) for x in np.asarray(kf["Tcw"], np.float64).reshape(12)]
+    return v
+
+
+def mappoint_view(mps, keep):
+    v = L.tm_mappoint_view()
+    if mps is None:
+        return v
+    arrs = [_host(mps["pos"], np.float32), _host(mps["normal"], np.float32), _host(mps["desc"], np.uint8),
+            _host(mps["min_dist"], np.float32), _host(mps["max_dist"], np.float32),
+            _host(mps.get("skip"), np.uint8)]
+    keep.extend(arrs)
+    v.n = int(mps["n"])
+    v.pos, v.normal, v.desc, v.min_dist, v.max_dist, v.skip = (_ptr(a) for a in arrs)
+    return v
+
+
+@dataclass
+class SearchParams:
+    hamming_max: int = 50
+    ratio_num: int = 3
+    ratio_den: int = 5
+    epi_chi2: float = 3.84
+    epipolar: bool = True
+    resolve: bool = True
+    rot_filter: bool = True
+    mode: int = TM_MODE_FUSED
+    lanes_per_query: int = 0
+
+    def struct(self):
+        return L.tm_search_params(self.hamming_max, self.ratio_num, self.ratio_den, self.epi_chi2,
+                                  int(self.epipolar), int(self.resolve), int(self.rot_filter),
+                                  int(self.mode), int(self.lanes_per_query))
+
+
+@dataclass
+class FuseParams:
+    chi2: float = 5.99
+    hamming_max: int = 50
+    radius_scale: float = 3.0
+
+    def struct(self):
+        return L.tm_fuse_params(self.chi2, self.hamming_max, self.radius_scale)
+
+
+def _split(arr, offsets):
+    return [arr[offsets[k]:offsets[k + 1]] for k in range(len(offsets) - 1)]
+
+
+def pack_batch(steps, kf_sizes):
+    """Concatenate the masks and map points of local-mapping steps into one batch.
+
+    steps: dicts with kf_id, nbrs (ids), optional q_free [n_Q], nbr_free (list of [n_T]),
+    optional mps (map-point dict).  kf_sizes: kf_id -> keypoint count.
+    Returns (tm_step array, masks uint8, concatenated map points dict, keep-alive list)."""
+    st = (L.tm_step * max(1, len(steps)))()
+    masks, keep = [], []
+    cols = {k: [] for k in ("pos", "normal", "desc", "min_dist", "max_dist", "skip")}
+    moff = mo = 0
+    any_skip = False
+    for k, s in enumerate(steps):
+        nb = np.ascontiguousarray(s["nbrs"], np.uint64)
+        keep.append(nb)
+        st[k].kf_id = int(s["kf_id"])
+        st[k].nbr_ids = nb.ctypes.data if len(nb) else None
+        st[k].n_nbrs = len(nb)
+        st[k].q_free_off = -1
+        st[k].nbr_free_off = -1
+        if s.get("q_free") is not None:
+            st[k].q_free_off = moff
+            masks.append(np.asarray(s["q_free"], np.uint8))
+            moff += len(masks[-1])
+        if s.get("nbr_free") is not None:
+            st[k].nbr_free_off = moff
+            for m in s["nbr_free"]:
+                masks.append(np.asarray(m, np.uint8))
+                moff += len(masks[-1])
+        mp = s.get("mps")
+        st[k].mp_begin = mo
+        st[k].mp_count = 0 if mp is None else int(mp["n"])
+        if mp is not None and mp["n"]:
+            for c in cols:
+                if c == "skip":
+                    sk = mp.get("skip")
+                    any_skip |= sk is not None
+                    cols[c].append(np.zeros(mp["n"], np.uint8) if sk is None else np.asarray(sk, np.uint8))
+                else:
+                    cols[c].append(np.asarray(mp[c]))
+            mo += int(mp["n"])
+    mask_arr = np.ascontiguousarray(np.concatenate(masks) if masks else np.zeros(0, np.uint8))
+    mps = dict(n=mo,
+               pos=np.ascontiguousarray(np.concatenate(cols["pos"]) if mo else np.zeros((0, 3)), np.float32),
+               normal=np.ascontiguousarray(np.concatenate(cols["normal"]) if mo else np.zeros((0, 3)), np.float32),
+               desc=np.ascontiguousarray(np.concatenate(cols["desc"]) if mo else np.zeros((0, 32)), np.uint8),
+               min_dist=np.ascontiguousarray(np.concatenate(cols["min_dist"]) if mo else np.zeros(0), np.float32),
+               max_dist=np.ascontiguousarray(np.concatenate(cols["max_dist"]) if mo else np.zeros(0), np.float32),
+               skip=np.ascontiguousarray(np.concatenate(cols["skip"]), np.uint8) if (mo and any_skip) else None)
+    return st, mask_arr, mps, keep
+
+
+class BatchResult:
+    """Results of a batch: per pair (in step then neighbour order) an int32 (k, 3) array of
+    (q_idx, t_idx, dist); per step an int32 (k, 3) array of (mp_idx, kp_idx, dist)."""
+
+    def __init__(self, matches, pair_offsets, fuse, fuse_offsets, ncmp_search, ncmp_fuse):
+        self.matches = matches
+        self.pair_offsets = pair_offsets
+        self.fuse = fuse
+        self.fuse_offsets = fuse_offsets
+        self.pairs = _split(matches, pair_offsets)
+        self.fuses = _split(fuse, fuse_offsets)
+        self.n_comparisons_search = ncmp_search
+        self.n_comparisons_fuse = ncmp_fuse
+
+
+def _result_struct(match_cap, n_pairs, fuse_cap, n_steps):
+    m = np.zeros((max(1, match_cap), 3), np.int32)
+    po = np.zeros(n_pairs + 1, np.int32)
+    f = np.zeros((max(1, fuse_cap), 3), np.int32)
+    fo = np.zeros(n_steps + 1, np.int32)
+    r = L.tm_batch_result()
+    r.matches, r.match_cap, r.pair_offsets = m.ctypes.data, match_cap, po.ctypes.data
+    r.fuse, r.fuse_cap, r.fuse_offsets = f.ctypes.data, fuse_cap, fo.ctypes.data
+    return r, (m, po, f, fo)
+
+
+def _collect(r, bufs):
+    m, po, f, fo = bufs
+    return BatchResult(m[:r.n_matches].copy(), po.copy(), f[:r.n_fuse].copy(), fo.copy(),
+                       int(r.n_comparisons_search), int(r.n_comparisons_fuse))
+
+
+def _result_caps(steps, kf_sizes, resolve=True):
+    mc = 0
+    for s in steps:
+        nq = kf_sizes[int(s["kf_id"])]
+        for t in s["nbrs"]:
+            nt = kf_sizes[int(t)]
+            mc += min(nq, nt) if resolve else nq
+    fc = sum(int(s["mps"]["n"]) for s in steps if s.get("mps") is not None)
+    return mc, fc
+
+
+class Context:
+    """A tm_ctx: one GPU, one camera, a keyframe store of max_kp-keypoint slots."""
+
+    def __init__(self, cam, max_kp=4096, budget=0, device=0):
+        self.cam = dict(cam)
+        self.max_kp = max_kp
+        h = ctypes.c_void_p()
+        c = camera_struct(cam)
+        check(tm_ctx_create(device, ctypes.byref(c), max_kp, budget, ctypes.byref(h)))  # noqa: F821
+        self.handle = h
+        self.sizes = {}
+
+    def close(self):
+        if self.handle:
+            check(tm_ctx_destroy(self.handle))  # noqa: F821
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- store
+    def add_keyframe(self, kf_id, kf, stream=None):
+        keep = []
+        v = keyframe_view(kf, keep)
+        check(tm_store_add_keyframe(self.handle, int(kf_id), ctypes.byref(v), _stream(stream)))  # noqa: F821
+        self.sizes[int(kf_id)] = v.n
+
+    def add_keyframes(self, ids, kfs, stream=None):
+        keep = []
+        n = len(ids)
+        views = (L.tm_keyframe_view * max(1, n))()
+        for k, kf in enumerate(kfs):
+            views[k] = keyframe_view(kf, keep)
+        idarr = np.ascontiguousarray(ids, np.uint64)
+        check(tm_store_add_keyframes(self.handle, n, idarr.ctypes.data, views, _stream(stream)))  # noqa: F821
+        for k in range(n):
+            self.sizes[int(ids[k])] = views[k].n
+
+    def remove_keyframe(self, kf_id):
+        check(tm_store_remove_keyframe(self.handle, int(kf_id)))  # noqa: F821
+        self.sizes.pop(int(kf_id), None)
+
+    def keyframe_size(self, kf_id):
+        n = ctypes.c_int32()
+        check(tm_store_keyframe_size(self.handle, int(kf_id), ctypes.byref(n)))  # noqa: F821
+        return n.value
+
+    def stats(self):
+        s = L.tm_store_stats()
+        check(tm_store_get_stats(self.handle, ctypes.byref(s)))  # noqa: F821
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    # ---------------------------------------------------------------- search / fuse
+    def search(self, kf_id, nbrs, q_free=None, nbr_free=None, params=None, stream=None):
+        """Per-pair match arrays (q_idx, t_idx, dist) in neighbour order, and the number of
+        descriptor comparisons."""
+        p = (params or SearchParams()).struct()
+        nb = np.ascontiguousarray(nbrs, np.uint64)
+        # result capacity from the known sizes; unknown ids are reported by the C call
+        nq = self.sizes.get(int(kf_id), self.max_kp)
+        cap = sum(min(nq, self.sizes.get(int(t), self.max_kp)) if p.resolve else nq for t in nb)
+        out = np.zeros((max(1, cap), 3), np.int32)
+        po = np.zeros(len(nb) + 1, np.int32)
+        n_out, ncmp = ctypes.c_size_t(), ctypes.c_uint64()
+        qf = _host(q_free, np.uint8)
+        if nbr_free is not None and isinstance(nbr_free, (list, tuple)):
+            nbr_free = np.concatenate([np.asarray(m, np.uint8) for m in nbr_free]) if len(nbr_free) else None
+        nf = _host(nbr_free, np.uint8)
+        check(tm_search_triangulation(self.handle, int(kf_id), nb.ctypes.data if len(nb) else None,  # noqa: F821
+                                      len(nb), ctypes.byref(p), _ptr(qf), _ptr(nf), out.ctypes.data,
+                                      cap, ctypes.byref(n_out), po.ctypes.data, ctypes.byref(ncmp),
+                                      _stream(stream)))
+        return _split(out[:n_out.value].copy(), po), int(ncmp.value)
+
+    def fuse(self, kf_id, mps, params=None, stream=None):
+        p = (params or FuseParams()).struct()
+        keep = []
+        v = mappoint_view(mps, keep)
+        out = np.zeros((max(1, v.n), 3), np.int32)
+        n_out, ncmp = ctypes.c_size_t(), ctypes.c_uint64()
+        check(tm_fuse(self.handle, int(kf_id), ctypes.byref(v), ctypes.byref(p), out.ctypes.data,  # noqa: F821
+                      v.n, ctypes.byref(n_out), ctypes.byref(ncmp), _stream(stream)))
+        return out[:n_out.value].copy(), int(ncmp.value)
+
+    # ---------------------------------------------------------------- batches
+    def _inputs(self, steps, masks=None, mps=None):
+        keep = []
+        if masks is None and mps is None:
+            st, masks, mps, k2 = pack_batch(steps, self.sizes)
+            keep.extend(k2)
+        else:
+            st = (L.tm_step * max(1, len(steps)))()
+            for k, s in enumerate(steps):
+                nb = np.ascontiguousarray(s["nbrs"], np.uint64)
+                keep.append(nb)
+                st[k].kf_id, st[k].nbr_ids, st[k].n_nbrs = int(s["kf_id"]), nb.ctypes.data if len(nb) else None, len(nb)
+                st[k].q_free_off = s.get("q_free_off", -1)
+                st[k].nbr_free_off = s.get("nbr_free_off", -1)
+                st[k].mp_begin, st[k].mp_count = s.get("mp_begin", 0), s.get("mp_count", 0)
+        inp = L.tm_batch_inputs()
+        keep.append(masks)
+        inp.masks = _ptr(masks) if masks is not None and len(masks) else None
+        inp.mask_bytes = 0 if masks is None else int(np.prod(masks.shape)) if isinstance(masks, np.ndarray) else masks.numel()
+        inp.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
+        keep.append(st)
+        return st, inp, keep
+
+    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None):
+        """One-shot batch (tm_batch_run).  Without masks/mps the steps carry their own
+        q_free / nbr_free / mps and are packed here."""
+        sp = sp or SearchParams()
+        st, inp, keep = self._inputs(steps, masks, mps)
+        mc, fc = _result_caps(steps, self.sizes, sp.resolve)
+        if masks is not None or mps is not None:
+            fc = max(fc, int(mps["n"]) if mps is not None else 0)
+        r, bufs = _result_struct(mc, sum(len(s["nbrs"]) for s in steps), fc, len(steps))
+        sps, fps = sp.struct(), (fp or FuseParams()).struct()
+        check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
+                           ctypes.byref(fps), ctypes.byref(r), _stream(stream)))
+        return _collect(r, bufs)
+
+    def plan(self, steps, masks=None, mps=None, sp=None, fp=None):
+        return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams())
+
+    def server(self, **cfg):
+        return Server(self, **cfg)
+
+
+class Plan:
+    """A prepared batch (tm_plan): inputs resident on the GPU, launch captured in a graph."""
+
+    def __init__(self, ctx, steps, masks, mps, sp, fp):
+        self.ctx = ctx
+        st, inp, self._keep = ctx._inputs(steps, masks, mps)
+        self.caps = _result_caps(steps, ctx.sizes, sp.resolve)
+        if mps is not None:
+            self.caps = (self.caps[0], max(self.caps[1], int(mps["n"])))
+        self.n_pairs = sum(len(s["nbrs"]) for s in steps)
+        self.n_steps = len(steps)
+        h = ctypes.c_void_p()
+        sps, fps = sp.struct(), fp.struct()
+        check(tm_plan_create(ctx.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
+                             ctypes.byref(fps), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        check(tm_plan_run(self.handle, _stream(stream)))  # noqa: F821
+
+    def results(self, stream=None):
+        r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps)
+        check(tm_plan_results(self.handle, ctypes.byref(r), _stream(stream)))  # noqa: F821
+        return _collect(r, bufs)
+
+    def info(self):
+        a, b, c, d = (ctypes.c_int32() for _ in range(4))
+        check(tm_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),  # noqa: F821
+                           ctypes.byref(d)))
+        return dict(threads=a.value, lanes=b.value, ctas=c.value, kernels_per_run=d.value)
+
+    def close(self):
+        if self.handle:
+            check(tm_plan_destroy(self.handle))  # noqa: F821
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server (tm_server_*)."""
+
+    def __init__(self, ctx, max_batch_requests=64, max_inflight_batches=3, queue_capacity=1 << 16,
+                 evict_after=0, sp=None, fp=None):
+        self.ctx = ctx
+        c = L.tm_server_config()
+        tm_server_config_default(ctypes.byref(c))  # noqa: F821
+        c.max_batch_requests, c.max_inflight_batches = max_batch_requests, max_inflight_batches
+        c.queue_capacity, c.evict_after = queue_capacity, evict_after
+        if sp is not None:
+            c.search = sp.struct()
+        if fp is not None:
+            c.fuse = fp.struct()
+        h = ctypes.c_void_p()
+        check(tm_server_start(ctx.handle, ctypes.byref(c), ctypes.byref(h)))  # noqa: F821
+        self.handle = h
+        self.meta = {}
+
+    def submit(self, kf_id, kf, nbrs, q_free=None, nbr_free=None, mps=None):
+        keep = []
+        r = L.tm_request()
+        r.kf_id = int(kf_id)
+        r.kf = keyframe_view(kf, keep)
+        nb = np.ascontiguousarray(nbrs, np.uint64)
+        r.nbr_ids, r.n_nbrs = (nb.ctypes.data if len(nb) else None), len(nb)
+        qf = _host(q_free, np.uint8)
+        if nbr_free is not None and isinstance(nbr_free, (list, tuple)):
+            nbr_free = np.concatenate([np.asarray(m, np.uint8) for m in nbr_free]) if len(nbr_free) else None
+        nf = _host(nbr_free, np.uint8)
+        r.q_free, r.nbr_free = _ptr(qf), _ptr(nf)
+        r.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
+        t = ctypes.c_uint64()
+        check(tm_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))  # noqa: F821
+        self.meta[t.value] = (len(nb),)
+        self.ctx.sizes[int(kf_id)] = r.kf.n
+        return t.value
+
+    def poll(self, ticket, timeout=0.0):
+        info = L.tm_request_info()
+        st = tm_server_poll(self.handle, ticket, float(timeout), ctypes.byref(info))  # noqa: F821
+        if st not in (TM_OK, TM_ERR_TIMEOUT):
+            check(st)
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def take(self, ticket):
+        """Waits for the request and returns (per-pair match arrays, fusion array, info)."""
+        info = self.poll(ticket, timeout=600.0)
+        if not info["done"]:
+            raise TMError(TM_ERR_TIMEOUT, "request %d not done" % ticket)
+        n_nbrs = self.meta.pop(ticket)[0]
+        m = np.zeros((max(1, info["n_matches"]), 3), np.int32)
+        po = np.zeros(n_nbrs + 1, np.int32)
+        f = np.zeros((max(1, info["n_fuse"]), 3), np.int32)
+        check(tm_server_take(self.handle, ticket, m.ctypes.data, po.ctypes.data, f.ctypes.data))  # noqa: F821
+        return _split(m[:info["n_matches"]], po), f[:info["n_fuse"]], info
+
+    def close(self):
+        if self.handle:
+            check(tm_server_stop(self.handle))  # noqa: F821
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,877 @@
+// Kernels of the local-mapping search path for sm_103a.
+//
+//   ingest_kernel      Sec. IV-B  keyframe enters the store: sort keypoints by BoW node,
+//                                 build the 64x48 projection-grid index (one CTA per KF)
+//   batch_kernel       Sec. IV-C  correspondence search, one CTA per (new KF, neighbour) pair:
+//                                 node join -> Hamming + epipolar gate -> best/second ->
+//                                 one match per target -> rotation histogram -> ordered
+//                                 compaction, all in shared memory
+//                      Sec. IV-D  fusion search, one thread per map point: projection gates ->
+//                                 grid window -> reprojection gate -> best Hamming
+//   copy_kernel                   gathers the per-item regions into one dense array
+//   pair_* / fuse_*    plain form: one pair per launch sequence, global scratch
+//
+// Floating point: every gate is evaluated with explicit round-to-nearest intrinsics in the
+// order stated next to it (no contraction, IEEE division and square root), so that a
+// decision equals the one of a plain float32 evaluation of the same expression.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace tmap {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------------- arithmetic
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Pyramid scale of a level: 1.2^l by repeated float multiplication.
+__device__ __forceinline__ float level_scale(int l) {
+    float s = 1.0f;
+    for (int k = 0; k < l; ++k) s = fmul(s, 1.2f);
+    return s;
+}
+
+// C = A*B for 3x3 float64, each entry summed over k = 0, 1, 2 in that order.
+__device__ void mat3_mul(const double *A, const double *B, double *C) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = dmul(A[r * 3 + 0], B[0 * 3 + c]);
+            s = dadd(s, dmul(A[r * 3 + 1], B[1 * 3 + c]));
+            s = dadd(s, dmul(A[r * 3 + 2], B[2 * 3 + c]));
+            C[r * 3 + c] = s;
+        }
+}
+
+// Fundamental matrix of the pair (Sec. IV-C epipolar validation): relative motion
+// R = R_Q R_T^T, t = t_Q - R t_T; F = K^-T [t]x R K^-1 in float64, products evaluated
+// ((K^-T [t]x) R) K^-1, each entry rounded to float32.  x_Q^T F x_T = 0.
+__device__ void fundamental_f32(const CamConst &cam, const double *Tq, const double *Tt,
+                                float *F) {
+    double Rq[9], RtT[9], tq[3], tt[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            Rq[r * 3 + c] = Tq[r * 4 + c];
+            RtT[c * 3 + r] = Tt[r * 4 + c];
+        }
+        tq[r] = Tq[r * 4 + 3];
+        tt[r] = Tt[r * 4 + 3];
+    }
+    double R[9];
+    mat3_mul(Rq, RtT, R);
+    double t[3];
+    for (int r = 0; r < 3; ++r) {
+        double s = dmul(R[r * 3 + 0], tt[0]);
+        s = dadd(s, dmul(R[r * 3 + 1], tt[1]));
+        s = dadd(s, dmul(R[r * 3 + 2], tt[2]));
+        t[r] = dsub(tq[r], s);
+    }
+    const double tx[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
+    const double Kinv[9] = {__ddiv_rn(1.0, cam.fx), 0.0, __ddiv_rn(-cam.cx, cam.fx),
+                            0.0, __ddiv_rn(1.0, cam.fy), __ddiv_rn(-cam.cy, cam.fy),
+                            0.0, 0.0, 1.0};
+    double KinvT[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) KinvT[r * 3 + c] = Kinv[c * 3 + r];
+    double A[9], B[9], Fd[9];
+    mat3_mul(KinvT, tx, A);
+    mat3_mul(A, R, B);
+    mat3_mul(B, Kinv, Fd);
+    for (int k = 0; k < 9; ++k) F[k] = __double2float_rn(Fd[k]);
+}
+
+// Epipolar line of a query in the target image: l = F^T x_Q = (a, b, c).
+struct Line { float a, b, c; };
+__device__ __forceinline__ Line epi_line(const float *F, float xq, float yq) {
+    Line l;
+    l.a = fadd(fadd(fmul(xq, F[0]), fmul(yq, F[3])), F[6]);
+    l.b = fadd(fadd(fmul(xq, F[1]), fmul(yq, F[4])), F[7]);
+    l.c = fadd(fadd(fmul(xq, F[2]), fmul(yq, F[5])), F[8]);
+    return l;
+}
+// dist^2 = num^2 / (a^2 + b^2) < thr, division-free: num^2 < thr * den.
+__device__ __forceinline__ bool epi_pass(const Line &l, float xt, float yt, float thr) {
+    const float num = fadd(fadd(fmul(l.a, xt), fmul(l.b, yt)), l.c);
+    const float den = fadd(fmul(l.a, l.a), fmul(l.b, l.b));
+    return den > 0.0f && fmul(num, num) < fmul(thr, den);
+}
+
+// Rotation bin: 30 bins of 12 degrees over angle_Q - angle_T wrapped into [0, 360).
+__device__ __forceinline__ int rot_bin(float aq, float at) {
+    float rot = fsub(aq, at);
+    if (rot < 0.0f) rot = fadd(rot, 360.0f);
+    int bin = (int)floorf(__fdiv_rn(rot, 12.0f));
+    if (bin >= kBins || bin < 0) bin = 0;  // (< 0 only for angles outside [0, 360))
+    return bin;
+}
+
+__device__ __forceinline__ int hamming(const uint4 &a0, const uint4 &a1, const uint4 &b0,
+                                       const uint4 &b1) {
+    return __popc(a0.x ^ b0.x) + __popc(a0.y ^ b0.y) + __popc(a0.z ^ b0.z) +
+           __popc(a0.w ^ b0.w) + __popc(a1.x ^ b1.x) + __popc(a1.y ^ b1.y) +
+           __popc(a1.z ^ b1.z) + __popc(a1.w ^ b1.w);
+}
+
+__device__ __forceinline__ int grid_cell(float v, float inv, int n) {
+    float f = floorf(fmul(v, inv));
+    f = fminf(fmaxf(f, 0.0f), float(n - 1));
+    return int(f);
+}
+
+template <typename P>
+__device__ __forceinline__ int lower_bound_u32(P a, int n, uint32_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+template <typename P>
+__device__ __forceinline__ int upper_bound_u32(P a, int lo, int n, uint32_t key) {
+    int hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive position of this thread's flag among the flags of the block (thread order),
+// and the block total.  Every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_scan_flag(bool flag, uint32_t *wtot, uint32_t &total) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned ball = __ballot_sync(kFull, flag);
+    const uint32_t pre = __popc(ball & ((1u << lane) - 1u));
+    if (lane == 0) wtot[warp] = __popc(ball);
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < nw ? wtot[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        if (lane < nw) wtot[lane] = v;
+    }
+    __syncthreads();
+    const uint32_t base = warp ? wtot[warp - 1] : 0u;
+    total = wtot[nw - 1];
+    __syncthreads();
+    return base + pre;
+}
+
+// Top-3 rotation bins as a bit mask (ties to the lower bin, empty bins never taken,
+// 2nd/3rd dropped when 10*count < count of the 1st).
+__device__ uint32_t top3_mask(const uint32_t *hist) {
+    int top[3] = {-1, -1, -1};
+    for (int r = 0; r < 3; ++r) {
+        int best = -1;
+        for (int b = 0; b < kBins; ++b) {
+            if (hist[b] == 0 || b == top[0] || b == top[1]) continue;
+            if (best < 0 || hist[b] > hist[best]) best = b;
+        }
+        top[r] = best;
+    }
+    uint32_t mask = 0;
+    if (top[0] >= 0) {
+        const uint32_t mx = hist[top[0]];
+        mask |= 1u << top[0];
+        for (int r = 1; r < 3; ++r)
+            if (top[r] >= 0 && !(10u * hist[top[r]] < mx)) mask |= 1u << top[r];
+    }
+    return mask;
+}
+
+// Packed per-query result: target (13 bits), distance (9 bits), rotation bin (5 bits).
+__device__ __forceinline__ uint32_t pack_res(uint32_t t, uint32_t d, uint32_t bin) {
+    return (t << 14) | (d << 5) | bin;
+}
+
+// ------------------------------------------------------------------------- ingest
+
+__device__ void bitonic_sort_u64(unsigned long long *a, int N) {
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = a[i], y = a[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+__device__ void bitonic_sort_u32(uint32_t *a, int N) {
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint32_t x = a[i], y = a[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
+    extern __shared__ unsigned long long skeys[];
+    const IngestJob &job = A.jobs[blockIdx.x];
+    const int n = job.n;
+    int N = 1;
+    while (N < n) N <<= 1;
+    const SlotLayout L = SlotLayout::make(A.cap);
+    unsigned char *base = job.slot;
+    // 1. stable sort by node: key = node << 32 | caller index
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        skeys[i] = i < n ? ((unsigned long long)A.node[job.src + i] << 32) | (unsigned)i
+                         : ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(skeys, N);
+    // 2. gather the keypoint arrays into node order
+    uint4 *desc = reinterpret_cast<uint4 *>(base + L.desc);
+    float2 *xy = reinterpret_cast<float2 *>(base + L.xy);
+    float *angle = reinterpret_cast<float *>(base + L.angle);
+    uint32_t *node = reinterpret_cast<uint32_t *>(base + L.node);
+    uint16_t *orig = reinterpret_cast<uint16_t *>(base + L.orig);
+    uint8_t *level = base + L.level;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const uint32_t o = (uint32_t)(skeys[p] & 0xFFFFFFFFull);
+        const uint32_t s = job.src + o;
+        desc[2 * p] = A.desc[2 * s];
+        desc[2 * p + 1] = A.desc[2 * s + 1];
+        xy[p] = A.xy[s];
+        angle[p] = A.angle[s];
+        node[p] = A.node[s];
+        orig[p] = (uint16_t)o;
+        const uint8_t lv = A.level[s];
+        level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
+    }
+    __syncthreads();
+    // 3. projection grid: sort (cell, sorted position), then cell starts by binary search
+    uint32_t *ck = reinterpret_cast<uint32_t *>(skeys);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        uint32_t key = kNone;
+        if (i < n) {
+            const float2 v = xy[i];
+            const int cx = grid_cell(v.x, A.cell_w_inv, kGridCols);
+            const int cy = grid_cell(v.y, A.cell_h_inv, kGridRows);
+            key = ((uint32_t)(cy * kGridCols + cx) << 16) | (uint32_t)i;
+        }
+        ck[i] = key;
+    }
+    __syncthreads();
+    bitonic_sort_u32(ck, N);
+    uint16_t *gitems = reinterpret_cast<uint16_t *>(base + L.grid_items);
+    uint16_t *gstart = reinterpret_cast<uint16_t *>(base + L.grid_start);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) gitems[k] = (uint16_t)(ck[k] & 0xFFFFu);
+    for (int c = threadIdx.x; c <= kGridCells; c += blockDim.x)
+        gstart[c] = (uint16_t)lower_bound_u32(ck, n, (uint32_t)c << 16);
+    if (threadIdx.x == 0) {
+        KfHeader *h = reinterpret_cast<KfHeader *>(base);
+        h->n = n;
+        h->cap = A.cap;
+        for (int k = 0; k < 12; ++k) h->Tcw[k] = job.Tcw[k];
+    }
+}
+
+// ------------------------------------------------------------------------- batch kernel
+
+struct ItemShared {
+    uint32_t hist[32];
+    uint32_t wtot[32];
+    float F[9];
+    float thr[kLevels];
+    float scale[kLevels];
+    float R[9], t[3], O[3];
+    uint32_t keep;
+    uint32_t item;
+    unsigned long long cmp;
+};
+
+// One (new keyframe, neighbour) pair.  Shared arrays (stride sn = max keypoints):
+//   tnode[sn]  neighbour's node ids (sorted)    win[sn]  per target: lowest (d << 16 | q)
+//   accq[sn]   per sorted query: (t << 16 | d)  res[sn]  per caller-order query: packed kept
+template <int G>
+__device__ void search_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
+                            uint32_t *sm, int sn, ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
+    const int nQ = Q.hdr->n, nT = T.hdr->n;
+    uint32_t *tnode = sm, *win = sm + sn, *accq = sm + 2 * sn, *res = sm + 3 * sn;
+    const int tid = threadIdx.x, bs = blockDim.x;
+
+    if (tid == 0) {
+        fundamental_f32(A.cam, Q.hdr->Tcw, T.hdr->Tcw, S.F);
+        S.cmp = 0ull;
+    }
+    if (tid < 32) S.hist[tid] = 0;
+    if (tid < kLevels) {
+        const float s = level_scale(tid);
+        S.thr[tid] = fmul(A.sp.epi_chi2, fmul(s, s));
+    }
+    for (int j = tid; j < nT; j += bs) { tnode[j] = T.node[j]; win[j] = kNone; }
+    for (int i = tid; i < nQ; i += bs) res[i] = kNone;
+    __syncthreads();
+
+    const uint8_t *mq = w.a == kNone ? nullptr : A.masks + w.a;
+    const uint8_t *mt = w.b == kNone ? nullptr : A.masks + w.b;
+    const bool epi = A.sp.epipolar != 0;
+
+    // Join + match: G lanes per query, node-sorted queries in consecutive groups.
+    const int gpc = bs / G, g = tid / G, sub = tid % G;
+    unsigned long long my_cmp = 0;
+    for (int p0 = 0; p0 < nQ; p0 += gpc) {
+        const int p = p0 + g;
+        uint32_t bkey = kNone;   // (dist << 16) | sorted target
+        uint32_t sec = 0xFFFFu;  // second-smallest distance
+        if (p < nQ && (!mq || mq[Q.orig[p]])) {
+            const uint32_t nd = Q.node[p];
+            const int lo = lower_bound_u32(tnode, nT, nd);
+            const int hi = (lo < nT && tnode[lo] == nd) ? upper_bound_u32(tnode, lo, nT, nd) : lo;
+            if (lo < hi) {
+                const uint4 q0 = Q.desc[2 * p], q1 = Q.desc[2 * p + 1];
+                const float2 xq = Q.xy[p];
+                const Line l = epi_line(S.F, xq.x, xq.y);
+                for (int j = lo + sub; j < hi; j += G) {
+                    if (mt && !mt[T.orig[j]]) continue;
+                    ++my_cmp;
+                    const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
+                    const uint32_t d = (uint32_t)hamming(q0, q1, t0, t1);
+                    if (epi) {
+                        const float2 xt = T.xy[j];
+                        if (!epi_pass(l, xt.x, xt.y, S.thr[T.level[j]])) continue;
+                    }
+                    const uint32_t key = (d << 16) | (uint32_t)j;
+                    if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
+                    else sec = min(sec, d);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            const uint32_t ob = __shfl_xor_sync(kFull, bkey, off);
+            const uint32_t os = __shfl_xor_sync(kFull, sec, off);
+            sec = min(min(sec, os), max(bkey, ob) >> 16);
+            bkey = min(bkey, ob);
+        }
+        if (sub == 0 && p < nQ) {
+            uint32_t acc = kNone;
+            if (bkey != kNone) {
+                const uint32_t best = bkey >> 16;
+                bool ok = (int)best <= A.sp.hamming_max;
+                if (ok && A.sp.ratio_num != 0 && sec != 0xFFFFu)
+                    ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sec;
+                if (ok) {
+                    const uint32_t j = bkey & 0xFFFFu;
+                    acc = (j << 16) | best;
+                    if (A.sp.resolve) atomicMin(&win[j], (best << 16) | Q.orig[p]);
+                }
+            }
+            accq[p] = acc;
+        }
+    }
+    if (my_cmp) atomicAdd(&S.cmp, my_cmp);
+    __syncthreads();
+
+    // One match per target, rotation histogram.
+    const bool rot = A.sp.rot_filter != 0;
+    for (int p = tid; p < nQ; p += bs) {
+        const uint32_t acc = accq[p];
+        if (acc == kNone) continue;
+        const uint32_t j = acc >> 16, d = acc & 0xFFFFu, io = Q.orig[p];
+        if (A.sp.resolve && win[j] != ((d << 16) | io)) continue;
+        uint32_t bin = 0;
+        if (rot) {
+            bin = (uint32_t)rot_bin(Q.angle[p], T.angle[j]);
+            atomicAdd(&S.hist[bin], 1u);
+        }
+        res[io] = pack_res(T.orig[j], d, bin);
+    }
+    __syncthreads();
+    if (tid == 0) S.keep = rot ? top3_mask(S.hist) : kNone;
+    __syncthreads();
+    const uint32_t keep = S.keep;
+
+    // Ordered compaction (caller's query order) into this item's region.
+    uint32_t base = 0;
+    for (int i0 = 0; i0 < nQ; i0 += bs) {
+        const int i = i0 + tid;
+        const uint32_t r = i < nQ ? res[i] : kNone;
+        const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
+        uint32_t tot;
+        const uint32_t pos = block_scan_flag(f, S.wtot, tot);
+        if (f) A.padded[w.out_off + base + pos] = Out3{i, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
+        base += tot;
+    }
+    if (tid == 0) {
+        A.counts[idx] = base;
+        if (S.cmp) atomicAdd(&A.ncmp[0], S.cmp);
+    }
+}
+
+// Fusion of up to blockDim map points into one keyframe, one thread per map point.
+// Returns the packed (keypoint, distance) or kNone; adds window comparisons to *cmp.
+__device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &cam,
+                                             const FuseConst &fp, const ItemShared &S,
+                                             const float *pos, const float *normal,
+                                             const uint4 *desc, float mind, float maxd,
+                                             unsigned long long &cmp) {
+    const float X = pos[0], Y = pos[1], Z = pos[2];
+    const float xc = fadd(fadd(fadd(fmul(S.R[0], X), fmul(S.R[1], Y)), fmul(S.R[2], Z)), S.t[0]);
+    const float yc = fadd(fadd(fadd(fmul(S.R[3], X), fmul(S.R[4], Y)), fmul(S.R[5], Z)), S.t[1]);
+    const float zc = fadd(fadd(fadd(fmul(S.R[6], X), fmul(S.R[7], Y)), fmul(S.R[8], Z)), S.t[2]);
+    if (!(zc > 0.0f)) return kNone;
+    const float x = __fdiv_rn(xc, zc), y = __fdiv_rn(yc, zc);
+    const float u = fadd(fmul(float(cam.fx), x), float(cam.cx));
+    const float v = fadd(fmul(float(cam.fy), y), float(cam.cy));
+    if (!(u >= 0.0f && u < float(cam.width) && v >= 0.0f && v < float(cam.height))) return kNone;
+    const float pox = fsub(X, S.O[0]), poy = fsub(Y, S.O[1]), poz = fsub(Z, S.O[2]);
+    const float dist = __fsqrt_rn(fadd(fadd(fmul(pox, pox), fmul(poy, poy)), fmul(poz, poz)));
+    if (dist < mind || dist > maxd) return kNone;
+    const float cosv = fadd(fadd(fmul(pox, normal[0]), fmul(poy, normal[1])), fmul(poz, normal[2]));
+    if (cosv < fmul(0.5f, dist)) return kNone;
+    int pl = kLevels - 1;
+    for (int l = 0; l < kLevels; ++l)
+        if (fmul(dist, S.scale[l]) >= maxd) { pl = l; break; }
+    const float r = fmul(fp.radius_scale, S.scale[pl]);
+    const int cx0 = grid_cell(fsub(u, r), cam.cell_w_inv, kGridCols) - 1;
+    const int cx1 = grid_cell(fadd(u, r), cam.cell_w_inv, kGridCols) + 1;
+    const int cy0 = grid_cell(fsub(v, r), cam.cell_h_inv, kGridRows) - 1;
+    const int cy1 = grid_cell(fadd(v, r), cam.cell_h_inv, kGridRows) + 1;
+    const uint4 m0 = desc[0], m1 = desc[1];
+    uint32_t best = kNone;  // (dist << 16) | caller keypoint index
+    for (int cy = max(cy0, 0); cy <= min(cy1, kGridRows - 1); ++cy) {
+        const int c0 = cy * kGridCols + max(cx0, 0), c1 = cy * kGridCols + min(cx1, kGridCols - 1);
+        const int k0 = T.grid_start[c0], k1 = T.grid_start[c1 + 1];
+        for (int k = k0; k < k1; ++k) {
+            const int j = T.grid_items[k];
+            const int lv = T.level[j];
+            if (lv != pl && lv != pl - 1) continue;
+            const float2 xt = T.xy[j];
+            if (!(fabsf(fsub(xt.x, u)) < r && fabsf(fsub(xt.y, v)) < r)) continue;
+            ++cmp;
+            const float ex = fsub(u, xt.x), ey = fsub(v, xt.y);
+            if (!(fadd(fmul(ex, ex), fmul(ey, ey)) <= S.thr[lv])) continue;
+            const uint32_t d = (uint32_t)hamming(m0, m1, T.desc[2 * j], T.desc[2 * j + 1]);
+            best = min(best, (d << 16) | (uint32_t)T.orig[j]);
+        }
+    }
+    if (best == kNone || (int)(best >> 16) > fp.hamming_max) return kNone;
+    return best;
+}
+
+// Pose-derived constants of a fusion target: R, t in float32 and the camera centre
+// O = -R^T t formed in float64; scale and reprojection thresholds per level.
+__device__ void fuse_setup(const KfHeader *h, float chi2, ItemShared &S) {
+    const int tid = threadIdx.x;
+    if (tid < 9) S.R[tid] = __double2float_rn(h->Tcw[(tid / 3) * 4 + tid % 3]);
+    if (tid >= 16 && tid < 19) {
+        const int c = tid - 16;
+        S.t[c] = __double2float_rn(h->Tcw[c * 4 + 3]);
+        double s = dmul(h->Tcw[0 * 4 + c], h->Tcw[0 * 4 + 3]);
+        s = dadd(s, dmul(h->Tcw[1 * 4 + c], h->Tcw[1 * 4 + 3]));
+        s = dadd(s, dmul(h->Tcw[2 * 4 + c], h->Tcw[2 * 4 + 3]));
+        S.O[c] = __double2float_rn(-s);
+    }
+    if (tid >= 32 && tid < 32 + kLevels) {
+        const float s = level_scale(tid - 32);
+        S.scale[tid - 32] = s;
+        S.thr[tid - 32] = fmul(chi2, fmul(s, s));
+    }
+}
+
+__device__ void fuse_item(const BatchArgs &A, const WorkItem &w, uint32_t idx, ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const KfView T = KfView::at(w.q, L);
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (tid == 0) S.cmp = 0ull;
+    fuse_setup(T.hdr, A.fp.chi2, S);
+    __syncthreads();
+    uint32_t base = 0;
+    for (int k0 = 0; k0 < (int)w.b; k0 += bs) {
+        const int k = k0 + tid;
+        const uint32_t m = w.a + (uint32_t)k;
+        unsigned long long cmp = 0;
+        uint32_t r = kNone;
+        if (k < (int)w.b && !(A.mp_skip && A.mp_skip[m]))
+            r = fuse_one(T, A.cam, A.fp, S, A.mp_pos + 3 * (size_t)m, A.mp_normal + 3 * (size_t)m,
+                         A.mp_desc + 2 * (size_t)m, A.mp_min[m], A.mp_max[m], cmp);
+        if (cmp) atomicAdd(&S.cmp, cmp);
+        uint32_t tot;
+        const uint32_t pos = block_scan_flag(r != kNone, S.wtot, tot);
+        if (r != kNone)
+            A.padded[w.out_off + base + pos] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
+        base += tot;
+    }
+    if (tid == 0) {
+        A.counts[idx] = base;
+        if (S.cmp) atomicAdd(&A.ncmp[1], S.cmp);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void search_dispatch(const BatchArgs &A, const WorkItem &w,
+                                                uint32_t idx, uint32_t *sm, int sn,
+                                                ItemShared &S) {
+    search_item<G>(A, w, idx, sm, sn, S);
+}
+
+__global__ void __launch_bounds__(512) batch_kernel(BatchArgs A, int sn) {
+    extern __shared__ uint32_t smem[];
+    __shared__ ItemShared S;
+    __shared__ bool s_last;
+    for (;;) {
+        if (threadIdx.x == 0) S.item = atomicAdd(&A.counters[0], 1u);
+        __syncthreads();
+        const uint32_t e = S.item;
+        __syncthreads();
+        if (e >= A.n_items) break;
+        const uint32_t idx = A.order[e];
+        const WorkItem w = A.items[idx];
+        if (w.kind == kItemSearch) {
+            switch (A.lanes) {
+                case 1: search_dispatch<1>(A, w, idx, smem, sn, S); break;
+                case 2: search_dispatch<2>(A, w, idx, smem, sn, S); break;
+                case 4: search_dispatch<4>(A, w, idx, smem, sn, S); break;
+                case 8: search_dispatch<8>(A, w, idx, smem, sn, S); break;
+                case 16: search_dispatch<16>(A, w, idx, smem, sn, S); break;
+                default: search_dispatch<32>(A, w, idx, smem, sn, S); break;
+            }
+        } else {
+            fuse_item(A, w, idx, S);
+        }
+        __syncthreads();
+    }
+    // The last CTA to finish turns the per-item counts into offsets (no waiting: every
+    // other CTA has published its counts before its increment).
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&A.counters[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int tid = threadIdx.x, bs = blockDim.x;
+    uint32_t base = 0;
+    for (uint32_t i0 = 0; i0 < A.n_items; i0 += bs) {
+        const uint32_t i = i0 + tid;
+        const uint32_t c = i < A.n_items ? __ldcg(A.counts + i) : 0u;
+        // block-wide inclusive scan of c
+        uint32_t v = c;
+        const unsigned lane = tid & 31u, warp = tid >> 5, nw = bs >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        if (lane == 31) S.wtot[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x = lane < nw ? S.wtot[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            if (lane < nw) S.wtot[lane] = x;
+        }
+        __syncthreads();
+        const uint32_t incl = v + (warp ? S.wtot[warp - 1] : 0u);
+        if (i < A.n_items) A.offsets[i] = base + incl - c;
+        const uint32_t tot = S.wtot[nw - 1];
+        __syncthreads();
+        base += tot;
+    }
+    if (tid == 0) A.offsets[A.n_items] = base;
+}
+
+__global__ void copy_kernel(BatchArgs A) {
+    for (uint32_t i = blockIdx.x; i < A.n_items; i += gridDim.x) {
+        const uint32_t cnt = A.counts[i], dst = A.offsets[i], src = A.items[i].out_off;
+        for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) A.dense[dst + k] = A.padded[src + k];
+    }
+}
+
+// ------------------------------------------------------------------------- plain form
+
+// Stage 1: match.  One group of G lanes per sorted query; node ranges found by binary search
+// in the neighbour's node array in global memory; winners per target by global atomicMin.
+template <int G>
+__global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *ts,
+                                  const uint8_t *mq, const uint8_t *mt, int cap, SearchConst sp,
+                                  CamConst cam, PairScratch scr, unsigned long long *ncmp) {
+    __shared__ float F[9];
+    __shared__ float thr[kLevels];
+    __shared__ unsigned long long s_cmp;
+    const SlotLayout L = SlotLayout::make(cap);
+    const KfView Q = KfView::at(qs, L), T = KfView::at(ts, L);
+    const int nQ = Q.hdr->n, nT = T.hdr->n;
+    if (threadIdx.x == 0) {
+        fundamental_f32(cam, Q.hdr->Tcw, T.hdr->Tcw, F);
+        s_cmp = 0ull;
+    }
+    if (threadIdx.x < kLevels) {
+        const float s = level_scale(threadIdx.x);
+        thr[threadIdx.x] = fmul(sp.epi_chi2, fmul(s, s));
+    }
+    __syncthreads();
+    const int g = threadIdx.x / G, sub = threadIdx.x % G;
+    const int p = blockIdx.x * (blockDim.x / G) + g;
+    uint32_t bkey = kNone, sec = 0xFFFFu;
+    unsigned long long my_cmp = 0;
+    if (p < nQ) {
+        const uint32_t io = Q.orig[p];
+        if (sub == 0) scr.res[io] = kNone;
+        if (!mq || mq[io]) {
+            const uint32_t nd = Q.node[p];
+            const int lo = lower_bound_u32(T.node, nT, nd);
+            const int hi = (lo < nT && T.node[lo] == nd) ? upper_bound_u32(T.node, lo, nT, nd) : lo;
+            if (lo < hi) {
+                const uint4 q0 = Q.desc[2 * p], q1 = Q.desc[2 * p + 1];
+                const float2 xq = Q.xy[p];
+                const Line l = epi_line(F, xq.x, xq.y);
+                for (int j = lo + sub; j < hi; j += G) {
+                    if (mt && !mt[T.orig[j]]) continue;
+                    ++my_cmp;
+                    const uint32_t d = (uint32_t)hamming(q0, q1, T.desc[2 * j], T.desc[2 * j + 1]);
+                    if (sp.epipolar) {
+                        const float2 xt = T.xy[j];
+                        if (!epi_pass(l, xt.x, xt.y, thr[T.level[j]])) continue;
+                    }
+                    const uint32_t key = (d << 16) | (uint32_t)j;
+                    if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
+                    else sec = min(sec, d);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const uint32_t ob = __shfl_xor_sync(kFull, bkey, off);
+        const uint32_t os = __shfl_xor_sync(kFull, sec, off);
+        sec = min(min(sec, os), max(bkey, ob) >> 16);
+        bkey = min(bkey, ob);
+    }
+    if (sub == 0 && p < nQ) {
+        uint32_t acc = kNone;
+        if (bkey != kNone) {
+            const uint32_t best = bkey >> 16;
+            bool ok = (int)best <= sp.hamming_max;
+            if (ok && sp.ratio_num != 0 && sec != 0xFFFFu)
+                ok = (long long)sp.ratio_den * best < (long long)sp.ratio_num * sec;
+            if (ok) {
+                const uint32_t j = bkey & 0xFFFFu;
+                acc = (j << 16) | best;
+                if (sp.resolve) atomicMin(&scr.win[j], (best << 16) | Q.orig[p]);
+            }
+        }
+        scr.accq[p] = acc;
+    }
+    if (my_cmp) atomicAdd(&s_cmp, my_cmp);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cmp) atomicAdd(ncmp, s_cmp);
+}
+
+// Stage 2: keep the winner of every target, histogram the rotation of kept matches.
+__global__ void pair_resolve_kernel(const unsigned char *qs, const unsigned char *ts, int cap,
+                                    SearchConst sp, PairScratch scr) {
+    const SlotLayout L = SlotLayout::make(cap);
+    const KfView Q = KfView::at(qs, L), T = KfView::at(ts, L);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Q.hdr->n) return;
+    const uint32_t acc = scr.accq[p];
+    if (acc == kNone) return;
+    const uint32_t j = acc >> 16, d = acc & 0xFFFFu, io = Q.orig[p];
+    if (sp.resolve && scr.win[j] != ((d << 16) | io)) return;
+    uint32_t bin = 0;
+    if (sp.rot_filter) {
+        bin = (uint32_t)rot_bin(Q.angle[p], T.angle[j]);
+        atomicAdd(&scr.hist[bin], 1u);
+    }
+    scr.res[io] = pack_res(T.orig[j], d, bin);
+}
+
+// Stage 3 (one CTA): top-3 bins, ordered compaction appended at *running.
+__global__ void pair_compact_kernel(const unsigned char *qs, int cap, SearchConst sp,
+                                    PairScratch scr, Out3 *dense, uint32_t *pair_offset) {
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t keep;
+    const SlotLayout L = SlotLayout::make(cap);
+    const KfView Q = KfView::at(qs, L);
+    const int nQ = Q.hdr->n;
+    if (threadIdx.x == 0) keep = sp.rot_filter ? top3_mask(scr.hist) : kNone;
+    __syncthreads();
+    const uint32_t start = *scr.running;
+    uint32_t base = 0;
+    for (int i0 = 0; i0 < nQ; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const uint32_t r = i < nQ ? scr.res[i] : kNone;
+        const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
+        uint32_t tot;
+        const uint32_t pos = block_scan_flag(f, wtot, tot);
+        if (f) dense[start + base + pos] = Out3{i, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
+        base += tot;
+    }
+    if (threadIdx.x == 0) {
+        pair_offset[0] = start;
+        *scr.running = start + base;
+    }
+}
+
+__global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float *pos,
+                                  const float *normal, const uint4 *desc, const float *mn,
+                                  const float *mx, const uint8_t *skip, int n, FuseConst fp,
+                                  CamConst cam, uint32_t *res, unsigned long long *ncmp) {
+    __shared__ ItemShared S;
+    const SlotLayout L = SlotLayout::make(cap);
+    const KfView T = KfView::at(ts, L);
+    if (threadIdx.x == 0) S.cmp = 0ull;
+    fuse_setup(T.hdr, fp.chi2, S);
+    __syncthreads();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long cmp = 0;
+    if (m < n) {
+        uint32_t r = kNone;
+        if (!(skip && skip[m]))
+            r = fuse_one(T, cam, fp, S, pos + 3 * (size_t)m, normal + 3 * (size_t)m,
+                         desc + 2 * (size_t)m, mn[m], mx[m], cmp);
+        res[m] = r;
+    }
+    if (cmp) atomicAdd(&S.cmp, cmp);
+    __syncthreads();
+    if (threadIdx.x == 0 && S.cmp) atomicAdd(ncmp, S.cmp);
+}
+
+__global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uint32_t *running,
+                                    uint32_t *offset_out) {
+    __shared__ uint32_t wtot[32];
+    const uint32_t start = *running;
+    uint32_t base = 0;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const uint32_t r = i < n ? res[i] : kNone;
+        uint32_t tot;
+        const uint32_t pos = block_scan_flag(r != kNone, wtot, tot);
+        if (r != kNone) dense[start + base + pos] = Out3{i, (int)(r & 0xFFFFu), (int)(r >> 16)};
+        base += tot;
+    }
+    if (threadIdx.x == 0) {
+        *offset_out = start;
+        *running = start + base;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- launchers
+
+size_t ingest_smem_bytes(int cap) {
+    size_t N = 1;
+    while (N < (size_t)cap) N <<= 1;
+    return N * sizeof(unsigned long long);
+}
+
+cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
+    if (a.n_jobs <= 0) return cudaSuccess;
+    const size_t smem = ingest_smem_bytes(a.cap);
+    cudaError_t e = cudaFuncSetAttribute(ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    ingest_kernel<<<a.n_jobs, 512, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t batch_smem_bytes(int smem_n) { return size_t(4) * 4 * (size_t)smem_n; }
+
+cudaError_t batch_kernel_prepare(size_t smem) {
+    return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int batch_ctas_per_sm(int threads, size_t smem) {
+    int n = 0;
+    if (batch_kernel_prepare(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, threads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int ctas, int threads, size_t smem, cudaStream_t s) {
+    const int sn = (int)(smem / 16);
+    batch_kernel<<<ctas, threads, smem, s>>>(a, sn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {
+    copy_kernel<<<ctas, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t pair_scratch_bytes(int cap) { return align128(size_t(cap) * 4) * 3 + 256; }
+
+PairScratch pair_scratch_at(void *base, int cap) {
+    unsigned char *b = static_cast<unsigned char *>(base);
+    const size_t a = align128(size_t(cap) * 4);
+    PairScratch s;
+    s.win = reinterpret_cast<uint32_t *>(b);
+    s.accq = reinterpret_cast<uint32_t *>(b + a);
+    s.res = reinterpret_cast<uint32_t *>(b + 2 * a);
+    s.hist = reinterpret_cast<uint32_t *>(b + 3 * a);
+    s.running = reinterpret_cast<uint32_t *>(b + 3 * a + 128);
+    return s;
+}
+
+cudaError_t launch_pair_plain(const unsigned char *q, const unsigned char *t, const uint8_t *mq,
+                              const uint8_t *mt, int nq, int nt, int cap, const SearchConst &sp,
+                              const CamConst &cam, const PairScratch &scr, Out3 *dense,
+                              uint32_t *pair_offset, unsigned long long *ncmp, int lanes,
+                              cudaStream_t s) {
+    cudaError_t e;
+    if (nt > 0 && (e = cudaMemsetAsync(scr.win, 0xFF, size_t(nt) * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(scr.hist, 0, 128, s)) != cudaSuccess) return e;
+    const int threads = 256;
+    if (nq > 0) {
+        const int per = threads / lanes;
+        const int grid = (nq + per - 1) / per;
+        switch (lanes) {
+            case 1: pair_match_kernel<1><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            case 2: pair_match_kernel<2><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            case 4: pair_match_kernel<4><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            case 8: pair_match_kernel<8><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            case 16: pair_match_kernel<16><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            default: pair_match_kernel<32><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        pair_resolve_kernel<<<(nq + 255) / 256, 256, 0, s>>>(q, t, cap, sp, scr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    pair_compact_kernel<<<1, 1024, 0, s>>>(q, cap, sp, scr, dense, pair_offset);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_plain(const unsigned char *t, int cap, const float *pos,
+                              const float *normal, const uint4 *desc, const float *mn,
+                              const float *mx, const uint8_t *skip, int n, const FuseConst &fp,
+                              const CamConst &cam, uint32_t *res, Out3 *dense, uint32_t *running,
+                              uint32_t *offset_out, unsigned long long *ncmp, cudaStream_t s) {
+    if (n > 0) {
+        fuse_plain_kernel<<<(n + 255) / 256, 256, 0, s>>>(t, cap, pos, normal, desc, mn, mx, skip,
+                                                          n, fp, cam, res, ncmp);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    fuse_compact_kernel<<<1, 1024, 0, s>>>(res, n, dense, running, offset_out);
+    return cudaGetLastError();
+}
+
+}  // namespace tmap

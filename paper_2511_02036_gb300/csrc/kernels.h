@@ -1,0 +1,46 @@
+// Host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "layout.cuh"
+
+namespace tmap {
+
+// Keyframe ingest: one CTA per keyframe sorts its keypoints by BoW node and builds the
+// projection-grid index inside its slot.
+size_t ingest_smem_bytes(int cap);
+cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
+
+// Persistent batch kernel (search pairs + fusion chunks) and its compaction pass.
+size_t batch_smem_bytes(int smem_n);
+int batch_ctas_per_sm(int threads, size_t smem);
+cudaError_t batch_kernel_prepare(size_t smem);
+cudaError_t launch_batch(const BatchArgs &a, int ctas, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
+
+// Plain per-pair form: every stage of one pair is its own launch, with global scratch.
+struct PairScratch {
+    uint32_t *win;      // [cap]   per target: lowest (dist, query) key
+    uint32_t *accq;     // [cap]   per sorted query: accepted (target, dist)
+    uint32_t *res;      // [cap]   per original query: kept (target, dist, bin)
+    uint32_t *hist;     // [32]    rotation histogram
+    uint32_t *running;  // [2]     running output offset, spare
+};
+size_t pair_scratch_bytes(int cap);
+PairScratch pair_scratch_at(void *base, int cap);
+// Runs one pair: dense output appended at *running; pair_offset[0] receives the start.
+cudaError_t launch_pair_plain(const unsigned char *q, const unsigned char *t, const uint8_t *mq,
+                              const uint8_t *mt, int nq, int nt, int cap, const SearchConst &sp,
+                              const CamConst &cam, const PairScratch &scr, Out3 *dense,
+                              uint32_t *pair_offset, unsigned long long *ncmp, int lanes,
+                              cudaStream_t s);
+// Plain fusion: one thread per map point, then an ordered compaction appended at *running;
+// offset_out[0] receives the start.
+cudaError_t launch_fuse_plain(const unsigned char *t, int cap, const float *pos,
+                              const float *normal, const uint4 *desc, const float *mn,
+                              const float *mx, const uint8_t *skip, int n, const FuseConst &fp,
+                              const CamConst &cam, uint32_t *res, Out3 *dense, uint32_t *running,
+                              uint32_t *offset_out, unsigned long long *ncmp, cudaStream_t s);
+
+}  // namespace tmap

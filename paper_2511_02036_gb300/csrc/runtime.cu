@@ -1,0 +1,1058 @@
+// Host runtime of the C ABI (include/tm.h): context, keyframe store, batches, plans,
+// autotuner.  The serving loop is in server.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "runtime.h"
+
+namespace tmap {
+
+// ------------------------------------------------------------------------- errors
+
+static thread_local std::string g_error;
+
+tm_status fail(tm_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return s;
+}
+
+tm_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(TM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------------- buffers
+
+cudaError_t DevBuf::reserve(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    release();
+    size_t want = std::max<size_t>(256, n + n / 4);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) { p = nullptr; cap = 0; return e; }
+    cap = want;
+    ++generation;
+    return cudaSuccess;
+}
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+cudaError_t PinBuf::reserve(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    release();
+    size_t want = std::max<size_t>(4096, n + n / 4);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e != cudaSuccess) { p = nullptr; cap = 0; return e; }
+    cap = want;
+    return cudaSuccess;
+}
+void PinBuf::release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace tmap
+
+using namespace tmap;
+
+// ------------------------------------------------------------------------- context
+
+extern "C" const char *tm_last_error(void) { return g_error.c_str(); }
+
+extern "C" void tm_search_params_default(tm_search_params *p) {
+    if (!p) return;
+    p->hamming_max = 50;
+    p->ratio_num = 3;
+    p->ratio_den = 5;
+    p->epi_chi2 = 3.84f;
+    p->epipolar = 1;
+    p->resolve = 1;
+    p->rot_filter = 1;
+    p->mode = TM_MODE_FUSED;
+    p->lanes_per_query = 0;
+}
+
+extern "C" void tm_fuse_params_default(tm_fuse_params *p) {
+    if (!p) return;
+    p->chi2 = 5.99f;
+    p->hamming_max = 50;
+    p->radius_scale = 3.0f;
+}
+
+extern "C" tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max_kp,
+                                   size_t mem_budget_bytes, tm_ctx **out) {
+    if (!out || !cam) return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: null argument");
+    *out = nullptr;
+    if (max_kp < 1 || max_kp > TM_MAX_KP_LIMIT)
+        return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: max_kp %d outside [1, %d]", max_kp,
+                    TM_MAX_KP_LIMIT);
+    if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0) || !(cam->fy > 0))
+        return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: bad camera");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: no device %d", device);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    tm_ctx *c = new tm_ctx();
+    c->device = device;
+    c->cam = *cam;
+    c->cap = (max_kp + 31) & ~31;
+    c->layout = SlotLayout::make(c->cap);
+    c->slot_bytes = c->layout.bytes;
+    c->budget = mem_budget_bytes;
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete c; return cuda_fail(e, "props"); }
+    c->num_sms = prop.multiProcessorCount;
+    c->camc.fx = cam->fx;
+    c->camc.fy = cam->fy;
+    c->camc.cx = cam->cx;
+    c->camc.cy = cam->cy;
+    c->camc.width = cam->width;
+    c->camc.height = cam->height;
+    c->camc.cell_w_inv = (float)kGridCols / (float)cam->width;
+    c->camc.cell_h_inv = (float)kGridRows / (float)cam->height;
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    const char *tc = getenv("TM_TUNE_CACHE");
+    if (tc) load_tuning(c, tc);
+    *out = c;
+    return TM_OK;
+}
+
+tm_ctx::~tm_ctx() {
+    cudaSetDevice(device);
+    if (stream) cudaStreamSynchronize(stream);
+    batch.release();
+    for (void *p : chunks) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+}
+
+extern "C" tm_status tm_ctx_destroy(tm_ctx *c) {
+    if (!c) return fail(TM_ERR_INVALID_ARG, "tm_ctx_destroy: null");
+    delete c;
+    return TM_OK;
+}
+
+cudaStream_t tmap::pick_stream(tm_ctx *c, void *s) {
+    return s ? static_cast<cudaStream_t>(s) : c->stream;
+}
+
+// ------------------------------------------------------------------------- store
+
+tm_status tmap::alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got) {
+    got.clear();
+    while ((int)got.size() < n) {
+        if (!c->free_slots.empty()) {
+            got.push_back(c->free_slots.back());
+            c->free_slots.pop_back();
+            continue;
+        }
+        size_t max_slots = c->budget ? c->budget / c->slot_bytes : (size_t)-1;
+        size_t have = c->slots.size();
+        if (have >= max_slots) break;
+        size_t want = std::min<size_t>(32, max_slots - have);
+        want = std::max<size_t>(want, (size_t)(n - (int)got.size()) < want ? (size_t)(n - (int)got.size()) : want);
+        size_t bytes = want * c->slot_bytes;
+        if (!c->budget) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < bytes + (size_t(1) << 30)) break;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        c->chunks.push_back(p);
+        for (size_t k = 0; k < want; ++k) {
+            Slot s;
+            s.ptr = static_cast<unsigned char *>(p) + k * c->slot_bytes;
+            c->slots.push_back(s);
+            c->free_slots.push_back((int)c->slots.size() - 1);
+        }
+        // hand out lowest slot ids first
+        std::sort(c->free_slots.begin(), c->free_slots.end(), std::greater<int>());
+    }
+    if ((int)got.size() < n) {
+        for (int s : got) c->free_slots.push_back(s);
+        got.clear();
+        return fail(TM_ERR_NO_MEMORY, "keyframe store full (%zu slots of %zu bytes, budget %zu)",
+                    c->slots.size(), c->slot_bytes, c->budget);
+    }
+    return TM_OK;
+}
+
+// Stage keyframes (host or device arrays) into the ingest buffers and enqueue the ingest
+// kernel on stream s.  Slots must already be reserved.  The caller synchronizes before the
+// staging buffers are reused.
+tm_status tmap::enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
+                             const int *slots, cudaStream_t s) {
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) total += (size_t)kfs[k].n;
+    const size_t N = (total + 31) & ~size_t(31);
+    // staged layout: desc | xy | angle | node | level | jobs
+    const size_t o_desc = 0, o_xy = o_desc + N * 32, o_ang = o_xy + N * 8, o_node = o_ang + N * 4,
+                 o_lvl = o_node + N * 4, o_jobs = align128(o_lvl + N), bytes = o_jobs + sizeof(IngestJob) * (size_t)n;
+    cudaError_t e;
+    if ((e = st.dev.reserve(bytes)) != cudaSuccess) return cuda_fail(e, "ingest staging");
+    if ((e = st.host.reserve(bytes)) != cudaSuccess) return cuda_fail(e, "ingest pinned staging");
+    unsigned char *h = static_cast<unsigned char *>(st.host.p);
+    unsigned char *d = static_cast<unsigned char *>(st.dev.p);
+    IngestJob *jobs = reinterpret_cast<IngestJob *>(h + o_jobs);
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        const tm_keyframe_view &v = kfs[k];
+        const size_t m = (size_t)v.n;
+        jobs[k].slot = c->slots[slots[k]].ptr;
+        jobs[k].src = (uint32_t)off;
+        jobs[k].n = v.n;
+        for (int q = 0; q < 12; ++q) jobs[k].Tcw[q] = v.Tcw[q];
+        if (m) {
+            if (is_device_ptr(v.desc)) {
+                if ((e = cudaMemcpyAsync(d + o_desc + off * 32, v.desc, m * 32, cudaMemcpyDeviceToDevice, s)) ||
+                    (e = cudaMemcpyAsync(d + o_xy + off * 8, v.xy, m * 8, cudaMemcpyDeviceToDevice, s)) ||
+                    (e = cudaMemcpyAsync(d + o_ang + off * 4, v.angle, m * 4, cudaMemcpyDeviceToDevice, s)) ||
+                    (e = cudaMemcpyAsync(d + o_node + off * 4, v.node, m * 4, cudaMemcpyDeviceToDevice, s)) ||
+                    (e = cudaMemcpyAsync(d + o_lvl + off, v.level, m, cudaMemcpyDeviceToDevice, s)))
+                    return cuda_fail(e, "ingest copy");
+            } else {
+                memcpy(h + o_desc + off * 32, v.desc, m * 32);
+                memcpy(h + o_xy + off * 8, v.xy, m * 8);
+                memcpy(h + o_ang + off * 4, v.angle, m * 4);
+                memcpy(h + o_node + off * 4, v.node, m * 4);
+                memcpy(h + o_lvl + off, v.level, m);
+                st.host_ranges.push_back({off, m});
+            }
+        }
+        off += m;
+    }
+    // one transfer of everything staged on the host (contiguous runs merged per array)
+    auto flush = [&](size_t base, size_t elt) -> cudaError_t {
+        size_t a = 0;
+        while (a < st.host_ranges.size()) {
+            size_t b = a;
+            size_t lo = st.host_ranges[a].first, hi = lo + st.host_ranges[a].second;
+            while (b + 1 < st.host_ranges.size() && st.host_ranges[b + 1].first == hi) {
+                ++b;
+                hi += st.host_ranges[b].second;
+            }
+            cudaError_t r = cudaMemcpyAsync(d + base + lo * elt, h + base + lo * elt, (hi - lo) * elt,
+                                            cudaMemcpyHostToDevice, s);
+            if (r != cudaSuccess) return r;
+            a = b + 1;
+        }
+        return cudaSuccess;
+    };
+    if ((e = flush(o_desc, 32)) || (e = flush(o_xy, 8)) || (e = flush(o_ang, 4)) ||
+        (e = flush(o_node, 4)) || (e = flush(o_lvl, 1)))
+        return cuda_fail(e, "ingest upload");
+    st.host_ranges.clear();
+    if ((e = cudaMemcpyAsync(d + o_jobs, jobs, sizeof(IngestJob) * (size_t)n, cudaMemcpyHostToDevice, s)))
+        return cuda_fail(e, "ingest jobs upload");
+    IngestArgs a;
+    a.jobs = reinterpret_cast<const IngestJob *>(d + o_jobs);
+    a.n_jobs = n;
+    a.cap = c->cap;
+    a.desc = reinterpret_cast<const uint4 *>(d + o_desc);
+    a.xy = reinterpret_cast<const float2 *>(d + o_xy);
+    a.angle = reinterpret_cast<const float *>(d + o_ang);
+    a.node = reinterpret_cast<const uint32_t *>(d + o_node);
+    a.level = d + o_lvl;
+    a.cell_w_inv = c->camc.cell_w_inv;
+    a.cell_h_inv = c->camc.cell_h_inv;
+    if ((e = launch_ingest(a, s)) != cudaSuccess) return cuda_fail(e, "ingest kernel");
+    return TM_OK;
+}
+
+tm_status tmap::validate_view(tm_ctx *c, const tm_keyframe_view &v) {
+    if (v.n < 0 || v.n > c->cap)
+        return fail(TM_ERR_INVALID_ARG, "keyframe has %d keypoints, capacity %d", v.n, c->cap);
+    if (v.n > 0 && (!v.desc || !v.xy || !v.angle || !v.level || !v.node))
+        return fail(TM_ERR_INVALID_ARG, "keyframe arrays must be non-null");
+    if (v.n > 0 && !is_device_ptr(v.level))
+        for (int i = 0; i < v.n; ++i)
+            if (v.level[i] >= TM_LEVELS)
+                return fail(TM_ERR_INVALID_ARG, "keypoint %d has level %d >= %d", i, v.level[i], TM_LEVELS);
+    return TM_OK;
+}
+
+tm_status tmap::store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyframe_view *kfs,
+                        cudaStream_t s, std::vector<int> &slots) {
+    for (int k = 0; k < n; ++k) {
+        tm_status st = validate_view(c, kfs[k]);
+        if (st) return st;
+        if (c->ids.count(ids[k])) return fail(TM_ERR_EXISTS, "keyframe %llu already stored", (unsigned long long)ids[k]);
+        for (int q = 0; q < k; ++q)
+            if (ids[q] == ids[k]) return fail(TM_ERR_EXISTS, "keyframe %llu given twice", (unsigned long long)ids[k]);
+    }
+    tm_status st = alloc_slots_locked(c, n, slots);
+    if (st) return st;
+    st = enqueue_ingest(c, c->ingest, n, kfs, slots.data(), s);
+    if (st) {
+        for (int sl : slots) c->free_slots.push_back(sl);
+        return st;
+    }
+    for (int k = 0; k < n; ++k) {
+        c->slots[slots[k]].n = kfs[k].n;
+        c->slots[slots[k]].refs = 0;
+        c->slots[slots[k]].id = ids[k];
+        c->ids[ids[k]] = slots[k];
+    }
+    return TM_OK;
+}
+
+extern "C" tm_status tm_store_add_keyframes(tm_ctx *c, int32_t n, const uint64_t *ids,
+                                            const tm_keyframe_view *kfs, void *stream) {
+    if (!c || n < 0 || (n > 0 && (!ids || !kfs))) return fail(TM_ERR_INVALID_ARG, "tm_store_add_keyframes: bad arguments");
+    if (n == 0) return TM_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaStream_t s = pick_stream(c, stream);
+    std::vector<int> slots;
+    tm_status st = store_add(c, n, ids, kfs, s, slots);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ingest");
+    return TM_OK;
+}
+
+extern "C" tm_status tm_store_add_keyframe(tm_ctx *c, uint64_t id, const tm_keyframe_view *kf,
+                                           void *stream) {
+    return tm_store_add_keyframes(c, 1, &id, kf, stream);
+}
+
+extern "C" tm_status tm_store_remove_keyframe(tm_ctx *c, uint64_t id) {
+    if (!c) return fail(TM_ERR_INVALID_ARG, "null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->ids.find(id);
+    if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)id);
+    Slot &sl = c->slots[it->second];
+    if (sl.refs > 0) return fail(TM_ERR_BUSY, "keyframe %llu is used by %d live plan(s)", (unsigned long long)id, sl.refs);
+    sl.n = 0;
+    c->free_slots.push_back(it->second);
+    c->ids.erase(it);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_store_keyframe_size(tm_ctx *c, uint64_t id, int32_t *n) {
+    if (!c || !n) return fail(TM_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->ids.find(id);
+    if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)id);
+    *n = c->slots[it->second].n;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_store_get_stats(tm_ctx *c, tm_store_stats *o) {
+    if (!c || !o) return fail(TM_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    o->device = c->device;
+    o->max_kp = c->cap;
+    o->slots_used = (int)c->ids.size();
+    size_t max_slots = c->budget ? c->budget / c->slot_bytes : 0;
+    o->slots_free_in_budget = c->budget ? (int)(max_slots - c->ids.size()) : -1;
+    o->slot_bytes = c->slot_bytes;
+    o->bytes_reserved = c->slots.size() * c->slot_bytes;
+    o->budget_bytes = c->budget;
+    return TM_OK;
+}
+
+// ------------------------------------------------------------------------- batches
+
+void BatchBuf::release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    for (DevBuf *b : {&items, &order, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
+                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch})
+        b->release();
+    h_stage.release();
+    h_out.release();
+}
+
+static SearchConst to_const(const tm_search_params &p) {
+    SearchConst s;
+    s.hamming_max = p.hamming_max;
+    s.ratio_num = p.ratio_num;
+    s.ratio_den = p.ratio_den;
+    s.epi_chi2 = p.epi_chi2;
+    s.epipolar = p.epipolar;
+    s.resolve = p.resolve;
+    s.rot_filter = p.rot_filter;
+    return s;
+}
+
+static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &fp) {
+    if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0))
+        return fail(TM_ERR_INVALID_ARG, "bad search parameters");
+    if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR)
+        return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
+    const int l = sp.lanes_per_query;
+    if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
+        return fail(TM_ERR_INVALID_ARG, "lanes_per_query must be 0, 1, 2, 4, 8, 16 or 32");
+    if (fp.hamming_max < 0 || !(fp.chi2 >= 0) || !(fp.radius_scale >= 0))
+        return fail(TM_ERR_INVALID_ARG, "bad fuse parameters");
+    return TM_OK;
+}
+
+// Build the work list of a batch and upload everything it needs (one transfer per array).
+// Caller holds c->mu.  On success B describes the batch and its slots are listed in B.slots.
+tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int n_steps,
+                            const tm_batch_inputs *in, const tm_search_params &sp,
+                            const tm_fuse_params &fp, cudaStream_t s) {
+    tm_status st = check_params(sp, fp);
+    if (st) return st;
+    if (n_steps < 0 || (n_steps > 0 && !steps)) return fail(TM_ERR_INVALID_ARG, "bad steps");
+    const size_t mask_bytes = in ? in->mask_bytes : 0;
+    const tm_mappoint_view mps = in ? in->mps : tm_mappoint_view{};
+    if (mask_bytes && !in->masks) return fail(TM_ERR_INVALID_ARG, "masks is null");
+    if (mps.n < 0) return fail(TM_ERR_INVALID_ARG, "negative map point count");
+    if (mps.n > 0 && (!mps.pos || !mps.normal || !mps.desc || !mps.min_dist || !mps.max_dist))
+        return fail(TM_ERR_INVALID_ARG, "map point arrays must be non-null");
+    std::vector<WorkItem> &items = B.h_items;
+    items.clear();
+    B.item_nq.clear();
+    B.item_nt.clear();
+    std::vector<int> slots_used;
+    B.step_pair_begin.assign(n_steps + 1, 0);
+    B.step_fuse_item.assign(n_steps + 1, 0);
+    B.n_pairs = 0;
+    uint32_t pad = 0;
+    int smem_n = 32;
+    auto slot_of = [&](uint64_t id, int &slot) -> tm_status {
+        auto it = c->ids.find(id);
+        if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)id);
+        slot = it->second;
+        return TM_OK;
+    };
+    for (int k = 0; k < n_steps; ++k) {
+        const tm_step &S = steps[k];
+        int qs;
+        if ((st = slot_of(S.kf_id, qs))) return st;
+        const int nq = c->slots[qs].n;
+        if (S.n_nbrs < 0 || (S.n_nbrs > 0 && !S.nbr_ids)) return fail(TM_ERR_INVALID_ARG, "step %d: bad neighbours", k);
+        if (S.q_free_off >= 0 && (size_t)S.q_free_off + (size_t)nq > mask_bytes)
+            return fail(TM_ERR_INVALID_ARG, "step %d: query mask outside masks", k);
+        B.step_pair_begin[k] = B.n_pairs;
+        size_t toff = S.nbr_free_off >= 0 ? (size_t)S.nbr_free_off : 0;
+        for (int j = 0; j < S.n_nbrs; ++j) {
+            int ts;
+            if ((st = slot_of(S.nbr_ids[j], ts))) return st;
+            const int nt = c->slots[ts].n;
+            if (S.nbr_free_off >= 0 && toff + (size_t)nt > mask_bytes)
+                return fail(TM_ERR_INVALID_ARG, "step %d: neighbour masks outside masks", k);
+            WorkItem w;
+            w.q = c->slots[qs].ptr;
+            w.t = c->slots[ts].ptr;
+            w.kind = kItemSearch;
+            w.out_off = pad;
+            w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;
+            w.b = S.nbr_free_off >= 0 ? (uint32_t)toff : kNone;
+            w.c = 0;
+            w.cost = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, (uint64_t)nq + nt + (uint64_t)nq * nt / 256);
+            pad += (uint32_t)(sp.resolve ? std::min(nq, nt) : nq);
+            smem_n = std::max(smem_n, std::max(nq, nt));
+            items.push_back(w);
+            B.item_nq.push_back(nq);
+            B.item_nt.push_back(nt);
+            slots_used.push_back(ts);
+            toff += (size_t)nt;
+            ++B.n_pairs;
+        }
+        slots_used.push_back(qs);
+    }
+    B.step_pair_begin[n_steps] = B.n_pairs;
+    B.n_search_items = (uint32_t)items.size();
+    for (int k = 0; k < n_steps; ++k) {
+        const tm_step &S = steps[k];
+        B.step_fuse_item[k] = (int)items.size();
+        if (S.mp_count <= 0) continue;
+        if (S.mp_begin < 0 || (int64_t)S.mp_begin + S.mp_count > mps.n)
+            return fail(TM_ERR_INVALID_ARG, "step %d: map point range outside the batch", k);
+        const int qs = c->ids[S.kf_id];
+        for (int b = 0; b < S.mp_count; b += kFuseChunk) {
+            WorkItem w;
+            w.q = c->slots[qs].ptr;
+            w.t = nullptr;
+            w.kind = kItemFuse;
+            w.out_off = pad;
+            w.a = (uint32_t)(S.mp_begin + b);
+            w.b = (uint32_t)std::min(kFuseChunk, S.mp_count - b);
+            w.c = (uint32_t)S.mp_begin;
+            w.cost = 2 * w.b;
+            pad += w.b;
+            items.push_back(w);
+        }
+    }
+    B.step_fuse_item[n_steps] = (int)items.size();
+    B.n_items = (uint32_t)items.size();
+    B.n_steps = n_steps;
+    B.total_pad = pad;
+    B.smem_n = (smem_n + 31) & ~31;
+    B.slots = slots_used;
+    // execution order: largest first (longest-processing-time-first over persistent CTAs)
+    std::vector<uint32_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return items[x].cost > items[y].cost; });
+    // device buffers
+    const size_t ni = std::max<size_t>(1, items.size());
+    const size_t nm = std::max<int>(1, mps.n);
+    cudaError_t e;
+    std::vector<void *> before = B.pointers();
+    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.order.reserve(ni * 4)) ||
+        (e = B.counts.reserve(ni * 4)) || (e = B.offsets.reserve((ni + 1) * 4)) ||
+        (e = B.ncmp.reserve(16)) || (e = B.counters.reserve(16)) ||
+        (e = B.padded.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
+        (e = B.dense.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
+        (e = B.masks.reserve(std::max<size_t>(16, mask_bytes))) ||
+        (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
+        (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
+        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)))
+        return cuda_fail(e, "batch buffers");
+    if (B.pointers() != before && B.graph) {
+        cudaGraphExecDestroy(B.graph);
+        B.graph = nullptr;
+    }
+    const size_t stage = ni * sizeof(WorkItem) + ni * 4;
+    if ((e = B.h_stage.reserve(stage))) return cuda_fail(e, "pinned staging");
+    unsigned char *h = static_cast<unsigned char *>(B.h_stage.p);
+    if (!items.empty()) memcpy(h, items.data(), items.size() * sizeof(WorkItem));
+    if (!order.empty()) memcpy(h + ni * sizeof(WorkItem), order.data(), order.size() * 4);
+    if ((e = cudaMemcpyAsync(B.items.p, h, items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(B.order.p, h + ni * sizeof(WorkItem), order.size() * 4, cudaMemcpyHostToDevice, s)))
+        return cuda_fail(e, "work list upload");
+    if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
+        return cuda_fail(e, "mask upload");
+    if (mps.n > 0) {
+        const size_t m = (size_t)mps.n;
+        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, s)) ||
+            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, s)) ||
+            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, s)) ||
+            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, s)) ||
+            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, s)))
+            return cuda_fail(e, "map point upload");
+        if (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, s)))
+            return cuda_fail(e, "map point upload");
+    }
+    BatchArgs &A = B.args;
+    A.items = static_cast<const WorkItem *>(B.items.p);
+    A.order = static_cast<const uint32_t *>(B.order.p);
+    A.n_items = B.n_items;
+    A.counters = static_cast<uint32_t *>(B.counters.p);
+    A.masks = static_cast<const uint8_t *>(B.masks.p);
+    A.mp_pos = static_cast<const float *>(B.mp_pos.p);
+    A.mp_normal = static_cast<const float *>(B.mp_normal.p);
+    A.mp_min = static_cast<const float *>(B.mp_min.p);
+    A.mp_max = static_cast<const float *>(B.mp_max.p);
+    A.mp_desc = static_cast<const uint4 *>(B.mp_desc.p);
+    A.mp_skip = (mps.n > 0 && mps.skip) ? static_cast<const uint8_t *>(B.mp_skip.p) : nullptr;
+    A.padded = static_cast<Out3 *>(B.padded.p);
+    A.counts = static_cast<uint32_t *>(B.counts.p);
+    A.offsets = static_cast<uint32_t *>(B.offsets.p);
+    A.ncmp = static_cast<unsigned long long *>(B.ncmp.p);
+    A.dense = static_cast<Out3 *>(B.dense.p);
+    A.status = static_cast<uint32_t *>(B.counters.p) + 2;
+    A.sp = to_const(sp);
+    A.fp.chi2 = fp.chi2;
+    A.fp.hamming_max = fp.hamming_max;
+    A.fp.radius_scale = fp.radius_scale;
+    A.cam = c->camc;
+    A.cap = c->cap;
+    B.sp = sp;
+    B.fp = fp;
+    return TM_OK;
+}
+
+std::vector<void *> BatchBuf::pointers() const {
+    return {items.p, order.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
+            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p};
+}
+
+// Enqueue the fused launch (counter reset, persistent kernel, compaction).
+tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s) {
+    cudaError_t e;
+    const size_t smem = batch_smem_bytes(B.smem_n);
+    if ((e = batch_kernel_prepare(smem))) return cuda_fail(e, "batch kernel attribute");
+    int per_sm = batch_ctas_per_sm(threads, smem);
+    if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "batch kernel does not fit: %d threads, %zu B shared", threads, smem);
+    B.args.lanes = lanes;
+    B.threads = threads;
+    B.lanes = lanes;
+    B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>(B.n_items, (uint32_t)(per_sm * c->num_sms)));
+    if ((e = cudaMemsetAsync(B.counters.p, 0, 16, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
+        return cuda_fail(e, "reset counters");
+    if (B.n_items == 0) {
+        if ((e = cudaMemsetAsync(B.offsets.p, 0, 4, s))) return cuda_fail(e, "offsets");
+        return TM_OK;
+    }
+    if ((e = launch_batch(B.args, B.ctas, threads, smem, s))) return cuda_fail(e, "batch kernel");
+    if ((e = launch_copy(B.args, std::min<int>(B.n_items, 4 * c->num_sms), s))) return cuda_fail(e, "copy kernel");
+    return TM_OK;
+}
+
+// Enqueue the plain per-pair form of the same batch.
+tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s) {
+    cudaError_t e;
+    const size_t scr_bytes = pair_scratch_bytes(c->cap);
+    const int max_mp = (int)B.total_pad;  // a step's map points never exceed the padded total
+    if ((e = B.scratch.reserve(scr_bytes + align128(size_t(std::max(1, max_mp)) * 4))))
+        return cuda_fail(e, "plain scratch");
+    PairScratch scr = pair_scratch_at(B.scratch.p, c->cap);
+    uint32_t *res = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(B.scratch.p) + scr_bytes);
+    if ((e = cudaMemsetAsync(scr.running, 0, 8, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
+        return cuda_fail(e, "reset");
+    B.lanes = lanes;
+    const std::vector<WorkItem> &items = B.h_items;
+    uint32_t *offs = static_cast<uint32_t *>(B.offsets.p);
+    unsigned long long *ncmp = static_cast<unsigned long long *>(B.ncmp.p);
+    const SearchConst sp = to_const(B.sp);
+    for (uint32_t i = 0; i < B.n_search_items; ++i) {
+        const WorkItem &w = items[i];
+        const int qn = B.item_nq[i], tn = B.item_nt[i];
+        const uint8_t *mq = w.a == kNone ? nullptr : B.args.masks + w.a;
+        const uint8_t *mt = w.b == kNone ? nullptr : B.args.masks + w.b;
+        if ((e = launch_pair_plain(w.q, w.t, mq, mt, qn, tn, c->cap, sp, c->camc, scr, B.args.dense,
+                                   offs + i, ncmp, lanes, s)))
+            return cuda_fail(e, "plain pair");
+    }
+    for (int k = 0; k < B.n_steps; ++k) {
+        const int f0 = B.step_fuse_item[k], f1 = B.step_fuse_item[k + 1];
+        if (f0 == f1) continue;
+        const WorkItem &w = items[f0];
+        const uint32_t begin = w.a;
+        uint32_t n = 0;
+        for (int f = f0; f < f1; ++f) n += items[f].b;
+        if ((e = launch_fuse_plain(w.q, c->cap, B.args.mp_pos + 3 * (size_t)begin,
+                                   B.args.mp_normal + 3 * (size_t)begin, B.args.mp_desc + 2 * (size_t)begin,
+                                   B.args.mp_min + begin, B.args.mp_max + begin,
+                                   B.args.mp_skip ? B.args.mp_skip + begin : nullptr, (int)n, B.args.fp,
+                                   c->camc, res, B.args.dense, scr.running, offs + f0, ncmp + 1, s)))
+            return cuda_fail(e, "plain fuse");
+    }
+    if ((e = cudaMemcpyAsync(offs + B.n_items, scr.running, 4, cudaMemcpyDeviceToDevice, s)))
+        return cuda_fail(e, "plain total");
+    return TM_OK;
+}
+
+// Download results of the last run of B into r (host offsets; matches host or device).
+tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s) {
+    (void)c;
+    cudaError_t e;
+    const size_t nio = (size_t)B.n_items + 1;
+    if ((e = B.h_out.reserve((nio + 2) * 4 + 16))) return cuda_fail(e, "pinned results");
+    uint32_t *ho = static_cast<uint32_t *>(B.h_out.p);
+    unsigned long long *hc = reinterpret_cast<unsigned long long *>(ho + ((nio + 1) & ~size_t(1)));
+    if ((e = cudaMemcpyAsync(ho, B.offsets.p, nio * 4, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "results");
+    const uint32_t search_total = ho[B.n_search_items];
+    const uint32_t total = ho[B.n_items];
+    const size_t nf = total - search_total;
+    r->n_matches = search_total;
+    r->n_fuse = nf;
+    r->n_comparisons_search = hc[0];
+    r->n_comparisons_fuse = hc[1];
+    if (search_total > r->match_cap || nf > r->fuse_cap)
+        return fail(TM_ERR_CAPACITY, "result buffers too small: %u matches (cap %zu), %zu fusion candidates (cap %zu)",
+                    search_total, r->match_cap, nf, r->fuse_cap);
+    if (r->pair_offsets)
+        for (int p = 0; p <= B.n_pairs; ++p) r->pair_offsets[p] = (int32_t)ho[p];
+    if (r->fuse_offsets)
+        for (int k = 0; k <= B.n_steps; ++k)
+            r->fuse_offsets[k] = (int32_t)(ho[B.step_fuse_item[k]] - search_total);
+    if (r->fuse_offsets && B.n_steps > 0) {
+        // steps without map points start where the next step starts
+        for (int k = B.n_steps - 1; k >= 0; --k)
+            if (B.step_fuse_item[k] == B.step_fuse_item[k + 1]) r->fuse_offsets[k] = r->fuse_offsets[k + 1];
+    }
+    const Out3 *d = static_cast<const Out3 *>(B.dense.p);
+    if (search_total && (e = cudaMemcpyAsync(r->matches, d, search_total * sizeof(Out3), cudaMemcpyDefault, s)))
+        return cuda_fail(e, "matches download");
+    if (nf && (e = cudaMemcpyAsync(r->fuse, d + search_total, nf * sizeof(Out3), cudaMemcpyDefault, s)))
+        return cuda_fail(e, "fusion download");
+    if ((e = cudaStreamSynchronize(s))) return cuda_fail(e, "results");
+    return TM_OK;
+}
+
+// ------------------------------------------------------------------------- tuning
+
+static const int kTuneThreads[] = {128, 256, 512};
+static const int kTuneLanes[] = {1, 2, 4, 8, 32};
+
+void tmap::load_tuning(tm_ctx *c, const char *path) {
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    int key, th, ln;
+    while (fscanf(f, "%d %d %d", &key, &th, &ln) == 3) c->tuned[key] = {th, ln};
+    fclose(f);
+}
+
+static void save_tuning(tm_ctx *c) {
+    const char *path = getenv("TM_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : c->tuned) fprintf(f, "%d %d %d\n", kv.first, kv.second.first, kv.second.second);
+    fclose(f);
+}
+
+// Density class of a batch: log2 of the mean candidates per query keypoint.
+static int density_key(uint64_t ncmp, uint64_t queries) {
+    if (!queries) return 0;
+    double r = (double)ncmp / (double)queries;
+    return (int)std::lround(std::log2(std::max(r, 0.25)) * 2.0);
+}
+
+static uint64_t batch_queries(tm_ctx *c, const BatchBuf &B, const tm_step *steps) {
+    uint64_t q = 0;
+    for (int k = 0; k < B.n_steps; ++k)
+        q += (uint64_t)c->slots[c->ids[steps[k].kf_id]].n * (uint64_t)steps[k].n_nbrs;
+    return q;
+}
+
+// Picks (threads, lanes) for a prepared batch: cached by density class, else measured.
+tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure) {
+    tm_status st;
+    if ((st = enqueue_fused(c, B, c->def_threads, c->def_lanes, s))) return st;
+    unsigned long long hc[2];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "tuning");
+    const int key = density_key(hc[0], batch_queries(c, B, steps));
+    auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) {
+        B.threads = it->second.first;
+        B.lanes = it->second.second;
+        return TM_OK;
+    }
+    if (!measure) {
+        B.threads = c->def_threads;
+        B.lanes = c->def_lanes;
+        return TM_OK;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt = c->def_threads, bl = c->def_lanes;
+    for (int th : kTuneThreads)
+        for (int ln : kTuneLanes) {
+            if (batch_ctas_per_sm(th, batch_smem_bytes(B.smem_n)) < 1) continue;
+            if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
+            float tot = 0.0f;
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(e0, s);
+                if ((st = enqueue_fused(c, B, th, ln, s))) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tot += ms;
+            }
+            if (st) break;
+            if (tot < best) { best = tot; bt = th; bl = ln; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    c->tuned[key] = {bt, bl};
+    save_tuning(c);
+    B.threads = bt;
+    B.lanes = bl;
+    return TM_OK;
+}
+
+// ------------------------------------------------------------------------- one-shot calls
+
+static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
+                                  const tm_batch_inputs *in, const tm_search_params &sp,
+                                  const tm_fuse_params &fp, tm_batch_result *res, cudaStream_t s) {
+    BatchBuf &B = c->batch;
+    tm_status st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
+    if (st) return st;
+    if (sp.mode == TM_MODE_PER_PAIR) {
+        st = enqueue_plain(c, B, sp.lanes_per_query ? sp.lanes_per_query : 1, s);
+    } else {
+        int th = c->def_threads, ln = c->def_lanes;
+        if (sp.lanes_per_query) ln = sp.lanes_per_query;
+        else if (!c->tuned.empty()) {
+            th = c->last_threads;
+            ln = c->last_lanes;
+        }
+        st = enqueue_fused(c, B, th, ln, s);
+    }
+    if (st) return st;
+    return fetch_results(c, B, res, s);
+}
+
+extern "C" tm_status tm_batch_run(tm_ctx *c, const tm_step *steps, int32_t n_steps,
+                                  const tm_batch_inputs *in, const tm_search_params *sp,
+                                  const tm_fuse_params *fp, tm_batch_result *res, void *stream) {
+    if (!c || !res) return fail(TM_ERR_INVALID_ARG, "tm_batch_run: null argument");
+    tm_search_params spd;
+    tm_fuse_params fpd;
+    tm_search_params_default(&spd);
+    tm_fuse_params_default(&fpd);
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return run_batch_locked(c, steps, n_steps, in, sp ? *sp : spd, fp ? *fp : fpd, res,
+                            pick_stream(c, stream));
+}
+
+extern "C" tm_status tm_search_triangulation(tm_ctx *c, uint64_t kf, const uint64_t *nbrs,
+                                             int32_t n_nbrs, const tm_search_params *params,
+                                             const uint8_t *q_free, const uint8_t *nbr_free,
+                                             tm_match *out, size_t cap, size_t *n_out,
+                                             int32_t *pair_offsets, uint64_t *n_comparisons,
+                                             void *stream) {
+    if (!c || !n_out || (n_nbrs > 0 && (!nbrs || !pair_offsets)) || n_nbrs < 0)
+        return fail(TM_ERR_INVALID_ARG, "tm_search_triangulation: bad arguments");
+    tm_search_params sp;
+    tm_fuse_params fp;
+    tm_search_params_default(&sp);
+    tm_fuse_params_default(&fp);
+    if (params) sp = *params;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    auto it = c->ids.find(kf);
+    if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)kf);
+    const int nq = c->slots[it->second].n;
+    size_t nt_sum = 0;
+    for (int k = 0; k < n_nbrs; ++k) {
+        auto jt = c->ids.find(nbrs[k]);
+        if (jt == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)nbrs[k]);
+        nt_sum += (size_t)c->slots[jt->second].n;
+    }
+    // masks: [q_free | nbr_free], uploaded in one call when both come from one place
+    std::vector<uint8_t> hm;
+    tm_batch_inputs in{};
+    tm_step st{};
+    st.kf_id = kf;
+    st.nbr_ids = nbrs;
+    st.n_nbrs = n_nbrs;
+    st.q_free_off = -1;
+    st.nbr_free_off = -1;
+    const bool dq = is_device_ptr(q_free), dn = is_device_ptr(nbr_free);
+    if ((q_free && dq) || (nbr_free && dn)) {
+        // device masks: gather them into the context's device scratch
+        cudaError_t e = c->mask_scratch.reserve(nq + nt_sum + 16);
+        if (e) return cuda_fail(e, "mask scratch");
+        unsigned char *d = static_cast<unsigned char *>(c->mask_scratch.p);
+        cudaStream_t s = pick_stream(c, stream);
+        if (q_free && (e = cudaMemcpyAsync(d, q_free, nq, cudaMemcpyDefault, s))) return cuda_fail(e, "mask");
+        if (nbr_free && (e = cudaMemcpyAsync(d + nq, nbr_free, nt_sum, cudaMemcpyDefault, s))) return cuda_fail(e, "mask");
+        in.masks = d;
+    } else {
+        hm.resize(nq + nt_sum);
+        if (q_free && nq) memcpy(hm.data(), q_free, nq);
+        if (nbr_free && nt_sum) memcpy(hm.data() + nq, nbr_free, nt_sum);
+        in.masks = hm.data();
+    }
+    in.mask_bytes = nq + nt_sum;
+    if (q_free) st.q_free_off = 0;
+    if (nbr_free) st.nbr_free_off = nq;
+    std::vector<int32_t> fo(2);
+    tm_batch_result r{};
+    r.matches = out;
+    r.match_cap = cap;
+    r.pair_offsets = pair_offsets;
+    r.fuse = nullptr;
+    r.fuse_cap = 0;
+    r.fuse_offsets = fo.data();
+    tm_status s2 = run_batch_locked(c, &st, 1, &in, sp, fp, &r, pick_stream(c, stream));
+    *n_out = r.n_matches;
+    if (n_comparisons) *n_comparisons = r.n_comparisons_search;
+    return s2;
+}
+
+extern "C" tm_status tm_fuse(tm_ctx *c, uint64_t kf, const tm_mappoint_view *mps,
+                             const tm_fuse_params *params, tm_fuse_match *out, size_t cap,
+                             size_t *n_out, uint64_t *n_comparisons, void *stream) {
+    if (!c || !mps || !n_out) return fail(TM_ERR_INVALID_ARG, "tm_fuse: null argument");
+    tm_search_params sp;
+    tm_fuse_params fp;
+    tm_search_params_default(&sp);
+    tm_fuse_params_default(&fp);
+    if (params) fp = *params;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    tm_step st{};
+    st.kf_id = kf;
+    st.n_nbrs = 0;
+    st.q_free_off = -1;
+    st.nbr_free_off = -1;
+    st.mp_begin = 0;
+    st.mp_count = mps->n;
+    tm_batch_inputs in{};
+    in.mps = *mps;
+    int32_t po[1] = {0}, fo[2] = {0, 0};
+    tm_batch_result r{};
+    r.matches = nullptr;
+    r.match_cap = 0;
+    r.pair_offsets = po;
+    r.fuse = out;
+    r.fuse_cap = cap;
+    r.fuse_offsets = fo;
+    tm_status s2 = run_batch_locked(c, &st, 1, &in, sp, fp, &r, pick_stream(c, stream));
+    *n_out = r.n_fuse;
+    if (n_comparisons) *n_comparisons = r.n_comparisons_fuse;
+    return s2;
+}
+
+// ------------------------------------------------------------------------- plans
+
+struct tm_plan {
+    tm_ctx *ctx = nullptr;
+    BatchBuf B;
+    std::vector<tm_step> steps;
+    std::vector<std::vector<uint64_t>> nbrs;
+    int kernels_per_run = 0;
+};
+
+extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_steps,
+                                    const tm_batch_inputs *in, const tm_search_params *sp,
+                                    const tm_fuse_params *fp, tm_plan **out) {
+    if (!c || !out) return fail(TM_ERR_INVALID_ARG, "tm_plan_create: null argument");
+    *out = nullptr;
+    tm_search_params spd;
+    tm_fuse_params fpd;
+    tm_search_params_default(&spd);
+    tm_fuse_params_default(&fpd);
+    if (sp) spd = *sp;
+    if (fp) fpd = *fp;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    tm_plan *P = new tm_plan();
+    P->ctx = c;
+    cudaStream_t s = c->stream;
+    tm_status st = prepare_batch(c, P->B, steps, n_steps, in, spd, fpd, s);
+    if (!st && spd.mode == TM_MODE_FUSED) {
+        if (spd.lanes_per_query) {
+            P->B.threads = c->def_threads;
+            P->B.lanes = spd.lanes_per_query;
+        } else {
+            const char *nt = getenv("TM_NO_TUNE");
+            st = tune_batch(c, P->B, steps, s, !(nt && nt[0] == '1'));
+            if (!st) {
+                c->last_threads = P->B.threads;
+                c->last_lanes = P->B.lanes;
+            }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (!st && e) st = cuda_fail(e, "plan upload");
+    if (st) {
+        P->B.release();
+        delete P;
+        return st;
+    }
+    if (spd.mode == TM_MODE_FUSED) {
+        // capture the launch in a CUDA graph
+        const int th = P->B.threads, ln = P->B.lanes;
+        if ((e = batch_kernel_prepare(batch_smem_bytes(P->B.smem_n)))) st = cuda_fail(e, "attribute");
+        cudaGraph_t g = nullptr;
+        if (!st && (e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
+            st = cuda_fail(e, "begin capture");
+        if (!st) {
+            tm_status s1 = enqueue_fused(c, P->B, th, ln, c->capture_stream);
+            e = cudaStreamEndCapture(c->capture_stream, &g);
+            if (s1) st = s1;
+            else if (e) st = cuda_fail(e, "end capture");
+        }
+        if (!st && (e = cudaGraphInstantiate(&P->B.graph, g, 0))) st = cuda_fail(e, "graph instantiate");
+        if (g) cudaGraphDestroy(g);
+        P->kernels_per_run = P->B.n_items ? 2 : 0;
+    } else {
+        P->kernels_per_run = 3 * (int)P->B.n_search_items;
+        for (int k = 0; k < P->B.n_steps; ++k)
+            if (P->B.step_fuse_item[k] != P->B.step_fuse_item[k + 1]) P->kernels_per_run += 2;
+        P->B.lanes = spd.lanes_per_query ? spd.lanes_per_query : 1;
+    }
+    if (st) {
+        P->B.release();
+        delete P;
+        return st;
+    }
+    for (int sl : P->B.slots) c->slots[sl].refs++;
+    P->steps.assign(steps, steps + n_steps);
+    P->nbrs.resize(n_steps);
+    for (int k = 0; k < n_steps; ++k) {
+        P->nbrs[k].assign(steps[k].nbr_ids, steps[k].nbr_ids + steps[k].n_nbrs);
+        P->steps[k].nbr_ids = P->nbrs[k].data();
+    }
+    *out = P;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_plan_run(tm_plan *P, void *stream) {
+    if (!P) return fail(TM_ERR_INVALID_ARG, "tm_plan_run: null plan");
+    tm_ctx *c = P->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t s = pick_stream(c, stream);
+    if (P->B.graph) {
+        cudaError_t e = cudaGraphLaunch(P->B.graph, s);
+        if (e) return cuda_fail(e, "graph launch");
+        return TM_OK;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (P->B.sp.mode == TM_MODE_PER_PAIR) return enqueue_plain(c, P->B, P->B.lanes, s);
+    return enqueue_fused(c, P->B, P->B.threads, P->B.lanes, s);
+}
+
+extern "C" tm_status tm_plan_results(tm_plan *P, tm_batch_result *res, void *stream) {
+    if (!P || !res) return fail(TM_ERR_INVALID_ARG, "tm_plan_results: null argument");
+    cudaSetDevice(P->ctx->device);
+    return fetch_results(P->ctx, P->B, res, pick_stream(P->ctx, stream));
+}
+
+extern "C" tm_status tm_plan_info(tm_plan *P, int32_t *threads, int32_t *lanes, int32_t *ctas,
+                                  int32_t *kernels) {
+    if (!P) return fail(TM_ERR_INVALID_ARG, "tm_plan_info: null plan");
+    if (threads) *threads = P->B.threads;
+    if (lanes) *lanes = P->B.lanes;
+    if (ctas) *ctas = P->B.ctas;
+    if (kernels) *kernels = P->kernels_per_run;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_plan_destroy(tm_plan *P) {
+    if (!P) return fail(TM_ERR_INVALID_ARG, "tm_plan_destroy: null plan");
+    tm_ctx *c = P->ctx;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+        cudaDeviceSynchronize();
+        for (int sl : P->B.slots) c->slots[sl].refs--;
+    }
+    P->B.release();
+    delete P;
+    return TM_OK;
+}

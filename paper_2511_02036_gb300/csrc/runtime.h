@@ -1,0 +1,113 @@
+// Internal host-side state of the library (context, store, batches).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+#include "layout.cuh"
+#include "tm.h"
+
+namespace tmap {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    unsigned generation = 0;
+    cudaError_t reserve(size_t n);  // grows (contents not kept)
+    void release();
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t n);
+    void release();
+};
+
+struct Slot {
+    unsigned char *ptr = nullptr;
+    int n = 0;
+    int refs = 0;
+    uint64_t id = 0;
+};
+
+// Staging area of keyframe ingest (device copy of the caller-order arrays + pinned mirror).
+struct IngestStage {
+    DevBuf dev;
+    PinBuf host;
+    std::vector<std::pair<size_t, size_t>> host_ranges;
+    void release() { dev.release(); host.release(); }
+};
+
+// Device and staging buffers of one batch, plus what the host needs to read its results.
+struct BatchBuf {
+    DevBuf items, order, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
+        counts, offsets, ncmp, counters, dense, scratch;
+    PinBuf h_stage, h_out;
+    std::vector<WorkItem> h_items;
+    std::vector<int> item_nq, item_nt;
+    std::vector<int> step_pair_begin, step_fuse_item, slots;
+    uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
+    int n_steps = 0, n_pairs = 0, smem_n = 32;
+    int threads = 256, lanes = 1, ctas = 0;
+    tm_search_params sp{};
+    tm_fuse_params fp{};
+    BatchArgs args{};
+    cudaGraphExec_t graph = nullptr;
+    std::vector<void *> pointers() const;
+    void release();
+};
+
+}  // namespace tmap
+
+struct tm_ctx {
+    int device = 0;
+    tm_camera cam{};
+    int cap = 0;
+    tmap::SlotLayout layout{};
+    size_t slot_bytes = 0, budget = 0;
+    int num_sms = 1;
+    tmap::CamConst camc{};
+    std::mutex mu;
+    std::unordered_map<uint64_t, int> ids;
+    std::vector<tmap::Slot> slots;
+    std::vector<int> free_slots;
+    std::vector<void *> chunks;
+    cudaStream_t stream = nullptr, capture_stream = nullptr;
+    tmap::IngestStage ingest;
+    tmap::BatchBuf batch;
+    tmap::DevBuf mask_scratch;
+    std::map<int, std::pair<int, int>> tuned;
+    int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1;
+    ~tm_ctx();
+};
+
+namespace tmap {
+
+tm_status fail(tm_status s, const char *fmt, ...);
+tm_status cuda_fail(cudaError_t e, const char *what);
+bool is_device_ptr(const void *p);
+cudaStream_t pick_stream(tm_ctx *c, void *s);
+tm_status validate_view(tm_ctx *c, const tm_keyframe_view &v);
+// Reserves n store slots (all or nothing) within the budget; caller holds c->mu.
+tm_status alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got);
+tm_status enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
+                         const int *slots, cudaStream_t s);
+tm_status store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyframe_view *kfs,
+                    cudaStream_t s, std::vector<int> &slots);
+tm_status prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int n_steps,
+                        const tm_batch_inputs *in, const tm_search_params &sp,
+                        const tm_fuse_params &fp, cudaStream_t s);
+tm_status enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s);
+tm_status enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s);
+tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s);
+tm_status tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure);
+void load_tuning(tm_ctx *c, const char *path);
+
+}  // namespace tmap

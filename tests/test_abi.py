@@ -1,0 +1,101 @@
+"""The C-ABI library loads and exports every function include/*.h declares, and the Python
+binding's structs have the C layout (no GPU needed: no compute call is made)."""
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(tm_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2511_02036_gb300 import _lib
+    return _lib.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only",
+                          os.path.join(ROOT, "paper_2511_02036_gb300", "libtm.so")],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert getattr(lib, n) is not None
+    from paper_2511_02036_gb300 import _lib as L
+    assert set(L.SIGNATURES) == set(names)
+
+
+def test_struct_layout_matches_c(lib):
+    from paper_2511_02036_gb300 import _lib as L
+    structs = ["tm_camera", "tm_keyframe_view", "tm_mappoint_view", "tm_search_params",
+               "tm_fuse_params", "tm_match", "tm_store_stats", "tm_step", "tm_batch_inputs",
+               "tm_batch_result", "tm_server_config", "tm_request", "tm_request_info"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tm.h"', "int main(void){"]
+    for s in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in getattr(L, s)._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "abi.c")
+        open(c, "w").write("\n".join(lines))
+        exe = os.path.join(d, "abi")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = dict(ln.split() for ln in out.splitlines())
+    for s in structs:
+        T = getattr(L, s)
+        assert int(got[s]) == ctypes.sizeof(T), s
+        for f, _ in T._fields_:
+            assert int(got["%s.%s" % (s, f)]) == getattr(T, f).offset, (s, f)
+
+
+def test_parameter_defaults(lib):
+    from paper_2511_02036_gb300 import _lib as L
+    import paper_2511_02036_gb300 as tm
+    p = L.tm_search_params()
+    lib.tm_search_params_default(ctypes.byref(p))
+    assert (p.hamming_max, p.ratio_num, p.ratio_den, p.epipolar, p.resolve, p.rot_filter) == (50, 3, 5, 1, 1, 1)
+    assert abs(p.epi_chi2 - 3.84) < 1e-6 and p.mode == tm.TM_MODE_FUSED and p.lanes_per_query == 0
+    f = L.tm_fuse_params()
+    lib.tm_fuse_params_default(ctypes.byref(f))
+    assert abs(f.chi2 - 5.99) < 1e-6 and f.hamming_max == 50 and f.radius_scale == 3.0
+    # the Python defaults mirror the C defaults
+    s = tm.SearchParams().struct()
+    for k, _ in L.tm_search_params._fields_:
+        if k != "epi_chi2":
+            assert getattr(s, k) == getattr(p, k), k
+
+
+def test_null_arguments_rejected(lib):
+    from paper_2511_02036_gb300 import _lib as L
+    # argument checks happen before any CUDA call
+    assert lib.tm_ctx_create(0, None, 100, 0, None) == L.TM_ERR_INVALID_ARG
+    assert lib.tm_ctx_destroy(None) == L.TM_ERR_INVALID_ARG
+    assert lib.tm_plan_run(None, None) == L.TM_ERR_INVALID_ARG
+    assert b"null" in lib.tm_last_error()
+    cam = L.tm_camera(640, 480, 450.0, 450.0, 320.0, 240.0)
+    h = ctypes.c_void_p()
+    assert lib.tm_ctx_create(0, ctypes.byref(cam), 0, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG
+    assert lib.tm_ctx_create(0, ctypes.byref(cam), L.TM_MAX_KP_LIMIT + 1, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG

@@ -1,0 +1,195 @@
+"""Batched path (one persistent launch for many steps, CUDA-graph plans, autotuning), the
+keyframe store's error behaviour, and full-size cfg2 parity in the benchmark's launch
+configuration.  GPU == oracle bit-exactly."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_02036_gb300 as tm
+    return tm
+
+
+def steps_of(w):
+    return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                 mps=s.get("mps")) for s in w["steps"]]
+
+
+def oracle_results(w):
+    pairs, fuses, cs, cf = [], [], 0, 0
+    for st in w["steps"]:
+        r, c = O.search_step(w["cam"], w["frames"], st)
+        pairs.extend(r)
+        cs += c
+        f, c2 = O.fuse_step(w["cam"], w["frames"], st)
+        fuses.append(f)
+        cf += c2
+    return pairs, fuses, cs, cf
+
+
+def assert_same(res, exp):
+    pairs, fuses, cs, cf = exp
+    assert len(res.pairs) == len(pairs) and len(res.fuses) == len(fuses)
+    for g, e in zip(res.pairs, pairs):
+        np.testing.assert_array_equal(g, e)
+    for g, e in zip(res.fuses, fuses):
+        np.testing.assert_array_equal(g, e)
+    assert res.n_comparisons_search == cs
+    assert res.n_comparisons_fuse == cf
+
+
+def load_all(ctx, w):
+    ids = sorted(set(i for s in w["steps"] for i in [s["q"]] + s["nbrs"]))
+    ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return W.make_cfg2(seed=2100, n_steps=6)
+
+
+def test_batch_run_small(tm, small_batch):
+    w = small_batch
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        for lanes in (0, 1, 4, 32):
+            assert_same(ctx.batch_run(steps_of(w), sp=tm.SearchParams(lanes_per_query=lanes)), exp)
+        assert_same(ctx.batch_run(steps_of(w), sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR)), exp)
+
+
+def test_plan_graph_replay(tm, small_batch):
+    w = small_batch
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        with ctx.plan(steps_of(w)) as plan:
+            info = plan.info()
+            assert info["kernels_per_run"] == 2 and info["ctas"] >= 1
+            for _ in range(3):
+                plan.run()
+                assert_same(plan.results(), exp)
+            # a keyframe used by a live plan cannot be removed
+            with pytest.raises(tm.TMError) as e:
+                ctx.remove_keyframe(w["steps"][0]["q"])
+            assert e.value.status == tm.TM_ERR_BUSY
+        ctx.remove_keyframe(w["steps"][0]["q"])
+        with ctx.plan(steps_of(w)[1:], sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR)) as plan:
+            plan.run()
+            r = plan.results()
+            n0 = len(w["steps"][0]["nbrs"])
+            for g, e in zip(r.pairs, exp[0][n0:]):
+                np.testing.assert_array_equal(g, e)
+
+
+def test_batch_order_invariance(tm, small_batch):
+    """A step's results do not depend on the other steps of the batch nor on their order."""
+    w = small_batch
+    steps = steps_of(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        full = ctx.batch_run(steps)
+        rev = ctx.batch_run(steps[::-1])
+        n = [len(s["nbrs"]) for s in steps]
+        starts = np.concatenate([[0], np.cumsum(n)])
+        rstarts = np.concatenate([[0], np.cumsum(n[::-1])])
+        for k in range(len(steps)):
+            kk = len(steps) - 1 - k
+            for j in range(n[k]):
+                np.testing.assert_array_equal(full.pairs[starts[k] + j], rev.pairs[rstarts[kk] + j])
+            np.testing.assert_array_equal(full.fuses[k], rev.fuses[kk])
+            alone = ctx.batch_run([steps[k]])
+            for j in range(n[k]):
+                np.testing.assert_array_equal(full.pairs[starts[k] + j], alone.pairs[j])
+            np.testing.assert_array_equal(full.fuses[k], alone.fuses[0])
+
+
+def test_store_errors(tm):
+    cam = W.CAM_CFG0
+    rng = np.random.default_rng(0)
+    a, b = W.random_keyframe(rng, 100, cam), W.random_keyframe(rng, 200, cam)
+    with tm.Context(cam, max_kp=256) as ctx:
+        ctx.add_keyframe(1, a)
+        with pytest.raises(tm.TMError) as e:
+            ctx.add_keyframe(1, b)
+        assert e.value.status == tm.TM_ERR_EXISTS
+        with pytest.raises(tm.TMError) as e:
+            ctx.search(1, [9])
+        assert e.value.status == tm.TM_ERR_NOT_FOUND
+        with pytest.raises(tm.TMError) as e:
+            ctx.add_keyframe(2, W.random_keyframe(rng, 300, cam))
+        assert e.value.status == tm.TM_ERR_INVALID_ARG
+        bad = dict(b)
+        bad["level"] = b["level"].copy()
+        bad["level"][5] = 9
+        with pytest.raises(tm.TMError) as e:
+            ctx.add_keyframe(3, bad)
+        assert e.value.status == tm.TM_ERR_INVALID_ARG
+        ctx.add_keyframe(2, b)
+        assert ctx.keyframe_size(2) == 200
+        ctx.remove_keyframe(2)
+        with pytest.raises(tm.TMError) as e:
+            ctx.remove_keyframe(2)
+        assert e.value.status == tm.TM_ERR_NOT_FOUND
+        # capacity: the C call reports the required count and writes nothing
+        a2 = dict(a)
+        a2["desc"] = a["desc"].copy()
+        ctx.add_keyframe(4, a2)
+        nb = np.array([4], np.uint64)
+        out = np.full((1, 3), -7, np.int32)
+        po = np.zeros(2, np.int32)
+        n_out = ctypes.c_size_t()
+        sp = tm.SearchParams(ratio_num=0, rot_filter=False, epipolar=False).struct()
+        st = tm.tm_search_triangulation(ctx.handle, 1, nb.ctypes.data, 1, ctypes.byref(sp), None, None,
+                                        out.ctypes.data, 0, ctypes.byref(n_out), po.ctypes.data, None, None)
+        assert st == tm.TM_ERR_CAPACITY and n_out.value == 100 and out[0, 0] == -7
+
+
+def test_memory_budget_admission(tm):
+    cam = W.CAM_CFG0
+    rng = np.random.default_rng(1)
+    with tm.Context(cam, max_kp=512) as probe:
+        slot = probe.stats()["slot_bytes"]
+    with tm.Context(cam, max_kp=512, budget=3 * slot + 10) as ctx:
+        for k in range(3):
+            ctx.add_keyframe(k, W.random_keyframe(rng, 300, cam))
+        with pytest.raises(tm.TMError) as e:
+            ctx.add_keyframe(3, W.random_keyframe(rng, 300, cam))
+        assert e.value.status == tm.TM_ERR_NO_MEMORY
+        # all-or-nothing batched add
+        with pytest.raises(tm.TMError):
+            ctx.add_keyframes([7, 8], [W.random_keyframe(rng, 10, cam)] * 2)
+        assert ctx.stats()["slots_used"] == 3
+        ctx.remove_keyframe(0)
+        ctx.add_keyframe(3, W.random_keyframe(rng, 300, cam))
+        assert ctx.stats()["slots_used"] == 3
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return W.make_cfg2()
+
+
+def test_cfg2_full_size_parity(tm, cfg2):
+    """The benchmark's workload (64 steps, 821 pairs, 537k map points) in the benchmark's
+    launch configuration (autotuned plan, CUDA graph): every pair and every step equals the
+    oracle."""
+    w = cfg2
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        with ctx.plan(steps_of(w)) as plan:
+            plan.run()
+            plan.run()
+            assert_same(plan.results(), exp)
