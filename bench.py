@@ -1,0 +1,483 @@
+"""Benchmark of the local-mapping search path (correspondence search + map-point fusion).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+A step is one pass of the whole hot path over one batch: the 64 new keyframes of a
+64-step EuRoC-shaped batch (5..20 neighbours and 600..2000 keypoints per frame, uneven)
+enter the device-resident store (sort by BoW node + projection grid), then every
+(new keyframe, neighbour) pair is searched and every step's map points are fused, in one
+persistent launch replayed from a CUDA graph.  Inputs are synthetic (seeded generator), all
+resident in HBM before the timed region; the L2 is flushed (256 MB written) before each
+timed step because the batch (~95 MB) fits in L2.  Prints one JSON line.
+
+`e2e` is the same workload through the public one-shot call with pinned host buffers:
+new keyframes, masks and map points copied in, results copied out, every step.
+The plain one-pair-per-launch form, the oracle on the host cores, and a continuous-batching
+serving run (Poisson arrivals) are reported next to it.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcomparisons/s and keyframes/s (search+fuse); p50/p99 per-keyframe latency"
+WORKLOAD = "cfg2: 64 independent EuRoC-shaped local-mapping steps, 752x480 f=458, 5-20 neighbours, 600-2000 keypoints/frame"
+KP_BYTES = 51     # per stored keypoint read by the path: desc 32, xy 8, angle 4, node 4, orig 2, level 1
+MP_BYTES = 65     # per map point: pos 12, normal 12, desc 32, min/max dist 8, skip 1
+OUT_BYTES = 12    # per emitted match / fusion candidate
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--serve-kf", type=int, default=600, help="keyframes of the serving stream (0: skip)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi -i accepts an index or a GPU UUID
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(kernel_file, profile):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if the
+    kernel source has not changed since the counters were taken."""
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", profile)))
+        src = open(os.path.join(ROOT, "paper_2511_02036_gb300", "csrc", kernel_file), "rb").read()
+        if prof.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None, "kernel changed since the ncu capture"
+        return prof["dram_bytes_per_launch"], prof.get("note")
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu capture"
+
+
+def steps_of(w):
+    return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                 mps=s.get("mps")) for s in w["steps"]]
+
+
+def algorithmic_bytes(w, res):
+    """Unique bytes the path must touch for one batch: every keyframe of the batch once
+    (keypoint arrays), the map points once, one mask byte per masked keypoint, 12 bytes per
+    output."""
+    ids = set()
+    mask = 0
+    for s in w["steps"]:
+        ids.add(s["q"])
+        ids.update(s["nbrs"])
+        if s.get("q_free") is not None:
+            mask += len(s["q_free"])
+        if s.get("nbr_free") is not None:
+            mask += sum(len(m) for m in s["nbr_free"])
+    kp = sum(w["frames"][i]["n"] for i in ids)
+    mp = sum(s["mps"]["n"] for s in w["steps"] if s.get("mps") is not None)
+    out = len(res.matches) + len(res.fuse)
+    return kp * KP_BYTES + mp * MP_BYTES + mask + out * OUT_BYTES, dict(keypoints=kp, map_points=mp,
+                                                                         mask_bytes=mask, outputs=out)
+
+
+def oracle_sample(w, seconds, t_limit=None):
+    """The oracle as it stands, single thread, over the workload's steps in order until
+    `seconds` of CPU work: returns (keyframes, comparisons, elapsed)."""
+    import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    n = cmp = 0
+    k = 0
+    while True:
+        st = w["steps"][k % len(w["steps"])]
+        _, c1 = O.search_step(w["cam"], w["frames"], st)
+        _, c2 = O.fuse_step(w["cam"], w["frames"], st)
+        n += 1
+        cmp += c1 + c2
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (t_limit and k >= t_limit):
+            return n, cmp, el
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from gen import workloads as W
+    import oracle as O
+    w = W.make_cfg2(seed=args.seed)
+    per = 4  # local-mapping steps (keyframes) per timed step: a bounded sample of the batch
+    for _ in range(args.warmup):
+        oracle_sample(w, 0.0, t_limit=1)
+    t0 = time.perf_counter()
+    n = cmp = 0
+    k = 0
+    for _ in range(args.steps):
+        for _ in range(per):
+            st = w["steps"][k % len(w["steps"])]
+            _, c1 = O.search_step(w["cam"], w["frames"], st)
+            _, c2 = O.fuse_step(w["cam"], w["frames"], st)
+            cmp += c1 + c2
+            n += 1
+            k += 1
+    el = time.perf_counter() - t0
+    kfps = n / el
+    line = {"impl": "reference", "metric": METRIC, "value": kfps, "unit": "keyframes/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "%d local-mapping steps per timed step" % per},
+            "gcomparisons_per_s": cmp / el / 1e9,
+            "cpu_baseline": {"value": kfps, "unit": "keyframes/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of the cfg2 batch in order, single thread" % n},
+            "e2e": {"value": kfps, "unit": "keyframes/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- my arm
+
+def run_mine(args, rank, world, local_rank):
+    import torch
+
+    import paper_2511_02036_gb300 as tm
+    from gen import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    # a stream of our own: the legacy default stream has handle 0, which the library reads
+    # as "use the context's stream"
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    dist = world > 1
+    if dist:
+        import torch.distributed as D
+
+    w = W.make_cfg2(seed=args.seed + 1000 * rank)  # weak scaling: each rank its own batch
+    steps = steps_of(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+    ctx = tm.Context(w["cam"], max_kp=2048, device=local_rank)
+    ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
+
+    # device-resident inputs
+    st_arr, masks, mps, _keep = tm.pack_batch(steps, ctx.sizes)
+    dt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d_masks = dt(masks)
+    d_mps = {k: (dt(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
+    d_new = [dict(desc=dt(f["desc"]), xy=dt(f["xy"]), angle=dt(f["angle"]), level=dt(f["level"]),
+                  node=dt(f["node"].view(np.int32)), Tcw=f["Tcw"])
+             for f in (w["frames"][i] for i in new_ids)]
+    off_steps = [dict(kf_id=st_arr[k].kf_id, nbrs=steps[k]["nbrs"], q_free_off=st_arr[k].q_free_off,
+                      nbr_free_off=st_arr[k].nbr_free_off, mp_begin=st_arr[k].mp_begin,
+                      mp_count=st_arr[k].mp_count) for k in range(len(steps))]
+    torch.cuda.synchronize(dev)
+    plan = ctx.plan(off_steps, masks=d_masks, mps=d_mps, new=(new_ids, d_new))
+    info = plan.info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist:
+            D.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        plan.run(stream)
+    torch.cuda.synchronize(dev)
+    res = plan.results(stream)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = []
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = Clocks(("GPU-%s" % uuid) if uuid is not None else local_rank)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        plan.run(stream)
+        ev1[k].record(stream)
+        stage.append(plan.stage_times())  # waits for this run (events inside the graph)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    stage = np.array(stage)
+    total_s = step_ms.sum() / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        D.all_reduce(t, op=D.ReduceOp.MAX)
+        total_s = float(t.item())
+    res2 = plan.results(stream)
+    assert np.array_equal(res.matches, res2.matches) and np.array_equal(res.fuse, res2.fuse)
+    n_kf = len(new_ids) * args.steps * world
+    ncmp = res.n_comparisons_search + res.n_comparisons_fuse
+    value = n_kf / total_s
+    gcomp = ncmp * args.steps * world / total_s / 1e9
+
+    # roofline of the dominant kernel (search + fusion), timed inside the graph
+    pk, pk_kind = peaks()
+    alg, parts = algorithmic_bytes(w, res)
+    kern_ms = float(stage[:, 1].mean())
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    traffic, traffic_note = kernel_traffic("kernels.cu", "batch_kernel_cfg2.json")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "kernel": "batch_kernel (search + fusion, persistent)", "peak_kind": pk_kind,
+            "algorithmic_bytes": alg, "algorithmic_parts": parts, "kernel_ms": kern_ms,
+            "traffic_note": traffic_note}
+
+    out = {"metric": METRIC, "value": value, "unit": "keyframes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
+           "data": "synthetic (seeded generator; EuRoC-shaped)",
+           "config": {"workload": WORKLOAD, "new_keyframes_per_step": len(new_ids),
+                      "pairs": sum(len(s["nbrs"]) for s in steps), "map_points": int(mps["n"]),
+                      "l2": "flushed before each timed step (256 MB written)",
+                      "launch": info, "parallelism": "replicas" if world == 1 else "dp%d" % world},
+           "gcomparisons_per_s": gcomp,
+           "comparisons_per_step": ncmp,
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                          "note": "batch form: every keyframe of a step completes with its batch"},
+           "stage_ms": {"ingest": float(stage[:, 0].mean()), "search_fuse": kern_ms,
+                        "compact": float(stage[:, 2].mean())},
+           "roofline": roof, "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
+           "wall_s_timed_region": t_wall}
+
+    # ---------------------------------------------------------------- plain per-pair form
+    if not args.no_plain:
+        pplan = None
+        try:
+            pplan = ctx.plan(off_steps, masks=d_masks, mps=d_mps, sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR))
+            pplan.run(stream)
+            torch.cuda.synchronize(dev)
+            pres = pplan.results(stream)
+            assert np.array_equal(pres.matches, res.matches) and np.array_equal(pres.fuse, res.fuse)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0.record(stream)
+                pplan.run(stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            pms = float(np.mean(ms))
+            out["plain_form"] = {"value": len(new_ids) / (pms / 1e3), "unit": "keyframes/s",
+                                 "ms_per_step": pms, "kernels_per_step": pplan.info()["kernels_per_run"],
+                                 "note": "same batch, one pair per launch sequence (memsets + 3 kernels per pair, 2 per fusion), keyframes already stored"}
+        finally:
+            if pplan is not None:
+                pplan.close()
+
+    plan.close()
+
+    # ---------------------------------------------------------------- end to end
+    if not args.no_e2e:
+        for i in new_ids:
+            ctx.remove_keyframe(i)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h_masks = pin(masks)
+        h_mps = {k: (pin(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
+        h_new = [dict(desc=pin(f["desc"]), xy=pin(f["xy"]), angle=pin(f["angle"]), level=pin(f["level"]),
+                      node=pin(f["node"].view(np.int32)), Tcw=f["Tcw"]) for f in (w["frames"][i] for i in new_ids)]
+        # bytes copied in per step: masks, map-point arrays, the new keyframes' arrays
+        # (desc 32 + xy 8 + angle 4 + level 1 + node 4 = 49 B per keypoint), the work list
+        h2d = (int(masks.nbytes) + sum(int(v.nbytes) for v in mps.values() if isinstance(v, np.ndarray))
+               + sum(w["frames"][i]["n"] for i in new_ids) * 49)
+        n_items = sum(len(s["nbrs"]) for s in steps) + sum((s["mps"]["n"] + 255) // 256 for s in steps)
+        h2d += n_items * 44
+        d2h = 4 * (n_items + 1) + 16 + OUT_BYTES * (len(res.matches) + len(res.fuse))
+
+        def e2e_step():
+            r = ctx.batch_run(off_steps, masks=h_masks, mps=h_mps, new=(new_ids, h_new))
+            for i in new_ids:
+                ctx.remove_keyframe(i)
+            return r
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(3, args.steps // 2)
+        for _ in range(ke):
+            r = e2e_step()
+        barrier()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev)
+            D.all_reduce(t, op=D.ReduceOp.MAX)
+            el = float(t.item())
+        assert np.array_equal(r.matches, res.matches) and np.array_equal(r.fuse, res.fuse)
+        out["e2e"] = {"value": len(new_ids) * ke * world / el, "unit": "keyframes/s",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": 1e3 * el / ke,
+                      "api": "tm_batch_run (pinned host buffers: new keyframes, masks, map points in; matches and fusion candidates out) + tm_store_remove_keyframe of the 64 new keyframes"}
+
+    # ---------------------------------------------------------------- serving
+    if args.serve_kf > 0 and rank == 0:
+        out["serving"] = run_serving(tm, args.serve_kf, local_rank)
+
+    # ---------------------------------------------------------------- oracle on host cores
+    if rank == 0:
+        n, cmp, el = oracle_sample(w, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": n / el, "unit": "keyframes/s", "cores": 1, "kind": "oracle",
+                               "sample": "%d local-mapping steps of the same batch in order (search + fusion), single thread, %.1f s" % (n, el),
+                               "gcomparisons_per_s": cmp / el / 1e9}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_serving(tm, n_kf, device):
+    """Continuous batching under Poisson arrivals at 20, 100 and 500 keyframes/s on a stream
+    of n_kf keyframes (cfg4 model), and the plain per-pair form served one request at a
+    time at 500 keyframes/s."""
+    from gen import workloads as W
+    w = W.make_stream_cfg4(seed=4000, n_kf=n_kf, duration_s=600.0 * n_kf / 3000.0)
+    out = {"keyframes": n_kf, "stream": "cfg4 model: 752x480, 1000-2000 keypoints, 5-20 neighbours"}
+
+    def serve(rate, **cfg):
+        rng = np.random.default_rng(7)
+        arr = np.cumsum(rng.exponential(1.0 / rate, n_kf))
+        with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+            with ctx.server(**cfg) as srv:
+                t0 = time.perf_counter()
+                t0_lib = tm.tm_now()
+                tickets = []
+                for k, st in enumerate(w["steps"]):
+                    while time.perf_counter() - t0 < arr[k]:
+                        time.sleep(1e-4)
+                    tickets.append(srv.submit(st["q"], w["frames"][st["q"]], st["nbrs"], st["q_free"],
+                                              st["nbr_free"], st["mps"]))
+                lat, done = [], 0.0
+                for t in tickets:
+                    info = srv.poll(t, timeout=600.0)
+                    assert info["done"] and info["status"] == 0
+                    lat.append(info["t_done"] - info["t_submit"])
+                    done = max(done, info["t_done"])
+                    srv.take(t)
+        lat = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "offered_kf_per_s": rate,
+                "served_kf_per_s": n_kf / (done - t0_lib)}
+
+    for rate in (20, 100, 500):
+        if rate == 20 and n_kf > 600:
+            continue
+        out["continuous_batching_%d" % rate] = serve(rate, max_batch_requests=64, max_inflight_batches=3)
+    out["plain_per_pair_500"] = serve(500, max_batch_requests=1, max_inflight_batches=1,
+                                      sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR))
+    return out
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch
+        import torch.distributed as D
+        torch.cuda.set_device(local_rank)
+        D.init_process_group("nccl" if args.impl == "mine" else "gloo")
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            import __graft_entry__ as g
+            if rank == 0 or world == 1:
+                g.build()
+            if world > 1:
+                import torch.distributed as D
+                D.barrier()
+                g.build()
+            run_mine(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as D
+            D.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -258,8 +258,11 @@ class Sequence:
         self.created_by = np.concatenate(created_by)
         npool = len(self.pts)
         p_geo = 1.0 / (1.0 + span)
-        self.first = self.created_by - rng.geometric(p_geo, npool) + 1
-        self.last = self.created_by + rng.geometric(p_geo, npool) - 1
+        span_max = 80  # geometric spans are cut at 80 frames (P > 80 is ~5e-6 at mean 6)
+        self.first = self.created_by - np.minimum(rng.geometric(p_geo, npool), span_max) + 1
+        self.last = self.created_by + np.minimum(rng.geometric(p_geo, npool), span_max) - 1
+        order = np.argsort(self.created_by, kind="stable")
+        assert np.all(order == np.arange(npool))  # created frame by frame
         self.base_desc = random_desc(rng, npool)
         self.base_node = rng.integers(0, n_nodes, npool)
         self.base_angle = rng.uniform(0, 360, npool)
@@ -268,7 +271,9 @@ class Sequence:
         # --- frames
         self.frames = []
         for k in range(nf):
-            cand = np.nonzero((self.first <= k) & (self.last >= k))[0]
+            lo = np.searchsorted(self.created_by, k - span_max)
+            hi = np.searchsorted(self.created_by, k + span_max, side="right")
+            cand = lo + np.nonzero((self.first[lo:hi] <= k) & (self.last[lo:hi] >= k))[0]
             u, v, z = project(poses[k], cam, self.pts[cand])
             ok = in_image(cam, u, v, z)
             cand, u, v = cand[ok], u[ok], v[ok]
@@ -301,57 +306,63 @@ class Sequence:
         Neighbour keypoints of mapped world points have one; in the new keyframe half of
         them are tracked (not free, and their map point is skipped by fusion).  Clutter
         keypoints of the neighbours are lifted to single-view map points until the map-point
-        batch reaches `n_mps` (default: half the neighbours' keypoints)."""
+        batch reaches `n_mps` (default: half the neighbours' keypoints).
+
+        Map points: position = world point + N(0, 5 mm); descriptor = that of its first
+        observing neighbour; normal = mean unit viewing direction over observing neighbours;
+        maxDist = distance to the first observer * 1.2^level, minDist = maxDist / 1.2^7."""
         rng = self.rng
         fq = self.frames[q]
         q_wp = fq["wp"]
-        tracked = np.zeros(fq["n"], bool)
-        mq = (q_wp >= 0)
+        mq = q_wp >= 0
         mq[mq] = self.mapped[q_wp[mq]]
+        tracked = np.zeros(fq["n"], bool)
         tracked[mq] = rng.random(int(mq.sum())) < tracked_frac
-        tracked_wp = set(int(w) for w in q_wp[tracked])
+        tracked_wp = np.unique(q_wp[tracked])
         q_free = (~tracked).astype(np.uint8)
-        nbr_free = []
-        mp_pos, mp_desc, mp_norm_acc, mp_ref, mp_wp = [], [], [], [], []
-        seen = {}
-        lifted = []
+        nbr_has, obs_w, obs_f, obs_j, clutter = [], [], [], [], []
         for f in nbrs:
             fr = self.frames[f]
             w = fr["wp"]
             has = np.zeros(fr["n"], bool)
             pool_idx = np.nonzero(w >= 0)[0]
-            m = self.mapped[w[pool_idx]]
-            has[pool_idx[m]] = True
-            for j in pool_idx[m]:
-                wid = int(w[j])
-                if wid not in seen:
-                    seen[wid] = (f, j)
-            lifted.append((f, np.nonzero(w < 0)[0]))
-            nbr_free.append(has)
-        # single-view map points from neighbour clutter
-        total_clutter = sum(len(c) for _, c in lifted)
+            sel = pool_idx[self.mapped[w[pool_idx]]]
+            has[sel] = True
+            obs_w.append(w[sel]); obs_f.append(np.full(len(sel), f)); obs_j.append(sel)
+            clutter.append(np.nonzero(w < 0)[0])
+            nbr_has.append(has)
+        nn = len(nbrs)
+        obs_w = np.concatenate(obs_w) if nn else np.zeros(0, np.int64)
+        obs_f = np.concatenate(obs_f) if nn else np.zeros(0, np.int64)
+        obs_j = np.concatenate(obs_j) if nn else np.zeros(0, np.int64)
+        uw, first = np.unique(obs_w, return_index=True)
+        n_pool = len(uw)
         if n_mps is None:
             n_mps = int(0.5 * sum(self.frames[f]["n"] for f in nbrs))
-        want = max(0, n_mps - len(seen))
-        frac = 0.0 if total_clutter == 0 else min(1.0, want / total_clutter)
+        total_clutter = sum(len(c) for c in clutter)
+        frac = 0.0 if total_clutter == 0 else min(1.0, max(0, n_mps - n_pool) / total_clutter)
         if clutter_mp_frac is not None:
             frac = clutter_mp_frac
-        pos, desc, normal, mind, maxd, skip, wps = [], [], [], [], [], [], []
-        for wid, (f, j) in sorted(seen.items()):
-            fr = self.frames[f]
-            p = self.pts[wid] + rng.normal(0, 0.005, 3)
-            pos.append(p)
-            desc.append(fr["desc"][j])
-            obs = [camera_center(self.frames[g]["Tcw"]) for g in nbrs
-                   if wid in self._wp_set(g)]
-            nrm = np.mean([(p - c) / np.linalg.norm(p - c) for c in obs], axis=0)
-            normal.append(nrm / np.linalg.norm(nrm))
-            dist = np.linalg.norm(p - camera_center(fr["Tcw"]))
-            mx = dist * SCALE_FACTOR ** int(fr["level"][j])
-            maxd.append(mx); mind.append(mx / SCALE_FACTOR ** (N_LEVELS - 1))
-            skip.append(1 if wid in tracked_wp else 0)
-            wps.append(wid)
-        for (f, idx), has in zip(lifted, nbr_free):
+        centers = {f: camera_center(self.frames[f]["Tcw"]) for f in nbrs}
+        # pool map points
+        pos_p = self.pts[uw] + rng.normal(0, 0.005, (n_pool, 3))
+        ref_f, ref_j = obs_f[first], obs_j[first]
+        desc_p = np.stack([self.frames[f]["desc"][j] for f, j in zip(ref_f, ref_j)]) \
+            if n_pool else np.zeros((0, DESC_BYTES), np.uint8)
+        slot = np.searchsorted(uw, obs_w)
+        cobs = np.stack([centers[f] for f in obs_f]) if len(obs_f) else np.zeros((0, 3))
+        v = pos_p[slot] - cobs
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        acc = np.zeros((n_pool, 3))
+        np.add.at(acc, slot, v)
+        nrm_p = acc / np.linalg.norm(acc, axis=1)[:, None] if n_pool else acc
+        cref = np.stack([centers[f] for f in ref_f]) if n_pool else np.zeros((0, 3))
+        lvl_ref = np.array([self.frames[f]["level"][j] for f, j in zip(ref_f, ref_j)], np.int64)
+        maxd_p = np.linalg.norm(pos_p - cref, axis=1) * SCALE_FACTOR ** lvl_ref
+        skip_p = np.isin(uw, tracked_wp).astype(np.uint8)
+        # single-view map points lifted from neighbour clutter
+        pos_c, desc_c, nrm_c, maxd_c = [], [], [], []
+        for f, idx, has in zip(nbrs, clutter, nbr_has):
             if frac <= 0 or len(idx) == 0:
                 continue
             take = idx[rng.random(len(idx)) < frac]
@@ -360,23 +371,23 @@ class Sequence:
             d = rng.uniform(2.0, 10.0, len(take))
             p = backproject(fr["Tcw"], self.cam, fr["xy"][take, 0].astype(np.float64),
                             fr["xy"][take, 1].astype(np.float64), d)
-            c = camera_center(fr["Tcw"])
-            for t_i, jj in enumerate(take):
-                pos.append(p[t_i]); desc.append(fr["desc"][jj])
-                nv = p[t_i] - c
-                normal.append(nv / np.linalg.norm(nv))
-                mx = np.linalg.norm(nv) * SCALE_FACTOR ** int(fr["level"][jj])
-                maxd.append(mx); mind.append(mx / SCALE_FACTOR ** (N_LEVELS - 1))
-                skip.append(0); wps.append(-1)
+            nv = p - centers[f]
+            dist = np.linalg.norm(nv, axis=1)
+            pos_c.append(p); desc_c.append(fr["desc"][take]); nrm_c.append(nv / dist[:, None])
+            maxd_c.append(dist * SCALE_FACTOR ** fr["level"][take].astype(np.int64))
+        nc = sum(len(x) for x in pos_c)
+        cat = lambda xs, shape: np.concatenate(xs) if xs else np.zeros(shape)  # noqa: E731
+        pos = np.concatenate([pos_p, cat(pos_c, (0, 3))])
         nm = len(pos)
+        maxd = np.concatenate([maxd_p, cat(maxd_c, (0,))])
         mps = dict(n=nm,
-                   pos=np.asarray(pos, np.float32).reshape(nm, 3),
-                   normal=np.asarray(normal, np.float32).reshape(nm, 3),
-                   desc=np.asarray(desc, np.uint8).reshape(nm, DESC_BYTES),
-                   min_dist=np.asarray(mind, np.float32).reshape(nm),
-                   max_dist=np.asarray(maxd, np.float32).reshape(nm),
-                   skip=np.asarray(skip, np.uint8).reshape(nm),
-                   wp=np.asarray(wps, np.int64).reshape(nm))
+                   pos=pos.astype(np.float32).reshape(nm, 3),
+                   normal=np.concatenate([nrm_p, cat(nrm_c, (0, 3))]).astype(np.float32).reshape(nm, 3),
+                   desc=np.concatenate([desc_p, cat(desc_c, (0, DESC_BYTES)).astype(np.uint8)]).reshape(nm, DESC_BYTES),
+                   min_dist=(maxd / SCALE_FACTOR ** (N_LEVELS - 1)).astype(np.float32),
+                   max_dist=maxd.astype(np.float32),
+                   skip=np.concatenate([skip_p, np.zeros(nc, np.uint8)]),
+                   wp=np.concatenate([uw, -np.ones(nc, np.int64)]))
         if nm:
             perm = rng.permutation(nm)
             for k in ("pos", "normal", "desc", "min_dist", "max_dist", "skip", "wp"):
@@ -384,18 +395,11 @@ class Sequence:
         step = dict(q=q, nbrs=list(nbrs), mps=mps)
         if with_masks:
             step["q_free"] = q_free
-            step["nbr_free"] = [(~h).astype(np.uint8) for h in nbr_free]
+            step["nbr_free"] = [(~h).astype(np.uint8) for h in nbr_has]
         else:
             step["q_free"] = None
             step["nbr_free"] = None
         return step
-
-    def _wp_set(self, f):
-        cache = self.__dict__.setdefault("_wps", {})
-        if f not in cache:
-            w = self.frames[f]["wp"]
-            cache[f] = set(int(x) for x in w[w >= 0])
-        return cache[f]
 
 
 # --------------------------------------------------------------------------- configurations

@@ -87,8 +87,11 @@ typedef struct {
     const uint8_t *skip;    /* [n] or NULL: 1 = already observed by the target keyframe     */
 } tm_mappoint_view;
 
-#define TM_MODE_FUSED 0      /* one CTA per pair, whole pipeline in shared memory (default) */
+#define TM_MODE_FUSED 0      /* one CTA per pair, whole pipeline in shared memory (default);
+                                the pair's keyframes are staged there by bulk copies when
+                                they fit, else read from global memory                      */
 #define TM_MODE_PER_PAIR 1   /* plain form: one pair at a time, one launch per stage        */
+#define TM_MODE_FUSED_GLOBAL 2 /* fused, keyframe arrays always read from global memory    */
 
 typedef struct {
     int32_t hamming_max;    /* accept best <= hamming_max (50)                              */
@@ -98,7 +101,7 @@ typedef struct {
     int32_t epipolar;       /* 1 = apply the epipolar gate                                  */
     int32_t resolve;        /* 1 = one match per target keypoint                            */
     int32_t rot_filter;     /* 1 = 30-bin rotation-histogram filter                         */
-    int32_t mode;           /* TM_MODE_FUSED or TM_MODE_PER_PAIR                            */
+    int32_t mode;           /* TM_MODE_FUSED, TM_MODE_PER_PAIR or TM_MODE_FUSED_GLOBAL      */
     int32_t lanes_per_query;/* 0 = autotuned; else 1, 2, 4, 8, 16 or 32                     */
 } tm_search_params;
 
@@ -190,6 +193,14 @@ typedef struct {
     const uint8_t *masks;    /* host or device, mask_bytes bytes (may be NULL if unused)    */
     size_t mask_bytes;
     tm_mappoint_view mps;    /* all steps' map points (n may be 0)                          */
+    /* Keyframes entering the store with this batch (Sec. IV-B), e.g. the steps' new
+     * keyframes: they are stored before the search runs, in the same launch sequence, and
+     * stay stored afterwards.  Ids must not be stored yet.  A plan stages them once and
+     * re-runs their ingest (same data, same slots) at every tm_plan_run, so that a run covers
+     * keyframe entry + search + fusion.  Arrays: host or device. */
+    int32_t n_new;
+    const uint64_t *new_ids;          /* host [n_new]                                       */
+    const tm_keyframe_view *new_kfs;  /* host [n_new]                                       */
 } tm_batch_inputs;
 
 /* Results, host buffers.  Search matches of all steps, step-major then neighbour order:
@@ -205,7 +216,8 @@ typedef struct {
 } tm_batch_result;
 
 /* One-shot: upload, one persistent launch, download.  TM_ERR_CAPACITY sets n_matches and
- * n_fuse to the required sizes and writes nothing else. */
+ * n_fuse to the required sizes and writes nothing else.  On any failure the batch's new
+ * keyframes are not stored. */
 tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
                        const tm_batch_inputs *in, const tm_search_params *sp,
                        const tm_fuse_params *fp, tm_batch_result *res, void *stream);
@@ -221,6 +233,10 @@ tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
 /* Launch configuration the plan uses: threads per CTA, lanes per query, CTAs, kernels per run. */
 tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
                        int32_t *kernels_per_run);
+/* Device time of the stages of the plan's last completed run, from CUDA events recorded inside
+ * its graph: ms[0] keyframe ingest, ms[1] search + fusion kernel, ms[2] compaction.  Waits
+ * for the run to finish.  A stage the plan does not have reads 0. */
+tm_status tm_plan_stage_times(tm_plan *plan, float ms[3]);
 tm_status tm_plan_destroy(tm_plan *plan);
 
 /* ---------------------------------------------------------------------------- serving

@@ -18,7 +18,8 @@ import numpy as np
 from . import _lib as L
 from ._lib import (TM_ERR_BUSY, TM_ERR_CAPACITY, TM_ERR_CUDA, TM_ERR_EXISTS,  # noqa: F401
                    TM_ERR_INVALID_ARG, TM_ERR_NO_MEMORY, TM_ERR_NOT_FOUND, TM_ERR_TIMEOUT,
-                   TM_MODE_FUSED, TM_MODE_PER_PAIR, TM_OK, TM_MAX_KP_LIMIT)
+                   TM_MODE_FUSED, TM_MODE_FUSED_GLOBAL, TM_MODE_PER_PAIR, TM_OK,
+                   TM_MAX_KP_LIMIT)
 
 _clib = L.load()
 for _name in L.SIGNATURES:
@@ -214,12 +215,13 @@ def _collect(r, bufs):
                        int(r.n_comparisons_search), int(r.n_comparisons_fuse))
 
 
-def _result_caps(steps, kf_sizes, resolve=True):
+def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
+    """Output capacities from the known keyframe sizes (unknown ids: the C call reports them)."""
     mc = 0
     for s in steps:
-        nq = kf_sizes[int(s["kf_id"])]
+        nq = kf_sizes.get(int(s["kf_id"]), default)
         for t in s["nbrs"]:
-            nt = kf_sizes[int(t)]
+            nt = kf_sizes.get(int(t), default)
             mc += min(nq, nt) if resolve else nq
     fc = sum(int(s["mps"]["n"]) for s in steps if s.get("mps") is not None)
     return mc, fc
@@ -313,7 +315,7 @@ class Context:
         return out[:n_out.value].copy(), int(ncmp.value)
 
     # ---------------------------------------------------------------- batches
-    def _inputs(self, steps, masks=None, mps=None):
+    def _inputs(self, steps, masks=None, mps=None, new=None):
         keep = []
         if masks is None and mps is None:
             st, masks, mps, k2 = pack_batch(steps, self.sizes)
@@ -332,25 +334,41 @@ class Context:
         inp.masks = _ptr(masks) if masks is not None and len(masks) else None
         inp.mask_bytes = 0 if masks is None else int(np.prod(masks.shape)) if isinstance(masks, np.ndarray) else masks.numel()
         inp.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
+        if new is not None:
+            ids, kfs = new
+            idarr = np.ascontiguousarray(ids, np.uint64)
+            views = (L.tm_keyframe_view * max(1, len(kfs)))()
+            for k, kf in enumerate(kfs):
+                views[k] = keyframe_view(kf, keep)
+                self.sizes[int(idarr[k])] = views[k].n
+            keep.extend([idarr, views])
+            inp.n_new, inp.new_ids, inp.new_kfs = len(kfs), idarr.ctypes.data, ctypes.addressof(views)
         keep.append(st)
         return st, inp, keep
 
-    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None):
+    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None):
         """One-shot batch (tm_batch_run).  Without masks/mps the steps carry their own
-        q_free / nbr_free / mps and are packed here."""
+        q_free / nbr_free / mps and are packed here.  new = (ids, keyframes) entering the
+        store with the batch."""
         sp = sp or SearchParams()
-        st, inp, keep = self._inputs(steps, masks, mps)
+        st, inp, keep = self._inputs(steps, masks, mps, new)
         mc, fc = _result_caps(steps, self.sizes, sp.resolve)
         if masks is not None or mps is not None:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
         r, bufs = _result_struct(mc, sum(len(s["nbrs"]) for s in steps), fc, len(steps))
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
-        check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
-                           ctypes.byref(fps), ctypes.byref(r), _stream(stream)))
+        try:
+            check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
+                               ctypes.byref(fps), ctypes.byref(r), _stream(stream)))
+        except TMError:
+            if new is not None:
+                for i in new[0]:
+                    self.sizes.pop(int(i), None)
+            raise
         return _collect(r, bufs)
 
-    def plan(self, steps, masks=None, mps=None, sp=None, fp=None):
-        return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams())
+    def plan(self, steps, masks=None, mps=None, sp=None, fp=None, new=None):
+        return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams(), new)
 
     def server(self, **cfg):
         return Server(self, **cfg)
@@ -359,9 +377,9 @@ class Context:
 class Plan:
     """A prepared batch (tm_plan): inputs resident on the GPU, launch captured in a graph."""
 
-    def __init__(self, ctx, steps, masks, mps, sp, fp):
+    def __init__(self, ctx, steps, masks, mps, sp, fp, new=None):
         self.ctx = ctx
-        st, inp, self._keep = ctx._inputs(steps, masks, mps)
+        st, inp, self._keep = ctx._inputs(steps, masks, mps, new)
         self.caps = _result_caps(steps, ctx.sizes, sp.resolve)
         if mps is not None:
             self.caps = (self.caps[0], max(self.caps[1], int(mps["n"])))
@@ -386,6 +404,12 @@ class Plan:
         check(tm_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),  # noqa: F821
                            ctypes.byref(d)))
         return dict(threads=a.value, lanes=b.value, ctas=c.value, kernels_per_run=d.value)
+
+    def stage_times(self):
+        """(ingest, search + fusion, compaction) device milliseconds of the last run."""
+        ms = np.zeros(3, np.float32)
+        check(tm_plan_stage_times(self.handle, ms.ctypes.data))  # noqa: F821
+        return tuple(float(x) for x in ms)
 
     def close(self):
         if self.handle:

@@ -6,7 +6,8 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtm.so")
+# TM_LIBRARY may name another build of the same sources (for example an instrumented one)
+LIB_PATH = os.environ.get("TM_LIBRARY") or os.path.join(_HERE, "libtm.so")
 
 c_i32, c_u64, c_i64, c_f32, c_f64, c_sz, c_p = (ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
                                                 ctypes.c_float, ctypes.c_double, ctypes.c_size_t,
@@ -23,6 +24,7 @@ TM_ERR_TIMEOUT = 7
 TM_ERR_BUSY = 8
 TM_MODE_FUSED = 0
 TM_MODE_PER_PAIR = 1
+TM_MODE_FUSED_GLOBAL = 2
 TM_MAX_KP_LIMIT = 8192
 
 
@@ -68,7 +70,8 @@ class tm_step(ctypes.Structure):
 
 
 class tm_batch_inputs(ctypes.Structure):
-    _fields_ = [("masks", c_p), ("mask_bytes", c_sz), ("mps", tm_mappoint_view)]
+    _fields_ = [("masks", c_p), ("mask_bytes", c_sz), ("mps", tm_mappoint_view),
+                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p)]
 
 
 class tm_batch_result(ctypes.Structure):
@@ -118,6 +121,7 @@ SIGNATURES = {
     "tm_plan_run": (c_i32, [c_p, c_p]),
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
+    "tm_plan_stage_times": (c_i32, [c_p, c_p]),
     "tm_plan_destroy": (c_i32, [c_p]),
     "tm_server_config_default": (None, [P(tm_server_config)]),
     "tm_server_start": (c_i32, [c_p, P(tm_server_config), P(c_p)]),

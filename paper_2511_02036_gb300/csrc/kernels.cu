@@ -54,7 +54,7 @@ __device__ void mat3_mul(const double *A, const double *B, double *C) {
 // Fundamental matrix of the pair (Sec. IV-C epipolar validation): relative motion
 // R = R_Q R_T^T, t = t_Q - R t_T; F = K^-T [t]x R K^-1 in float64, products evaluated
 // ((K^-T [t]x) R) K^-1, each entry rounded to float32.  x_Q^T F x_T = 0.
-__device__ void fundamental_f32(const CamConst &cam, const double *Tq, const double *Tt,
+__device__ __noinline__ void fundamental_f32(const CamConst &cam, const double *Tq, const double *Tt,
                                 float *F) {
     double Rq[9], RtT[9], tq[3], tt[3];
     for (int r = 0; r < 3; ++r) {
@@ -197,50 +197,70 @@ __device__ __forceinline__ uint32_t pack_res(uint32_t t, uint32_t d, uint32_t bi
 
 // ------------------------------------------------------------------------- ingest
 
-__device__ void bitonic_sort_u64(unsigned long long *a, int N) {
-    for (int k = 2; k <= N; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long x = a[i], y = a[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) { a[i] = y; a[ixj] = x; }
-                }
+constexpr int kSortE = 8;  // keys per thread-chunk of the block merge sort
+
+// Sorts N unique keys in shared memory (N a power of two >= kSortE): every chunk of kSortE
+// keys is sorted in registers, then runs are merged pairwise (merge path: each chunk of the
+// output finds its split point by binary search and merges kSortE keys).  a and b are two
+// buffers of N keys; returns the one holding the result.  All threads of the block call it.
+template <typename K>
+__device__ K *block_merge_sort(K *a, K *b, int N) {
+    const int chunks = N / kSortE;
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        K r[kSortE];
+#pragma unroll
+        for (int k = 0; k < kSortE; ++k) r[k] = a[c * kSortE + k];
+#pragma unroll
+        for (int pass = 0; pass < kSortE; ++pass)
+#pragma unroll
+            for (int k = pass & 1; k + 1 < kSortE; k += 2)
+                if (r[k + 1] < r[k]) { const K t = r[k]; r[k] = r[k + 1]; r[k + 1] = t; }
+#pragma unroll
+        for (int k = 0; k < kSortE; ++k) a[c * kSortE + k] = r[k];
+    }
+    __syncthreads();
+    K *src = a, *dst = b;
+    for (int L = kSortE; L < N; L <<= 1) {
+        for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+            const int o = c * kSortE;
+            const int pb = (o / (2 * L)) * (2 * L), d = o - pb;
+            const K *A = src + pb, *B = src + pb + L;
+            int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] < B[d - 1 - mid]) lo = mid + 1; else hi = mid;
             }
-            __syncthreads();
-        }
-}
-__device__ void bitonic_sort_u32(uint32_t *a, int N) {
-    for (int k = 2; k <= N; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint32_t x = a[i], y = a[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) { a[i] = y; a[ixj] = x; }
-                }
+            int ia = lo, ib = d - lo;
+#pragma unroll
+            for (int k = 0; k < kSortE; ++k) {
+                const bool take_a = ib >= L || (ia < L && A[ia] < B[ib]);
+                dst[o + k] = take_a ? A[ia++] : B[ib++];
             }
-            __syncthreads();
         }
+        __syncthreads();
+        K *t = src; src = dst; dst = t;
+    }
+    return src;
 }
 
+// One CTA per keyframe entering the store (Sec. IV-B): stable order by BoW node (key
+// node << 32 | caller index), gather of every keypoint array into that order, then the
+// projection grid (key cell << 16 | node-order position) and its cell starts.
 __global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
-    extern __shared__ unsigned long long skeys[];
+    extern __shared__ __align__(16) unsigned long long skeys[];
     const IngestJob &job = A.jobs[blockIdx.x];
     const int n = job.n;
-    int N = 1;
+    int N = kSortE;
     while (N < n) N <<= 1;
     const SlotLayout L = SlotLayout::make(A.cap);
     unsigned char *base = job.slot;
-    // 1. stable sort by node: key = node << 32 | caller index
+    unsigned long long *k0 = skeys, *k1 = skeys + N;
+    // padding keys are distinct and above every real key
     for (int i = threadIdx.x; i < N; i += blockDim.x)
-        skeys[i] = i < n ? ((unsigned long long)A.node[job.src + i] << 32) | (unsigned)i
-                         : ~0ull;
+        k0[i] = i < n ? ((unsigned long long)A.node[job.src + i] << 32) | (unsigned)i
+                      : ~0ull - (unsigned long long)i;
     __syncthreads();
-    bitonic_sort_u64(skeys, N);
-    // 2. gather the keypoint arrays into node order
+    const unsigned long long *sorted = block_merge_sort(k0, k1, N);
     uint4 *desc = reinterpret_cast<uint4 *>(base + L.desc);
     float2 *xy = reinterpret_cast<float2 *>(base + L.xy);
     float *angle = reinterpret_cast<float *>(base + L.angle);
@@ -248,7 +268,7 @@ __global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
     uint16_t *orig = reinterpret_cast<uint16_t *>(base + L.orig);
     uint8_t *level = base + L.level;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const uint32_t o = (uint32_t)(skeys[p] & 0xFFFFFFFFull);
+        const uint32_t o = (uint32_t)(sorted[p] & 0xFFFFFFFFull);
         const uint32_t s = job.src + o;
         desc[2 * p] = A.desc[2 * s];
         desc[2 * p + 1] = A.desc[2 * s + 1];
@@ -260,20 +280,19 @@ __global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
         level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
     }
     __syncthreads();
-    // 3. projection grid: sort (cell, sorted position), then cell starts by binary search
-    uint32_t *ck = reinterpret_cast<uint32_t *>(skeys);
+    uint32_t *c0 = reinterpret_cast<uint32_t *>(skeys), *c1 = c0 + N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        uint32_t key = kNone;
+        uint32_t key = 0xFFFFFFFFu - (uint32_t)i;
         if (i < n) {
             const float2 v = xy[i];
             const int cx = grid_cell(v.x, A.cell_w_inv, kGridCols);
             const int cy = grid_cell(v.y, A.cell_h_inv, kGridRows);
             key = ((uint32_t)(cy * kGridCols + cx) << 16) | (uint32_t)i;
         }
-        ck[i] = key;
+        c0[i] = key;
     }
     __syncthreads();
-    bitonic_sort_u32(ck, N);
+    const uint32_t *ck = block_merge_sort(c0, c1, N);
     uint16_t *gitems = reinterpret_cast<uint16_t *>(base + L.grid_items);
     uint16_t *gstart = reinterpret_cast<uint16_t *>(base + L.grid_start);
     for (int k = threadIdx.x; k < n; k += blockDim.x) gitems[k] = (uint16_t)(ck[k] & 0xFFFFu);
@@ -287,6 +306,53 @@ __global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
     }
 }
 
+// ------------------------------------------------------------------------- TMA helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's (and, after a CTA barrier, the CTA's) generic-proxy shared-memory
+// accesses before later async-proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity to complete, at most ~2 s of SM clock.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 4000000000ll) return false;
+    return true;
+}
+
 // ------------------------------------------------------------------------- batch kernel
 
 struct ItemShared {
@@ -298,58 +364,70 @@ struct ItemShared {
     float R[9], t[3], O[3];
     uint32_t keep;
     uint32_t item;
-    unsigned long long cmp;
+    uint32_t cmp;
 };
 
-// One (new keyframe, neighbour) pair.  Shared arrays (stride sn = max keypoints):
-//   tnode[sn]  neighbour's node ids (sorted)    win[sn]  per target: lowest (d << 16 | q)
-//   accq[sn]   per sorted query: (t << 16 | d)  res[sn]  per caller-order query: packed kept
+// Adds a per-thread count to S.cmp: one shared atomic per warp.  All threads of the warp call.
+__device__ __forceinline__ void warp_count(uint32_t v, uint32_t *dst) {
+    const uint32_t sum = __reduce_add_sync(kFull, v);
+    if ((threadIdx.x & 31u) == 0 && sum) atomicAdd(dst, sum);
+}
+
+// Top-3 rotation bins by warp 0 (same rule as top3_mask).  All lanes of warp 0 call.
+__device__ __forceinline__ uint32_t top3_mask_warp(const uint32_t *hist) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t c = lane < (uint32_t)kBins ? hist[lane] : 0u;
+    uint32_t taken = 0, mask = 0, mx = 0;
+    for (int r = 0; r < 3; ++r) {
+        // highest count wins, ties to the lowest bin; empty or taken bins never
+        const uint32_t key = (c > 0 && !((taken >> lane) & 1u)) ? (c << 5) | (31u - lane) : 0u;
+        const uint32_t m = __reduce_max_sync(kFull, key);
+        if (m == 0) break;
+        const uint32_t b = 31u - (m & 31u), cnt = m >> 5;
+        if (r == 0) mx = cnt;
+        if (r == 0 || !(10u * cnt < mx)) mask |= 1u << b;
+        taken |= 1u << b;
+    }
+    return mask;
+}
+
+// Pair state shared by the staged and unstaged search.
+struct PairArrays {
+    KfView Q, T;               // keypoint arrays of both keyframes (shared or global memory)
+    const uint32_t *tnode;     // neighbour's node ids, node order (shared memory)
+    uint32_t *win;             // [nT] per target: lowest (dist << 16 | caller query index)
+    uint32_t *accq;            // [nQ] per node-order query: (target << 16 | dist) or kNone
+    uint32_t *res;             // [nQ] per caller-order query: packed kept match or kNone
+    const uint8_t *mq, *mt;    // eligibility masks indexed by caller order, or null
+};
+
+// Correspondence search of one (new keyframe, neighbour) pair (Sec. IV-C).  S.F, S.thr,
+// S.hist (zero) and S.cmp (zero) are set and win[0..nT) = kNone before the call.
 template <int G>
-__device__ void search_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
-                            uint32_t *sm, int sn, ItemShared &S) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
-    const int nQ = Q.hdr->n, nT = T.hdr->n;
-    uint32_t *tnode = sm, *win = sm + sn, *accq = sm + 2 * sn, *res = sm + 3 * sn;
+__device__ __forceinline__ void search_core(const BatchArgs &A, const WorkItem &w, uint32_t idx, int nQ, int nT,
+                            const PairArrays &P, ItemShared &S) {
+    const KfView &Q = P.Q, &T = P.T;
     const int tid = threadIdx.x, bs = blockDim.x;
-
-    if (tid == 0) {
-        fundamental_f32(A.cam, Q.hdr->Tcw, T.hdr->Tcw, S.F);
-        S.cmp = 0ull;
-    }
-    if (tid < 32) S.hist[tid] = 0;
-    if (tid < kLevels) {
-        const float s = level_scale(tid);
-        S.thr[tid] = fmul(A.sp.epi_chi2, fmul(s, s));
-    }
-    for (int j = tid; j < nT; j += bs) { tnode[j] = T.node[j]; win[j] = kNone; }
-    for (int i = tid; i < nQ; i += bs) res[i] = kNone;
-    __syncthreads();
-
-    const uint8_t *mq = w.a == kNone ? nullptr : A.masks + w.a;
-    const uint8_t *mt = w.b == kNone ? nullptr : A.masks + w.b;
     const bool epi = A.sp.epipolar != 0;
-
     // Join + match: G lanes per query, node-sorted queries in consecutive groups.
     const int gpc = bs / G, g = tid / G, sub = tid % G;
-    unsigned long long my_cmp = 0;
+    uint32_t my_cmp = 0;
     for (int p0 = 0; p0 < nQ; p0 += gpc) {
         const int p = p0 + g;
-        uint32_t bkey = kNone;   // (dist << 16) | sorted target
+        uint32_t bkey = kNone;   // (dist << 16) | node-order target
         uint32_t sec = 0xFFFFu;  // second-smallest distance
-        if (p < nQ && (!mq || mq[Q.orig[p]])) {
+        if (p < nQ && (!P.mq || P.mq[Q.orig[p]])) {
             const uint32_t nd = Q.node[p];
-            const int lo = lower_bound_u32(tnode, nT, nd);
-            const int hi = (lo < nT && tnode[lo] == nd) ? upper_bound_u32(tnode, lo, nT, nd) : lo;
+            const int lo = lower_bound_u32(P.tnode, nT, nd);
+            const int hi = (lo < nT && P.tnode[lo] == nd) ? upper_bound_u32(P.tnode, lo, nT, nd) : lo;
             if (lo < hi) {
                 const uint4 q0 = Q.desc[2 * p], q1 = Q.desc[2 * p + 1];
                 const float2 xq = Q.xy[p];
                 const Line l = epi_line(S.F, xq.x, xq.y);
                 for (int j = lo + sub; j < hi; j += G) {
-                    if (mt && !mt[T.orig[j]]) continue;
+                    if (P.mt && !P.mt[T.orig[j]]) continue;
                     ++my_cmp;
-                    const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
-                    const uint32_t d = (uint32_t)hamming(q0, q1, t0, t1);
+                    const uint32_t d = (uint32_t)hamming(q0, q1, T.desc[2 * j], T.desc[2 * j + 1]);
                     if (epi) {
                         const float2 xt = T.xy[j];
                         if (!epi_pass(l, xt.x, xt.y, S.thr[T.level[j]])) continue;
@@ -377,31 +455,44 @@ __device__ void search_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
                 if (ok) {
                     const uint32_t j = bkey & 0xFFFFu;
                     acc = (j << 16) | best;
-                    if (A.sp.resolve) atomicMin(&win[j], (best << 16) | Q.orig[p]);
+                    if (A.sp.resolve) atomicMin(&P.win[j], (best << 16) | Q.orig[p]);
                 }
             }
-            accq[p] = acc;
+            P.accq[p] = acc;  // (may alias Q.node[p], read above by this group only)
         }
     }
-    if (my_cmp) atomicAdd(&S.cmp, my_cmp);
+    warp_count(my_cmp, &S.cmp);
     __syncthreads();
 
-    // One match per target, rotation histogram.
+    // One match per target, rotation histogram (one atomic per distinct bin per warp);
+    // every caller-order query gets its res.
     const bool rot = A.sp.rot_filter != 0;
-    for (int p = tid; p < nQ; p += bs) {
-        const uint32_t acc = accq[p];
-        if (acc == kNone) continue;
-        const uint32_t j = acc >> 16, d = acc & 0xFFFFu, io = Q.orig[p];
-        if (A.sp.resolve && win[j] != ((d << 16) | io)) continue;
-        uint32_t bin = 0;
-        if (rot) {
-            bin = (uint32_t)rot_bin(Q.angle[p], T.angle[j]);
-            atomicAdd(&S.hist[bin], 1u);
+    for (int p0 = 0; p0 < nQ; p0 += bs) {
+        const int p = p0 + tid;
+        uint32_t bin = kNone;
+        if (p < nQ) {
+            const uint32_t acc = P.accq[p], io = Q.orig[p];
+            uint32_t r = kNone;
+            if (acc != kNone) {
+                const uint32_t j = acc >> 16, d = acc & 0xFFFFu;
+                if (!A.sp.resolve || P.win[j] == ((d << 16) | io)) {
+                    bin = rot ? (uint32_t)rot_bin(Q.angle[p], T.angle[j]) : 0u;
+                    r = pack_res(T.orig[j], d, bin);
+                }
+            }
+            P.res[io] = r;
         }
-        res[io] = pack_res(T.orig[j], d, bin);
+        if (rot) {
+            const unsigned peers = __match_any_sync(kFull, bin);
+            if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
+                atomicAdd(&S.hist[bin], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
-    if (tid == 0) S.keep = rot ? top3_mask(S.hist) : kNone;
+    if (tid < 32) {
+        const uint32_t k = rot ? top3_mask_warp(S.hist) : kNone;
+        if (tid == 0) S.keep = k;
+    }
     __syncthreads();
     const uint32_t keep = S.keep;
 
@@ -409,7 +500,7 @@ __device__ void search_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
     uint32_t base = 0;
     for (int i0 = 0; i0 < nQ; i0 += bs) {
         const int i = i0 + tid;
-        const uint32_t r = i < nQ ? res[i] : kNone;
+        const uint32_t r = i < nQ ? P.res[i] : kNone;
         const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
         uint32_t tot;
         const uint32_t pos = block_scan_flag(f, S.wtot, tot);
@@ -418,18 +509,124 @@ __device__ void search_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
     }
     if (tid == 0) {
         A.counts[idx] = base;
-        if (S.cmp) atomicAdd(&A.ncmp[0], S.cmp);
+        if (S.cmp) atomicAdd(&A.ncmp[0], (unsigned long long)S.cmp);
     }
 }
 
-// Fusion of up to blockDim map points into one keyframe, one thread per map point.
-// Returns the packed (keypoint, distance) or kNone; adds window comparisons to *cmp.
+// Pair constants: fundamental matrix (formed by the pair-setup kernel), thresholds,
+// histogram and counter reset.
+__device__ __forceinline__ void pair_setup(const BatchArgs &A, uint32_t idx, ItemShared &S) {
+    const int tid = threadIdx.x;
+    if (tid < 9) S.F[tid] = A.pair_F[9 * (size_t)idx + tid];
+    if (tid == 9) S.cmp = 0u;
+    if (tid < 32) S.hist[tid] = 0;
+    if (tid >= 32 && tid < 32 + kLevels) {
+        const float s = level_scale(tid - 32);
+        S.thr[tid - 32] = fmul(A.sp.epi_chi2, fmul(s, s));
+    }
+}
+
+// Unstaged pair: keypoint arrays read from global memory; shared arrays of stride sn.
+template <int G>
+__device__ __forceinline__ void search_item_global(const BatchArgs &A, const WorkItem &w, uint32_t idx,
+                                   uint32_t *sm, int sn, ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    PairArrays P;
+    P.Q = KfView::at(w.q, L);
+    P.T = KfView::at(w.t, L);
+    const int nQ = P.Q.hdr->n, nT = P.T.hdr->n;
+    uint32_t *tnode = sm;
+    P.tnode = tnode;
+    P.win = sm + sn;
+    P.accq = sm + 2 * sn;
+    P.res = sm + 3 * sn;
+    P.mq = w.a == kNone ? nullptr : A.masks + w.a;
+    P.mt = w.b == kNone ? nullptr : A.masks + w.b;
+    pair_setup(A, idx, S);
+    for (int j = threadIdx.x; j < nT; j += blockDim.x) { tnode[j] = P.T.node[j]; P.win[j] = kNone; }
+    __syncthreads();
+    search_core<G>(A, w, idx, nQ, nT, P, S);
+}
+
+// Staged pair: both keyframes' arrays are brought into shared memory by bulk copies (one
+// mbarrier phase), the masks by plain loads, so that the whole pipeline runs from shared
+// memory.  accq overlays the query node array (each entry is read by its own query group
+// before it is written), res overlays the query descriptors (dead after the match loop).
+// Returns false if the copies did not complete in time.
+template <int G>
+__device__ __forceinline__ bool search_item_staged(const BatchArgs &A, const WorkItem &w, uint32_t idx,
+                                   unsigned char *sm, uint64_t *bar, uint32_t parity,
+                                   ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const StageLayout G2 = StageLayout::make(A.sn);
+    const KfView Qg = KfView::at(w.q, L), Tg = KfView::at(w.t, L);
+    const int nQ = Qg.hdr->n, nT = Tg.hdr->n;
+    const uint32_t q16 = (uint32_t)((nQ + 15) & ~15), t16 = (uint32_t)((nT + 15) & ~15);
+    PairArrays P;
+    P.Q = Qg;
+    P.T = Tg;
+    P.Q.desc = reinterpret_cast<const uint4 *>(sm + G2.qdesc);
+    P.Q.xy = reinterpret_cast<const float2 *>(sm + G2.qxy);
+    P.Q.node = reinterpret_cast<const uint32_t *>(sm + G2.qnode);
+    P.Q.angle = reinterpret_cast<const float *>(sm + G2.qangle);
+    P.Q.orig = reinterpret_cast<const uint16_t *>(sm + G2.qorig);
+    P.T.desc = reinterpret_cast<const uint4 *>(sm + G2.tdesc);
+    P.T.xy = reinterpret_cast<const float2 *>(sm + G2.txy);
+    P.T.node = reinterpret_cast<const uint32_t *>(sm + G2.tnode);
+    P.T.angle = reinterpret_cast<const float *>(sm + G2.tangle);
+    P.T.orig = reinterpret_cast<const uint16_t *>(sm + G2.torig);
+    P.T.level = sm + G2.tlevel;
+    P.tnode = P.T.node;
+    P.win = reinterpret_cast<uint32_t *>(sm + G2.win);
+    P.accq = reinterpret_cast<uint32_t *>(sm + G2.qnode);
+    P.res = reinterpret_cast<uint32_t *>(sm + G2.qdesc);
+    uint8_t *tmask = sm + G2.tmask, *qmask = sm + G2.qmask;
+    P.mq = w.a == kNone ? nullptr : qmask;
+    P.mt = w.b == kNone ? nullptr : tmask;
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        const uint32_t bytes = q16 * (32 + 8 + 4 + 4 + 2) + t16 * (32 + 8 + 4 + 4 + 2 + 1);
+        mbar_expect_tx(bar, bytes);
+        if (q16) {
+            bulk_g2s(sm + G2.qdesc, Qg.desc, q16 * 32, bar);
+            bulk_g2s(sm + G2.qxy, Qg.xy, q16 * 8, bar);
+            bulk_g2s(sm + G2.qnode, Qg.node, q16 * 4, bar);
+            bulk_g2s(sm + G2.qangle, Qg.angle, q16 * 4, bar);
+            bulk_g2s(sm + G2.qorig, Qg.orig, q16 * 2, bar);
+        }
+        if (t16) {
+            bulk_g2s(sm + G2.tdesc, Tg.desc, t16 * 32, bar);
+            bulk_g2s(sm + G2.txy, Tg.xy, t16 * 8, bar);
+            bulk_g2s(sm + G2.tnode, Tg.node, t16 * 4, bar);
+            bulk_g2s(sm + G2.tangle, Tg.angle, t16 * 4, bar);
+            bulk_g2s(sm + G2.torig, Tg.orig, t16 * 2, bar);
+            bulk_g2s(sm + G2.tlevel, Tg.level, t16, bar);
+        }
+    }
+    pair_setup(A, idx, S);
+    uint32_t *win = P.win;
+    for (int j = threadIdx.x; j < nT; j += blockDim.x) win[j] = kNone;
+    if (P.mq)
+        for (int i = threadIdx.x; i < nQ; i += blockDim.x) qmask[i] = A.masks[w.a + i];
+    if (P.mt)
+        for (int j = threadIdx.x; j < nT; j += blockDim.x) tmask[j] = A.masks[w.b + j];
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity));
+    if (!ok) return false;
+    search_core<G>(A, w, idx, nQ, nT, P, S);
+    return true;
+}
+
+// Fusion of map points into one keyframe, one thread per map point (Sec. IV-D).
+// Returns the packed (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
 __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &cam,
                                              const FuseConst &fp, const ItemShared &S,
                                              const float *pos, const float *normal,
                                              const uint4 *desc, float mind, float maxd,
-                                             unsigned long long &cmp) {
+                                             uint32_t &cmp) {
+    // every global load of the map point first, so that their latencies overlap
     const float X = pos[0], Y = pos[1], Z = pos[2];
+    const float nx = normal[0], ny = normal[1], nz = normal[2];
+    const uint4 m0 = desc[0], m1 = desc[1];
     const float xc = fadd(fadd(fadd(fmul(S.R[0], X), fmul(S.R[1], Y)), fmul(S.R[2], Z)), S.t[0]);
     const float yc = fadd(fadd(fadd(fmul(S.R[3], X), fmul(S.R[4], Y)), fmul(S.R[5], Z)), S.t[1]);
     const float zc = fadd(fadd(fadd(fmul(S.R[6], X), fmul(S.R[7], Y)), fmul(S.R[8], Z)), S.t[2]);
@@ -441,7 +638,7 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
     const float pox = fsub(X, S.O[0]), poy = fsub(Y, S.O[1]), poz = fsub(Z, S.O[2]);
     const float dist = __fsqrt_rn(fadd(fadd(fmul(pox, pox), fmul(poy, poy)), fmul(poz, poz)));
     if (dist < mind || dist > maxd) return kNone;
-    const float cosv = fadd(fadd(fmul(pox, normal[0]), fmul(poy, normal[1])), fmul(poz, normal[2]));
+    const float cosv = fadd(fadd(fmul(pox, nx), fmul(poy, ny)), fmul(poz, nz));
     if (cosv < fmul(0.5f, dist)) return kNone;
     int pl = kLevels - 1;
     for (int l = 0; l < kLevels; ++l)
@@ -451,7 +648,6 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
     const int cx1 = grid_cell(fadd(u, r), cam.cell_w_inv, kGridCols) + 1;
     const int cy0 = grid_cell(fsub(v, r), cam.cell_h_inv, kGridRows) - 1;
     const int cy1 = grid_cell(fadd(v, r), cam.cell_h_inv, kGridRows) + 1;
-    const uint4 m0 = desc[0], m1 = desc[1];
     uint32_t best = kNone;  // (dist << 16) | caller keypoint index
     for (int cy = max(cy0, 0); cy <= min(cy1, kGridRows - 1); ++cy) {
         const int c0 = cy * kGridCols + max(cx0, 0), c1 = cy * kGridCols + min(cx1, kGridCols - 1);
@@ -475,7 +671,7 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
 
 // Pose-derived constants of a fusion target: R, t in float32 and the camera centre
 // O = -R^T t formed in float64; scale and reprojection thresholds per level.
-__device__ void fuse_setup(const KfHeader *h, float chi2, ItemShared &S) {
+__device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, ItemShared &S) {
     const int tid = threadIdx.x;
     if (tid < 9) S.R[tid] = __double2float_rn(h->Tcw[(tid / 3) * 4 + tid % 3]);
     if (tid >= 16 && tid < 19) {
@@ -493,23 +689,21 @@ __device__ void fuse_setup(const KfHeader *h, float chi2, ItemShared &S) {
     }
 }
 
-__device__ void fuse_item(const BatchArgs &A, const WorkItem &w, uint32_t idx, ItemShared &S) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    const KfView T = KfView::at(w.q, L);
+// The map points of one fusion item against keyframe view T, in tiles of blockDim, with
+// ordered compaction into the item's region.
+__device__ __forceinline__ void fuse_core(const BatchArgs &A, const WorkItem &w, uint32_t idx, const KfView &T,
+                          ItemShared &S) {
     const int tid = threadIdx.x, bs = blockDim.x;
-    if (tid == 0) S.cmp = 0ull;
-    fuse_setup(T.hdr, A.fp.chi2, S);
-    __syncthreads();
     uint32_t base = 0;
     for (int k0 = 0; k0 < (int)w.b; k0 += bs) {
         const int k = k0 + tid;
         const uint32_t m = w.a + (uint32_t)k;
-        unsigned long long cmp = 0;
+        uint32_t cmp = 0;
         uint32_t r = kNone;
         if (k < (int)w.b && !(A.mp_skip && A.mp_skip[m]))
             r = fuse_one(T, A.cam, A.fp, S, A.mp_pos + 3 * (size_t)m, A.mp_normal + 3 * (size_t)m,
                          A.mp_desc + 2 * (size_t)m, A.mp_min[m], A.mp_max[m], cmp);
-        if (cmp) atomicAdd(&S.cmp, cmp);
+        warp_count(cmp, &S.cmp);
         uint32_t tot;
         const uint32_t pos = block_scan_flag(r != kNone, S.wtot, tot);
         if (r != kNone)
@@ -518,21 +712,88 @@ __device__ void fuse_item(const BatchArgs &A, const WorkItem &w, uint32_t idx, I
     }
     if (tid == 0) {
         A.counts[idx] = base;
-        if (S.cmp) atomicAdd(&A.ncmp[1], S.cmp);
+        if (S.cmp) atomicAdd(&A.ncmp[1], (unsigned long long)S.cmp);
     }
 }
 
-template <int G>
-__device__ __forceinline__ void search_dispatch(const BatchArgs &A, const WorkItem &w,
-                                                uint32_t idx, uint32_t *sm, int sn,
-                                                ItemShared &S) {
-    search_item<G>(A, w, idx, sm, sn, S);
+__device__ __forceinline__ void fuse_item_global(const BatchArgs &A, const WorkItem &w, uint32_t idx, ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const KfView T = KfView::at(w.q, L);
+    if (threadIdx.x == 0) S.cmp = 0u;
+    fuse_setup(T.hdr, A.fp.chi2, S);
+    __syncthreads();
+    fuse_core(A, w, idx, T, S);
 }
 
-__global__ void __launch_bounds__(512) batch_kernel(BatchArgs A, int sn) {
-    extern __shared__ uint32_t smem[];
+// Staged fusion: the target keyframe's keypoint arrays and grid index are bulk-copied into
+// shared memory first.
+__device__ __forceinline__ bool fuse_item_staged(const BatchArgs &A, const WorkItem &w, uint32_t idx,
+                                 unsigned char *sm, uint64_t *bar, uint32_t parity, ItemShared &S) {
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const StageLayout G2 = StageLayout::make(A.sn);
+    const KfView Tg = KfView::at(w.q, L);
+    const int nT = Tg.hdr->n;
+    const uint32_t t16 = (uint32_t)((nT + 15) & ~15);
+    KfView T = Tg;
+    T.desc = reinterpret_cast<const uint4 *>(sm + G2.fdesc);
+    T.xy = reinterpret_cast<const float2 *>(sm + G2.fxy);
+    T.orig = reinterpret_cast<const uint16_t *>(sm + G2.forig);
+    T.level = sm + G2.flevel;
+    T.grid_start = reinterpret_cast<const uint16_t *>(sm + G2.fgstart);
+    T.grid_items = reinterpret_cast<const uint16_t *>(sm + G2.fgitems);
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, (uint32_t)(t16 * (32 + 8 + 2 + 1 + 2) + StageLayout::kGridStartBytes));
+        bulk_g2s(sm + G2.fgstart, Tg.grid_start, (uint32_t)StageLayout::kGridStartBytes, bar);
+        if (t16) {
+            bulk_g2s(sm + G2.fdesc, Tg.desc, t16 * 32, bar);
+            bulk_g2s(sm + G2.fxy, Tg.xy, t16 * 8, bar);
+            bulk_g2s(sm + G2.forig, Tg.orig, t16 * 2, bar);
+            bulk_g2s(sm + G2.flevel, Tg.level, t16, bar);
+            bulk_g2s(sm + G2.fgitems, Tg.grid_items, t16 * 2, bar);
+        }
+        S.cmp = 0u;
+    }
+    fuse_setup(Tg.hdr, A.fp.chi2, S);
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity));
+    if (!ok) return false;
+    fuse_core(A, w, idx, T, S);
+    return true;
+}
+
+template <int G>
+__device__ __forceinline__ bool run_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
+                                         unsigned char *sm, uint64_t *bar, uint32_t &parity,
+                                         ItemShared &S) {
+    if (A.staged) {
+        const bool ok = w.kind == kItemSearch ? search_item_staged<G>(A, w, idx, sm, bar, parity, S)
+                                              : fuse_item_staged(A, w, idx, sm, bar, parity, S);
+        parity ^= 1u;
+        return ok;
+    }
+    if (w.kind == kItemSearch)
+        search_item_global<G>(A, w, idx, reinterpret_cast<uint32_t *>(sm), A.sn, S);
+    else
+        fuse_item_global(A, w, idx, S);
+    return true;
+}
+
+// Persistent kernel: CTAs take work items (largest first) from an atomic counter until none
+// is left; the last CTA to finish turns the per-item counts into offsets.  Compiled for at
+// most 512 threads (up to 128 registers) and for 1024 threads (up to 64 registers).
+template <int kMaxThreads>
+__global__ void __launch_bounds__(kMaxThreads) batch_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ ItemShared S;
+    __shared__ __align__(8) uint64_t bar;
     __shared__ bool s_last;
+    if (threadIdx.x == 0 && A.staged) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    bool healthy = true;
     for (;;) {
         if (threadIdx.x == 0) S.item = atomicAdd(&A.counters[0], 1u);
         __syncthreads();
@@ -541,22 +802,26 @@ __global__ void __launch_bounds__(512) batch_kernel(BatchArgs A, int sn) {
         if (e >= A.n_items) break;
         const uint32_t idx = A.order[e];
         const WorkItem w = A.items[idx];
-        if (w.kind == kItemSearch) {
-            switch (A.lanes) {
-                case 1: search_dispatch<1>(A, w, idx, smem, sn, S); break;
-                case 2: search_dispatch<2>(A, w, idx, smem, sn, S); break;
-                case 4: search_dispatch<4>(A, w, idx, smem, sn, S); break;
-                case 8: search_dispatch<8>(A, w, idx, smem, sn, S); break;
-                case 16: search_dispatch<16>(A, w, idx, smem, sn, S); break;
-                default: search_dispatch<32>(A, w, idx, smem, sn, S); break;
-            }
-        } else {
-            fuse_item(A, w, idx, S);
+        bool ok;
+        switch (A.lanes) {
+            case 1: ok = run_item<1>(A, w, idx, smem, &bar, parity, S); break;
+            case 2: ok = run_item<2>(A, w, idx, smem, &bar, parity, S); break;
+            case 4: ok = run_item<4>(A, w, idx, smem, &bar, parity, S); break;
+            case 8: ok = run_item<8>(A, w, idx, smem, &bar, parity, S); break;
+            case 16: ok = run_item<16>(A, w, idx, smem, &bar, parity, S); break;
+            default: ok = run_item<32>(A, w, idx, smem, &bar, parity, S); break;
+        }
+        if (!ok) {  // a bulk copy did not land in time: report and stop taking work
+            if (threadIdx.x == 0) atomicOr(&A.counters[2], kStatusTimeout);
+            healthy = false;
+            break;
         }
         __syncthreads();
     }
-    // The last CTA to finish turns the per-item counts into offsets (no waiting: every
-    // other CTA has published its counts before its increment).
+    if (!healthy) {
+        // give the copies in flight a last bounded chance to land before the CTA exits
+        mbar_wait_bounded(&bar, parity ^ 1u);
+    }
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(&A.counters[1], 1u) == gridDim.x - 1;
@@ -569,7 +834,6 @@ __global__ void __launch_bounds__(512) batch_kernel(BatchArgs A, int sn) {
     for (uint32_t i0 = 0; i0 < A.n_items; i0 += bs) {
         const uint32_t i = i0 + tid;
         const uint32_t c = i < A.n_items ? __ldcg(A.counts + i) : 0u;
-        // block-wide inclusive scan of c
         uint32_t v = c;
         const unsigned lane = tid & 31u, warp = tid >> 5, nw = bs >> 5;
         for (int o = 1; o < 32; o <<= 1) {
@@ -596,10 +860,28 @@ __global__ void __launch_bounds__(512) batch_kernel(BatchArgs A, int sn) {
     if (tid == 0) A.offsets[A.n_items] = base;
 }
 
+// Pair setup (one thread per search item): the fundamental matrix of every pair from the
+// poses in the store, float64 rounded to float32.
+__global__ void pair_setup_kernel(BatchArgs A) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n_search) return;
+    const WorkItem w = A.items[i];
+    const KfHeader *qh = reinterpret_cast<const KfHeader *>(w.q);
+    const KfHeader *th = reinterpret_cast<const KfHeader *>(w.t);
+    double tq[12], tt[12];
+    for (int k = 0; k < 12; ++k) { tq[k] = qh->Tcw[k]; tt[k] = th->Tcw[k]; }
+    float F[9];
+    fundamental_f32(A.cam, tq, tt, F);
+    for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
+}
+
+// Gathers the per-item regions into the dense output, one warp per item.
 __global__ void copy_kernel(BatchArgs A) {
-    for (uint32_t i = blockIdx.x; i < A.n_items; i += gridDim.x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n_items; i += warps) {
         const uint32_t cnt = A.counts[i], dst = A.offsets[i], src = A.items[i].out_off;
-        for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) A.dense[dst + k] = A.padded[src + k];
+        for (uint32_t k = lane; k < cnt; k += 32) A.dense[dst + k] = A.padded[src + k];
     }
 }
 
@@ -736,11 +1018,11 @@ __global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float 
     __shared__ ItemShared S;
     const SlotLayout L = SlotLayout::make(cap);
     const KfView T = KfView::at(ts, L);
-    if (threadIdx.x == 0) S.cmp = 0ull;
+    if (threadIdx.x == 0) S.cmp = 0u;
     fuse_setup(T.hdr, fp.chi2, S);
     __syncthreads();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long cmp = 0;
+    uint32_t cmp = 0;
     if (m < n) {
         uint32_t r = kNone;
         if (!(skip && skip[m]))
@@ -748,9 +1030,9 @@ __global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float 
                          desc + 2 * (size_t)m, mn[m], mx[m], cmp);
         res[m] = r;
     }
-    if (cmp) atomicAdd(&S.cmp, cmp);
+    warp_count(cmp, &S.cmp);
     __syncthreads();
-    if (threadIdx.x == 0 && S.cmp) atomicAdd(ncmp, S.cmp);
+    if (threadIdx.x == 0 && S.cmp) atomicAdd(ncmp, (unsigned long long)S.cmp);
 }
 
 __global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uint32_t *running,
@@ -777,9 +1059,9 @@ __global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uin
 // ------------------------------------------------------------------------- launchers
 
 size_t ingest_smem_bytes(int cap) {
-    size_t N = 1;
+    size_t N = kSortE;
     while (N < (size_t)cap) N <<= 1;
-    return N * sizeof(unsigned long long);
+    return 2 * N * sizeof(unsigned long long);  // two merge buffers
 }
 
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
@@ -792,28 +1074,39 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t batch_smem_bytes(int smem_n) { return size_t(4) * 4 * (size_t)smem_n; }
+size_t batch_smem_bytes(int smem_n, bool staged) {
+    return staged ? StageLayout::make(smem_n).bytes : size_t(4) * 4 * (size_t)smem_n;
+}
 
 cudaError_t batch_kernel_prepare(size_t smem) {
-    return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 int batch_ctas_per_sm(int threads, size_t smem) {
     int n = 0;
     if (batch_kernel_prepare(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, threads, smem) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = threads <= 512
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<512>, threads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1024>, threads, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_batch(const BatchArgs &a, int ctas, int threads, size_t smem, cudaStream_t s) {
-    const int sn = (int)(smem / 16);
-    batch_kernel<<<ctas, threads, smem, s>>>(a, sn);
+    if (threads <= 512) batch_kernel<512><<<ctas, threads, smem, s>>>(a);
+    else batch_kernel<1024><<<ctas, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_setup(const BatchArgs &a, cudaStream_t s) {
+    if (a.n_search == 0) return cudaSuccess;
+    pair_setup_kernel<<<(a.n_search + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {
-    copy_kernel<<<ctas, 128, 0, s>>>(a);
+    copy_kernel<<<ctas, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,8 @@ constexpr int kGridCols = 64;
 constexpr int kGridRows = 48;
 constexpr int kGridCells = kGridCols * kGridRows;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr int kFuseChunk = 256;  // map points per fusion work item (one per thread)
+constexpr int kFuseChunk = 256;         // map points per fusion item, unstaged kernel
+constexpr int kFuseChunkStaged = 2048;  // map points per fusion item, staged kernel
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
@@ -95,7 +96,49 @@ struct IngestArgs {
     float cell_w_inv, cell_h_inv;  // grid cells per pixel
 };
 
+// Shared-memory carve of the staged batch kernel for a stride of sn keypoints (a multiple
+// of 16).  A search item stages both keyframes of its pair; a fusion item stages its target
+// keyframe and its projection grid.  The two carves overlay the same memory.
+struct StageLayout {
+    size_t tdesc, qdesc, txy, qxy, tnode, qnode, tangle, qangle, win, torig, qorig, tlevel,
+        tmask, qmask, search_bytes;
+    size_t fdesc, fxy, forig, flevel, fgstart, fgitems, fuse_bytes, bytes;
+    static constexpr size_t kGridStartBytes = ((size_t(kGridCells + 1) * 2 + 15) / 16) * 16;
+    __host__ __device__ static StageLayout make(int sn) {
+        StageLayout L;
+        const size_t n = (size_t)sn;
+        size_t o = 0;
+        L.tdesc = o;  o = align128(o + n * 32);
+        L.qdesc = o;  o = align128(o + n * 32);
+        L.txy = o;    o = align128(o + n * 8);
+        L.qxy = o;    o = align128(o + n * 8);
+        L.tnode = o;  o = align128(o + n * 4);
+        L.qnode = o;  o = align128(o + n * 4);
+        L.tangle = o; o = align128(o + n * 4);
+        L.qangle = o; o = align128(o + n * 4);
+        L.win = o;    o = align128(o + n * 4);
+        L.torig = o;  o = align128(o + n * 2);
+        L.qorig = o;  o = align128(o + n * 2);
+        L.tlevel = o; o = align128(o + n);
+        L.tmask = o;  o = align128(o + n);
+        L.qmask = o;  o = align128(o + n);
+        L.search_bytes = o;
+        o = 0;
+        L.fdesc = o;   o = align128(o + n * 32);
+        L.fxy = o;     o = align128(o + n * 8);
+        L.forig = o;   o = align128(o + n * 2);
+        L.flevel = o;  o = align128(o + n);
+        L.fgstart = o; o = align128(o + kGridStartBytes);
+        L.fgitems = o; o = align128(o + n * 2);
+        L.fuse_bytes = o;
+        L.bytes = L.search_bytes > L.fuse_bytes ? L.search_bytes : L.fuse_bytes;
+        return L;
+    }
+};
+
 enum : uint32_t { kItemSearch = 0, kItemFuse = 1 };
+// Device status word bits.
+enum : uint32_t { kStatusTimeout = 1u };
 
 // One unit of the persistent launch: a (new keyframe, neighbour) pair, or a chunk of up to
 // kFuseChunk map points fused into a keyframe.
@@ -135,7 +178,7 @@ struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
     const uint32_t *order;        // execution order (largest first)
     uint32_t n_items;
-    uint32_t *counters;           // [0] next item, [1] CTAs done
+    uint32_t *counters;           // [0] next item, [1] CTAs done, [2] status
     const uint8_t *masks;
     const float *mp_pos, *mp_normal, *mp_min, *mp_max;
     const uint4 *mp_desc;
@@ -144,6 +187,8 @@ struct BatchArgs {
     uint32_t *counts;             // [n_items]
     uint32_t *offsets;            // [n_items + 1] exclusive scan of counts, written by last CTA
     unsigned long long *ncmp;     // [2] search, fuse comparisons
+    float *pair_F;                // [n_search][9] fundamental matrix of each search item
+    uint32_t n_search;            // search items come first in logical order
     Out3 *dense;                  // compacted output
     uint32_t *status;             // device error word
     SearchConst sp;
@@ -151,6 +196,8 @@ struct BatchArgs {
     CamConst cam;
     int32_t cap;                  // slot capacity (keypoints)
     int32_t lanes;                // lanes per query
+    int32_t staged;               // 1: TMA-staged kernel, sn = stage stride
+    int32_t sn;
 };
 
 }  // namespace tmap

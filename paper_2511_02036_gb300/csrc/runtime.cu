@@ -126,6 +126,7 @@ extern "C" tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete c; return cuda_fail(e, "props"); }
     c->num_sms = prop.multiProcessorCount;
+    c->max_smem = prop.sharedMemPerBlockOptin;
     c->camc.fx = cam->fx;
     c->camc.fy = cam->fy;
     c->camc.cx = cam->cx;
@@ -208,11 +209,10 @@ tm_status tmap::alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got) {
     return TM_OK;
 }
 
-// Stage keyframes (host or device arrays) into the ingest buffers and enqueue the ingest
-// kernel on stream s.  Slots must already be reserved.  The caller synchronizes before the
-// staging buffers are reused.
-tm_status tmap::enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
-                             const int *slots, cudaStream_t s) {
+// Stage keyframes (host or device arrays) into the ingest buffers on stream s.  Slots must
+// already be reserved.  The caller synchronizes before the staging buffers are reused.
+tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
+                             const int *slots, cudaStream_t s, IngestArgs &a) {
     size_t total = 0;
     for (int k = 0; k < n; ++k) total += (size_t)kfs[k].n;
     const size_t N = (total + 31) & ~size_t(31);
@@ -275,7 +275,6 @@ tm_status tmap::enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfr
     st.host_ranges.clear();
     if ((e = cudaMemcpyAsync(d + o_jobs, jobs, sizeof(IngestJob) * (size_t)n, cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "ingest jobs upload");
-    IngestArgs a;
     a.jobs = reinterpret_cast<const IngestJob *>(d + o_jobs);
     a.n_jobs = n;
     a.cap = c->cap;
@@ -286,7 +285,16 @@ tm_status tmap::enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfr
     a.level = d + o_lvl;
     a.cell_w_inv = c->camc.cell_w_inv;
     a.cell_h_inv = c->camc.cell_h_inv;
-    if ((e = launch_ingest(a, s)) != cudaSuccess) return cuda_fail(e, "ingest kernel");
+    return TM_OK;
+}
+
+tm_status tmap::enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
+                               const int *slots, cudaStream_t s) {
+    IngestArgs a;
+    tm_status r = stage_ingest(c, st, n, kfs, slots, s, a);
+    if (r) return r;
+    cudaError_t e = launch_ingest(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     return TM_OK;
 }
 
@@ -389,10 +397,16 @@ void BatchBuf::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
     for (DevBuf *b : {&items, &order, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch})
+                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F})
         b->release();
     h_stage.release();
     h_out.release();
+    ingest.release();
+    for (cudaEvent_t &e : ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
 }
 
 static SearchConst to_const(const tm_search_params &p) {
@@ -410,7 +424,7 @@ static SearchConst to_const(const tm_search_params &p) {
 static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &fp) {
     if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0))
         return fail(TM_ERR_INVALID_ARG, "bad search parameters");
-    if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR)
+    if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR && sp.mode != TM_MODE_FUSED_GLOBAL)
         return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
     const int l = sp.lanes_per_query;
     if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
@@ -434,6 +448,48 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if (mps.n < 0) return fail(TM_ERR_INVALID_ARG, "negative map point count");
     if (mps.n > 0 && (!mps.pos || !mps.normal || !mps.desc || !mps.min_dist || !mps.max_dist))
         return fail(TM_ERR_INVALID_ARG, "map point arrays must be non-null");
+    // keyframes entering the store with this batch: reserve slots and stage them; the ingest
+    // kernel runs at the head of every launch of the batch
+    B.n_new = 0;
+    std::vector<int> new_slots;
+    const int n_new = in ? in->n_new : 0;
+    if (n_new < 0 || (n_new > 0 && (!in->new_ids || !in->new_kfs)))
+        return fail(TM_ERR_INVALID_ARG, "bad new keyframes");
+    if (n_new > 0) {
+        for (int k = 0; k < n_new; ++k) {
+            if ((st = validate_view(c, in->new_kfs[k]))) return st;
+            if (c->ids.count(in->new_ids[k]))
+                return fail(TM_ERR_EXISTS, "keyframe %llu already stored", (unsigned long long)in->new_ids[k]);
+            for (int q = 0; q < k; ++q)
+                if (in->new_ids[q] == in->new_ids[k])
+                    return fail(TM_ERR_EXISTS, "keyframe %llu given twice", (unsigned long long)in->new_ids[k]);
+        }
+        if ((st = alloc_slots_locked(c, n_new, new_slots))) return st;
+        if ((st = stage_ingest(c, B.ingest, n_new, in->new_kfs, new_slots.data(), s, B.ingest_args))) {
+            for (int sl : new_slots) c->free_slots.push_back(sl);
+            return st;
+        }
+        for (int k = 0; k < n_new; ++k) {
+            Slot &sl = c->slots[new_slots[k]];
+            sl.n = in->new_kfs[k].n;
+            sl.refs = 0;
+            sl.id = in->new_ids[k];
+            c->ids[in->new_ids[k]] = new_slots[k];
+        }
+        B.n_new = n_new;
+    }
+    // on failure below, the new keyframes are taken out of the store again
+    struct Rollback {
+        tm_ctx *c; const tm_batch_inputs *in; std::vector<int> *slots; BatchBuf *B; bool armed = true;
+        ~Rollback() {
+            if (!armed || slots->empty()) return;
+            for (size_t k = 0; k < slots->size(); ++k) {
+                c->ids.erase(in->new_ids[k]);
+                c->free_slots.push_back((*slots)[k]);
+            }
+            B->n_new = 0;
+        }
+    } rollback{c, in, &new_slots, &B};
     std::vector<WorkItem> &items = B.h_items;
     items.clear();
     B.item_nq.clear();
@@ -488,6 +544,16 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     }
     B.step_pair_begin[n_steps] = B.n_pairs;
     B.n_search_items = (uint32_t)items.size();
+    // staged kernel when every keyframe of the batch fits in shared memory
+    int max_n = 0;
+    for (int k = 0; k < n_steps; ++k) {
+        max_n = std::max(max_n, c->slots[c->ids[steps[k].kf_id]].n);
+        for (int j = 0; j < steps[k].n_nbrs; ++j) max_n = std::max(max_n, c->slots[c->ids[steps[k].nbr_ids[j]]].n);
+    }
+    const int sn16 = std::max(16, (max_n + 15) & ~15);
+    const size_t static_smem = 2048;
+    B.staged = sp.mode == TM_MODE_FUSED && StageLayout::make(sn16).bytes + static_smem <= c->max_smem;
+    const int fuse_chunk = B.staged ? kFuseChunkStaged : kFuseChunk;
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
         B.step_fuse_item[k] = (int)items.size();
@@ -495,14 +561,14 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         if (S.mp_begin < 0 || (int64_t)S.mp_begin + S.mp_count > mps.n)
             return fail(TM_ERR_INVALID_ARG, "step %d: map point range outside the batch", k);
         const int qs = c->ids[S.kf_id];
-        for (int b = 0; b < S.mp_count; b += kFuseChunk) {
+        for (int b = 0; b < S.mp_count; b += fuse_chunk) {
             WorkItem w;
             w.q = c->slots[qs].ptr;
             w.t = nullptr;
             w.kind = kItemFuse;
             w.out_off = pad;
             w.a = (uint32_t)(S.mp_begin + b);
-            w.b = (uint32_t)std::min(kFuseChunk, S.mp_count - b);
+            w.b = (uint32_t)std::min(fuse_chunk, S.mp_count - b);
             w.c = (uint32_t)S.mp_begin;
             w.cost = 2 * w.b;
             pad += w.b;
@@ -510,10 +576,11 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         }
     }
     B.step_fuse_item[n_steps] = (int)items.size();
+    for (int sl : new_slots) slots_used.push_back(sl);
     B.n_items = (uint32_t)items.size();
     B.n_steps = n_steps;
     B.total_pad = pad;
-    B.smem_n = (smem_n + 31) & ~31;
+    B.smem_n = B.staged ? sn16 : ((smem_n + 31) & ~31);
     B.slots = slots_used;
     // execution order: largest first (longest-processing-time-first over persistent CTAs)
     std::vector<uint32_t> order(items.size());
@@ -533,7 +600,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.masks.reserve(std::max<size_t>(16, mask_bytes))) ||
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
-        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)))
+        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
+        (e = B.pair_F.reserve(std::max<size_t>(1, B.n_search_items) * 9 * sizeof(float))))
         return cuda_fail(e, "batch buffers");
     if (B.pointers() != before && B.graph) {
         cudaGraphExecDestroy(B.graph);
@@ -578,26 +646,54 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.ncmp = static_cast<unsigned long long *>(B.ncmp.p);
     A.dense = static_cast<Out3 *>(B.dense.p);
     A.status = static_cast<uint32_t *>(B.counters.p) + 2;
+    A.pair_F = static_cast<float *>(B.pair_F.p);
+    A.n_search = B.n_search_items;
     A.sp = to_const(sp);
     A.fp.chi2 = fp.chi2;
     A.fp.hamming_max = fp.hamming_max;
     A.fp.radius_scale = fp.radius_scale;
     A.cam = c->camc;
     A.cap = c->cap;
+    A.staged = B.staged ? 1 : 0;
+    A.sn = B.smem_n;
     B.sp = sp;
     B.fp = fp;
+    rollback.armed = false;
     return TM_OK;
 }
 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, order.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p};
+            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p, pair_F.p};
 }
 
-// Enqueue the fused launch (counter reset, persistent kernel, compaction).
+// Takes the keyframes that entered the store with batch B out again (failed call).
+static void drop_new_keyframes(tm_ctx *c, BatchBuf &B, const tm_batch_inputs *in) {
+    if (!in || B.n_new <= 0) return;
+    for (int k = 0; k < B.n_new; ++k) {
+        auto it = c->ids.find(in->new_ids[k]);
+        if (it == c->ids.end()) continue;
+        c->free_slots.push_back(it->second);
+        c->ids.erase(it);
+    }
+    B.n_new = 0;
+}
+
+// Records a stage-boundary event; inside a stream capture it must become an event-record
+// node of the graph, which needs the external flag.
+static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e) return e;
+    return cudaEventRecordWithFlags(ev, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                               : cudaEventRecordDefault);
+}
+
+// Enqueue the fused launch (ingest of new keyframes, counter reset, persistent kernel,
+// compaction).
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s) {
     cudaError_t e;
-    const size_t smem = batch_smem_bytes(B.smem_n);
+    const size_t smem = batch_smem_bytes(B.smem_n, B.staged);
     if ((e = batch_kernel_prepare(smem))) return cuda_fail(e, "batch kernel attribute");
     int per_sm = batch_ctas_per_sm(threads, smem);
     if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "batch kernel does not fit: %d threads, %zu B shared", threads, smem);
@@ -605,14 +701,22 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     B.threads = threads;
     B.lanes = lanes;
     B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>(B.n_items, (uint32_t)(per_sm * c->num_sms)));
+    const bool timed = B.ev[0] != nullptr;
+    if (timed && (e = record_stage(B.ev[0], s))) return cuda_fail(e, "event");
+    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
     if ((e = cudaMemsetAsync(B.counters.p, 0, 16, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
         return cuda_fail(e, "reset counters");
+    if ((e = launch_pair_setup(B.args, s))) return cuda_fail(e, "pair setup kernel");
+    if (timed && (e = record_stage(B.ev[1], s))) return cuda_fail(e, "event");
     if (B.n_items == 0) {
         if ((e = cudaMemsetAsync(B.offsets.p, 0, 4, s))) return cuda_fail(e, "offsets");
-        return TM_OK;
+    } else if ((e = launch_batch(B.args, B.ctas, threads, smem, s))) {
+        return cuda_fail(e, "batch kernel");
     }
-    if ((e = launch_batch(B.args, B.ctas, threads, smem, s))) return cuda_fail(e, "batch kernel");
-    if ((e = launch_copy(B.args, std::min<int>(B.n_items, 4 * c->num_sms), s))) return cuda_fail(e, "copy kernel");
+    if (timed && (e = record_stage(B.ev[2], s))) return cuda_fail(e, "event");
+    if (B.n_items && (e = launch_copy(B.args, std::min<int>(B.n_items, 4 * c->num_sms), s)))
+        return cuda_fail(e, "copy kernel");
+    if (timed && (e = record_stage(B.ev[3], s))) return cuda_fail(e, "event");
     return TM_OK;
 }
 
@@ -624,6 +728,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
     if ((e = B.scratch.reserve(scr_bytes + align128(size_t(std::max(1, max_mp)) * 4))))
         return cuda_fail(e, "plain scratch");
     PairScratch scr = pair_scratch_at(B.scratch.p, c->cap);
+    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
     uint32_t *res = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(B.scratch.p) + scr_bytes);
     if ((e = cudaMemsetAsync(scr.running, 0, 8, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
         return cuda_fail(e, "reset");
@@ -665,13 +770,17 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
     (void)c;
     cudaError_t e;
     const size_t nio = (size_t)B.n_items + 1;
-    if ((e = B.h_out.reserve((nio + 2) * 4 + 16))) return cuda_fail(e, "pinned results");
+    if ((e = B.h_out.reserve((nio + 2) * 4 + 32))) return cuda_fail(e, "pinned results");
     uint32_t *ho = static_cast<uint32_t *>(B.h_out.p);
     unsigned long long *hc = reinterpret_cast<unsigned long long *>(ho + ((nio + 1) & ~size_t(1)));
+    uint32_t *hs = reinterpret_cast<uint32_t *>(hc + 2);
     if ((e = cudaMemcpyAsync(ho, B.offsets.p, nio * 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
+    if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
+        return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory did not complete in time");
     const uint32_t search_total = ho[B.n_search_items];
     const uint32_t total = ho[B.n_items];
     const size_t nf = total - search_total;
@@ -703,8 +812,13 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 
 // ------------------------------------------------------------------------- tuning
 
-static const int kTuneThreads[] = {128, 256, 512};
+static const int kTuneThreadsGlobal[] = {128, 256, 512};
+static const int kTuneThreadsStaged[] = {512, 1024};
 static const int kTuneLanes[] = {1, 2, 4, 8, 32};
+
+// Default launch shape: one 1024-thread CTA per SM for the staged kernel (its shared memory
+// holds a whole pair), 256-thread CTAs otherwise.
+int tmap::default_threads(const BatchBuf &B) { return B.staged ? 1024 : 256; }
 
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
@@ -740,12 +854,12 @@ static uint64_t batch_queries(tm_ctx *c, const BatchBuf &B, const tm_step *steps
 // Picks (threads, lanes) for a prepared batch: cached by density class, else measured.
 tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure) {
     tm_status st;
-    if ((st = enqueue_fused(c, B, c->def_threads, c->def_lanes, s))) return st;
+    if ((st = enqueue_fused(c, B, default_threads(B), c->def_lanes, s))) return st;
     unsigned long long hc[2];
     cudaError_t e;
     if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "tuning");
-    const int key = density_key(hc[0], batch_queries(c, B, steps));
+    const int key = density_key(hc[0], batch_queries(c, B, steps)) * 2 + (B.staged ? 1 : 0);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) {
         B.threads = it->second.first;
@@ -753,7 +867,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         return TM_OK;
     }
     if (!measure) {
-        B.threads = c->def_threads;
+        B.threads = default_threads(B);
         B.lanes = c->def_lanes;
         return TM_OK;
     }
@@ -761,10 +875,13 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt = c->def_threads, bl = c->def_lanes;
-    for (int th : kTuneThreads)
+    int bt = default_threads(B), bl = c->def_lanes;
+    std::vector<int> threads_set;
+    if (B.staged) threads_set.assign(std::begin(kTuneThreadsStaged), std::end(kTuneThreadsStaged));
+    else threads_set.assign(std::begin(kTuneThreadsGlobal), std::end(kTuneThreadsGlobal));
+    for (int th : threads_set)
         for (int ln : kTuneLanes) {
-            if (batch_ctas_per_sm(th, batch_smem_bytes(B.smem_n)) < 1) continue;
+            if (batch_ctas_per_sm(th, batch_smem_bytes(B.smem_n, B.staged)) < 1) continue;
             if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
             float tot = 0.0f;
             for (int r = 0; r < 3; ++r) {
@@ -800,16 +917,20 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     if (sp.mode == TM_MODE_PER_PAIR) {
         st = enqueue_plain(c, B, sp.lanes_per_query ? sp.lanes_per_query : 1, s);
     } else {
-        int th = c->def_threads, ln = c->def_lanes;
+        int th = default_threads(B), ln = c->def_lanes;
         if (sp.lanes_per_query) ln = sp.lanes_per_query;
-        else if (!c->tuned.empty()) {
+        else if (c->last_staged == (int)B.staged) {
             th = c->last_threads;
             ln = c->last_lanes;
         }
         st = enqueue_fused(c, B, th, ln, s);
     }
-    if (st) return st;
-    return fetch_results(c, B, res, s);
+    if (!st) st = fetch_results(c, B, res, s);
+    if (st) {
+        cudaStreamSynchronize(s);
+        drop_new_keyframes(c, B, in);
+    }
+    return st;
 }
 
 extern "C" tm_status tm_batch_run(tm_ctx *c, const tm_step *steps, int32_t n_steps,
@@ -953,9 +1074,9 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
     P->ctx = c;
     cudaStream_t s = c->stream;
     tm_status st = prepare_batch(c, P->B, steps, n_steps, in, spd, fpd, s);
-    if (!st && spd.mode == TM_MODE_FUSED) {
+    if (!st && spd.mode != TM_MODE_PER_PAIR) {
         if (spd.lanes_per_query) {
-            P->B.threads = c->def_threads;
+            P->B.threads = default_threads(P->B);
             P->B.lanes = spd.lanes_per_query;
         } else {
             const char *nt = getenv("TM_NO_TUNE");
@@ -963,20 +1084,24 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
             if (!st) {
                 c->last_threads = P->B.threads;
                 c->last_lanes = P->B.lanes;
+                c->last_staged = P->B.staged ? 1 : 0;
             }
         }
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (!st && e) st = cuda_fail(e, "plan upload");
     if (st) {
+        drop_new_keyframes(c, P->B, in);
         P->B.release();
         delete P;
         return st;
     }
-    if (spd.mode == TM_MODE_FUSED) {
-        // capture the launch in a CUDA graph
+    if (spd.mode != TM_MODE_PER_PAIR) {
+        // capture the launch in a CUDA graph, with events at the stage boundaries
         const int th = P->B.threads, ln = P->B.lanes;
-        if ((e = batch_kernel_prepare(batch_smem_bytes(P->B.smem_n)))) st = cuda_fail(e, "attribute");
+        for (cudaEvent_t &ev : P->B.ev)
+            if (!st && (e = cudaEventCreate(&ev))) st = cuda_fail(e, "events");
+        if ((e = batch_kernel_prepare(batch_smem_bytes(P->B.smem_n, P->B.staged)))) st = cuda_fail(e, "attribute");
         cudaGraph_t g = nullptr;
         if (!st && (e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
             st = cuda_fail(e, "begin capture");
@@ -988,14 +1113,16 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         }
         if (!st && (e = cudaGraphInstantiate(&P->B.graph, g, 0))) st = cuda_fail(e, "graph instantiate");
         if (g) cudaGraphDestroy(g);
-        P->kernels_per_run = P->B.n_items ? 2 : 0;
+        P->kernels_per_run = (P->B.n_items ? 2 : 0) + (P->B.n_search_items ? 1 : 0) + (P->B.n_new ? 1 : 0);
     } else {
-        P->kernels_per_run = 3 * (int)P->B.n_search_items;
+        P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)
             if (P->B.step_fuse_item[k] != P->B.step_fuse_item[k + 1]) P->kernels_per_run += 2;
         P->B.lanes = spd.lanes_per_query ? spd.lanes_per_query : 1;
     }
     if (st) {
+        cudaStreamSynchronize(c->stream);
+        drop_new_keyframes(c, P->B, in);
         P->B.release();
         delete P;
         return st;
@@ -1039,6 +1166,18 @@ extern "C" tm_status tm_plan_info(tm_plan *P, int32_t *threads, int32_t *lanes, 
     if (lanes) *lanes = P->B.lanes;
     if (ctas) *ctas = P->B.ctas;
     if (kernels) *kernels = P->kernels_per_run;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
+    if (!P || !ms) return fail(TM_ERR_INVALID_ARG, "tm_plan_stage_times: null argument");
+    ms[0] = ms[1] = ms[2] = 0.0f;
+    if (!P->B.ev[0]) return TM_OK;
+    cudaSetDevice(P->ctx->device);
+    cudaError_t e = cudaEventSynchronize(P->B.ev[3]);
+    if (e) return cuda_fail(e, "stage events");
+    for (int k = 0; k < 3; ++k)
+        if ((e = cudaEventElapsedTime(&ms[k], P->B.ev[k], P->B.ev[k + 1]))) return cuda_fail(e, "stage times");
     return TM_OK;
 }
 

@@ -48,18 +48,23 @@ struct IngestStage {
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, order, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, offsets, ncmp, counters, dense, scratch;
+        counts, offsets, ncmp, counters, dense, scratch, pair_F;
     PinBuf h_stage, h_out;
+    IngestStage ingest;            // keyframes entering the store with this batch
+    IngestArgs ingest_args{};
+    int n_new = 0;
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
     uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
     int n_steps = 0, n_pairs = 0, smem_n = 32;
+    bool staged = false;  // keyframes of every item fit in shared memory (TMA-staged kernel)
     int threads = 256, lanes = 1, ctas = 0;
     tm_search_params sp{};
     tm_fuse_params fp{};
     BatchArgs args{};
     cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries (plans)
     std::vector<void *> pointers() const;
     void release();
 };
@@ -73,6 +78,7 @@ struct tm_ctx {
     tmap::SlotLayout layout{};
     size_t slot_bytes = 0, budget = 0;
     int num_sms = 1;
+    size_t max_smem = 0;  // opt-in shared memory per block
     tmap::CamConst camc{};
     std::mutex mu;
     std::unordered_map<uint64_t, int> ids;
@@ -84,7 +90,7 @@ struct tm_ctx {
     tmap::BatchBuf batch;
     tmap::DevBuf mask_scratch;
     std::map<int, std::pair<int, int>> tuned;
-    int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1;
+    int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1, last_staged = -1;
     ~tm_ctx();
 };
 
@@ -97,6 +103,10 @@ cudaStream_t pick_stream(tm_ctx *c, void *s);
 tm_status validate_view(tm_ctx *c, const tm_keyframe_view &v);
 // Reserves n store slots (all or nothing) within the budget; caller holds c->mu.
 tm_status alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got);
+// Copies keyframes (host or device arrays) into staging buffers on stream s and fills the
+// ingest kernel's arguments; enqueue_ingest also launches it.
+tm_status stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
+                       const int *slots, cudaStream_t s, IngestArgs &args);
 tm_status enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
                          const int *slots, cudaStream_t s);
 tm_status store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyframe_view *kfs,
@@ -109,5 +119,7 @@ tm_status enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s);
 tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s);
 tm_status tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure);
 void load_tuning(tm_ctx *c, const char *path);
+// Threads per CTA used when no tuned value applies.
+int default_threads(const BatchBuf &B);
 
 }  // namespace tmap

@@ -66,6 +66,8 @@ def test_batch_run_small(tm, small_batch):
         load_all(ctx, w)
         for lanes in (0, 1, 4, 32):
             assert_same(ctx.batch_run(steps_of(w), sp=tm.SearchParams(lanes_per_query=lanes)), exp)
+            assert_same(ctx.batch_run(steps_of(w), sp=tm.SearchParams(lanes_per_query=lanes,
+                                                                      mode=tm.TM_MODE_FUSED_GLOBAL)), exp)
         assert_same(ctx.batch_run(steps_of(w), sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR)), exp)
 
 
@@ -76,7 +78,7 @@ def test_plan_graph_replay(tm, small_batch):
         load_all(ctx, w)
         with ctx.plan(steps_of(w)) as plan:
             info = plan.info()
-            assert info["kernels_per_run"] == 2 and info["ctas"] >= 1
+            assert info["kernels_per_run"] == 3 and info["ctas"] >= 1
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -187,9 +189,45 @@ def test_cfg2_full_size_parity(tm, cfg2):
     oracle."""
     w = cfg2
     exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
     with tm.Context(w["cam"], max_kp=2048) as ctx:
-        load_all(ctx, w)
-        with ctx.plan(steps_of(w)) as plan:
+        ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
+        with ctx.plan(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids])) as plan:
             plan.run()
             plan.run()
             assert_same(plan.results(), exp)
+            ms = plan.stage_times()
+            assert all(t > 0 for t in ms)
+
+
+def test_new_keyframes_enter_with_the_batch(tm, small_batch):
+    """The steps' new keyframes are ingested in the batch's own launch sequence (one-shot and
+    replayed by a plan's graph): same results; on failure they are not stored."""
+    w = small_batch
+    exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        new = (new_ids, [w["frames"][i] for i in new_ids])
+        assert_same(ctx.batch_run(steps_of(w), new=new), exp)
+        assert ctx.keyframe_size(new_ids[0]) == w["frames"][new_ids[0]]["n"]
+        # already stored now: the call fails and stores nothing more
+        with pytest.raises(tm.TMError) as e:
+            ctx.batch_run(steps_of(w), new=new)
+        assert e.value.status == tm.TM_ERR_EXISTS
+        for i in new_ids:
+            ctx.remove_keyframe(i)
+        # a failing batch (unknown neighbour) leaves the new keyframes out of the store
+        bad = steps_of(w)
+        bad[0] = dict(bad[0], nbrs=[10 ** 9])
+        with pytest.raises(tm.TMError):
+            ctx.batch_run(bad, new=new)
+        with pytest.raises(tm.TMError):
+            ctx.keyframe_size(new_ids[0])
+        with ctx.plan(steps_of(w), new=new) as plan:
+            assert plan.info()["kernels_per_run"] == 4
+            for _ in range(3):
+                plan.run()
+                assert_same(plan.results(), exp)
