@@ -287,6 +287,37 @@ tm_status tm_server_stop(tm_server *srv);
 /* Monotonic clock used by the server (seconds). */
 double tm_now(void);
 
+/* ---------------------------------------------------------------------------- no allocation
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory -- code running while a CUDA graph is being captured, code under a fixed
+ * memory budget or in a real-time loop that forbids allocation after start-up, or a host
+ * without a tm_ctx (whose keyframe store allocates).
+ *
+ * Correspondence search of one keyframe pair, with the same results as tm_search_
+ * triangulation(q, [t]).  It allocates nothing: its scratch -- both keyframes in node order
+ * with their projection grids, the per-pair arrays and the counters -- lives in one fixed
+ * array inside the library (about 256 KB, held by every GPU that loads the library until
+ * the process exits).
+ *   q, t       keyframes of at most TM_NOALLOC_MAX_KP keypoints each; their arrays must be
+ *              device memory (Tcw is read from the struct); larger ones are rejected with
+ *              TM_ERR_INVALID_ARG
+ *   q_free, t_free  device [n] or NULL
+ *   out        device tm_match [q->n], matches sorted by q_idx
+ *   n_out      device uint32: number of matches
+ *   n_comparisons   device uint64 or NULL
+ * Asynchronous on `stream` (NULL: the legacy default stream): results are valid once the
+ * stream reaches this call, and the inputs must stay valid until then.  The first call on a
+ * device looks up the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  Every call uses the same array and
+ * leaves its contents behind (each call clears what must start at zero): calls whose work
+ * may overlap on the GPU -- on different streams or threads -- race with one another;
+ * calls on one stream run one after the other. */
+#define TM_NOALLOC_MAX_KP 2048
+tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyframe_view *q,
+                                 const tm_keyframe_view *t, const tm_search_params *params,
+                                 const uint8_t *q_free, const uint8_t *t_free, tm_match *out,
+                                 uint32_t *n_out, uint64_t *n_comparisons, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -130,6 +130,8 @@ SIGNATURES = {
     "tm_server_take": (c_i32, [c_p, c_u64, c_p, c_p, c_p]),
     "tm_server_stop": (c_i32, [c_p]),
     "tm_now": (c_f64, []),
+    "tm_search_pair_noalloc": (c_i32, [P(tm_camera), P(tm_keyframe_view), P(tm_keyframe_view),
+                                       P(tm_search_params), c_p, c_p, c_p, c_p, c_p, c_p]),
 }
 
 _lib = None

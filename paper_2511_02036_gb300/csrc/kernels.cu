@@ -1168,3 +1168,164 @@ cudaError_t launch_fuse_plain(const unsigned char *t, int cap, const float *pos,
 }
 
 }  // namespace tmap
+
+// ------------------------------------------------------------------------- no-allocation variant
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA graph is being
+// captured, code under an allocator that must not grow (a fixed memory budget, a real-time
+// loop that forbids allocation after start-up), or a host without a tm_ctx and its store.
+// For them tm_search_pair_noalloc searches one keyframe pair with the plain per-pair kernels,
+// keeping all of its scratch -- the two node-sorted keyframe slots, the per-pair arrays and
+// the counters -- in the file-scope array below, which every GPU that loads the library holds
+// until the process exits.
+
+#include "runtime.h"
+
+namespace {
+
+constexpr int kNoAllocMaxKp = TM_NOALLOC_MAX_KP;
+constexpr size_t kNoAllocSlot = tmap::SlotLayout::make(kNoAllocMaxKp).bytes;
+constexpr size_t kNoAllocPair = tmap::align128(size_t(kNoAllocMaxKp) * 4) * 3 + 256;
+// [slot Q | slot T | pair scratch | two ingest jobs | n_comparisons]
+constexpr size_t kNoAllocJobs = 2 * kNoAllocSlot + kNoAllocPair;
+constexpr size_t kNoAllocCmp = kNoAllocJobs + tmap::align128(2 * sizeof(tmap::IngestJob));
+constexpr size_t kNoAllocBytes = kNoAllocCmp + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Writes the two ingest jobs (passed by value) into the scratch array.
+__global__ void noalloc_jobs_kernel(tmap::IngestJob *dst, tmap::IngestJob q, tmap::IngestJob t) {
+    dst[0] = q;
+    dst[1] = t;
+}
+
+// Device address of the scratch array for the current device, looked up once per device.
+// (In host code g_noalloc_scratch names a host-side stand-in, not device memory.)
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[64] = {nullptr};
+
+tm_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= 64) return tmap::fail(TM_ERR_INVALID_ARG, "device %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return tmap::cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return TM_OK;
+}
+
+bool device_accessible(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyframe_view *q,
+                                            const tm_keyframe_view *t,
+                                            const tm_search_params *params,
+                                            const uint8_t *q_free, const uint8_t *t_free,
+                                            tm_match *out, uint32_t *n_out,
+                                            uint64_t *n_comparisons, void *stream) {
+    using namespace tmap;
+    if (!cam || !q || !t || !out || !n_out)
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: null argument");
+    if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0) || !(cam->fy > 0))
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad camera");
+    for (const tm_keyframe_view *v : {q, t}) {
+        if (v->n < 0 || v->n > kNoAllocMaxKp)
+            return fail(TM_ERR_INVALID_ARG,
+                        "tm_search_pair_noalloc: %d keypoints exceed the limit of %d per keyframe "
+                        "(the size of the library's fixed scratch array)", v->n, kNoAllocMaxKp);
+        if (v->n > 0 && !(device_accessible(v->desc) && device_accessible(v->xy) &&
+                          device_accessible(v->angle) && device_accessible(v->level) &&
+                          device_accessible(v->node)))
+            return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: keyframe arrays must be device memory");
+    }
+    if (!device_accessible(out) || !device_accessible(n_out) ||
+        (n_comparisons && !device_accessible(n_comparisons)) ||
+        (q_free && !device_accessible(q_free)) || (t_free && !device_accessible(t_free)))
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: masks and outputs must be device memory");
+    tm_search_params sp;
+    tm_search_params_default(&sp);
+    if (params) sp = *params;
+    if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0))
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad search parameters");
+    const int l = sp.lanes_per_query ? sp.lanes_per_query : 1;
+    if (!(l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad lanes_per_query");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    unsigned char *scr = nullptr;
+    tm_status st = noalloc_scratch(dev, &scr);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char *slot_q = scr, *slot_t = scr + kNoAllocSlot;
+    PairScratch ps = pair_scratch_at(scr + 2 * kNoAllocSlot, kNoAllocMaxKp);
+    IngestJob *jobs = reinterpret_cast<IngestJob *>(scr + kNoAllocJobs);
+    unsigned long long *ncmp = reinterpret_cast<unsigned long long *>(scr + kNoAllocCmp);
+    // the scratch keeps the previous call's contents: clear what must start at zero
+    if ((e = cudaMemsetAsync(ps.running, 0, 8, s)) || (e = cudaMemsetAsync(ncmp, 0, 8, s)))
+        return cuda_fail(e, "scratch reset");
+    IngestJob jq{}, jt{};
+    jq.slot = slot_q;
+    jq.src = 0;
+    jq.n = q->n;
+    jt.slot = slot_t;
+    jt.src = 0;
+    jt.n = t->n;
+    for (int k = 0; k < 12; ++k) {
+        jq.Tcw[k] = q->Tcw[k];
+        jt.Tcw[k] = t->Tcw[k];
+    }
+    noalloc_jobs_kernel<<<1, 1, 0, s>>>(jobs, jq, jt);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "job kernel");
+    CamConst cc;
+    cc.fx = cam->fx;
+    cc.fy = cam->fy;
+    cc.cx = cam->cx;
+    cc.cy = cam->cy;
+    cc.width = cam->width;
+    cc.height = cam->height;
+    cc.cell_w_inv = (float)kGridCols / (float)cam->width;
+    cc.cell_h_inv = (float)kGridRows / (float)cam->height;
+    const tm_keyframe_view *views[2] = {q, t};
+    for (int k = 0; k < 2; ++k) {  // node order and grid of each keyframe, into its scratch slot
+        IngestArgs a;
+        a.jobs = jobs + k;
+        a.n_jobs = 1;
+        a.cap = kNoAllocMaxKp;
+        a.desc = reinterpret_cast<const uint4 *>(views[k]->desc);
+        a.xy = reinterpret_cast<const float2 *>(views[k]->xy);
+        a.angle = views[k]->angle;
+        a.node = views[k]->node;
+        a.level = views[k]->level;
+        a.cell_w_inv = cc.cell_w_inv;
+        a.cell_h_inv = cc.cell_h_inv;
+        if ((e = launch_ingest(a, s))) return cuda_fail(e, "ingest kernel");
+    }
+    SearchConst sc;
+    sc.hamming_max = sp.hamming_max;
+    sc.ratio_num = sp.ratio_num;
+    sc.ratio_den = sp.ratio_den;
+    sc.epi_chi2 = sp.epi_chi2;
+    sc.epipolar = sp.epipolar;
+    sc.resolve = sp.resolve;
+    sc.rot_filter = sp.rot_filter;
+    uint32_t *pair_offset = ps.running + 1;  // start of the output (always 0 here)
+    if ((e = launch_pair_plain(slot_q, slot_t, q_free, t_free, q->n, t->n, kNoAllocMaxKp, sc, cc, ps,
+                               reinterpret_cast<Out3 *>(out), pair_offset, ncmp, l, s)))
+        return cuda_fail(e, "pair kernels");
+    if ((e = cudaMemcpyAsync(n_out, ps.running, 4, cudaMemcpyDeviceToDevice, s))) return cuda_fail(e, "count");
+    if (n_comparisons && (e = cudaMemcpyAsync(n_comparisons, ncmp, 8, cudaMemcpyDeviceToDevice, s)))
+        return cuda_fail(e, "comparisons");
+    return TM_OK;
+}

@@ -34,8 +34,8 @@ struct KfHeader {
 // Byte offsets of the arrays of a slot with capacity `cap` keypoints.
 struct SlotLayout {
     size_t desc, xy, angle, node, orig, level, grid_start, grid_items, bytes;
-    __host__ __device__ static SlotLayout make(int cap) {
-        SlotLayout L;
+    __host__ __device__ static constexpr SlotLayout make(int cap) {
+        SlotLayout L{};
         size_t o = align128(sizeof(KfHeader));
         L.desc = o;       o = align128(o + size_t(cap) * 32);
         L.xy = o;         o = align128(o + size_t(cap) * 8);
