@@ -87,11 +87,9 @@ typedef struct {
     const uint8_t *skip;    /* [n] or NULL: 1 = already observed by the target keyframe     */
 } tm_mappoint_view;
 
-#define TM_MODE_FUSED 0      /* one CTA per pair, whole pipeline in shared memory (default);
-                                the pair's keyframes are staged there by bulk copies when
-                                they fit, else read from global memory                      */
+#define TM_MODE_FUSED 0      /* all pairs and map points of the call in one launch sequence
+                                (join, match, finalize, compaction kernels; default)        */
 #define TM_MODE_PER_PAIR 1   /* plain form: one pair at a time, one launch per stage        */
-#define TM_MODE_FUSED_GLOBAL 2 /* fused, keyframe arrays always read from global memory    */
 
 typedef struct {
     int32_t hamming_max;    /* accept best <= hamming_max (50)                              */
@@ -101,7 +99,7 @@ typedef struct {
     int32_t epipolar;       /* 1 = apply the epipolar gate                                  */
     int32_t resolve;        /* 1 = one match per target keypoint                            */
     int32_t rot_filter;     /* 1 = 30-bin rotation-histogram filter                         */
-    int32_t mode;           /* TM_MODE_FUSED, TM_MODE_PER_PAIR or TM_MODE_FUSED_GLOBAL      */
+    int32_t mode;           /* TM_MODE_FUSED or TM_MODE_PER_PAIR                            */
     int32_t lanes_per_query;/* 0 = autotuned; else 1, 2, 4, 8, 16 or 32                     */
 } tm_search_params;
 

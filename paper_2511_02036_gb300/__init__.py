@@ -18,8 +18,7 @@ import numpy as np
 from . import _lib as L
 from ._lib import (TM_ERR_BUSY, TM_ERR_CAPACITY, TM_ERR_CUDA, TM_ERR_EXISTS,  # noqa: F401
                    TM_ERR_INVALID_ARG, TM_ERR_NO_MEMORY, TM_ERR_NOT_FOUND, TM_ERR_TIMEOUT,
-                   TM_MODE_FUSED, TM_MODE_FUSED_GLOBAL, TM_MODE_PER_PAIR, TM_OK,
-                   TM_MAX_KP_LIMIT)
+                   TM_MODE_FUSED, TM_MODE_PER_PAIR, TM_OK, TM_MAX_KP_LIMIT)
 
 _clib = L.load()
 for _name in L.SIGNATURES:

@@ -24,7 +24,6 @@ TM_ERR_TIMEOUT = 7
 TM_ERR_BUSY = 8
 TM_MODE_FUSED = 0
 TM_MODE_PER_PAIR = 1
-TM_MODE_FUSED_GLOBAL = 2
 TM_MAX_KP_LIMIT = 8192
 
 

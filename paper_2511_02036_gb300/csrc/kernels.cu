@@ -353,27 +353,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-// ------------------------------------------------------------------------- batch kernel
+// ------------------------------------------------------------------------- batch pipeline
+//
+// A batch runs as four kernels over flat work lists, so that every SM holds many independent
+// warps and no CTA waits on another:
+//   join_kernel      per pair: F; each query's candidate range (binary search of its node in
+//                    the neighbour's node array, both staged by bulk copies); the neighbour's
+//                    eligibility in node order; per-target winners reset.
+//   match_kernel     warp units of 32 queries: Hamming + epipolar gate over the range,
+//                    best/second, accept, atomicMin on the target's winner.
+//   fuse_kernel      per 256 map points (a parallel branch of the launch graph): projection
+//                    gates, grid window in the staged target, best Hamming.
+//   finalize_kernel  per pair: one match per target, rotation histogram, top-3 filter,
+//                    ordered compaction; the last CTA turns per-item counts into offsets.
+//   copy_kernel      per-item regions into one dense array.
 
-struct ItemShared {
-    uint32_t hist[32];
-    uint32_t wtot[32];
-    float F[9];
-    float thr[kLevels];
-    float scale[kLevels];
-    float R[9], t[3], O[3];
-    uint32_t keep;
-    uint32_t item;
-    uint32_t cmp;
+// Per-target state: (dist << 16 | caller query index) of the best accepted query.
+// Per-query state: node-order candidate range lo | hi << 16 (join), accepted (target << 16 | dist)
+// or kNone (match).
+
+struct FuseK {
+    float R[9], t[3], O[3], scale[kLevels], thr[kLevels];
 };
 
-// Adds a per-thread count to S.cmp: one shared atomic per warp.  All threads of the warp call.
+// Adds a per-thread count to *dst: one atomic per warp.  All threads of the warp call.
 __device__ __forceinline__ void warp_count(uint32_t v, uint32_t *dst) {
     const uint32_t sum = __reduce_add_sync(kFull, v);
     if ((threadIdx.x & 31u) == 0 && sum) atomicAdd(dst, sum);
 }
 
-// Top-3 rotation bins by warp 0 (same rule as top3_mask).  All lanes of warp 0 call.
+// Top-3 rotation bins by one warp (same rule as top3_mask).  All lanes of the warp call.
 __device__ __forceinline__ uint32_t top3_mask_warp(const uint32_t *hist) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t c = lane < (uint32_t)kBins ? hist[lane] : 0u;
@@ -391,235 +400,10 @@ __device__ __forceinline__ uint32_t top3_mask_warp(const uint32_t *hist) {
     return mask;
 }
 
-// Pair state shared by the staged and unstaged search.
-struct PairArrays {
-    KfView Q, T;               // keypoint arrays of both keyframes (shared or global memory)
-    const uint32_t *tnode;     // neighbour's node ids, node order (shared memory)
-    uint32_t *win;             // [nT] per target: lowest (dist << 16 | caller query index)
-    uint32_t *accq;            // [nQ] per node-order query: (target << 16 | dist) or kNone
-    uint32_t *res;             // [nQ] per caller-order query: packed kept match or kNone
-    const uint8_t *mq, *mt;    // eligibility masks indexed by caller order, or null
-};
-
-// Correspondence search of one (new keyframe, neighbour) pair (Sec. IV-C).  S.F, S.thr,
-// S.hist (zero) and S.cmp (zero) are set and win[0..nT) = kNone before the call.
-template <int G>
-__device__ __forceinline__ void search_core(const BatchArgs &A, const WorkItem &w, uint32_t idx, int nQ, int nT,
-                            const PairArrays &P, ItemShared &S) {
-    const KfView &Q = P.Q, &T = P.T;
-    const int tid = threadIdx.x, bs = blockDim.x;
-    const bool epi = A.sp.epipolar != 0;
-    // Join + match: G lanes per query, node-sorted queries in consecutive groups.
-    const int gpc = bs / G, g = tid / G, sub = tid % G;
-    uint32_t my_cmp = 0;
-    for (int p0 = 0; p0 < nQ; p0 += gpc) {
-        const int p = p0 + g;
-        uint32_t bkey = kNone;   // (dist << 16) | node-order target
-        uint32_t sec = 0xFFFFu;  // second-smallest distance
-        if (p < nQ && (!P.mq || P.mq[Q.orig[p]])) {
-            const uint32_t nd = Q.node[p];
-            const int lo = lower_bound_u32(P.tnode, nT, nd);
-            const int hi = (lo < nT && P.tnode[lo] == nd) ? upper_bound_u32(P.tnode, lo, nT, nd) : lo;
-            if (lo < hi) {
-                const uint4 q0 = Q.desc[2 * p], q1 = Q.desc[2 * p + 1];
-                const float2 xq = Q.xy[p];
-                const Line l = epi_line(S.F, xq.x, xq.y);
-                for (int j = lo + sub; j < hi; j += G) {
-                    if (P.mt && !P.mt[T.orig[j]]) continue;
-                    ++my_cmp;
-                    const uint32_t d = (uint32_t)hamming(q0, q1, T.desc[2 * j], T.desc[2 * j + 1]);
-                    if (epi) {
-                        const float2 xt = T.xy[j];
-                        if (!epi_pass(l, xt.x, xt.y, S.thr[T.level[j]])) continue;
-                    }
-                    const uint32_t key = (d << 16) | (uint32_t)j;
-                    if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
-                    else sec = min(sec, d);
-                }
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            const uint32_t ob = __shfl_xor_sync(kFull, bkey, off);
-            const uint32_t os = __shfl_xor_sync(kFull, sec, off);
-            sec = min(min(sec, os), max(bkey, ob) >> 16);
-            bkey = min(bkey, ob);
-        }
-        if (sub == 0 && p < nQ) {
-            uint32_t acc = kNone;
-            if (bkey != kNone) {
-                const uint32_t best = bkey >> 16;
-                bool ok = (int)best <= A.sp.hamming_max;
-                if (ok && A.sp.ratio_num != 0 && sec != 0xFFFFu)
-                    ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sec;
-                if (ok) {
-                    const uint32_t j = bkey & 0xFFFFu;
-                    acc = (j << 16) | best;
-                    if (A.sp.resolve) atomicMin(&P.win[j], (best << 16) | Q.orig[p]);
-                }
-            }
-            P.accq[p] = acc;  // (may alias Q.node[p], read above by this group only)
-        }
-    }
-    warp_count(my_cmp, &S.cmp);
-    __syncthreads();
-
-    // One match per target, rotation histogram (one atomic per distinct bin per warp);
-    // every caller-order query gets its res.
-    const bool rot = A.sp.rot_filter != 0;
-    for (int p0 = 0; p0 < nQ; p0 += bs) {
-        const int p = p0 + tid;
-        uint32_t bin = kNone;
-        if (p < nQ) {
-            const uint32_t acc = P.accq[p], io = Q.orig[p];
-            uint32_t r = kNone;
-            if (acc != kNone) {
-                const uint32_t j = acc >> 16, d = acc & 0xFFFFu;
-                if (!A.sp.resolve || P.win[j] == ((d << 16) | io)) {
-                    bin = rot ? (uint32_t)rot_bin(Q.angle[p], T.angle[j]) : 0u;
-                    r = pack_res(T.orig[j], d, bin);
-                }
-            }
-            P.res[io] = r;
-        }
-        if (rot) {
-            const unsigned peers = __match_any_sync(kFull, bin);
-            if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
-                atomicAdd(&S.hist[bin], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
-    if (tid < 32) {
-        const uint32_t k = rot ? top3_mask_warp(S.hist) : kNone;
-        if (tid == 0) S.keep = k;
-    }
-    __syncthreads();
-    const uint32_t keep = S.keep;
-
-    // Ordered compaction (caller's query order) into this item's region.
-    uint32_t base = 0;
-    for (int i0 = 0; i0 < nQ; i0 += bs) {
-        const int i = i0 + tid;
-        const uint32_t r = i < nQ ? P.res[i] : kNone;
-        const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
-        uint32_t tot;
-        const uint32_t pos = block_scan_flag(f, S.wtot, tot);
-        if (f) A.padded[w.out_off + base + pos] = Out3{i, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
-        base += tot;
-    }
-    if (tid == 0) {
-        A.counts[idx] = base;
-        if (S.cmp) atomicAdd(&A.ncmp[0], (unsigned long long)S.cmp);
-    }
-}
-
-// Pair constants: fundamental matrix (formed by the pair-setup kernel), thresholds,
-// histogram and counter reset.
-__device__ __forceinline__ void pair_setup(const BatchArgs &A, uint32_t idx, ItemShared &S) {
-    const int tid = threadIdx.x;
-    if (tid < 9) S.F[tid] = A.pair_F[9 * (size_t)idx + tid];
-    if (tid == 9) S.cmp = 0u;
-    if (tid < 32) S.hist[tid] = 0;
-    if (tid >= 32 && tid < 32 + kLevels) {
-        const float s = level_scale(tid - 32);
-        S.thr[tid - 32] = fmul(A.sp.epi_chi2, fmul(s, s));
-    }
-}
-
-// Unstaged pair: keypoint arrays read from global memory; shared arrays of stride sn.
-template <int G>
-__device__ __forceinline__ void search_item_global(const BatchArgs &A, const WorkItem &w, uint32_t idx,
-                                   uint32_t *sm, int sn, ItemShared &S) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    PairArrays P;
-    P.Q = KfView::at(w.q, L);
-    P.T = KfView::at(w.t, L);
-    const int nQ = P.Q.hdr->n, nT = P.T.hdr->n;
-    uint32_t *tnode = sm;
-    P.tnode = tnode;
-    P.win = sm + sn;
-    P.accq = sm + 2 * sn;
-    P.res = sm + 3 * sn;
-    P.mq = w.a == kNone ? nullptr : A.masks + w.a;
-    P.mt = w.b == kNone ? nullptr : A.masks + w.b;
-    pair_setup(A, idx, S);
-    for (int j = threadIdx.x; j < nT; j += blockDim.x) { tnode[j] = P.T.node[j]; P.win[j] = kNone; }
-    __syncthreads();
-    search_core<G>(A, w, idx, nQ, nT, P, S);
-}
-
-// Staged pair: both keyframes' arrays are brought into shared memory by bulk copies (one
-// mbarrier phase), the masks by plain loads, so that the whole pipeline runs from shared
-// memory.  accq overlays the query node array (each entry is read by its own query group
-// before it is written), res overlays the query descriptors (dead after the match loop).
-// Returns false if the copies did not complete in time.
-template <int G>
-__device__ __forceinline__ bool search_item_staged(const BatchArgs &A, const WorkItem &w, uint32_t idx,
-                                   unsigned char *sm, uint64_t *bar, uint32_t parity,
-                                   ItemShared &S) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    const StageLayout G2 = StageLayout::make(A.sn);
-    const KfView Qg = KfView::at(w.q, L), Tg = KfView::at(w.t, L);
-    const int nQ = Qg.hdr->n, nT = Tg.hdr->n;
-    const uint32_t q16 = (uint32_t)((nQ + 15) & ~15), t16 = (uint32_t)((nT + 15) & ~15);
-    PairArrays P;
-    P.Q = Qg;
-    P.T = Tg;
-    P.Q.desc = reinterpret_cast<const uint4 *>(sm + G2.qdesc);
-    P.Q.xy = reinterpret_cast<const float2 *>(sm + G2.qxy);
-    P.Q.node = reinterpret_cast<const uint32_t *>(sm + G2.qnode);
-    P.Q.angle = reinterpret_cast<const float *>(sm + G2.qangle);
-    P.Q.orig = reinterpret_cast<const uint16_t *>(sm + G2.qorig);
-    P.T.desc = reinterpret_cast<const uint4 *>(sm + G2.tdesc);
-    P.T.xy = reinterpret_cast<const float2 *>(sm + G2.txy);
-    P.T.node = reinterpret_cast<const uint32_t *>(sm + G2.tnode);
-    P.T.angle = reinterpret_cast<const float *>(sm + G2.tangle);
-    P.T.orig = reinterpret_cast<const uint16_t *>(sm + G2.torig);
-    P.T.level = sm + G2.tlevel;
-    P.tnode = P.T.node;
-    P.win = reinterpret_cast<uint32_t *>(sm + G2.win);
-    P.accq = reinterpret_cast<uint32_t *>(sm + G2.qnode);
-    P.res = reinterpret_cast<uint32_t *>(sm + G2.qdesc);
-    uint8_t *tmask = sm + G2.tmask, *qmask = sm + G2.qmask;
-    P.mq = w.a == kNone ? nullptr : qmask;
-    P.mt = w.b == kNone ? nullptr : tmask;
-    if (threadIdx.x == 0) {
-        fence_proxy_async();
-        const uint32_t bytes = q16 * (32 + 8 + 4 + 4 + 2) + t16 * (32 + 8 + 4 + 4 + 2 + 1);
-        mbar_expect_tx(bar, bytes);
-        if (q16) {
-            bulk_g2s(sm + G2.qdesc, Qg.desc, q16 * 32, bar);
-            bulk_g2s(sm + G2.qxy, Qg.xy, q16 * 8, bar);
-            bulk_g2s(sm + G2.qnode, Qg.node, q16 * 4, bar);
-            bulk_g2s(sm + G2.qangle, Qg.angle, q16 * 4, bar);
-            bulk_g2s(sm + G2.qorig, Qg.orig, q16 * 2, bar);
-        }
-        if (t16) {
-            bulk_g2s(sm + G2.tdesc, Tg.desc, t16 * 32, bar);
-            bulk_g2s(sm + G2.txy, Tg.xy, t16 * 8, bar);
-            bulk_g2s(sm + G2.tnode, Tg.node, t16 * 4, bar);
-            bulk_g2s(sm + G2.tangle, Tg.angle, t16 * 4, bar);
-            bulk_g2s(sm + G2.torig, Tg.orig, t16 * 2, bar);
-            bulk_g2s(sm + G2.tlevel, Tg.level, t16, bar);
-        }
-    }
-    pair_setup(A, idx, S);
-    uint32_t *win = P.win;
-    for (int j = threadIdx.x; j < nT; j += blockDim.x) win[j] = kNone;
-    if (P.mq)
-        for (int i = threadIdx.x; i < nQ; i += blockDim.x) qmask[i] = A.masks[w.a + i];
-    if (P.mt)
-        for (int j = threadIdx.x; j < nT; j += blockDim.x) tmask[j] = A.masks[w.b + j];
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity));
-    if (!ok) return false;
-    search_core<G>(A, w, idx, nQ, nT, P, S);
-    return true;
-}
-
-// Fusion of map points into one keyframe, one thread per map point (Sec. IV-D).
-// Returns the packed (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
+// Fusion of one map point into keyframe T (Sec. IV-D).  Returns the packed
+// (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
 __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &cam,
-                                             const FuseConst &fp, const ItemShared &S,
+                                             const FuseConst &fp, const FuseK &K,
                                              const float *pos, const float *normal,
                                              const uint4 *desc, float mind, float maxd,
                                              uint32_t &cmp) {
@@ -627,23 +411,23 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
     const float X = pos[0], Y = pos[1], Z = pos[2];
     const float nx = normal[0], ny = normal[1], nz = normal[2];
     const uint4 m0 = desc[0], m1 = desc[1];
-    const float xc = fadd(fadd(fadd(fmul(S.R[0], X), fmul(S.R[1], Y)), fmul(S.R[2], Z)), S.t[0]);
-    const float yc = fadd(fadd(fadd(fmul(S.R[3], X), fmul(S.R[4], Y)), fmul(S.R[5], Z)), S.t[1]);
-    const float zc = fadd(fadd(fadd(fmul(S.R[6], X), fmul(S.R[7], Y)), fmul(S.R[8], Z)), S.t[2]);
+    const float xc = fadd(fadd(fadd(fmul(K.R[0], X), fmul(K.R[1], Y)), fmul(K.R[2], Z)), K.t[0]);
+    const float yc = fadd(fadd(fadd(fmul(K.R[3], X), fmul(K.R[4], Y)), fmul(K.R[5], Z)), K.t[1]);
+    const float zc = fadd(fadd(fadd(fmul(K.R[6], X), fmul(K.R[7], Y)), fmul(K.R[8], Z)), K.t[2]);
     if (!(zc > 0.0f)) return kNone;
     const float x = __fdiv_rn(xc, zc), y = __fdiv_rn(yc, zc);
     const float u = fadd(fmul(float(cam.fx), x), float(cam.cx));
     const float v = fadd(fmul(float(cam.fy), y), float(cam.cy));
     if (!(u >= 0.0f && u < float(cam.width) && v >= 0.0f && v < float(cam.height))) return kNone;
-    const float pox = fsub(X, S.O[0]), poy = fsub(Y, S.O[1]), poz = fsub(Z, S.O[2]);
+    const float pox = fsub(X, K.O[0]), poy = fsub(Y, K.O[1]), poz = fsub(Z, K.O[2]);
     const float dist = __fsqrt_rn(fadd(fadd(fmul(pox, pox), fmul(poy, poy)), fmul(poz, poz)));
     if (dist < mind || dist > maxd) return kNone;
     const float cosv = fadd(fadd(fmul(pox, nx), fmul(poy, ny)), fmul(poz, nz));
     if (cosv < fmul(0.5f, dist)) return kNone;
     int pl = kLevels - 1;
     for (int l = 0; l < kLevels; ++l)
-        if (fmul(dist, S.scale[l]) >= maxd) { pl = l; break; }
-    const float r = fmul(fp.radius_scale, S.scale[pl]);
+        if (fmul(dist, K.scale[l]) >= maxd) { pl = l; break; }
+    const float r = fmul(fp.radius_scale, K.scale[pl]);
     const int cx0 = grid_cell(fsub(u, r), cam.cell_w_inv, kGridCols) - 1;
     const int cx1 = grid_cell(fadd(u, r), cam.cell_w_inv, kGridCols) + 1;
     const int cy0 = grid_cell(fsub(v, r), cam.cell_h_inv, kGridRows) - 1;
@@ -660,7 +444,7 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
             if (!(fabsf(fsub(xt.x, u)) < r && fabsf(fsub(xt.y, v)) < r)) continue;
             ++cmp;
             const float ex = fsub(u, xt.x), ey = fsub(v, xt.y);
-            if (!(fadd(fmul(ex, ex), fmul(ey, ey)) <= S.thr[lv])) continue;
+            if (!(fadd(fmul(ex, ex), fmul(ey, ey)) <= K.thr[lv])) continue;
             const uint32_t d = (uint32_t)hamming(m0, m1, T.desc[2 * j], T.desc[2 * j + 1]);
             best = min(best, (d << 16) | (uint32_t)T.orig[j]);
         }
@@ -670,166 +454,306 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
 }
 
 // Pose-derived constants of a fusion target: R, t in float32 and the camera centre
-// O = -R^T t formed in float64; scale and reprojection thresholds per level.
-__device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, ItemShared &S) {
+// O = -R^T t formed in float64 and rounded; scale and reprojection thresholds per level.
+// Threads 0..39 of the calling CTA write K.
+__device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, FuseK &K) {
     const int tid = threadIdx.x;
-    if (tid < 9) S.R[tid] = __double2float_rn(h->Tcw[(tid / 3) * 4 + tid % 3]);
+    if (tid < 9) K.R[tid] = __double2float_rn(h->Tcw[(tid / 3) * 4 + tid % 3]);
     if (tid >= 16 && tid < 19) {
         const int c = tid - 16;
-        S.t[c] = __double2float_rn(h->Tcw[c * 4 + 3]);
+        K.t[c] = __double2float_rn(h->Tcw[c * 4 + 3]);
         double s = dmul(h->Tcw[0 * 4 + c], h->Tcw[0 * 4 + 3]);
         s = dadd(s, dmul(h->Tcw[1 * 4 + c], h->Tcw[1 * 4 + 3]));
         s = dadd(s, dmul(h->Tcw[2 * 4 + c], h->Tcw[2 * 4 + 3]));
-        S.O[c] = __double2float_rn(-s);
+        K.O[c] = __double2float_rn(-s);
     }
     if (tid >= 32 && tid < 32 + kLevels) {
         const float s = level_scale(tid - 32);
-        S.scale[tid - 32] = s;
-        S.thr[tid - 32] = fmul(chi2, fmul(s, s));
+        K.scale[tid - 32] = s;
+        K.thr[tid - 32] = fmul(chi2, fmul(s, s));
     }
 }
 
-// The map points of one fusion item against keyframe view T, in tiles of blockDim, with
-// ordered compaction into the item's region.
-__device__ __forceinline__ void fuse_core(const BatchArgs &A, const WorkItem &w, uint32_t idx, const KfView &T,
-                          ItemShared &S) {
+// ---------------------------------------------------------------- join (S1, S2)
+
+// One CTA per pair.
+
+__global__ void __launch_bounds__(256) join_kernel(BatchArgs A) {
+    extern __shared__ __align__(16) uint32_t jnode[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ bool ok_all;
     const int tid = threadIdx.x, bs = blockDim.x;
-    uint32_t base = 0;
-    for (int k0 = 0; k0 < (int)w.b; k0 += bs) {
-        const int k = k0 + tid;
-        const uint32_t m = w.a + (uint32_t)k;
-        uint32_t cmp = 0;
-        uint32_t r = kNone;
-        if (k < (int)w.b && !(A.mp_skip && A.mp_skip[m]))
-            r = fuse_one(T, A.cam, A.fp, S, A.mp_pos + 3 * (size_t)m, A.mp_normal + 3 * (size_t)m,
-                         A.mp_desc + 2 * (size_t)m, A.mp_min[m], A.mp_max[m], cmp);
-        warp_count(cmp, &S.cmp);
-        uint32_t tot;
-        const uint32_t pos = block_scan_flag(r != kNone, S.wtot, tot);
-        if (r != kNone)
-            A.padded[w.out_off + base + pos] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
-        base += tot;
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const uint32_t i = blockIdx.x;
+    const WorkItem w = A.items[i];
+    const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
+    const int nQ = (int)w.nq, nT = (int)w.nt;
+    const uint32_t q16 = (uint32_t)((nQ + 15) & ~15), t16 = (uint32_t)((nT + 15) & ~15);
+    uint32_t *qn = jnode, *tn = jnode + A.sn;
+    if (tid == 0) {
+        // both node arrays into shared memory with one bulk copy each
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, (q16 + t16) * 4);
+        if (q16) bulk_g2s(qn, Q.node, q16 * 4, &bar);
+        if (t16) bulk_g2s(tn, T.node, t16 * 4, &bar);
+    }
+    __syncthreads();
+    // meanwhile: targets' eligibility in node order, winners reset
+    uint32_t *win = A.win + w.t_off;
+    uint8_t *tel = A.tmask_n ? A.tmask_n + w.t_off : nullptr;
+    for (int j = tid; j < nT; j += bs) {
+        win[j] = kNone;
+        if (tel) tel[j] = w.b == kNone ? 1 : A.masks[w.b + T.orig[j]];
     }
     if (tid == 0) {
-        A.counts[idx] = base;
-        if (S.cmp) atomicAdd(&A.ncmp[1], (unsigned long long)S.cmp);
+        float F[9];
+        fundamental_f32(A.cam, Q.hdr->Tcw, T.hdr->Tcw, F);
+        for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
     }
-}
-
-__device__ __forceinline__ void fuse_item_global(const BatchArgs &A, const WorkItem &w, uint32_t idx, ItemShared &S) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    const KfView T = KfView::at(w.q, L);
-    if (threadIdx.x == 0) S.cmp = 0u;
-    fuse_setup(T.hdr, A.fp.chi2, S);
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (tid == 0) ok_all = true;
     __syncthreads();
-    fuse_core(A, w, idx, T, S);
+    if (!ok) ok_all = false;
+    __syncthreads();
+    if (!ok_all) {
+        if (tid == 0) atomicOr(&A.counters[2], kStatusTimeout);
+        return;
+    }
+    // candidate range of every eligible query
+    uint32_t *qr = A.qrange + w.res_off;
+    for (int p = tid; p < nQ; p += bs) {
+        uint32_t rg = 0;
+        if (w.a == kNone || A.masks[w.a + Q.orig[p]]) {
+            const uint32_t nd = qn[p];
+            const int lo = lower_bound_u32(tn, nT, nd);
+            const int hi = (lo < nT && tn[lo] == nd) ? upper_bound_u32(tn, lo, nT, nd) : lo;
+            rg = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        qr[p] = rg;
+    }
 }
 
-// Staged fusion: the target keyframe's keypoint arrays and grid index are bulk-copied into
-// shared memory first.
-__device__ __forceinline__ bool fuse_item_staged(const BatchArgs &A, const WorkItem &w, uint32_t idx,
-                                 unsigned char *sm, uint64_t *bar, uint32_t parity, ItemShared &S) {
+// ---------------------------------------------------------------- match (S3, S7-S9)
+
+// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  Every
+// load of a round is issued before its first use: the query's range, descriptor, position
+// and caller index together, then each candidate's eligibility, descriptor, position and
+// level together.
+template <int G>
+__device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, uint32_t &cmp) {
     const SlotLayout L = SlotLayout::make(A.cap);
-    const StageLayout G2 = StageLayout::make(A.sn);
-    const KfView Tg = KfView::at(w.q, L);
-    const int nT = Tg.hdr->n;
-    const uint32_t t16 = (uint32_t)((nT + 15) & ~15);
-    KfView T = Tg;
-    T.desc = reinterpret_cast<const uint4 *>(sm + G2.fdesc);
-    T.xy = reinterpret_cast<const float2 *>(sm + G2.fxy);
-    T.orig = reinterpret_cast<const uint16_t *>(sm + G2.forig);
-    T.level = sm + G2.flevel;
-    T.grid_start = reinterpret_cast<const uint16_t *>(sm + G2.fgstart);
-    T.grid_items = reinterpret_cast<const uint16_t *>(sm + G2.fgitems);
-    if (threadIdx.x == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(bar, (uint32_t)(t16 * (32 + 8 + 2 + 1 + 2) + StageLayout::kGridStartBytes));
-        bulk_g2s(sm + G2.fgstart, Tg.grid_start, (uint32_t)StageLayout::kGridStartBytes, bar);
-        if (t16) {
-            bulk_g2s(sm + G2.fdesc, Tg.desc, t16 * 32, bar);
-            bulk_g2s(sm + G2.fxy, Tg.xy, t16 * 8, bar);
-            bulk_g2s(sm + G2.forig, Tg.orig, t16 * 2, bar);
-            bulk_g2s(sm + G2.flevel, Tg.level, t16, bar);
-            bulk_g2s(sm + G2.fgitems, Tg.grid_items, t16 * 2, bar);
+    const KfView Q = KfView::at(un.q, L), T = KfView::at(un.t, L);
+    const uint32_t lane = threadIdx.x & 31u, sub = lane % G;
+    float F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
+    const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
+    const bool epi = A.sp.epipolar != 0;
+#pragma unroll 1
+    for (int r = 0; r < G; ++r) {
+        const int p = (int)(un.group * 32u) + r * (32 / G) + (int)(lane / G);
+        const bool in = p < (int)un.nq;
+        const int pc = in ? p : 0;  // (a valid index for the speculative loads)
+        const uint32_t rg = in ? A.qrange[un.res_off + p] : 0u;
+        const uint4 q0 = Q.desc[2 * pc], q1 = Q.desc[2 * pc + 1];
+        const float2 xq = Q.xy[pc];
+        const uint32_t io = Q.orig[pc];
+        const int lo = (int)(rg & 0xFFFFu), hi = (int)(rg >> 16);
+        uint32_t bkey = kNone, sec = 0xFFFFu;
+        if (lo < hi) {
+            const Line l = epi_line(F, xq.x, xq.y);
+            for (int j = lo + (int)sub; j < hi; j += G) {
+                const uint8_t el = tel ? tel[j] : (uint8_t)1;
+                const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
+                const float2 xt = T.xy[j];
+                const int lv = T.level[j];
+                if (!el) continue;
+                ++cmp;
+                const uint32_t d = (uint32_t)hamming(q0, q1, t0, t1);
+                if (epi) {
+                    const float s = level_scale(lv);
+                    if (!epi_pass(l, xt.x, xt.y, fmul(A.sp.epi_chi2, fmul(s, s)))) continue;
+                }
+                const uint32_t key = (d << 16) | (uint32_t)j;
+                if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
+                else sec = min(sec, d);
+            }
         }
-        S.cmp = 0u;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            const uint32_t ob = __shfl_xor_sync(kFull, bkey, off);
+            const uint32_t os = __shfl_xor_sync(kFull, sec, off);
+            sec = min(min(sec, os), max(bkey, ob) >> 16);
+            bkey = min(bkey, ob);
+        }
+        if (sub == 0 && in) {
+            uint32_t acc = kNone;
+            if (bkey != kNone) {
+                const uint32_t best = bkey >> 16;
+                bool ok = (int)best <= A.sp.hamming_max;
+                if (ok && A.sp.ratio_num != 0 && sec != 0xFFFFu)
+                    ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sec;
+                if (ok) {
+                    const uint32_t j = bkey & 0xFFFFu;
+                    acc = (j << 16) | best;
+                    if (A.sp.resolve) atomicMin(&A.win[un.t_off + j], (best << 16) | io);
+                }
+            }
+            A.acc[un.res_off + p] = acc;
+        }
     }
-    fuse_setup(Tg.hdr, A.fp.chi2, S);
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity));
-    if (!ok) return false;
-    fuse_core(A, w, idx, T, S);
-    return true;
 }
 
 template <int G>
-__device__ __forceinline__ bool run_item(const BatchArgs &A, const WorkItem &w, uint32_t idx,
-                                         unsigned char *sm, uint64_t *bar, uint32_t &parity,
-                                         ItemShared &S) {
-    if (A.staged) {
-        const bool ok = w.kind == kItemSearch ? search_item_staged<G>(A, w, idx, sm, bar, parity, S)
-                                              : fuse_item_staged(A, w, idx, sm, bar, parity, S);
-        parity ^= 1u;
-        return ok;
+__global__ void __launch_bounds__(256) match_kernel(BatchArgs A) {
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t cs = 0;
+    for (uint32_t u = warp; u < A.n_units; u += warps) {
+        const Unit un = A.units[u];
+        match_group<G>(A, un, cs);
     }
-    if (w.kind == kItemSearch)
-        search_item_global<G>(A, w, idx, reinterpret_cast<uint32_t *>(sm), A.sn, S);
-    else
-        fuse_item_global(A, w, idx, S);
-    return true;
+    const uint32_t s = __reduce_add_sync(kFull, cs);
+    if ((threadIdx.x & 31u) == 0 && s) atomicAdd(&A.ncmp[0], (unsigned long long)s);
 }
 
-// Persistent kernel: CTAs take work items (largest first) from an atomic counter until none
-// is left; the last CTA to finish turns the per-item counts into offsets.  Compiled for at
-// most 512 threads (up to 128 registers) and for 1024 threads (up to 64 registers).
-template <int kMaxThreads>
-__global__ void __launch_bounds__(kMaxThreads) batch_kernel(BatchArgs A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ ItemShared S;
+// ---------------------------------------------------------------- fusion (S7-S9)
+
+// One fusion item (up to 256 map points of a step) per CTA.  The target keyframe's grid
+// index, positions, caller indices and levels are bulk-copied into shared memory; each
+// thread projects one map point, walks the grid window in shared memory and reads the
+// descriptors of the keypoints that pass the reprojection gate; ordered compaction.
+__global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) unsigned char fsm[];
+    __shared__ FuseK K;
     __shared__ __align__(8) uint64_t bar;
-    __shared__ bool s_last;
-    if (threadIdx.x == 0 && A.staged) {
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t scmp;
+    __shared__ bool ok_all;
+    const int tid = threadIdx.x;
+    const uint32_t item = A.n_search + blockIdx.x;
+    if (item >= A.n_items) return;
+    const WorkItem w = A.items[item];
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const FuseStage FS = FuseStage::make((int)A.fsn);
+    const KfView Tg = KfView::at(w.q, L);
+    const int nT = Tg.hdr->n;
+    const uint32_t t16 = (uint32_t)((nT + 15) & ~15);
+    if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
+        mbar_expect_tx(&bar, (uint32_t)(t16 * (8 + 2 + 2 + 1) + FuseStage::kGridStartBytes));
+        bulk_g2s(fsm + FS.gstart, Tg.grid_start, (uint32_t)FuseStage::kGridStartBytes, &bar);
+        if (t16) {
+            bulk_g2s(fsm + FS.xy, Tg.xy, t16 * 8, &bar);
+            bulk_g2s(fsm + FS.gitems, Tg.grid_items, t16 * 2, &bar);
+            bulk_g2s(fsm + FS.orig, Tg.orig, t16 * 2, &bar);
+            bulk_g2s(fsm + FS.level, Tg.level, t16, &bar);
+        }
+        scmp = 0u;
     }
+    fuse_setup(Tg.hdr, A.fp.chi2, K);
+    const uint32_t m = w.a + (uint32_t)tid;
+    const bool have = tid < (int)w.b && !(A.mp_skip && A.mp_skip[m]);
     __syncthreads();
-    uint32_t parity = 0;
-    bool healthy = true;
-    for (;;) {
-        if (threadIdx.x == 0) S.item = atomicAdd(&A.counters[0], 1u);
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (tid == 0) ok_all = true;
+    __syncthreads();
+    if (!ok) ok_all = false;
+    __syncthreads();
+    if (!ok_all) {
+        if (tid == 0) atomicOr(&A.counters[2], kStatusTimeout);
+        return;
+    }
+    KfView T = Tg;
+    T.xy = reinterpret_cast<const float2 *>(fsm + FS.xy);
+    T.grid_start = reinterpret_cast<const uint16_t *>(fsm + FS.gstart);
+    T.grid_items = reinterpret_cast<const uint16_t *>(fsm + FS.gitems);
+    T.orig = reinterpret_cast<const uint16_t *>(fsm + FS.orig);
+    T.level = fsm + FS.level;
+    uint32_t cmp = 0, r = kNone;
+    if (have)
+        r = fuse_one(T, A.cam, A.fp, K, A.mp_pos + 3 * (size_t)m, A.mp_normal + 3 * (size_t)m,
+                     A.mp_desc + 2 * (size_t)m, A.mp_min[m], A.mp_max[m], cmp);
+    warp_count(cmp, &scmp);
+    uint32_t tot;
+    const uint32_t pos = block_scan_flag(r != kNone, wtot, tot);
+    if (r != kNone) A.padded[w.out_off + pos] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
+    if (tid == 0) {
+        A.counts[item] = tot;
+        if (scmp) atomicAdd(&A.ncmp[1], (unsigned long long)scmp);
+    }
+}
+
+// ---------------------------------------------------------------- finalize (S4-S6)
+
+// One pair per CTA: the accepted query of each target keeps it only if it is the target's
+// winner; kept matches are binned by rotation, the top-3 bins kept, the pair compacted in
+// caller query order.  The last CTA of the launch turns per-item counts into offsets.
+__global__ void __launch_bounds__(256) finalize_kernel(BatchArgs A) {
+    extern __shared__ __align__(16) uint32_t fres[];  // [sn] per caller-order query
+    __shared__ uint32_t hist[32];
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t keep;
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (blockIdx.x < A.n_search) {
+        const uint32_t i = blockIdx.x;
+        const WorkItem w = A.items[i];
+        const SlotLayout L = SlotLayout::make(A.cap);
+        const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
+        const int nQ = (int)w.nq;
+        const bool rot = A.sp.rot_filter != 0;
+        if (tid < 32) hist[tid] = 0;
         __syncthreads();
-        const uint32_t e = S.item;
-        __syncthreads();
-        if (e >= A.n_items) break;
-        const uint32_t idx = A.order[e];
-        const WorkItem w = A.items[idx];
-        bool ok;
-        switch (A.lanes) {
-            case 1: ok = run_item<1>(A, w, idx, smem, &bar, parity, S); break;
-            case 2: ok = run_item<2>(A, w, idx, smem, &bar, parity, S); break;
-            case 4: ok = run_item<4>(A, w, idx, smem, &bar, parity, S); break;
-            case 8: ok = run_item<8>(A, w, idx, smem, &bar, parity, S); break;
-            case 16: ok = run_item<16>(A, w, idx, smem, &bar, parity, S); break;
-            default: ok = run_item<32>(A, w, idx, smem, &bar, parity, S); break;
+        for (int p0 = 0; p0 < nQ; p0 += bs) {
+            const int p = p0 + tid;
+            uint32_t bin = kNone;
+            if (p < nQ) {
+                const uint32_t acc = A.acc[w.res_off + p], io = Q.orig[p];
+                uint32_t r = kNone;
+                if (acc != kNone) {
+                    const uint32_t j = acc >> 16, d = acc & 0xFFFFu;
+                    if (!A.sp.resolve || A.win[w.t_off + j] == ((d << 16) | io)) {
+                        bin = rot ? (uint32_t)rot_bin(Q.angle[p], T.angle[j]) : 0u;
+                        r = pack_res(T.orig[j], d, bin);
+                    }
+                }
+                fres[io] = r;
+            }
+            if (rot) {
+                const unsigned peers = __match_any_sync(kFull, bin);
+                if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
+                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+            }
         }
-        if (!ok) {  // a bulk copy did not land in time: report and stop taking work
-            if (threadIdx.x == 0) atomicOr(&A.counters[2], kStatusTimeout);
-            healthy = false;
-            break;
+        __syncthreads();
+        if (tid < 32) {
+            const uint32_t k = rot ? top3_mask_warp(hist) : kNone;
+            if (tid == 0) keep = k;
         }
         __syncthreads();
+        uint32_t base = 0;
+        for (int i0 = 0; i0 < nQ; i0 += bs) {
+            const int q = i0 + tid;
+            const uint32_t r = q < nQ ? fres[q] : kNone;
+            const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
+            uint32_t tot;
+            const uint32_t pos = block_scan_flag(f, wtot, tot);
+            if (f) A.padded[w.out_off + base + pos] = Out3{q, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
+            base += tot;
+        }
+        if (tid == 0) A.counts[i] = base;
     }
-    if (!healthy) {
-        // give the copies in flight a last bounded chance to land before the CTA exits
-        mbar_wait_bounded(&bar, parity ^ 1u);
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&A.counters[1], 1u) == gridDim.x - 1;
-    }
+    // the last CTA to finish turns the per-item counts into offsets (no waiting: every other
+    // CTA published its counts before its increment; fusion counts came from match_kernel)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&A.counters[1], 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int tid = threadIdx.x, bs = blockDim.x;
     uint32_t base = 0;
     for (uint32_t i0 = 0; i0 < A.n_items; i0 += bs) {
         const uint32_t i = i0 + tid;
@@ -840,39 +764,24 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(BatchArgs A) {
             const uint32_t y = __shfl_up_sync(kFull, v, o);
             if ((int)lane >= o) v += y;
         }
-        if (lane == 31) S.wtot[warp] = v;
+        if (lane == 31) wtot[warp] = v;
         __syncthreads();
         if (warp == 0) {
-            uint32_t x = lane < nw ? S.wtot[lane] : 0u;
+            uint32_t x = lane < nw ? wtot[lane] : 0u;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(kFull, x, o);
                 if ((int)lane >= o) x += y;
             }
-            if (lane < nw) S.wtot[lane] = x;
+            if (lane < nw) wtot[lane] = x;
         }
         __syncthreads();
-        const uint32_t incl = v + (warp ? S.wtot[warp - 1] : 0u);
+        const uint32_t incl = v + (warp ? wtot[warp - 1] : 0u);
         if (i < A.n_items) A.offsets[i] = base + incl - c;
-        const uint32_t tot = S.wtot[nw - 1];
+        const uint32_t tot = wtot[nw - 1];
         __syncthreads();
         base += tot;
     }
     if (tid == 0) A.offsets[A.n_items] = base;
-}
-
-// Pair setup (one thread per search item): the fundamental matrix of every pair from the
-// poses in the store, float64 rounded to float32.
-__global__ void pair_setup_kernel(BatchArgs A) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n_search) return;
-    const WorkItem w = A.items[i];
-    const KfHeader *qh = reinterpret_cast<const KfHeader *>(w.q);
-    const KfHeader *th = reinterpret_cast<const KfHeader *>(w.t);
-    double tq[12], tt[12];
-    for (int k = 0; k < 12; ++k) { tq[k] = qh->Tcw[k]; tt[k] = th->Tcw[k]; }
-    float F[9];
-    fundamental_f32(A.cam, tq, tt, F);
-    for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
 }
 
 // Gathers the per-item regions into the dense output, one warp per item.
@@ -1015,24 +924,25 @@ __global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float 
                                   const float *normal, const uint4 *desc, const float *mn,
                                   const float *mx, const uint8_t *skip, int n, FuseConst fp,
                                   CamConst cam, uint32_t *res, unsigned long long *ncmp) {
-    __shared__ ItemShared S;
+    __shared__ FuseK K;
+    __shared__ uint32_t scmp;
     const SlotLayout L = SlotLayout::make(cap);
     const KfView T = KfView::at(ts, L);
-    if (threadIdx.x == 0) S.cmp = 0u;
-    fuse_setup(T.hdr, fp.chi2, S);
+    if (threadIdx.x == 0) scmp = 0u;
+    fuse_setup(T.hdr, fp.chi2, K);
     __syncthreads();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cmp = 0;
     if (m < n) {
         uint32_t r = kNone;
         if (!(skip && skip[m]))
-            r = fuse_one(T, cam, fp, S, pos + 3 * (size_t)m, normal + 3 * (size_t)m,
+            r = fuse_one(T, cam, fp, K, pos + 3 * (size_t)m, normal + 3 * (size_t)m,
                          desc + 2 * (size_t)m, mn[m], mx[m], cmp);
         res[m] = r;
     }
-    warp_count(cmp, &S.cmp);
+    warp_count(cmp, &scmp);
     __syncthreads();
-    if (threadIdx.x == 0 && S.cmp) atomicAdd(ncmp, (unsigned long long)S.cmp);
+    if (threadIdx.x == 0 && scmp) atomicAdd(ncmp, (unsigned long long)scmp);
 }
 
 __global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uint32_t *running,
@@ -1074,34 +984,63 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t batch_smem_bytes(int smem_n, bool staged) {
-    return staged ? StageLayout::make(smem_n).bytes : size_t(4) * 4 * (size_t)smem_n;
-}
-
-cudaError_t batch_kernel_prepare(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_join(const BatchArgs &a, cudaStream_t s) {
+    const uint32_t blocks = a.n_search;
+    if (blocks == 0) return cudaSuccess;
+    const size_t smem = size_t(8) * (size_t)a.sn;  // both node arrays
+    cudaError_t e = cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-int batch_ctas_per_sm(int threads, size_t smem) {
-    int n = 0;
-    if (batch_kernel_prepare(smem) != cudaSuccess) return 0;
-    cudaError_t e = threads <= 512
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<512>, threads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1024>, threads, smem);
-    return e == cudaSuccess ? n : 0;
-}
-
-cudaError_t launch_batch(const BatchArgs &a, int ctas, int threads, size_t smem, cudaStream_t s) {
-    if (threads <= 512) batch_kernel<512><<<ctas, threads, smem, s>>>(a);
-    else batch_kernel<1024><<<ctas, threads, smem, s>>>(a);
+    join_kernel<<<blocks, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_setup(const BatchArgs &a, cudaStream_t s) {
-    if (a.n_search == 0) return cudaSuccess;
-    pair_setup_kernel<<<(a.n_search + 127) / 128, 128, 0, s>>>(a);
+template <int G>
+static cudaError_t launch_match_g(const BatchArgs &a, int ctas, cudaStream_t s) {
+    match_kernel<G><<<ctas, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int match_ctas_per_sm(int lanes) {
+    int n = 0;
+    cudaError_t e;
+    switch (lanes) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<1>, 256, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<2>, 256, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<4>, 256, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<8>, 256, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<16>, 256, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<32>, 256, 0); break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_match(const BatchArgs &a, int ctas, cudaStream_t s) {
+    if (a.n_units == 0) return cudaSuccess;
+    switch (a.lanes) {
+        case 1: return launch_match_g<1>(a, ctas, s);
+        case 2: return launch_match_g<2>(a, ctas, s);
+        case 4: return launch_match_g<4>(a, ctas, s);
+        case 8: return launch_match_g<8>(a, ctas, s);
+        case 16: return launch_match_g<16>(a, ctas, s);
+        default: return launch_match_g<32>(a, ctas, s);
+    }
+}
+
+cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s) {
+    const uint32_t blocks = a.n_items - a.n_search;
+    if (blocks == 0) return cudaSuccess;
+    const size_t smem = FuseStage::make((int)a.fsn).bytes;
+    cudaError_t e = cudaFuncSetAttribute(fuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fuse_kernel<<<blocks, kFuseChunk, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const BatchArgs &a, cudaStream_t s) {
+    const size_t smem = size_t(4) * (size_t)a.sn;
+    cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    finalize_kernel<<<a.n_search > 0 ? a.n_search : 1, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -12,16 +12,14 @@ namespace tmap {
 size_t ingest_smem_bytes(int cap);
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
 
-// Persistent batch kernel (search pairs + fusion chunks) and its compaction pass.
-// Dynamic shared memory of the batch kernel for a keypoint stride smem_n (staged: both
-// keyframes of a pair in shared memory; unstaged: four per-keypoint arrays).
-size_t batch_smem_bytes(int smem_n, bool staged);
-int batch_ctas_per_sm(int threads, size_t smem);
-cudaError_t batch_kernel_prepare(size_t smem);
-cudaError_t launch_batch(const BatchArgs &a, int ctas, int threads, size_t smem, cudaStream_t s);
+// Batch pipeline: join (per pair and per step), match (warp units), finalize (per pair,
+// offsets), copy (dense output).
+cudaError_t launch_join(const BatchArgs &a, cudaStream_t s);
+int match_ctas_per_sm(int lanes);
+cudaError_t launch_match(const BatchArgs &a, int ctas, cudaStream_t s);
+cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s);
+cudaError_t launch_finalize(const BatchArgs &a, cudaStream_t s);
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
-// Pair setup: fundamental matrix of every search item (one thread per item).
-cudaError_t launch_pair_setup(const BatchArgs &a, cudaStream_t s);
 
 // Plain per-pair form: every stage of one pair is its own launch, with global scratch.
 struct PairScratch {

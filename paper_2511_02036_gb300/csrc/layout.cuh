@@ -18,8 +18,8 @@ constexpr int kGridCols = 64;
 constexpr int kGridRows = 48;
 constexpr int kGridCells = kGridCols * kGridRows;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr int kFuseChunk = 256;         // map points per fusion item, unstaged kernel
-constexpr int kFuseChunkStaged = 2048;  // map points per fusion item, staged kernel
+constexpr int kFuseChunk = 256; // map points per fusion item (one CTA of the fusion kernel)
+constexpr int kQueryGroup = 32; // queries per search unit (one warp)
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
@@ -96,52 +96,12 @@ struct IngestArgs {
     float cell_w_inv, cell_h_inv;  // grid cells per pixel
 };
 
-// Shared-memory carve of the staged batch kernel for a stride of sn keypoints (a multiple
-// of 16).  A search item stages both keyframes of its pair; a fusion item stages its target
-// keyframe and its projection grid.  The two carves overlay the same memory.
-struct StageLayout {
-    size_t tdesc, qdesc, txy, qxy, tnode, qnode, tangle, qangle, win, torig, qorig, tlevel,
-        tmask, qmask, search_bytes;
-    size_t fdesc, fxy, forig, flevel, fgstart, fgitems, fuse_bytes, bytes;
-    static constexpr size_t kGridStartBytes = ((size_t(kGridCells + 1) * 2 + 15) / 16) * 16;
-    __host__ __device__ static StageLayout make(int sn) {
-        StageLayout L;
-        const size_t n = (size_t)sn;
-        size_t o = 0;
-        L.tdesc = o;  o = align128(o + n * 32);
-        L.qdesc = o;  o = align128(o + n * 32);
-        L.txy = o;    o = align128(o + n * 8);
-        L.qxy = o;    o = align128(o + n * 8);
-        L.tnode = o;  o = align128(o + n * 4);
-        L.qnode = o;  o = align128(o + n * 4);
-        L.tangle = o; o = align128(o + n * 4);
-        L.qangle = o; o = align128(o + n * 4);
-        L.win = o;    o = align128(o + n * 4);
-        L.torig = o;  o = align128(o + n * 2);
-        L.qorig = o;  o = align128(o + n * 2);
-        L.tlevel = o; o = align128(o + n);
-        L.tmask = o;  o = align128(o + n);
-        L.qmask = o;  o = align128(o + n);
-        L.search_bytes = o;
-        o = 0;
-        L.fdesc = o;   o = align128(o + n * 32);
-        L.fxy = o;     o = align128(o + n * 8);
-        L.forig = o;   o = align128(o + n * 2);
-        L.flevel = o;  o = align128(o + n);
-        L.fgstart = o; o = align128(o + kGridStartBytes);
-        L.fgitems = o; o = align128(o + n * 2);
-        L.fuse_bytes = o;
-        L.bytes = L.search_bytes > L.fuse_bytes ? L.search_bytes : L.fuse_bytes;
-        return L;
-    }
-};
-
 enum : uint32_t { kItemSearch = 0, kItemFuse = 1 };
 // Device status word bits.
 enum : uint32_t { kStatusTimeout = 1u };
 
-// One unit of the persistent launch: a (new keyframe, neighbour) pair, or a chunk of up to
-// kFuseChunk map points fused into a keyframe.
+// An output item: a (new keyframe, neighbour) pair of a step, or up to kFuseChunk map points
+// of a step fused into the step's new keyframe.
 struct WorkItem {
     const unsigned char *q;  // search: new keyframe slot; fuse: target keyframe slot
     const unsigned char *t;  // search: neighbour slot; fuse: unused
@@ -150,7 +110,41 @@ struct WorkItem {
     uint32_t a;              // search: byte offset of q mask (kNone: all free); fuse: first mp
     uint32_t b;              // search: byte offset of t mask;                   fuse: mp count
     uint32_t c;              // fuse: first mp of the step (output mp_idx = m - c)
+    uint32_t nq, nt;         // search: keypoint counts
+    uint32_t res_off;        // search: first per-query entry (range, accepted match)
+    uint32_t t_off;          // search: first per-target entry (winner, eligibility)
+    uint32_t step;           // fuse: step index (target constants)
     uint32_t cost;           // scheduling estimate
+    uint32_t pad;
+};
+
+// A unit of the match kernel, one warp: 32 node-order queries of a search item, with what
+// the warp needs of the item (so that it reads one record).
+struct Unit {
+    const unsigned char *q, *t;  // slots of the pair
+    uint32_t item;
+    uint32_t group;              // queries 32*group ..
+    uint32_t nq;
+    uint32_t res_off, t_off;
+    uint32_t pad;
+};
+
+// Shared-memory carve of a fusion CTA: the target keyframe's grid and the keypoint arrays the
+// window test reads, for a capacity of sn keypoints (a multiple of 16).
+struct FuseStage {
+    size_t xy, gstart, gitems, orig, level, bytes;
+    static constexpr size_t kGridStartBytes = ((size_t(kGridCells + 1) * 2 + 15) / 16) * 16;
+    __host__ __device__ static constexpr FuseStage make(int sn) {
+        FuseStage L{};
+        size_t o = 0;
+        L.xy = o;     o = align128(o + size_t(sn) * 8);
+        L.gstart = o; o = align128(o + kGridStartBytes);
+        L.gitems = o; o = align128(o + size_t(sn) * 2);
+        L.orig = o;   o = align128(o + size_t(sn) * 2);
+        L.level = o;  o = align128(o + size_t(sn));
+        L.bytes = o;
+        return L;
+    }
 };
 
 struct SearchConst {
@@ -173,31 +167,35 @@ struct CamConst {
 
 struct Out3 { int32_t a, b, c; };
 
-// Arguments of the persistent batch kernel and its copy pass.
+// Arguments of the batch kernels (join, match, finalize, copy).
 struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
-    const uint32_t *order;        // execution order (largest first)
     uint32_t n_items;
-    uint32_t *counters;           // [0] next item, [1] CTAs done, [2] status
-    const uint8_t *masks;
+    uint32_t n_search;            // search items come first
+    const Unit *units;            // match kernel work list
+    uint32_t n_units;
+    uint32_t fsn;                 // fusion kernel stage capacity (largest target, rounded to 16)
+    uint32_t *counters;           // [0] spare, [1] finalize CTAs done, [2] status
+    const uint8_t *masks;         // caller-order eligibility masks
     const float *mp_pos, *mp_normal, *mp_min, *mp_max;
     const uint4 *mp_desc;
     const uint8_t *mp_skip;
     Out3 *padded;                 // per-item regions
     uint32_t *counts;             // [n_items]
-    uint32_t *offsets;            // [n_items + 1] exclusive scan of counts, written by last CTA
+    uint32_t *offsets;            // [n_items + 1] exclusive scan of counts
     unsigned long long *ncmp;     // [2] search, fuse comparisons
-    float *pair_F;                // [n_search][9] fundamental matrix of each search item
-    uint32_t n_search;            // search items come first in logical order
     Out3 *dense;                  // compacted output
-    uint32_t *status;             // device error word
+    float *pair_F;                // [n_search][9] fundamental matrix of each pair
+    uint32_t *qrange;             // per query (node order): candidate range lo | hi << 16
+    uint32_t *acc;                // per query (node order): accepted (target << 16 | dist)
+    uint32_t *win;                // per target (node order): winner (dist << 16 | query)
+    uint8_t *tmask_n;             // per target (node order): eligible, or null if no masks
     SearchConst sp;
     FuseConst fp;
     CamConst cam;
     int32_t cap;                  // slot capacity (keypoints)
     int32_t lanes;                // lanes per query
-    int32_t staged;               // 1: TMA-staged kernel, sn = stage stride
-    int32_t sn;
+    int32_t sn;                   // largest keypoint count of the batch's pairs (rounded to 32)
 };
 
 }  // namespace tmap

@@ -396,8 +396,9 @@ extern "C" tm_status tm_store_get_stats(tm_ctx *c, tm_store_stats *o) {
 void BatchBuf::release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
-    for (DevBuf *b : {&items, &order, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F})
+    for (DevBuf *b : {&items, &units, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
+                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F,
+                      &qrange, &acc, &win, &tmask_n})
         b->release();
     h_stage.release();
     h_out.release();
@@ -407,6 +408,11 @@ void BatchBuf::release() {
             cudaEventDestroy(e);
             e = nullptr;
         }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (aux) cudaStreamDestroy(aux);
+    fork = join = nullptr;
+    aux = nullptr;
 }
 
 static SearchConst to_const(const tm_search_params &p) {
@@ -424,7 +430,7 @@ static SearchConst to_const(const tm_search_params &p) {
 static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &fp) {
     if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0))
         return fail(TM_ERR_INVALID_ARG, "bad search parameters");
-    if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR && sp.mode != TM_MODE_FUSED_GLOBAL)
+    if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR)
         return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
     const int l = sp.lanes_per_query;
     if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
@@ -498,7 +504,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.step_pair_begin.assign(n_steps + 1, 0);
     B.step_fuse_item.assign(n_steps + 1, 0);
     B.n_pairs = 0;
-    uint32_t pad = 0;
+    uint32_t pad = 0, res_off = 0, t_off = 0;
     int smem_n = 32;
     auto slot_of = [&](uint64_t id, int &slot) -> tm_status {
         auto it = c->ids.find(id);
@@ -506,6 +512,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         slot = it->second;
         return TM_OK;
     };
+    bool any_mask = false;
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
         int qs;
@@ -522,16 +529,22 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             const int nt = c->slots[ts].n;
             if (S.nbr_free_off >= 0 && toff + (size_t)nt > mask_bytes)
                 return fail(TM_ERR_INVALID_ARG, "step %d: neighbour masks outside masks", k);
-            WorkItem w;
+            WorkItem w{};
             w.q = c->slots[qs].ptr;
             w.t = c->slots[ts].ptr;
             w.kind = kItemSearch;
             w.out_off = pad;
             w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;
             w.b = S.nbr_free_off >= 0 ? (uint32_t)toff : kNone;
-            w.c = 0;
+            w.nq = (uint32_t)nq;
+            w.nt = (uint32_t)nt;
+            w.res_off = res_off;
+            w.t_off = t_off;
             w.cost = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, (uint64_t)nq + nt + (uint64_t)nq * nt / 256);
+            any_mask |= w.b != kNone;
             pad += (uint32_t)(sp.resolve ? std::min(nq, nt) : nq);
+            res_off += (uint32_t)nq;
+            t_off += (uint32_t)nt;
             smem_n = std::max(smem_n, std::max(nq, nt));
             items.push_back(w);
             B.item_nq.push_back(nq);
@@ -544,16 +557,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     }
     B.step_pair_begin[n_steps] = B.n_pairs;
     B.n_search_items = (uint32_t)items.size();
-    // staged kernel when every keyframe of the batch fits in shared memory
-    int max_n = 0;
-    for (int k = 0; k < n_steps; ++k) {
-        max_n = std::max(max_n, c->slots[c->ids[steps[k].kf_id]].n);
-        for (int j = 0; j < steps[k].n_nbrs; ++j) max_n = std::max(max_n, c->slots[c->ids[steps[k].nbr_ids[j]]].n);
-    }
-    const int sn16 = std::max(16, (max_n + 15) & ~15);
-    const size_t static_smem = 2048;
-    B.staged = sp.mode == TM_MODE_FUSED && StageLayout::make(sn16).bytes + static_smem <= c->max_smem;
-    const int fuse_chunk = B.staged ? kFuseChunkStaged : kFuseChunk;
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
         B.step_fuse_item[k] = (int)items.size();
@@ -561,15 +564,15 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         if (S.mp_begin < 0 || (int64_t)S.mp_begin + S.mp_count > mps.n)
             return fail(TM_ERR_INVALID_ARG, "step %d: map point range outside the batch", k);
         const int qs = c->ids[S.kf_id];
-        for (int b = 0; b < S.mp_count; b += fuse_chunk) {
-            WorkItem w;
+        for (int b = 0; b < S.mp_count; b += kFuseChunk) {
+            WorkItem w{};
             w.q = c->slots[qs].ptr;
-            w.t = nullptr;
             w.kind = kItemFuse;
             w.out_off = pad;
             w.a = (uint32_t)(S.mp_begin + b);
-            w.b = (uint32_t)std::min(fuse_chunk, S.mp_count - b);
+            w.b = (uint32_t)std::min(kFuseChunk, S.mp_count - b);
             w.c = (uint32_t)S.mp_begin;
+            w.step = (uint32_t)k;
             w.cost = 2 * w.b;
             pad += w.b;
             items.push_back(w);
@@ -580,19 +583,36 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.n_items = (uint32_t)items.size();
     B.n_steps = n_steps;
     B.total_pad = pad;
-    B.smem_n = B.staged ? sn16 : ((smem_n + 31) & ~31);
+    B.smem_n = (smem_n + 31) & ~31;
     B.slots = slots_used;
-    // execution order: largest first (longest-processing-time-first over persistent CTAs)
-    std::vector<uint32_t> order(items.size());
+    B.res_total = res_off;
+    B.t_total = t_off;
+    // match-kernel units: query groups of the pairs, largest pairs first, then fusion items
+    std::vector<uint32_t> order(B.n_search_items);
     for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t x, uint32_t y) { return items[x].cost > items[y].cost; });
+    std::vector<Unit> units;
+    for (uint32_t i : order) {
+        const WorkItem &w = items[i];
+        for (uint32_t g = 0; g * kQueryGroup < w.nq; ++g)
+            units.push_back(Unit{w.q, w.t, i, g, w.nq, w.res_off, w.t_off, 0u});
+    }
+    B.n_units = (uint32_t)units.size();
+    // fusion stage: the largest target of the batch
+    int fuse_n = 0;
+    for (uint32_t i = B.n_search_items; i < items.size(); ++i)
+        fuse_n = std::max(fuse_n, c->slots[c->ids[steps[items[i].step].kf_id]].n);
+    B.fsn = (uint32_t)std::max(16, (fuse_n + 15) & ~15);
     // device buffers
     const size_t ni = std::max<size_t>(1, items.size());
     const size_t nm = std::max<int>(1, mps.n);
+    const size_t nu = std::max<size_t>(1, units.size());
+    const size_t nsi = std::max<size_t>(1, B.n_search_items);
+    const size_t nres = std::max<size_t>(1, res_off), ntt = std::max<size_t>(16, t_off);
     cudaError_t e;
     std::vector<void *> before = B.pointers();
-    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.order.reserve(ni * 4)) ||
+    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.units.reserve(nu * sizeof(Unit))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.offsets.reserve((ni + 1) * 4)) ||
         (e = B.ncmp.reserve(16)) || (e = B.counters.reserve(16)) ||
         (e = B.padded.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
@@ -601,19 +621,23 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (e = B.pair_F.reserve(std::max<size_t>(1, B.n_search_items) * 9 * sizeof(float))))
+        (e = B.pair_F.reserve(nsi * 9 * sizeof(float))) || (e = B.qrange.reserve(nres * 4)) ||
+        (e = B.acc.reserve(nres * 4)) || (e = B.win.reserve(ntt * 4)) ||
+        (e = B.tmask_n.reserve(ntt)))
         return cuda_fail(e, "batch buffers");
     if (B.pointers() != before && B.graph) {
         cudaGraphExecDestroy(B.graph);
         B.graph = nullptr;
     }
-    const size_t stage = ni * sizeof(WorkItem) + ni * 4;
+    // one pinned staging area, one transfer per table: items, units
+    const size_t o_units = align128(ni * sizeof(WorkItem));
+    const size_t stage = o_units + nu * sizeof(Unit);
     if ((e = B.h_stage.reserve(stage))) return cuda_fail(e, "pinned staging");
     unsigned char *h = static_cast<unsigned char *>(B.h_stage.p);
     if (!items.empty()) memcpy(h, items.data(), items.size() * sizeof(WorkItem));
-    if (!order.empty()) memcpy(h + ni * sizeof(WorkItem), order.data(), order.size() * 4);
+    if (!units.empty()) memcpy(h + o_units, units.data(), units.size() * sizeof(Unit));
     if ((e = cudaMemcpyAsync(B.items.p, h, items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(B.order.p, h + ni * sizeof(WorkItem), order.size() * 4, cudaMemcpyHostToDevice, s)))
+        (e = cudaMemcpyAsync(B.units.p, h + o_units, units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "work list upload");
     if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
         return cuda_fail(e, "mask upload");
@@ -630,8 +654,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     }
     BatchArgs &A = B.args;
     A.items = static_cast<const WorkItem *>(B.items.p);
-    A.order = static_cast<const uint32_t *>(B.order.p);
     A.n_items = B.n_items;
+    A.n_search = B.n_search_items;
+    A.units = static_cast<const Unit *>(B.units.p);
+    A.n_units = B.n_units;
     A.counters = static_cast<uint32_t *>(B.counters.p);
     A.masks = static_cast<const uint8_t *>(B.masks.p);
     A.mp_pos = static_cast<const float *>(B.mp_pos.p);
@@ -645,16 +671,18 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.offsets = static_cast<uint32_t *>(B.offsets.p);
     A.ncmp = static_cast<unsigned long long *>(B.ncmp.p);
     A.dense = static_cast<Out3 *>(B.dense.p);
-    A.status = static_cast<uint32_t *>(B.counters.p) + 2;
     A.pair_F = static_cast<float *>(B.pair_F.p);
-    A.n_search = B.n_search_items;
+    A.qrange = static_cast<uint32_t *>(B.qrange.p);
+    A.acc = static_cast<uint32_t *>(B.acc.p);
+    A.win = static_cast<uint32_t *>(B.win.p);
+    A.tmask_n = any_mask ? static_cast<uint8_t *>(B.tmask_n.p) : nullptr;
+    A.fsn = B.fsn;
     A.sp = to_const(sp);
     A.fp.chi2 = fp.chi2;
     A.fp.hamming_max = fp.hamming_max;
     A.fp.radius_scale = fp.radius_scale;
     A.cam = c->camc;
     A.cap = c->cap;
-    A.staged = B.staged ? 1 : 0;
     A.sn = B.smem_n;
     B.sp = sp;
     B.fp = fp;
@@ -663,8 +691,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 }
 
 std::vector<void *> BatchBuf::pointers() const {
-    return {items.p, order.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p, pair_F.p};
+    return {items.p, units.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
+            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p, pair_F.p,
+            qrange.p, acc.p, win.p, tmask_n.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -693,28 +722,36 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 // compaction).
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s) {
     cudaError_t e;
-    const size_t smem = batch_smem_bytes(B.smem_n, B.staged);
-    if ((e = batch_kernel_prepare(smem))) return cuda_fail(e, "batch kernel attribute");
-    int per_sm = batch_ctas_per_sm(threads, smem);
-    if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "batch kernel does not fit: %d threads, %zu B shared", threads, smem);
+    (void)threads;  // the match kernel runs 256-thread CTAs of independent warps
     B.args.lanes = lanes;
-    B.threads = threads;
+    B.threads = 256;
     B.lanes = lanes;
-    B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>(B.n_items, (uint32_t)(per_sm * c->num_sms)));
+    const int per_sm = match_ctas_per_sm(lanes);
+    if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "match kernel does not fit");
+    B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_units + 7) / 8, (uint32_t)(per_sm * c->num_sms)));
     const bool timed = B.ev[0] != nullptr;
     if (timed && (e = record_stage(B.ev[0], s))) return cuda_fail(e, "event");
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
     if ((e = cudaMemsetAsync(B.counters.p, 0, 16, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
         return cuda_fail(e, "reset counters");
-    if ((e = launch_pair_setup(B.args, s))) return cuda_fail(e, "pair setup kernel");
-    if (timed && (e = record_stage(B.ev[1], s))) return cuda_fail(e, "event");
-    if (B.n_items == 0) {
-        if ((e = cudaMemsetAsync(B.offsets.p, 0, 4, s))) return cuda_fail(e, "offsets");
-    } else if ((e = launch_batch(B.args, B.ctas, threads, smem, s))) {
-        return cuda_fail(e, "batch kernel");
+    // fusion runs as a parallel branch, joined before finalize (whose last CTA needs its counts)
+    const bool branch = B.n_items > B.n_search_items;
+    if (branch) {
+        if (!B.aux && ((e = cudaStreamCreateWithFlags(&B.aux, cudaStreamNonBlocking)) ||
+                       (e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming)) ||
+                       (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming))))
+            return cuda_fail(e, "fusion branch");
+        if ((e = cudaEventRecord(B.fork, s)) || (e = cudaStreamWaitEvent(B.aux, B.fork, 0)) ||
+            (e = launch_fuse(B.args, B.aux)) || (e = cudaEventRecord(B.join, B.aux)))
+            return cuda_fail(e, "fusion kernel");
     }
+    if ((e = launch_join(B.args, s))) return cuda_fail(e, "join kernel");
+    if (timed && (e = record_stage(B.ev[1], s))) return cuda_fail(e, "event");
+    if ((e = launch_match(B.args, B.ctas, s))) return cuda_fail(e, "match kernel");
+    if (branch && (e = cudaStreamWaitEvent(s, B.join, 0))) return cuda_fail(e, "fusion join");
+    if ((e = launch_finalize(B.args, s))) return cuda_fail(e, "finalize kernel");
     if (timed && (e = record_stage(B.ev[2], s))) return cuda_fail(e, "event");
-    if (B.n_items && (e = launch_copy(B.args, std::min<int>(B.n_items, 4 * c->num_sms), s)))
+    if (B.n_items && (e = launch_copy(B.args, std::min<int>((B.n_items + 7) / 8, 8 * c->num_sms), s)))
         return cuda_fail(e, "copy kernel");
     if (timed && (e = record_stage(B.ev[3], s))) return cuda_fail(e, "event");
     return TM_OK;
@@ -812,13 +849,10 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 
 // ------------------------------------------------------------------------- tuning
 
-static const int kTuneThreadsGlobal[] = {128, 256, 512};
-static const int kTuneThreadsStaged[] = {512, 1024};
 static const int kTuneLanes[] = {1, 2, 4, 8, 32};
 
-// Default launch shape: one 1024-thread CTA per SM for the staged kernel (its shared memory
-// holds a whole pair), 256-thread CTAs otherwise.
-int tmap::default_threads(const BatchBuf &B) { return B.staged ? 1024 : 256; }
+// Default launch shape: 256-thread CTAs (several per SM).
+int tmap::default_threads(const BatchBuf &B) { (void)B; return 256; }
 
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
@@ -859,7 +893,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaError_t e;
     if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "tuning");
-    const int key = density_key(hc[0], batch_queries(c, B, steps)) * 2 + (B.staged ? 1 : 0);
+    const int key = density_key(hc[0], batch_queries(c, B, steps));
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) {
         B.threads = it->second.first;
@@ -876,12 +910,9 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bt = default_threads(B), bl = c->def_lanes;
-    std::vector<int> threads_set;
-    if (B.staged) threads_set.assign(std::begin(kTuneThreadsStaged), std::end(kTuneThreadsStaged));
-    else threads_set.assign(std::begin(kTuneThreadsGlobal), std::end(kTuneThreadsGlobal));
+    const int threads_set[] = {256};
     for (int th : threads_set)
         for (int ln : kTuneLanes) {
-            if (batch_ctas_per_sm(th, batch_smem_bytes(B.smem_n, B.staged)) < 1) continue;
             if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
             float tot = 0.0f;
             for (int r = 0; r < 3; ++r) {
@@ -919,7 +950,7 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     } else {
         int th = default_threads(B), ln = c->def_lanes;
         if (sp.lanes_per_query) ln = sp.lanes_per_query;
-        else if (c->last_staged == (int)B.staged) {
+        else if (c->last_staged == 1) {
             th = c->last_threads;
             ln = c->last_lanes;
         }
@@ -1084,7 +1115,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
             if (!st) {
                 c->last_threads = P->B.threads;
                 c->last_lanes = P->B.lanes;
-                c->last_staged = P->B.staged ? 1 : 0;
+                c->last_staged = 1;
             }
         }
     }
@@ -1101,7 +1132,6 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         const int th = P->B.threads, ln = P->B.lanes;
         for (cudaEvent_t &ev : P->B.ev)
             if (!st && (e = cudaEventCreate(&ev))) st = cuda_fail(e, "events");
-        if ((e = batch_kernel_prepare(batch_smem_bytes(P->B.smem_n, P->B.staged)))) st = cuda_fail(e, "attribute");
         cudaGraph_t g = nullptr;
         if (!st && (e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
             st = cuda_fail(e, "begin capture");
@@ -1113,7 +1143,11 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         }
         if (!st && (e = cudaGraphInstantiate(&P->B.graph, g, 0))) st = cuda_fail(e, "graph instantiate");
         if (g) cudaGraphDestroy(g);
-        P->kernels_per_run = (P->B.n_items ? 2 : 0) + (P->B.n_search_items ? 1 : 0) + (P->B.n_new ? 1 : 0);
+        // join and match (when there are pairs), fuse (when there are map points), finalize,
+        // copy (when there are items), ingest (when keyframes enter with the batch)
+        P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_units ? 1 : 0) +
+                             (P->B.n_items > P->B.n_search_items ? 1 : 0) + 1 + (P->B.n_items ? 1 : 0) +
+                             (P->B.n_new ? 1 : 0);
     } else {
         P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)

@@ -47,8 +47,8 @@ struct IngestStage {
 
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
-    DevBuf items, order, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, offsets, ncmp, counters, dense, scratch, pair_F;
+    DevBuf items, units, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
+        counts, offsets, ncmp, counters, dense, scratch, pair_F, qrange, acc, win, tmask_n;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -56,15 +56,17 @@ struct BatchBuf {
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
-    uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
+    uint32_t n_items = 0, n_search_items = 0, total_pad = 0, n_units = 0;
+    uint32_t res_total = 0, t_total = 0, fsn = 16;
     int n_steps = 0, n_pairs = 0, smem_n = 32;
-    bool staged = false;  // keyframes of every item fit in shared memory (TMA-staged kernel)
     int threads = 256, lanes = 1, ctas = 0;
     tm_search_params sp{};
     tm_fuse_params fp{};
     BatchArgs args{};
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries (plans)
+    cudaStream_t aux = nullptr;          // fusion branch of the launch
+    cudaEvent_t fork = nullptr, join = nullptr;
     std::vector<void *> pointers() const;
     void release();
 };
