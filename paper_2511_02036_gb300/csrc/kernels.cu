@@ -2,12 +2,14 @@
 //
 //   ingest_kernel      Sec. IV-B  keyframe enters the store: sort keypoints by BoW node,
 //                                 build the 64x48 projection-grid index (one CTA per KF)
-//   batch_kernel       Sec. IV-C  correspondence search, one CTA per (new KF, neighbour) pair:
-//                                 node join -> Hamming + epipolar gate -> best/second ->
-//                                 one match per target -> rotation histogram -> ordered
-//                                 compaction, all in shared memory
-//                      Sec. IV-D  fusion search, one thread per map point: projection gates ->
+//   prep_kernel        Sec. IV-C  per (new KF, neighbour) pair: fundamental matrix, per-target
+//                                 state reset, neighbour eligibility in node order
+//   match_kernel       Sec. IV-C  warp per 32 queries: node join -> Hamming + epipolar gate ->
+//                                 best/second -> accept -> per-target winner (atomicMin)
+//   fuse_kernel        Sec. IV-D  fusion search, one thread per map point: projection gates ->
 //                                 grid window -> reprojection gate -> best Hamming
+//   finalize_kernel    Sec. IV-C  per pair: one match per target -> rotation histogram ->
+//                                 top-3 bins -> ordered compaction; offsets
 //   copy_kernel                   gathers the per-item regions into one dense array
 //   pair_* / fuse_*    plain form: one pair per launch sequence, global scratch
 //
@@ -197,7 +199,8 @@ __device__ __forceinline__ uint32_t pack_res(uint32_t t, uint32_t d, uint32_t bi
 
 // ------------------------------------------------------------------------- ingest
 
-constexpr int kSortE = 8;  // keys per thread-chunk of the block merge sort
+constexpr int kSortE = 2;            // keys per thread-chunk of the block merge sort
+constexpr int kIngestThreads = 1024;
 
 // Sorts N unique keys in shared memory (N a power of two >= kSortE): every chunk of kSortE
 // keys is sorted in registers, then runs are merged pairwise (merge path: each chunk of the
@@ -223,7 +226,7 @@ __device__ K *block_merge_sort(K *a, K *b, int N) {
     for (int L = kSortE; L < N; L <<= 1) {
         for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
             const int o = c * kSortE;
-            const int pb = (o / (2 * L)) * (2 * L), d = o - pb;
+            const int pb = o & ~(2 * L - 1), d = o - pb;
             const K *A = src + pb, *B = src + pb + L;
             int lo = d > L ? d - L : 0, hi = d < L ? d : L;
             while (lo < hi) {
@@ -244,61 +247,75 @@ __device__ K *block_merge_sort(K *a, K *b, int N) {
 }
 
 // One CTA per keyframe entering the store (Sec. IV-B): stable order by BoW node (key
-// node << 32 | caller index), gather of every keypoint array into that order, then the
-// projection grid (key cell << 16 | node-order position) and its cell starts.
-__global__ void __launch_bounds__(512) ingest_kernel(IngestArgs A) {
+// node << 32 | caller index); gather of every keypoint array into that order, forming each
+// keypoint's projection-grid key (cell << 16 | node-order position) on the way; sort of the
+// grid keys; cell starts by one pass over the sorted keys.
+__global__ void __launch_bounds__(kIngestThreads) ingest_kernel(IngestArgs A) {
     extern __shared__ __align__(16) unsigned long long skeys[];
+    __shared__ uint16_t gs[kGridCells + 1];
     const IngestJob &job = A.jobs[blockIdx.x];
     const int n = job.n;
+    const int tid = threadIdx.x, bs = blockDim.x;
     int N = kSortE;
     while (N < n) N <<= 1;
     const SlotLayout L = SlotLayout::make(A.cap);
     unsigned char *base = job.slot;
     unsigned long long *k0 = skeys, *k1 = skeys + N;
     // padding keys are distinct and above every real key
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
+    for (int i = tid; i < N; i += bs)
         k0[i] = i < n ? ((unsigned long long)A.node[job.src + i] << 32) | (unsigned)i
                       : ~0ull - (unsigned long long)i;
     __syncthreads();
     const unsigned long long *sorted = block_merge_sort(k0, k1, N);
+    // the other buffer holds the two grid-key buffers of N 32-bit keys each
+    uint32_t *c0 = reinterpret_cast<uint32_t *>(sorted == k0 ? k1 : k0), *c1 = c0 + N;
     uint4 *desc = reinterpret_cast<uint4 *>(base + L.desc);
     float2 *xy = reinterpret_cast<float2 *>(base + L.xy);
     float *angle = reinterpret_cast<float *>(base + L.angle);
     uint32_t *node = reinterpret_cast<uint32_t *>(base + L.node);
     uint16_t *orig = reinterpret_cast<uint16_t *>(base + L.orig);
     uint8_t *level = base + L.level;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const uint32_t o = (uint32_t)(sorted[p] & 0xFFFFFFFFull);
-        const uint32_t s = job.src + o;
-        desc[2 * p] = A.desc[2 * s];
-        desc[2 * p + 1] = A.desc[2 * s + 1];
-        xy[p] = A.xy[s];
-        angle[p] = A.angle[s];
-        node[p] = A.node[s];
-        orig[p] = (uint16_t)o;
-        const uint8_t lv = A.level[s];
-        level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
-    }
-    __syncthreads();
-    uint32_t *c0 = reinterpret_cast<uint32_t *>(skeys), *c1 = c0 + N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        uint32_t key = 0xFFFFFFFFu - (uint32_t)i;
-        if (i < n) {
-            const float2 v = xy[i];
+    for (int p = tid; p < N; p += bs) {
+        uint32_t key = 0xFFFFFFFFu - (uint32_t)p;  // padding: above every real key
+        if (p < n) {
+            const uint32_t o = (uint32_t)(sorted[p] & 0xFFFFFFFFull);
+            const uint32_t s = job.src + o;
+            const uint4 d0 = A.desc[2 * s], d1 = A.desc[2 * s + 1];
+            const float2 v = A.xy[s];
+            const float an = A.angle[s];
+            const uint32_t nd = A.node[s];
+            const uint8_t lv = A.level[s];
+            desc[2 * p] = d0;
+            desc[2 * p + 1] = d1;
+            xy[p] = v;
+            angle[p] = an;
+            node[p] = nd;
+            orig[p] = (uint16_t)o;
+            level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
             const int cx = grid_cell(v.x, A.cell_w_inv, kGridCols);
             const int cy = grid_cell(v.y, A.cell_h_inv, kGridRows);
-            key = ((uint32_t)(cy * kGridCols + cx) << 16) | (uint32_t)i;
+            key = ((uint32_t)(cy * kGridCols + cx) << 16) | (uint32_t)p;
         }
-        c0[i] = key;
+        c0[p] = key;
     }
     __syncthreads();
     const uint32_t *ck = block_merge_sort(c0, c1, N);
     uint16_t *gitems = reinterpret_cast<uint16_t *>(base + L.grid_items);
+    // cell c starts at the first sorted entry whose cell is >= c: every entry k sets the starts
+    // of the cells after its predecessor's cell up to its own
+    for (int k = tid; k < n; k += bs) {
+        const uint32_t e = ck[k];
+        gitems[k] = (uint16_t)(e & 0xFFFFu);
+        const int c = (int)(e >> 16);
+        const int cp = k > 0 ? (int)(ck[k - 1] >> 16) : -1;
+        for (int cc = cp + 1; cc <= c; ++cc) gs[cc] = (uint16_t)k;
+    }
+    const int clast = n > 0 ? (int)(ck[n - 1] >> 16) : -1;
+    for (int cc = clast + 1 + tid; cc <= kGridCells; cc += bs) gs[cc] = (uint16_t)n;
+    __syncthreads();
     uint16_t *gstart = reinterpret_cast<uint16_t *>(base + L.grid_start);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) gitems[k] = (uint16_t)(ck[k] & 0xFFFFu);
-    for (int c = threadIdx.x; c <= kGridCells; c += blockDim.x)
-        gstart[c] = (uint16_t)lower_bound_u32(ck, n, (uint32_t)c << 16);
-    if (threadIdx.x == 0) {
+    for (int c = tid; c <= kGridCells; c += bs) gstart[c] = gs[c];
+    if (tid == 0) {
         KfHeader *h = reinterpret_cast<KfHeader *>(base);
         h->n = n;
         h->cap = A.cap;
@@ -355,13 +372,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ------------------------------------------------------------------------- batch pipeline
 //
-// A batch runs as four kernels over flat work lists, so that every SM holds many independent
+// A batch runs as a few kernels over flat work lists, so that every SM holds many independent
 // warps and no CTA waits on another:
-//   join_kernel      per pair: F; each query's candidate range (binary search of its node in
-//                    the neighbour's node array, both staged by bulk copies); the neighbour's
-//                    eligibility in node order; per-target winners reset.
-//   match_kernel     warp units of 32 queries: Hamming + epipolar gate over the range,
-//                    best/second, accept, atomicMin on the target's winner.
+//   prep_kernel      per pair: F; the neighbour's eligibility in node order; per-target
+//                    winners reset.  Needs only poses and stored keyframes, so it runs beside
+//                    the ingest of the batch's new keyframes.
+//   match_kernel     warp units of 32 node-order queries: candidate ranges (the BoW join, a
+//                    warp-cooperative search of the neighbour's node array), Hamming +
+//                    epipolar gate over each range, best/second, accept, atomicMin on the
+//                    target's winner.
 //   fuse_kernel      per 256 map points (a parallel branch of the launch graph): projection
 //                    gates, grid window in the staged target, best Hamming.
 //   finalize_kernel  per pair: one match per target, rotation histogram, top-3 filter,
@@ -369,8 +388,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 //   copy_kernel      per-item regions into one dense array.
 
 // Per-target state: (dist << 16 | caller query index) of the best accepted query.
-// Per-query state: node-order candidate range lo | hi << 16 (join), accepted (target << 16 | dist)
-// or kNone (match).
+// Per-query state (node order): accepted (target << 16 | dist) or kNone.
 
 struct FuseK {
     float R[9], t[3], O[3], scale[kLevels], thr[kLevels];
@@ -474,94 +492,133 @@ __device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, FuseK 
     }
 }
 
-// ---------------------------------------------------------------- join (S1, S2)
+// ---------------------------------------------------------------- prep (S1)
 
-// One CTA per pair.
-
-__global__ void __launch_bounds__(256) join_kernel(BatchArgs A) {
-    extern __shared__ __align__(16) uint32_t jnode[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ bool ok_all;
+// One CTA per pair, independent of the keyframes entering with the batch (poses come from the
+// work item), so that it runs beside their ingest: thread 0 forms F in float64; the others reset
+// the target's winners and gather its eligibility into node order.
+__global__ void __launch_bounds__(256) prep_kernel(BatchArgs A) {
     const int tid = threadIdx.x, bs = blockDim.x;
-    const SlotLayout L = SlotLayout::make(A.cap);
     const uint32_t i = blockIdx.x;
     const WorkItem w = A.items[i];
-    const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
-    const int nQ = (int)w.nq, nT = (int)w.nt;
-    const uint32_t q16 = (uint32_t)((nQ + 15) & ~15), t16 = (uint32_t)((nT + 15) & ~15);
-    uint32_t *qn = jnode, *tn = jnode + A.sn;
     if (tid == 0) {
-        // both node arrays into shared memory with one bulk copy each
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        mbar_expect_tx(&bar, (q16 + t16) * 4);
-        if (q16) bulk_g2s(qn, Q.node, q16 * 4, &bar);
-        if (t16) bulk_g2s(tn, T.node, t16 * 4, &bar);
+        float F[9];
+        fundamental_f32(A.cam, w.pq, w.pt, F);
+        for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
     }
-    __syncthreads();
-    // meanwhile: targets' eligibility in node order, winners reset
+    const SlotLayout L = SlotLayout::make(A.cap);
+    const KfView T = KfView::at(w.t, L);
+    const int nT = (int)w.nt;
     uint32_t *win = A.win + w.t_off;
     uint8_t *tel = A.tmask_n ? A.tmask_n + w.t_off : nullptr;
     for (int j = tid; j < nT; j += bs) {
         win[j] = kNone;
         if (tel) tel[j] = w.b == kNone ? 1 : A.masks[w.b + T.orig[j]];
     }
-    if (tid == 0) {
-        float F[9];
-        fundamental_f32(A.cam, Q.hdr->Tcw, T.hdr->Tcw, F);
-        for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
+}
+
+// ---------------------------------------------------------------- match (S2, S3, S4)
+
+// Lower bound of kl and upper bound of ku in the sorted array a[0, n), found together by the
+// whole warp: each round, 32 evenly spaced pivots are compared with the key and the answer's
+// interval shrinks to one pivot gap (3 rounds for n = 2048).  Lanes agree on every value.
+__device__ __forceinline__ void warp_bounds(const uint32_t *a, int n, uint32_t kl, uint32_t ku,
+                                            int &lb, int &ub) {
+    const int lane = (int)(threadIdx.x & 31u);
+    int l0 = 0, h0 = n, l1 = 0, h1 = n;  // answers lie in [l0, h0] and [l1, h1]
+    while (l0 < h0 || l1 < h1) {
+        const int s0 = (h0 - l0 + 31) >> 5, s1 = (h1 - l1 + 31) >> 5;
+        const int x0 = l0 + lane * s0, x1 = l1 + lane * s1;
+        const bool v0 = l0 < h0 && x0 < h0, v1 = l1 < h1 && x1 < h1;
+        const uint32_t a0 = v0 ? a[x0] : 0u, a1 = v1 ? a[x1] : 0u;
+        const int c0 = __popc(__ballot_sync(kFull, v0 && a0 < kl));
+        const int c1 = __popc(__ballot_sync(kFull, v1 && a1 <= ku));
+        if (l0 < h0) {
+            const int nl = c0 > 0 ? l0 + (c0 - 1) * s0 + 1 : l0, xc = l0 + c0 * s0;
+            h0 = (c0 < 32 && xc < h0) ? xc : h0;
+            l0 = nl;
+            if (s0 == 1) h0 = l0;
+        }
+        if (l1 < h1) {
+            const int nl = c1 > 0 ? l1 + (c1 - 1) * s1 + 1 : l1, xc = l1 + c1 * s1;
+            h1 = (c1 < 32 && xc < h1) ? xc : h1;
+            l1 = nl;
+            if (s1 == 1) h1 = l1;
+        }
     }
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (tid == 0) ok_all = true;
-    __syncthreads();
-    if (!ok) ok_all = false;
-    __syncthreads();
-    if (!ok_all) {
-        if (tid == 0) atomicOr(&A.counters[2], kStatusTimeout);
+    lb = l0;
+    ub = l1;
+}
+
+// Each lane's candidate range [lo, hi) for its key k inside the window a[lb, ub), which holds
+// every key of the warp: chunks of 32 are loaded once and searched with shuffles; long windows
+// are searched per lane.
+__device__ __forceinline__ void lane_range(const uint32_t *a, int lb, int ub, uint32_t k, int &lo,
+                                           int &hi) {
+    const int lane = (int)(threadIdx.x & 31u);
+    lo = lb;
+    hi = lb;
+    if (ub - lb > 128) {
+        int l = lb, h = ub;
+        while (l < h) { const int m = (l + h) >> 1; if (a[m] < k) l = m + 1; else h = m; }
+        lo = l;
+        h = ub;
+        while (l < h) { const int m = (l + h) >> 1; if (a[m] <= k) l = m + 1; else h = m; }
+        hi = l;
         return;
     }
-    // candidate range of every eligible query
-    uint32_t *qr = A.qrange + w.res_off;
-    for (int p = tid; p < nQ; p += bs) {
-        uint32_t rg = 0;
-        if (w.a == kNone || A.masks[w.a + Q.orig[p]]) {
-            const uint32_t nd = qn[p];
-            const int lo = lower_bound_u32(tn, nT, nd);
-            const int hi = (lo < nT && tn[lo] == nd) ? upper_bound_u32(tn, lo, nT, nd) : lo;
-            rg = (uint32_t)lo | ((uint32_t)hi << 16);
+    for (int c = lb; c < ub; c += 32) {
+        const int m = min(32, ub - c);
+        const uint32_t t = lane < m ? a[c + lane] : 0u;
+        int x = 0, y = 0;  // entries of the chunk below k, not above k
+#pragma unroll
+        for (int st = 32; st >= 1; st >>= 1) {
+            const uint32_t tx = __shfl_sync(kFull, t, x + st - 1);
+            const uint32_t ty = __shfl_sync(kFull, t, y + st - 1);
+            if (x + st <= m && tx < k) x += st;
+            if (y + st <= m && ty <= k) y += st;
         }
-        qr[p] = rg;
+        lo += x;
+        hi += y;
     }
 }
 
-// ---------------------------------------------------------------- match (S3, S7-S9)
-
-// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  Every
-// load of a round is issued before its first use: the query's range, descriptor, position
-// and caller index together, then each candidate's eligibility, descriptor, position and
-// level together.
+// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  The warp
+// first finds every query's same-node candidate range in the neighbour's node array (the BoW
+// join); then, per round, every load is issued before its first use: the query's descriptor
+// and position, then each candidate's eligibility, descriptor, position and level together.
 template <int G>
 __device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, uint32_t &cmp) {
     const SlotLayout L = SlotLayout::make(A.cap);
     const KfView Q = KfView::at(un.q, L), T = KfView::at(un.t, L);
     const uint32_t lane = threadIdx.x & 31u, sub = lane % G;
+    const int p0 = (int)(un.group * 32u);
+    const int nloc = min(32, (int)un.nq - p0);
+    // the lane's own query of the join (the last one repeated past the end)
+    const int pj = p0 + min((int)lane, nloc - 1);
+    const uint32_t nd = Q.node[pj];
+    const uint32_t io_j = Q.orig[pj];
     float F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
+    const uint32_t el_j = un.qmask == kNone ? 1u : (uint32_t)A.masks[un.qmask + io_j];
+    int lb, ub, lo_j, hi_j;
+    warp_bounds(T.node, (int)un.nt, __shfl_sync(kFull, nd, 0), __shfl_sync(kFull, nd, nloc - 1), lb, ub);
+    lane_range(T.node, lb, ub, nd, lo_j, hi_j);
+    if (!el_j) hi_j = lo_j;  // an ineligible query has no candidates
     const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
     const bool epi = A.sp.epipolar != 0;
 #pragma unroll 1
     for (int r = 0; r < G; ++r) {
-        const int p = (int)(un.group * 32u) + r * (32 / G) + (int)(lane / G);
-        const bool in = p < (int)un.nq;
-        const int pc = in ? p : 0;  // (a valid index for the speculative loads)
-        const uint32_t rg = in ? A.qrange[un.res_off + p] : 0u;
+        const int ql = r * (32 / G) + (int)(lane / G);
+        const bool in = ql < nloc;
+        const int p = p0 + ql, pc = in ? p : p0;  // (a valid index for the speculative loads)
+        const int lo = __shfl_sync(kFull, lo_j, ql & 31), hi = __shfl_sync(kFull, hi_j, ql & 31);
+        const uint32_t io = __shfl_sync(kFull, io_j, ql & 31);
         const uint4 q0 = Q.desc[2 * pc], q1 = Q.desc[2 * pc + 1];
         const float2 xq = Q.xy[pc];
-        const uint32_t io = Q.orig[pc];
-        const int lo = (int)(rg & 0xFFFFu), hi = (int)(rg >> 16);
         uint32_t bkey = kNone, sec = 0xFFFFu;
-        if (lo < hi) {
+        if (in && lo < hi) {
             const Line l = epi_line(F, xq.x, xq.y);
             for (int j = lo + (int)sub; j < hi; j += G) {
                 const uint8_t el = tel ? tel[j] : (uint8_t)1;
@@ -980,17 +1037,13 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    ingest_kernel<<<a.n_jobs, 512, smem, s>>>(a);
+    ingest_kernel<<<a.n_jobs, kIngestThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_join(const BatchArgs &a, cudaStream_t s) {
-    const uint32_t blocks = a.n_search;
-    if (blocks == 0) return cudaSuccess;
-    const size_t smem = size_t(8) * (size_t)a.sn;  // both node arrays
-    cudaError_t e = cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    join_kernel<<<blocks, 256, smem, s>>>(a);
+cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s) {
+    if (a.n_search == 0) return cudaSuccess;
+    prep_kernel<<<a.n_search, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

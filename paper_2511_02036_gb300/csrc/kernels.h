@@ -12,9 +12,9 @@ namespace tmap {
 size_t ingest_smem_bytes(int cap);
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
 
-// Batch pipeline: join (per pair and per step), match (warp units), finalize (per pair,
-// offsets), copy (dense output).
-cudaError_t launch_join(const BatchArgs &a, cudaStream_t s);
+// Batch pipeline: prep (per pair: F, winners, target eligibility), match (warp units: join
+// and search), fuse (per 256 map points), finalize (per pair, offsets), copy (dense output).
+cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s);
 int match_ctas_per_sm(int lanes);
 cudaError_t launch_match(const BatchArgs &a, int ctas, cudaStream_t s);
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s);

@@ -105,6 +105,8 @@ enum : uint32_t { kStatusTimeout = 1u };
 struct WorkItem {
     const unsigned char *q;  // search: new keyframe slot; fuse: target keyframe slot
     const unsigned char *t;  // search: neighbour slot; fuse: unused
+    const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
+                             // keyframe entering with the batch, so that F does not wait for it)
     uint32_t kind;
     uint32_t out_off;        // first entry of this item's region in the padded output
     uint32_t a;              // search: byte offset of q mask (kNone: all free); fuse: first mp
@@ -124,8 +126,9 @@ struct Unit {
     const unsigned char *q, *t;  // slots of the pair
     uint32_t item;
     uint32_t group;              // queries 32*group ..
-    uint32_t nq;
+    uint32_t nq, nt;
     uint32_t res_off, t_off;
+    uint32_t qmask;              // byte offset of Q's eligibility mask, or kNone
     uint32_t pad;
 };
 
@@ -167,7 +170,7 @@ struct CamConst {
 
 struct Out3 { int32_t a, b, c; };
 
-// Arguments of the batch kernels (join, match, finalize, copy).
+// Arguments of the batch kernels (prep, match, fuse, finalize, copy).
 struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
     uint32_t n_items;
@@ -186,7 +189,6 @@ struct BatchArgs {
     unsigned long long *ncmp;     // [2] search, fuse comparisons
     Out3 *dense;                  // compacted output
     float *pair_F;                // [n_search][9] fundamental matrix of each pair
-    uint32_t *qrange;             // per query (node order): candidate range lo | hi << 16
     uint32_t *acc;                // per query (node order): accepted (target << 16 | dist)
     uint32_t *win;                // per target (node order): winner (dist << 16 | query)
     uint8_t *tmask_n;             // per target (node order): eligible, or null if no masks

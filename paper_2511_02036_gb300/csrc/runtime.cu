@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -398,7 +399,7 @@ void BatchBuf::release() {
     graph = nullptr;
     for (DevBuf *b : {&items, &units, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
                       &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F,
-                      &qrange, &acc, &win, &tmask_n})
+                      &acc, &win, &tmask_n})
         b->release();
     h_stage.release();
     h_out.release();
@@ -409,6 +410,11 @@ void BatchBuf::release() {
             e = nullptr;
         }
     if (fork) cudaEventDestroy(fork);
+    if (pfork) cudaEventDestroy(pfork);
+    if (pjoin) cudaEventDestroy(pjoin);
+    if (paux) cudaStreamDestroy(paux);
+    pfork = pjoin = nullptr;
+    paux = nullptr;
     if (join) cudaEventDestroy(join);
     if (aux) cudaStreamDestroy(aux);
     fork = join = nullptr;
@@ -496,6 +502,19 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             B->n_new = 0;
         }
     } rollback{c, in, &new_slots, &B};
+    // pose of a keyframe as the prep kernel reads it: from the slot header, or from the ingest
+    // job of a keyframe entering with this batch (so that prep need not wait for its ingest)
+    std::unordered_map<int, int> new_index;
+    for (size_t k = 0; k < new_slots.size(); ++k) new_index[new_slots[k]] = (int)k;
+    auto pose_of = [&](int slot) -> const double * {
+        auto it = new_index.find(slot);
+        const unsigned char *p = it != new_index.end()
+            ? reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) + sizeof(IngestJob) * (size_t)it->second +
+                  offsetof(IngestJob, Tcw)
+            : c->slots[slot].ptr + offsetof(KfHeader, Tcw);
+        return reinterpret_cast<const double *>(p);
+    };
+    B.nbr_new = false;
     std::vector<WorkItem> &items = B.h_items;
     items.clear();
     B.item_nq.clear();
@@ -532,6 +551,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             WorkItem w{};
             w.q = c->slots[qs].ptr;
             w.t = c->slots[ts].ptr;
+            w.pq = pose_of(qs);
+            w.pt = pose_of(ts);
+            B.nbr_new |= new_index.count(ts) != 0;
             w.kind = kItemSearch;
             w.out_off = pad;
             w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;
@@ -596,7 +618,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     for (uint32_t i : order) {
         const WorkItem &w = items[i];
         for (uint32_t g = 0; g * kQueryGroup < w.nq; ++g)
-            units.push_back(Unit{w.q, w.t, i, g, w.nq, w.res_off, w.t_off, 0u});
+            units.push_back(Unit{w.q, w.t, i, g, w.nq, w.nt, w.res_off, w.t_off, w.a, 0u});
     }
     B.n_units = (uint32_t)units.size();
     // fusion stage: the largest target of the batch
@@ -621,7 +643,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (e = B.pair_F.reserve(nsi * 9 * sizeof(float))) || (e = B.qrange.reserve(nres * 4)) ||
+        (e = B.pair_F.reserve(nsi * 9 * sizeof(float))) ||
         (e = B.acc.reserve(nres * 4)) || (e = B.win.reserve(ntt * 4)) ||
         (e = B.tmask_n.reserve(ntt)))
         return cuda_fail(e, "batch buffers");
@@ -672,7 +694,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.ncmp = static_cast<unsigned long long *>(B.ncmp.p);
     A.dense = static_cast<Out3 *>(B.dense.p);
     A.pair_F = static_cast<float *>(B.pair_F.p);
-    A.qrange = static_cast<uint32_t *>(B.qrange.p);
     A.acc = static_cast<uint32_t *>(B.acc.p);
     A.win = static_cast<uint32_t *>(B.win.p);
     A.tmask_n = any_mask ? static_cast<uint8_t *>(B.tmask_n.p) : nullptr;
@@ -693,7 +714,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, units.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p, pair_F.p,
-            qrange.p, acc.p, win.p, tmask_n.p};
+            acc.p, win.p, tmask_n.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -718,8 +739,8 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
                                                                                : cudaEventRecordDefault);
 }
 
-// Enqueue the fused launch (ingest of new keyframes, counter reset, persistent kernel,
-// compaction).
+// Enqueue the batch pipeline: prep beside the ingest of new keyframes, then match with the
+// fusion kernel as a parallel branch, finalize, copy.
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s) {
     cudaError_t e;
     (void)threads;  // the match kernel runs 256-thread CTAs of independent warps
@@ -731,7 +752,20 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_units + 7) / 8, (uint32_t)(per_sm * c->num_sms)));
     const bool timed = B.ev[0] != nullptr;
     if (timed && (e = record_stage(B.ev[0], s))) return cuda_fail(e, "event");
+    // prep needs the stored neighbours only: a branch beside the ingest, unless a neighbour
+    // enters with this batch
+    const bool pbranch = B.n_new > 0 && B.n_search_items > 0 && !B.nbr_new;
+    if (pbranch) {
+        if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
+                        (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
+                        (e = cudaEventCreateWithFlags(&B.pjoin, cudaEventDisableTiming))))
+            return cuda_fail(e, "prep branch");
+        if ((e = cudaEventRecord(B.pfork, s)) || (e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) ||
+            (e = launch_prep(B.args, B.paux)) || (e = cudaEventRecord(B.pjoin, B.paux)))
+            return cuda_fail(e, "prep kernel");
+    }
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
+    if (!pbranch && (e = launch_prep(B.args, s))) return cuda_fail(e, "prep kernel");
     if ((e = cudaMemsetAsync(B.counters.p, 0, 16, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
         return cuda_fail(e, "reset counters");
     // fusion runs as a parallel branch, joined before finalize (whose last CTA needs its counts)
@@ -745,7 +779,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
             (e = launch_fuse(B.args, B.aux)) || (e = cudaEventRecord(B.join, B.aux)))
             return cuda_fail(e, "fusion kernel");
     }
-    if ((e = launch_join(B.args, s))) return cuda_fail(e, "join kernel");
+    if (pbranch && (e = cudaStreamWaitEvent(s, B.pjoin, 0))) return cuda_fail(e, "prep join");
     if (timed && (e = record_stage(B.ev[1], s))) return cuda_fail(e, "event");
     if ((e = launch_match(B.args, B.ctas, s))) return cuda_fail(e, "match kernel");
     if (branch && (e = cudaStreamWaitEvent(s, B.join, 0))) return cuda_fail(e, "fusion join");
@@ -1143,7 +1177,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         }
         if (!st && (e = cudaGraphInstantiate(&P->B.graph, g, 0))) st = cuda_fail(e, "graph instantiate");
         if (g) cudaGraphDestroy(g);
-        // join and match (when there are pairs), fuse (when there are map points), finalize,
+        // prep and match (when there are pairs), fuse (when there are map points), finalize,
         // copy (when there are items), ingest (when keyframes enter with the batch)
         P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_units ? 1 : 0) +
                              (P->B.n_items > P->B.n_search_items ? 1 : 0) + 1 + (P->B.n_items ? 1 : 0) +

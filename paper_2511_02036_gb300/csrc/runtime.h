@@ -48,11 +48,12 @@ struct IngestStage {
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, units, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, offsets, ncmp, counters, dense, scratch, pair_F, qrange, acc, win, tmask_n;
+        counts, offsets, ncmp, counters, dense, scratch, pair_F, acc, win, tmask_n;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
     int n_new = 0;
+    bool nbr_new = false;          // a neighbour of some pair enters with this batch
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
@@ -67,6 +68,8 @@ struct BatchBuf {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries (plans)
     cudaStream_t aux = nullptr;          // fusion branch of the launch
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t paux = nullptr;         // prep branch (beside the ingest)
+    cudaEvent_t pfork = nullptr, pjoin = nullptr;
     std::vector<void *> pointers() const;
     void release();
 };
