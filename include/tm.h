@@ -57,9 +57,14 @@ typedef struct tm_ctx tm_ctx;
 typedef struct tm_plan tm_plan;
 typedef struct tm_server tm_server;
 
+/* Largest image side accepted (pixels).  The fusion window's grid cells are found with a
+ * fixed 0.01 px margin, which bounds the float32 rounding of the window test for images up to
+ * this size. */
+#define TM_MAX_IMAGE_SIZE 16384
+
 /* Pinhole camera shared by all keyframes of a context. */
 typedef struct {
-    int32_t width, height; /* image size in pixels                                         */
+    int32_t width, height; /* image size in pixels, 1 .. TM_MAX_IMAGE_SIZE                  */
     double fx, fy, cx, cy; /* intrinsics in pixels                                         */
 } tm_camera;
 
@@ -227,14 +232,20 @@ tm_status tm_plan_create(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
                          const tm_batch_inputs *in, const tm_search_params *sp,
                          const tm_fuse_params *fp, tm_plan **out);
 tm_status tm_plan_run(tm_plan *plan, void *stream);
+/* The same run from a second graph that also records CUDA events at the stage boundaries
+ * (each event node adds a few microseconds), for tm_plan_stage_times. */
+tm_status tm_plan_run_timed(tm_plan *plan, void *stream);
 tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
 /* Launch configuration the plan uses: threads per CTA, lanes per query, CTAs, kernels per run. */
 tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
                        int32_t *kernels_per_run);
-/* Device time of the stages of the plan's last completed run, from CUDA events recorded inside
- * its graph: ms[0] keyframe ingest, ms[1] search + fusion kernel, ms[2] compaction.  Waits
- * for the run to finish.  A stage the plan does not have reads 0. */
-tm_status tm_plan_stage_times(tm_plan *plan, float ms[3]);
+/* Device time of the stages of the plan's last run when it was a tm_plan_run_timed, from the
+ * CUDA events recorded inside its graph (all zero otherwise).  The search branch (prep ->
+ * match -> finalize) runs beside the store branch (ingest -> fusion): ms[0] ingest, ms[1]
+ * prep, ms[2] match kernel, ms[3] finalize kernel, ms[4] fusion kernel (from the later of
+ * ingest and prep), ms[5] offsets + copy after both branches.  Waits for the run to finish. */
+#define TM_PLAN_STAGES 6
+tm_status tm_plan_stage_times(tm_plan *plan, float ms[TM_PLAN_STAGES]);
 tm_status tm_plan_destroy(tm_plan *plan);
 
 /* ---------------------------------------------------------------------------- serving

@@ -390,8 +390,10 @@ class Plan:
                              ctypes.byref(fps), ctypes.byref(h)))
         self.handle = h
 
-    def run(self, stream=None):
-        check(tm_plan_run(self.handle, _stream(stream)))  # noqa: F821
+    def run(self, stream=None, timed=False):
+        """Replays the plan's graph; with timed=True the graph that also records stage events."""
+        fn = tm_plan_run_timed if timed else tm_plan_run  # noqa: F821
+        check(fn(self.handle, _stream(stream)))
 
     def results(self, stream=None):
         r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps)
@@ -405,8 +407,9 @@ class Plan:
         return dict(threads=a.value, lanes=b.value, ctas=c.value, kernels_per_run=d.value)
 
     def stage_times(self):
-        """(ingest, search + fusion, compaction) device milliseconds of the last run."""
-        ms = np.zeros(3, np.float32)
+        """(ingest, prep, match, finalize, fusion, offsets + copy) device milliseconds of the last
+        run if it was timed (run(timed=True)); zeros otherwise."""
+        ms = np.zeros(L.TM_PLAN_STAGES, np.float32)
         check(tm_plan_stage_times(self.handle, ms.ctypes.data))  # noqa: F821
         return tuple(float(x) for x in ms)
 

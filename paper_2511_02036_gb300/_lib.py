@@ -25,6 +25,8 @@ TM_ERR_BUSY = 8
 TM_MODE_FUSED = 0
 TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
+TM_MAX_IMAGE_SIZE = 16384
+TM_PLAN_STAGES = 6
 
 
 class tm_camera(ctypes.Structure):
@@ -118,6 +120,7 @@ SIGNATURES = {
     "tm_plan_create": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                                P(tm_fuse_params), P(c_p)]),
     "tm_plan_run": (c_i32, [c_p, c_p]),
+    "tm_plan_run_timed": (c_i32, [c_p, c_p]),
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
     "tm_plan_stage_times": (c_i32, [c_p, c_p]),

@@ -42,52 +42,50 @@ __device__ __forceinline__ float level_scale(int l) {
     return s;
 }
 
-// C = A*B for 3x3 float64, each entry summed over k = 0, 1, 2 in that order.
-__device__ void mat3_mul(const double *A, const double *B, double *C) {
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double s = dmul(A[r * 3 + 0], B[0 * 3 + c]);
-            s = dadd(s, dmul(A[r * 3 + 1], B[1 * 3 + c]));
-            s = dadd(s, dmul(A[r * 3 + 2], B[2 * 3 + c]));
-            C[r * 3 + c] = s;
-        }
-}
-
 // Fundamental matrix of the pair (Sec. IV-C epipolar validation): relative motion
 // R = R_Q R_T^T, t = t_Q - R t_T; F = K^-T [t]x R K^-1 in float64, products evaluated
-// ((K^-T [t]x) R) K^-1, each entry rounded to float32.  x_Q^T F x_T = 0.
-__device__ __noinline__ void fundamental_f32(const CamConst &cam, const double *Tq, const double *Tt,
-                                float *F) {
-    double Rq[9], RtT[9], tq[3], tt[3];
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            Rq[r * 3 + c] = Tq[r * 4 + c];
-            RtT[c * 3 + r] = Tt[r * 4 + c];
-        }
-        tq[r] = Tq[r * 4 + 3];
-        tt[r] = Tt[r * 4 + 3];
-    }
-    double R[9];
-    mat3_mul(Rq, RtT, R);
-    double t[3];
-    for (int r = 0; r < 3; ++r) {
-        double s = dmul(R[r * 3 + 0], tt[0]);
-        s = dadd(s, dmul(R[r * 3 + 1], tt[1]));
-        s = dadd(s, dmul(R[r * 3 + 2], tt[2]));
-        t[r] = dsub(tq[r], s);
-    }
-    const double tx[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
-    const double Kinv[9] = {__ddiv_rn(1.0, cam.fx), 0.0, __ddiv_rn(-cam.cx, cam.fx),
-                            0.0, __ddiv_rn(1.0, cam.fy), __ddiv_rn(-cam.cy, cam.fy),
-                            0.0, 0.0, 1.0};
-    double KinvT[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) KinvT[r * 3 + c] = Kinv[c * 3 + r];
-    double A[9], B[9], Fd[9];
-    mat3_mul(KinvT, tx, A);
-    mat3_mul(A, R, B);
-    mat3_mul(B, Kinv, Fd);
-    for (int k = 0; k < 9; ++k) F[k] = __double2float_rn(Fd[k]);
+// ((K^-T [t]x) R) K^-1, each entry of each 3x3 product summed over k = 0, 1, 2 in that order,
+// then rounded to float32.  x_Q^T F x_T = 0.
+// Computed by nine lanes of a warp, lane e = 3r + c holding entry (r, c) of each 3x3 product,
+// so that each lane runs ~25 float64 operations rather than one thread running ~240 (float64
+// issue is narrow on this part).  All lanes of the warp call it; lanes 0..8 write F.
+__device__ __noinline__ void fundamental_lanes(const CamConst &cam, const double *Tq, const double *Tt,
+                                               float *Fout) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int e = lane < 9 ? lane : 0, r = e / 3, c = e % 3;
+    // R = R_Q R_T^T
+    double R = dmul(Tq[r * 4 + 0], Tt[c * 4 + 0]);
+    R = dadd(R, dmul(Tq[r * 4 + 1], Tt[c * 4 + 1]));
+    R = dadd(R, dmul(Tq[r * 4 + 2], Tt[c * 4 + 2]));
+    // t = t_Q - R t_T (row r of R from lanes 3r .. 3r + 2)
+    const double Rr0 = __shfl_sync(kFull, R, 3 * r), Rr1 = __shfl_sync(kFull, R, 3 * r + 1),
+                 Rr2 = __shfl_sync(kFull, R, 3 * r + 2);
+    double s = dmul(Rr0, Tt[0 * 4 + 3]);
+    s = dadd(s, dmul(Rr1, Tt[1 * 4 + 3]));
+    s = dadd(s, dmul(Rr2, Tt[2 * 4 + 3]));
+    const double tr = dsub(Tq[r * 4 + 3], s);
+    const double t0 = __shfl_sync(kFull, tr, 0), t1 = __shfl_sync(kFull, tr, 3), t2 = __shfl_sync(kFull, tr, 6);
+    const double tx[9] = {0.0, -t2, t1, t2, 0.0, -t0, -t1, t0, 0.0};
+    const double Kinv[9] = {cam.kinv[0], 0.0, cam.kinv[1], 0.0, cam.kinv[2], cam.kinv[3], 0.0, 0.0, 1.0};
+    // A = K^-T [t]x
+    double Am = dmul(Kinv[0 * 3 + r], tx[0 * 3 + c]);
+    Am = dadd(Am, dmul(Kinv[1 * 3 + r], tx[1 * 3 + c]));
+    Am = dadd(Am, dmul(Kinv[2 * 3 + r], tx[2 * 3 + c]));
+    // B = A R
+    const double Ar0 = __shfl_sync(kFull, Am, 3 * r), Ar1 = __shfl_sync(kFull, Am, 3 * r + 1),
+                 Ar2 = __shfl_sync(kFull, Am, 3 * r + 2);
+    const double R0c = __shfl_sync(kFull, R, c), R1c = __shfl_sync(kFull, R, 3 + c),
+                 R2c = __shfl_sync(kFull, R, 6 + c);
+    double B = dmul(Ar0, R0c);
+    B = dadd(B, dmul(Ar1, R1c));
+    B = dadd(B, dmul(Ar2, R2c));
+    // F = B K^-1
+    const double Br0 = __shfl_sync(kFull, B, 3 * r), Br1 = __shfl_sync(kFull, B, 3 * r + 1),
+                 Br2 = __shfl_sync(kFull, B, 3 * r + 2);
+    double F = dmul(Br0, Kinv[0 * 3 + c]);
+    F = dadd(F, dmul(Br1, Kinv[1 * 3 + c]));
+    F = dadd(F, dmul(Br2, Kinv[2 * 3 + c]));
+    if (lane < 9) Fout[lane] = __double2float_rn(F);
 }
 
 // Epipolar line of a query in the target image: l = F^T x_Q = (a, b, c).
@@ -170,6 +168,32 @@ __device__ __forceinline__ uint32_t block_scan_flag(bool flag, uint32_t *wtot, u
     return base + pre;
 }
 
+// Exclusive prefix sum of one value per thread over the block (thread order), and the block
+// total.  Every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_scan_add(uint32_t x, uint32_t *wtot, uint32_t &total) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t v = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, v, o);
+        if ((int)lane >= o) v += y;
+    }
+    if (lane == 31) wtot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nw ? wtot[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, t, o);
+            if ((int)lane >= o) t += y;
+        }
+        if (lane < nw) wtot[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t r = v - x + (warp ? wtot[warp - 1] : 0u);
+    total = wtot[nw - 1];
+    __syncthreads();
+    return r;
+}
+
 // Top-3 rotation bins as a bit mask (ties to the lower bin, empty bins never taken,
 // 2nd/3rd dropped when 10*count < count of the 1st).
 __device__ uint32_t top3_mask(const uint32_t *hist) {
@@ -201,6 +225,7 @@ __device__ __forceinline__ uint32_t pack_res(uint32_t t, uint32_t d, uint32_t bi
 
 constexpr int kSortE = 2;            // keys per thread-chunk of the block merge sort
 constexpr int kIngestThreads = 1024;
+constexpr int kCellSortMax = 64;     // largest bucket or cell sorted in place (insertion sort)
 
 // Sorts N unique keys in shared memory (N a power of two >= kSortE): every chunk of kSortE
 // keys is sorted in registers, then runs are merged pairwise (merge path: each chunk of the
@@ -246,75 +271,163 @@ __device__ K *block_merge_sort(K *a, K *b, int N) {
     return src;
 }
 
-// One CTA per keyframe entering the store (Sec. IV-B): stable order by BoW node (key
-// node << 32 | caller index); gather of every keypoint array into that order, forming each
-// keypoint's projection-grid key (cell << 16 | node-order position) on the way; sort of the
-// grid keys; cell starts by one pass over the sorted keys.
-__global__ void __launch_bounds__(kIngestThreads) ingest_kernel(IngestArgs A) {
-    extern __shared__ __align__(16) unsigned long long skeys[];
+// Stored node key: a bijection of the 32-bit BoW node id (multiplication by an odd constant,
+// then xor of the high half into the low half), so that equal keys are equal nodes and the top
+// bits spread any id range evenly over the buckets.
+__device__ __forceinline__ uint32_t node_key(uint32_t node) {
+    const uint32_t y = node * 0x9E3779B1u;
+    return y ^ (y >> 16);
+}
+
+// Stable counting sort of n small keys key(i) < nb (i = 0 .. n-1) into out[0, n) (the items
+// i in key order, i ascending within a key), with start[k] = first output of key k (k <= nb).
+// counts: nb words of shared memory.  Returns the largest count; each bucket is then ordered
+// by the caller's rule (insertion sort) when that count is small.  All threads call it.
+template <typename KeyF>
+__device__ uint32_t block_count_place(int n, int nb, KeyF key, uint32_t *counts, uint16_t *start,
+                                      uint16_t *out, uint32_t *wtot, uint32_t *s_max) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int k = tid; k < nb; k += bs) counts[k] = 0u;
+    if (tid == 0) *s_max = 0u;
+    __syncthreads();
+    for (int i = tid; i < n; i += bs) atomicAdd(&counts[key(i)], 1u);
+    __syncthreads();
+    const int per = (nb + bs - 1) / bs, cb = min(tid * per, nb), ce = min(cb + per, nb);
+    uint32_t sum = 0, mx = 0;
+    for (int k = cb; k < ce; ++k) { sum += counts[k]; mx = max(mx, counts[k]); }
+    uint32_t total;
+    uint32_t run = block_scan_add(sum, wtot, total);
+    for (int k = cb; k < ce; ++k) {
+        const uint32_t c = counts[k];
+        start[k] = (uint16_t)run;
+        counts[k] = run;  // placement cursor
+        run += c;
+    }
+    if (tid == 0) start[nb] = (uint16_t)n;
+    mx = __reduce_max_sync(kFull, mx);
+    if ((tid & 31) == 0) atomicMax(s_max, mx);
+    __syncthreads();
+    for (int i = tid; i < n; i += bs) out[atomicAdd(&counts[key(i)], 1u)] = (uint16_t)i;
+    __syncthreads();
+    return *s_max;
+}
+
+// Puts every segment [start[k], start[k+1]) of v in ascending order of less(.,.) (insertion
+// sort, one thread per segment).  All threads call it.
+template <typename Less>
+__device__ void block_sort_segments(uint16_t *v, const uint16_t *start, int nb, Less less) {
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const int b = start[k], e = start[k + 1];
+        for (int i = b + 1; i < e; ++i) {
+            const uint16_t x = v[i];
+            int j = i - 1;
+            while (j >= b && less(x, v[j])) { v[j + 1] = v[j]; --j; }
+            v[j + 1] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Dynamic shared memory of the ingest kernel for a slot capacity (N = power of two >= cap):
+// kbuf 16N bytes (the fallback merge sorts; otherwise node keys, cells, cell lists) and the
+// node order 2N bytes.
+__host__ __device__ constexpr size_t ingest_pow2(int cap) {
+    size_t N = kSortE;
+    while (N < (size_t)cap) N <<= 1;
+    return N;
+}
+
+// One CTA per keyframe entering the store (Sec. IV-B).  Keypoints are put in node-key order
+// (stable: caller order within a node) by a counting sort over the key's top 12 bits and an
+// insertion sort inside each bucket; every keypoint array is gathered into that order while
+// each keypoint's projection-grid cell is taken; the grid's cell lists come from a second
+// counting sort (node order inside each cell).  A bucket or cell with more than kCellSortMax
+// keypoints switches that sort to a merge sort of (key, position) pairs.  40 registers a
+// thread: a 1024-thread CTA leaves a third of the register file to the prep CTAs beside it.
+__global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
+    extern __shared__ __align__(16) unsigned char ism[];
+    __shared__ uint32_t counts[kBuckets];
+    __shared__ uint16_t bstart[kBuckets + 1];
     __shared__ uint16_t gs[kGridCells + 1];
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t s_max;
     const IngestJob &job = A.jobs[blockIdx.x];
     const int n = job.n;
     const int tid = threadIdx.x, bs = blockDim.x;
     int N = kSortE;
     while (N < n) N <<= 1;
+    const int NC = (int)ingest_pow2(A.cap);  // carve by capacity (same offsets for every CTA)
+    unsigned long long *k0 = reinterpret_cast<unsigned long long *>(ism);
+    unsigned long long *k1 = k0 + N;
+    uint32_t *skey = reinterpret_cast<uint32_t *>(ism + 8 * (size_t)NC);   // inside k1's region
+    uint16_t *ord = reinterpret_cast<uint16_t *>(ism + 16 * (size_t)NC);
     const SlotLayout L = SlotLayout::make(A.cap);
     unsigned char *base = job.slot;
-    unsigned long long *k0 = skeys, *k1 = skeys + N;
-    // padding keys are distinct and above every real key
-    for (int i = tid; i < N; i += bs)
-        k0[i] = i < n ? ((unsigned long long)A.node[job.src + i] << 32) | (unsigned)i
-                      : ~0ull - (unsigned long long)i;
+    // node keys in caller order
+    for (int i = tid; i < n; i += bs) skey[i] = node_key(A.node[job.src + i]);
     __syncthreads();
-    const unsigned long long *sorted = block_merge_sort(k0, k1, N);
-    // the other buffer holds the two grid-key buffers of N 32-bit keys each
-    uint32_t *c0 = reinterpret_cast<uint32_t *>(sorted == k0 ? k1 : k0), *c1 = c0 + N;
+    const uint32_t bmax = block_count_place(
+        n, kBuckets, [&](int i) { return (int)(skey[i] >> (32 - kBucketBits)); }, counts, bstart, ord,
+        wtot, &s_max);
+    if (bmax <= (uint32_t)kCellSortMax) {
+        block_sort_segments(ord, bstart, kBuckets, [&](uint16_t x, uint16_t y) {
+            return skey[x] < skey[y] || (skey[x] == skey[y] && x < y);
+        });
+    } else {
+        for (int i = tid; i < N; i += bs)
+            k0[i] = i < n ? ((unsigned long long)skey[i] << 32) | (unsigned)i : ~0ull - (unsigned long long)i;
+        __syncthreads();
+        const unsigned long long *sorted = block_merge_sort(k0, k1, N);
+        for (int p = tid; p < n; p += bs) ord[p] = (uint16_t)(sorted[p] & 0xFFFFu);
+        __syncthreads();
+    }
+    // gather into node order; each keypoint's cell.  kbuf now holds: c0 [N] u32 | c1 [N] u32
+    // (fallback grid sort), pcell [N] u16 and glist [N] u16 after them.
+    uint32_t *c0 = reinterpret_cast<uint32_t *>(ism), *c1 = c0 + N;
+    uint16_t *pcell = reinterpret_cast<uint16_t *>(ism + 8 * (size_t)NC);
+    uint16_t *glist = pcell + NC;
     uint4 *desc = reinterpret_cast<uint4 *>(base + L.desc);
     float2 *xy = reinterpret_cast<float2 *>(base + L.xy);
     float *angle = reinterpret_cast<float *>(base + L.angle);
     uint32_t *node = reinterpret_cast<uint32_t *>(base + L.node);
     uint16_t *orig = reinterpret_cast<uint16_t *>(base + L.orig);
     uint8_t *level = base + L.level;
-    for (int p = tid; p < N; p += bs) {
-        uint32_t key = 0xFFFFFFFFu - (uint32_t)p;  // padding: above every real key
-        if (p < n) {
-            const uint32_t o = (uint32_t)(sorted[p] & 0xFFFFFFFFull);
-            const uint32_t s = job.src + o;
-            const uint4 d0 = A.desc[2 * s], d1 = A.desc[2 * s + 1];
-            const float2 v = A.xy[s];
-            const float an = A.angle[s];
-            const uint32_t nd = A.node[s];
-            const uint8_t lv = A.level[s];
-            desc[2 * p] = d0;
-            desc[2 * p + 1] = d1;
-            xy[p] = v;
-            angle[p] = an;
-            node[p] = nd;
-            orig[p] = (uint16_t)o;
-            level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
-            const int cx = grid_cell(v.x, A.cell_w_inv, kGridCols);
-            const int cy = grid_cell(v.y, A.cell_h_inv, kGridRows);
-            key = ((uint32_t)(cy * kGridCols + cx) << 16) | (uint32_t)p;
-        }
-        c0[p] = key;
+    for (int p = tid; p < n; p += bs) {
+        const uint32_t o = ord[p];
+        const uint32_t s = job.src + o;
+        const uint4 d0 = A.desc[2 * s], d1 = A.desc[2 * s + 1];
+        const float2 v = A.xy[s];
+        const float an = A.angle[s];
+        const uint32_t nd = A.node[s];
+        const uint8_t lv = A.level[s];
+        desc[2 * p] = d0;
+        desc[2 * p + 1] = d1;
+        xy[p] = v;
+        angle[p] = an;
+        node[p] = node_key(nd);
+        orig[p] = (uint16_t)o;
+        level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
+        pcell[p] = (uint16_t)(grid_cell(v.y, A.cell_h_inv, kGridRows) * kGridCols +
+                              grid_cell(v.x, A.cell_w_inv, kGridCols));
     }
     __syncthreads();
-    const uint32_t *ck = block_merge_sort(c0, c1, N);
+    const uint32_t cmax = block_count_place(
+        n, kGridCells, [&](int p) { return (int)pcell[p]; }, counts, gs, glist, wtot, &s_max);
     uint16_t *gitems = reinterpret_cast<uint16_t *>(base + L.grid_items);
-    // cell c starts at the first sorted entry whose cell is >= c: every entry k sets the starts
-    // of the cells after its predecessor's cell up to its own
-    for (int k = tid; k < n; k += bs) {
-        const uint32_t e = ck[k];
-        gitems[k] = (uint16_t)(e & 0xFFFFu);
-        const int c = (int)(e >> 16);
-        const int cp = k > 0 ? (int)(ck[k - 1] >> 16) : -1;
-        for (int cc = cp + 1; cc <= c; ++cc) gs[cc] = (uint16_t)k;
+    if (cmax <= (uint32_t)kCellSortMax) {
+        block_sort_segments(glist, gs, kGridCells, [](uint16_t x, uint16_t y) { return x < y; });
+        for (int k = tid; k < n; k += bs) gitems[k] = glist[k];
+    } else {
+        for (int p = tid; p < N; p += bs)
+            c0[p] = p < n ? ((uint32_t)pcell[p] << 16) | (uint32_t)p : 0xFFFFFFFFu - (uint32_t)p;
+        __syncthreads();
+        const uint32_t *ck = block_merge_sort(c0, c1, N);
+        for (int k = tid; k < n; k += bs) gitems[k] = (uint16_t)(ck[k] & 0xFFFFu);
     }
-    const int clast = n > 0 ? (int)(ck[n - 1] >> 16) : -1;
-    for (int cc = clast + 1 + tid; cc <= kGridCells; cc += bs) gs[cc] = (uint16_t)n;
-    __syncthreads();
     uint16_t *gstart = reinterpret_cast<uint16_t *>(base + L.grid_start);
     for (int c = tid; c <= kGridCells; c += bs) gstart[c] = gs[c];
+    uint16_t *bst = reinterpret_cast<uint16_t *>(base + L.bstart);
+    for (int b = tid; b <= kBuckets; b += bs) bst[b] = bstart[b];
     if (tid == 0) {
         KfHeader *h = reinterpret_cast<KfHeader *>(base);
         h->n = n;
@@ -446,13 +559,16 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
     for (int l = 0; l < kLevels; ++l)
         if (fmul(dist, K.scale[l]) >= maxd) { pl = l; break; }
     const float r = fmul(fp.radius_scale, K.scale[pl]);
-    const int cx0 = grid_cell(fsub(u, r), cam.cell_w_inv, kGridCols) - 1;
-    const int cx1 = grid_cell(fadd(u, r), cam.cell_w_inv, kGridCols) + 1;
-    const int cy0 = grid_cell(fsub(v, r), cam.cell_h_inv, kGridRows) - 1;
-    const int cy1 = grid_cell(fadd(v, r), cam.cell_h_inv, kGridRows) + 1;
+    // cells of the window: a keypoint passing |x - u| < r in float32 lies within r + 1e-6 px of
+    // u, so edges moved out by 0.01 px bound every such keypoint, and the cell of an edge bounds
+    // the cell of the keypoint (rounding and floor are monotone)
+    const int cx0 = grid_cell(fsub(fsub(u, r), 0.01f), cam.cell_w_inv, kGridCols);
+    const int cx1 = grid_cell(fadd(fadd(u, r), 0.01f), cam.cell_w_inv, kGridCols);
+    const int cy0 = grid_cell(fsub(fsub(v, r), 0.01f), cam.cell_h_inv, kGridRows);
+    const int cy1 = grid_cell(fadd(fadd(v, r), 0.01f), cam.cell_h_inv, kGridRows);
     uint32_t best = kNone;  // (dist << 16) | caller keypoint index
-    for (int cy = max(cy0, 0); cy <= min(cy1, kGridRows - 1); ++cy) {
-        const int c0 = cy * kGridCols + max(cx0, 0), c1 = cy * kGridCols + min(cx1, kGridCols - 1);
+    for (int cy = cy0; cy <= cy1; ++cy) {
+        const int c0 = cy * kGridCols + cx0, c1 = cy * kGridCols + cx1;
         const int k0 = T.grid_start[c0], k1 = T.grid_start[c1 + 1];
         for (int k = k0; k < k1; ++k) {
             const int j = T.grid_items[k];
@@ -494,118 +610,64 @@ __device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, FuseK 
 
 // ---------------------------------------------------------------- prep (S1)
 
+constexpr int kPrepThreads = 128;
+
 // One CTA per pair, independent of the keyframes entering with the batch (poses come from the
-// work item), so that it runs beside their ingest: thread 0 forms F in float64; the others reset
-// the target's winners and gather its eligibility into node order.
-__global__ void __launch_bounds__(256) prep_kernel(BatchArgs A) {
+// work item), so that it runs beside their ingest: warp 0 forms F (nine lanes); all threads
+// reset the target's winners and gather its eligibility into node order.  CTA 0 also zeroes
+// the batch's counters (comparisons, status), which every later kernel of the batch updates.
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(BatchArgs A) {
     const int tid = threadIdx.x, bs = blockDim.x;
     const uint32_t i = blockIdx.x;
-    const WorkItem w = A.items[i];
-    if (tid == 0) {
-        float F[9];
-        fundamental_f32(A.cam, w.pq, w.pt, F);
-        for (int k = 0; k < 9; ++k) A.pair_F[9 * (size_t)i + k] = F[k];
+    if (i == 0 && tid < 4) {
+        A.counters[tid] = 0u;
+        if (tid < 2) A.ncmp[tid] = 0ull;
     }
-    const SlotLayout L = SlotLayout::make(A.cap);
+    if (i >= A.n_search) return;
+    const WorkItem w = A.items[i];
+    const SlotLayout &L = A.L;
     const KfView T = KfView::at(w.t, L);
     const int nT = (int)w.nt;
+    if (tid < 32) fundamental_lanes(A.cam, w.pq, w.pt, A.pair_F + 9 * (size_t)i);
     uint32_t *win = A.win + w.t_off;
     uint8_t *tel = A.tmask_n ? A.tmask_n + w.t_off : nullptr;
-    for (int j = tid; j < nT; j += bs) {
-        win[j] = kNone;
-        if (tel) tel[j] = w.b == kNone ? 1 : A.masks[w.b + T.orig[j]];
+    constexpr int U = 8;  // targets per thread and pass: all their loads in flight together
+    for (int j0 = 0; j0 < nT; j0 += U * bs) {
+        uint32_t o[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int j = j0 + k * bs + tid;
+            o[k] = (tel && w.b != kNone && j < nT) ? T.orig[j] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int j = j0 + k * bs + tid;
+            if (j < nT) {
+                win[j] = kNone;
+                if (tel) tel[j] = w.b == kNone ? 1 : A.masks[w.b + o[k]];
+            }
+        }
     }
 }
 
 // ---------------------------------------------------------------- match (S2, S3, S4)
 
-// Lower bound of kl and upper bound of ku in the sorted array a[0, n), found together by the
-// whole warp: each round, 32 evenly spaced pivots are compared with the key and the answer's
-// interval shrinks to one pivot gap (3 rounds for n = 2048).  Lanes agree on every value.
-__device__ __forceinline__ void warp_bounds(const uint32_t *a, int n, uint32_t kl, uint32_t ku,
-                                            int &lb, int &ub) {
-    const int lane = (int)(threadIdx.x & 31u);
-    int l0 = 0, h0 = n, l1 = 0, h1 = n;  // answers lie in [l0, h0] and [l1, h1]
-    while (l0 < h0 || l1 < h1) {
-        const int s0 = (h0 - l0 + 31) >> 5, s1 = (h1 - l1 + 31) >> 5;
-        const int x0 = l0 + lane * s0, x1 = l1 + lane * s1;
-        const bool v0 = l0 < h0 && x0 < h0, v1 = l1 < h1 && x1 < h1;
-        const uint32_t a0 = v0 ? a[x0] : 0u, a1 = v1 ? a[x1] : 0u;
-        const int c0 = __popc(__ballot_sync(kFull, v0 && a0 < kl));
-        const int c1 = __popc(__ballot_sync(kFull, v1 && a1 <= ku));
-        if (l0 < h0) {
-            const int nl = c0 > 0 ? l0 + (c0 - 1) * s0 + 1 : l0, xc = l0 + c0 * s0;
-            h0 = (c0 < 32 && xc < h0) ? xc : h0;
-            l0 = nl;
-            if (s0 == 1) h0 = l0;
-        }
-        if (l1 < h1) {
-            const int nl = c1 > 0 ? l1 + (c1 - 1) * s1 + 1 : l1, xc = l1 + c1 * s1;
-            h1 = (c1 < 32 && xc < h1) ? xc : h1;
-            l1 = nl;
-            if (s1 == 1) h1 = l1;
-        }
-    }
-    lb = l0;
-    ub = l1;
-}
-
-// Each lane's candidate range [lo, hi) for its key k inside the window a[lb, ub), which holds
-// every key of the warp: chunks of 32 are loaded once and searched with shuffles; long windows
-// are searched per lane.
-__device__ __forceinline__ void lane_range(const uint32_t *a, int lb, int ub, uint32_t k, int &lo,
-                                           int &hi) {
-    const int lane = (int)(threadIdx.x & 31u);
-    lo = lb;
-    hi = lb;
-    if (ub - lb > 128) {
-        int l = lb, h = ub;
-        while (l < h) { const int m = (l + h) >> 1; if (a[m] < k) l = m + 1; else h = m; }
-        lo = l;
-        h = ub;
-        while (l < h) { const int m = (l + h) >> 1; if (a[m] <= k) l = m + 1; else h = m; }
-        hi = l;
-        return;
-    }
-    for (int c = lb; c < ub; c += 32) {
-        const int m = min(32, ub - c);
-        const uint32_t t = lane < m ? a[c + lane] : 0u;
-        int x = 0, y = 0;  // entries of the chunk below k, not above k
-#pragma unroll
-        for (int st = 32; st >= 1; st >>= 1) {
-            const uint32_t tx = __shfl_sync(kFull, t, x + st - 1);
-            const uint32_t ty = __shfl_sync(kFull, t, y + st - 1);
-            if (x + st <= m && tx < k) x += st;
-            if (y + st <= m && ty <= k) y += st;
-        }
-        lo += x;
-        hi += y;
-    }
-}
-
-// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  The warp
-// first finds every query's same-node candidate range in the neighbour's node array (the BoW
-// join); then, per round, every load is issued before its first use: the query's descriptor
-// and position, then each candidate's eligibility, descriptor, position and level together.
+// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  The BoW
+// join is a lookup in the neighbour's node index: a query's same-node candidates are the
+// positions of its key's bucket whose key equals its own.  Every load of a round is issued
+// before its first use: the query's bucket bounds, descriptor and position together, then
+// each candidate's key, eligibility, descriptor, position and level together.
 template <int G>
-__device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, uint32_t &cmp) {
-    const SlotLayout L = SlotLayout::make(A.cap);
-    const KfView Q = KfView::at(un.q, L), T = KfView::at(un.t, L);
+__device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, const float *thr,
+                                            uint32_t &cmp) {
+    const SlotLayout &L = A.L;
+    const KfView T = KfView::at(un.t, L);
     const uint32_t lane = threadIdx.x & 31u, sub = lane % G;
     const int p0 = (int)(un.group * 32u);
     const int nloc = min(32, (int)un.nq - p0);
-    // the lane's own query of the join (the last one repeated past the end)
-    const int pj = p0 + min((int)lane, nloc - 1);
-    const uint32_t nd = Q.node[pj];
-    const uint32_t io_j = Q.orig[pj];
     float F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
-    const uint32_t el_j = un.qmask == kNone ? 1u : (uint32_t)A.masks[un.qmask + io_j];
-    int lb, ub, lo_j, hi_j;
-    warp_bounds(T.node, (int)un.nt, __shfl_sync(kFull, nd, 0), __shfl_sync(kFull, nd, nloc - 1), lb, ub);
-    lane_range(T.node, lb, ub, nd, lo_j, hi_j);
-    if (!el_j) hi_j = lo_j;  // an ineligible query has no candidates
     const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
     const bool epi = A.sp.epipolar != 0;
 #pragma unroll 1
@@ -613,27 +675,29 @@ __device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, 
         const int ql = r * (32 / G) + (int)(lane / G);
         const bool in = ql < nloc;
         const int p = p0 + ql, pc = in ? p : p0;  // (a valid index for the speculative loads)
-        const int lo = __shfl_sync(kFull, lo_j, ql & 31), hi = __shfl_sync(kFull, hi_j, ql & 31);
-        const uint32_t io = __shfl_sync(kFull, io_j, ql & 31);
-        const uint4 q0 = Q.desc[2 * pc], q1 = Q.desc[2 * pc + 1];
-        const float2 xq = Q.xy[pc];
+        const uint32_t nk = un.qnode[pc];
+        const uint32_t key = un.qraw ? node_key(nk) : nk;
+        const uint32_t io = un.qorig ? (uint32_t)un.qorig[pc] : (uint32_t)pc;
+        const uint32_t b = key >> (32 - kBucketBits);
+        const int bs = T.bstart[b], be = T.bstart[b + 1];
+        const uint4 q0 = un.qdesc[2 * pc], q1 = un.qdesc[2 * pc + 1];
+        const float2 xq = un.qxy[pc];
+        const bool el = un.qmask == kNone || A.masks[un.qmask + io];
         uint32_t bkey = kNone, sec = 0xFFFFu;
-        if (in && lo < hi) {
+        if (in && el && bs < be) {
             const Line l = epi_line(F, xq.x, xq.y);
-            for (int j = lo + (int)sub; j < hi; j += G) {
-                const uint8_t el = tel ? tel[j] : (uint8_t)1;
+            for (int j = bs + (int)sub; j < be; j += G) {
+                const uint32_t tk = T.node[j];
+                const uint8_t te = tel ? tel[j] : (uint8_t)1;
                 const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
                 const float2 xt = T.xy[j];
                 const int lv = T.level[j];
-                if (!el) continue;
+                if (tk != key || !te) continue;
                 ++cmp;
                 const uint32_t d = (uint32_t)hamming(q0, q1, t0, t1);
-                if (epi) {
-                    const float s = level_scale(lv);
-                    if (!epi_pass(l, xt.x, xt.y, fmul(A.sp.epi_chi2, fmul(s, s)))) continue;
-                }
-                const uint32_t key = (d << 16) | (uint32_t)j;
-                if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
+                if (epi && !epi_pass(l, xt.x, xt.y, thr[lv])) continue;
+                const uint32_t k2 = (d << 16) | (uint32_t)j;
+                if (k2 < bkey) { sec = min(sec, bkey >> 16); bkey = k2; }
                 else sec = min(sec, d);
             }
         }
@@ -662,14 +726,140 @@ __device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, 
     }
 }
 
+// Merge of two partial (best key, second distance) states of one query: the two smallest
+// candidates of the union.  Associative and commutative; identity (kNone, 0xFFFF).
+__device__ __forceinline__ void merge_best2(uint32_t &b, uint32_t &s, uint32_t ob, uint32_t os) {
+    s = min(min(s, os), max(b, ob) >> 16);
+    b = min(b, ob);
+}
+
+// 32 node-order queries of one pair, their candidates spread evenly over the lanes.  Each lane
+// first finds its query's bucket in the neighbour's node index; the (query, candidate) entries
+// of all 32 queries are then numbered by a warp prefix sum over the bucket sizes and taken 32
+// per round, lane k handling entry k of the round (its query found by a search over the prefix
+// sums, its key and epipolar line taken from the owner lane by shuffles, its descriptor loaded
+// together with the candidate's arrays).
+// A round's entries of one query sit in adjacent lanes: a segmented shuffle reduction merges
+// them and the segment's first lane folds the result into the query's state in shared memory.
+// The warp thus waits ~ceil(sum / 32) load rounds instead of the largest bucket.
+__device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit &un, const float *thr,
+                                                 uint2 *st, uint32_t &cmp) {
+    const SlotLayout &L = A.L;
+    const KfView T = KfView::at(un.t, L);
+    const int lane = (int)(threadIdx.x & 31u);
+    const int p0 = (int)(un.group * 32u);
+    const int nloc = min(32, (int)un.nq - p0);
+    const bool in = lane < nloc;
+    const int p = p0 + (in ? lane : 0);
+    const uint32_t nk = un.qnode[p];
+    const uint32_t key = un.qraw ? node_key(nk) : nk;
+    const uint32_t io = un.qorig ? (uint32_t)un.qorig[p] : (uint32_t)p;
+    const float2 xq = un.qxy[p];
+    float F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
+    const uint32_t b = key >> (32 - kBucketBits);
+    const int bs = T.bstart[b], be = T.bstart[b + 1];
+    const bool el = un.qmask == kNone || A.masks[un.qmask + io];
+    const Line l = epi_line(F, xq.x, xq.y);
+    // entries of this lane's query, numbered across the warp
+    const int c = (in && el) ? be - bs : 0;
+    int off = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, off, o);
+        if (lane >= o) off += y;
+    }
+    const int total = __shfl_sync(kFull, off, 31);
+    off -= c;  // exclusive
+    st[lane] = make_uint2(kNone, 0xFFFFu);
+    __syncwarp();
+    const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
+    const bool epi = A.sp.epipolar != 0;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        // owner: the last query whose first entry is <= k (it has entries, as k < total)
+        int i = 0;
+#pragma unroll
+        for (int s2 = 16; s2 >= 1; s2 >>= 1) {
+            const int oi = __shfl_sync(kFull, off, (i + s2) & 31);
+            if (i + s2 < 32 && oi <= k) i += s2;
+        }
+        const int j0 = __shfl_sync(kFull, bs, i) + (k - __shfl_sync(kFull, off, i));
+        const uint32_t ky = __shfl_sync(kFull, key, i);
+        Line li;
+        li.a = __shfl_sync(kFull, l.a, i); li.b = __shfl_sync(kFull, l.b, i); li.c = __shfl_sync(kFull, l.c, i);
+        const bool valid = k < total;
+        const int j = valid ? j0 : 0;            // (valid indices for the speculative loads:
+        const int pq = p0 + (valid ? i : 0);     //  past the last entry, i may name no query)
+        const uint4 a0 = un.qdesc[2 * pq], a1 = un.qdesc[2 * pq + 1];
+        const uint32_t tk = T.node[j];
+        const uint8_t te = tel ? tel[j] : (uint8_t)1;
+        const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
+        const float2 xt = T.xy[j];
+        const int lv = T.level[j];
+        uint32_t bk = kNone, sc = 0xFFFFu;
+        if (valid && tk == ky && te) {
+            ++cmp;
+            const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
+            if (!epi || epi_pass(li, xt.x, xt.y, thr[lv])) bk = (d << 16) | (uint32_t)j;
+        }
+        // segmented merge over the lanes of each query (suffix within the segment)
+#pragma unroll
+        for (int s2 = 1; s2 < 32; s2 <<= 1) {
+            const uint32_t ob = __shfl_down_sync(kFull, bk, s2);
+            const uint32_t os = __shfl_down_sync(kFull, sc, s2);
+            const int oi = __shfl_down_sync(kFull, i, s2);
+            if (lane + s2 < 32 && oi == i) merge_best2(bk, sc, ob, os);
+        }
+        const int prev = __shfl_up_sync(kFull, i, 1);
+        if (valid && (lane == 0 || prev != i)) {
+            uint2 v = st[i];
+            merge_best2(v.x, v.y, bk, sc);
+            st[i] = v;
+        }
+        __syncwarp();
+    }
+    if (in) {
+        const uint2 v = st[lane];
+        uint32_t acc = kNone;
+        if (v.x != kNone) {
+            const uint32_t best = v.x >> 16;
+            bool ok = (int)best <= A.sp.hamming_max;
+            if (ok && A.sp.ratio_num != 0 && v.y != 0xFFFFu)
+                ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * v.y;
+            if (ok) {
+                const uint32_t j = v.x & 0xFFFFu;
+                acc = (j << 16) | best;
+                if (A.sp.resolve) atomicMin(&A.win[un.t_off + j], (best << 16) | io);
+            }
+        }
+        A.acc[un.res_off + p0 + lane] = acc;
+    }
+    __syncwarp();
+}
+
 template <int G>
-__global__ void __launch_bounds__(256) match_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(256, 4) match_kernel(BatchArgs A) {
+    __shared__ float thr[kLevels];  // epipolar threshold chi2 * sigma^2 of each level
+    __shared__ uint2 qstate[8][32]; // per warp: (best key, second distance) of its 32 queries
+    if (threadIdx.x < kLevels) {
+        const float s = level_scale(threadIdx.x);
+        thr[threadIdx.x] = fmul(A.sp.epi_chi2, fmul(s, s));
+    }
+    __syncthreads();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    uint2 *st = qstate[(threadIdx.x >> 5) & 7];
     uint32_t cs = 0;
+    Unit un{};
+    if (warp < A.n_units) un = A.units[warp];
     for (uint32_t u = warp; u < A.n_units; u += warps) {
-        const Unit un = A.units[u];
-        match_group<G>(A, un, cs);
+        Unit nx{};  // the next unit's record, loaded while this one is searched
+        if (u + warps < A.n_units) nx = A.units[u + warps];
+        if (G == 1) match_group_flat(A, un, thr, st, cs);
+        else match_group<G>(A, un, thr, cs);
+        un = nx;
     }
     const uint32_t s = __reduce_add_sync(kFull, cs);
     if ((threadIdx.x & 31u) == 0 && s) atomicAdd(&A.ncmp[0], (unsigned long long)s);
@@ -692,7 +882,7 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     const uint32_t item = A.n_search + blockIdx.x;
     if (item >= A.n_items) return;
     const WorkItem w = A.items[item];
-    const SlotLayout L = SlotLayout::make(A.cap);
+    const SlotLayout &L = A.L;
     const FuseStage FS = FuseStage::make((int)A.fsn);
     const KfView Tg = KfView::at(w.q, L);
     const int nT = Tg.hdr->n;
@@ -747,42 +937,62 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
 
 // One pair per CTA: the accepted query of each target keeps it only if it is the target's
 // winner; kept matches are binned by rotation, the top-3 bins kept, the pair compacted in
-// caller query order.  The last CTA of the launch turns per-item counts into offsets.
+// caller query order.
 __global__ void __launch_bounds__(256) finalize_kernel(BatchArgs A) {
     extern __shared__ __align__(16) uint32_t fres[];  // [sn] per caller-order query
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t keep;
-    __shared__ bool s_last;
     const int tid = threadIdx.x, bs = blockDim.x;
-    if (blockIdx.x < A.n_search) {
+    {
         const uint32_t i = blockIdx.x;
         const WorkItem w = A.items[i];
-        const SlotLayout L = SlotLayout::make(A.cap);
-        const KfView Q = KfView::at(w.q, L), T = KfView::at(w.t, L);
+        const SlotLayout &L = A.L;
+        const KfView T = KfView::at(w.t, L);
         const int nQ = (int)w.nq;
         const bool rot = A.sp.rot_filter != 0;
         if (tid < 32) hist[tid] = 0;
         __syncthreads();
-        for (int p0 = 0; p0 < nQ; p0 += bs) {
-            const int p = p0 + tid;
-            uint32_t bin = kNone;
-            if (p < nQ) {
-                const uint32_t acc = A.acc[w.res_off + p], io = Q.orig[p];
-                uint32_t r = kNone;
-                if (acc != kNone) {
-                    const uint32_t j = acc >> 16, d = acc & 0xFFFFu;
-                    if (!A.sp.resolve || A.win[w.t_off + j] == ((d << 16) | io)) {
-                        bin = rot ? (uint32_t)rot_bin(Q.angle[p], T.angle[j]) : 0u;
-                        r = pack_res(T.orig[j], d, bin);
-                    }
-                }
-                fres[io] = r;
+        constexpr int U = 4;  // queries per thread and pass: all their loads in flight together
+        for (int p0 = 0; p0 < nQ; p0 += U * bs) {
+            uint32_t acc[U], io[U], wv[U], to[U];
+            float qa[U], ta[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int p = p0 + k * bs + tid;
+                acc[k] = p < nQ ? A.acc[w.res_off + p] : kNone;
+                io[k] = p < nQ ? (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p) : 0u;
             }
-            if (rot) {
-                const unsigned peers = __match_any_sync(kFull, bin);
-                if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
-                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int p = p0 + k * bs + tid;
+                const uint32_t j = acc[k] >> 16;
+                const bool a = acc[k] != kNone;
+                wv[k] = (a && A.sp.resolve) ? A.win[w.t_off + j] : 0u;
+                to[k] = a ? (uint32_t)T.orig[j] : 0u;
+                qa[k] = (a && rot) ? w.qangle[p] : 0.0f;
+                ta[k] = (a && rot) ? T.angle[j] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int p = p0 + k * bs + tid;
+                uint32_t bin = kNone;
+                if (p < nQ) {
+                    uint32_t r = kNone;
+                    if (acc[k] != kNone) {
+                        const uint32_t d = acc[k] & 0xFFFFu;
+                        if (!A.sp.resolve || wv[k] == ((d << 16) | io[k])) {
+                            bin = rot ? (uint32_t)rot_bin(qa[k], ta[k]) : 0u;
+                            r = pack_res(to[k], d, bin);
+                        }
+                    }
+                    fres[io[k]] = r;
+                }
+                if (rot) {
+                    const unsigned peers = __match_any_sync(kFull, bin);
+                    if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
+                        atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+                }
             }
         }
         __syncthreads();
@@ -803,52 +1013,43 @@ __global__ void __launch_bounds__(256) finalize_kernel(BatchArgs A) {
         }
         if (tid == 0) A.counts[i] = base;
     }
-    // the last CTA to finish turns the per-item counts into offsets (no waiting: every other
-    // CTA published its counts before its increment; fusion counts came from match_kernel)
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&A.counters[1], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    uint32_t base = 0;
-    for (uint32_t i0 = 0; i0 < A.n_items; i0 += bs) {
-        const uint32_t i = i0 + tid;
-        const uint32_t c = i < A.n_items ? __ldcg(A.counts + i) : 0u;
-        uint32_t v = c;
-        const unsigned lane = tid & 31u, warp = tid >> 5, nw = bs >> 5;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, v, o);
-            if ((int)lane >= o) v += y;
-        }
-        if (lane == 31) wtot[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t x = lane < nw ? wtot[lane] : 0u;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, x, o);
-                if ((int)lane >= o) x += y;
-            }
-            if (lane < nw) wtot[lane] = x;
-        }
-        __syncthreads();
-        const uint32_t incl = v + (warp ? wtot[warp - 1] : 0u);
-        if (i < A.n_items) A.offsets[i] = base + incl - c;
-        const uint32_t tot = wtot[nw - 1];
-        __syncthreads();
-        base += tot;
-    }
-    if (tid == 0) A.offsets[A.n_items] = base;
 }
 
-// Gathers the per-item regions into the dense output, one warp per item.
-__global__ void copy_kernel(BatchArgs A) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n_items; i += warps) {
-        const uint32_t cnt = A.counts[i], dst = A.offsets[i], src = A.items[i].out_off;
-        for (uint32_t k = lane; k < cnt; k += 32) A.dense[dst + k] = A.padded[src + k];
+// Per-item counts -> offsets, and the per-item regions gathered into the dense output.  Every
+// CTA scans the counts itself (a few thousand words, read from L2), segment by segment, so
+// that no CTA waits for another; CTA 0 publishes the offsets.  Warps copy items.
+constexpr int kCopyThreads = 1024;
+constexpr int kCopySeg = 8192;  // items per scan segment (offsets held in shared memory)
+__global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
+    __shared__ uint32_t offs[kCopySeg];
+    __shared__ uint32_t wtot[32];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const uint32_t lane = tid & 31u, wid = tid >> 5, nw = bs >> 5;
+    const uint32_t gw = blockIdx.x * nw + wid, gws = gridDim.x * nw;
+    uint32_t base = 0;
+    for (uint32_t s0 = 0; s0 < A.n_items; s0 += kCopySeg) {
+        const uint32_t ns = min((uint32_t)kCopySeg, A.n_items - s0);
+        const uint32_t per = (ns + bs - 1) / bs, cb = min(tid * per, ns), ce = min(cb + per, ns);
+        uint32_t sum = 0;
+        for (uint32_t k = cb; k < ce; ++k) sum += A.counts[s0 + k];
+        uint32_t total;
+        uint32_t run = block_scan_add(sum, wtot, total) + base;
+        for (uint32_t k = cb; k < ce; ++k) {
+            offs[k] = run;
+            run += A.counts[s0 + k];
+        }
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (uint32_t k = tid; k < ns; k += bs) A.offsets[s0 + k] = offs[k];
+        for (uint32_t k = gw; k < ns; k += gws) {
+            const uint32_t i = s0 + k;
+            const uint32_t cnt = A.counts[i], dst = offs[k], src = A.items[i].out_off;
+            for (uint32_t e = lane; e < cnt; e += 32) A.dense[dst + e] = A.padded[src + e];
+        }
+        base += total;
+        __syncthreads();
     }
+    if (blockIdx.x == 0 && tid == 0) A.offsets[A.n_items] = base;
 }
 
 // ------------------------------------------------------------------------- plain form
@@ -865,10 +1066,8 @@ __global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *
     const SlotLayout L = SlotLayout::make(cap);
     const KfView Q = KfView::at(qs, L), T = KfView::at(ts, L);
     const int nQ = Q.hdr->n, nT = T.hdr->n;
-    if (threadIdx.x == 0) {
-        fundamental_f32(cam, Q.hdr->Tcw, T.hdr->Tcw, F);
-        s_cmp = 0ull;
-    }
+    if (threadIdx.x < 32) fundamental_lanes(cam, Q.hdr->Tcw, T.hdr->Tcw, F);
+    if (threadIdx.x == 0) s_cmp = 0ull;
     if (threadIdx.x < kLevels) {
         const float s = level_scale(threadIdx.x);
         thr[threadIdx.x] = fmul(sp.epi_chi2, fmul(s, s));
@@ -1025,11 +1224,7 @@ __global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uin
 
 // ------------------------------------------------------------------------- launchers
 
-size_t ingest_smem_bytes(int cap) {
-    size_t N = kSortE;
-    while (N < (size_t)cap) N <<= 1;
-    return 2 * N * sizeof(unsigned long long);  // two merge buffers
-}
+size_t ingest_smem_bytes(int cap) { return 18 * ingest_pow2(cap); }
 
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
     if (a.n_jobs <= 0) return cudaSuccess;
@@ -1042,8 +1237,7 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s) {
-    if (a.n_search == 0) return cudaSuccess;
-    prep_kernel<<<a.n_search, 256, 0, s>>>(a);
+    prep_kernel<<<a.n_search > 0 ? a.n_search : 1, kPrepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1093,12 +1287,13 @@ cudaError_t launch_finalize(const BatchArgs &a, cudaStream_t s) {
     const size_t smem = size_t(4) * (size_t)a.sn;
     cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    finalize_kernel<<<a.n_search > 0 ? a.n_search : 1, 256, smem, s>>>(a);
+    if (a.n_search == 0) return cudaSuccess;
+    finalize_kernel<<<a.n_search, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {
-    copy_kernel<<<ctas, 256, 0, s>>>(a);
+    copy_kernel<<<ctas, kCopyThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1229,8 +1424,10 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     using namespace tmap;
     if (!cam || !q || !t || !out || !n_out)
         return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: null argument");
-    if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0) || !(cam->fy > 0))
-        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad camera");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > TM_MAX_IMAGE_SIZE ||
+        cam->height > TM_MAX_IMAGE_SIZE || !(cam->fx > 0) || !(cam->fy > 0))
+        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad camera (image sides 1..%d px, fx, fy > 0)",
+                    TM_MAX_IMAGE_SIZE);
     for (const tm_keyframe_view *v : {q, t}) {
         if (v->n < 0 || v->n > kNoAllocMaxKp)
             return fail(TM_ERR_INVALID_ARG,
@@ -1280,15 +1477,7 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     }
     noalloc_jobs_kernel<<<1, 1, 0, s>>>(jobs, jq, jt);
     if ((e = cudaGetLastError())) return cuda_fail(e, "job kernel");
-    CamConst cc;
-    cc.fx = cam->fx;
-    cc.fy = cam->fy;
-    cc.cx = cam->cx;
-    cc.cy = cam->cy;
-    cc.width = cam->width;
-    cc.height = cam->height;
-    cc.cell_w_inv = (float)kGridCols / (float)cam->width;
-    cc.cell_h_inv = (float)kGridRows / (float)cam->height;
+    const CamConst cc = CamConst::make(cam->fx, cam->fy, cam->cx, cam->cy, cam->width, cam->height);
     const tm_keyframe_view *views[2] = {q, t};
     for (int k = 0; k < 2; ++k) {  // node order and grid of each keyframe, into its scratch slot
         IngestArgs a;

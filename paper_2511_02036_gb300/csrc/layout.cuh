@@ -2,9 +2,12 @@
 //
 // A keyframe occupies one fixed-size slot (Sec. IV-B: immutable keyframe data, resident
 // until removal).  Inside a slot every array is SoA, 128-byte aligned, and the keypoints are
-// stored in BoW-node order (stable: ties keep the caller's order), so that a node bucket is
-// a contiguous range and the candidates of one query are read with consecutive 32-byte
-// descriptor loads.  `orig` maps a sorted position back to the caller's keypoint index.
+// stored grouped by BoW node: in ascending order of the node key (a bijective mix of the node
+// id, stored in `node`), caller order within a node, so that a node's keypoints are a
+// contiguous range read with consecutive 32-byte descriptor loads.  `bstart` indexes that
+// order by the key's top kBucketBits bits (bucket b = positions bstart[b] .. bstart[b+1]), so
+// a query finds its node's keypoints in one bucket.  `orig` maps a position back to the
+// caller's keypoint index; `grid_start`/`grid_items` index positions by projection-grid cell.
 #pragma once
 
 #include <stddef.h>
@@ -18,6 +21,8 @@ constexpr int kGridCols = 64;
 constexpr int kGridRows = 48;
 constexpr int kGridCells = kGridCols * kGridRows;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kBucketBits = 12;  // node-key buckets of a keyframe's node index
+constexpr int kBuckets = 1 << kBucketBits;
 constexpr int kFuseChunk = 256; // map points per fusion item (one CTA of the fusion kernel)
 constexpr int kQueryGroup = 32; // queries per search unit (one warp)
 
@@ -33,7 +38,7 @@ struct KfHeader {
 
 // Byte offsets of the arrays of a slot with capacity `cap` keypoints.
 struct SlotLayout {
-    size_t desc, xy, angle, node, orig, level, grid_start, grid_items, bytes;
+    size_t desc, xy, angle, node, orig, level, grid_start, grid_items, bstart, bytes;
     __host__ __device__ static constexpr SlotLayout make(int cap) {
         SlotLayout L{};
         size_t o = align128(sizeof(KfHeader));
@@ -45,6 +50,7 @@ struct SlotLayout {
         L.level = o;      o = align128(o + size_t(cap) * 1);
         L.grid_start = o; o = align128(o + size_t(kGridCells + 1) * 2);
         L.grid_items = o; o = align128(o + size_t(cap) * 2);
+        L.bstart = o;     o = align128(o + size_t(kBuckets + 1) * 2);
         L.bytes = o;
         return L;
     }
@@ -61,6 +67,7 @@ struct KfView {
     const uint8_t *level;
     const uint16_t *grid_start;  // [kGridCells + 1]
     const uint16_t *grid_items;  // sorted positions, grouped by cell
+    const uint16_t *bstart;      // [kBuckets + 1] first position of each node-key bucket
     __host__ __device__ static KfView at(const unsigned char *base, const SlotLayout &L) {
         KfView v;
         v.hdr = reinterpret_cast<const KfHeader *>(base);
@@ -72,6 +79,7 @@ struct KfView {
         v.level = base + L.level;
         v.grid_start = reinterpret_cast<const uint16_t *>(base + L.grid_start);
         v.grid_items = reinterpret_cast<const uint16_t *>(base + L.grid_items);
+        v.bstart = reinterpret_cast<const uint16_t *>(base + L.bstart);
         return v;
     }
 };
@@ -107,6 +115,8 @@ struct WorkItem {
     const unsigned char *t;  // search: neighbour slot; fuse: unused
     const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
                              // keyframe entering with the batch, so that F does not wait for it)
+    const float *qangle;     // search: Q's angles in the order the search visits Q (below)
+    const uint16_t *qorig;   // search: caller index of each visited position, or null (identity)
     uint32_t kind;
     uint32_t out_off;        // first entry of this item's region in the padded output
     uint32_t a;              // search: byte offset of q mask (kNone: all free); fuse: first mp
@@ -120,16 +130,23 @@ struct WorkItem {
     uint32_t pad;
 };
 
-// A unit of the match kernel, one warp: 32 node-order queries of a search item, with what
-// the warp needs of the item (so that it reads one record).
+// A unit of the match kernel, one warp: 32 queries of a search item, with what the warp needs
+// of the item (so that it reads one record).  The queries are read where they are: a stored
+// keyframe from its slot (node order, keys stored, `qorig` maps back), a keyframe entering with
+// the batch from the staged caller-order arrays (raw node ids, identity order), so that the
+// search need not wait for its ingest.
 struct Unit {
-    const unsigned char *q, *t;  // slots of the pair
+    const unsigned char *t;      // neighbour slot
+    const uint4 *qdesc;          // [nq][2]
+    const float2 *qxy;
+    const uint32_t *qnode;       // node keys, or raw node ids if qraw
+    const uint16_t *qorig;       // caller index of each position, or null (identity)
     uint32_t item;
     uint32_t group;              // queries 32*group ..
     uint32_t nq, nt;
     uint32_t res_off, t_off;
     uint32_t qmask;              // byte offset of Q's eligibility mask, or kNone
-    uint32_t pad;
+    uint32_t qraw;
 };
 
 // Shared-memory carve of a fusion CTA: the target keyframe's grid and the keypoint arrays the
@@ -164,8 +181,25 @@ struct FuseConst {
 
 struct CamConst {
     double fx, fy, cx, cy;
+    double kinv[4];               // K^-1 entries 1/fx, -cx/fx, 1/fy, -cy/fy (float64 divisions)
     int32_t width, height;
     float cell_w_inv, cell_h_inv;
+    static CamConst make(double fx, double fy, double cx, double cy, int32_t w, int32_t h) {
+        CamConst c;
+        c.fx = fx;
+        c.fy = fy;
+        c.cx = cx;
+        c.cy = cy;
+        c.kinv[0] = 1.0 / fx;
+        c.kinv[1] = -cx / fx;
+        c.kinv[2] = 1.0 / fy;
+        c.kinv[3] = -cy / fy;
+        c.width = w;
+        c.height = h;
+        c.cell_w_inv = (float)kGridCols / (float)w;
+        c.cell_h_inv = (float)kGridRows / (float)h;
+        return c;
+    }
 };
 
 struct Out3 { int32_t a, b, c; };
@@ -181,6 +215,7 @@ struct BatchArgs {
     uint32_t *counters;           // [0] spare, [1] finalize CTAs done, [2] status
     const uint8_t *masks;         // caller-order eligibility masks
     const float *mp_pos, *mp_normal, *mp_min, *mp_max;
+    uint32_t n_mp;                // map points of the batch
     const uint4 *mp_desc;
     const uint8_t *mp_skip;
     Out3 *padded;                 // per-item regions
@@ -196,6 +231,7 @@ struct BatchArgs {
     FuseConst fp;
     CamConst cam;
     int32_t cap;                  // slot capacity (keypoints)
+    SlotLayout L;                 // array offsets of a slot of that capacity
     int32_t lanes;                // lanes per query
     int32_t sn;                   // largest keypoint count of the batch's pairs (rounded to 32)
 };

@@ -110,8 +110,10 @@ extern "C" tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max
     if (max_kp < 1 || max_kp > TM_MAX_KP_LIMIT)
         return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: max_kp %d outside [1, %d]", max_kp,
                     TM_MAX_KP_LIMIT);
-    if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0) || !(cam->fy > 0))
-        return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: bad camera");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > TM_MAX_IMAGE_SIZE ||
+        cam->height > TM_MAX_IMAGE_SIZE || !(cam->fx > 0) || !(cam->fy > 0))
+        return fail(TM_ERR_INVALID_ARG, "tm_ctx_create: bad camera (image sides 1..%d px, fx, fy > 0)",
+                    TM_MAX_IMAGE_SIZE);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -128,14 +130,7 @@ extern "C" tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete c; return cuda_fail(e, "props"); }
     c->num_sms = prop.multiProcessorCount;
     c->max_smem = prop.sharedMemPerBlockOptin;
-    c->camc.fx = cam->fx;
-    c->camc.fy = cam->fy;
-    c->camc.cx = cam->cx;
-    c->camc.cy = cam->cy;
-    c->camc.width = cam->width;
-    c->camc.height = cam->height;
-    c->camc.cell_w_inv = (float)kGridCols / (float)cam->width;
-    c->camc.cell_h_inv = (float)kGridRows / (float)cam->height;
+    c->camc = CamConst::make(cam->fx, cam->fy, cam->cx, cam->cy, cam->width, cam->height);
     if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         delete c;
@@ -227,11 +222,13 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
     unsigned char *d = static_cast<unsigned char *>(st.dev.p);
     IngestJob *jobs = reinterpret_cast<IngestJob *>(h + o_jobs);
     size_t off = 0;
+    st.src.assign((size_t)n, 0u);
     for (int k = 0; k < n; ++k) {
         const tm_keyframe_view &v = kfs[k];
         const size_t m = (size_t)v.n;
         jobs[k].slot = c->slots[slots[k]].ptr;
         jobs[k].src = (uint32_t)off;
+        st.src[k] = (uint32_t)off;
         jobs[k].n = v.n;
         for (int q = 0; q < 12; ++q) jobs[k].Tcw[q] = v.Tcw[q];
         if (m) {
@@ -396,7 +393,8 @@ extern "C" tm_status tm_store_get_stats(tm_ctx *c, tm_store_stats *o) {
 
 void BatchBuf::release() {
     if (graph) cudaGraphExecDestroy(graph);
-    graph = nullptr;
+    if (graph_timed) cudaGraphExecDestroy(graph_timed);
+    graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &units, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
                       &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F,
                       &acc, &win, &tmask_n})
@@ -514,8 +512,27 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             : c->slots[slot].ptr + offsetof(KfHeader, Tcw);
         return reinterpret_cast<const double *>(p);
     };
+    // where the search reads a query keyframe: a stored one from its slot, one entering with
+    // this batch from its staged caller-order arrays (so that the search need not wait for its
+    // ingest)
+    const SlotLayout SL = SlotLayout::make(c->cap);
+    struct QView { const uint4 *desc; const float2 *xy; const uint32_t *node; const uint16_t *orig;
+                   const float *angle; uint32_t raw; };
+    auto qview_of = [&](int slot) -> QView {
+        auto it = new_index.find(slot);
+        if (it != new_index.end()) {
+            const IngestArgs &a = B.ingest_args;
+            const uint32_t src = B.ingest.src[(size_t)it->second];
+            return QView{a.desc + 2 * (size_t)src, a.xy + src, a.node + src, nullptr, a.angle + src, 1u};
+        }
+        const unsigned char *b = c->slots[slot].ptr;
+        return QView{reinterpret_cast<const uint4 *>(b + SL.desc), reinterpret_cast<const float2 *>(b + SL.xy),
+                     reinterpret_cast<const uint32_t *>(b + SL.node), reinterpret_cast<const uint16_t *>(b + SL.orig),
+                     reinterpret_cast<const float *>(b + SL.angle), 0u};
+    };
     B.nbr_new = false;
     std::vector<WorkItem> &items = B.h_items;
+    std::vector<QView> item_qv;
     items.clear();
     B.item_nq.clear();
     B.item_nt.clear();
@@ -553,6 +570,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.t = c->slots[ts].ptr;
             w.pq = pose_of(qs);
             w.pt = pose_of(ts);
+            const QView qv = qview_of(qs);
+            w.qangle = qv.angle;
+            w.qorig = qv.orig;
+            item_qv.push_back(qv);
             B.nbr_new |= new_index.count(ts) != 0;
             w.kind = kItemSearch;
             w.out_off = pad;
@@ -618,7 +639,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     for (uint32_t i : order) {
         const WorkItem &w = items[i];
         for (uint32_t g = 0; g * kQueryGroup < w.nq; ++g)
-            units.push_back(Unit{w.q, w.t, i, g, w.nq, w.nt, w.res_off, w.t_off, w.a, 0u});
+            units.push_back(Unit{w.t, item_qv[i].desc, item_qv[i].xy, item_qv[i].node, item_qv[i].orig, i, g,
+                                 w.nq, w.nt, w.res_off, w.t_off, w.a, item_qv[i].raw});
     }
     B.n_units = (uint32_t)units.size();
     // fusion stage: the largest target of the batch
@@ -647,9 +669,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.acc.reserve(nres * 4)) || (e = B.win.reserve(ntt * 4)) ||
         (e = B.tmask_n.reserve(ntt)))
         return cuda_fail(e, "batch buffers");
-    if (B.pointers() != before && B.graph) {
-        cudaGraphExecDestroy(B.graph);
-        B.graph = nullptr;
+    if (B.pointers() != before && (B.graph || B.graph_timed)) {
+        if (B.graph) cudaGraphExecDestroy(B.graph);
+        if (B.graph_timed) cudaGraphExecDestroy(B.graph_timed);
+        B.graph = B.graph_timed = nullptr;
     }
     // one pinned staging area, one transfer per table: items, units
     const size_t o_units = align128(ni * sizeof(WorkItem));
@@ -686,6 +709,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.mp_normal = static_cast<const float *>(B.mp_normal.p);
     A.mp_min = static_cast<const float *>(B.mp_min.p);
     A.mp_max = static_cast<const float *>(B.mp_max.p);
+    A.n_mp = (uint32_t)std::max(0, mps.n);
     A.mp_desc = static_cast<const uint4 *>(B.mp_desc.p);
     A.mp_skip = (mps.n > 0 && mps.skip) ? static_cast<const uint8_t *>(B.mp_skip.p) : nullptr;
     A.padded = static_cast<Out3 *>(B.padded.p);
@@ -704,6 +728,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.fp.radius_scale = fp.radius_scale;
     A.cam = c->camc;
     A.cap = c->cap;
+    A.L = SlotLayout::make(c->cap);
     A.sn = B.smem_n;
     B.sp = sp;
     B.fp = fp;
@@ -739,9 +764,15 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
                                                                                : cudaEventRecordDefault);
 }
 
-// Enqueue the batch pipeline: prep beside the ingest of new keyframes, then match with the
-// fusion kernel as a parallel branch, finalize, copy.
-tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s) {
+// Enqueue the batch pipeline as a graph of kernels only (no memset or event nodes, which cost
+// several microseconds each inside a graph).  Two branches:
+//   search: prep (F, winners, eligibility, counters) -> match -> finalize, on `paux`; it reads
+//           new keyframes from their staged arrays, so it runs beside their ingest (unless a
+//           neighbour enters with the batch: then it starts after the ingest);
+//   store:  ingest of new keyframes -> fusion (needs their grids and prep's counters), on s;
+// joined before copy (offsets + dense output).  With `timed`, events E0..E7 mark: start, prep,
+// match, finalize done (search branch), ingest, fusion done, join, copy done.
+tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed) {
     cudaError_t e;
     (void)threads;  // the match kernel runs 256-thread CTAs of independent warps
     B.args.lanes = lanes;
@@ -750,44 +781,38 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     const int per_sm = match_ctas_per_sm(lanes);
     if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "match kernel does not fit");
     B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_units + 7) / 8, (uint32_t)(per_sm * c->num_sms)));
-    const bool timed = B.ev[0] != nullptr;
-    if (timed && (e = record_stage(B.ev[0], s))) return cuda_fail(e, "event");
-    // prep needs the stored neighbours only: a branch beside the ingest, unless a neighbour
-    // enters with this batch
-    const bool pbranch = B.n_new > 0 && B.n_search_items > 0 && !B.nbr_new;
-    if (pbranch) {
-        if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
-                        (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
-                        (e = cudaEventCreateWithFlags(&B.pjoin, cudaEventDisableTiming))))
-            return cuda_fail(e, "prep branch");
-        if ((e = cudaEventRecord(B.pfork, s)) || (e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) ||
-            (e = launch_prep(B.args, B.paux)) || (e = cudaEventRecord(B.pjoin, B.paux)))
-            return cuda_fail(e, "prep kernel");
-    }
+    if (timed && !B.ev[0])
+        for (cudaEvent_t &ev : B.ev)
+            if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
+    if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
+                    (e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming)) ||
+                    (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming)) ||
+                    (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
+                    (e = cudaEventCreateWithFlags(&B.pjoin, cudaEventDisableTiming))))
+        return cuda_fail(e, "launch branches");
+    auto mark = [&](int k, cudaStream_t st) { return timed ? record_stage(B.ev[k], st) : cudaSuccess; };
+    if ((e = mark(0, s))) return cuda_fail(e, "event");
+    const bool after_ingest = B.n_new > 0 && B.nbr_new;
+    if (!after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
-    if (!pbranch && (e = launch_prep(B.args, s))) return cuda_fail(e, "prep kernel");
-    if ((e = cudaMemsetAsync(B.counters.p, 0, 16, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
-        return cuda_fail(e, "reset counters");
-    // fusion runs as a parallel branch, joined before finalize (whose last CTA needs its counts)
-    const bool branch = B.n_items > B.n_search_items;
-    if (branch) {
-        if (!B.aux && ((e = cudaStreamCreateWithFlags(&B.aux, cudaStreamNonBlocking)) ||
-                       (e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming)) ||
-                       (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming))))
-            return cuda_fail(e, "fusion branch");
-        if ((e = cudaEventRecord(B.fork, s)) || (e = cudaStreamWaitEvent(B.aux, B.fork, 0)) ||
-            (e = launch_fuse(B.args, B.aux)) || (e = cudaEventRecord(B.join, B.aux)))
-            return cuda_fail(e, "fusion kernel");
-    }
-    if (pbranch && (e = cudaStreamWaitEvent(s, B.pjoin, 0))) return cuda_fail(e, "prep join");
-    if (timed && (e = record_stage(B.ev[1], s))) return cuda_fail(e, "event");
-    if ((e = launch_match(B.args, B.ctas, s))) return cuda_fail(e, "match kernel");
-    if (branch && (e = cudaStreamWaitEvent(s, B.join, 0))) return cuda_fail(e, "fusion join");
-    if ((e = launch_finalize(B.args, s))) return cuda_fail(e, "finalize kernel");
-    if (timed && (e = record_stage(B.ev[2], s))) return cuda_fail(e, "event");
-    if (B.n_items && (e = launch_copy(B.args, std::min<int>((B.n_items + 7) / 8, 8 * c->num_sms), s)))
+    if ((e = mark(4, s))) return cuda_fail(e, "event");
+    if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
+    // search branch
+    if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = launch_prep(B.args, B.paux)) ||
+        (e = mark(1, B.paux)) || (e = cudaEventRecord(B.pjoin, B.paux)) ||
+        (e = launch_match(B.args, B.ctas, B.paux)) || (e = mark(2, B.paux)) ||
+        (e = launch_finalize(B.args, B.paux)) || (e = mark(3, B.paux)) ||
+        (e = cudaEventRecord(B.join, B.paux)))
+        return cuda_fail(e, "search branch");
+    // store branch: fusion after the ingest and prep's counter reset
+    if ((e = cudaStreamWaitEvent(s, B.pjoin, 0)) ||
+        (B.n_items > B.n_search_items && (e = launch_fuse(B.args, s))) || (e = mark(5, s)) ||
+        (e = cudaStreamWaitEvent(s, B.join, 0)) || (e = mark(6, s)))
+        return cuda_fail(e, "fusion kernel");
+    // copy: about one warp per item (32 per CTA), at most one CTA per SM
+    if ((e = launch_copy(B.args, (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_items + 31) / 32, c->num_sms)), s)))
         return cuda_fail(e, "copy kernel");
-    if (timed && (e = record_stage(B.ev[3], s))) return cuda_fail(e, "event");
+    if ((e = mark(7, s))) return cuda_fail(e, "event");
     return TM_OK;
 }
 
@@ -1120,6 +1145,7 @@ struct tm_plan {
     std::vector<tm_step> steps;
     std::vector<std::vector<uint64_t>> nbrs;
     int kernels_per_run = 0;
+    bool timed_last = false;  // the last run was tm_plan_run_timed
 };
 
 extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_steps,
@@ -1162,26 +1188,27 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         return st;
     }
     if (spd.mode != TM_MODE_PER_PAIR) {
-        // capture the launch in a CUDA graph, with events at the stage boundaries
+        // capture the launch in two CUDA graphs: kernels only, and the same with events at the
+        // stage boundaries (tm_plan_run_timed)
         const int th = P->B.threads, ln = P->B.lanes;
-        for (cudaEvent_t &ev : P->B.ev)
-            if (!st && (e = cudaEventCreate(&ev))) st = cuda_fail(e, "events");
-        cudaGraph_t g = nullptr;
-        if (!st && (e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
-            st = cuda_fail(e, "begin capture");
-        if (!st) {
-            tm_status s1 = enqueue_fused(c, P->B, th, ln, c->capture_stream);
-            e = cudaStreamEndCapture(c->capture_stream, &g);
-            if (s1) st = s1;
-            else if (e) st = cuda_fail(e, "end capture");
+        for (int timed = 0; timed < 2 && !st; ++timed) {
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
+                st = cuda_fail(e, "begin capture");
+            if (!st) {
+                tm_status s1 = enqueue_fused(c, P->B, th, ln, c->capture_stream, timed != 0);
+                e = cudaStreamEndCapture(c->capture_stream, &g);
+                if (s1) st = s1;
+                else if (e) st = cuda_fail(e, "end capture");
+            }
+            cudaGraphExec_t &x = timed ? P->B.graph_timed : P->B.graph;
+            if (!st && (e = cudaGraphInstantiate(&x, g, 0))) st = cuda_fail(e, "graph instantiate");
+            if (g) cudaGraphDestroy(g);
         }
-        if (!st && (e = cudaGraphInstantiate(&P->B.graph, g, 0))) st = cuda_fail(e, "graph instantiate");
-        if (g) cudaGraphDestroy(g);
-        // prep and match (when there are pairs), fuse (when there are map points), finalize,
-        // copy (when there are items), ingest (when keyframes enter with the batch)
-        P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_units ? 1 : 0) +
-                             (P->B.n_items > P->B.n_search_items ? 1 : 0) + 1 + (P->B.n_items ? 1 : 0) +
-                             (P->B.n_new ? 1 : 0);
+        // prep, match (when there are pairs), fuse (when there are map points), finalize (when
+        // there are pairs), copy, ingest (when keyframes enter with the batch)
+        P->kernels_per_run = 1 + (P->B.n_units ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
+                             (P->B.n_search_items ? 1 : 0) + 1 + (P->B.n_new ? 1 : 0);
     } else {
         P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)
@@ -1206,20 +1233,27 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
     return TM_OK;
 }
 
-extern "C" tm_status tm_plan_run(tm_plan *P, void *stream) {
+static tm_status plan_run(tm_plan *P, void *stream, bool timed) {
     if (!P) return fail(TM_ERR_INVALID_ARG, "tm_plan_run: null plan");
     tm_ctx *c = P->ctx;
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);
-    if (P->B.graph) {
-        cudaError_t e = cudaGraphLaunch(P->B.graph, s);
+    cudaGraphExec_t g = timed ? P->B.graph_timed : P->B.graph;
+    if (g) {
+        cudaError_t e = cudaGraphLaunch(g, s);
         if (e) return cuda_fail(e, "graph launch");
+        P->timed_last = timed;
         return TM_OK;
     }
     std::lock_guard<std::mutex> lk(c->mu);
+    P->timed_last = false;
     if (P->B.sp.mode == TM_MODE_PER_PAIR) return enqueue_plain(c, P->B, P->B.lanes, s);
     return enqueue_fused(c, P->B, P->B.threads, P->B.lanes, s);
 }
+
+extern "C" tm_status tm_plan_run(tm_plan *P, void *stream) { return plan_run(P, stream, false); }
+
+extern "C" tm_status tm_plan_run_timed(tm_plan *P, void *stream) { return plan_run(P, stream, true); }
 
 extern "C" tm_status tm_plan_results(tm_plan *P, tm_batch_result *res, void *stream) {
     if (!P || !res) return fail(TM_ERR_INVALID_ARG, "tm_plan_results: null argument");
@@ -1239,13 +1273,20 @@ extern "C" tm_status tm_plan_info(tm_plan *P, int32_t *threads, int32_t *lanes, 
 
 extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     if (!P || !ms) return fail(TM_ERR_INVALID_ARG, "tm_plan_stage_times: null argument");
-    ms[0] = ms[1] = ms[2] = 0.0f;
-    if (!P->B.ev[0]) return TM_OK;
+    for (int k = 0; k < TM_PLAN_STAGES; ++k) ms[k] = 0.0f;
+    if (!P->timed_last || !P->B.ev[0]) return TM_OK;
     cudaSetDevice(P->ctx->device);
-    cudaError_t e = cudaEventSynchronize(P->B.ev[3]);
+    cudaError_t e = cudaEventSynchronize(P->B.ev[7]);
     if (e) return cuda_fail(e, "stage events");
-    for (int k = 0; k < 3; ++k)
-        if ((e = cudaEventElapsedTime(&ms[k], P->B.ev[k], P->B.ev[k + 1]))) return cuda_fail(e, "stage times");
+    float t[8] = {0};
+    for (int k = 1; k < 8; ++k)
+        if ((e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k]))) return cuda_fail(e, "stage times");
+    ms[0] = t[4];                         // ingest
+    ms[1] = t[1];                         // prep
+    ms[2] = t[2] - t[1];                  // match
+    ms[3] = t[3] - t[2];                  // finalize
+    ms[4] = t[5] - std::max(t[4], t[1]);  // fusion
+    ms[5] = t[7] - t[6];                  // offsets + copy
     return TM_OK;
 }
 

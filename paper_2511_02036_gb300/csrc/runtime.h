@@ -42,6 +42,7 @@ struct IngestStage {
     DevBuf dev;
     PinBuf host;
     std::vector<std::pair<size_t, size_t>> host_ranges;
+    std::vector<uint32_t> src;  // first staged keypoint of each keyframe
     void release() { dev.release(); host.release(); }
 };
 
@@ -64,11 +65,12 @@ struct BatchBuf {
     tm_search_params sp{};
     tm_fuse_params fp{};
     BatchArgs args{};
-    cudaGraphExec_t graph = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries (plans)
-    cudaStream_t aux = nullptr;          // fusion branch of the launch
+    cudaGraphExec_t graph = nullptr;        // kernels only
+    cudaGraphExec_t graph_timed = nullptr;  // the same with events at the stage boundaries
+    cudaEvent_t ev[8] = {};                 // stage boundaries (timed graph)
+    cudaStream_t aux = nullptr;          // (unused)
     cudaEvent_t fork = nullptr, join = nullptr;
-    cudaStream_t paux = nullptr;         // prep branch (beside the ingest)
+    cudaStream_t paux = nullptr;         // search branch (beside the ingest)
     cudaEvent_t pfork = nullptr, pjoin = nullptr;
     std::vector<void *> pointers() const;
     void release();
@@ -119,7 +121,7 @@ tm_status store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyframe_vie
 tm_status prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int n_steps,
                         const tm_batch_inputs *in, const tm_search_params &sp,
                         const tm_fuse_params &fp, cudaStream_t s);
-tm_status enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s);
+tm_status enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed = false);
 tm_status enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s);
 tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s);
 tm_status tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure);

@@ -99,3 +99,5 @@ def test_null_arguments_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.tm_ctx_create(0, ctypes.byref(cam), 0, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG
     assert lib.tm_ctx_create(0, ctypes.byref(cam), L.TM_MAX_KP_LIMIT + 1, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG
+    wide = L.tm_camera(L.TM_MAX_IMAGE_SIZE + 1, 480, 450.0, 450.0, 320.0, 240.0)
+    assert lib.tm_ctx_create(0, ctypes.byref(wide), 100, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG

@@ -195,8 +195,11 @@ def test_cfg2_full_size_parity(tm, cfg2):
             plan.run()
             plan.run()
             assert_same(plan.results(), exp)
+            assert all(t == 0 for t in plan.stage_times())  # untimed graph: no events
+            plan.run(timed=True)
+            assert_same(plan.results(), exp)
             ms = plan.stage_times()
-            assert all(t > 0 for t in ms)
+            assert len(ms) == 6 and all(t > 0 for t in ms)
 
 
 def test_new_keyframes_enter_with_the_batch(tm, small_batch):
