@@ -155,24 +155,20 @@ def algorithmic_bytes(w, res):
                                                                          mask_bytes=mask, outputs=out)
 
 
-def match_bytes(w):
-    """Unique bytes the match kernel must touch for one batch: of each query keyframe its
-    descriptors, positions, node keys, caller indices and mask bytes (47 B per keypoint), of
-    each neighbour its descriptors, positions, node keys and levels (45 B per keypoint), and per
-    pair the accepted match of every query (4 B) and the winner word and eligibility byte of
-    every target (5 B)."""
+def search_bytes(w, res):
+    """Unique bytes the search kernel must touch for one batch: of each query keyframe its
+    descriptors, positions, node keys, caller indices, angles and mask bytes (51 B per
+    keypoint), of each neighbour its descriptors, positions, node keys, levels, caller indices,
+    angles and mask bytes (52 B per keypoint) and its node-key bucket table (8208 B), and 12 B
+    per output match."""
     qs, ts = set(), set()
-    per_pair = 0
     for s in w["steps"]:
         qs.add(s["q"])
-        nq = w["frames"][s["q"]]["n"]
-        for t in s["nbrs"]:
-            ts.add(t)
-            per_pair += 4 * nq + 5 * w["frames"][t]["n"]
+        ts.update(s["nbrs"])
     q = sum(w["frames"][i]["n"] for i in qs)
     t = sum(w["frames"][i]["n"] for i in ts)
-    return 47 * q + 45 * t + per_pair, dict(query_keypoints=q, neighbour_keypoints=t,
-                                             per_pair_bytes=per_pair)
+    return 51 * q + 52 * t + 8208 * len(ts) + OUT_BYTES * len(res.matches), dict(
+        query_keypoints=q, neighbour_keypoints=t, neighbours=len(ts), matches=len(res.matches))
 
 
 def oracle_sample(w, seconds, t_limit=None):
@@ -321,14 +317,14 @@ def run_mine(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (match), timed by the events around it in the timed graph
     pk, pk_kind = peaks()
-    alg, parts = match_bytes(w)
+    alg, parts = search_bytes(w, res)
     path_bytes, path_parts = algorithmic_bytes(w, res)
-    kern_ms = float(stage[:, 2].mean())
+    kern_ms = float(stage[:, 0].mean())
     achieved = alg / (kern_ms / 1e3) / 1e9
-    traffic, traffic_note = kernel_traffic("kernels.cu", "match_kernel_cfg2.json")
+    traffic, traffic_note = kernel_traffic("kernels.cu", "search_kernel_cfg2.json")
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "kernel": "match_kernel (node join + Hamming/epipolar search, warp per 32 queries)",
+            "kernel": "search_kernel (CTA per pair: F, node join, Hamming/epipolar search, one match per target, rotation filter, compaction)",
             "peak_kind": pk_kind, "algorithmic_bytes": alg, "algorithmic_parts": parts,
             "kernel_ms": kern_ms, "traffic_note": traffic_note,
             "path_algorithmic_bytes": path_bytes, "path_parts": path_parts}
@@ -345,12 +341,11 @@ def run_mine(args, rank, world, local_rank):
            "comparisons_per_step": ncmp,
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                           "note": "batch form: every keyframe of a step completes with its batch"},
-           "stage_ms": {"ingest": float(stage[:, 0].mean()), "prep": float(stage[:, 1].mean()),
-                        "match": kern_ms, "finalize": float(stage[:, 3].mean()),
-                        "fuse": float(stage[:, 4].mean()), "copy": float(stage[:, 5].mean()),
+           "stage_ms": {"search": kern_ms, "ingest": float(stage[:, 1].mean()),
+                        "fuse": float(stage[:, 2].mean()), "copy": float(stage[:, 3].mean()),
                         "note": "from the plan's timed graph (an event node at each stage boundary "
-                                "adds a few us); the search branch (prep, match, finalize) runs beside "
-                                "the store branch (ingest, fuse); value and ms_per_step come from the "
+                                "adds a few us); the search kernel runs beside the store branch "
+                                "(ingest, then fuse); value and ms_per_step come from the "
                                 "kernels-only graph"},
            "roofline": roof, "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
            "wall_s_timed_region": t_wall}

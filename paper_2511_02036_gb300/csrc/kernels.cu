@@ -1,16 +1,15 @@
 // Kernels of the local-mapping search path for sm_103a.
 //
-//   ingest_kernel      Sec. IV-B  keyframe enters the store: sort keypoints by BoW node,
-//                                 build the 64x48 projection-grid index (one CTA per KF)
-//   prep_kernel        Sec. IV-C  per (new KF, neighbour) pair: fundamental matrix, per-target
-//                                 state reset, neighbour eligibility in node order
-//   match_kernel       Sec. IV-C  warp per 32 queries: node join -> Hamming + epipolar gate ->
-//                                 best/second -> accept -> per-target winner (atomicMin)
+//   ingest_kernel      Sec. IV-B  keyframe enters the store: group keypoints by BoW node key,
+//                                 build the node-key bucket table and the 64x48 projection-grid
+//                                 index (one CTA per keyframe)
+//   search_kernel      Sec. IV-C  one CTA per (new KF, neighbour) pair: fundamental matrix ->
+//                                 node join (bucket lookup) -> Hamming + epipolar gate ->
+//                                 best/second -> accept -> one match per target -> rotation
+//                                 histogram -> top-3 bins -> ordered compaction
 //   fuse_kernel        Sec. IV-D  fusion search, one thread per map point: projection gates ->
 //                                 grid window -> reprojection gate -> best Hamming
-//   finalize_kernel    Sec. IV-C  per pair: one match per target -> rotation histogram ->
-//                                 top-3 bins -> ordered compaction; offsets
-//   copy_kernel                   gathers the per-item regions into one dense array
+//   copy_kernel                   per-item counts -> offsets; regions -> one dense array
 //   pair_* / fuse_*    plain form: one pair per launch sequence, global scratch
 //
 // Floating point: every gate is evaluated with explicit round-to-nearest intrinsics in the
@@ -485,23 +484,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ------------------------------------------------------------------------- batch pipeline
 //
-// A batch runs as a few kernels over flat work lists, so that every SM holds many independent
-// warps and no CTA waits on another:
-//   prep_kernel      per pair: F; the neighbour's eligibility in node order; per-target
-//                    winners reset.  Needs only poses and stored keyframes, so it runs beside
-//                    the ingest of the batch's new keyframes.
-//   match_kernel     warp units of 32 node-order queries: candidate ranges (the BoW join, a
-//                    warp-cooperative search of the neighbour's node array), Hamming +
-//                    epipolar gate over each range, best/second, accept, atomicMin on the
-//                    target's winner.
-//   fuse_kernel      per 256 map points (a parallel branch of the launch graph): projection
-//                    gates, grid window in the staged target, best Hamming.
-//   finalize_kernel  per pair: one match per target, rotation histogram, top-3 filter,
-//                    ordered compaction; the last CTA turns per-item counts into offsets.
-//   copy_kernel      per-item regions into one dense array.
-
-// Per-target state: (dist << 16 | caller query index) of the best accepted query.
-// Per-query state (node order): accepted (target << 16 | dist) or kNone.
+// A batch runs as two branches of a graph, joined before copy:
+//   search   search_kernel, one CTA per pair (largest first): everything of Sec. IV-C for the
+//            pair, with the neighbour's node index, the winners, the accepted matches and the
+//            results in shared memory.  It reads a new keyframe from its staged arrays, so it
+//            runs beside the ingest.
+//   store    ingest_kernel, then fuse_kernel (CTA per 256 map points of a step: projection
+//            gates, grid window in the staged target, best Hamming).
+//   copy     per-item counts -> offsets, per-item regions -> dense output, comparison totals.
 
 struct FuseK {
     float R[9], t[3], O[3], scale[kLevels], thr[kLevels];
@@ -608,123 +598,7 @@ __device__ __forceinline__ void fuse_setup(const KfHeader *h, float chi2, FuseK 
     }
 }
 
-// ---------------------------------------------------------------- prep (S1)
-
-constexpr int kPrepThreads = 128;
-
-// One CTA per pair, independent of the keyframes entering with the batch (poses come from the
-// work item), so that it runs beside their ingest: warp 0 forms F (nine lanes); all threads
-// reset the target's winners and gather its eligibility into node order.  CTA 0 also zeroes
-// the batch's counters (comparisons, status), which every later kernel of the batch updates.
-__global__ void __launch_bounds__(kPrepThreads) prep_kernel(BatchArgs A) {
-    const int tid = threadIdx.x, bs = blockDim.x;
-    const uint32_t i = blockIdx.x;
-    if (i == 0 && tid < 4) {
-        A.counters[tid] = 0u;
-        if (tid < 2) A.ncmp[tid] = 0ull;
-    }
-    if (i >= A.n_search) return;
-    const WorkItem w = A.items[i];
-    const SlotLayout &L = A.L;
-    const KfView T = KfView::at(w.t, L);
-    const int nT = (int)w.nt;
-    if (tid < 32) fundamental_lanes(A.cam, w.pq, w.pt, A.pair_F + 9 * (size_t)i);
-    uint32_t *win = A.win + w.t_off;
-    uint8_t *tel = A.tmask_n ? A.tmask_n + w.t_off : nullptr;
-    constexpr int U = 8;  // targets per thread and pass: all their loads in flight together
-    for (int j0 = 0; j0 < nT; j0 += U * bs) {
-        uint32_t o[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int j = j0 + k * bs + tid;
-            o[k] = (tel && w.b != kNone && j < nT) ? T.orig[j] : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int j = j0 + k * bs + tid;
-            if (j < nT) {
-                win[j] = kNone;
-                if (tel) tel[j] = w.b == kNone ? 1 : A.masks[w.b + o[k]];
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------- match (S2, S3, S4)
-
-// 32 node-order queries of one pair, G lanes per query (32/G queries per round).  The BoW
-// join is a lookup in the neighbour's node index: a query's same-node candidates are the
-// positions of its key's bucket whose key equals its own.  Every load of a round is issued
-// before its first use: the query's bucket bounds, descriptor and position together, then
-// each candidate's key, eligibility, descriptor, position and level together.
-template <int G>
-__device__ __forceinline__ void match_group(const BatchArgs &A, const Unit &un, const float *thr,
-                                            uint32_t &cmp) {
-    const SlotLayout &L = A.L;
-    const KfView T = KfView::at(un.t, L);
-    const uint32_t lane = threadIdx.x & 31u, sub = lane % G;
-    const int p0 = (int)(un.group * 32u);
-    const int nloc = min(32, (int)un.nq - p0);
-    float F[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
-    const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
-    const bool epi = A.sp.epipolar != 0;
-#pragma unroll 1
-    for (int r = 0; r < G; ++r) {
-        const int ql = r * (32 / G) + (int)(lane / G);
-        const bool in = ql < nloc;
-        const int p = p0 + ql, pc = in ? p : p0;  // (a valid index for the speculative loads)
-        const uint32_t nk = un.qnode[pc];
-        const uint32_t key = un.qraw ? node_key(nk) : nk;
-        const uint32_t io = un.qorig ? (uint32_t)un.qorig[pc] : (uint32_t)pc;
-        const uint32_t b = key >> (32 - kBucketBits);
-        const int bs = T.bstart[b], be = T.bstart[b + 1];
-        const uint4 q0 = un.qdesc[2 * pc], q1 = un.qdesc[2 * pc + 1];
-        const float2 xq = un.qxy[pc];
-        const bool el = un.qmask == kNone || A.masks[un.qmask + io];
-        uint32_t bkey = kNone, sec = 0xFFFFu;
-        if (in && el && bs < be) {
-            const Line l = epi_line(F, xq.x, xq.y);
-            for (int j = bs + (int)sub; j < be; j += G) {
-                const uint32_t tk = T.node[j];
-                const uint8_t te = tel ? tel[j] : (uint8_t)1;
-                const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
-                const float2 xt = T.xy[j];
-                const int lv = T.level[j];
-                if (tk != key || !te) continue;
-                ++cmp;
-                const uint32_t d = (uint32_t)hamming(q0, q1, t0, t1);
-                if (epi && !epi_pass(l, xt.x, xt.y, thr[lv])) continue;
-                const uint32_t k2 = (d << 16) | (uint32_t)j;
-                if (k2 < bkey) { sec = min(sec, bkey >> 16); bkey = k2; }
-                else sec = min(sec, d);
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            const uint32_t ob = __shfl_xor_sync(kFull, bkey, off);
-            const uint32_t os = __shfl_xor_sync(kFull, sec, off);
-            sec = min(min(sec, os), max(bkey, ob) >> 16);
-            bkey = min(bkey, ob);
-        }
-        if (sub == 0 && in) {
-            uint32_t acc = kNone;
-            if (bkey != kNone) {
-                const uint32_t best = bkey >> 16;
-                bool ok = (int)best <= A.sp.hamming_max;
-                if (ok && A.sp.ratio_num != 0 && sec != 0xFFFFu)
-                    ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sec;
-                if (ok) {
-                    const uint32_t j = bkey & 0xFFFFu;
-                    acc = (j << 16) | best;
-                    if (A.sp.resolve) atomicMin(&A.win[un.t_off + j], (best << 16) | io);
-                }
-            }
-            A.acc[un.res_off + p] = acc;
-        }
-    }
-}
+// ---------------------------------------------------------------- search (S1-S6)
 
 // Merge of two partial (best key, second distance) states of one query: the two smallest
 // candidates of the union.  Associative and commutative; identity (kNone, 0xFFFF).
@@ -733,37 +607,64 @@ __device__ __forceinline__ void merge_best2(uint32_t &b, uint32_t &s, uint32_t o
     b = min(b, ob);
 }
 
-// 32 node-order queries of one pair, their candidates spread evenly over the lanes.  Each lane
-// first finds its query's bucket in the neighbour's node index; the (query, candidate) entries
-// of all 32 queries are then numbered by a warp prefix sum over the bucket sizes and taken 32
-// per round, lane k handling entry k of the round (its query found by a search over the prefix
-// sums, its key and epipolar line taken from the owner lane by shuffles, its descriptor loaded
-// together with the candidate's arrays).
-// A round's entries of one query sit in adjacent lanes: a segmented shuffle reduction merges
-// them and the segment's first lane folds the result into the query's state in shared memory.
-// The warp thus waits ~ceil(sum / 32) load rounds instead of the largest bucket.
-__device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit &un, const float *thr,
-                                                 uint2 *st, uint32_t &cmp) {
-    const SlotLayout &L = A.L;
-    const KfView T = KfView::at(un.t, L);
+// The loads of a warp's 32-query group that depend on nothing else: issued one group ahead, so
+// that their latency overlaps the previous group's search.
+struct QLoad {
+    uint32_t nk;   // node key or raw node id
+    uint32_t io;   // caller index
+    float2 xq;
+    int el;        // eligible (1/0), or -1: not loaded yet (stored query keyframe with masks)
+};
+__device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &w, int g) {
     const int lane = (int)(threadIdx.x & 31u);
-    const int p0 = (int)(un.group * 32u);
-    const int nloc = min(32, (int)un.nq - p0);
+    const int p0 = g * 32;
+    const bool in = lane < (int)w.nq - p0;
+    const int p = p0 + (in ? lane : 0);
+    QLoad q;
+    q.nk = w.qnode[p];
+    q.xq = w.qxy[p];
+    if (w.qorig) {
+        q.io = w.qorig[p];
+        q.el = !in ? 0 : (w.a == kNone ? 1 : -1);
+    } else {
+        q.io = (uint32_t)p;
+        q.el = in && (w.a == kNone || A.masks[w.a + (uint32_t)p]);
+    }
+    return q;
+}
+
+// 32 queries (positions 32g ..) of the CTA's pair, by one warp.  Each lane finds its query's
+// candidates in the neighbour's node index staged in shared memory: the bucket of its key,
+// then the run of equal keys inside it (keys ascend within a bucket).  The (query, candidate)
+// entries of the 32 queries are numbered by a warp prefix sum and taken 32 per round, lane k
+// handling entry k (its query found by a search over the prefix sums; key-equal and eligible
+// by construction or by the staged eligibility), so that the warp waits ~ceil(entries / 32)
+// rounds of candidate loads instead of the largest bucket.  A round's entries of one query
+// sit in adjacent lanes: a segmented shuffle reduction merges (best, second) and the
+// segment's first lane folds it into the query's state.  The accepted match of each query goes
+// to acc[], its claim on the target to win[] (shared atomicMin).
+__device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                             const float *F, const float *thr, const uint32_t *tkey,
+                                             const uint16_t *bst, const uint8_t *tel, uint32_t *win,
+                                             uint32_t *acc, uint2 *st, int g, const QLoad &q,
+                                             uint32_t &cmp) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int p0 = g * 32;
+    const int nloc = min(32, (int)w.nq - p0);
     const bool in = lane < nloc;
     const int p = p0 + (in ? lane : 0);
-    const uint32_t nk = un.qnode[p];
-    const uint32_t key = un.qraw ? node_key(nk) : nk;
-    const uint32_t io = un.qorig ? (uint32_t)un.qorig[p] : (uint32_t)p;
-    const float2 xq = un.qxy[p];
-    float F[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = A.pair_F[9 * (size_t)un.item + k];
+    const uint32_t nk = q.nk, io = q.io;
+    const float2 xq = q.xq;
+    const bool el = q.el >= 0 ? q.el != 0 : (A.masks[w.a + io] != 0);
+    const uint32_t key = w.qraw ? node_key(nk) : nk;
     const uint32_t b = key >> (32 - kBucketBits);
-    const int bs = T.bstart[b], be = T.bstart[b + 1];
-    const bool el = un.qmask == kNone || A.masks[un.qmask + io];
+    int lo = bst[b];
+    const int be = bst[b + 1];
+    while (lo < be && tkey[lo] < key) ++lo;
+    int hi = lo;
+    while (hi < be && tkey[hi] == key) ++hi;
     const Line l = epi_line(F, xq.x, xq.y);
-    // entries of this lane's query, numbered across the warp
-    const int c = (in && el) ? be - bs : 0;
+    const int c = el ? hi - lo : 0;
     int off = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -774,7 +675,6 @@ __device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit 
     off -= c;  // exclusive
     st[lane] = make_uint2(kNone, 0xFFFFu);
     __syncwarp();
-    const uint8_t *tel = A.tmask_n ? A.tmask_n + un.t_off : nullptr;
     const bool epi = A.sp.epipolar != 0;
     for (int k0 = 0; k0 < total; k0 += 32) {
         const int k = k0 + lane;
@@ -785,24 +685,22 @@ __device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit 
             const int oi = __shfl_sync(kFull, off, (i + s2) & 31);
             if (i + s2 < 32 && oi <= k) i += s2;
         }
-        const int j0 = __shfl_sync(kFull, bs, i) + (k - __shfl_sync(kFull, off, i));
-        const uint32_t ky = __shfl_sync(kFull, key, i);
+        const int j0 = __shfl_sync(kFull, lo, i) + (k - __shfl_sync(kFull, off, i));
         Line li;
-        li.a = __shfl_sync(kFull, l.a, i); li.b = __shfl_sync(kFull, l.b, i); li.c = __shfl_sync(kFull, l.c, i);
-        const bool valid = k < total;
-        const int j = valid ? j0 : 0;            // (valid indices for the speculative loads:
-        const int pq = p0 + (valid ? i : 0);     //  past the last entry, i may name no query)
-        const uint4 a0 = un.qdesc[2 * pq], a1 = un.qdesc[2 * pq + 1];
-        const uint32_t tk = T.node[j];
-        const uint8_t te = tel ? tel[j] : (uint8_t)1;
-        const uint4 t0 = T.desc[2 * j], t1 = T.desc[2 * j + 1];
-        const float2 xt = T.xy[j];
-        const int lv = T.level[j];
+        li.a = __shfl_sync(kFull, l.a, i);
+        li.b = __shfl_sync(kFull, l.b, i);
+        li.c = __shfl_sync(kFull, l.c, i);
+        const bool valid = k < total && tel[j0];  // (j0 is a candidate only when k < total)
         uint32_t bk = kNone, sc = 0xFFFFu;
-        if (valid && tk == ky && te) {
+        if (valid) {
+            const int pq = p0 + i;
+            const uint4 a0 = w.qdesc[2 * pq], a1 = w.qdesc[2 * pq + 1];
+            const uint4 t0 = T.desc[2 * j0], t1 = T.desc[2 * j0 + 1];
+            const float2 xt = T.xy[j0];
+            const int lv = T.level[j0];
             ++cmp;
             const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
-            if (!epi || epi_pass(li, xt.x, xt.y, thr[lv])) bk = (d << 16) | (uint32_t)j;
+            if (!epi || epi_pass(li, xt.x, xt.y, thr[lv])) bk = (d << 16) | (uint32_t)j0;
         }
         // segmented merge over the lanes of each query (suffix within the segment)
 #pragma unroll
@@ -813,7 +711,7 @@ __device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit 
             if (lane + s2 < 32 && oi == i) merge_best2(bk, sc, ob, os);
         }
         const int prev = __shfl_up_sync(kFull, i, 1);
-        if (valid && (lane == 0 || prev != i)) {
+        if (k < total && (lane == 0 || prev != i)) {
             uint2 v = st[i];
             merge_best2(v.x, v.y, bk, sc);
             st[i] = v;
@@ -822,7 +720,7 @@ __device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit 
     }
     if (in) {
         const uint2 v = st[lane];
-        uint32_t acc = kNone;
+        uint32_t a = kNone;
         if (v.x != kNone) {
             const uint32_t best = v.x >> 16;
             bool ok = (int)best <= A.sp.hamming_max;
@@ -830,39 +728,184 @@ __device__ __forceinline__ void match_group_flat(const BatchArgs &A, const Unit 
                 ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * v.y;
             if (ok) {
                 const uint32_t j = v.x & 0xFFFFu;
-                acc = (j << 16) | best;
-                if (A.sp.resolve) atomicMin(&A.win[un.t_off + j], (best << 16) | io);
+                a = (j << 16) | best;
+                if (A.sp.resolve) atomicMin(&win[j], (best << 16) | io);
             }
         }
-        A.acc[un.res_off + p0 + lane] = acc;
+        acc[p] = a;
     }
     __syncwarp();
 }
 
-template <int G>
-__global__ void __launch_bounds__(256, 4) match_kernel(BatchArgs A) {
-    __shared__ float thr[kLevels];  // epipolar threshold chi2 * sigma^2 of each level
-    __shared__ uint2 qstate[8][32]; // per warp: (best key, second distance) of its 32 queries
-    if (threadIdx.x < kLevels) {
-        const float s = level_scale(threadIdx.x);
-        thr[threadIdx.x] = fmul(A.sp.epi_chi2, fmul(s, s));
+constexpr int kSearchMaxWarps = 16;
+
+// One CTA per (new keyframe, neighbour) pair, largest pairs first (Sec. IV-C, all of S1-S6):
+//   setup    the neighbour's node keys and bucket table into shared memory (bulk copies);
+//            F by nine lanes of warp 0 (float64); winners reset; the neighbour's eligibility
+//            gathered into node order;
+//   search   warps take 32-query groups (search_group);
+//   finalize each query's accepted match is kept only if it is its target's winner; kept
+//            matches are binned by rotation, the top-3 bins kept, and the pair compacted in
+//            caller query order into its output region.
+// Comparisons (and a timed-out bulk copy) are recorded per item for the copy kernel.
+__global__ void __launch_bounds__(256, 4) search_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) unsigned char ssm[];
+    __shared__ float F[9];
+    __shared__ float thr[kLevels];
+    __shared__ uint2 qst[kSearchMaxWarps][32];
+    __shared__ uint32_t hist[32];
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t keep, scmp;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ bool ok_all;
+    const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
+    const uint32_t i = A.porder[blockIdx.x];
+    const WorkItem w = A.items[i];
+    const SearchStage S = SearchStage::make(A.sn);
+    uint32_t *tkey = reinterpret_cast<uint32_t *>(ssm + S.tkey);
+    uint16_t *bst = reinterpret_cast<uint16_t *>(ssm + S.bst);
+    uint32_t *win = reinterpret_cast<uint32_t *>(ssm + S.win);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(ssm + S.acc);
+    uint8_t *tel = ssm + S.tel;
+    const KfView T = KfView::at(w.t, A.L);
+    const int nQ = (int)w.nq, nT = (int)w.nt;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
+        mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes);
+        if (kb) bulk_g2s(tkey, T.node, kb, &bar);
+        bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
+        scmp = 0u;
+    }
+    if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid < kLevels) {
+        const float sc = level_scale(tid);
+        thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
+    }
+    if (tid < 32) hist[tid] = 0u;
+    QLoad cur = {};
+    if (wid * 32 < nQ) cur = load_group(A, w, wid);  // the first group's loads overlap the setup
+    constexpr int U = 8;  // targets per thread and pass: all their loads in flight together
+    for (int j0 = 0; j0 < nT; j0 += U * bs) {
+        uint32_t o[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int j = j0 + k * bs + tid;
+            o[k] = (w.b != kNone && j < nT) ? T.orig[j] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int j = j0 + k * bs + tid;
+            if (j < nT) {
+                win[j] = kNone;
+                tel[j] = w.b == kNone ? 1 : (A.masks[w.b + o[k]] != 0);
+            }
+        }
     }
     __syncthreads();
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    uint2 *st = qstate[(threadIdx.x >> 5) & 7];
-    uint32_t cs = 0;
-    Unit un{};
-    if (warp < A.n_units) un = A.units[warp];
-    for (uint32_t u = warp; u < A.n_units; u += warps) {
-        Unit nx{};  // the next unit's record, loaded while this one is searched
-        if (u + warps < A.n_units) nx = A.units[u + warps];
-        if (G == 1) match_group_flat(A, un, thr, st, cs);
-        else match_group<G>(A, un, thr, cs);
-        un = nx;
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (tid == 0) ok_all = true;
+    __syncthreads();
+    if (!ok) ok_all = false;
+    __syncthreads();
+    if (!ok_all) {
+        if (tid == 0) {
+            A.counts[i] = 0u;
+            A.item_cmp[i] = kItemTimeout;
+        }
+        return;
     }
-    const uint32_t s = __reduce_add_sync(kFull, cs);
-    if ((threadIdx.x & 31u) == 0 && s) atomicAdd(&A.ncmp[0], (unsigned long long)s);
+    uint32_t cmp = 0;
+    for (int g = wid; g * 32 < nQ; g += nw) {
+        QLoad nxt = {};
+        if ((g + nw) * 32 < nQ) nxt = load_group(A, w, g + nw);
+        search_group(A, w, T, F, thr, tkey, bst, tel, win, acc, qst[wid], g, cur, cmp);
+        cur = nxt;
+    }
+    warp_count(cmp, &scmp);
+    __syncthreads();
+    // finalize: one match per target, rotation histogram (results by caller index in tkey[])
+    uint32_t *fres = tkey;
+    const bool rot = A.sp.rot_filter != 0;
+    constexpr int V = 4;  // queries per thread and pass
+    for (int p0 = 0; p0 < nQ; p0 += V * bs) {
+        uint32_t ac[V], io[V], to[V];
+        float qa[V], ta[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int p = p0 + k * bs + tid;
+            ac[k] = p < nQ ? acc[p] : kNone;
+            io[k] = p < nQ ? (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int p = p0 + k * bs + tid;
+            const uint32_t j = ac[k] >> 16;
+            const bool a = ac[k] != kNone && (!A.sp.resolve || win[j] == (((ac[k] & 0xFFFFu) << 16) | io[k]));
+            if (!a) ac[k] = kNone;
+            to[k] = a ? (uint32_t)T.orig[j] : 0u;
+            qa[k] = (a && rot) ? w.qangle[p] : 0.0f;
+            ta[k] = (a && rot) ? T.angle[j] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int p = p0 + k * bs + tid;
+            uint32_t bin = kNone;
+            if (p < nQ) {
+                uint32_t r = kNone;
+                if (ac[k] != kNone) {
+                    bin = rot ? (uint32_t)rot_bin(qa[k], ta[k]) : 0u;
+                    r = pack_res(to[k], ac[k] & 0xFFFFu, bin);
+                }
+                fres[io[k]] = r;
+            }
+            if (rot) {
+                const unsigned peers = __match_any_sync(kFull, bin);
+                if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
+                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const uint32_t k = rot ? top3_mask_warp(hist) : kNone;
+        if (tid == 0) keep = k;
+    }
+    __syncthreads();
+    // ordered compaction: warp k owns caller indices [k*per, (k+1)*per); a count pass, a scan
+    // of the warp totals, a write pass
+    const int lane = tid & 31, per = (((nQ + nw - 1) / nw) + 31) & ~31;
+    const int qb = wid * per, qe = min(qb + per, nQ);
+    uint32_t wc = 0;
+    for (int q0 = qb; q0 < qe; q0 += 32) {
+        const int q = q0 + lane;
+        const uint32_t r = q < qe ? fres[q] : kNone;
+        wc += __popc(__ballot_sync(kFull, r != kNone && ((keep >> (r & 31u)) & 1u)));
+    }
+    if (lane == 0) wtot[wid] = wc;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (int k = 0; k < nw; ++k) {
+        const uint32_t v = wtot[k];
+        if (k < wid) base += v;
+        total += v;
+    }
+    for (int q0 = qb; q0 < qe; q0 += 32) {
+        const int q = q0 + lane;
+        const uint32_t r = q < qe ? fres[q] : kNone;
+        const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
+        const unsigned m = __ballot_sync(kFull, f);
+        if (f) {
+            const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+            A.padded[w.out_off + pos] = Out3{q, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
+        }
+        base += __popc(m);
+    }
+    if (tid == 0) {
+        A.counts[i] = total;
+        A.item_cmp[i] = scmp;
+    }
 }
 
 // ---------------------------------------------------------------- fusion (S7-S9)
@@ -910,7 +953,10 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     if (!ok) ok_all = false;
     __syncthreads();
     if (!ok_all) {
-        if (tid == 0) atomicOr(&A.counters[2], kStatusTimeout);
+        if (tid == 0) {
+            A.counts[item] = 0u;
+            A.item_cmp[item] = kItemTimeout;
+        }
         return;
     }
     KfView T = Tg;
@@ -929,95 +975,14 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     if (r != kNone) A.padded[w.out_off + pos] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
     if (tid == 0) {
         A.counts[item] = tot;
-        if (scmp) atomicAdd(&A.ncmp[1], (unsigned long long)scmp);
-    }
-}
-
-// ---------------------------------------------------------------- finalize (S4-S6)
-
-// One pair per CTA: the accepted query of each target keeps it only if it is the target's
-// winner; kept matches are binned by rotation, the top-3 bins kept, the pair compacted in
-// caller query order.
-__global__ void __launch_bounds__(256) finalize_kernel(BatchArgs A) {
-    extern __shared__ __align__(16) uint32_t fres[];  // [sn] per caller-order query
-    __shared__ uint32_t hist[32];
-    __shared__ uint32_t wtot[32];
-    __shared__ uint32_t keep;
-    const int tid = threadIdx.x, bs = blockDim.x;
-    {
-        const uint32_t i = blockIdx.x;
-        const WorkItem w = A.items[i];
-        const SlotLayout &L = A.L;
-        const KfView T = KfView::at(w.t, L);
-        const int nQ = (int)w.nq;
-        const bool rot = A.sp.rot_filter != 0;
-        if (tid < 32) hist[tid] = 0;
-        __syncthreads();
-        constexpr int U = 4;  // queries per thread and pass: all their loads in flight together
-        for (int p0 = 0; p0 < nQ; p0 += U * bs) {
-            uint32_t acc[U], io[U], wv[U], to[U];
-            float qa[U], ta[U];
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int p = p0 + k * bs + tid;
-                acc[k] = p < nQ ? A.acc[w.res_off + p] : kNone;
-                io[k] = p < nQ ? (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p) : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int p = p0 + k * bs + tid;
-                const uint32_t j = acc[k] >> 16;
-                const bool a = acc[k] != kNone;
-                wv[k] = (a && A.sp.resolve) ? A.win[w.t_off + j] : 0u;
-                to[k] = a ? (uint32_t)T.orig[j] : 0u;
-                qa[k] = (a && rot) ? w.qangle[p] : 0.0f;
-                ta[k] = (a && rot) ? T.angle[j] : 0.0f;
-            }
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int p = p0 + k * bs + tid;
-                uint32_t bin = kNone;
-                if (p < nQ) {
-                    uint32_t r = kNone;
-                    if (acc[k] != kNone) {
-                        const uint32_t d = acc[k] & 0xFFFFu;
-                        if (!A.sp.resolve || wv[k] == ((d << 16) | io[k])) {
-                            bin = rot ? (uint32_t)rot_bin(qa[k], ta[k]) : 0u;
-                            r = pack_res(to[k], d, bin);
-                        }
-                    }
-                    fres[io[k]] = r;
-                }
-                if (rot) {
-                    const unsigned peers = __match_any_sync(kFull, bin);
-                    if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
-                        atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-                }
-            }
-        }
-        __syncthreads();
-        if (tid < 32) {
-            const uint32_t k = rot ? top3_mask_warp(hist) : kNone;
-            if (tid == 0) keep = k;
-        }
-        __syncthreads();
-        uint32_t base = 0;
-        for (int i0 = 0; i0 < nQ; i0 += bs) {
-            const int q = i0 + tid;
-            const uint32_t r = q < nQ ? fres[q] : kNone;
-            const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
-            uint32_t tot;
-            const uint32_t pos = block_scan_flag(f, wtot, tot);
-            if (f) A.padded[w.out_off + base + pos] = Out3{q, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
-            base += tot;
-        }
-        if (tid == 0) A.counts[i] = base;
+        A.item_cmp[item] = scmp;
     }
 }
 
 // Per-item counts -> offsets, and the per-item regions gathered into the dense output.  Every
 // CTA scans the counts itself (a few thousand words, read from L2), segment by segment, so
-// that no CTA waits for another; CTA 0 publishes the offsets.  Warps copy items.
+// that no CTA waits for another; CTA 0 publishes the offsets, the comparison totals (search,
+// fusion) and the status of the run.  Warps copy items.
 constexpr int kCopyThreads = 1024;
 constexpr int kCopySeg = 8192;  // items per scan segment (offsets held in shared memory)
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
@@ -1026,12 +991,22 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
     const int tid = threadIdx.x, bs = blockDim.x;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nw = bs >> 5;
     const uint32_t gw = blockIdx.x * nw + wid, gws = gridDim.x * nw;
+    __shared__ unsigned long long csum[2][32];
+    __shared__ uint32_t sflags;
     uint32_t base = 0;
+    unsigned long long cs = 0, cf = 0;  // comparisons of search and fusion items (CTA 0)
+    uint32_t flags = 0;
     for (uint32_t s0 = 0; s0 < A.n_items; s0 += kCopySeg) {
         const uint32_t ns = min((uint32_t)kCopySeg, A.n_items - s0);
         const uint32_t per = (ns + bs - 1) / bs, cb = min(tid * per, ns), ce = min(cb + per, ns);
         uint32_t sum = 0;
         for (uint32_t k = cb; k < ce; ++k) sum += A.counts[s0 + k];
+        if (blockIdx.x == 0)
+            for (uint32_t k = cb; k < ce; ++k) {
+                const uint32_t v = A.item_cmp[s0 + k];
+                flags |= v & kItemTimeout;
+                if (s0 + k < A.n_search) cs += v & ~kItemTimeout; else cf += v & ~kItemTimeout;
+            }
         uint32_t total;
         uint32_t run = block_scan_add(sum, wtot, total) + base;
         for (uint32_t k = cb; k < ce; ++k) {
@@ -1049,7 +1024,29 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
         base += total;
         __syncthreads();
     }
-    if (blockIdx.x == 0 && tid == 0) A.offsets[A.n_items] = base;
+    if (blockIdx.x == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            cs += __shfl_down_sync(kFull, cs, o);
+            cf += __shfl_down_sync(kFull, cf, o);
+        }
+        flags = __reduce_or_sync(kFull, flags);
+        if (tid == 0) sflags = 0u;
+        if ((tid & 31) == 0) {
+            csum[0][wid] = cs;
+            csum[1][wid] = cf;
+        }
+        __syncthreads();
+        if ((tid & 31) == 0 && flags) atomicOr(&sflags, flags);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long a = 0, b = 0;
+            for (uint32_t q = 0; q < nw; ++q) { a += csum[0][q]; b += csum[1][q]; }
+            A.ncmp[0] = a;
+            A.ncmp[1] = b;
+            A.counters[2] = sflags ? kStatusTimeout : 0u;
+            A.offsets[A.n_items] = base;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------- plain form
@@ -1226,70 +1223,58 @@ __global__ void fuse_compact_kernel(const uint32_t *res, int n, Out3 *dense, uin
 
 size_t ingest_smem_bytes(int cap) { return 18 * ingest_pow2(cap); }
 
-cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
+// Launch with a scheduling priority (cudaLaunchAttributePriority; kept by stream capture in
+// the graph's kernel node): when SMs free up, CTAs of higher-priority kernels are placed
+// first.  prio 0 = the stream's default.
+template <typename... Args>
+static cudaError_t launch_prio(void (*k)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               int prio, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = prio ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {
     if (a.n_jobs <= 0) return cudaSuccess;
     const size_t smem = ingest_smem_bytes(a.cap);
     cudaError_t e = cudaFuncSetAttribute(ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    ingest_kernel<<<a.n_jobs, kIngestThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_prio(ingest_kernel, dim3(a.n_jobs), dim3(kIngestThreads), smem, s, prio, a);
 }
 
-cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s) {
-    prep_kernel<<<a.n_search > 0 ? a.n_search : 1, kPrepThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
+size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 
-template <int G>
-static cudaError_t launch_match_g(const BatchArgs &a, int ctas, cudaStream_t s) {
-    match_kernel<G><<<ctas, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-int match_ctas_per_sm(int lanes) {
+int search_ctas_per_sm(int threads, int sn) {
     int n = 0;
-    cudaError_t e;
-    switch (lanes) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<1>, 256, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<2>, 256, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<4>, 256, 0); break;
-        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<8>, 256, 0); break;
-        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<16>, 256, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, match_kernel<32>, 256, 0); break;
-    }
-    return e == cudaSuccess ? n : 0;
+    const size_t smem = search_smem_bytes(sn);
+    if (cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel, threads, smem) == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_match(const BatchArgs &a, int ctas, cudaStream_t s) {
-    if (a.n_units == 0) return cudaSuccess;
-    switch (a.lanes) {
-        case 1: return launch_match_g<1>(a, ctas, s);
-        case 2: return launch_match_g<2>(a, ctas, s);
-        case 4: return launch_match_g<4>(a, ctas, s);
-        case 8: return launch_match_g<8>(a, ctas, s);
-        case 16: return launch_match_g<16>(a, ctas, s);
-        default: return launch_match_g<32>(a, ctas, s);
-    }
+cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio) {
+    if (a.n_search == 0) return cudaSuccess;
+    const size_t smem = search_smem_bytes(a.sn);
+    cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_prio(search_kernel, dim3(a.n_search), dim3(threads), smem, s, prio, a);
 }
 
-cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s) {
+cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio) {
     const uint32_t blocks = a.n_items - a.n_search;
     if (blocks == 0) return cudaSuccess;
     const size_t smem = FuseStage::make((int)a.fsn).bytes;
     cudaError_t e = cudaFuncSetAttribute(fuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fuse_kernel<<<blocks, kFuseChunk, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const BatchArgs &a, cudaStream_t s) {
-    const size_t smem = size_t(4) * (size_t)a.sn;
-    cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (a.n_search == 0) return cudaSuccess;
-    finalize_kernel<<<a.n_search, 256, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_prio(fuse_kernel, dim3(blocks), dim3(kFuseChunk), smem, s, prio, a);
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {

@@ -10,15 +10,15 @@ namespace tmap {
 // Keyframe ingest: one CTA per keyframe sorts its keypoints by BoW node and builds the
 // projection-grid index inside its slot.
 size_t ingest_smem_bytes(int cap);
-cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
+// prio: scheduling priority of the launch (0 = the stream's; lower numbers are higher
+// priority, within cudaDeviceGetStreamPriorityRange).
+cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio = 0);
 
-// Batch pipeline: prep (per pair: F, winners, target eligibility), match (warp units: join
-// and search), fuse (per 256 map points), finalize (per pair, offsets), copy (dense output).
-cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s);
-int match_ctas_per_sm(int lanes);
-cudaError_t launch_match(const BatchArgs &a, int ctas, cudaStream_t s);
-cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s);
-cudaError_t launch_finalize(const BatchArgs &a, cudaStream_t s);
+// Batch pipeline: search (CTA per pair), fuse (CTA per 256 map points), copy.
+size_t search_smem_bytes(int sn);
+int search_ctas_per_sm(int threads, int sn);
+cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio = 0);
+cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
 
 // Plain per-pair form: every stage of one pair is its own launch, with global scratch.

@@ -107,46 +107,54 @@ struct IngestArgs {
 enum : uint32_t { kItemSearch = 0, kItemFuse = 1 };
 // Device status word bits.
 enum : uint32_t { kStatusTimeout = 1u };
+constexpr uint32_t kItemTimeout = 0x80000000u;  // item_cmp flag: a bounded wait ran out
 
 // An output item: a (new keyframe, neighbour) pair of a step, or up to kFuseChunk map points
-// of a step fused into the step's new keyframe.
+// of a step fused into the step's new keyframe.  The query keyframe of a pair is read where it
+// is: a stored keyframe from its slot (positions in node-key order, keys stored, `qorig` maps a
+// position to the caller's index), a keyframe entering with the batch from its staged
+// caller-order arrays (raw node ids, identity order), so that the search need not wait for its
+// ingest.
 struct WorkItem {
-    const unsigned char *q;  // search: new keyframe slot; fuse: target keyframe slot
-    const unsigned char *t;  // search: neighbour slot; fuse: unused
+    const unsigned char *q;  // fuse: target keyframe slot
+    const unsigned char *t;  // search: neighbour slot
     const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
-                             // keyframe entering with the batch, so that F does not wait for it)
-    const float *qangle;     // search: Q's angles in the order the search visits Q (below)
-    const uint16_t *qorig;   // search: caller index of each visited position, or null (identity)
+                             // keyframe entering with the batch)
+    const uint4 *qdesc;      // search: Q's arrays in the order the search visits Q
+    const float2 *qxy;
+    const uint32_t *qnode;   //   node keys, or raw node ids if qraw
+    const uint16_t *qorig;   //   caller index of each position, or null (identity)
+    const float *qangle;
+    uint32_t qraw;
     uint32_t kind;
     uint32_t out_off;        // first entry of this item's region in the padded output
     uint32_t a;              // search: byte offset of q mask (kNone: all free); fuse: first mp
     uint32_t b;              // search: byte offset of t mask;                   fuse: mp count
     uint32_t c;              // fuse: first mp of the step (output mp_idx = m - c)
     uint32_t nq, nt;         // search: keypoint counts
-    uint32_t res_off;        // search: first per-query entry (range, accepted match)
-    uint32_t t_off;          // search: first per-target entry (winner, eligibility)
-    uint32_t step;           // fuse: step index (target constants)
+    uint32_t step;           // fuse: step index
     uint32_t cost;           // scheduling estimate
-    uint32_t pad;
 };
 
-// A unit of the match kernel, one warp: 32 queries of a search item, with what the warp needs
-// of the item (so that it reads one record).  The queries are read where they are: a stored
-// keyframe from its slot (node order, keys stored, `qorig` maps back), a keyframe entering with
-// the batch from the staged caller-order arrays (raw node ids, identity order), so that the
-// search need not wait for its ingest.
-struct Unit {
-    const unsigned char *t;      // neighbour slot
-    const uint4 *qdesc;          // [nq][2]
-    const float2 *qxy;
-    const uint32_t *qnode;       // node keys, or raw node ids if qraw
-    const uint16_t *qorig;       // caller index of each position, or null (identity)
-    uint32_t item;
-    uint32_t group;              // queries 32*group ..
-    uint32_t nq, nt;
-    uint32_t res_off, t_off;
-    uint32_t qmask;              // byte offset of Q's eligibility mask, or kNone
-    uint32_t qraw;
+constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;
+
+// Shared-memory carve of a search CTA (one pair) for a capacity of sn keypoints (a multiple
+// of 32): the neighbour's node keys and bucket table (bulk copies), its per-target winners and
+// eligibility, the per-query accepted matches; after the search the key array holds the
+// per-caller-query results.
+struct SearchStage {
+    size_t tkey, bst, win, acc, tel, bytes;
+    __host__ __device__ static constexpr SearchStage make(int sn) {
+        SearchStage L{};
+        size_t o = 0;
+        L.tkey = o; o = align128(o + size_t(sn) * 4);
+        L.bst = o;  o = align128(o + kBucketTableBytes);
+        L.win = o;  o = align128(o + size_t(sn) * 4);
+        L.acc = o;  o = align128(o + size_t(sn) * 4);
+        L.tel = o;  o = align128(o + size_t(sn));
+        L.bytes = o;
+        return L;
+    }
 };
 
 // Shared-memory carve of a fusion CTA: the target keyframe's grid and the keypoint arrays the
@@ -204,15 +212,14 @@ struct CamConst {
 
 struct Out3 { int32_t a, b, c; };
 
-// Arguments of the batch kernels (prep, match, fuse, finalize, copy).
+// Arguments of the batch kernels (search, fuse, copy).
 struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
     uint32_t n_items;
     uint32_t n_search;            // search items come first
-    const Unit *units;            // match kernel work list
-    uint32_t n_units;
-    uint32_t fsn;                 // fusion kernel stage capacity (largest target, rounded to 16)
-    uint32_t *counters;           // [0] spare, [1] finalize CTAs done, [2] status
+    const uint32_t *porder;       // search CTA b takes item porder[b] (largest pairs first)
+    uint32_t fsn;                 // fusion stage capacity (largest target, rounded to 16)
+    uint32_t *counters;           // [2] status of the last run (kStatusTimeout)
     const uint8_t *masks;         // caller-order eligibility masks
     const float *mp_pos, *mp_normal, *mp_min, *mp_max;
     uint32_t n_mp;                // map points of the batch
@@ -220,20 +227,17 @@ struct BatchArgs {
     const uint8_t *mp_skip;
     Out3 *padded;                 // per-item regions
     uint32_t *counts;             // [n_items]
+    uint32_t *item_cmp;           // [n_items] comparisons of the item | kItemTimeout
     uint32_t *offsets;            // [n_items + 1] exclusive scan of counts
-    unsigned long long *ncmp;     // [2] search, fuse comparisons
+    unsigned long long *ncmp;     // [2] search, fuse comparisons (written by copy)
     Out3 *dense;                  // compacted output
-    float *pair_F;                // [n_search][9] fundamental matrix of each pair
-    uint32_t *acc;                // per query (node order): accepted (target << 16 | dist)
-    uint32_t *win;                // per target (node order): winner (dist << 16 | query)
-    uint8_t *tmask_n;             // per target (node order): eligible, or null if no masks
     SearchConst sp;
     FuseConst fp;
     CamConst cam;
     int32_t cap;                  // slot capacity (keypoints)
     SlotLayout L;                 // array offsets of a slot of that capacity
-    int32_t lanes;                // lanes per query
-    int32_t sn;                   // largest keypoint count of the batch's pairs (rounded to 32)
+    int32_t sn;                   // search stage capacity: largest keypoint count of the batch's
+                                  // pairs, rounded to 32
 };
 
 }  // namespace tmap

@@ -395,9 +395,8 @@ void BatchBuf::release() {
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
-    for (DevBuf *b : {&items, &units, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &offsets, &ncmp, &counters, &dense, &scratch, &pair_F,
-                      &acc, &win, &tmask_n})
+    for (DevBuf *b : {&items, &porder, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch})
         b->release();
     h_stage.release();
     h_out.release();
@@ -532,7 +531,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     };
     B.nbr_new = false;
     std::vector<WorkItem> &items = B.h_items;
-    std::vector<QView> item_qv;
+
     items.clear();
     B.item_nq.clear();
     B.item_nt.clear();
@@ -540,7 +539,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.step_pair_begin.assign(n_steps + 1, 0);
     B.step_fuse_item.assign(n_steps + 1, 0);
     B.n_pairs = 0;
-    uint32_t pad = 0, res_off = 0, t_off = 0;
+    uint32_t pad = 0;
     int smem_n = 32;
     auto slot_of = [&](uint64_t id, int &slot) -> tm_status {
         auto it = c->ids.find(id);
@@ -548,7 +547,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         slot = it->second;
         return TM_OK;
     };
-    bool any_mask = false;
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
         int qs;
@@ -571,9 +569,12 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.pq = pose_of(qs);
             w.pt = pose_of(ts);
             const QView qv = qview_of(qs);
-            w.qangle = qv.angle;
+            w.qdesc = qv.desc;
+            w.qxy = qv.xy;
+            w.qnode = qv.node;
             w.qorig = qv.orig;
-            item_qv.push_back(qv);
+            w.qangle = qv.angle;
+            w.qraw = qv.raw;
             B.nbr_new |= new_index.count(ts) != 0;
             w.kind = kItemSearch;
             w.out_off = pad;
@@ -581,13 +582,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.b = S.nbr_free_off >= 0 ? (uint32_t)toff : kNone;
             w.nq = (uint32_t)nq;
             w.nt = (uint32_t)nt;
-            w.res_off = res_off;
-            w.t_off = t_off;
             w.cost = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, (uint64_t)nq + nt + (uint64_t)nq * nt / 256);
-            any_mask |= w.b != kNone;
             pad += (uint32_t)(sp.resolve ? std::min(nq, nt) : nq);
-            res_off += (uint32_t)nq;
-            t_off += (uint32_t)nt;
             smem_n = std::max(smem_n, std::max(nq, nt));
             items.push_back(w);
             B.item_nq.push_back(nq);
@@ -628,21 +624,11 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.total_pad = pad;
     B.smem_n = (smem_n + 31) & ~31;
     B.slots = slots_used;
-    B.res_total = res_off;
-    B.t_total = t_off;
-    // match-kernel units: query groups of the pairs, largest pairs first, then fusion items
+    // search CTAs take the pairs largest first
     std::vector<uint32_t> order(B.n_search_items);
     for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t x, uint32_t y) { return items[x].cost > items[y].cost; });
-    std::vector<Unit> units;
-    for (uint32_t i : order) {
-        const WorkItem &w = items[i];
-        for (uint32_t g = 0; g * kQueryGroup < w.nq; ++g)
-            units.push_back(Unit{w.t, item_qv[i].desc, item_qv[i].xy, item_qv[i].node, item_qv[i].orig, i, g,
-                                 w.nq, w.nt, w.res_off, w.t_off, w.a, item_qv[i].raw});
-    }
-    B.n_units = (uint32_t)units.size();
     // fusion stage: the largest target of the batch
     int fuse_n = 0;
     for (uint32_t i = B.n_search_items; i < items.size(); ++i)
@@ -651,38 +637,35 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     // device buffers
     const size_t ni = std::max<size_t>(1, items.size());
     const size_t nm = std::max<int>(1, mps.n);
-    const size_t nu = std::max<size_t>(1, units.size());
     const size_t nsi = std::max<size_t>(1, B.n_search_items);
-    const size_t nres = std::max<size_t>(1, res_off), ntt = std::max<size_t>(16, t_off);
     cudaError_t e;
     std::vector<void *> before = B.pointers();
-    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.units.reserve(nu * sizeof(Unit))) ||
-        (e = B.counts.reserve(ni * 4)) || (e = B.offsets.reserve((ni + 1) * 4)) ||
+    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.porder.reserve(nsi * 4)) ||
+        (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
+        (e = B.offsets.reserve((ni + 1) * 4)) ||
         (e = B.ncmp.reserve(16)) || (e = B.counters.reserve(16)) ||
         (e = B.padded.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
         (e = B.dense.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
         (e = B.masks.reserve(std::max<size_t>(16, mask_bytes))) ||
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
-        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (e = B.pair_F.reserve(nsi * 9 * sizeof(float))) ||
-        (e = B.acc.reserve(nres * 4)) || (e = B.win.reserve(ntt * 4)) ||
-        (e = B.tmask_n.reserve(ntt)))
+        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)))
         return cuda_fail(e, "batch buffers");
     if (B.pointers() != before && (B.graph || B.graph_timed)) {
         if (B.graph) cudaGraphExecDestroy(B.graph);
         if (B.graph_timed) cudaGraphExecDestroy(B.graph_timed);
         B.graph = B.graph_timed = nullptr;
     }
-    // one pinned staging area, one transfer per table: items, units
-    const size_t o_units = align128(ni * sizeof(WorkItem));
-    const size_t stage = o_units + nu * sizeof(Unit);
+    // one pinned staging area, one transfer per table: items, pair order
+    const size_t o_order = align128(ni * sizeof(WorkItem));
+    const size_t stage = o_order + nsi * 4;
     if ((e = B.h_stage.reserve(stage))) return cuda_fail(e, "pinned staging");
     unsigned char *h = static_cast<unsigned char *>(B.h_stage.p);
     if (!items.empty()) memcpy(h, items.data(), items.size() * sizeof(WorkItem));
-    if (!units.empty()) memcpy(h + o_units, units.data(), units.size() * sizeof(Unit));
+    if (!order.empty()) memcpy(h + o_order, order.data(), order.size() * 4);
     if ((e = cudaMemcpyAsync(B.items.p, h, items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(B.units.p, h + o_units, units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s)))
+        (!order.empty() &&
+         (e = cudaMemcpyAsync(B.porder.p, h + o_order, order.size() * 4, cudaMemcpyHostToDevice, s))))
         return cuda_fail(e, "work list upload");
     if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
         return cuda_fail(e, "mask upload");
@@ -701,8 +684,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.items = static_cast<const WorkItem *>(B.items.p);
     A.n_items = B.n_items;
     A.n_search = B.n_search_items;
-    A.units = static_cast<const Unit *>(B.units.p);
-    A.n_units = B.n_units;
+    A.porder = static_cast<const uint32_t *>(B.porder.p);
     A.counters = static_cast<uint32_t *>(B.counters.p);
     A.masks = static_cast<const uint8_t *>(B.masks.p);
     A.mp_pos = static_cast<const float *>(B.mp_pos.p);
@@ -717,10 +699,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.offsets = static_cast<uint32_t *>(B.offsets.p);
     A.ncmp = static_cast<unsigned long long *>(B.ncmp.p);
     A.dense = static_cast<Out3 *>(B.dense.p);
-    A.pair_F = static_cast<float *>(B.pair_F.p);
-    A.acc = static_cast<uint32_t *>(B.acc.p);
-    A.win = static_cast<uint32_t *>(B.win.p);
-    A.tmask_n = any_mask ? static_cast<uint8_t *>(B.tmask_n.p) : nullptr;
+    A.item_cmp = static_cast<uint32_t *>(B.item_cmp.p);
     A.fsn = B.fsn;
     A.sp = to_const(sp);
     A.fp.chi2 = fp.chi2;
@@ -737,9 +716,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 }
 
 std::vector<void *> BatchBuf::pointers() const {
-    return {items.p, units.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, offsets.p, ncmp.p, counters.p, dense.p, pair_F.p,
-            acc.p, win.p, tmask_n.p};
+    return {items.p, porder.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
+            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -766,53 +744,47 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 
 // Enqueue the batch pipeline as a graph of kernels only (no memset or event nodes, which cost
 // several microseconds each inside a graph).  Two branches:
-//   search: prep (F, winners, eligibility, counters) -> match -> finalize, on `paux`; it reads
-//           new keyframes from their staged arrays, so it runs beside their ingest (unless a
-//           neighbour enters with the batch: then it starts after the ingest);
-//   store:  ingest of new keyframes -> fusion (needs their grids and prep's counters), on s;
-// joined before copy (offsets + dense output).  With `timed`, events E0..E7 mark: start, prep,
-// match, finalize done (search branch), ingest, fusion done, join, copy done.
+//   search: search_kernel (one CTA per pair) on `paux`, at high priority; it reads new keyframes
+//           from their staged arrays, so it runs beside their ingest (unless a neighbour enters
+//           with the batch: then it starts after the ingest);
+//   store:  ingest of new keyframes -> fusion (needs their grids), on s, at low priority;
+// joined before copy (offsets, dense output, comparison totals, status).  `threads` = threads
+// per search CTA.  With `timed`, events E0..E4 mark: start, search done, ingest done, fusion
+// done, copy done.
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed) {
     cudaError_t e;
-    (void)threads;  // the match kernel runs 256-thread CTAs of independent warps
-    B.args.lanes = lanes;
-    B.threads = 256;
+    B.threads = threads;
     B.lanes = lanes;
-    const int per_sm = match_ctas_per_sm(lanes);
-    if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "match kernel does not fit");
-    B.ctas = (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_units + 7) / 8, (uint32_t)(per_sm * c->num_sms)));
+    B.ctas = (int)B.n_search_items;
+    if (search_ctas_per_sm(threads, B.args.sn) < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
     if (timed && !B.ev[0])
         for (cudaEvent_t &ev : B.ev)
             if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
     if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
-                    (e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming)) ||
-                    (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming)) ||
                     (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
-                    (e = cudaEventCreateWithFlags(&B.pjoin, cudaEventDisableTiming))))
+                    (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming))))
         return cuda_fail(e, "launch branches");
     auto mark = [&](int k, cudaStream_t st) { return timed ? record_stage(B.ev[k], st) : cudaSuccess; };
+    // the search branch is the critical path: its CTAs are placed before the store branch's
+    // when SMs free up (priorities within the device's range; `hi` is numerically lowest)
+    int lo_p = 0, hi_p = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p))) return cuda_fail(e, "priorities");
     if ((e = mark(0, s))) return cuda_fail(e, "event");
     const bool after_ingest = B.n_new > 0 && B.nbr_new;
     if (!after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
-    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
-    if ((e = mark(4, s))) return cuda_fail(e, "event");
+    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, lo_p))) return cuda_fail(e, "ingest kernel");
+    if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
-    // search branch
-    if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = launch_prep(B.args, B.paux)) ||
-        (e = mark(1, B.paux)) || (e = cudaEventRecord(B.pjoin, B.paux)) ||
-        (e = launch_match(B.args, B.ctas, B.paux)) || (e = mark(2, B.paux)) ||
-        (e = launch_finalize(B.args, B.paux)) || (e = mark(3, B.paux)) ||
-        (e = cudaEventRecord(B.join, B.paux)))
-        return cuda_fail(e, "search branch");
-    // store branch: fusion after the ingest and prep's counter reset
-    if ((e = cudaStreamWaitEvent(s, B.pjoin, 0)) ||
-        (B.n_items > B.n_search_items && (e = launch_fuse(B.args, s))) || (e = mark(5, s)) ||
-        (e = cudaStreamWaitEvent(s, B.join, 0)) || (e = mark(6, s)))
+    if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = launch_search(B.args, threads, B.paux, hi_p)) ||
+        (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
+        return cuda_fail(e, "search kernel");
+    if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
+        (e = cudaStreamWaitEvent(s, B.join, 0)))
         return cuda_fail(e, "fusion kernel");
     // copy: about one warp per item (32 per CTA), at most one CTA per SM
     if ((e = launch_copy(B.args, (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_items + 31) / 32, c->num_sms)), s)))
         return cuda_fail(e, "copy kernel");
-    if ((e = mark(7, s))) return cuda_fail(e, "event");
+    if ((e = mark(4, s))) return cuda_fail(e, "event");
     return TM_OK;
 }
 
@@ -908,7 +880,6 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 
 // ------------------------------------------------------------------------- tuning
 
-static const int kTuneLanes[] = {1, 2, 4, 8, 32};
 
 // Default launch shape: 256-thread CTAs (several per SM).
 int tmap::default_threads(const BatchBuf &B) { (void)B; return 256; }
@@ -969,9 +940,10 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bt = default_threads(B), bl = c->def_lanes;
-    const int threads_set[] = {256};
+    // threads per search CTA (warps sharing one pair); lanes per query only shape the plain form
+    const int threads_set[] = {128, 256};
     for (int th : threads_set)
-        for (int ln : kTuneLanes) {
+        for (int ln : {c->def_lanes}) {
             if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
             float tot = 0.0f;
             for (int r = 0; r < 3; ++r) {
@@ -1205,10 +1177,10 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
             if (!st && (e = cudaGraphInstantiate(&x, g, 0))) st = cuda_fail(e, "graph instantiate");
             if (g) cudaGraphDestroy(g);
         }
-        // prep, match (when there are pairs), fuse (when there are map points), finalize (when
-        // there are pairs), copy, ingest (when keyframes enter with the batch)
-        P->kernels_per_run = 1 + (P->B.n_units ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
-                             (P->B.n_search_items ? 1 : 0) + 1 + (P->B.n_new ? 1 : 0);
+        // search (when there are pairs), fuse (when there are map points), copy, ingest (when
+        // keyframes enter with the batch)
+        P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
+                             1 + (P->B.n_new ? 1 : 0);
     } else {
         P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)
@@ -1276,17 +1248,15 @@ extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     for (int k = 0; k < TM_PLAN_STAGES; ++k) ms[k] = 0.0f;
     if (!P->timed_last || !P->B.ev[0]) return TM_OK;
     cudaSetDevice(P->ctx->device);
-    cudaError_t e = cudaEventSynchronize(P->B.ev[7]);
+    cudaError_t e = cudaEventSynchronize(P->B.ev[4]);
     if (e) return cuda_fail(e, "stage events");
-    float t[8] = {0};
-    for (int k = 1; k < 8; ++k)
+    float t[5] = {0};
+    for (int k = 1; k < 5; ++k)
         if ((e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k]))) return cuda_fail(e, "stage times");
-    ms[0] = t[4];                         // ingest
-    ms[1] = t[1];                         // prep
-    ms[2] = t[2] - t[1];                  // match
-    ms[3] = t[3] - t[2];                  // finalize
-    ms[4] = t[5] - std::max(t[4], t[1]);  // fusion
-    ms[5] = t[7] - t[6];                  // offsets + copy
+    ms[0] = t[1];                         // search kernel (from the start)
+    ms[1] = t[2];                         // ingest (from the start)
+    ms[2] = t[3] - t[2];                  // fusion (after the ingest)
+    ms[3] = t[4] - std::max(t[1], t[3]);  // offsets + copy (after both branches)
     return TM_OK;
 }
 

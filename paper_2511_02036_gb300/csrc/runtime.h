@@ -48,8 +48,8 @@ struct IngestStage {
 
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
-    DevBuf items, units, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, offsets, ncmp, counters, dense, scratch, pair_F, acc, win, tmask_n;
+    DevBuf items, porder, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
+        counts, item_cmp, offsets, ncmp, counters, dense, scratch;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -58,7 +58,7 @@ struct BatchBuf {
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
-    uint32_t n_items = 0, n_search_items = 0, total_pad = 0, n_units = 0;
+    uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
     uint32_t res_total = 0, t_total = 0, fsn = 16;
     int n_steps = 0, n_pairs = 0, smem_n = 32;
     int threads = 256, lanes = 1, ctas = 0;
@@ -67,7 +67,7 @@ struct BatchBuf {
     BatchArgs args{};
     cudaGraphExec_t graph = nullptr;        // kernels only
     cudaGraphExec_t graph_timed = nullptr;  // the same with events at the stage boundaries
-    cudaEvent_t ev[8] = {};                 // stage boundaries (timed graph)
+    cudaEvent_t ev[5] = {};                 // stage boundaries (timed graph)
     cudaStream_t aux = nullptr;          // (unused)
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)
