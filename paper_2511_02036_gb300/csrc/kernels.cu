@@ -748,7 +748,7 @@ constexpr int kSearchMaxWarps = 16;
 //            matches are binned by rotation, the top-3 bins kept, and the pair compacted in
 //            caller query order into its output region.
 // Comparisons (and a timed-out bulk copy) are recorded per item for the copy kernel.
-__global__ void __launch_bounds__(256, 4) search_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ float F[9];
     __shared__ float thr[kLevels];
