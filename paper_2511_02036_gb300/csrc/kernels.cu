@@ -523,15 +523,28 @@ __device__ __forceinline__ uint32_t top3_mask_warp(const uint32_t *hist) {
 
 // Fusion of one map point into keyframe T (Sec. IV-D).  Returns the packed
 // (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
+struct MapPoint {
+    float X, Y, Z, nx, ny, nz, mind, maxd;
+    uint4 d0, d1;
+};
+// Every global load of a map point, issued together.
+__device__ __forceinline__ MapPoint load_mp(const float *pos, const float *normal, const uint4 *desc,
+                                            float mind, float maxd) {
+    MapPoint q;
+    q.X = pos[0]; q.Y = pos[1]; q.Z = pos[2];
+    q.nx = normal[0]; q.ny = normal[1]; q.nz = normal[2];
+    q.d0 = desc[0]; q.d1 = desc[1];
+    q.mind = mind; q.maxd = maxd;
+    return q;
+}
+
 __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &cam,
                                              const FuseConst &fp, const FuseK &K,
-                                             const float *pos, const float *normal,
-                                             const uint4 *desc, float mind, float maxd,
-                                             uint32_t &cmp) {
-    // every global load of the map point first, so that their latencies overlap
-    const float X = pos[0], Y = pos[1], Z = pos[2];
-    const float nx = normal[0], ny = normal[1], nz = normal[2];
-    const uint4 m0 = desc[0], m1 = desc[1];
+                                             const MapPoint &q, uint32_t &cmp) {
+    const float X = q.X, Y = q.Y, Z = q.Z;
+    const float nx = q.nx, ny = q.ny, nz = q.nz;
+    const uint4 m0 = q.d0, m1 = q.d1;
+    const float mind = q.mind, maxd = q.maxd;
     const float xc = fadd(fadd(fadd(fmul(K.R[0], X), fmul(K.R[1], Y)), fmul(K.R[2], Z)), K.t[0]);
     const float yc = fadd(fadd(fadd(fmul(K.R[3], X), fmul(K.R[4], Y)), fmul(K.R[5], Z)), K.t[1]);
     const float zc = fadd(fadd(fadd(fmul(K.R[6], X), fmul(K.R[7], Y)), fmul(K.R[8], Z)), K.t[2]);
@@ -928,7 +941,7 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     const SlotLayout &L = A.L;
     const FuseStage FS = FuseStage::make((int)A.fsn);
     const KfView Tg = KfView::at(w.q, L);
-    const int nT = Tg.hdr->n;
+    const int nT = (int)w.nt;  // the target's keypoint count (set by the host)
     const uint32_t t16 = (uint32_t)((nT + 15) & ~15);
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -946,6 +959,10 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     fuse_setup(Tg.hdr, A.fp.chi2, K);
     const uint32_t m = w.a + (uint32_t)tid;
     const bool have = tid < (int)w.b && !(A.mp_skip && A.mp_skip[m]);
+    // the map point's loads overlap the staging
+    const uint32_t mc = tid < (int)w.b ? m : w.a;  // (a valid index for the speculative loads)
+    const MapPoint mp = load_mp(A.mp_pos + 3 * (size_t)mc, A.mp_normal + 3 * (size_t)mc,
+                                A.mp_desc + 2 * (size_t)mc, A.mp_min[mc], A.mp_max[mc]);
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (tid == 0) ok_all = true;
@@ -966,9 +983,7 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     T.orig = reinterpret_cast<const uint16_t *>(fsm + FS.orig);
     T.level = fsm + FS.level;
     uint32_t cmp = 0, r = kNone;
-    if (have)
-        r = fuse_one(T, A.cam, A.fp, K, A.mp_pos + 3 * (size_t)m, A.mp_normal + 3 * (size_t)m,
-                     A.mp_desc + 2 * (size_t)m, A.mp_min[m], A.mp_max[m], cmp);
+    if (have) r = fuse_one(T, A.cam, A.fp, K, mp, cmp);
     warp_count(cmp, &scmp);
     uint32_t tot;
     const uint32_t pos = block_scan_flag(r != kNone, wtot, tot);
@@ -1189,8 +1204,8 @@ __global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float 
     if (m < n) {
         uint32_t r = kNone;
         if (!(skip && skip[m]))
-            r = fuse_one(T, cam, fp, K, pos + 3 * (size_t)m, normal + 3 * (size_t)m,
-                         desc + 2 * (size_t)m, mn[m], mx[m], cmp);
+            r = fuse_one(T, cam, fp, K, load_mp(pos + 3 * (size_t)m, normal + 3 * (size_t)m,
+                                                desc + 2 * (size_t)m, mn[m], mx[m]), cmp);
         res[m] = r;
     }
     warp_count(cmp, &scmp);

@@ -611,6 +611,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.a = (uint32_t)(S.mp_begin + b);
             w.b = (uint32_t)std::min(kFuseChunk, S.mp_count - b);
             w.c = (uint32_t)S.mp_begin;
+            w.nt = (uint32_t)c->slots[qs].n;
             w.step = (uint32_t)k;
             w.cost = 2 * w.b;
             pad += w.b;
