@@ -93,7 +93,7 @@ typedef struct {
 } tm_mappoint_view;
 
 #define TM_MODE_FUSED 0      /* all pairs and map points of the call in one launch sequence
-                                (join, match, finalize, compaction kernels; default)        */
+                                (search kernel: a CTA per pair; fusion; copy; default)     */
 #define TM_MODE_PER_PAIR 1   /* plain form: one pair at a time, one launch per stage        */
 
 typedef struct {
@@ -105,7 +105,9 @@ typedef struct {
     int32_t resolve;        /* 1 = one match per target keypoint                            */
     int32_t rot_filter;     /* 1 = 30-bin rotation-histogram filter                         */
     int32_t mode;           /* TM_MODE_FUSED or TM_MODE_PER_PAIR                            */
-    int32_t lanes_per_query;/* 0 = autotuned; else 1, 2, 4, 8, 16 or 32                     */
+    int32_t lanes_per_query;/* TM_MODE_PER_PAIR: lanes per query 1, 2, 4, 8, 16 or 32 (0 = 1);
+                               TM_MODE_FUSED spreads each 32-query group's candidates over
+                               its warp's lanes and ignores it                              */
 } tm_search_params;
 
 typedef struct {
@@ -125,7 +127,7 @@ typedef struct {
 } tm_store_stats;
 
 /* Defaults: the readings of the design notes (50, 3/5, 3.84, all gates on, fused mode,
- * autotuned lanes; 5.99, 50, 3.0). */
+ * lanes 0; 5.99, 50, 3.0). */
 void tm_search_params_default(tm_search_params *p);
 void tm_fuse_params_default(tm_fuse_params *p);
 
@@ -180,7 +182,7 @@ tm_status tm_fuse(tm_ctx *ctx, uint64_t kf, const tm_mappoint_view *mps,
                   size_t *n_out, uint64_t *n_comparisons, void *stream);
 
 /* ---------------------------------------------------------------------------- batches
- * Many local-mapping steps in one persistent launch.  Masks and map points of all steps are
+ * Many local-mapping steps in one launch sequence.  Masks and map points of all steps are
  * passed once, concatenated (one transfer each); a step names its ranges in them. */
 typedef struct {
     uint64_t kf_id;          /* new keyframe (stored)                                       */
@@ -218,7 +220,7 @@ typedef struct {
     uint64_t n_comparisons_search, n_comparisons_fuse;
 } tm_batch_result;
 
-/* One-shot: upload, one persistent launch, download.  TM_ERR_CAPACITY sets n_matches and
+/* One-shot: upload, one launch sequence, download.  TM_ERR_CAPACITY sets n_matches and
  * n_fuse to the required sizes and writes nothing else.  On any failure the batch's new
  * keyframes are not stored. */
 tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
@@ -236,7 +238,8 @@ tm_status tm_plan_run(tm_plan *plan, void *stream);
  * (each event node adds a few microseconds), for tm_plan_stage_times. */
 tm_status tm_plan_run_timed(tm_plan *plan, void *stream);
 tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
-/* Launch configuration the plan uses: threads per CTA, lanes per query, CTAs, kernels per run. */
+/* Launch configuration the plan uses: threads per search CTA (autotuned), lanes per query (the
+ * parameter as given), search CTAs (one per pair), kernels per run. */
 tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
                        int32_t *kernels_per_run);
 /* Device time of the stages of the plan's last run when it was a tm_plan_run_timed, from the
