@@ -4,9 +4,9 @@
 
 A step is one pass of the whole hot path over one batch: the 64 new keyframes of a
 64-step EuRoC-shaped batch (5..20 neighbours and 600..2000 keypoints per frame, uneven)
-enter the device-resident store (sort by BoW node + projection grid), then every
-(new keyframe, neighbour) pair is searched and every step's map points are fused, in one
-persistent launch replayed from a CUDA graph.  Inputs are synthetic (seeded generator), all
+enter the device-resident store (grouping by BoW node + projection grid), then every
+(new keyframe, neighbour) pair is searched and every step's map points are fused: one replay
+of a CUDA graph of four kernels.  Inputs are synthetic (seeded generator), all
 resident in HBM before the timed region; the L2 is flushed (256 MB written) before each
 timed step because the batch (~95 MB) fits in L2.  Prints one JSON line.
 
@@ -155,6 +155,28 @@ def algorithmic_bytes(w, res):
                                                                          mask_bytes=mask, outputs=out)
 
 
+def rank_seed(seed, rank):
+    """Workload seed of a rank: weak scaling, every rank its own batch of the same shape."""
+    return seed + 1000 * rank
+
+
+def slowest(seconds, dist, device=None):
+    """The slowest rank's time (all-reduce MAX over the process group when distributed)."""
+    if not dist:
+        return float(seconds)
+    import torch
+    import torch.distributed as D
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    D.all_reduce(t, op=D.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world, dist, device=None):
+    """Whole-job throughput: the units every rank processed / the slowest rank's time."""
+    t = slowest(seconds, dist, device)
+    return units_per_rank * world / t, t
+
+
 def search_bytes(w, res):
     """Unique bytes the search kernel must touch for one batch: of each query keyframe its
     descriptors, positions, node keys, caller indices, angles and mask bytes (51 B per
@@ -246,7 +268,7 @@ def run_mine(args, rank, world, local_rank):
     if dist:
         import torch.distributed as D
 
-    w = W.make_cfg2(seed=args.seed + 1000 * rank)  # weak scaling: each rank its own batch
+    w = W.make_cfg2(seed=rank_seed(args.seed, rank))  # weak scaling: each rank its own batch
     steps = steps_of(w)
     new_ids = [s["q"] for s in w["steps"]]
     old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
@@ -303,16 +325,10 @@ def run_mine(args, rank, world, local_rank):
         plan.run(stream, timed=True)
         stage.append(plan.stage_times())  # waits for this run
     stage = np.array(stage)
-    total_s = step_ms.sum() / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        D.all_reduce(t, op=D.ReduceOp.MAX)
-        total_s = float(t.item())
+    value, total_s = job_throughput(len(new_ids) * args.steps, step_ms.sum() / 1e3, world, dist, dev)
     res2 = plan.results(stream)
     assert np.array_equal(res.matches, res2.matches) and np.array_equal(res.fuse, res2.fuse)
-    n_kf = len(new_ids) * args.steps * world
     ncmp = res.n_comparisons_search + res.n_comparisons_fuse
-    value = n_kf / total_s
     gcomp = ncmp * args.steps * world / total_s / 1e9
 
     # roofline of the dominant kernel (match), timed by the events around it in the timed graph
@@ -410,13 +426,9 @@ def run_mine(args, rank, world, local_rank):
         for _ in range(ke):
             r = e2e_step()
         barrier()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            D.all_reduce(t, op=D.ReduceOp.MAX)
-            el = float(t.item())
+        e2e_value, el = job_throughput(len(new_ids) * ke, time.perf_counter() - t0, world, dist, dev)
         assert np.array_equal(r.matches, res.matches) and np.array_equal(r.fuse, res.fuse)
-        out["e2e"] = {"value": len(new_ids) * ke * world / el, "unit": "keyframes/s",
+        out["e2e"] = {"value": e2e_value, "unit": "keyframes/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "ms_per_step": 1e3 * el / ke,
                       "api": "tm_batch_run (pinned host buffers: new keyframes, masks, map points in; matches and fusion candidates out) + tm_store_remove_keyframe of the 64 new keyframes"}
