@@ -251,6 +251,20 @@ tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t 
 tm_status tm_plan_stage_times(tm_plan *plan, float ms[TM_PLAN_STAGES]);
 tm_status tm_plan_destroy(tm_plan *plan);
 
+/* ---------------------------------------------------------------------------- test hooks
+ * Settings of a context that later batches (tm_batch_run, new plans, the server) take, for
+ * testing failure detection without faulting the GPU.  The search and fusion kernels wait for
+ * their bulk copies into shared memory with a bounded wait; when it runs out, the kernel
+ * records it, returns without touching the copied data, and the call reports TM_ERR_TIMEOUT.
+ *   TM_DEBUG_WAIT_LIMIT    the bound in SM clock cycles (default 4e9, about 2 s)
+ *   TM_DEBUG_STARVE_WAITS  non-zero: after its copies have landed, every such kernel also
+ *                          awaits a barrier that nothing arrives at, so that the bound runs
+ *                          out with no copy in flight; 0 restores normal operation
+ * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, limit <= 0). */
+#define TM_DEBUG_WAIT_LIMIT 1
+#define TM_DEBUG_STARVE_WAITS 2
+tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
+
 /* ---------------------------------------------------------------------------- serving
  * Continuous batching.  A host thread admits submitted requests in arrival order as
  * in-flight batch slots and store memory allow, ingests their keyframes, and launches

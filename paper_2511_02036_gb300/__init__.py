@@ -366,6 +366,11 @@ class Context:
             raise
         return _collect(r, bufs)
 
+    def debug_set(self, what, value):
+        """Test hooks of the context (tm_debug_set): L.TM_DEBUG_WAIT_LIMIT (SM cycles),
+        L.TM_DEBUG_STARVE_WAITS (bounded device waits run out)."""
+        check(tm_debug_set(self.handle, int(what), int(value)))  # noqa: F821
+
     def plan(self, steps, masks=None, mps=None, sp=None, fp=None, new=None):
         return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams(), new)
 

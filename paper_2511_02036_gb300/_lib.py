@@ -27,6 +27,8 @@ TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
 TM_MAX_IMAGE_SIZE = 16384
 TM_PLAN_STAGES = 4
+TM_DEBUG_WAIT_LIMIT = 1
+TM_DEBUG_STARVE_WAITS = 2
 
 
 class tm_camera(ctypes.Structure):
@@ -120,6 +122,7 @@ SIGNATURES = {
     "tm_plan_create": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                                P(tm_fuse_params), P(c_p)]),
     "tm_plan_run": (c_i32, [c_p, c_p]),
+    "tm_debug_set": (c_i32, [c_p, c_i32, ctypes.c_int64]),
     "tm_plan_run_timed": (c_i32, [c_p, c_p]),
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),

@@ -474,12 +474,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the phase with the given parity to complete, at most ~2 s of SM clock.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Waits for the phase with the given parity to complete, at most `limit` SM clock cycles
+// (~2 s by default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 4000000000ll) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Bounded wait for a CTA's bulk copies (phase 0 of bar).  With the `starve` test hook the
+// copies are awaited as usual and then a second barrier that nothing arrives at is awaited, so
+// that the bound runs out with no copy in flight.  Every thread of the CTA calls it; `never`
+// is initialized (count 1) by the thread that initialized bar.
+__device__ __forceinline__ bool staged_wait(uint64_t *bar, uint64_t *never, const BatchArgs &A) {
+    bool ok = mbar_wait_bounded(bar, 0, A.wait_limit);
+    if (ok && A.starve) ok = mbar_wait_bounded(never, 0, A.wait_limit);
+    return ok;
 }
 
 // ------------------------------------------------------------------------- batch pipeline
@@ -769,7 +780,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t keep, scmp;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, never;
     __shared__ bool ok_all;
     const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
     const uint32_t i = A.porder[blockIdx.x];
@@ -784,6 +795,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     const int nQ = (int)w.nq, nT = (int)w.nt;
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&never, 1);
         fence_mbar_init();
         const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
         mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes);
@@ -817,7 +829,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
         }
     }
     __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0);
+    const bool ok = staged_wait(&bar, &never, A);
     if (tid == 0) ok_all = true;
     __syncthreads();
     if (!ok) ok_all = false;
@@ -930,7 +942,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
 __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char fsm[];
     __shared__ FuseK K;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, never;
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t scmp;
     __shared__ bool ok_all;
@@ -945,6 +957,7 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     const uint32_t t16 = (uint32_t)((nT + 15) & ~15);
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&never, 1);
         fence_mbar_init();
         mbar_expect_tx(&bar, (uint32_t)(t16 * (8 + 2 + 2 + 1) + FuseStage::kGridStartBytes));
         bulk_g2s(fsm + FS.gstart, Tg.grid_start, (uint32_t)FuseStage::kGridStartBytes, &bar);
@@ -964,7 +977,7 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     const MapPoint mp = load_mp(A.mp_pos + 3 * (size_t)mc, A.mp_normal + 3 * (size_t)mc,
                                 A.mp_desc + 2 * (size_t)mc, A.mp_min[mc], A.mp_max[mc]);
     __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0);
+    const bool ok = staged_wait(&bar, &never, A);
     if (tid == 0) ok_all = true;
     __syncthreads();
     if (!ok) ok_all = false;

@@ -238,6 +238,9 @@ struct BatchArgs {
     SlotLayout L;                 // array offsets of a slot of that capacity
     int32_t sn;                   // search stage capacity: largest keypoint count of the batch's
                                   // pairs, rounded to 32
+    long long wait_limit;         // bound of a bulk-copy wait, SM clock cycles
+    uint32_t starve;              // test hook: after the copies, await a barrier nothing arrives
+                                  // at, so that the bounded wait runs out
 };
 
 }  // namespace tmap

@@ -709,6 +709,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.cam = c->camc;
     A.cap = c->cap;
     A.L = SlotLayout::make(c->cap);
+    A.wait_limit = c->wait_limit;
+    A.starve = c->starve;
     A.sn = B.smem_n;
     B.sp = sp;
     B.fp = fp;
@@ -1120,6 +1122,22 @@ struct tm_plan {
     int kernels_per_run = 0;
     bool timed_last = false;  // the last run was tm_plan_run_timed
 };
+
+extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
+    if (!c) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    switch (what) {
+        case TM_DEBUG_WAIT_LIMIT:
+            if (value <= 0) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: wait limit must be > 0");
+            c->wait_limit = (long long)value;
+            return TM_OK;
+        case TM_DEBUG_STARVE_WAITS:
+            c->starve = value ? 1u : 0u;
+            return TM_OK;
+        default:
+            return fail(TM_ERR_INVALID_ARG, "tm_debug_set: unknown setting %d", (int)what);
+    }
+}
 
 extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_steps,
                                     const tm_batch_inputs *in, const tm_search_params *sp,

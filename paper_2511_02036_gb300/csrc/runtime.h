@@ -98,6 +98,8 @@ struct tm_ctx {
     tmap::DevBuf mask_scratch;
     std::map<int, std::pair<int, int>> tuned;
     int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1, last_staged = -1;
+    long long wait_limit = 4000000000ll;  // bound of device bulk-copy waits (SM cycles)
+    uint32_t starve = 0;                  // test hook: bounded waits run out (no copy in flight)
     ~tm_ctx();
 };
 

@@ -232,3 +232,28 @@ def test_new_keyframes_enter_with_the_batch(tm, small_batch):
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
+
+
+def test_bounded_wait_reports_timeout(tm, small_batch):
+    """Failure detection without a GPU fault: the search and fusion kernels' bounded waits are
+    made to run out (a barrier that nothing arrives at, after the copies have landed); the
+    call reports TM_ERR_TIMEOUT, stores nothing, and the context keeps working."""
+    from paper_2511_02036_gb300 import _lib as L
+    w = small_batch
+    exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        ctx.debug_set(L.TM_DEBUG_WAIT_LIMIT, 20_000_000)  # ~10 ms of SM clock
+        ctx.debug_set(L.TM_DEBUG_STARVE_WAITS, 1)
+        with pytest.raises(tm.TMError) as e:
+            ctx.batch_run(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids]))
+        assert e.value.status == tm.TM_ERR_TIMEOUT
+        with pytest.raises(tm.TMError):
+            ctx.keyframe_size(new_ids[0])  # the failed batch stored nothing
+        ctx.debug_set(L.TM_DEBUG_STARVE_WAITS, 0)
+        assert_same(ctx.batch_run(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids])), exp)
+        with pytest.raises(tm.TMError) as e:
+            ctx.debug_set(99, 1)
+        assert e.value.status == tm.TM_ERR_INVALID_ARG
