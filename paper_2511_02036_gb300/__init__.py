@@ -86,6 +86,44 @@ def keyframe_view(kf, keep):
     return v
 
 
+def _struct_dtype(ctype):
+    """numpy structured dtype with the field offsets and size of a ctypes Structure, so that an
+    array of records can be filled column by column and passed as the C array."""
+    names, formats, offsets = [], [], []
+    for name, ct in ctype._fields_:
+        if ct is ctypes.c_void_p:
+            fmt = np.uint64
+        elif hasattr(ct, "_length_"):
+            fmt = (np.dtype(ct._type_), ct._length_)
+        else:
+            fmt = np.dtype(ct)
+        names.append(name)
+        formats.append(fmt)
+        offsets.append(getattr(ctype, name).offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets,
+                     "itemsize": ctypes.sizeof(ctype)})
+
+
+_KF_DT = _struct_dtype(L.tm_keyframe_view)
+_STEP_DT = _struct_dtype(L.tm_step)
+
+
+def keyframe_views(kfs, keep):
+    """An array of tm_keyframe_view records (numpy structured, C layout) for keyframe dicts."""
+    v = np.zeros(max(1, len(kfs)), _KF_DT)
+    for k, kf in enumerate(kfs):
+        arrs = [_host(kf["desc"], np.uint8), _host(kf["xy"], np.float32), _host(kf["angle"], np.float32),
+                _host(kf["level"], np.uint8), _host(kf["node"], np.uint32)]
+        keep.extend(arrs)
+        v["n"][k] = len(arrs[0])
+        for name, a in zip(("desc", "xy", "angle", "level", "node"), arrs):
+            v[name][k] = _ptr(a) or 0
+    if len(kfs):
+        v["Tcw"][:len(kfs)] = np.asarray([np.asarray(kf["Tcw"], np.float64).reshape(12) for kf in kfs])
+    keep.append(v)
+    return v
+
+
 def mappoint_view(mps, keep):
     v = L.tm_mappoint_view()
     if mps is None:
@@ -191,10 +229,23 @@ class BatchResult:
         self.pair_offsets = pair_offsets
         self.fuse = fuse
         self.fuse_offsets = fuse_offsets
-        self.pairs = _split(matches, pair_offsets)
-        self.fuses = _split(fuse, fuse_offsets)
+        self._pairs = self._fuses = None
         self.n_comparisons_search = ncmp_search
         self.n_comparisons_fuse = ncmp_fuse
+
+    @property
+    def pairs(self):
+        """Per pair, its rows of `matches` (views, split on first use)."""
+        if self._pairs is None:
+            self._pairs = _split(self.matches, self.pair_offsets)
+        return self._pairs
+
+    @property
+    def fuses(self):
+        """Per step, its rows of `fuse` (views, split on first use)."""
+        if self._fuses is None:
+            self._fuses = _split(self.fuse, self.fuse_offsets)
+        return self._fuses
 
 
 def _result_struct(match_cap, n_pairs, fuse_cap, n_steps):
@@ -216,14 +267,44 @@ def _collect(r, bufs):
 
 def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
     """Output capacities from the known keyframe sizes (unknown ids: the C call reports them)."""
-    mc = 0
-    for s in steps:
-        nq = kf_sizes.get(int(s["kf_id"]), default)
-        for t in s["nbrs"]:
-            nt = kf_sizes.get(int(t), default)
-            mc += min(nq, nt) if resolve else nq
+    g = kf_sizes.get
+    nq = np.fromiter((g(int(s["kf_id"]), default) for s in steps), np.int64, len(steps))
+    cnt = np.fromiter((len(s["nbrs"]) for s in steps), np.int64, len(steps))
+    nt = np.fromiter((g(int(t), default) for s in steps for t in s["nbrs"]), np.int64, int(cnt.sum()))
+    nqp = np.repeat(nq, cnt)
+    mc = int(np.minimum(nqp, nt).sum() if resolve else nqp.sum())
     fc = sum(int(s["mps"]["n"]) for s in steps if s.get("mps") is not None)
     return mc, fc
+
+
+class _ResultBuffers:
+    """Host result buffers of a context, reused across one-shot calls (pinned when torch is
+    available, so that the results come back by DMA) and grown as needed."""
+
+    def __init__(self):
+        self.m = self.po = self.f = self.fo = None
+
+    @staticmethod
+    def _grow(a, n, width):
+        if a is not None and a.shape[0] >= n:
+            return a
+        n = max(n, 1024)
+        try:
+            import torch
+            t = torch.empty((n, width) if width else (n,), dtype=torch.int32).pin_memory()
+            return t.numpy()
+        except Exception:  # no torch or no CUDA runtime: pageable memory
+            return np.empty((n, width) if width else (n,), np.int32)
+
+    def struct(self, match_cap, n_pairs, fuse_cap, n_steps):
+        self.m = self._grow(self.m, max(1, match_cap), 3)
+        self.po = self._grow(self.po, n_pairs + 1, 0)
+        self.f = self._grow(self.f, max(1, fuse_cap), 3)
+        self.fo = self._grow(self.fo, n_steps + 1, 0)
+        r = L.tm_batch_result()
+        r.matches, r.match_cap, r.pair_offsets = self.m.ctypes.data, match_cap, self.po.ctypes.data
+        r.fuse, r.fuse_cap, r.fuse_offsets = self.f.ctypes.data, fuse_cap, self.fo.ctypes.data
+        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1])
 
 
 class Context:
@@ -237,6 +318,7 @@ class Context:
         check(tm_ctx_create(device, ctypes.byref(c), max_kp, budget, ctypes.byref(h)))  # noqa: F821
         self.handle = h
         self.sizes = {}
+        self._res = None
 
     def close(self):
         if self.handle:
@@ -320,14 +402,21 @@ class Context:
             st, masks, mps, k2 = pack_batch(steps, self.sizes)
             keep.extend(k2)
         else:
-            st = (L.tm_step * max(1, len(steps)))()
-            for k, s in enumerate(steps):
-                nb = np.ascontiguousarray(s["nbrs"], np.uint64)
-                keep.append(nb)
-                st[k].kf_id, st[k].nbr_ids, st[k].n_nbrs = int(s["kf_id"]), nb.ctypes.data if len(nb) else None, len(nb)
-                st[k].q_free_off = s.get("q_free_off", -1)
-                st[k].nbr_free_off = s.get("nbr_free_off", -1)
-                st[k].mp_begin, st[k].mp_count = s.get("mp_begin", 0), s.get("mp_count", 0)
+            n = len(steps)
+            arr = np.zeros(max(1, n), _STEP_DT)
+            cnt = np.fromiter((len(s["nbrs"]) for s in steps), np.int64, n)
+            nbrs = np.fromiter((t for s in steps for t in s["nbrs"]), np.uint64, int(cnt.sum()))
+            keep.append(nbrs)
+            off = np.concatenate([[0], np.cumsum(cnt)[:-1]]) if n else np.zeros(0, np.int64)
+            arr["kf_id"][:n] = np.fromiter((s["kf_id"] for s in steps), np.uint64, n)
+            arr["n_nbrs"][:n] = cnt
+            arr["nbr_ids"][:n] = np.where(cnt > 0, nbrs.ctypes.data + 8 * off, 0)
+            arr["q_free_off"][:n] = np.fromiter((s.get("q_free_off", -1) for s in steps), np.int64, n)
+            arr["nbr_free_off"][:n] = np.fromiter((s.get("nbr_free_off", -1) for s in steps), np.int64, n)
+            arr["mp_begin"][:n] = np.fromiter((s.get("mp_begin", 0) for s in steps), np.int64, n)
+            arr["mp_count"][:n] = np.fromiter((s.get("mp_count", 0) for s in steps), np.int64, n)
+            st = arr.ctypes.data
+            keep.append(arr)
         inp = L.tm_batch_inputs()
         keep.append(masks)
         inp.masks = _ptr(masks) if masks is not None and len(masks) else None
@@ -336,12 +425,11 @@ class Context:
         if new is not None:
             ids, kfs = new
             idarr = np.ascontiguousarray(ids, np.uint64)
-            views = (L.tm_keyframe_view * max(1, len(kfs)))()
-            for k, kf in enumerate(kfs):
-                views[k] = keyframe_view(kf, keep)
-                self.sizes[int(idarr[k])] = views[k].n
-            keep.extend([idarr, views])
-            inp.n_new, inp.new_ids, inp.new_kfs = len(kfs), idarr.ctypes.data, ctypes.addressof(views)
+            views = keyframe_views(kfs, keep)
+            for i, n in zip(idarr.tolist(), views["n"][:len(kfs)].tolist()):
+                self.sizes[i] = n
+            keep.append(idarr)
+            inp.n_new, inp.new_ids, inp.new_kfs = len(kfs), idarr.ctypes.data, views.ctypes.data
         keep.append(st)
         return st, inp, keep
 
@@ -354,7 +442,9 @@ class Context:
         mc, fc = _result_caps(steps, self.sizes, sp.resolve)
         if masks is not None or mps is not None:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
-        r, bufs = _result_struct(mc, sum(len(s["nbrs"]) for s in steps), fc, len(steps))
+        if self._res is None:
+            self._res = _ResultBuffers()
+        r, bufs = self._res.struct(mc, sum(len(s["nbrs"]) for s in steps), fc, len(steps))
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
             check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821

@@ -435,6 +435,35 @@ __global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
     }
 }
 
+// Copies `bytes` from src to dst with the widest accesses both alignments allow; all threads
+// of the CTA take part.
+__device__ __forceinline__ void block_copy(unsigned char *dst, const unsigned char *src, size_t bytes) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes;
+    if ((al & 15) == 0) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(src);
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+        for (size_t k = tid; k < bytes / 16; k += bs) d[k] = s[k];
+    } else if ((al & 3) == 0) {
+        const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+        uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+        for (size_t k = tid; k < bytes / 4; k += bs) d[k] = s[k];
+    } else {
+        for (size_t k = tid; k < bytes; k += bs) dst[k] = src[k];
+    }
+}
+
+struct StageOffsets { size_t o[5]; };
+
+// One CTA per keyframe in page-locked host memory: its five arrays into the staging area.
+__global__ void __launch_bounds__(256) stage_gather_kernel(const GatherJob *jobs, unsigned char *base,
+                                                           StageOffsets offs) {
+    const GatherJob g = jobs[blockIdx.x];
+    const uint32_t elt[5] = {32, 8, 4, 4, 1};  // desc, xy, angle, node, level
+    for (int q = 0; q < 5; ++q)
+        block_copy(base + offs.o[q] + (size_t)g.dst * elt[q], g.src[q], (size_t)g.n * elt[q]);
+}
+
 // ------------------------------------------------------------------------- TMA helpers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -1268,6 +1297,15 @@ static cudaError_t launch_prio(void (*k)(Args...), dim3 grid, dim3 block, size_t
     cfg.attrs = at;
     cfg.numAttrs = prio ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+cudaError_t launch_stage_gather(const GatherJob *jobs, int n, unsigned char *base, const size_t offs[5],
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    StageOffsets o;
+    for (int q = 0; q < 5; ++q) o.o[q] = offs[q];
+    stage_gather_kernel<<<n, 256, 0, s>>>(jobs, base, o);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {

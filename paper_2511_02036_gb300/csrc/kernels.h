@@ -13,6 +13,10 @@ size_t ingest_smem_bytes(int cap);
 // prio: scheduling priority of the launch (0 = the stream's; lower numbers are higher
 // priority, within cudaDeviceGetStreamPriorityRange).
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio = 0);
+// Copies keyframes from page-locked host memory into the staging area `base` (array offsets
+// offs: desc, xy, angle, node, level), one CTA per job.
+cudaError_t launch_stage_gather(const GatherJob *jobs, int n, unsigned char *base, const size_t offs[5],
+                                cudaStream_t s);
 
 // Batch pipeline: search (CTA per pair), fuse (CTA per 256 map points), copy.
 size_t search_smem_bytes(int sn);

@@ -92,6 +92,14 @@ struct IngestJob {
     double Tcw[12];
 };
 
+// A keyframe in page-locked host memory whose arrays a kernel copies into the staging area:
+// desc, xy, angle, node, level (device addresses of the host pages), first staged keypoint, n.
+struct GatherJob {
+    const unsigned char *src[5];
+    uint32_t dst;
+    uint32_t n;
+};
+
 struct IngestArgs {
     const IngestJob *jobs;
     int32_t n_jobs;

@@ -75,6 +75,18 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister), which kernels
+// may read directly; null for anything else.
+const void *pinned_device_ptr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 }  // namespace tmap
 
 using namespace tmap;
@@ -214,7 +226,8 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
     const size_t N = (total + 31) & ~size_t(31);
     // staged layout: desc | xy | angle | node | level | jobs
     const size_t o_desc = 0, o_xy = o_desc + N * 32, o_ang = o_xy + N * 8, o_node = o_ang + N * 4,
-                 o_lvl = o_node + N * 4, o_jobs = align128(o_lvl + N), bytes = o_jobs + sizeof(IngestJob) * (size_t)n;
+                 o_lvl = o_node + N * 4, o_jobs = align128(o_lvl + N),
+                 bytes = align128(o_jobs + sizeof(IngestJob) * (size_t)n) + sizeof(GatherJob) * (size_t)n;
     cudaError_t e;
     if ((e = st.dev.reserve(bytes)) != cudaSuccess) return cuda_fail(e, "ingest staging");
     if ((e = st.host.reserve(bytes)) != cudaSuccess) return cuda_fail(e, "ingest pinned staging");
@@ -223,6 +236,7 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
     IngestJob *jobs = reinterpret_cast<IngestJob *>(h + o_jobs);
     size_t off = 0;
     st.src.assign((size_t)n, 0u);
+    std::vector<GatherJob> gather;  // keyframes in page-locked host memory: read by a kernel
     for (int k = 0; k < n; ++k) {
         const tm_keyframe_view &v = kfs[k];
         const size_t m = (size_t)v.n;
@@ -231,7 +245,15 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
         st.src[k] = (uint32_t)off;
         jobs[k].n = v.n;
         for (int q = 0; q < 12; ++q) jobs[k].Tcw[q] = v.Tcw[q];
-        if (m) {
+        const void *pd[5] = {pinned_device_ptr(v.desc), pinned_device_ptr(v.xy), pinned_device_ptr(v.angle),
+                             pinned_device_ptr(v.node), pinned_device_ptr(v.level)};
+        if (m && pd[0] && pd[1] && pd[2] && pd[3] && pd[4]) {
+            GatherJob g;
+            for (int q = 0; q < 5; ++q) g.src[q] = static_cast<const unsigned char *>(pd[q]);
+            g.dst = (uint32_t)off;
+            g.n = (uint32_t)m;
+            gather.push_back(g);
+        } else if (m) {
             if (is_device_ptr(v.desc)) {
                 if ((e = cudaMemcpyAsync(d + o_desc + off * 32, v.desc, m * 32, cudaMemcpyDeviceToDevice, s)) ||
                     (e = cudaMemcpyAsync(d + o_xy + off * 8, v.xy, m * 8, cudaMemcpyDeviceToDevice, s)) ||
@@ -273,6 +295,17 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
     st.host_ranges.clear();
     if ((e = cudaMemcpyAsync(d + o_jobs, jobs, sizeof(IngestJob) * (size_t)n, cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "ingest jobs upload");
+    if (!gather.empty()) {
+        // the gather jobs follow the ingest jobs in both staging areas
+        const size_t o_g = align128(o_jobs + sizeof(IngestJob) * (size_t)n);
+        const size_t gb = sizeof(GatherJob) * gather.size();
+        if (o_g + gb > st.dev.cap || o_g + gb > st.host.cap) return fail(TM_ERR_CUDA, "ingest staging: gather jobs");
+        memcpy(h + o_g, gather.data(), gb);
+        const size_t offs[5] = {o_desc, o_xy, o_ang, o_node, o_lvl};
+        if ((e = cudaMemcpyAsync(d + o_g, h + o_g, gb, cudaMemcpyHostToDevice, s)) ||
+            (e = launch_stage_gather(reinterpret_cast<const GatherJob *>(d + o_g), (int)gather.size(), d, offs, s)))
+            return cuda_fail(e, "ingest staging gather");
+    }
     a.jobs = reinterpret_cast<const IngestJob *>(d + o_jobs);
     a.n_jobs = n;
     a.cap = c->cap;

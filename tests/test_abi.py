@@ -8,6 +8,8 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -101,3 +103,33 @@ def test_null_arguments_rejected(lib):
     assert lib.tm_ctx_create(0, ctypes.byref(cam), L.TM_MAX_KP_LIMIT + 1, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG
     wide = L.tm_camera(L.TM_MAX_IMAGE_SIZE + 1, 480, 450.0, 450.0, 320.0, 240.0)
     assert lib.tm_ctx_create(0, ctypes.byref(wide), 100, 0, ctypes.byref(h)) == L.TM_ERR_INVALID_ARG
+
+
+def test_struct_arrays_match_ctypes_layout():
+    """The binding fills arrays of C records through numpy structured views; each field must
+    land where the ctypes (and C) layout puts it."""
+    import paper_2511_02036_gb300 as tm
+    from paper_2511_02036_gb300 import _lib as L
+    keep = []
+    kfs = [dict(desc=np.zeros((3, 32), np.uint8), xy=np.zeros((3, 2), np.float32),
+                angle=np.zeros(3, np.float32), level=np.zeros(3, np.uint8),
+                node=np.arange(3, dtype=np.uint32), Tcw=np.arange(12, dtype=np.float64) + 10 * k)
+           for k in range(2)]
+    v = tm.keyframe_views(kfs, keep)
+    for k in range(2):
+        c = L.tm_keyframe_view.from_address(v.ctypes.data + k * ctypes.sizeof(L.tm_keyframe_view))
+        assert c.n == 3 and c.node == kfs[k]["node"].ctypes.data and c.desc == kfs[k]["desc"].ctypes.data
+        assert list(c.Tcw) == list(kfs[k]["Tcw"])
+    steps = [dict(kf_id=5, nbrs=[1, 2], q_free_off=7, nbr_free_off=9, mp_begin=3, mp_count=4),
+             dict(kf_id=6, nbrs=[], mp_count=0)]
+    ctx = tm.Context.__new__(tm.Context)
+    ctx.sizes = {}
+    st, inp, keep2 = ctx._inputs(steps, masks=np.zeros(16, np.uint8),
+                                 mps=dict(n=0, pos=None, normal=None, desc=None, min_dist=None, max_dist=None))
+    c0 = L.tm_step.from_address(st)
+    c1 = L.tm_step.from_address(st + ctypes.sizeof(L.tm_step))
+    assert (c0.kf_id, c0.n_nbrs, c0.q_free_off, c0.nbr_free_off, c0.mp_begin, c0.mp_count) == (5, 2, 7, 9, 3, 4)
+    assert list((ctypes.c_uint64 * 2).from_address(c0.nbr_ids)) == [1, 2]
+    assert (c1.kf_id, c1.n_nbrs, c1.q_free_off, c1.mp_count) == (6, 0, -1, 0)
+    # result capacities: sum over pairs of min(n_Q, n_T)
+    assert tm._result_caps([dict(kf_id=1, nbrs=[2, 3]), dict(kf_id=2, nbrs=[1])], {1: 10, 2: 4, 3: 20}) == (4 + 10 + 4, 0)

@@ -257,3 +257,28 @@ def test_bounded_wait_reports_timeout(tm, small_batch):
         with pytest.raises(tm.TMError) as e:
             ctx.debug_set(99, 1)
         assert e.value.status == tm.TM_ERR_INVALID_ARG
+
+
+def test_pinned_host_inputs(tm, small_batch):
+    """New keyframes, masks and map points in page-locked host memory (torch pinned tensors):
+    the keyframes are gathered by a kernel straight from host memory; results equal the
+    oracle's, twice in a row (the context's reused result buffers)."""
+    torch = pytest.importorskip("torch")
+    w = small_batch
+    exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        st_arr, masks, mps, _keep = tm.pack_batch(steps_of(w), ctx.sizes)
+        steps = [dict(kf_id=st_arr[k].kf_id, nbrs=w["steps"][k]["nbrs"], q_free_off=st_arr[k].q_free_off,
+                      nbr_free_off=st_arr[k].nbr_free_off, mp_begin=st_arr[k].mp_begin,
+                      mp_count=st_arr[k].mp_count) for k in range(len(w["steps"]))]
+        h_mps = {k: (pin(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
+        h_new = [dict(desc=pin(f["desc"]), xy=pin(f["xy"]), angle=pin(f["angle"]), level=pin(f["level"]),
+                      node=pin(f["node"].view(np.int32)), Tcw=f["Tcw"]) for f in (w["frames"][i] for i in new_ids)]
+        for _ in range(2):
+            assert_same(ctx.batch_run(steps, masks=pin(masks), mps=h_mps, new=(new_ids, h_new)), exp)
+            for i in new_ids:
+                ctx.remove_keyframe(i)
