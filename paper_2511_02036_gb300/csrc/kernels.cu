@@ -698,8 +698,8 @@ __device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &
 // to acc[], its claim on the target to win[] (shared atomicMin).
 __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
                                              const float *F, const float *thr, const uint32_t *tkey,
-                                             const uint16_t *bst, const uint8_t *tel, uint32_t *win,
-                                             uint32_t *acc, uint2 *st, int g, const QLoad &q,
+                                             const uint16_t *bst, const uint16_t *ep, const uint16_t *epos,
+                                             uint32_t *win, uint32_t *acc, uint2 *st, int g, const QLoad &q,
                                              uint32_t &cmp) {
     const int lane = (int)(threadIdx.x & 31u);
     const int p0 = g * 32;
@@ -717,7 +717,9 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     int hi = lo;
     while (hi < be && tkey[hi] == key) ++hi;
     const Line l = epi_line(F, xq.x, xq.y);
-    const int c = el ? hi - lo : 0;
+    // the eligible candidates: positions epos[elo .. elo + c)
+    const int elo = ep[lo];
+    const int c = el ? (int)ep[hi] - elo : 0;
     int off = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -738,12 +740,13 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             const int oi = __shfl_sync(kFull, off, (i + s2) & 31);
             if (i + s2 < 32 && oi <= k) i += s2;
         }
-        const int j0 = __shfl_sync(kFull, lo, i) + (k - __shfl_sync(kFull, off, i));
+        const int e0 = __shfl_sync(kFull, elo, i) + (k - __shfl_sync(kFull, off, i));
         Line li;
         li.a = __shfl_sync(kFull, l.a, i);
         li.b = __shfl_sync(kFull, l.b, i);
         li.c = __shfl_sync(kFull, l.c, i);
-        const bool valid = k < total && tel[j0];  // (j0 is a candidate only when k < total)
+        const bool valid = k < total;
+        const int j0 = valid ? (int)epos[e0] : 0;
         uint32_t bk = kNone, sc = 0xFFFFu;
         if (valid) {
             const int pq = p0 + i;
@@ -755,9 +758,10 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
             if (!epi || epi_pass(li, xt.x, xt.y, thr[lv])) bk = (d << 16) | (uint32_t)j0;
         }
-        // segmented merge over the lanes of each query (suffix within the segment)
-#pragma unroll
-        for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        // segmented merge over the lanes of each query (suffix within the segment), as many
+        // doubling steps as the round's longest segment needs
+        const int seg = __reduce_max_sync(kFull, (unsigned)__popc(__match_any_sync(kFull, i)));
+        for (int s2 = 1; s2 < seg; s2 <<= 1) {
             const uint32_t ob = __shfl_down_sync(kFull, bk, s2);
             const uint32_t os = __shfl_down_sync(kFull, sc, s2);
             const int oi = __shfl_down_sync(kFull, i, s2);
@@ -790,7 +794,6 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     __syncwarp();
 }
 
-constexpr int kSearchMaxWarps = 16;
 
 // One CTA per (new keyframe, neighbour) pair, largest pairs first (Sec. IV-C, all of S1-S6):
 //   setup    the neighbour's node keys and bucket table into shared memory (bulk copies);
@@ -805,7 +808,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ float F[9];
     __shared__ float thr[kLevels];
-    __shared__ uint2 qst[kSearchMaxWarps][32];
+    __shared__ uint2 qst[8][32];  // per warp (at most 256 threads)
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t keep, scmp;
@@ -819,7 +822,9 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     uint16_t *bst = reinterpret_cast<uint16_t *>(ssm + S.bst);
     uint32_t *win = reinterpret_cast<uint32_t *>(ssm + S.win);
     uint32_t *acc = reinterpret_cast<uint32_t *>(ssm + S.acc);
-    uint8_t *tel = ssm + S.tel;
+    uint16_t *ep = reinterpret_cast<uint16_t *>(ssm + S.ep);
+    uint16_t *epos = reinterpret_cast<uint16_t *>(ssm + S.epos);
+    uint8_t *tel = reinterpret_cast<uint8_t *>(acc);  // eligibility bytes, until the search
     const KfView T = KfView::at(w.t, A.L);
     const int nQ = (int)w.nq, nT = (int)w.nt;
     if (tid == 0) {
@@ -858,6 +863,19 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
         }
     }
     __syncthreads();
+    {
+        // eligible positions in node order: thread t takes the run [t*per, (t+1)*per)
+        const int per = (nT + bs - 1) / bs, jb = min(tid * per, nT), je = min(jb + per, nT);
+        uint32_t cnt = 0;
+        for (int j = jb; j < je; ++j) cnt += tel[j];
+        uint32_t tot;
+        uint32_t run = block_scan_add(cnt, wtot, tot);
+        for (int j = jb; j < je; ++j) {
+            ep[j] = (uint16_t)run;
+            if (tel[j]) epos[run++] = (uint16_t)j;
+        }
+        if (tid == 0) ep[nT] = (uint16_t)tot;
+    }
     const bool ok = staged_wait(&bar, &never, A);
     if (tid == 0) ok_all = true;
     __syncthreads();
@@ -874,7 +892,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     for (int g = wid; g * 32 < nQ; g += nw) {
         QLoad nxt = {};
         if ((g + nw) * 32 < nQ) nxt = load_group(A, w, g + nw);
-        search_group(A, w, T, F, thr, tkey, bst, tel, win, acc, qst[wid], g, cur, cmp);
+        search_group(A, w, T, F, thr, tkey, bst, ep, epos, win, acc, qst[wid], g, cur, cmp);
         cur = nxt;
     }
     warp_count(cmp, &scmp);

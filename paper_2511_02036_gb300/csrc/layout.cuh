@@ -147,11 +147,13 @@ struct WorkItem {
 constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;
 
 // Shared-memory carve of a search CTA (one pair) for a capacity of sn keypoints (a multiple
-// of 32): the neighbour's node keys and bucket table (bulk copies), its per-target winners and
-// eligibility, the per-query accepted matches; after the search the key array holds the
-// per-caller-query results.
+// of 32): the neighbour's node keys and bucket table (bulk copies), its per-target winners,
+// its eligible positions in node order (epos) with their prefix counts (ep: eligible
+// positions before j), and the per-query accepted matches (whose space first holds the
+// per-target eligibility bytes); after the search the key array holds the per-caller-query
+// results.
 struct SearchStage {
-    size_t tkey, bst, win, acc, tel, bytes;
+    size_t tkey, bst, win, acc, ep, epos, bytes;
     __host__ __device__ static constexpr SearchStage make(int sn) {
         SearchStage L{};
         size_t o = 0;
@@ -159,7 +161,8 @@ struct SearchStage {
         L.bst = o;  o = align128(o + kBucketTableBytes);
         L.win = o;  o = align128(o + size_t(sn) * 4);
         L.acc = o;  o = align128(o + size_t(sn) * 4);
-        L.tel = o;  o = align128(o + size_t(sn));
+        L.ep = o;   o = align128(o + size_t(sn + 1) * 2);
+        L.epos = o; o = align128(o + size_t(sn) * 2);
         L.bytes = o;
         return L;
     }
