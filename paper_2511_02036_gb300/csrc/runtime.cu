@@ -785,8 +785,8 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 //           with the batch: then it starts after the ingest);
 //   store:  ingest of new keyframes -> fusion (needs their grids), on s, at low priority;
 // joined before copy (offsets, dense output, comparison totals, status).  `threads` = threads
-// per search CTA.  With `timed`, events E0..E4 mark: start, search done, ingest done, fusion
-// done, copy done.
+// per search CTA.  With `timed`, events E0..E5 mark: start, search done, ingest done, fusion
+// done, copy done, search start (on the search branch, right before the kernel).
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed) {
     cudaError_t e;
     B.threads = threads;
@@ -811,7 +811,8 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, lo_p))) return cuda_fail(e, "ingest kernel");
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
-    if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = launch_search(B.args, threads, B.paux, hi_p)) ||
+    if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
+        (e = launch_search(B.args, threads, B.paux, hi_p)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
     if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
@@ -1302,10 +1303,10 @@ extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     cudaSetDevice(P->ctx->device);
     cudaError_t e = cudaEventSynchronize(P->B.ev[4]);
     if (e) return cuda_fail(e, "stage events");
-    float t[5] = {0};
-    for (int k = 1; k < 5; ++k)
+    float t[6] = {0};
+    for (int k = 1; k < 6; ++k)
         if ((e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k]))) return cuda_fail(e, "stage times");
-    ms[0] = t[1];                         // search kernel (from the start)
+    ms[0] = t[1] - t[5];                  // search kernel (between the events around it)
     ms[1] = t[2];                         // ingest (from the start)
     ms[2] = t[3] - t[2];                  // fusion (after the ingest)
     ms[3] = t[4] - std::max(t[1], t[3]);  // offsets + copy (after both branches)
