@@ -402,8 +402,14 @@ def run_mine(args, rank, world, local_rank):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
         h_masks = pin(masks)
         h_mps = {k: (pin(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
-        h_new = [dict(desc=pin(f["desc"]), xy=pin(f["xy"]), angle=pin(f["angle"]), level=pin(f["level"]),
-                      node=pin(f["node"].view(np.int32)), Tcw=f["Tcw"]) for f in (w["frames"][i] for i in new_ids)]
+        # the new keyframes packed one after another, one pinned array per field (as a producer
+        # streaming keyframes into a staging buffer would hand them over)
+        fr = [w["frames"][i] for i in new_ids]
+        h_new = dict(n=[f["n"] for f in fr], desc=pin(np.concatenate([f["desc"] for f in fr])),
+                     xy=pin(np.concatenate([f["xy"] for f in fr])), angle=pin(np.concatenate([f["angle"] for f in fr])),
+                     level=pin(np.concatenate([f["level"] for f in fr])),
+                     node=pin(np.concatenate([f["node"] for f in fr]).view(np.int32)),
+                     Tcw=np.stack([np.asarray(f["Tcw"], np.float64).reshape(12) for f in fr]))
         # bytes copied in per step: masks, map-point arrays, the new keyframes' arrays
         # (desc 32 + xy 8 + angle 4 + level 1 + node 4 = 49 B per keypoint), the work list
         h2d = (int(masks.nbytes) + sum(int(v.nbytes) for v in mps.values() if isinstance(v, np.ndarray))

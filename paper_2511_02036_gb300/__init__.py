@@ -124,6 +124,26 @@ def keyframe_views(kfs, keep):
     return v
 
 
+def keyframe_views_packed(packed, keep):
+    """tm_keyframe_view records for keyframes packed one after another in one array per field:
+    packed = dict(n=[counts], desc (N, 32), xy (N, 2), angle (N,), level (N,), node (N,),
+    Tcw (k, 12) or (k, 3, 4)); numpy arrays or torch tensors (host or device)."""
+    n = np.asarray(packed["n"], np.int64).reshape(-1)
+    k = len(n)
+    start = np.concatenate([[0], np.cumsum(n)[:-1]]) if k else np.zeros(0, np.int64)
+    v = np.zeros(max(1, k), _KF_DT)
+    v["n"][:k] = n
+    for name, dt, elt in (("desc", np.uint8, 32), ("xy", np.float32, 8), ("angle", np.float32, 4),
+                          ("level", np.uint8, 1), ("node", np.uint32, 4)):
+        a = _host(packed[name], dt)
+        keep.append(a)
+        v[name][:k] = np.where(n > 0, (_ptr(a) or 0) + elt * start, 0)
+    if k:
+        v["Tcw"][:k] = np.asarray(packed["Tcw"], np.float64).reshape(k, 12)
+    keep.append(v)
+    return v
+
+
 def mappoint_view(mps, keep):
     v = L.tm_mappoint_view()
     if mps is None:
@@ -425,18 +445,19 @@ class Context:
         if new is not None:
             ids, kfs = new
             idarr = np.ascontiguousarray(ids, np.uint64)
-            views = keyframe_views(kfs, keep)
-            for i, n in zip(idarr.tolist(), views["n"][:len(kfs)].tolist()):
+            views = keyframe_views_packed(kfs, keep) if isinstance(kfs, dict) else keyframe_views(kfs, keep)
+            for i, n in zip(idarr.tolist(), views["n"][:len(idarr)].tolist()):
                 self.sizes[i] = n
             keep.append(idarr)
-            inp.n_new, inp.new_ids, inp.new_kfs = len(kfs), idarr.ctypes.data, views.ctypes.data
+            inp.n_new, inp.new_ids, inp.new_kfs = len(idarr), idarr.ctypes.data, views.ctypes.data
         keep.append(st)
         return st, inp, keep
 
     def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None):
         """One-shot batch (tm_batch_run).  Without masks/mps the steps carry their own
         q_free / nbr_free / mps and are packed here.  new = (ids, keyframes) entering the
-        store with the batch."""
+        store with the batch: a list of keyframe dicts, or one packed dict (see
+        keyframe_views_packed)."""
         sp = sp or SearchParams()
         st, inp, keep = self._inputs(steps, masks, mps, new)
         mc, fc = _result_caps(steps, self.sizes, sp.resolve)

@@ -133,3 +133,30 @@ def test_struct_arrays_match_ctypes_layout():
     assert (c1.kf_id, c1.n_nbrs, c1.q_free_off, c1.mp_count) == (6, 0, -1, 0)
     # result capacities: sum over pairs of min(n_Q, n_T)
     assert tm._result_caps([dict(kf_id=1, nbrs=[2, 3]), dict(kf_id=2, nbrs=[1])], {1: 10, 2: 4, 3: 20}) == (4 + 10 + 4, 0)
+
+
+def test_packed_keyframe_views():
+    """Keyframes packed one after another in one array per field give the same records as the
+    per-keyframe form (pointers at each keyframe's first element)."""
+    import paper_2511_02036_gb300 as tm
+    from paper_2511_02036_gb300 import _lib as L
+    rng = np.random.default_rng(0)
+    ns = [3, 0, 5]
+    N = sum(ns)
+    packed = dict(n=ns, desc=rng.integers(0, 255, (N, 32), dtype=np.uint8), xy=rng.random((N, 2), np.float32),
+                  angle=rng.random(N, np.float32), level=rng.integers(0, 8, N, dtype=np.uint8),
+                  node=rng.integers(0, 99, N, dtype=np.uint32), Tcw=rng.random((3, 12)))
+    keep = []
+    v = tm.keyframe_views_packed(packed, keep)
+    off = 0
+    for k, n in enumerate(ns):
+        c = L.tm_keyframe_view.from_address(v.ctypes.data + k * ctypes.sizeof(L.tm_keyframe_view))
+        assert c.n == n and list(c.Tcw) == list(packed["Tcw"][k])
+        if n:
+            assert c.desc == packed["desc"].ctypes.data + 32 * off
+            assert c.xy == packed["xy"].ctypes.data + 8 * off
+            assert c.node == packed["node"].ctypes.data + 4 * off
+            assert c.level == packed["level"].ctypes.data + off
+        else:
+            assert c.desc is None or c.desc == 0
+        off += n

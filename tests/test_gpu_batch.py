@@ -278,7 +278,13 @@ def test_pinned_host_inputs(tm, small_batch):
         h_mps = {k: (pin(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
         h_new = [dict(desc=pin(f["desc"]), xy=pin(f["xy"]), angle=pin(f["angle"]), level=pin(f["level"]),
                       node=pin(f["node"].view(np.int32)), Tcw=f["Tcw"]) for f in (w["frames"][i] for i in new_ids)]
-        for _ in range(2):
-            assert_same(ctx.batch_run(steps, masks=pin(masks), mps=h_mps, new=(new_ids, h_new)), exp)
+        fr = [w["frames"][i] for i in new_ids]
+        packed = dict(n=[f["n"] for f in fr], desc=pin(np.concatenate([f["desc"] for f in fr])),
+                      xy=pin(np.concatenate([f["xy"] for f in fr])), angle=pin(np.concatenate([f["angle"] for f in fr])),
+                      level=pin(np.concatenate([f["level"] for f in fr])),
+                      node=pin(np.concatenate([f["node"] for f in fr]).view(np.int32)),
+                      Tcw=np.stack([np.asarray(f["Tcw"], np.float64).reshape(12) for f in fr]))
+        for new in (h_new, h_new, packed):
+            assert_same(ctx.batch_run(steps, masks=pin(masks), mps=h_mps, new=(new_ids, new)), exp)
             for i in new_ids:
                 ctx.remove_keyframe(i)
