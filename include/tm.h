@@ -108,6 +108,13 @@ typedef struct {
     int32_t lanes_per_query;/* TM_MODE_PER_PAIR: lanes per query 1, 2, 4, 8, 16 or 32 (0 = 1);
                                TM_MODE_FUSED spreads each 32-query group's candidates over
                                its warp's lanes and ignores it                              */
+    int32_t dense_min;      /* TM_MODE_FUSED: a query whose BoW node holds >= dense_min
+                               keypoints of the neighbour is compared with all of them on
+                               the tensor cores (descriptors as +-1 fp8 vectors, Hamming =
+                               (256 - dot) / 2, exact); same results.  0 = off (default),
+                               else >= 16.  Worth it for dense nodes (~64 and more); each
+                               call with it on runs one more kernel.  TM_MODE_PER_PAIR
+                               ignores it.                                                   */
 } tm_search_params;
 
 typedef struct {

@@ -168,11 +168,12 @@ class SearchParams:
     rot_filter: bool = True
     mode: int = TM_MODE_FUSED
     lanes_per_query: int = 0
+    dense_min: int = 0      # tensor-core blocks for nodes with >= dense_min neighbour keypoints
 
     def struct(self):
         return L.tm_search_params(self.hamming_max, self.ratio_num, self.ratio_den, self.epi_chi2,
                                   int(self.epipolar), int(self.resolve), int(self.rot_filter),
-                                  int(self.mode), int(self.lanes_per_query))
+                                  int(self.mode), int(self.lanes_per_query), int(self.dense_min))
 
 
 @dataclass

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "tm.h"
 
 namespace tmap {
 
@@ -700,7 +701,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
                                              const float *F, const float *thr, const uint32_t *tkey,
                                              const uint16_t *bst, const uint16_t *ep, const uint16_t *epos,
                                              uint32_t *win, uint32_t *acc, uint2 *st, int g, const QLoad &q,
-                                             uint32_t &cmp) {
+                                             uint32_t &cmp, uint32_t *dfail) {
     const int lane = (int)(threadIdx.x & 31u);
     const int p0 = g * 32;
     const int nloc = min(32, (int)w.nq - p0);
@@ -719,7 +720,13 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     const Line l = epi_line(F, xq.x, xq.y);
     // the eligible candidates: positions epos[elo .. elo + c)
     const int elo = ep[lo];
-    const int c = el ? (int)ep[hi] - elo : 0;
+    int c = el ? (int)ep[hi] - elo : 0;
+    // a query of a dense node block: its candidates were compared on the tensor cores
+    const bool dz = A.sp.dense_min > 0 && hi - lo >= A.sp.dense_min;
+    if (dz) {
+        cmp += (uint32_t)c;
+        c = 0;
+    }
     int off = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -728,7 +735,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     }
     const int total = __shfl_sync(kFull, off, 31);
     off -= c;  // exclusive
-    st[lane] = make_uint2(kNone, 0xFFFFu);
+    st[lane] = (dz && el) ? A.dres[w.c + (uint32_t)p] : make_uint2(kNone, 0xFFFFu);
     __syncwarp();
     const bool epi = A.sp.epipolar != 0;
     for (int k0 = 0; k0 < total; k0 += 32) {
@@ -778,6 +785,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     if (in) {
         const uint2 v = st[lane];
         uint32_t a = kNone;
+        if (v.y == kNone) *dfail = 1u;  // the dense tile of this query timed out
         if (v.x != kNone) {
             const uint32_t best = v.x >> 16;
             bool ok = (int)best <= A.sp.hamming_max;
@@ -792,6 +800,306 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
         acc[p] = a;
     }
     __syncwarp();
+}
+
+
+// ---------------------------------------------------------------- dense node blocks (S3b)
+//
+// A query whose BoW node holds at least dense_min keypoints of the neighbour belongs to a
+// dense block: all eligible queries of that node against all keypoints of the node in the
+// neighbour (Sec. IV-C's candidate set, unchanged).  Their Hamming distances come from the
+// tensor cores.  A descriptor bit b becomes the fp8 (e4m3) value +1 (b = 0) or -1 (b = 1), so
+// the dot product of two descriptors is 256 - 2 * Hamming: an integer of magnitude <= 256,
+// exact in the float32 accumulator whatever the summation order.
+//
+// dense_kernel: CTA (pair, split) takes every splits-th dense run of the neighbour.  Per run,
+// tiles of 128 queries x 256 keypoints: both operands expanded into shared memory (K-major
+// core matrices, no swizzle), eight tcgen05.mma of K = 32 issued by one thread into a
+// 128-lane x 256-column float32 accumulator in tensor memory, completion by tcgen05.commit on
+// an mbarrier (bounded wait).  Then thread r reads query r's row (tcgen05.ld) and applies the
+// epipolar gate and the (best, second) merge of the candidate rounds to each column.  The
+// query's state goes to dres; search_kernel counts the query's comparisons and takes that
+// state instead of visiting its candidates.
+
+constexpr int kDenseThreads = 128;                 // M: one accumulator lane (query) per thread
+constexpr int kDenseCols = 256;                    // N per tile = tensor-memory columns
+constexpr int kDenseMinRun = 16;                   // smallest dense_min accepted
+constexpr int kDenseRunCap = TM_MAX_KP_LIMIT / kDenseMinRun;  // dense runs of a neighbour
+constexpr uint32_t kDenseTileBytes = 2048;         // 8 rows x 256 one-byte K values
+constexpr uint32_t kDenseA = 0;                                            // 128 x 256 B
+constexpr uint32_t kDenseB = kDenseA + kDenseThreads / 8 * kDenseTileBytes;  // 256 x 256 B
+constexpr uint32_t kDenseCx = kDenseB + kDenseCols / 8 * kDenseTileBytes;
+constexpr uint32_t kDenseCy = kDenseCx + kDenseCols * 4;
+constexpr uint32_t kDenseCthr = kDenseCy + kDenseCols * 4;
+constexpr uint32_t kDenseQlist = kDenseCthr + kDenseCols * 4;             // 2 x 128 u16
+constexpr uint32_t kDenseRuns = kDenseQlist + 2 * kDenseThreads * 2;      // kDenseRunCap u16
+constexpr uint32_t kDenseSmem = kDenseRuns + kDenseRunCap * 2;
+// > 1/3 of an SM's shared memory: at most two dense CTAs per SM, so their 2 x 256 columns
+// never exceed the SM's 512 tensor-memory columns and the allocation cannot wait on a CTA
+// that is not running
+static_assert(3 * (kDenseSmem + 1024) > 233472, "dense CTAs must not exceed two per SM");
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A * B^T, A: M x 32 e4m3, B: N x 32 e4m3 (shared-memory descriptors).
+__device__ __forceinline__ void tc_mma_e4m3(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Arrives once on bar when every tcgen05.mma this thread issued before has completed.
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+// 32 consecutive accumulator columns of the warp's 32 lanes (lane = thread), then the wait
+// that makes them valid (the registers pass through the wait so no use moves above it).
+__device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+        "%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
+                   "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
+                   "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x 16
+// bytes; lbo = byte step between core matrices along K, sbo = along M (N); bit 46 = the
+// descriptor version of this architecture.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+    const uint64_t a = smem_addr(p);
+    return ((a & 0x3FFFFull) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f8f6f4: float32 accumulator (bits 4-5 = 1), A and B e4m3
+// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_e4m3_f32(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// Four descriptor bits -> four e4m3 bytes, +1.0 (0x38) for a 0 bit, -1.0 (0xB8) for a 1 bit
+// (the multiply moves bit i to bit 8i; the terms do not overlap, so nothing carries).
+__device__ __forceinline__ uint32_t pm1_bytes(uint32_t x) {
+    return (((x * 0x00204081u) & 0x01010101u) << 7) | 0x38383838u;
+}
+// Row r of a K-major operand tile: bit k of the descriptor (32-bit word k / 32) at K index k;
+// 8-row groups kDenseTileBytes apart, 16-byte K chunks 128 bytes apart within a group.
+__device__ __forceinline__ void expand_row(unsigned char *tile, int r, const uint4 *d) {
+    const uint4 a = d[0], b = d[1];
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    unsigned char *row = tile + (r >> 3) * kDenseTileBytes + (r & 7) * 16;
+#pragma unroll
+    for (int kc = 0; kc < 16; ++kc) {
+        const uint32_t h = (w[kc >> 1] >> ((kc & 1) * 16)) & 0xFFFFu;
+        *reinterpret_cast<uint4 *>(row + kc * 128) =
+            make_uint4(pm1_bytes(h & 15u), pm1_bytes((h >> 4) & 15u), pm1_bytes((h >> 8) & 15u), pm1_bytes(h >> 12));
+    }
+}
+
+__global__ void __launch_bounds__(kDenseThreads, 1) dense_kernel(BatchArgs A) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ float F[9];
+    __shared__ float thr[kLevels];
+    __shared__ uint32_t wtot[32];
+    __shared__ uint32_t s_taddr, s_fail;
+    __shared__ __align__(8) uint64_t bar, never;
+    unsigned char *sa = dsm + kDenseA, *sb = dsm + kDenseB;
+    float *cx = reinterpret_cast<float *>(dsm + kDenseCx);
+    float *cy = reinterpret_cast<float *>(dsm + kDenseCy);
+    float *cthr = reinterpret_cast<float *>(dsm + kDenseCthr);
+    uint16_t *qlist = reinterpret_cast<uint16_t *>(dsm + kDenseQlist);
+    uint16_t *runs = reinterpret_cast<uint16_t *>(dsm + kDenseRuns);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t splits = A.dsplit, item = blockIdx.x / splits, split = blockIdx.x % splits;
+    const WorkItem w = A.items[item];
+    const KfView T = KfView::at(w.t, A.L);
+    const int nQ = (int)w.nq, nT = (int)w.nt, dmin = A.sp.dense_min;
+    // the neighbour's dense runs (node keys ascend), numbered in position order
+    auto dense_start = [&](int j) {
+        const uint32_t k = T.node[j];
+        return (j == 0 || T.node[j - 1] != k) && j + dmin - 1 < nT && T.node[j + dmin - 1] == k;
+    };
+    const int per = (nT + kDenseThreads - 1) / kDenseThreads, jb = min(tid * per, nT), je = min(jb + per, nT);
+    uint32_t cnt = 0;
+    for (int j = jb; j < je; ++j) cnt += dense_start(j) ? 1u : 0u;
+    uint32_t total;
+    uint32_t r = block_scan_add(cnt, wtot, total);
+    for (int j = jb; j < je; ++j)
+        if (dense_start(j)) {
+            if (r % splits == split) runs[r / splits] = (uint16_t)j;
+            ++r;
+        }
+    const int nrun = total > split ? (int)((total - split + splits - 1) / splits) : 0;
+    if (nrun == 0) return;  // uniform: total comes from the block scan
+    if (wid == 0) {
+        tmem_alloc(&s_taddr, kDenseCols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init(&never, 1);
+        fence_mbar_init();
+        s_fail = 0u;
+    }
+    if (wid == 1) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid < kLevels) {
+        const float sc = level_scale(tid);
+        thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = s_taddr;
+    const uint32_t tlane = tbase + ((uint32_t)(wid * 32) << 16);  // this warp's 32 lanes
+    const bool epi = A.sp.epipolar != 0;
+    uint32_t phase = 0;
+    for (int rr = 0; rr < nrun; ++rr) {
+        const int lo = runs[rr];
+        const uint32_t key = T.node[lo];
+        const int hi = upper_bound_u32(T.node, lo + dmin, nT, key);
+        const int ncol = hi - lo;
+        bool b_ready = false;  // B operand of a one-tile run, kept over its query tiles
+        int scan = 0, qn = 0;  // next query position to scan, queries listed (both uniform)
+        while (scan < nQ || qn > 0) {
+            // list the node's eligible queries, ascending position, until a tile is full
+            while (qn < kDenseThreads && scan < nQ) {
+                const int p = scan + tid;
+                bool f = false;
+                if (p < nQ) {
+                    const uint32_t nk = w.qnode[p];
+                    if ((w.qraw ? node_key(nk) : nk) == key)
+                        f = w.a == kNone || A.masks[w.a + (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p)] != 0;
+                }
+                const unsigned m = __ballot_sync(kFull, f);
+                if (lane == 0) wtot[wid] = (uint32_t)__popc(m);
+                __syncthreads();
+                uint32_t base = (uint32_t)qn, add = 0;
+                for (int k = 0; k < kDenseThreads / 32; ++k) {
+                    const uint32_t v = wtot[k];
+                    if (k < wid) base += v;
+                    add += v;
+                }
+                if (f) qlist[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)p;
+                qn += (int)add;
+                scan += kDenseThreads;
+                __syncthreads();
+            }
+            const int rows = min(qn, kDenseThreads);
+            if (rows > 0) {
+                const int p = tid < rows ? (int)qlist[tid] : 0;
+                Line l{};
+                uint32_t bk = kNone, sc = 0xFFFFu;
+                if (tid < rows) {
+                    const float2 xq = w.qxy[p];
+                    l = epi_line(F, xq.x, xq.y);
+                    expand_row(sa, tid, w.qdesc + 2 * p);
+                }
+                for (int n0 = 0; n0 < ncol; n0 += kDenseCols) {
+                    const int nc = min(kDenseCols, ncol - n0), nmma = (nc + 31) & ~31;
+                    if (!b_ready) {
+                        for (int c = tid; c < nc; c += kDenseThreads) {
+                            const int j = lo + n0 + c;
+                            expand_row(sb, c, T.desc + 2 * j);
+                            const float2 xy = T.xy[j];
+                            const bool e = w.b == kNone || A.masks[w.b + T.orig[j]] != 0;
+                            cx[c] = xy.x;
+                            cy[c] = xy.y;
+                            cthr[c] = e ? thr[T.level[j]] : -1.0f;
+                        }
+                        b_ready = ncol <= kDenseCols;
+                    }
+                    fence_proxy_async();  // operand writes -> the tensor cores' reads
+                    __syncthreads();
+                    if (!s_fail) {
+                        if (tid == 0) {
+                            tc_fence_after();
+                            const uint32_t idesc = idesc_e4m3_f32(kDenseThreads, nmma);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)  // K = 256 bits in steps of 32
+                                tc_mma_e4m3(tbase, smem_desc(sa + 256 * k, 128, kDenseTileBytes),
+                                            smem_desc(sb + 256 * k, 128, kDenseTileBytes), idesc, k > 0);
+                            tc_commit(&bar);
+                        }
+                        bool ok = mbar_wait_bounded(&bar, phase, A.wait_limit);
+                        if (ok && A.starve) ok = mbar_wait_bounded(&never, 0, A.wait_limit);
+                        phase ^= 1u;
+                        if (!ok) s_fail = 1u;
+                        tc_fence_before();
+                        __syncthreads();
+                        tc_fence_after();
+                        if (!s_fail) {
+                            for (int c0 = 0; c0 < nmma; c0 += 32) {
+                                uint32_t v[32];
+                                tc_load32(tlane + (uint32_t)c0, v);
+                                if (tid < rows) {
+#pragma unroll
+                                    for (int k = 0; k < 32; ++k) {
+                                        const int c = c0 + k;
+                                        if (c < nc) {
+                                            const int dot = (int)__int_as_float(v[k]);
+                                            const uint32_t d = (uint32_t)(256 - dot) >> 1;
+                                            const float th = cthr[c];
+                                            if (th >= 0.0f && (!epi || epi_pass(l, cx[c], cy[c], th))) {
+                                                const uint32_t kk = (d << 16) | (uint32_t)(lo + n0 + c);
+                                                sc = min(sc, max(bk, kk) >> 16);
+                                                bk = min(bk, kk);
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncthreads();  // accumulator and operands free for the next tile
+                }
+                if (tid < rows) A.dres[w.c + (uint32_t)p] = s_fail ? make_uint2(kNone, kNone) : make_uint2(bk, sc);
+            }
+            // drop the tile's queries from the list
+            const int rest = qn - rows;
+            const uint16_t v = tid < rest ? qlist[rows + tid] : (uint16_t)0;
+            __syncthreads();
+            if (tid < rest) qlist[tid] = v;
+            qn = rest;
+            __syncthreads();
+        }
+    }
+    // after a wait that ran out, the tile's MMAs may still be in flight: wait for them (again
+    // bounded) before the accumulator is released
+    if (s_fail) mbar_wait_bounded(&bar, phase ^ 1u, A.wait_limit);
+    tc_fence_before();
+    __syncthreads();
+    if (wid == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, kDenseCols);
+    }
 }
 
 
@@ -811,7 +1119,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     __shared__ uint2 qst[8][32];  // per warp (at most 256 threads)
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
-    __shared__ uint32_t keep, scmp;
+    __shared__ uint32_t keep, scmp, sdfail;
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ bool ok_all;
     const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
@@ -836,6 +1144,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
         if (kb) bulk_g2s(tkey, T.node, kb, &bar);
         bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
         scmp = 0u;
+        sdfail = 0u;
     }
     if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
     if (tid < kLevels) {
@@ -892,7 +1201,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     for (int g = wid; g * 32 < nQ; g += nw) {
         QLoad nxt = {};
         if ((g + nw) * 32 < nQ) nxt = load_group(A, w, g + nw);
-        search_group(A, w, T, F, thr, tkey, bst, ep, epos, win, acc, qst[wid], g, cur, cmp);
+        search_group(A, w, T, F, thr, tkey, bst, ep, epos, win, acc, qst[wid], g, cur, cmp, &sdfail);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
@@ -976,7 +1285,7 @@ __global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
     }
     if (tid == 0) {
         A.counts[i] = total;
-        A.item_cmp[i] = scmp;
+        A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
     }
 }
 
@@ -1352,6 +1661,15 @@ cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int p
     return launch_prio(search_kernel, dim3(a.n_search), dim3(threads), smem, s, prio, a);
 }
 
+size_t dense_smem_bytes() { return kDenseSmem; }
+
+cudaError_t launch_dense(const BatchArgs &a, cudaStream_t s, int prio) {
+    if (a.n_search == 0 || a.sp.dense_min <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem);
+    if (e != cudaSuccess) return e;
+    return launch_prio(dense_kernel, dim3(a.n_search * a.dsplit), dim3(kDenseThreads), kDenseSmem, s, prio, a);
+}
+
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio) {
     const uint32_t blocks = a.n_items - a.n_search;
     if (blocks == 0) return cudaSuccess;
@@ -1570,6 +1888,7 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     sc.epipolar = sp.epipolar;
     sc.resolve = sp.resolve;
     sc.rot_filter = sp.rot_filter;
+    sc.dense_min = 0;
     uint32_t *pair_offset = ps.running + 1;  // start of the output (always 0 here)
     if ((e = launch_pair_plain(slot_q, slot_t, q_free, t_free, q->n, t->n, kNoAllocMaxKp, sc, cc, ps,
                                reinterpret_cast<Out3 *>(out), pair_offset, ncmp, l, s)))

@@ -22,6 +22,10 @@ cudaError_t launch_stage_gather(const GatherJob *jobs, int n, unsigned char *bas
 size_t search_smem_bytes(int sn);
 int search_ctas_per_sm(int threads, int sn);
 cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio = 0);
+// Dense node blocks on the tensor cores (a.sp.dense_min > 0): a.n_search * a.dsplit CTAs;
+// writes a.dres, which launch_search then reads (same stream, before it).
+size_t dense_smem_bytes();
+cudaError_t launch_dense(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
 

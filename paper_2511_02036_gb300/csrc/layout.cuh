@@ -138,7 +138,8 @@ struct WorkItem {
     uint32_t out_off;        // first entry of this item's region in the padded output
     uint32_t a;              // search: byte offset of q mask (kNone: all free); fuse: first mp
     uint32_t b;              // search: byte offset of t mask;                   fuse: mp count
-    uint32_t c;              // fuse: first mp of the step (output mp_idx = m - c)
+    uint32_t c;              // fuse: first mp of the step (output mp_idx = m - c);
+                             // search: first entry of the pair's queries in BatchArgs::dres
     uint32_t nq, nt;         // search: keypoint counts
     uint32_t step;           // fuse: step index
     uint32_t cost;           // scheduling estimate
@@ -190,6 +191,7 @@ struct SearchConst {
     int32_t hamming_max, ratio_num, ratio_den;
     float epi_chi2;
     int32_t epipolar, resolve, rot_filter;
+    int32_t dense_min;            // dense node blocks (tensor cores) from this run length; 0 = off
 };
 
 struct FuseConst {
@@ -252,6 +254,9 @@ struct BatchArgs {
     long long wait_limit;         // bound of a bulk-copy wait, SM clock cycles
     uint32_t starve;              // test hook: after the copies, await a barrier nothing arrives
                                   // at, so that the bounded wait runs out
+    uint2 *dres;                  // [sum of nq over search items] per-query (best key, second) of
+                                  // dense queries, at WorkItem::c + position
+    uint32_t dsplit;              // dense kernel CTAs per search item
 };
 
 }  // namespace tmap

@@ -106,6 +106,7 @@ extern "C" void tm_search_params_default(tm_search_params *p) {
     p->rot_filter = 1;
     p->mode = TM_MODE_FUSED;
     p->lanes_per_query = 0;
+    p->dense_min = 0;
 }
 
 extern "C" void tm_fuse_params_default(tm_fuse_params *p) {
@@ -429,7 +430,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &porder, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres})
         b->release();
     h_stage.release();
     h_out.release();
@@ -460,6 +461,7 @@ static SearchConst to_const(const tm_search_params &p) {
     s.epipolar = p.epipolar;
     s.resolve = p.resolve;
     s.rot_filter = p.rot_filter;
+    s.dense_min = p.mode == TM_MODE_FUSED ? p.dense_min : 0;
     return s;
 }
 
@@ -468,6 +470,8 @@ static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &
         return fail(TM_ERR_INVALID_ARG, "bad search parameters");
     if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR)
         return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
+    if (sp.dense_min != 0 && sp.dense_min < 16)
+        return fail(TM_ERR_INVALID_ARG, "dense_min must be 0 or >= 16 (got %d)", sp.dense_min);
     const int l = sp.lanes_per_query;
     if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
         return fail(TM_ERR_INVALID_ARG, "lanes_per_query must be 0, 1, 2, 4, 8, 16 or 32");
@@ -572,7 +576,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.step_pair_begin.assign(n_steps + 1, 0);
     B.step_fuse_item.assign(n_steps + 1, 0);
     B.n_pairs = 0;
-    uint32_t pad = 0;
+    uint32_t pad = 0, dq = 0;
     int smem_n = 32;
     auto slot_of = [&](uint64_t id, int &slot) -> tm_status {
         auto it = c->ids.find(id);
@@ -616,6 +620,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.nq = (uint32_t)nq;
             w.nt = (uint32_t)nt;
             w.cost = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, (uint64_t)nq + nt + (uint64_t)nq * nt / 256);
+            w.c = dq;
+            dq += (uint32_t)nq;
             pad += (uint32_t)(sp.resolve ? std::min(nq, nt) : nq);
             smem_n = std::max(smem_n, std::max(nq, nt));
             items.push_back(w);
@@ -683,7 +689,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.masks.reserve(std::max<size_t>(16, mask_bytes))) ||
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
-        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)))
+        (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
+        (sp.dense_min > 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))))
         return cuda_fail(e, "batch buffers");
     if (B.pointers() != before && (B.graph || B.graph_timed)) {
         if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -745,6 +752,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.wait_limit = c->wait_limit;
     A.starve = c->starve;
     A.sn = B.smem_n;
+    A.dres = static_cast<uint2 *>(B.dres.p);
+    // dense kernel: about two CTAs per SM over the pairs (a CTA takes every dsplit-th dense
+    // run of its pair)
+    A.dsplit = (uint32_t)std::max(1, std::min(64, (2 * c->num_sms + (int)nsi - 1) / (int)nsi));
     B.sp = sp;
     B.fp = fp;
     rollback.armed = false;
@@ -753,7 +764,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, porder.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p};
+            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -812,7 +823,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
-        (e = launch_search(B.args, threads, B.paux, hi_p)) ||
+        (e = launch_dense(B.args, B.paux, hi_p)) || (e = launch_search(B.args, threads, B.paux, hi_p)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
     if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
@@ -885,7 +896,7 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
     if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
-        return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory did not complete in time");
+        return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory or a tensor-core product did not complete in time");
     const uint32_t search_total = ho[B.n_search_items];
     const uint32_t total = ho[B.n_items];
     const size_t nf = total - search_total;
@@ -1233,7 +1244,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         // search (when there are pairs), fuse (when there are map points), copy, ingest (when
         // keyframes enter with the batch)
         P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
-                             1 + (P->B.n_new ? 1 : 0);
+                             1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0);
     } else {
         P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)

@@ -49,7 +49,7 @@ struct IngestStage {
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, porder, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, item_cmp, offsets, ncmp, counters, dense, scratch;
+        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
