@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-node (tensor-core) workload")
     return ap.parse_args()
 
 
@@ -439,6 +440,10 @@ def run_mine(args, rank, world, local_rank):
                       "ms_per_step": 1e3 * el / ke,
                       "api": "tm_batch_run (pinned host buffers: new keyframes, masks, map points in; matches and fusion candidates out) + tm_store_remove_keyframe of the 64 new keyframes"}
 
+    # ---------------------------------------------------------------- dense node blocks
+    if not args.no_dense and rank == 0:
+        out["dense_blocks"] = run_dense(tm, stream, flush, local_rank, max(3, args.steps // 2))
+
     # ---------------------------------------------------------------- serving
     if args.serve_kf > 0 and rank == 0:
         out["serving"] = run_serving(tm, args.serve_kf, local_rank)
@@ -452,6 +457,79 @@ def run_mine(args, rank, world, local_rank):
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def dense_comparisons(w, st, dmin):
+    """(query, candidate) pairs of a step inside dense node blocks: per pair and node with at
+    least dmin neighbour keypoints, eligible queries x eligible neighbour keypoints."""
+    Q = w["frames"][st["q"]]
+    fq = np.ones(Q["n"], bool) if st.get("q_free") is None else np.asarray(st["q_free"]) != 0
+    total = 0
+    for k, t in enumerate(st["nbrs"]):
+        T = w["frames"][t]
+        ft = np.ones(T["n"], bool) if st.get("nbr_free") is None else np.asarray(st["nbr_free"][k]) != 0
+        nodes, counts = np.unique(T["node"], return_counts=True)
+        for nd in nodes[counts >= dmin]:
+            total += int(np.count_nonzero(fq & (Q["node"] == nd))) * int(np.count_nonzero(ft & (T["node"] == nd)))
+    return total
+
+
+def run_dense(tm, stream, flush, device, reps):
+    """cfg3b: the TUM-VI-shaped step (new keyframe + 20 neighbours, 1500 keypoints, 16 BoW
+    nodes, so ~94 x 94 same-node blocks): search with the dense blocks on the tensor cores
+    (dense_min 64) against the candidate rounds (dense_min 0), same results required."""
+    import torch
+    from gen import workloads as W
+    w = W.make_cfg3b()
+    st = w["steps"][0]
+    steps = [dict(kf_id=st["q"], nbrs=st["nbrs"], q_free=st.get("q_free"), nbr_free=st.get("nbr_free"))]
+    out = {"workload": "cfg3b: TUM-VI-shaped step, 512x512 f=190, new keyframe + 20 neighbours, 1500 keypoints, 16 BoW nodes, masks",
+           "dense_min": 64}
+    with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+        ids = [st["q"]] + list(st["nbrs"])
+        ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
+        results = {}
+        for name, dmin in (("tensor_cores", 64), ("candidate_rounds", 0)):
+            with ctx.plan(steps, sp=tm.SearchParams(dense_min=dmin)) as plan:
+                for _ in range(3):
+                    plan.run(stream)
+                torch.cuda.synchronize()
+                res = plan.results(stream)
+                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                for k in range(reps):
+                    flush.zero_()
+                    e0[k].record(stream)
+                    plan.run(stream)
+                    e1[k].record(stream)
+                torch.cuda.synchronize()
+                ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+                stage = []
+                for _ in range(reps):
+                    flush.zero_()
+                    plan.run(stream, timed=True)
+                    stage.append(plan.stage_times())
+                stage = np.array(stage).mean(axis=0)
+                results[name] = res
+                out[name] = {"ms_per_step": ms, "keyframes_per_s": 1e3 / ms,
+                             "gcomparisons_per_s": res.n_comparisons_search / (ms / 1e3) / 1e9,
+                             "search_kernel_ms": float(stage[0]), "dense_kernel_ms": float(stage[4]),
+                             "kernels_per_run": plan.info()["kernels_per_run"]}
+        a, b = results["tensor_cores"], results["candidate_rounds"]
+        assert np.array_equal(a.matches, b.matches) and a.n_comparisons_search == b.n_comparisons_search
+        ncmp_dense = dense_comparisons(w, st, 64)
+        pk, pk_kind = peaks()
+        fp8_peak = 2.0 * pk["bf16_tflops"]  # dense fp8 = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
+        dms = out["tensor_cores"]["dense_kernel_ms"]
+        flops = 2.0 * 256 * ncmp_dense  # one 256-long +-1 dot product per (query, candidate)
+        out["comparisons"] = a.n_comparisons_search
+        out["dense_comparisons"] = ncmp_dense
+        out["speedup"] = out["candidate_rounds"]["ms_per_step"] / out["tensor_cores"]["ms_per_step"]
+        out["roofline"] = {"bound": "tensor", "kernel": "dense_kernel", "achieved": flops / (dms / 1e3) / 1e12,
+                           "peak": fp8_peak, "unit": "TFLOP/s", "frac": flops / (dms / 1e3) / 1e12 / fp8_peak,
+                           "peak_kind": pk_kind + " bf16 burst x 2 (fp8/bf16 nominal ratio)",
+                           "algorithmic_flops": flops, "traffic": None}
+    return out
 
 
 def run_serving(tm, n_kf, device):

@@ -524,8 +524,8 @@ class Plan:
         return dict(threads=a.value, lanes=b.value, ctas=c.value, kernels_per_run=d.value)
 
     def stage_times(self):
-        """(ingest, prep, match, finalize, fusion, offsets + copy) device milliseconds of the last
-        run if it was timed (run(timed=True)); zeros otherwise."""
+        """(search kernel, ingest, fusion, offsets + copy, dense blocks) device milliseconds of
+        the last run if it was timed (run(timed=True)); zeros otherwise."""
         ms = np.zeros(L.TM_PLAN_STAGES, np.float32)
         check(tm_plan_stage_times(self.handle, ms.ctypes.data))  # noqa: F821
         return tuple(float(x) for x in ms)

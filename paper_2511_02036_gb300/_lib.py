@@ -26,7 +26,7 @@ TM_MODE_FUSED = 0
 TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
 TM_MAX_IMAGE_SIZE = 16384
-TM_PLAN_STAGES = 4
+TM_PLAN_STAGES = 5
 TM_DEBUG_WAIT_LIMIT = 1
 TM_DEBUG_STARVE_WAITS = 2
 

@@ -98,10 +98,13 @@ __device__ __forceinline__ Line epi_line(const float *F, float xq, float yq) {
     return l;
 }
 // dist^2 = num^2 / (a^2 + b^2) < thr, division-free: num^2 < thr * den.
-__device__ __forceinline__ bool epi_pass(const Line &l, float xt, float yt, float thr) {
+__device__ __forceinline__ float epi_den(const Line &l) { return fadd(fmul(l.a, l.a), fmul(l.b, l.b)); }
+__device__ __forceinline__ bool epi_pass_den(const Line &l, float den, float xt, float yt, float thr) {
     const float num = fadd(fadd(fmul(l.a, xt), fmul(l.b, yt)), l.c);
-    const float den = fadd(fmul(l.a, l.a), fmul(l.b, l.b));
     return den > 0.0f && fmul(num, num) < fmul(thr, den);
+}
+__device__ __forceinline__ bool epi_pass(const Line &l, float xt, float yt, float thr) {
+    return epi_pass_den(l, epi_den(l), xt, yt, thr);
 }
 
 // Rotation bin: 30 bins of 12 degrees over angle_Q - angle_T wrapped into [0, 360).
@@ -812,32 +815,38 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
 // the dot product of two descriptors is 256 - 2 * Hamming: an integer of magnitude <= 256,
 // exact in the float32 accumulator whatever the summation order.
 //
-// dense_kernel: CTA (pair, split) takes every splits-th dense run of the neighbour.  Per run,
-// tiles of 128 queries x 256 keypoints: both operands expanded into shared memory (K-major
-// core matrices, no swizzle), eight tcgen05.mma of K = 32 issued by one thread into a
-// 128-lane x 256-column float32 accumulator in tensor memory, completion by tcgen05.commit on
-// an mbarrier (bounded wait).  Then thread r reads query r's row (tcgen05.ld) and applies the
-// epipolar gate and the (best, second) merge of the candidate rounds to each column.  The
+// dense_kernel: CTA (pair, split) takes every splits-th dense run of the neighbour (found in
+// its node keys staged in shared memory).  Per run, tiles of 128 queries x 128 keypoints: both
+// operands expanded into shared memory (K-major core matrices, no swizzle; two threads per
+// row, one uint4 of the descriptor each), eight tcgen05.mma of K = 32 issued by one thread
+// into a 128-lane x 128-column float32 accumulator in tensor memory, completion by
+// tcgen05.commit on an mbarrier (bounded wait).  Then the two warps of each 32-lane group read
+// their half of the columns of their lanes' rows (tcgen05.ld) and apply the epipolar gate and
+// the (best, second) merge of the candidate rounds to each column; the halves are merged.  The
 // query's state goes to dres; search_kernel counts the query's comparisons and takes that
 // state instead of visiting its candidates.
 
-constexpr int kDenseThreads = 128;                 // M: one accumulator lane (query) per thread
-constexpr int kDenseCols = 256;                    // N per tile = tensor-memory columns
+constexpr int kDenseRows = 128;                    // M: queries per tile (accumulator lanes)
+constexpr int kDenseCols = 128;                    // N per tile = tensor-memory columns
+constexpr int kDenseThreads = 256;                 // two warps per 32-lane group: column halves
 constexpr int kDenseMinRun = 16;                   // smallest dense_min accepted
 constexpr int kDenseRunCap = TM_MAX_KP_LIMIT / kDenseMinRun;  // dense runs of a neighbour
+constexpr int kDenseScan = 4;                      // query positions per thread and scan pass
+constexpr int kDenseQcap = kDenseRows + kDenseScan * kDenseThreads;  // listed queries, at most
 constexpr uint32_t kDenseTileBytes = 2048;         // 8 rows x 256 one-byte K values
-constexpr uint32_t kDenseA = 0;                                            // 128 x 256 B
-constexpr uint32_t kDenseB = kDenseA + kDenseThreads / 8 * kDenseTileBytes;  // 256 x 256 B
-constexpr uint32_t kDenseCx = kDenseB + kDenseCols / 8 * kDenseTileBytes;
-constexpr uint32_t kDenseCy = kDenseCx + kDenseCols * 4;
-constexpr uint32_t kDenseCthr = kDenseCy + kDenseCols * 4;
-constexpr uint32_t kDenseQlist = kDenseCthr + kDenseCols * 4;             // 2 x 128 u16
-constexpr uint32_t kDenseRuns = kDenseQlist + 2 * kDenseThreads * 2;      // kDenseRunCap u16
-constexpr uint32_t kDenseSmem = kDenseRuns + kDenseRunCap * 2;
-// > 1/3 of an SM's shared memory: at most two dense CTAs per SM, so their 2 x 256 columns
-// never exceed the SM's 512 tensor-memory columns and the allocation cannot wait on a CTA
-// that is not running
-static_assert(3 * (kDenseSmem + 1024) > 233472, "dense CTAs must not exceed two per SM");
+constexpr uint32_t kDenseA = 0;                                          // 128 x 256 B
+constexpr uint32_t kDenseB = kDenseA + kDenseRows / 8 * kDenseTileBytes;  // 128 x 256 B
+constexpr uint32_t kDenseCol = kDenseB + kDenseCols / 8 * kDenseTileBytes;  // float4 (x, y, thr, -)
+constexpr uint32_t kDensePart = kDenseCol + kDenseCols * 16;             // uint2 per row
+constexpr uint32_t kDenseQlist = kDensePart + kDenseRows * 8;            // kDenseQcap u16
+constexpr uint32_t kDenseRuns = kDenseQlist + kDenseQcap * 2;            // kDenseRunCap x (lo, hi) u16
+constexpr uint32_t kDenseSmem = kDenseRuns + kDenseRunCap * 4;
+// the neighbour's node keys are staged in the B area before the first tile
+static_assert(kDenseCols / 8 * kDenseTileBytes >= TM_MAX_KP_LIMIT * 4, "B area holds the keys");
+// > 1/4 of an SM's shared memory: at most three dense CTAs per SM, so their 3 x 128 columns
+// never exceed the SM's 512 tensor-memory columns and an allocation cannot wait on a CTA that
+// is not running
+static_assert(4 * (kDenseSmem + 1024) > 233472, "dense CTAs must not exceed three per SM");
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
@@ -869,26 +878,20 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                      smem_addr(bar))
                  : "memory");
 }
-// 32 consecutive accumulator columns of the warp's 32 lanes (lane = thread), then the wait
-// that makes them valid (the registers pass through the wait so no use moves above it).
-__device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 consecutive accumulator columns of the warp's 32 lanes, then the wait (as tc_load32).
+__device__ __forceinline__ void tc_load16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
-        "%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          "=r"(v[15])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
                    "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
-                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
-                   "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
-                   "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                   "+r"(v[14]), "+r"(v[15])
                  :
                  : "memory");
 }
@@ -909,21 +912,21 @@ __device__ __forceinline__ uint32_t idesc_e4m3_f32(int m, int n) {
 __device__ __forceinline__ uint32_t pm1_bytes(uint32_t x) {
     return (((x * 0x00204081u) & 0x01010101u) << 7) | 0x38383838u;
 }
-// Row r of a K-major operand tile: bit k of the descriptor (32-bit word k / 32) at K index k;
-// 8-row groups kDenseTileBytes apart, 16-byte K chunks 128 bytes apart within a group.
-__device__ __forceinline__ void expand_row(unsigned char *tile, int r, const uint4 *d) {
-    const uint4 a = d[0], b = d[1];
-    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    unsigned char *row = tile + (r >> 3) * kDenseTileBytes + (r & 7) * 16;
+// Half h (descriptor bits 128h .. 128h + 127, one uint4) of row r of a K-major operand tile:
+// bit k of the descriptor (32-bit word k / 32) at K index k; 8-row groups kDenseTileBytes
+// apart, 16-byte K chunks 128 bytes apart within a group.
+__device__ __forceinline__ void expand_half_row(unsigned char *tile, int r, int h, const uint4 &d) {
+    const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+    unsigned char *row = tile + (r >> 3) * kDenseTileBytes + (r & 7) * 16 + h * 8 * 128;
 #pragma unroll
-    for (int kc = 0; kc < 16; ++kc) {
-        const uint32_t h = (w[kc >> 1] >> ((kc & 1) * 16)) & 0xFFFFu;
+    for (int kc = 0; kc < 8; ++kc) {
+        const uint32_t x = (w[kc >> 1] >> ((kc & 1) * 16)) & 0xFFFFu;
         *reinterpret_cast<uint4 *>(row + kc * 128) =
-            make_uint4(pm1_bytes(h & 15u), pm1_bytes((h >> 4) & 15u), pm1_bytes((h >> 8) & 15u), pm1_bytes(h >> 12));
+            make_uint4(pm1_bytes(x & 15u), pm1_bytes((x >> 4) & 15u), pm1_bytes((x >> 8) & 15u), pm1_bytes(x >> 12));
     }
 }
 
-__global__ void __launch_bounds__(kDenseThreads, 1) dense_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ float F[9];
     __shared__ float thr[kLevels];
@@ -931,44 +934,62 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_kernel(BatchArgs A) {
     __shared__ uint32_t s_taddr, s_fail;
     __shared__ __align__(8) uint64_t bar, never;
     unsigned char *sa = dsm + kDenseA, *sb = dsm + kDenseB;
-    float *cx = reinterpret_cast<float *>(dsm + kDenseCx);
-    float *cy = reinterpret_cast<float *>(dsm + kDenseCy);
-    float *cthr = reinterpret_cast<float *>(dsm + kDenseCthr);
+    float4 *col = reinterpret_cast<float4 *>(dsm + kDenseCol);
+    uint2 *part = reinterpret_cast<uint2 *>(dsm + kDensePart);
     uint16_t *qlist = reinterpret_cast<uint16_t *>(dsm + kDenseQlist);
     uint16_t *runs = reinterpret_cast<uint16_t *>(dsm + kDenseRuns);
+    uint32_t *tkey = reinterpret_cast<uint32_t *>(sb);  // the neighbour's node keys, until the first tile
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int row = tid & (kDenseRows - 1), half = tid / kDenseRows;  // warps 4-7: second half
     const uint32_t splits = A.dsplit, item = blockIdx.x / splits, split = blockIdx.x % splits;
     const WorkItem w = A.items[item];
     const KfView T = KfView::at(w.t, A.L);
     const int nQ = (int)w.nq, nT = (int)w.nt, dmin = A.sp.dense_min;
-    // the neighbour's dense runs (node keys ascend), numbered in position order
-    auto dense_start = [&](int j) {
-        const uint32_t k = T.node[j];
-        return (j == 0 || T.node[j - 1] != k) && j + dmin - 1 < nT && T.node[j + dmin - 1] == k;
-    };
-    const int per = (nT + kDenseThreads - 1) / kDenseThreads, jb = min(tid * per, nT), je = min(jb + per, nT);
-    uint32_t cnt = 0;
-    for (int j = jb; j < je; ++j) cnt += dense_start(j) ? 1u : 0u;
-    uint32_t total;
-    uint32_t r = block_scan_add(cnt, wtot, total);
-    for (int j = jb; j < je; ++j)
-        if (dense_start(j)) {
-            if (r % splits == split) runs[r / splits] = (uint16_t)j;
-            ++r;
+    for (int j0 = 0; j0 < nT; j0 += kDenseScan * kDenseThreads) {
+        uint32_t v[kDenseScan];
+#pragma unroll
+        for (int u = 0; u < kDenseScan; ++u) {
+            const int j = j0 + u * kDenseThreads + tid;
+            v[u] = j < nT ? T.node[j] : 0u;
         }
+#pragma unroll
+        for (int u = 0; u < kDenseScan; ++u) {
+            const int j = j0 + u * kDenseThreads + tid;
+            if (j < nT) tkey[j] = v[u];
+        }
+    }
+    __syncthreads();
+    // the neighbour's dense runs (node keys ascend), numbered in position order; this CTA
+    // takes every splits-th
+    const int per = (nT + kDenseThreads - 1) / kDenseThreads, jb = min(tid * per, nT), je = min(jb + per, nT);
+    uint64_t starts = 0;  // bit j - jb: a dense run starts at j (per <= 32)
+    for (int j = jb; j < je; ++j) {
+        const uint32_t k = tkey[j];
+        if ((j == 0 || tkey[j - 1] != k) && j + dmin - 1 < nT && tkey[j + dmin - 1] == k) starts |= 1ull << (j - jb);
+    }
+    uint32_t total;
+    uint32_t r = block_scan_add((uint32_t)__popcll(starts), wtot, total);
+    for (uint64_t m = starts; m; m &= m - 1) {
+        const int j = jb + __ffsll((long long)m) - 1;
+        if (r % splits == split) {
+            runs[2 * (r / splits)] = (uint16_t)j;
+            runs[2 * (r / splits) + 1] = (uint16_t)upper_bound_u32(tkey, j + dmin, nT, tkey[j]);
+        }
+        ++r;
+    }
     const int nrun = total > split ? (int)((total - split + splits - 1) / splits) : 0;
     if (nrun == 0) return;  // uniform: total comes from the block scan
     if (wid == 0) {
         tmem_alloc(&s_taddr, kDenseCols);
         tmem_relinquish();
     }
-    if (tid == 0) {
+    if (tid == 32) {
         mbar_init(&bar, 1);
         mbar_init(&never, 1);
         fence_mbar_init();
         s_fail = 0u;
     }
-    if (wid == 1) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (wid == 2) fundamental_lanes(A.cam, w.pq, w.pt, F);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
@@ -977,118 +998,145 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_kernel(BatchArgs A) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = s_taddr;
-    const uint32_t tlane = tbase + ((uint32_t)(wid * 32) << 16);  // this warp's 32 lanes
+    const uint32_t tlane = tbase + ((uint32_t)((wid & 3) * 32) << 16);  // this warp's 32 lanes
     const bool epi = A.sp.epipolar != 0;
     uint32_t phase = 0;
     for (int rr = 0; rr < nrun; ++rr) {
-        const int lo = runs[rr];
+        const int lo = runs[2 * rr], hi = runs[2 * rr + 1];
         const uint32_t key = T.node[lo];
-        const int hi = upper_bound_u32(T.node, lo + dmin, nT, key);
         const int ncol = hi - lo;
         bool b_ready = false;  // B operand of a one-tile run, kept over its query tiles
-        int scan = 0, qn = 0;  // next query position to scan, queries listed (both uniform)
-        while (scan < nQ || qn > 0) {
-            // list the node's eligible queries, ascending position, until a tile is full
-            while (qn < kDenseThreads && scan < nQ) {
-                const int p = scan + tid;
-                bool f = false;
-                if (p < nQ) {
-                    const uint32_t nk = w.qnode[p];
-                    if ((w.qraw ? node_key(nk) : nk) == key)
-                        f = w.a == kNone || A.masks[w.a + (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p)] != 0;
-                }
-                const unsigned m = __ballot_sync(kFull, f);
-                if (lane == 0) wtot[wid] = (uint32_t)__popc(m);
+        // the node's eligible queries in ascending position: qlist[head .. qn) (uniform counts)
+        int scan = 0, head = 0, qn = 0;
+        for (;;) {
+            if (qn - head < kDenseRows && scan < nQ) {
+                const int rest = qn - head;  // < 128: at most one entry per thread to move
+                const uint16_t v = tid < rest ? qlist[head + tid] : (uint16_t)0;
                 __syncthreads();
-                uint32_t base = (uint32_t)qn, add = 0;
-                for (int k = 0; k < kDenseThreads / 32; ++k) {
-                    const uint32_t v = wtot[k];
-                    if (k < wid) base += v;
-                    add += v;
+                if (tid < rest) qlist[tid] = v;
+                qn = rest;
+                head = 0;
+                while (qn < kDenseRows && scan < nQ) {
+                    uint32_t nk[kDenseScan];
+#pragma unroll
+                    for (int u = 0; u < kDenseScan; ++u) {
+                        const int p = scan + u * kDenseThreads + tid;
+                        nk[u] = p < nQ ? w.qnode[p] : 0u;
+                    }
+                    unsigned m[kDenseScan];
+#pragma unroll
+                    for (int u = 0; u < kDenseScan; ++u) {
+                        const int p = scan + u * kDenseThreads + tid;
+                        bool f = p < nQ && (w.qraw ? node_key(nk[u]) : nk[u]) == key;
+                        if (f && w.a != kNone)
+                            f = A.masks[w.a + (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p)] != 0;
+                        m[u] = __ballot_sync(kFull, f);
+                    }
+                    if (lane == 0)
+#pragma unroll
+                        for (int u = 0; u < kDenseScan; ++u) wtot[u * 8 + wid] = (uint32_t)__popc(m[u]);
+                    __syncthreads();
+                    // entries in (pass u, warp, lane) order = ascending position
+                    uint32_t run = (uint32_t)qn;
+#pragma unroll
+                    for (int u = 0; u < kDenseScan; ++u) {
+                        uint32_t before = run;
+                        for (int k = 0; k < kDenseThreads / 32; ++k) {
+                            const uint32_t c = wtot[u * 8 + k];
+                            if (k < wid) before += c;
+                            run += c;
+                        }
+                        if ((m[u] >> lane) & 1u)
+                            qlist[before + __popc(m[u] & ((1u << lane) - 1u))] = (uint16_t)(scan + u * kDenseThreads + tid);
+                    }
+                    qn = (int)run;
+                    scan += kDenseScan * kDenseThreads;
+                    __syncthreads();
                 }
-                if (f) qlist[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)p;
-                qn += (int)add;
-                scan += kDenseThreads;
-                __syncthreads();
             }
-            const int rows = min(qn, kDenseThreads);
-            if (rows > 0) {
-                const int p = tid < rows ? (int)qlist[tid] : 0;
-                Line l{};
-                uint32_t bk = kNone, sc = 0xFFFFu;
-                if (tid < rows) {
-                    const float2 xq = w.qxy[p];
-                    l = epi_line(F, xq.x, xq.y);
-                    expand_row(sa, tid, w.qdesc + 2 * p);
-                }
-                for (int n0 = 0; n0 < ncol; n0 += kDenseCols) {
-                    const int nc = min(kDenseCols, ncol - n0), nmma = (nc + 31) & ~31;
-                    if (!b_ready) {
-                        for (int c = tid; c < nc; c += kDenseThreads) {
-                            const int j = lo + n0 + c;
-                            expand_row(sb, c, T.desc + 2 * j);
+            const int rows = min(qn - head, kDenseRows);
+            if (rows == 0) break;  // every position scanned and every listed query done
+            const bool mine = row < rows;
+            const int p = mine ? (int)qlist[head + row] : 0;
+            Line l{};
+            float den = 0.0f;
+            uint32_t bk = kNone, sc = 0xFFFFu;
+            if (mine) {
+                const float2 xq = w.qxy[p];
+                l = epi_line(F, xq.x, xq.y);
+                den = epi_den(l);
+                expand_half_row(sa, row, half, w.qdesc[2 * p + half]);
+            }
+            for (int n0 = 0; n0 < ncol; n0 += kDenseCols) {
+                const int nc = min(kDenseCols, ncol - n0), nmma = (nc + 15) & ~15;
+                if (!b_ready) {
+                    if (row < nc) {
+                        const int j = lo + n0 + row;
+                        expand_half_row(sb, row, half, T.desc[2 * j + half]);
+                        if (half == 0) {
                             const float2 xy = T.xy[j];
                             const bool e = w.b == kNone || A.masks[w.b + T.orig[j]] != 0;
-                            cx[c] = xy.x;
-                            cy[c] = xy.y;
-                            cthr[c] = e ? thr[T.level[j]] : -1.0f;
+                            col[row] = make_float4(xy.x, xy.y, e ? thr[T.level[j]] : -1.0f, 0.0f);
                         }
-                        b_ready = ncol <= kDenseCols;
                     }
-                    fence_proxy_async();  // operand writes -> the tensor cores' reads
-                    __syncthreads();
-                    if (!s_fail) {
-                        if (tid == 0) {
-                            tc_fence_after();
-                            const uint32_t idesc = idesc_e4m3_f32(kDenseThreads, nmma);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k)  // K = 256 bits in steps of 32
-                                tc_mma_e4m3(tbase, smem_desc(sa + 256 * k, 128, kDenseTileBytes),
-                                            smem_desc(sb + 256 * k, 128, kDenseTileBytes), idesc, k > 0);
-                            tc_commit(&bar);
-                        }
-                        bool ok = mbar_wait_bounded(&bar, phase, A.wait_limit);
-                        if (ok && A.starve) ok = mbar_wait_bounded(&never, 0, A.wait_limit);
-                        phase ^= 1u;
-                        if (!ok) s_fail = 1u;
-                        tc_fence_before();
-                        __syncthreads();
+                    b_ready = ncol <= kDenseCols;
+                }
+                fence_proxy_async();  // operand writes -> the tensor cores' reads
+                __syncthreads();
+                if (!s_fail) {
+                    if (tid == 0) {
                         tc_fence_after();
-                        if (!s_fail) {
-                            for (int c0 = 0; c0 < nmma; c0 += 32) {
-                                uint32_t v[32];
-                                tc_load32(tlane + (uint32_t)c0, v);
-                                if (tid < rows) {
+                        const uint32_t idesc = idesc_e4m3_f32(kDenseRows, nmma);
 #pragma unroll
-                                    for (int k = 0; k < 32; ++k) {
-                                        const int c = c0 + k;
-                                        if (c < nc) {
-                                            const int dot = (int)__int_as_float(v[k]);
-                                            const uint32_t d = (uint32_t)(256 - dot) >> 1;
-                                            const float th = cthr[c];
-                                            if (th >= 0.0f && (!epi || epi_pass(l, cx[c], cy[c], th))) {
-                                                const uint32_t kk = (d << 16) | (uint32_t)(lo + n0 + c);
-                                                sc = min(sc, max(bk, kk) >> 16);
-                                                bk = min(bk, kk);
-                                            }
+                        for (int k = 0; k < 8; ++k)  // K = 256 bits in steps of 32
+                            tc_mma_e4m3(tbase, smem_desc(sa + 256 * k, 128, kDenseTileBytes),
+                                        smem_desc(sb + 256 * k, 128, kDenseTileBytes), idesc, k > 0);
+                        tc_commit(&bar);
+                    }
+                    bool ok = mbar_wait_bounded(&bar, phase, A.wait_limit);
+                    if (ok && A.starve) ok = mbar_wait_bounded(&never, 0, A.wait_limit);
+                    phase ^= 1u;
+                    if (!ok) s_fail = 1u;
+                    tc_fence_before();
+                    __syncthreads();
+                    tc_fence_after();
+                    if (!s_fail) {
+                        // this warp's half of the columns (split in 16-column steps), 16 at a time
+                        const int mid = ((nmma / 16 + 1) / 2) * 16;
+                        for (int c0 = half ? mid : 0; c0 < (half ? nmma : mid); c0 += 16) {
+                            uint32_t v[16];
+                            tc_load16(tlane + (uint32_t)c0, v);
+                            if (mine) {
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) {
+                                    const int c = c0 + k;
+                                    if (c < nc) {
+                                        const int dot = (int)__int_as_float(v[k]);
+                                        const uint32_t d = (uint32_t)(256 - dot) >> 1;
+                                        const float4 cc = col[c];
+                                        if (cc.z >= 0.0f && (!epi || epi_pass_den(l, den, cc.x, cc.y, cc.z))) {
+                                            const uint32_t kk = (d << 16) | (uint32_t)(lo + n0 + c);
+                                            sc = min(sc, max(bk, kk) >> 16);
+                                            bk = min(bk, kk);
                                         }
                                     }
                                 }
                             }
                         }
                     }
-                    tc_fence_before();
-                    __syncthreads();  // accumulator and operands free for the next tile
                 }
-                if (tid < rows) A.dres[w.c + (uint32_t)p] = s_fail ? make_uint2(kNone, kNone) : make_uint2(bk, sc);
+                tc_fence_before();
+                __syncthreads();  // accumulator and operands free for the next tile
             }
-            // drop the tile's queries from the list
-            const int rest = qn - rows;
-            const uint16_t v = tid < rest ? qlist[rows + tid] : (uint16_t)0;
+            // the two column halves of each query: merged by the first
+            if (half == 1 && mine) part[row] = make_uint2(bk, sc);
             __syncthreads();
-            if (tid < rest) qlist[tid] = v;
-            qn = rest;
-            __syncthreads();
+            if (half == 0 && mine) {
+                const uint2 o = part[row];
+                merge_best2(bk, sc, o.x, o.y);
+                A.dres[w.c + (uint32_t)p] = s_fail ? make_uint2(kNone, kNone) : make_uint2(bk, sc);
+            }
+            head += rows;
         }
     }
     // after a wait that ran out, the tile's MMAs may still be in flight: wait for them (again

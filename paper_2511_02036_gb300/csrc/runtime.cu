@@ -753,9 +753,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.starve = c->starve;
     A.sn = B.smem_n;
     A.dres = static_cast<uint2 *>(B.dres.p);
-    // dense kernel: about two CTAs per SM over the pairs (a CTA takes every dsplit-th dense
-    // run of its pair)
-    A.dsplit = (uint32_t)std::max(1, std::min(64, (2 * c->num_sms + (int)nsi - 1) / (int)nsi));
+    // dense kernel: at most one wave of three CTAs per SM over the pairs (a CTA takes every
+    // dsplit-th dense run of its pair)
+    A.dsplit = (uint32_t)std::max(1, std::min(64, 3 * c->num_sms / (int)nsi));
     B.sp = sp;
     B.fp = fp;
     rollback.armed = false;
@@ -797,7 +797,8 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 //   store:  ingest of new keyframes -> fusion (needs their grids), on s, at low priority;
 // joined before copy (offsets, dense output, comparison totals, status).  `threads` = threads
 // per search CTA.  With `timed`, events E0..E5 mark: start, search done, ingest done, fusion
-// done, copy done, search start (on the search branch, right before the kernel).
+// done, copy done, search start (on the search branch, right before the kernel); E6 (with dense
+// node blocks) between the dense and the search kernel.
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed) {
     cudaError_t e;
     B.threads = threads;
@@ -823,7 +824,9 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
-        (e = launch_dense(B.args, B.paux, hi_p)) || (e = launch_search(B.args, threads, B.paux, hi_p)) ||
+        (e = launch_dense(B.args, B.paux, hi_p)) ||
+        (B.args.sp.dense_min > 0 && B.n_search_items > 0 && (e = mark(6, B.paux))) ||
+        (e = launch_search(B.args, threads, B.paux, hi_p)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
     if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
@@ -1314,13 +1317,15 @@ extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     cudaSetDevice(P->ctx->device);
     cudaError_t e = cudaEventSynchronize(P->B.ev[4]);
     if (e) return cuda_fail(e, "stage events");
-    float t[6] = {0};
-    for (int k = 1; k < 6; ++k)
+    const bool dense = P->B.args.sp.dense_min > 0 && P->B.n_search_items > 0;
+    float t[7] = {0};
+    for (int k = 1; k < (dense ? 7 : 6); ++k)
         if ((e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k]))) return cuda_fail(e, "stage times");
-    ms[0] = t[1] - t[5];                  // search kernel (between the events around it)
+    ms[0] = t[1] - (dense ? t[6] : t[5]); // search kernel (between the events around it)
     ms[1] = t[2];                         // ingest (from the start)
     ms[2] = t[3] - t[2];                  // fusion (after the ingest)
     ms[3] = t[4] - std::max(t[1], t[3]);  // offsets + copy (after both branches)
+    ms[4] = dense ? t[6] - t[5] : 0.0f;   // dense node blocks (before the search kernel)
     return TM_OK;
 }
 

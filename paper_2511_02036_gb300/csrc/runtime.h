@@ -67,7 +67,7 @@ struct BatchBuf {
     BatchArgs args{};
     cudaGraphExec_t graph = nullptr;        // kernels only
     cudaGraphExec_t graph_timed = nullptr;  // the same with events at the stage boundaries
-    cudaEvent_t ev[6] = {};                 // stage boundaries (timed graph)
+    cudaEvent_t ev[7] = {};                 // stage boundaries (timed graph)
     cudaStream_t aux = nullptr;          // (unused)
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)

@@ -125,12 +125,14 @@ def test_dense_plan_counts_its_kernel(tm, dense_step):
         load_step(tm, ctx, w, st)
         with ctx.plan(steps, sp=tm.SearchParams(dense_min=16)) as plan:
             assert plan.info()["kernels_per_run"] == 3  # dense, search, copy
-            for _ in range(2):
-                plan.run()
+            for timed in (False, True):
+                plan.run(timed=timed)
                 res = plan.results()
                 for g, e in zip(res.pairs, exp):
                     np.testing.assert_array_equal(g, e)
                 assert res.n_comparisons_search == ecmp
+            ms = plan.stage_times()
+            assert ms[0] > 0 and ms[4] > 0 and ms[3] > 0  # search, dense, copy
 
 
 def test_dense_bounded_wait_reports_timeout(tm, dense_step):
