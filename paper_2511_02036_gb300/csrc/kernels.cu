@@ -1160,11 +1160,14 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
 //            matches are binned by rotation, the top-3 bins kept, and the pair compacted in
 //            caller query order into its output region.
 // Comparisons (and a timed-out bulk copy) are recorded per item for the copy kernel.
-__global__ void __launch_bounds__(256, 5) search_kernel(BatchArgs A) {
+// kMaxT: largest block size of the instance; 256 (five CTAs per SM, the batched form) or 1024
+// (one CTA per SM: a few large pairs, where more warps per pair hide more latency).
+template <int kMaxT>
+__global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ float F[9];
     __shared__ float thr[kLevels];
-    __shared__ uint2 qst[8][32];  // per warp (at most 256 threads)
+    __shared__ uint2 qst[kMaxT / 32][32];  // per warp
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t keep, scmp, sdfail;
@@ -1694,19 +1697,25 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {
 
 size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 
+// the search kernel instance for a block size
+static void (*search_fn(int threads))(BatchArgs) {
+    return threads <= 256 ? search_kernel<256> : search_kernel<1024>;
+}
+
 int search_ctas_per_sm(int threads, int sn) {
     int n = 0;
     const size_t smem = search_smem_bytes(sn);
-    if (cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_kernel, threads, smem) == cudaSuccess ? n : 0;
+    if (threads < 32 || threads > 1024 || threads % 32) return 0;
+    if (cudaFuncSetAttribute(search_fn(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_fn(threads), threads, smem) == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio) {
     if (a.n_search == 0) return cudaSuccess;
     const size_t smem = search_smem_bytes(a.sn);
-    cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(search_fn(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_prio(search_kernel, dim3(a.n_search), dim3(threads), smem, s, prio, a);
+    return launch_prio(search_fn(threads), dim3(a.n_search), dim3(threads), smem, s, prio, a);
 }
 
 size_t dense_smem_bytes() { return kDenseSmem; }

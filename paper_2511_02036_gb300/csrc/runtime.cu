@@ -933,7 +933,12 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 
 
 // Default launch shape: 256-thread CTAs (several per SM).
-int tmap::default_threads(const BatchBuf &B) { (void)B; return 256; }
+// 256 threads per search CTA (five per SM) for batches of many pairs; with fewer pairs than
+// SMs every pair has an SM of its own, and 1024 threads (32 warps on its 32-query groups) hide
+// more of each pair's load latency.
+int tmap::default_threads(const tm_ctx *c, const BatchBuf &B) {
+    return (int)B.n_search_items * 2 <= c->num_sms ? 1024 : 256;
+}
 
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
@@ -969,12 +974,13 @@ static uint64_t batch_queries(tm_ctx *c, const BatchBuf &B, const tm_step *steps
 // Picks (threads, lanes) for a prepared batch: cached by density class, else measured.
 tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure) {
     tm_status st;
-    if ((st = enqueue_fused(c, B, default_threads(B), c->def_lanes, s))) return st;
+    if ((st = enqueue_fused(c, B, default_threads(c, B), c->def_lanes, s))) return st;
     unsigned long long hc[2];
     cudaError_t e;
     if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "tuning");
-    const int key = density_key(hc[0], batch_queries(c, B, steps));
+    // density class, and whether the pairs are fewer than the SMs (the block size choices differ)
+    const int key = density_key(hc[0], batch_queries(c, B, steps)) * 2 + ((int)B.n_search_items < c->num_sms ? 1 : 0);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) {
         B.threads = it->second.first;
@@ -982,7 +988,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         return TM_OK;
     }
     if (!measure) {
-        B.threads = default_threads(B);
+        B.threads = default_threads(c, B);
         B.lanes = c->def_lanes;
         return TM_OK;
     }
@@ -990,9 +996,10 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt = default_threads(B), bl = c->def_lanes;
+    int bt = default_threads(c, B), bl = c->def_lanes;
     // threads per search CTA (warps sharing one pair); lanes per query only shape the plain form
-    const int threads_set[] = {128, 256};
+    std::vector<int> threads_set = {128, 256};
+    if ((int)B.n_search_items < c->num_sms) threads_set.insert(threads_set.end(), {512, 1024});
     for (int th : threads_set)
         for (int ln : {c->def_lanes}) {
             if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
@@ -1030,9 +1037,11 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     if (sp.mode == TM_MODE_PER_PAIR) {
         st = enqueue_plain(c, B, sp.lanes_per_query ? sp.lanes_per_query : 1, s);
     } else {
-        int th = default_threads(B), ln = c->def_lanes;
+        int th = default_threads(c, B), ln = c->def_lanes;
         if (sp.lanes_per_query) ln = sp.lanes_per_query;
-        else if (c->last_staged == 1) {
+        else if (c->last_staged == 1 && (c->last_threads > 256) == (th > 256)) {
+            // the last tuned plan's choice, if it was made for the same regime (pairs below
+            // or above the SM count)
             th = c->last_threads;
             ln = c->last_lanes;
         }
@@ -1206,7 +1215,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
     tm_status st = prepare_batch(c, P->B, steps, n_steps, in, spd, fpd, s);
     if (!st && spd.mode != TM_MODE_PER_PAIR) {
         if (spd.lanes_per_query) {
-            P->B.threads = default_threads(P->B);
+            P->B.threads = default_threads(c, P->B);
             P->B.lanes = spd.lanes_per_query;
         } else {
             const char *nt = getenv("TM_NO_TUNE");

@@ -129,6 +129,6 @@ tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t
 tm_status tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure);
 void load_tuning(tm_ctx *c, const char *path);
 // Threads per CTA used when no tuned value applies.
-int default_threads(const BatchBuf &B);
+int default_threads(const tm_ctx *c, const BatchBuf &B);
 
 }  // namespace tmap

@@ -273,9 +273,12 @@ bool admit(tm_server *S, Flight &F) {
             tm_status st = prepare_batch(c, F.B, steps.data(), (int)steps.size(), &in, S->cfg.search,
                                          S->cfg.fuse, F.stream);
             if (!st) {
-                int th = default_threads(F.B), ln = c->def_lanes;
+                int th = default_threads(c, F.B), ln = c->def_lanes;
                 if (S->cfg.search.lanes_per_query) ln = S->cfg.search.lanes_per_query;
-                else if (c->last_staged == 1) { th = c->last_threads; ln = c->last_lanes; }
+                else if (c->last_staged == 1 && (c->last_threads > 256) == (th > 256)) {
+                    th = c->last_threads;
+                    ln = c->last_lanes;
+                }
                 st = S->cfg.search.mode == TM_MODE_PER_PAIR ? enqueue_plain(c, F.B, ln, F.stream)
                                                             : enqueue_fused(c, F.B, th, ln, F.stream);
             }
