@@ -349,7 +349,7 @@ __host__ __device__ constexpr size_t ingest_pow2(int cap) {
 // thread: a 1024-thread CTA leaves a third of the register file to the prep CTAs beside it.
 __global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
     extern __shared__ __align__(16) unsigned char ism[];
-    __shared__ uint32_t counts[kBuckets];
+    __shared__ uint32_t counts[kBuckets > kGridCells ? kBuckets : kGridCells];  // both sorts
     __shared__ uint16_t bstart[kBuckets + 1];
     __shared__ uint16_t gs[kGridCells + 1];
     __shared__ uint32_t wtot[32];
@@ -394,6 +394,7 @@ __global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
     float *angle = reinterpret_cast<float *>(base + L.angle);
     uint32_t *node = reinterpret_cast<uint32_t *>(base + L.node);
     uint16_t *orig = reinterpret_cast<uint16_t *>(base + L.orig);
+    uint16_t *pos = reinterpret_cast<uint16_t *>(base + L.pos);
     uint8_t *level = base + L.level;
     for (int p = tid; p < n; p += bs) {
         const uint32_t o = ord[p];
@@ -409,6 +410,7 @@ __global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
         angle[p] = an;
         node[p] = node_key(nd);
         orig[p] = (uint16_t)o;
+        pos[o] = (uint16_t)p;
         level[p] = lv < kLevels ? lv : (uint8_t)(kLevels - 1);
         pcell[p] = (uint16_t)(grid_cell(v.y, A.cell_h_inv, kGridRows) * kGridCols +
                               grid_cell(v.x, A.cell_w_inv, kGridCols));
@@ -495,6 +497,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+// Hint: bring [p, p + bytes) into L2 (16-byte aligned address, size a multiple of 16; no
+// completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, uint32_t bytes) {
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -989,7 +996,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
         fence_mbar_init();
         s_fail = 0u;
     }
-    if (wid == 2) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid < 9) F[tid] = w.F[tid];
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
@@ -1174,8 +1181,8 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ bool ok_all;
     const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
-    const uint32_t i = A.porder[blockIdx.x];
-    const WorkItem w = A.items[i];
+    const WorkItem w = A.sitems[blockIdx.x];
+    const uint32_t i = w.idx;
     const SearchStage S = SearchStage::make(A.sn);
     uint32_t *tkey = reinterpret_cast<uint32_t *>(ssm + S.tkey);
     uint16_t *bst = reinterpret_cast<uint16_t *>(ssm + S.bst);
@@ -1197,7 +1204,14 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         scmp = 0u;
         sdfail = 0u;
     }
-    if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid == 32) {
+        // the arrays the candidate rounds read, into L2 while the setup runs (each neighbour's
+        // descriptors are read once, so their loads would otherwise wait on DRAM)
+        bulk_prefetch_l2(T.desc, 32u * (uint32_t)nT);
+        bulk_prefetch_l2(T.xy, (8u * (uint32_t)nT) & ~15u);
+        bulk_prefetch_l2(w.qdesc, 32u * (uint32_t)nQ);
+    }
+    if (tid < 9) F[tid] = w.F[tid];
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
@@ -1205,20 +1219,24 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     if (tid < 32) hist[tid] = 0u;
     QLoad cur = {};
     if (wid * 32 < nQ) cur = load_group(A, w, wid);  // the first group's loads overlap the setup
+    // the neighbour's eligibility into node order: caller index c's mask byte goes to its
+    // position pos[c] (both loads coalesced and independent)
     constexpr int U = 8;  // targets per thread and pass: all their loads in flight together
     for (int j0 = 0; j0 < nT; j0 += U * bs) {
-        uint32_t o[U];
+        uint32_t m[U], ps[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-            const int j = j0 + k * bs + tid;
-            o[k] = (w.b != kNone && j < nT) ? T.orig[j] : 0u;
+            const int c = j0 + k * bs + tid;
+            const bool in = w.b != kNone && c < nT;
+            m[k] = in ? A.masks[w.b + (uint32_t)c] : 1u;
+            ps[k] = in ? T.pos[c] : (uint32_t)c;
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-            const int j = j0 + k * bs + tid;
-            if (j < nT) {
-                win[j] = kNone;
-                tel[j] = w.b == kNone ? 1 : (A.masks[w.b + o[k]] != 0);
+            const int c = j0 + k * bs + tid;
+            if (c < nT) {
+                win[c] = kNone;
+                tel[ps[k]] = m[k] != 0u;
             }
         }
     }

@@ -7,7 +7,8 @@
 // contiguous range read with consecutive 32-byte descriptor loads.  `bstart` indexes that
 // order by the key's top kBucketBits bits (bucket b = positions bstart[b] .. bstart[b+1]), so
 // a query finds its node's keypoints in one bucket.  `orig` maps a position back to the
-// caller's keypoint index; `grid_start`/`grid_items` index positions by projection-grid cell.
+// caller's keypoint index and `pos` is its inverse; `grid_start`/`grid_items` index positions
+// by projection-grid cell.
 #pragma once
 
 #include <stddef.h>
@@ -38,7 +39,7 @@ struct KfHeader {
 
 // Byte offsets of the arrays of a slot with capacity `cap` keypoints.
 struct SlotLayout {
-    size_t desc, xy, angle, node, orig, level, grid_start, grid_items, bstart, bytes;
+    size_t desc, xy, angle, node, orig, pos, level, grid_start, grid_items, bstart, bytes;
     __host__ __device__ static constexpr SlotLayout make(int cap) {
         SlotLayout L{};
         size_t o = align128(sizeof(KfHeader));
@@ -47,6 +48,7 @@ struct SlotLayout {
         L.angle = o;      o = align128(o + size_t(cap) * 4);
         L.node = o;       o = align128(o + size_t(cap) * 4);
         L.orig = o;       o = align128(o + size_t(cap) * 2);
+        L.pos = o;        o = align128(o + size_t(cap) * 2);
         L.level = o;      o = align128(o + size_t(cap) * 1);
         L.grid_start = o; o = align128(o + size_t(kGridCells + 1) * 2);
         L.grid_items = o; o = align128(o + size_t(cap) * 2);
@@ -64,6 +66,7 @@ struct KfView {
     const float *angle;
     const uint32_t *node;
     const uint16_t *orig;
+    const uint16_t *pos;         // caller index -> position (inverse of orig)
     const uint8_t *level;
     const uint16_t *grid_start;  // [kGridCells + 1]
     const uint16_t *grid_items;  // sorted positions, grouped by cell
@@ -76,6 +79,7 @@ struct KfView {
         v.angle = reinterpret_cast<const float *>(base + L.angle);
         v.node = reinterpret_cast<const uint32_t *>(base + L.node);
         v.orig = reinterpret_cast<const uint16_t *>(base + L.orig);
+        v.pos = reinterpret_cast<const uint16_t *>(base + L.pos);
         v.level = base + L.level;
         v.grid_start = reinterpret_cast<const uint16_t *>(base + L.grid_start);
         v.grid_items = reinterpret_cast<const uint16_t *>(base + L.grid_items);
@@ -126,8 +130,6 @@ constexpr uint32_t kItemTimeout = 0x80000000u;  // item_cmp flag: a bounded wait
 struct WorkItem {
     const unsigned char *q;  // fuse: target keyframe slot
     const unsigned char *t;  // search: neighbour slot
-    const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
-                             // keyframe entering with the batch)
     const uint4 *qdesc;      // search: Q's arrays in the order the search visits Q
     const float2 *qxy;
     const uint32_t *qnode;   //   node keys, or raw node ids if qraw
@@ -143,6 +145,8 @@ struct WorkItem {
     uint32_t nq, nt;         // search: keypoint counts
     uint32_t step;           // fuse: step index
     uint32_t cost;           // scheduling estimate
+    uint32_t idx;            // search: logical index of the item (its counts / comparisons)
+    float F[9];              // search: fundamental matrix of the pair (row-major, x_Q^T F x_T = 0)
 };
 
 constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;
@@ -230,7 +234,7 @@ struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
     uint32_t n_items;
     uint32_t n_search;            // search items come first
-    const uint32_t *porder;       // search CTA b takes item porder[b] (largest pairs first)
+    const WorkItem *sitems;       // the search items in launch order (largest pairs first)
     uint32_t fsn;                 // fusion stage capacity (largest target, rounded to 16)
     uint32_t *counters;           // [2] status of the last run (kStatusTimeout)
     const uint8_t *masks;         // caller-order eligibility masks

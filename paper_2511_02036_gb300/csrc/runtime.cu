@@ -362,6 +362,7 @@ tm_status tmap::store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyfra
         c->slots[slots[k]].n = kfs[k].n;
         c->slots[slots[k]].refs = 0;
         c->slots[slots[k]].id = ids[k];
+        memcpy(c->slots[slots[k]].Tcw, kfs[k].Tcw, sizeof(kfs[k].Tcw));
         c->ids[ids[k]] = slots[k];
     }
     return TM_OK;
@@ -429,7 +430,7 @@ void BatchBuf::release() {
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
-    for (DevBuf *b : {&items, &porder, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
+    for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
                       &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres})
         b->release();
     h_stage.release();
@@ -450,6 +451,52 @@ void BatchBuf::release() {
     if (aux) cudaStreamDestroy(aux);
     fork = join = nullptr;
     aux = nullptr;
+}
+
+// Fundamental matrix of a pair on the host (Sec. IV-C epipolar validation): relative motion
+// R = R_Q R_T^T, t = t_Q - R t_T; F = K^-T [t]x R K^-1 in float64, products evaluated
+// ((K^-T [t]x) R) K^-1, each entry of each 3x3 product summed over k = 0, 1, 2 in that order
+// (no contraction: the host compiler runs with -ffp-contract=off), then rounded to float32.
+// The same operations in the same order as the device's fundamental_lanes (plain form), so
+// both give the same bits.
+static void fundamental_host(const CamConst &cam, const double *Tq, const double *Tt, float *F) {
+    double R[9], t[3], A[9], Bm[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = Tq[r * 4 + 0] * Tt[c * 4 + 0];
+            v = v + Tq[r * 4 + 1] * Tt[c * 4 + 1];
+            v = v + Tq[r * 4 + 2] * Tt[c * 4 + 2];
+            R[r * 3 + c] = v;
+        }
+    for (int r = 0; r < 3; ++r) {
+        double s = R[r * 3 + 0] * Tt[0 * 4 + 3];
+        s = s + R[r * 3 + 1] * Tt[1 * 4 + 3];
+        s = s + R[r * 3 + 2] * Tt[2 * 4 + 3];
+        t[r] = Tq[r * 4 + 3] - s;
+    }
+    const double tx[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
+    const double Ki[9] = {cam.kinv[0], 0.0, cam.kinv[1], 0.0, cam.kinv[2], cam.kinv[3], 0.0, 0.0, 1.0};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = Ki[0 * 3 + r] * tx[0 * 3 + c];
+            v = v + Ki[1 * 3 + r] * tx[1 * 3 + c];
+            v = v + Ki[2 * 3 + r] * tx[2 * 3 + c];
+            A[r * 3 + c] = v;
+        }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = A[r * 3 + 0] * R[0 * 3 + c];
+            v = v + A[r * 3 + 1] * R[1 * 3 + c];
+            v = v + A[r * 3 + 2] * R[2 * 3 + c];
+            Bm[r * 3 + c] = v;
+        }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = Bm[r * 3 + 0] * Ki[0 * 3 + c];
+            v = v + Bm[r * 3 + 1] * Ki[1 * 3 + c];
+            v = v + Bm[r * 3 + 2] * Ki[2 * 3 + c];
+            F[r * 3 + c] = (float)v;
+        }
 }
 
 static SearchConst to_const(const tm_search_params &p) {
@@ -520,6 +567,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             sl.n = in->new_kfs[k].n;
             sl.refs = 0;
             sl.id = in->new_ids[k];
+            memcpy(sl.Tcw, in->new_kfs[k].Tcw, sizeof(sl.Tcw));
             c->ids[in->new_ids[k]] = new_slots[k];
         }
         B.n_new = n_new;
@@ -536,18 +584,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             B->n_new = 0;
         }
     } rollback{c, in, &new_slots, &B};
-    // pose of a keyframe as the prep kernel reads it: from the slot header, or from the ingest
-    // job of a keyframe entering with this batch (so that prep need not wait for its ingest)
     std::unordered_map<int, int> new_index;
     for (size_t k = 0; k < new_slots.size(); ++k) new_index[new_slots[k]] = (int)k;
-    auto pose_of = [&](int slot) -> const double * {
-        auto it = new_index.find(slot);
-        const unsigned char *p = it != new_index.end()
-            ? reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) + sizeof(IngestJob) * (size_t)it->second +
-                  offsetof(IngestJob, Tcw)
-            : c->slots[slot].ptr + offsetof(KfHeader, Tcw);
-        return reinterpret_cast<const double *>(p);
-    };
     // where the search reads a query keyframe: a stored one from its slot, one entering with
     // this batch from its staged caller-order arrays (so that the search need not wait for its
     // ingest)
@@ -603,8 +641,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             WorkItem w{};
             w.q = c->slots[qs].ptr;
             w.t = c->slots[ts].ptr;
-            w.pq = pose_of(qs);
-            w.pt = pose_of(ts);
+            fundamental_host(c->camc, c->slots[qs].Tcw, c->slots[ts].Tcw, w.F);
             const QView qv = qview_of(qs);
             w.qdesc = qv.desc;
             w.qxy = qv.xy;
@@ -680,7 +717,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     const size_t nsi = std::max<size_t>(1, B.n_search_items);
     cudaError_t e;
     std::vector<void *> before = B.pointers();
-    if ((e = B.items.reserve(ni * sizeof(WorkItem))) || (e = B.porder.reserve(nsi * 4)) ||
+    if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nsi * sizeof(WorkItem))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
         (e = B.offsets.reserve((ni + 1) * 4)) ||
         (e = B.ncmp.reserve(16)) || (e = B.counters.reserve(16)) ||
@@ -697,16 +734,18 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         if (B.graph_timed) cudaGraphExecDestroy(B.graph_timed);
         B.graph = B.graph_timed = nullptr;
     }
-    // one pinned staging area, one transfer per table: items, pair order
+    // one pinned staging area, one transfer for both tables: items (logical order), then the
+    // search items again in launch order (each with its logical index)
+    for (uint32_t k = 0; k < B.n_search_items; ++k) items[k].idx = k;
     const size_t o_order = align128(ni * sizeof(WorkItem));
-    const size_t stage = o_order + nsi * 4;
-    if ((e = B.h_stage.reserve(stage))) return cuda_fail(e, "pinned staging");
+    const size_t stage = o_order + order.size() * sizeof(WorkItem);
+    if ((e = B.h_stage.reserve(std::max<size_t>(stage, 128)))) return cuda_fail(e, "pinned staging");
     unsigned char *h = static_cast<unsigned char *>(B.h_stage.p);
     if (!items.empty()) memcpy(h, items.data(), items.size() * sizeof(WorkItem));
-    if (!order.empty()) memcpy(h + o_order, order.data(), order.size() * 4);
-    if ((e = cudaMemcpyAsync(B.items.p, h, items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s)) ||
-        (!order.empty() &&
-         (e = cudaMemcpyAsync(B.porder.p, h + o_order, order.size() * 4, cudaMemcpyHostToDevice, s))))
+    WorkItem *hs = reinterpret_cast<WorkItem *>(h + o_order);
+    for (size_t k = 0; k < order.size(); ++k) hs[k] = items[order[k]];
+    if (!items.empty() &&
+        (e = cudaMemcpyAsync(B.items.p, h, order.empty() ? items.size() * sizeof(WorkItem) : stage, cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "work list upload");
     if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
         return cuda_fail(e, "mask upload");
@@ -725,7 +764,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.items = static_cast<const WorkItem *>(B.items.p);
     A.n_items = B.n_items;
     A.n_search = B.n_search_items;
-    A.porder = static_cast<const uint32_t *>(B.porder.p);
+    A.sitems = reinterpret_cast<const WorkItem *>(static_cast<unsigned char *>(B.items.p) + align128(ni * sizeof(WorkItem)));
     A.counters = static_cast<uint32_t *>(B.counters.p);
     A.masks = static_cast<const uint8_t *>(B.masks.p);
     A.mp_pos = static_cast<const float *>(B.mp_pos.p);
@@ -763,7 +802,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 }
 
 std::vector<void *> BatchBuf::pointers() const {
-    return {items.p, porder.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
+    return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p};
 }
 

@@ -35,6 +35,7 @@ struct Slot {
     int n = 0;
     int refs = 0;
     uint64_t id = 0;
+    double Tcw[12] = {};  // host copy of the pose (pair setup)
 };
 
 // Staging area of keyframe ingest (device copy of the caller-order arrays + pinned mirror).
@@ -48,7 +49,7 @@ struct IngestStage {
 
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
-    DevBuf items, porder, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
+    DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
         counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
