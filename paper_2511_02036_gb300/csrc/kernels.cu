@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
         fence_mbar_init();
         s_fail = 0u;
     }
-    if (tid < 9) F[tid] = w.F[tid];
+    if (wid == 2) fundamental_lanes(A.cam, w.pq, w.pt, F);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
@@ -1211,7 +1211,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         bulk_prefetch_l2(T.xy, (8u * (uint32_t)nT) & ~15u);
         bulk_prefetch_l2(w.qdesc, 32u * (uint32_t)nQ);
     }
-    if (tid < 9) F[tid] = w.F[tid];
+    if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));

@@ -146,7 +146,8 @@ struct WorkItem {
     uint32_t step;           // fuse: step index
     uint32_t cost;           // scheduling estimate
     uint32_t idx;            // search: logical index of the item (its counts / comparisons)
-    float F[9];              // search: fundamental matrix of the pair (row-major, x_Q^T F x_T = 0)
+    const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
+                             // keyframe entering with the batch)
 };
 
 constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;

@@ -362,7 +362,6 @@ tm_status tmap::store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyfra
         c->slots[slots[k]].n = kfs[k].n;
         c->slots[slots[k]].refs = 0;
         c->slots[slots[k]].id = ids[k];
-        memcpy(c->slots[slots[k]].Tcw, kfs[k].Tcw, sizeof(kfs[k].Tcw));
         c->ids[ids[k]] = slots[k];
     }
     return TM_OK;
@@ -441,62 +440,31 @@ void BatchBuf::release() {
             cudaEventDestroy(e);
             e = nullptr;
         }
-    if (fork) cudaEventDestroy(fork);
     if (pfork) cudaEventDestroy(pfork);
-    if (pjoin) cudaEventDestroy(pjoin);
     if (paux) cudaStreamDestroy(paux);
-    pfork = pjoin = nullptr;
-    paux = nullptr;
     if (join) cudaEventDestroy(join);
-    if (aux) cudaStreamDestroy(aux);
-    fork = join = nullptr;
-    aux = nullptr;
+    pfork = join = nullptr;
+    paux = nullptr;
+    if (mpre) cudaEventDestroy(mpre);
+    if (mready) cudaEventDestroy(mready);
+    if (mcopy) cudaStreamDestroy(mcopy);
+    mpre = mready = nullptr;
+    mcopy = nullptr;
+    forked = mp_async = false;
 }
 
-// Fundamental matrix of a pair on the host (Sec. IV-C epipolar validation): relative motion
-// R = R_Q R_T^T, t = t_Q - R t_T; F = K^-T [t]x R K^-1 in float64, products evaluated
-// ((K^-T [t]x) R) K^-1, each entry of each 3x3 product summed over k = 0, 1, 2 in that order
-// (no contraction: the host compiler runs with -ffp-contract=off), then rounded to float32.
-// The same operations in the same order as the device's fundamental_lanes (plain form), so
-// both give the same bits.
-static void fundamental_host(const CamConst &cam, const double *Tq, const double *Tt, float *F) {
-    double R[9], t[3], A[9], Bm[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double v = Tq[r * 4 + 0] * Tt[c * 4 + 0];
-            v = v + Tq[r * 4 + 1] * Tt[c * 4 + 1];
-            v = v + Tq[r * 4 + 2] * Tt[c * 4 + 2];
-            R[r * 3 + c] = v;
-        }
-    for (int r = 0; r < 3; ++r) {
-        double s = R[r * 3 + 0] * Tt[0 * 4 + 3];
-        s = s + R[r * 3 + 1] * Tt[1 * 4 + 3];
-        s = s + R[r * 3 + 2] * Tt[2 * 4 + 3];
-        t[r] = Tq[r * 4 + 3] - s;
-    }
-    const double tx[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
-    const double Ki[9] = {cam.kinv[0], 0.0, cam.kinv[1], 0.0, cam.kinv[2], cam.kinv[3], 0.0, 0.0, 1.0};
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double v = Ki[0 * 3 + r] * tx[0 * 3 + c];
-            v = v + Ki[1 * 3 + r] * tx[1 * 3 + c];
-            v = v + Ki[2 * 3 + r] * tx[2 * 3 + c];
-            A[r * 3 + c] = v;
-        }
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double v = A[r * 3 + 0] * R[0 * 3 + c];
-            v = v + A[r * 3 + 1] * R[1 * 3 + c];
-            v = v + A[r * 3 + 2] * R[2 * 3 + c];
-            Bm[r * 3 + c] = v;
-        }
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double v = Bm[r * 3 + 0] * Ki[0 * 3 + c];
-            v = v + Bm[r * 3 + 1] * Ki[1 * 3 + c];
-            v = v + Bm[r * 3 + 2] * Ki[2 * 3 + c];
-            F[r * 3 + c] = (float)v;
-        }
+// The search branch's stream and events, and the map-point copy stream, created on first use.
+static tm_status ensure_branches(BatchBuf &B) {
+    cudaError_t e;
+    if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
+                    (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
+                    (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming))))
+        return cuda_fail(e, "launch branches");
+    if (!B.mcopy && ((e = cudaStreamCreateWithFlags(&B.mcopy, cudaStreamNonBlocking)) ||
+                     (e = cudaEventCreateWithFlags(&B.mpre, cudaEventDisableTiming)) ||
+                     (e = cudaEventCreateWithFlags(&B.mready, cudaEventDisableTiming))))
+        return cuda_fail(e, "map point stream");
+    return TM_OK;
 }
 
 static SearchConst to_const(const tm_search_params &p) {
@@ -567,7 +535,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             sl.n = in->new_kfs[k].n;
             sl.refs = 0;
             sl.id = in->new_ids[k];
-            memcpy(sl.Tcw, in->new_kfs[k].Tcw, sizeof(sl.Tcw));
             c->ids[in->new_ids[k]] = new_slots[k];
         }
         B.n_new = n_new;
@@ -584,8 +551,19 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             B->n_new = 0;
         }
     } rollback{c, in, &new_slots, &B};
+    // pose of a keyframe as the search kernel reads it: from the slot header, or from the
+    // ingest job of a keyframe entering with this batch (so that the search need not wait for
+    // its ingest)
     std::unordered_map<int, int> new_index;
     for (size_t k = 0; k < new_slots.size(); ++k) new_index[new_slots[k]] = (int)k;
+    auto pose_of = [&](int slot) -> const double * {
+        auto it = new_index.find(slot);
+        const unsigned char *p = it != new_index.end()
+            ? reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) + sizeof(IngestJob) * (size_t)it->second +
+                  offsetof(IngestJob, Tcw)
+            : c->slots[slot].ptr + offsetof(KfHeader, Tcw);
+        return reinterpret_cast<const double *>(p);
+    };
     // where the search reads a query keyframe: a stored one from its slot, one entering with
     // this batch from its staged caller-order arrays (so that the search need not wait for its
     // ingest)
@@ -641,7 +619,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             WorkItem w{};
             w.q = c->slots[qs].ptr;
             w.t = c->slots[ts].ptr;
-            fundamental_host(c->camc, c->slots[qs].Tcw, c->slots[ts].Tcw, w.F);
+            w.pq = pose_of(qs);
+            w.pt = pose_of(ts);
             const QView qv = qview_of(qs);
             w.qdesc = qv.desc;
             w.qxy = qv.xy;
@@ -749,16 +728,37 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         return cuda_fail(e, "work list upload");
     if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
         return cuda_fail(e, "mask upload");
+    // a one-shot batch forks its search branch here (it needs the work list, the masks and the
+    // staged keyframes, not the map points) unless a neighbour enters with the batch, and copies
+    // the map points on a stream of their own that only the fusion kernel awaits
+    cudaStream_t ms = s;
+    B.forked = B.mp_async = false;
+    if (B.early_fork) {
+        if ((st = ensure_branches(B))) return st;
+        if (!(B.n_new > 0 && B.nbr_new)) {
+            if ((e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
+            B.forked = true;
+        }
+        if (mps.n > 0) {
+            if ((e = cudaEventRecord(B.mpre, s)) || (e = cudaStreamWaitEvent(B.mcopy, B.mpre, 0)))
+                return cuda_fail(e, "map point stream");
+            ms = B.mcopy;
+        }
+    }
     if (mps.n > 0) {
         const size_t m = (size_t)mps.n;
-        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, s)) ||
-            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, s)) ||
-            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, s)) ||
-            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, s)) ||
-            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, s)))
+        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, ms)) ||
+            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, ms)) ||
+            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, ms)) ||
+            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, ms)) ||
+            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, ms)))
             return cuda_fail(e, "map point upload");
-        if (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, s)))
+        if (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, ms)))
             return cuda_fail(e, "map point upload");
+        if (ms != s) {
+            if ((e = cudaEventRecord(B.mready, ms))) return cuda_fail(e, "map point stream");
+            B.mp_async = true;
+        }
     }
     BatchArgs &A = B.args;
     A.items = static_cast<const WorkItem *>(B.items.p);
@@ -847,10 +847,8 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if (timed && !B.ev[0])
         for (cudaEvent_t &ev : B.ev)
             if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
-    if (!B.paux && ((e = cudaStreamCreateWithFlags(&B.paux, cudaStreamNonBlocking)) ||
-                    (e = cudaEventCreateWithFlags(&B.pfork, cudaEventDisableTiming)) ||
-                    (e = cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming))))
-        return cuda_fail(e, "launch branches");
+    tm_status bst = ensure_branches(B);
+    if (bst) return bst;
     auto mark = [&](int k, cudaStream_t st) { return timed ? record_stage(B.ev[k], st) : cudaSuccess; };
     // the search branch is the critical path: its CTAs are placed before the store branch's
     // when SMs free up (priorities within the device's range; `hi` is numerically lowest)
@@ -858,7 +856,9 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if ((e = cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p))) return cuda_fail(e, "priorities");
     if ((e = mark(0, s))) return cuda_fail(e, "event");
     const bool after_ingest = B.n_new > 0 && B.nbr_new;
-    if (!after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
+    const bool forked = B.forked, mp_async = B.mp_async;  // set by prepare_batch, for this enqueue only
+    B.forked = B.mp_async = false;
+    if (!after_ingest && !forked && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, lo_p))) return cuda_fail(e, "ingest kernel");
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
@@ -868,6 +868,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
         (e = launch_search(B.args, threads, B.paux, hi_p)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
+    if (mp_async && (e = cudaStreamWaitEvent(s, B.mready, 0))) return cuda_fail(e, "map points");
     if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
         (e = cudaStreamWaitEvent(s, B.join, 0)))
         return cuda_fail(e, "fusion kernel");
@@ -1071,7 +1072,9 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
                                   const tm_batch_inputs *in, const tm_search_params &sp,
                                   const tm_fuse_params &fp, tm_batch_result *res, cudaStream_t s) {
     BatchBuf &B = c->batch;
+    B.early_fork = sp.mode != TM_MODE_PER_PAIR;  // one-shot: nothing of this enqueue is captured
     tm_status st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
+    B.early_fork = false;
     if (st) return st;
     if (sp.mode == TM_MODE_PER_PAIR) {
         st = enqueue_plain(c, B, sp.lanes_per_query ? sp.lanes_per_query : 1, s);

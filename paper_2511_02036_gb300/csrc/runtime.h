@@ -35,7 +35,6 @@ struct Slot {
     int n = 0;
     int refs = 0;
     uint64_t id = 0;
-    double Tcw[12] = {};  // host copy of the pose (pair setup)
 };
 
 // Staging area of keyframe ingest (device copy of the caller-order arrays + pinned mirror).
@@ -69,10 +68,15 @@ struct BatchBuf {
     cudaGraphExec_t graph = nullptr;        // kernels only
     cudaGraphExec_t graph_timed = nullptr;  // the same with events at the stage boundaries
     cudaEvent_t ev[7] = {};                 // stage boundaries (timed graph)
-    cudaStream_t aux = nullptr;          // (unused)
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t join = nullptr;          // end of the search branch
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)
-    cudaEvent_t pfork = nullptr, pjoin = nullptr;
+    cudaEvent_t pfork = nullptr;         // start of the search branch
+    // one-shot batches (early_fork): the search branch forks right after the work list and the
+    // masks are uploaded, and the map points are copied on mcopy, which the fusion kernel
+    // awaits (mready); forked / mp_async say that prepare_batch did so for the next enqueue
+    bool early_fork = false, forked = false, mp_async = false;
+    cudaStream_t mcopy = nullptr;
+    cudaEvent_t mpre = nullptr, mready = nullptr;
     std::vector<void *> pointers() const;
     void release();
 };

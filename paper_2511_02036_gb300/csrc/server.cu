@@ -212,7 +212,6 @@ bool admit(tm_server *S, Flight &F) {
                     sl.n = views[k].n;
                     sl.refs = 0;
                     sl.id = ids[k];
-                    memcpy(sl.Tcw, views[k].Tcw, sizeof(sl.Tcw));
                     c->ids[ids[k]] = slots[k];
                     S->history.push_back(ids[k]);
                 }
