@@ -160,6 +160,9 @@ tm_status tm_store_add_keyframes(tm_ctx *ctx, int32_t n, const uint64_t *kf_ids,
                                  const tm_keyframe_view *kfs, void *stream);
 /* Frees the slot (Sec. IV-B: resident until removed).  TM_ERR_BUSY while a plan uses it. */
 tm_status tm_store_remove_keyframe(tm_ctx *ctx, uint64_t kf_id);
+/* The same for n keyframes; all or nothing (TM_ERR_NOT_FOUND, TM_ERR_BUSY, or
+ * TM_ERR_INVALID_ARG for an id given twice, and nothing is removed). */
+tm_status tm_store_remove_keyframes(tm_ctx *ctx, int32_t n, const uint64_t *kf_ids);
 /* Number of keypoints of a stored keyframe, or TM_ERR_NOT_FOUND. */
 tm_status tm_store_keyframe_size(tm_ctx *ctx, uint64_t kf_id, int32_t *n);
 

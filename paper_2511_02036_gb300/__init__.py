@@ -186,6 +186,56 @@ class FuseParams:
         return L.tm_fuse_params(self.chi2, self.hamming_max, self.radius_scale)
 
 
+@dataclass
+class StepTable:
+    """Local-mapping steps as columns, for batches whose masks and map points are already
+    packed (tm_step fields, one entry per step; the neighbour ids of all steps back to back in
+    step order): kf_id, n_nbrs, nbr_ids, and optionally q_free_off / nbr_free_off (byte offsets
+    into the batch's masks, -1 = all free) and mp_begin / mp_count (range of the batch's map
+    points).  batch_run and plan take it in place of a list of step dicts and then need no
+    Python loop over the pairs."""
+    kf_id: np.ndarray
+    n_nbrs: np.ndarray
+    nbr_ids: np.ndarray
+    q_free_off: np.ndarray = None
+    nbr_free_off: np.ndarray = None
+    mp_begin: np.ndarray = None
+    mp_count: np.ndarray = None
+
+    @classmethod
+    def from_steps(cls, steps):
+        """From step dicts with kf_id, nbrs and the optional offset fields above."""
+        n = len(steps)
+        cnt = np.fromiter((len(s["nbrs"]) for s in steps), np.int32, n)
+        col = lambda k, d, dt: np.fromiter((s.get(k, d) for s in steps), dt, n)  # noqa: E731
+        return cls(np.fromiter((s["kf_id"] for s in steps), np.uint64, n), cnt,
+                   np.fromiter((t for s in steps for t in s["nbrs"]), np.uint64, int(cnt.sum())),
+                   col("q_free_off", -1, np.int64), col("nbr_free_off", -1, np.int64),
+                   col("mp_begin", 0, np.int32), col("mp_count", 0, np.int32))
+
+    def __len__(self):
+        return len(self.kf_id)
+
+    def records(self, keep):
+        """tm_step records (numpy structured array, C layout); the arrays they point into are
+        appended to keep."""
+        n = len(self.kf_id)
+        arr = np.zeros(max(1, n), _STEP_DT)
+        cnt = np.asarray(self.n_nbrs, np.int64)
+        nbrs = np.ascontiguousarray(self.nbr_ids, np.uint64)
+        keep.append(nbrs)
+        off = np.concatenate([[0], np.cumsum(cnt)[:-1]]) if n else np.zeros(0, np.int64)
+        arr["kf_id"][:n] = self.kf_id
+        arr["n_nbrs"][:n] = cnt
+        arr["nbr_ids"][:n] = np.where(cnt > 0, nbrs.ctypes.data + 8 * off, 0)
+        arr["q_free_off"][:n] = -1 if self.q_free_off is None else self.q_free_off
+        arr["nbr_free_off"][:n] = -1 if self.nbr_free_off is None else self.nbr_free_off
+        arr["mp_begin"][:n] = 0 if self.mp_begin is None else self.mp_begin
+        arr["mp_count"][:n] = 0 if self.mp_count is None else self.mp_count
+        keep.append(arr)
+        return arr
+
+
 def _split(arr, offsets):
     return [arr[offsets[k]:offsets[k + 1]] for k in range(len(offsets) - 1)]
 
@@ -289,6 +339,11 @@ def _collect(r, bufs):
 def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
     """Output capacities from the known keyframe sizes (unknown ids: the C call reports them)."""
     g = kf_sizes.get
+    if isinstance(steps, StepTable):
+        # per step only: at most n_Q matches per pair (the looser bound; no lookup per pair)
+        nq = np.fromiter((g(int(k), default) for k in steps.kf_id.tolist()), np.int64, len(steps))
+        mc = int((nq * np.asarray(steps.n_nbrs, np.int64)).sum())
+        return mc, 0 if steps.mp_count is None else int(np.asarray(steps.mp_count, np.int64).sum())
     nq = np.fromiter((g(int(s["kf_id"]), default) for s in steps), np.int64, len(steps))
     cnt = np.fromiter((len(s["nbrs"]) for s in steps), np.int64, len(steps))
     nt = np.fromiter((g(int(t), default) for s in steps for t in s["nbrs"]), np.int64, int(cnt.sum()))
@@ -374,6 +429,13 @@ class Context:
         check(tm_store_remove_keyframe(self.handle, int(kf_id)))  # noqa: F821
         self.sizes.pop(int(kf_id), None)
 
+    def remove_keyframes(self, kf_ids):
+        """Removes several keyframes in one call (all or nothing)."""
+        ids = np.ascontiguousarray(kf_ids, np.uint64)
+        check(tm_store_remove_keyframes(self.handle, len(ids), ids.ctypes.data))  # noqa: F821
+        for i in ids.tolist():
+            self.sizes.pop(i, None)
+
     def keyframe_size(self, kf_id):
         n = ctypes.c_int32()
         check(tm_store_keyframe_size(self.handle, int(kf_id), ctypes.byref(n)))  # noqa: F821
@@ -422,6 +484,9 @@ class Context:
         if masks is None and mps is None:
             st, masks, mps, k2 = pack_batch(steps, self.sizes)
             keep.extend(k2)
+        elif isinstance(steps, StepTable):
+            arr = steps.records(keep)
+            st = arr.ctypes.data
         else:
             n = len(steps)
             arr = np.zeros(max(1, n), _STEP_DT)
@@ -466,7 +531,8 @@ class Context:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
         if self._res is None:
             self._res = _ResultBuffers()
-        r, bufs = self._res.struct(mc, sum(len(s["nbrs"]) for s in steps), fc, len(steps))
+        n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
+        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps))
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
             check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
@@ -499,7 +565,7 @@ class Plan:
         self.caps = _result_caps(steps, ctx.sizes, sp.resolve)
         if mps is not None:
             self.caps = (self.caps[0], max(self.caps[1], int(mps["n"])))
-        self.n_pairs = sum(len(s["nbrs"]) for s in steps)
+        self.n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
         self.n_steps = len(steps)
         h = ctypes.c_void_p()
         sps, fps = sp.struct(), fp.struct()

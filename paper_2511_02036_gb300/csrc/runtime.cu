@@ -12,6 +12,8 @@
 
 #include "runtime.h"
 
+#include <unordered_set>
+
 namespace tmap {
 
 // ------------------------------------------------------------------------- errors
@@ -397,6 +399,30 @@ extern "C" tm_status tm_store_remove_keyframe(tm_ctx *c, uint64_t id) {
     sl.n = 0;
     c->free_slots.push_back(it->second);
     c->ids.erase(it);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_store_remove_keyframes(tm_ctx *c, int32_t n, const uint64_t *ids) {
+    if (!c || n < 0 || (n > 0 && !ids)) return fail(TM_ERR_INVALID_ARG, "tm_store_remove_keyframes: bad arguments");
+    std::lock_guard<std::mutex> lk(c->mu);
+    // all or nothing: every id is checked before any slot is freed
+    std::unordered_set<uint64_t> seen;
+    seen.reserve((size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        auto it = c->ids.find(ids[k]);
+        if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)ids[k]);
+        const Slot &sl = c->slots[it->second];
+        if (sl.refs > 0)
+            return fail(TM_ERR_BUSY, "keyframe %llu is used by %d live plan(s)", (unsigned long long)ids[k], sl.refs);
+        if (!seen.insert(ids[k]).second)
+            return fail(TM_ERR_INVALID_ARG, "keyframe %llu given twice", (unsigned long long)ids[k]);
+    }
+    for (int32_t k = 0; k < n; ++k) {
+        auto it = c->ids.find(ids[k]);
+        c->slots[it->second].n = 0;
+        c->free_slots.push_back(it->second);
+        c->ids.erase(it);
+    }
     return TM_OK;
 }
 

@@ -160,3 +160,23 @@ def test_packed_keyframe_views():
         else:
             assert c.desc is None or c.desc == 0
         off += n
+
+
+def test_step_table_records_match_step_dicts():
+    """StepTable.records gives the same tm_step records as the dict path (pointers aside)."""
+    import paper_2511_02036_gb300 as tm
+    steps = [dict(kf_id=7, nbrs=[1, 2, 3], q_free_off=0, nbr_free_off=10, mp_begin=0, mp_count=5),
+             dict(kf_id=8, nbrs=[], q_free_off=-1, nbr_free_off=-1, mp_begin=5, mp_count=0),
+             dict(kf_id=9, nbrs=[4], mp_begin=5, mp_count=2)]
+    keep = []
+    t = tm.StepTable.from_steps(steps)
+    rec = t.records(keep)
+    assert len(t) == 3 and list(t.nbr_ids) == [1, 2, 3, 4]
+    assert list(rec["kf_id"]) == [7, 8, 9] and list(rec["n_nbrs"]) == [3, 0, 1]
+    assert list(rec["q_free_off"]) == [0, -1, -1] and list(rec["nbr_free_off"]) == [10, -1, -1]
+    assert list(rec["mp_begin"]) == [0, 5, 5] and list(rec["mp_count"]) == [5, 0, 2]
+    nb = keep[0]
+    assert rec["nbr_ids"][0] == nb.ctypes.data and rec["nbr_ids"][1] == 0
+    assert rec["nbr_ids"][2] == nb.ctypes.data + 8 * 3
+    mc, fc = tm._result_caps(t, {7: 100, 8: 50, 9: 10})
+    assert mc == 100 * 3 + 10 * 1 and fc == 7

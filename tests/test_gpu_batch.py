@@ -156,6 +156,44 @@ def test_store_errors(tm):
         assert st == tm.TM_ERR_CAPACITY and n_out.value == 100 and out[0, 0] == -7
 
 
+def test_remove_keyframes_all_or_nothing(tm):
+    cam = W.CAM_CFG0
+    rng = np.random.default_rng(1)
+    with tm.Context(cam, max_kp=256) as ctx:
+        ctx.add_keyframes([1, 2, 3], [W.random_keyframe(rng, 50 + 10 * k, cam) for k in range(3)])
+        for bad, status in (([1, 9], tm.TM_ERR_NOT_FOUND), ([2, 2], tm.TM_ERR_INVALID_ARG)):
+            with pytest.raises(tm.TMError) as e:
+                ctx.remove_keyframes(bad)
+            assert e.value.status == status
+        assert [ctx.keyframe_size(i) for i in (1, 2, 3)] == [50, 60, 70]  # nothing removed
+        ctx.remove_keyframes([3, 1])
+        assert ctx.keyframe_size(2) == 60
+        for i in (1, 3):
+            with pytest.raises(tm.TMError):
+                ctx.keyframe_size(i)
+        ctx.remove_keyframes([])
+
+
+def test_step_table_batches(tm, small_batch):
+    """A batch described by a StepTable (columns) gives the same results as step dicts."""
+    w = small_batch
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        st_arr, masks, mps, _keep = tm.pack_batch(steps_of(w), ctx.sizes)
+        table = tm.StepTable(np.array([st_arr[k].kf_id for k in range(len(w["steps"]))], np.uint64),
+                             np.array([len(s["nbrs"]) for s in w["steps"]], np.int32),
+                             np.concatenate([np.asarray(s["nbrs"], np.uint64) for s in w["steps"]]),
+                             np.array([st_arr[k].q_free_off for k in range(len(w["steps"]))]),
+                             np.array([st_arr[k].nbr_free_off for k in range(len(w["steps"]))]),
+                             np.array([st_arr[k].mp_begin for k in range(len(w["steps"]))], np.int32),
+                             np.array([st_arr[k].mp_count for k in range(len(w["steps"]))], np.int32))
+        assert_same(ctx.batch_run(table, masks=masks, mps=mps), exp)
+        with ctx.plan(table, masks=masks, mps=mps) as plan:
+            plan.run()
+            assert_same(plan.results(), exp)
+
+
 def test_memory_budget_admission(tm):
     cam = W.CAM_CFG0
     rng = np.random.default_rng(1)
