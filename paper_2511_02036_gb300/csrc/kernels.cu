@@ -1278,7 +1278,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     // finalize: one match per target, rotation histogram (results by caller index in tkey[])
     uint32_t *fres = tkey;
     const bool rot = A.sp.rot_filter != 0;
-    constexpr int V = 4;  // queries per thread and pass
+    constexpr int V = 2;  // queries per thread and pass
     for (int p0 = 0; p0 < nQ; p0 += V * bs) {
         uint32_t ac[V], io[V], to[V];
         float qa[V], ta[V];
