@@ -535,6 +535,30 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if (mps.n < 0) return fail(TM_ERR_INVALID_ARG, "negative map point count");
     if (mps.n > 0 && (!mps.pos || !mps.normal || !mps.desc || !mps.min_dist || !mps.max_dist))
         return fail(TM_ERR_INVALID_ARG, "map point arrays must be non-null");
+    std::vector<void *> before = B.pointers();
+    // a one-shot batch copies its map points first, on a stream of their own that only the
+    // fusion kernel awaits, so that the copy runs under the host work below
+    B.forked = B.mp_async = false;
+    bool mp_copied = false;
+    if (B.early_fork && mps.n > 0) {
+        const size_t m = (size_t)mps.n;
+        cudaError_t e;
+        if ((st = ensure_branches(B))) return st;
+        if ((e = B.mp_pos.reserve(m * 12)) || (e = B.mp_normal.reserve(m * 12)) || (e = B.mp_desc.reserve(m * 32)) ||
+            (e = B.mp_min.reserve(m * 4)) || (e = B.mp_max.reserve(m * 4)) || (e = B.mp_skip.reserve(m)))
+            return cuda_fail(e, "batch buffers");
+        if ((e = cudaEventRecord(B.mpre, s)) || (e = cudaStreamWaitEvent(B.mcopy, B.mpre, 0)))
+            return cuda_fail(e, "map point stream");
+        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, B.mcopy)) ||
+            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, B.mcopy)) ||
+            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, B.mcopy)) ||
+            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, B.mcopy)) ||
+            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, B.mcopy)) ||
+            (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, B.mcopy))) ||
+            (e = cudaEventRecord(B.mready, B.mcopy)))
+            return cuda_fail(e, "map point upload");
+        B.mp_async = mp_copied = true;
+    }
     // keyframes entering the store with this batch: reserve slots and stage them; the ingest
     // kernel runs at the head of every launch of the batch
     B.n_new = 0;
@@ -721,7 +745,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     const size_t nm = std::max<int>(1, mps.n);
     const size_t nsi = std::max<size_t>(1, B.n_search_items);
     cudaError_t e;
-    std::vector<void *> before = B.pointers();
     if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nsi * sizeof(WorkItem))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
         (e = B.offsets.reserve((ni + 1) * 4)) ||
@@ -755,23 +778,16 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if (mask_bytes && (e = cudaMemcpyAsync(B.masks.p, in->masks, mask_bytes, cudaMemcpyDefault, s)))
         return cuda_fail(e, "mask upload");
     // a one-shot batch forks its search branch here (it needs the work list, the masks and the
-    // staged keyframes, not the map points) unless a neighbour enters with the batch, and copies
-    // the map points on a stream of their own that only the fusion kernel awaits
-    cudaStream_t ms = s;
-    B.forked = B.mp_async = false;
+    // staged keyframes, not the map points) unless a neighbour enters with the batch
     if (B.early_fork) {
         if ((st = ensure_branches(B))) return st;
         if (!(B.n_new > 0 && B.nbr_new)) {
             if ((e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
             B.forked = true;
         }
-        if (mps.n > 0) {
-            if ((e = cudaEventRecord(B.mpre, s)) || (e = cudaStreamWaitEvent(B.mcopy, B.mpre, 0)))
-                return cuda_fail(e, "map point stream");
-            ms = B.mcopy;
-        }
     }
-    if (mps.n > 0) {
+    const cudaStream_t ms = s;
+    if (mps.n > 0 && !mp_copied) {
         const size_t m = (size_t)mps.n;
         if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, ms)) ||
             (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, ms)) ||
@@ -781,10 +797,6 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             return cuda_fail(e, "map point upload");
         if (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, ms)))
             return cuda_fail(e, "map point upload");
-        if (ms != s) {
-            if ((e = cudaEventRecord(B.mready, ms))) return cuda_fail(e, "map point stream");
-            B.mp_async = true;
-        }
     }
     BatchArgs &A = B.args;
     A.items = static_cast<const WorkItem *>(B.items.p);
@@ -1101,7 +1113,12 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     B.early_fork = sp.mode != TM_MODE_PER_PAIR;  // one-shot: nothing of this enqueue is captured
     tm_status st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
     B.early_fork = false;
-    if (st) return st;
+    if (st) {
+        // copies of the caller's arrays may be in flight: done before the call returns
+        if (B.mcopy) cudaStreamSynchronize(B.mcopy);
+        cudaStreamSynchronize(s);
+        return st;
+    }
     if (sp.mode == TM_MODE_PER_PAIR) {
         st = enqueue_plain(c, B, sp.lanes_per_query ? sp.lanes_per_query : 1, s);
     } else {
@@ -1117,6 +1134,7 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     }
     if (!st) st = fetch_results(c, B, res, s);
     if (st) {
+        if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(s);
         drop_new_keyframes(c, B, in);
     }
