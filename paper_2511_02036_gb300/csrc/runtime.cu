@@ -638,7 +638,13 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     items.clear();
     B.item_nq.clear();
     B.item_nt.clear();
+    size_t n_pairs_max = 0;
+    for (int k = 0; k < n_steps; ++k) n_pairs_max += (size_t)std::max(0, steps[k].n_nbrs);
+    items.reserve(n_pairs_max + 64);
+    B.item_nq.reserve(n_pairs_max);
+    B.item_nt.reserve(n_pairs_max);
     std::vector<int> slots_used;
+    slots_used.reserve(n_pairs_max + (size_t)n_steps + new_slots.size());
     B.step_pair_begin.assign(n_steps + 1, 0);
     B.step_fuse_item.assign(n_steps + 1, 0);
     B.n_pairs = 0;
@@ -660,6 +666,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             return fail(TM_ERR_INVALID_ARG, "step %d: query mask outside masks", k);
         B.step_pair_begin[k] = B.n_pairs;
         size_t toff = S.nbr_free_off >= 0 ? (size_t)S.nbr_free_off : 0;
+        const double *pq = pose_of(qs);  // the query keyframe's parts, once per step
+        const QView qv = qview_of(qs);
+        unsigned char *qptr = c->slots[qs].ptr;
         for (int j = 0; j < S.n_nbrs; ++j) {
             int ts;
             if ((st = slot_of(S.nbr_ids[j], ts))) return st;
@@ -667,18 +676,21 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             if (S.nbr_free_off >= 0 && toff + (size_t)nt > mask_bytes)
                 return fail(TM_ERR_INVALID_ARG, "step %d: neighbour masks outside masks", k);
             WorkItem w{};
-            w.q = c->slots[qs].ptr;
+            w.q = qptr;
             w.t = c->slots[ts].ptr;
-            w.pq = pose_of(qs);
-            w.pt = pose_of(ts);
-            const QView qv = qview_of(qs);
+            w.pq = pq;
+            const auto tn = new_index.find(ts);
+            w.pt = tn != new_index.end()
+                ? reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) +
+                                                   sizeof(IngestJob) * (size_t)tn->second + offsetof(IngestJob, Tcw))
+                : reinterpret_cast<const double *>(c->slots[ts].ptr + offsetof(KfHeader, Tcw));
             w.qdesc = qv.desc;
             w.qxy = qv.xy;
             w.qnode = qv.node;
             w.qorig = qv.orig;
             w.qangle = qv.angle;
             w.qraw = qv.raw;
-            B.nbr_new |= new_index.count(ts) != 0;
+            B.nbr_new |= tn != new_index.end();
             w.kind = kItemSearch;
             w.out_off = pad;
             w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;
