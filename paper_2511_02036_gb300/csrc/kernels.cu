@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     __shared__ uint2 qst[kMaxT / 32][32];  // per warp
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
-    __shared__ uint32_t keep, scmp, sdfail;
+    __shared__ uint32_t keep, scmp, sdfail, nacc;
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ bool ok_all;
     const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
@@ -1203,6 +1203,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
         scmp = 0u;
         sdfail = 0u;
+        nacc = 0u;
     }
     if (tid == 32) {
         // the arrays the candidate rounds read, into L2 while the setup runs (each neighbour's
@@ -1275,46 +1276,40 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     }
     warp_count(cmp, &scmp);
     __syncthreads();
-    // finalize: one match per target, rotation histogram (results by caller index in tkey[])
+    // finalize: one match per target, rotation histogram (results by caller index in tkey[]).
+    // Only the accepted queries are visited: their positions are listed first (in ep[], free
+    // after the search) by a ballot compaction of acc[].
     uint32_t *fres = tkey;
+    uint16_t *alist = ep;
     const bool rot = A.sp.rot_filter != 0;
-    constexpr int V = 2;  // queries per thread and pass
-    for (int p0 = 0; p0 < nQ; p0 += V * bs) {
-        uint32_t ac[V], io[V], to[V];
-        float qa[V], ta[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const int p = p0 + k * bs + tid;
-            ac[k] = p < nQ ? acc[p] : kNone;
-            io[k] = p < nQ ? (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p) : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const int p = p0 + k * bs + tid;
-            const uint32_t j = ac[k] >> 16;
-            const bool a = ac[k] != kNone && (!A.sp.resolve || win[j] == (((ac[k] & 0xFFFFu) << 16) | io[k]));
-            if (!a) ac[k] = kNone;
-            to[k] = a ? (uint32_t)T.orig[j] : 0u;
-            qa[k] = (a && rot) ? w.qangle[p] : 0.0f;
-            ta[k] = (a && rot) ? T.angle[j] : 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const int p = p0 + k * bs + tid;
-            uint32_t bin = kNone;
-            if (p < nQ) {
-                uint32_t r = kNone;
-                if (ac[k] != kNone) {
-                    bin = rot ? (uint32_t)rot_bin(qa[k], ta[k]) : 0u;
-                    r = pack_res(to[k], ac[k] & 0xFFFFu, bin);
-                }
-                fres[io[k]] = r;
+    const int ln = tid & 31;
+    for (int q = tid; q < nQ; q += bs) fres[q] = kNone;
+    for (int p0 = 0; p0 < nQ; p0 += bs) {
+        const int p = p0 + tid;
+        const bool a = p < nQ && acc[p] != kNone;
+        const unsigned m = __ballot_sync(kFull, a);
+        uint32_t base = 0;
+        if (ln == 0 && m) base = atomicAdd(&nacc, (uint32_t)__popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (a) alist[base + __popc(m & ((1u << ln) - 1u))] = (uint16_t)p;
+    }
+    __syncthreads();
+    const int na = (int)nacc;
+    for (int e0 = 0; e0 < na; e0 += bs) {
+        const int e = e0 + tid;
+        uint32_t bin = kNone;
+        if (e < na) {
+            const int p = alist[e];
+            const uint32_t ac = acc[p], j = ac >> 16, d = ac & 0xFFFFu;
+            const uint32_t io = w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p;
+            if (!A.sp.resolve || win[j] == ((d << 16) | io)) {
+                bin = rot ? (uint32_t)rot_bin(w.qangle[p], T.angle[j]) : 0u;
+                fres[io] = pack_res(T.orig[j], d, bin);
             }
-            if (rot) {
-                const unsigned peers = __match_any_sync(kFull, bin);
-                if (bin != kNone && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1))
-                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-            }
+        }
+        if (rot) {
+            const unsigned peers = __match_any_sync(kFull, bin);
+            if (bin != kNone && ln == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
     }
     __syncthreads();
