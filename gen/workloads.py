@@ -299,7 +299,37 @@ class Sequence:
             self.frames.append(permute_keyframe(kf, rng.permutation(int(n_kp[k]))))
 
     # ------------------------------------------------------------------ one local-mapping step
-    def step(self, q, nbrs, n_mps=None, tracked_frac=0.5, with_masks=True, clutter_mp_frac=None):
+    def _forward_mps(self, q, mapped_obs, nbr_mapped_w, nbr_w):
+        """The new keyframe's own map points (see step) and their per-neighbour skip bytes."""
+        fq = self.frames[q]
+        rng = np.random.default_rng([len(self.frames), q, 0x5eed])
+        wq = fq["wp"]
+        new_obs = wq >= 0
+        new_obs[new_obs] = ~self.mapped[wq[new_obs]]
+        idx = np.nonzero(mapped_obs | new_obs)[0]
+        wps, first = np.unique(wq[idx], return_index=True)
+        j = idx[first]  # the first observing keypoint of each world point
+        is_new = ~self.mapped[wps]
+        n = len(wps)
+        pos = self.pts[wps] + rng.normal(0, 0.005, (n, 3))
+        c = camera_center(fq["Tcw"])
+        v = pos - c
+        dist = np.linalg.norm(v, axis=1)
+        maxd = dist * SCALE_FACTOR ** fq["level"][j].astype(np.int64)
+        mps = dict(n=n, pos=pos.astype(np.float32).reshape(n, 3),
+                   normal=(v / dist[:, None]).astype(np.float32).reshape(n, 3),
+                   desc=np.ascontiguousarray(fq["desc"][j]).reshape(n, DESC_BYTES),
+                   min_dist=(maxd / SCALE_FACTOR ** (N_LEVELS - 1)).astype(np.float32),
+                   max_dist=maxd.astype(np.float32), wp=wps)
+        partner = np.full(n, -1)  # a new point's triangulation partner: the first neighbour seeing it
+        for k in range(len(nbr_w) - 1, -1, -1):
+            partner[np.isin(wps, nbr_w[k])] = k
+        skip = [(np.where(is_new, partner == k, np.isin(wps, mw))).astype(np.uint8)
+                for k, mw in enumerate(nbr_mapped_w)]
+        return mps, skip
+
+    def step(self, q, nbrs, n_mps=None, tracked_frac=0.5, with_masks=True, clutter_mp_frac=None,
+             forward=False):
         """The local-mapping step of keyframe `q` against neighbour frames `nbrs`.
 
         Masks: a keypoint is not free for triangulation when it already has a map point.
@@ -310,7 +340,17 @@ class Sequence:
 
         Map points: position = world point + N(0, 5 mm); descriptor = that of its first
         observing neighbour; normal = mean unit viewing direction over observing neighbours;
-        maxDist = distance to the first observer * 1.2^level, minDist = maxDist / 1.2^7."""
+        maxDist = distance to the first observer * 1.2^level, minDist = maxDist / 1.2^7.
+
+        forward=True adds the new keyframe's own map points as fwd_mps: one per world point
+        it observes that is either mapped (tracked) or shared but not yet mapped (as if just
+        triangulated from this step's matches), from its first keypoint of that point:
+        position + N(0, 5 mm), that keypoint's descriptor, the unit direction from the new
+        keyframe's centre, maxDist = distance * 1.2^level.  Per neighbour, fwd_skip is 1 where
+        the neighbour already observes the point: for a mapped point, any neighbour with a
+        keypoint of it; for a new point, its triangulation partner (the first neighbour with
+        a keypoint of it).  Drawn from a stream of their own, so the rest of the step is the
+        same with or without them."""
         rng = self.rng
         fq = self.frames[q]
         q_wp = fq["wp"]
@@ -320,7 +360,7 @@ class Sequence:
         tracked[mq] = rng.random(int(mq.sum())) < tracked_frac
         tracked_wp = np.unique(q_wp[tracked])
         q_free = (~tracked).astype(np.uint8)
-        nbr_has, obs_w, obs_f, obs_j, clutter = [], [], [], [], []
+        nbr_has, obs_w, obs_f, obs_j, clutter, nbr_mapped_w, nbr_w = [], [], [], [], [], [], []
         for f in nbrs:
             fr = self.frames[f]
             w = fr["wp"]
@@ -328,6 +368,8 @@ class Sequence:
             pool_idx = np.nonzero(w >= 0)[0]
             sel = pool_idx[self.mapped[w[pool_idx]]]
             has[sel] = True
+            nbr_mapped_w.append(w[sel])
+            nbr_w.append(w[w >= 0])
             obs_w.append(w[sel]); obs_f.append(np.full(len(sel), f)); obs_j.append(sel)
             clutter.append(np.nonzero(w < 0)[0])
             nbr_has.append(has)
@@ -393,6 +435,8 @@ class Sequence:
             for k in ("pos", "normal", "desc", "min_dist", "max_dist", "skip", "wp"):
                 mps[k] = np.ascontiguousarray(mps[k][perm])
         step = dict(q=q, nbrs=list(nbrs), mps=mps)
+        if forward:
+            step["fwd_mps"], step["fwd_skip"] = self._forward_mps(q, mq, nbr_mapped_w, nbr_w)
         if with_masks:
             step["q_free"] = q_free
             step["nbr_free"] = [(~h).astype(np.uint8) for h in nbr_has]
@@ -405,7 +449,7 @@ class Sequence:
 # --------------------------------------------------------------------------- configurations
 
 def make_step_workload(seed, cam, n_nbrs, n_kp, share, flip_p, n_nodes, n_mps=None,
-                       spacing=0.125, with_masks=True, noise_scale_px=1.0):
+                       spacing=0.125, with_masks=True, noise_scale_px=1.0, forward=False):
     """One local-mapping step: the new keyframe is the last frame of a short trajectory and
     its covisible neighbours are the `n_nbrs` frames before it."""
     rng = np.random.default_rng(seed)
@@ -416,13 +460,13 @@ def make_step_workload(seed, cam, n_nbrs, n_kp, share, flip_p, n_nodes, n_mps=No
                    noise_scale_px=noise_scale_px)
     q = nf - 1
     nbrs = list(range(q - 1, -1, -1))
-    step = seq.step(q, nbrs, n_mps=n_mps, with_masks=with_masks)
+    step = seq.step(q, nbrs, n_mps=n_mps, with_masks=with_masks, forward=forward)
     return dict(cam=cam, frames=seq.frames, steps=[step])
 
 
-def make_cfg1(seed=1000, with_masks=True, scale=1.0):
+def make_cfg1(seed=1000, with_masks=True, scale=1.0, forward=False):
     return make_step_workload(seed, CAM_EUROC, 10, int(1200 * scale), 0.4, 0.06, 1000,
-                              n_mps=int(6000 * scale), with_masks=with_masks)
+                              n_mps=int(6000 * scale), with_masks=with_masks, forward=forward)
 
 
 def make_cfg3(seed=3000, n_nodes=10000, with_masks=True, n_nbrs=20, n_kp=1500):
@@ -435,7 +479,7 @@ def make_cfg3b(seed=3500, **kw):
 
 
 def make_cfg2(seed=2000, n_steps=64, nbr_range=(5, 20), kp_range=(600, 2000),
-              with_masks=True):
+              with_masks=True, forward=False):
     """Independent local-mapping steps with uneven neighbour and keypoint counts, all with
     the cfg1 camera, descriptor and vocabulary model.  Frames of all steps are numbered
     consecutively in one `frames` list."""
@@ -448,7 +492,7 @@ def make_cfg2(seed=2000, n_steps=64, nbr_range=(5, 20), kp_range=(600, 2000),
         poses = trajectory(nn + 1, 0.125, heading0=sub.uniform(0, 360))
         seq = Sequence(sub, CAM_EUROC, poses, nkp, 0.4, 0.06, 1000)
         q = nn
-        st = seq.step(q, list(range(q - 1, -1, -1)), with_masks=with_masks)
+        st = seq.step(q, list(range(q - 1, -1, -1)), with_masks=with_masks, forward=forward)
         base = len(frames)
         frames.extend(seq.frames)
         st["q"] += base

@@ -202,6 +202,14 @@ typedef struct {
     int64_t nbr_free_off;    /* byte offset of the neighbours' concatenated masks, -1 = free*/
     int32_t mp_begin;        /* this step's map points are mps[mp_begin, mp_begin+mp_count) */
     int32_t mp_count;        /*   fused into kf_id; 0 = no fusion                           */
+    /* Forward fusion (Sec. IV-D, the other direction): the new keyframe's own map points
+     * mps[fwd_mp_begin, fwd_mp_begin+fwd_mp_count) fused into every neighbour.  fwd_skip_off:
+     * byte offset in masks of n_nbrs x fwd_mp_count bytes, neighbour-major (1 = the map point
+     * is already observed by that neighbour: skipped), or -1 = none skipped.  Read only when
+     * fwd_mp_count > 0. */
+    int32_t fwd_mp_begin;
+    int32_t fwd_mp_count;
+    int64_t fwd_skip_off;
 } tm_step;
 
 typedef struct {
@@ -221,13 +229,19 @@ typedef struct {
 /* Results, host buffers.  Search matches of all steps, step-major then neighbour order:
  * pair p (counting pairs over all steps) is matches[pair_offsets[p] .. pair_offsets[p+1]).
  * Fusion candidates of step s are fuse[fuse_offsets[s] .. fuse_offsets[s+1]), mp_idx
- * relative to the step's mp_begin. */
+ * relative to the step's mp_begin.  Forward-fusion candidates of pair p (the step's new
+ * keyframe's map points in neighbour p's keypoints) are fwd[fwd_offsets[p] ..
+ * fwd_offsets[p+1]), mp_idx relative to the step's fwd_mp_begin; fwd and fwd_offsets may be
+ * NULL when no step asks for forward fusion. */
 typedef struct {
     tm_match *matches; size_t match_cap; size_t n_matches;
     int32_t *pair_offsets;   /* [total pairs + 1]                                           */
     tm_fuse_match *fuse; size_t fuse_cap; size_t n_fuse;
     int32_t *fuse_offsets;   /* [n_steps + 1]                                               */
     uint64_t n_comparisons_search, n_comparisons_fuse;
+    tm_fuse_match *fwd; size_t fwd_cap; size_t n_fwd;
+    int32_t *fwd_offsets;    /* [total pairs + 1]                                           */
+    uint64_t n_comparisons_fwd;
 } tm_batch_result;
 
 /* One-shot: upload, one launch sequence, download.  TM_ERR_CAPACITY sets n_matches and

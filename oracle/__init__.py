@@ -209,3 +209,22 @@ def fuse_step(cam, frames, step, params=None):
     if step.get("mps") is None:
         return np.zeros((0, 3), np.int32), 0
     return fuse(cam, frames[step["q"]], step["mps"], params)
+
+
+def fuse_forward_step(cam, frames, step, params=None):
+    """Forward fusion of a step (Sec. IV-D, the other direction): the new keyframe's own map
+    points fused into each neighbour in turn, skipping those the neighbour already observes.
+    The same per-keyframe fusion as fuse(), applied per neighbour; returns per neighbour an
+    int32 (k, 3) array of (mp_idx, kp_idx, dist) and the total number of window comparisons."""
+    fw = step.get("fwd_mps")
+    if fw is None:
+        return [np.zeros((0, 3), np.int32) for _ in step["nbrs"]], 0
+    res, ncmp = [], 0
+    for k, f in enumerate(step["nbrs"]):
+        mps = dict(fw)
+        sk = step.get("fwd_skip")
+        mps["skip"] = None if sk is None else np.asarray(sk[k], np.uint8)
+        r, c = fuse(cam, frames[f], mps, params)
+        res.append(r)
+        ncmp += c
+    return res, ncmp

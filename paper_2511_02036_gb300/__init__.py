@@ -201,6 +201,9 @@ class StepTable:
     nbr_free_off: np.ndarray = None
     mp_begin: np.ndarray = None
     mp_count: np.ndarray = None
+    fwd_mp_begin: np.ndarray = None
+    fwd_mp_count: np.ndarray = None
+    fwd_skip_off: np.ndarray = None
 
     @classmethod
     def from_steps(cls, steps):
@@ -211,7 +214,9 @@ class StepTable:
         return cls(np.fromiter((s["kf_id"] for s in steps), np.uint64, n), cnt,
                    np.fromiter((t for s in steps for t in s["nbrs"]), np.uint64, int(cnt.sum())),
                    col("q_free_off", -1, np.int64), col("nbr_free_off", -1, np.int64),
-                   col("mp_begin", 0, np.int32), col("mp_count", 0, np.int32))
+                   col("mp_begin", 0, np.int32), col("mp_count", 0, np.int32),
+                   col("fwd_mp_begin", 0, np.int32), col("fwd_mp_count", 0, np.int32),
+                   col("fwd_skip_off", -1, np.int64))
 
     def __len__(self):
         return len(self.kf_id)
@@ -232,6 +237,9 @@ class StepTable:
         arr["nbr_free_off"][:n] = -1 if self.nbr_free_off is None else self.nbr_free_off
         arr["mp_begin"][:n] = 0 if self.mp_begin is None else self.mp_begin
         arr["mp_count"][:n] = 0 if self.mp_count is None else self.mp_count
+        arr["fwd_mp_begin"][:n] = 0 if self.fwd_mp_begin is None else self.fwd_mp_begin
+        arr["fwd_mp_count"][:n] = 0 if self.fwd_mp_count is None else self.fwd_mp_count
+        arr["fwd_skip_off"][:n] = -1 if self.fwd_skip_off is None else self.fwd_skip_off
         keep.append(arr)
         return arr
 
@@ -244,7 +252,9 @@ def pack_batch(steps, kf_sizes):
     """Concatenate the masks and map points of local-mapping steps into one batch.
 
     steps: dicts with kf_id, nbrs (ids), optional q_free [n_Q], nbr_free (list of [n_T]),
-    optional mps (map-point dict).  kf_sizes: kf_id -> keypoint count.
+    optional mps (map-point dict, fused into kf_id), optional fwd_mps (the new keyframe's own
+    map points, fused into every neighbour) with fwd_skip (per neighbour a [fwd n] uint8
+    array, 1 = already observed by that neighbour).  kf_sizes: kf_id -> keypoint count.
     Returns (tm_step array, masks uint8, concatenated map points dict, keep-alive list)."""
     st = (L.tm_step * max(1, len(steps)))()
     masks, keep = [], []
@@ -259,6 +269,7 @@ def pack_batch(steps, kf_sizes):
         st[k].n_nbrs = len(nb)
         st[k].q_free_off = -1
         st[k].nbr_free_off = -1
+        st[k].fwd_skip_off = -1
         if s.get("q_free") is not None:
             st[k].q_free_off = moff
             masks.append(np.asarray(s["q_free"], np.uint8))
@@ -280,6 +291,18 @@ def pack_batch(steps, kf_sizes):
                 else:
                     cols[c].append(np.asarray(mp[c]))
             mo += int(mp["n"])
+        fw = s.get("fwd_mps")
+        st[k].fwd_mp_begin = mo
+        st[k].fwd_mp_count = 0 if fw is None else int(fw["n"])
+        if fw is not None and fw["n"]:
+            for c in cols:  # (their per-batch skip bytes are unused: forward items skip by fwd_skip)
+                cols[c].append(np.zeros(fw["n"], np.uint8) if c == "skip" else np.asarray(fw[c]))
+            mo += int(fw["n"])
+            if s.get("fwd_skip") is not None:
+                st[k].fwd_skip_off = moff
+                for m in s["fwd_skip"]:
+                    masks.append(np.asarray(m, np.uint8))
+                    moff += len(masks[-1])
     mask_arr = np.ascontiguousarray(np.concatenate(masks) if masks else np.zeros(0, np.uint8))
     mps = dict(n=mo,
                pos=np.ascontiguousarray(np.concatenate(cols["pos"]) if mo else np.zeros((0, 3)), np.float32),
@@ -293,16 +316,29 @@ def pack_batch(steps, kf_sizes):
 
 class BatchResult:
     """Results of a batch: per pair (in step then neighbour order) an int32 (k, 3) array of
-    (q_idx, t_idx, dist); per step an int32 (k, 3) array of (mp_idx, kp_idx, dist)."""
+    (q_idx, t_idx, dist); per step an int32 (k, 3) array of (mp_idx, kp_idx, dist); per pair
+    the forward-fusion candidates (the step's new keyframe's map points, mp_idx relative to
+    fwd_mp_begin, in the neighbour's keypoints)."""
 
-    def __init__(self, matches, pair_offsets, fuse, fuse_offsets, ncmp_search, ncmp_fuse):
+    def __init__(self, matches, pair_offsets, fuse, fuse_offsets, ncmp_search, ncmp_fuse,
+                 fwd=None, fwd_offsets=None, ncmp_fwd=0):
         self.matches = matches
         self.pair_offsets = pair_offsets
         self.fuse = fuse
         self.fuse_offsets = fuse_offsets
-        self._pairs = self._fuses = None
+        self.fwd = np.zeros((0, 3), np.int32) if fwd is None else fwd
+        self.fwd_offsets = np.zeros(len(pair_offsets), np.int32) if fwd_offsets is None else fwd_offsets
+        self._pairs = self._fuses = self._fwds = None
         self.n_comparisons_search = ncmp_search
         self.n_comparisons_fuse = ncmp_fuse
+        self.n_comparisons_fwd = ncmp_fwd
+
+    @property
+    def fwds(self):
+        """Per pair, its forward-fusion rows of `fwd` (views, split on first use)."""
+        if self._fwds is None:
+            self._fwds = _split(self.fwd, self.fwd_offsets)
+        return self._fwds
 
     @property
     def pairs(self):
@@ -319,21 +355,41 @@ class BatchResult:
         return self._fuses
 
 
-def _result_struct(match_cap, n_pairs, fuse_cap, n_steps):
+def _result_struct(match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0):
     m = np.zeros((max(1, match_cap), 3), np.int32)
     po = np.zeros(n_pairs + 1, np.int32)
     f = np.zeros((max(1, fuse_cap), 3), np.int32)
     fo = np.zeros(n_steps + 1, np.int32)
+    w = np.zeros((max(1, fwd_cap), 3), np.int32)
+    wo = np.zeros(n_pairs + 1, np.int32)
     r = L.tm_batch_result()
     r.matches, r.match_cap, r.pair_offsets = m.ctypes.data, match_cap, po.ctypes.data
     r.fuse, r.fuse_cap, r.fuse_offsets = f.ctypes.data, fuse_cap, fo.ctypes.data
-    return r, (m, po, f, fo)
+    r.fwd, r.fwd_cap, r.fwd_offsets = w.ctypes.data, fwd_cap, wo.ctypes.data
+    return r, (m, po, f, fo, w, wo)
 
 
 def _collect(r, bufs):
-    m, po, f, fo = bufs
+    m, po, f, fo, w, wo = bufs
     return BatchResult(m[:r.n_matches].copy(), po.copy(), f[:r.n_fuse].copy(), fo.copy(),
-                       int(r.n_comparisons_search), int(r.n_comparisons_fuse))
+                       int(r.n_comparisons_search), int(r.n_comparisons_fuse),
+                       w[:r.n_fwd].copy(), wo.copy(), int(r.n_comparisons_fwd))
+
+
+def _fwd_cap(steps):
+    """Forward-fusion output capacity: every neighbour of a step times its forward map points."""
+    if isinstance(steps, StepTable):
+        if steps.fwd_mp_count is None:
+            return 0
+        return int((np.asarray(steps.fwd_mp_count, np.int64) * np.asarray(steps.n_nbrs, np.int64)).sum())
+    tot = 0
+    for s in steps:
+        c = s.get("fwd_mp_count")
+        if c is None:
+            fw = s.get("fwd_mps")
+            c = 0 if fw is None else int(fw["n"])
+        tot += int(c) * len(s["nbrs"])
+    return tot
 
 
 def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
@@ -358,7 +414,7 @@ class _ResultBuffers:
     available, so that the results come back by DMA) and grown as needed."""
 
     def __init__(self):
-        self.m = self.po = self.f = self.fo = None
+        self.m = self.po = self.f = self.fo = self.w = self.wo = None
 
     @staticmethod
     def _grow(a, n, width):
@@ -372,15 +428,18 @@ class _ResultBuffers:
         except Exception:  # no torch or no CUDA runtime: pageable memory
             return np.empty((n, width) if width else (n,), np.int32)
 
-    def struct(self, match_cap, n_pairs, fuse_cap, n_steps):
+    def struct(self, match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0):
         self.m = self._grow(self.m, max(1, match_cap), 3)
         self.po = self._grow(self.po, n_pairs + 1, 0)
         self.f = self._grow(self.f, max(1, fuse_cap), 3)
         self.fo = self._grow(self.fo, n_steps + 1, 0)
+        self.w = self._grow(self.w, max(1, fwd_cap), 3)
+        self.wo = self._grow(self.wo, n_pairs + 1, 0)
         r = L.tm_batch_result()
         r.matches, r.match_cap, r.pair_offsets = self.m.ctypes.data, match_cap, self.po.ctypes.data
         r.fuse, r.fuse_cap, r.fuse_offsets = self.f.ctypes.data, fuse_cap, self.fo.ctypes.data
-        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1])
+        r.fwd, r.fwd_cap, r.fwd_offsets = self.w.ctypes.data, fwd_cap, self.wo.ctypes.data
+        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1], self.w, self.wo[:n_pairs + 1])
 
 
 class Context:
@@ -501,6 +560,9 @@ class Context:
             arr["nbr_free_off"][:n] = np.fromiter((s.get("nbr_free_off", -1) for s in steps), np.int64, n)
             arr["mp_begin"][:n] = np.fromiter((s.get("mp_begin", 0) for s in steps), np.int64, n)
             arr["mp_count"][:n] = np.fromiter((s.get("mp_count", 0) for s in steps), np.int64, n)
+            arr["fwd_mp_begin"][:n] = np.fromiter((s.get("fwd_mp_begin", 0) for s in steps), np.int64, n)
+            arr["fwd_mp_count"][:n] = np.fromiter((s.get("fwd_mp_count", 0) for s in steps), np.int64, n)
+            arr["fwd_skip_off"][:n] = np.fromiter((s.get("fwd_skip_off", -1) for s in steps), np.int64, n)
             st = arr.ctypes.data
             keep.append(arr)
         inp = L.tm_batch_inputs()
@@ -532,7 +594,7 @@ class Context:
         if self._res is None:
             self._res = _ResultBuffers()
         n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
-        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps))
+        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps))
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
             check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
@@ -567,6 +629,7 @@ class Plan:
             self.caps = (self.caps[0], max(self.caps[1], int(mps["n"])))
         self.n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
         self.n_steps = len(steps)
+        self.fwd_cap = _fwd_cap(steps)
         h = ctypes.c_void_p()
         sps, fps = sp.struct(), fp.struct()
         check(tm_plan_create(ctx.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
@@ -579,7 +642,7 @@ class Plan:
         check(fn(self.handle, _stream(stream)))
 
     def results(self, stream=None):
-        r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps)
+        r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps, self.fwd_cap)
         check(tm_plan_results(self.handle, ctypes.byref(r), _stream(stream)))  # noqa: F821
         return _collect(r, bufs)
 

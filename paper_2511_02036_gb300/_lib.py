@@ -70,7 +70,8 @@ class tm_store_stats(ctypes.Structure):
 class tm_step(ctypes.Structure):
     _fields_ = [("kf_id", c_u64), ("nbr_ids", c_p), ("n_nbrs", c_i32),
                 ("q_free_off", c_i64), ("nbr_free_off", c_i64), ("mp_begin", c_i32),
-                ("mp_count", c_i32)]
+                ("mp_count", c_i32), ("fwd_mp_begin", c_i32), ("fwd_mp_count", c_i32),
+                ("fwd_skip_off", c_i64)]
 
 
 class tm_batch_inputs(ctypes.Structure):
@@ -82,7 +83,8 @@ class tm_batch_result(ctypes.Structure):
     _fields_ = [("matches", c_p), ("match_cap", c_sz), ("n_matches", c_sz),
                 ("pair_offsets", c_p), ("fuse", c_p), ("fuse_cap", c_sz), ("n_fuse", c_sz),
                 ("fuse_offsets", c_p), ("n_comparisons_search", c_u64),
-                ("n_comparisons_fuse", c_u64)]
+                ("n_comparisons_fuse", c_u64), ("fwd", c_p), ("fwd_cap", c_sz), ("n_fwd", c_sz),
+                ("fwd_offsets", c_p), ("n_comparisons_fwd", c_u64)]
 
 
 class tm_server_config(ctypes.Structure):

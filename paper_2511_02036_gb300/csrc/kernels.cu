@@ -1391,7 +1391,8 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     }
     fuse_setup(Tg.hdr, A.fp.chi2, K);
     const uint32_t m = w.a + (uint32_t)tid;
-    const bool have = tid < (int)w.b && !(A.mp_skip && A.mp_skip[m]);
+    const bool have = tid < (int)w.b &&
+                      !(w.skip != kNone ? A.masks[w.skip + (uint32_t)tid] != 0 : (A.mp_skip && A.mp_skip[m]));
     // the map point's loads overlap the staging
     const uint32_t mc = tid < (int)w.b ? m : w.a;  // (a valid index for the speculative loads)
     const MapPoint mp = load_mp(A.mp_pos + 3 * (size_t)mc, A.mp_normal + 3 * (size_t)mc,
@@ -1439,10 +1440,10 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
     const int tid = threadIdx.x, bs = blockDim.x;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nw = bs >> 5;
     const uint32_t gw = blockIdx.x * nw + wid, gws = gridDim.x * nw;
-    __shared__ unsigned long long csum[2][32];
+    __shared__ unsigned long long csum[3][32];
     __shared__ uint32_t sflags;
     uint32_t base = 0;
-    unsigned long long cs = 0, cf = 0;  // comparisons of search and fusion items (CTA 0)
+    unsigned long long cs = 0, cf = 0, cw = 0;  // comparisons: search, fusion, forward fusion (CTA 0)
     uint32_t flags = 0;
     for (uint32_t s0 = 0; s0 < A.n_items; s0 += kCopySeg) {
         const uint32_t ns = min((uint32_t)kCopySeg, A.n_items - s0);
@@ -1453,7 +1454,9 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
             for (uint32_t k = cb; k < ce; ++k) {
                 const uint32_t v = A.item_cmp[s0 + k];
                 flags |= v & kItemTimeout;
-                if (s0 + k < A.n_search) cs += v & ~kItemTimeout; else cf += v & ~kItemTimeout;
+                if (s0 + k < A.n_search) cs += v & ~kItemTimeout;
+                else if (s0 + k < A.n_search + A.n_bwd) cf += v & ~kItemTimeout;
+                else cw += v & ~kItemTimeout;
             }
         uint32_t total;
         uint32_t run = block_scan_add(sum, wtot, total) + base;
@@ -1476,21 +1479,24 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
         for (int o = 16; o > 0; o >>= 1) {
             cs += __shfl_down_sync(kFull, cs, o);
             cf += __shfl_down_sync(kFull, cf, o);
+            cw += __shfl_down_sync(kFull, cw, o);
         }
         flags = __reduce_or_sync(kFull, flags);
         if (tid == 0) sflags = 0u;
         if ((tid & 31) == 0) {
             csum[0][wid] = cs;
             csum[1][wid] = cf;
+            csum[2][wid] = cw;
         }
         __syncthreads();
         if ((tid & 31) == 0 && flags) atomicOr(&sflags, flags);
         __syncthreads();
         if (tid == 0) {
-            unsigned long long a = 0, b = 0;
-            for (uint32_t q = 0; q < nw; ++q) { a += csum[0][q]; b += csum[1][q]; }
+            unsigned long long a = 0, b = 0, f = 0;
+            for (uint32_t q = 0; q < nw; ++q) { a += csum[0][q]; b += csum[1][q]; f += csum[2][q]; }
             A.ncmp[0] = a;
             A.ncmp[1] = b;
+            A.ncmp[2] = f;
             A.counters[2] = sflags ? kStatusTimeout : 0u;
             A.offsets[A.n_items] = base;
         }

@@ -146,6 +146,8 @@ struct WorkItem {
     uint32_t step;           // fuse: step index
     uint32_t cost;           // scheduling estimate
     uint32_t idx;            // search: logical index of the item (its counts / comparisons)
+    uint32_t skip;           // fuse: byte offset in masks of the item's per-map-point skip
+                             //   bytes (forward fusion), or kNone: the batch's mp_skip
     const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
                              // keyframe entering with the batch)
 };
@@ -235,6 +237,8 @@ struct BatchArgs {
     const WorkItem *items;        // logical order (search items first, then fuse items)
     uint32_t n_items;
     uint32_t n_search;            // search items come first
+    uint32_t n_bwd;               // then this many fusion items into the new keyframes; the
+                                  // rest fuse the new keyframes' map points into neighbours
     const WorkItem *sitems;       // the search items in launch order (largest pairs first)
     uint32_t fsn;                 // fusion stage capacity (largest target, rounded to 16)
     uint32_t *counters;           // [2] status of the last run (kStatusTimeout)
@@ -247,7 +251,7 @@ struct BatchArgs {
     uint32_t *counts;             // [n_items]
     uint32_t *item_cmp;           // [n_items] comparisons of the item | kItemTimeout
     uint32_t *offsets;            // [n_items + 1] exclusive scan of counts
-    unsigned long long *ncmp;     // [2] search, fuse comparisons (written by copy)
+    unsigned long long *ncmp;     // [3] search, fuse, forward-fuse comparisons (written by copy)
     Out3 *dense;                  // compacted output
     SearchConst sp;
     FuseConst fp;

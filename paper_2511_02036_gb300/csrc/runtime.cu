@@ -730,12 +730,51 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.c = (uint32_t)S.mp_begin;
             w.nt = (uint32_t)c->slots[qs].n;
             w.step = (uint32_t)k;
+            w.skip = kNone;
             w.cost = 2 * w.b;
             pad += w.b;
             items.push_back(w);
         }
     }
     B.step_fuse_item[n_steps] = (int)items.size();
+    B.n_bwd_items = (uint32_t)items.size() - B.n_search_items;
+    // forward fusion: the new keyframe's map points into each neighbour (Sec. IV-D)
+    B.pair_fwd_item.assign((size_t)B.n_pairs + 1, 0);
+    B.any_fwd = false;
+    {
+        int p = 0;
+        for (int k = 0; k < n_steps; ++k) {
+            const tm_step &S = steps[k];
+            const int cnt = S.fwd_mp_count;
+            if (cnt < 0 || (cnt > 0 && (S.fwd_mp_begin < 0 || (int64_t)S.fwd_mp_begin + cnt > mps.n)))
+                return fail(TM_ERR_INVALID_ARG, "step %d: forward map point range outside the batch", k);
+            if (cnt > 0 && S.fwd_skip_off >= 0 &&
+                (size_t)S.fwd_skip_off + (size_t)S.n_nbrs * (size_t)cnt > mask_bytes)
+                return fail(TM_ERR_INVALID_ARG, "step %d: forward skip bytes outside masks", k);
+            for (int j = 0; j < S.n_nbrs; ++j, ++p) {
+                B.pair_fwd_item[p] = (int)items.size();
+                if (cnt <= 0) continue;
+                B.any_fwd = true;
+                const int ts = c->ids[S.nbr_ids[j]];
+                for (int b = 0; b < cnt; b += kFuseChunk) {
+                    WorkItem w{};
+                    w.q = c->slots[ts].ptr;
+                    w.kind = kItemFuse;
+                    w.out_off = pad;
+                    w.a = (uint32_t)(S.fwd_mp_begin + b);
+                    w.b = (uint32_t)std::min(kFuseChunk, cnt - b);
+                    w.c = (uint32_t)S.fwd_mp_begin;
+                    w.nt = (uint32_t)c->slots[ts].n;
+                    w.step = (uint32_t)k;
+                    w.skip = S.fwd_skip_off >= 0 ? (uint32_t)((size_t)S.fwd_skip_off + (size_t)j * cnt + b) : kNone;
+                    w.cost = 2 * w.b;
+                    pad += w.b;
+                    items.push_back(w);
+                }
+            }
+        }
+        B.pair_fwd_item[B.n_pairs] = (int)items.size();
+    }
     for (int sl : new_slots) slots_used.push_back(sl);
     B.n_items = (uint32_t)items.size();
     B.n_steps = n_steps;
@@ -747,10 +786,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t x, uint32_t y) { return items[x].cost > items[y].cost; });
-    // fusion stage: the largest target of the batch
+    // fusion stage: the largest target of the batch (new keyframes, and neighbours for
+    // forward fusion)
     int fuse_n = 0;
-    for (uint32_t i = B.n_search_items; i < items.size(); ++i)
-        fuse_n = std::max(fuse_n, c->slots[c->ids[steps[items[i].step].kf_id]].n);
+    for (uint32_t i = B.n_search_items; i < items.size(); ++i) fuse_n = std::max(fuse_n, (int)items[i].nt);
     B.fsn = (uint32_t)std::max(16, (fuse_n + 15) & ~15);
     // device buffers
     const size_t ni = std::max<size_t>(1, items.size());
@@ -760,7 +799,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nsi * sizeof(WorkItem))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
         (e = B.offsets.reserve((ni + 1) * 4)) ||
-        (e = B.ncmp.reserve(16)) || (e = B.counters.reserve(16)) ||
+        (e = B.ncmp.reserve(24)) || (e = B.counters.reserve(16)) ||
         (e = B.padded.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
         (e = B.dense.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
         (e = B.masks.reserve(std::max<size_t>(16, mask_bytes))) ||
@@ -814,6 +853,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.items = static_cast<const WorkItem *>(B.items.p);
     A.n_items = B.n_items;
     A.n_search = B.n_search_items;
+    A.n_bwd = B.n_bwd_items;
     A.sitems = reinterpret_cast<const WorkItem *>(static_cast<unsigned char *>(B.items.p) + align128(ni * sizeof(WorkItem)));
     A.counters = static_cast<uint32_t *>(B.counters.p);
     A.masks = static_cast<const uint8_t *>(B.masks.p);
@@ -939,7 +979,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
     PairScratch scr = pair_scratch_at(B.scratch.p, c->cap);
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
     uint32_t *res = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(B.scratch.p) + scr_bytes);
-    if ((e = cudaMemsetAsync(scr.running, 0, 8, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 16, s)))
+    if ((e = cudaMemsetAsync(scr.running, 0, 8, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 24, s)))
         return cuda_fail(e, "reset");
     B.lanes = lanes;
     const std::vector<WorkItem> &items = B.h_items;
@@ -969,6 +1009,20 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
                                    c->camc, res, B.args.dense, scr.running, offs + f0, ncmp + 1, s)))
             return cuda_fail(e, "plain fuse");
     }
+    for (int p = 0; p < B.n_pairs && B.any_fwd; ++p) {  // forward fusion, pair by pair
+        const int f0 = B.pair_fwd_item[p], f1 = B.pair_fwd_item[p + 1];
+        if (f0 == f1) continue;
+        const WorkItem &w = items[f0];
+        const uint32_t begin = w.a;
+        uint32_t n = 0;
+        for (int f = f0; f < f1; ++f) n += items[f].b;
+        if ((e = launch_fuse_plain(w.q, c->cap, B.args.mp_pos + 3 * (size_t)begin,
+                                   B.args.mp_normal + 3 * (size_t)begin, B.args.mp_desc + 2 * (size_t)begin,
+                                   B.args.mp_min + begin, B.args.mp_max + begin,
+                                   w.skip != kNone ? B.args.masks + w.skip : nullptr, (int)n, B.args.fp,
+                                   c->camc, res, B.args.dense, scr.running, offs + f0, ncmp + 2, s)))
+            return cuda_fail(e, "plain forward fuse");
+    }
     if ((e = cudaMemcpyAsync(offs + B.n_items, scr.running, 4, cudaMemcpyDeviceToDevice, s)))
         return cuda_fail(e, "plain total");
     return TM_OK;
@@ -979,27 +1033,31 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
     (void)c;
     cudaError_t e;
     const size_t nio = (size_t)B.n_items + 1;
-    if ((e = B.h_out.reserve((nio + 2) * 4 + 32))) return cuda_fail(e, "pinned results");
+    if ((e = B.h_out.reserve((nio + 2) * 4 + 48))) return cuda_fail(e, "pinned results");
     uint32_t *ho = static_cast<uint32_t *>(B.h_out.p);
     unsigned long long *hc = reinterpret_cast<unsigned long long *>(ho + ((nio + 1) & ~size_t(1)));
-    uint32_t *hs = reinterpret_cast<uint32_t *>(hc + 2);
+    uint32_t *hs = reinterpret_cast<uint32_t *>(hc + 3);
     if ((e = cudaMemcpyAsync(ho, B.offsets.p, nio * 4, cudaMemcpyDeviceToHost, s)) ||
-        (e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hc, B.ncmp.p, 24, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
     if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
         return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory or a tensor-core product did not complete in time");
     const uint32_t search_total = ho[B.n_search_items];
+    const uint32_t bwd_end = ho[B.n_search_items + B.n_bwd_items];
     const uint32_t total = ho[B.n_items];
-    const size_t nf = total - search_total;
+    const size_t nf = bwd_end - search_total, nw = total - bwd_end;
     r->n_matches = search_total;
     r->n_fuse = nf;
+    r->n_fwd = nw;
     r->n_comparisons_search = hc[0];
     r->n_comparisons_fuse = hc[1];
-    if (search_total > r->match_cap || nf > r->fuse_cap)
-        return fail(TM_ERR_CAPACITY, "result buffers too small: %u matches (cap %zu), %zu fusion candidates (cap %zu)",
-                    search_total, r->match_cap, nf, r->fuse_cap);
+    r->n_comparisons_fwd = hc[2];
+    if (search_total > r->match_cap || nf > r->fuse_cap || (nw && (!r->fwd || nw > r->fwd_cap)))
+        return fail(TM_ERR_CAPACITY, "result buffers too small: %u matches (cap %zu), %zu fusion candidates (cap %zu), "
+                    "%zu forward-fusion candidates (cap %zu)", search_total, r->match_cap, nf, r->fuse_cap, nw,
+                    r->fwd ? r->fwd_cap : (size_t)0);
     if (r->pair_offsets)
         for (int p = 0; p <= B.n_pairs; ++p) r->pair_offsets[p] = (int32_t)ho[p];
     if (r->fuse_offsets)
@@ -1010,11 +1068,19 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
         for (int k = B.n_steps - 1; k >= 0; --k)
             if (B.step_fuse_item[k] == B.step_fuse_item[k + 1]) r->fuse_offsets[k] = r->fuse_offsets[k + 1];
     }
+    if (r->fwd_offsets) {
+        for (int p = 0; p <= B.n_pairs; ++p) r->fwd_offsets[p] = (int32_t)(ho[B.pair_fwd_item[p]] - bwd_end);
+        // pairs without forward items start where the next pair starts
+        for (int p = B.n_pairs - 1; p >= 0; --p)
+            if (B.pair_fwd_item[p] == B.pair_fwd_item[p + 1]) r->fwd_offsets[p] = r->fwd_offsets[p + 1];
+    }
     const Out3 *d = static_cast<const Out3 *>(B.dense.p);
     if (search_total && (e = cudaMemcpyAsync(r->matches, d, search_total * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "matches download");
     if (nf && (e = cudaMemcpyAsync(r->fuse, d + search_total, nf * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "fusion download");
+    if (nw && (e = cudaMemcpyAsync(r->fwd, d + bwd_end, nw * sizeof(Out3), cudaMemcpyDefault, s)))
+        return cuda_fail(e, "forward fusion download");
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(e, "results");
     return TM_OK;
 }

@@ -58,6 +58,9 @@ struct BatchBuf {
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
+    std::vector<int> pair_fwd_item;  // [pairs + 1] first forward-fusion item of each pair
+    uint32_t n_bwd_items = 0;        // fusion items into the new keyframes
+    bool any_fwd = false;            // some step asks for forward fusion
     uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
     uint32_t res_total = 0, t_total = 0, fsn = 16;
     int n_steps = 0, n_pairs = 0, smem_n = 32;

@@ -180,3 +180,22 @@ def test_step_table_records_match_step_dicts():
     assert rec["nbr_ids"][2] == nb.ctypes.data + 8 * 3
     mc, fc = tm._result_caps(t, {7: 100, 8: 50, 9: 10})
     assert mc == 100 * 3 + 10 * 1 and fc == 7
+
+
+def test_pack_batch_forward_fusion_ranges():
+    """Forward map points follow the step's own map points in the batch arrays; their skip
+    bytes follow the step's masks, neighbour-major."""
+    import paper_2511_02036_gb300 as tm
+    mp = lambda n, v: dict(n=n, pos=np.full((n, 3), v, np.float32), normal=np.zeros((n, 3), np.float32),  # noqa: E731
+                           desc=np.zeros((n, 32), np.uint8), min_dist=np.zeros(n, np.float32),
+                           max_dist=np.ones(n, np.float32), skip=np.zeros(n, np.uint8))
+    steps = [dict(kf_id=1, nbrs=[2, 3], q_free=np.ones(4, np.uint8), nbr_free=[np.ones(5, np.uint8), np.ones(6, np.uint8)],
+                  mps=mp(7, 1.0), fwd_mps=mp(3, 2.0), fwd_skip=[np.array([1, 0, 0], np.uint8), np.array([0, 0, 1], np.uint8)]),
+             dict(kf_id=4, nbrs=[2], mps=mp(2, 3.0))]
+    st, masks, mps, _keep = tm.pack_batch(steps, {1: 4, 2: 5, 3: 6, 4: 8})
+    assert (st[0].mp_begin, st[0].mp_count, st[0].fwd_mp_begin, st[0].fwd_mp_count) == (0, 7, 7, 3)
+    assert (st[1].mp_begin, st[1].mp_count, st[1].fwd_mp_count, st[1].fwd_skip_off) == (10, 2, 0, -1)
+    assert st[0].q_free_off == 0 and st[0].nbr_free_off == 4 and st[0].fwd_skip_off == 15
+    assert list(masks[15:21]) == [1, 0, 0, 0, 0, 1] and len(masks) == 21
+    assert mps["n"] == 12 and mps["pos"][7, 0] == 2.0 and mps["pos"][10, 0] == 3.0
+    assert tm._fwd_cap(steps) == 3 * 2

@@ -326,3 +326,73 @@ def test_pinned_host_inputs(tm, small_batch):
             assert_same(ctx.batch_run(steps, masks=pin(masks), mps=h_mps, new=(new_ids, new)), exp)
             for i in new_ids:
                 ctx.remove_keyframe(i)
+
+
+def forward_steps(w, skip=True):
+    return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                 mps=s.get("mps"), fwd_mps=s["fwd_mps"], fwd_skip=s["fwd_skip"] if skip else None)
+            for s in w["steps"]]
+
+
+def oracle_forward(w, skip=True):
+    out, ncmp = [], 0
+    for st in w["steps"]:
+        s2 = dict(st)
+        if not skip:
+            s2["fwd_skip"] = None
+        r, c = O.fuse_forward_step(w["cam"], w["frames"], s2)
+        out.extend(r)
+        ncmp += c
+    return out, ncmp
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_forward_fusion_batch(tm, mode):
+    """Forward fusion (the new keyframes' map points into every neighbour, with per-neighbour
+    skip bytes) beside the search and the backward fusion: every array equals the oracle's."""
+    w = W.make_cfg2(seed=2200, n_steps=5, forward=True)
+    exp = oracle_results(w)
+    efw, ecw = oracle_forward(w)
+    assert sum(len(x) for x in efw) > 100
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        res = ctx.batch_run(forward_steps(w), sp=tm.SearchParams(mode=mode))
+        assert_same(res, exp)
+        assert len(res.fwds) == len(efw)
+        for g, e in zip(res.fwds, efw):
+            np.testing.assert_array_equal(g, e)
+        assert res.n_comparisons_fwd == ecw
+        # no skip bytes: every map point into every neighbour
+        efw2, ecw2 = oracle_forward(w, skip=False)
+        res2 = ctx.batch_run(forward_steps(w, skip=False), sp=tm.SearchParams(mode=mode))
+        for g, e in zip(res2.fwds, efw2):
+            np.testing.assert_array_equal(g, e)
+        assert res2.n_comparisons_fwd == ecw2 and ecw2 > ecw
+
+
+def test_forward_fusion_plan_and_mixed_steps(tm):
+    """A plan with forward fusion, and a batch where only some steps ask for it (their pairs
+    get empty forward lists)."""
+    w = W.make_cfg2(seed=2201, n_steps=4, forward=True)
+    exp = oracle_results(w)
+    efw, ecw = oracle_forward(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        with ctx.plan(forward_steps(w)) as plan:
+            for _ in range(2):
+                plan.run()
+                r = plan.results()
+                assert_same(r, exp)
+                for g, e in zip(r.fwds, efw):
+                    np.testing.assert_array_equal(g, e)
+                assert r.n_comparisons_fwd == ecw
+        steps = forward_steps(w)
+        for k in (1, 3):
+            steps[k] = {key: v for key, v in steps[k].items() if key not in ("fwd_mps", "fwd_skip")}
+        r = ctx.batch_run(steps)
+        p = 0
+        for k, st in enumerate(w["steps"]):
+            for j in range(len(st["nbrs"])):
+                e = efw[p] if k not in (1, 3) else np.zeros((0, 3), np.int32)
+                np.testing.assert_array_equal(r.fwds[p], e)
+                p += 1

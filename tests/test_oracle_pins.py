@@ -388,3 +388,29 @@ def test_fuse_planted():
     assert np.all(np.diff(m[:, 0]) > 0)
     dd = np.bitwise_count(np.bitwise_xor(mps["desc"][m[:, 0]], Q["desc"][m[:, 1]])).sum(1)
     np.testing.assert_array_equal(dd, m[:, 2])
+
+
+def test_forward_fusion_skip_and_independence():
+    """Forward fusion (the new keyframe's map points into each neighbour): every map point is
+    fused independently of the others, so with skip flags the result is exactly the rows of
+    the unflagged map points in the result without flags; and a neighbour that observes every
+    map point gets nothing and costs no comparisons."""
+    w = W.make_cfg1(forward=True)
+    st = w["steps"][0]
+    fw = st["fwd_mps"]
+    assert fw["n"] > 50 and len(st["fwd_skip"]) == len(st["nbrs"])
+    res, ncmp = O.fuse_forward_step(w["cam"], w["frames"], st)
+    assert len(res) == len(st["nbrs"]) and ncmp > 0
+    some = False
+    for k, f in enumerate(st["nbrs"]):
+        free = dict(fw)
+        free["skip"] = None
+        full, _ = O.fuse(w["cam"], w["frames"][f], free)
+        keep = st["fwd_skip"][k][full[:, 0]] == 0 if len(full) else np.zeros(0, bool)
+        np.testing.assert_array_equal(res[k], full[keep])
+        some |= bool(len(res[k]))
+    assert some
+    allskip = dict(st)
+    allskip["fwd_skip"] = [np.ones(fw["n"], np.uint8) for _ in st["nbrs"]]
+    r2, c2 = O.fuse_forward_step(w["cam"], w["frames"], allskip)
+    assert c2 == 0 and all(len(x) == 0 for x in r2)
