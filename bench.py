@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-node (tensor-core) workload")
+    ap.add_argument("--no-forward", action="store_true", help="skip the step with forward-direction fusion")
     return ap.parse_args()
 
 
@@ -447,6 +448,10 @@ def run_mine(args, rank, world, local_rank):
     if not args.no_dense and rank == 0:
         out["dense_blocks"] = run_dense(tm, stream, flush, local_rank, max(3, args.steps // 2))
 
+    # ---------------------------------------------------------------- forward fusion
+    if not args.no_forward and rank == 0:
+        out["forward_fusion"] = run_forward(tm, stream, flush, local_rank, max(3, args.steps // 2), args.seed)
+
     # ---------------------------------------------------------------- serving
     if args.serve_kf > 0 and rank == 0:
         out["serving"] = run_serving(tm, args.serve_kf, local_rank)
@@ -532,6 +537,44 @@ def run_dense(tm, stream, flush, device, reps):
                            "peak": fp8_peak, "unit": "TFLOP/s", "frac": flops / (dms / 1e3) / 1e12 / fp8_peak,
                            "peak_kind": pk_kind + " bf16 burst x 2 (fp8/bf16 nominal ratio)",
                            "algorithmic_flops": flops, "traffic": None}
+    return out
+
+
+def run_forward(tm, stream, flush, device, reps, seed):
+    """The cfg2 batch with forward-direction fusion as well (Sec. IV-D: the new keyframes' own
+    map points fused into every neighbour, skipping those a neighbour already observes), as one
+    plan: step time and the forward work, against the same batch without it."""
+    import torch
+    from gen import workloads as W
+    w = W.make_cfg2(seed=seed, forward=True)
+    new_ids = [s["q"] for s in w["steps"]]
+    old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+    out = {"workload": "cfg2 + forward fusion: the same 64 steps; per step its new keyframe's map points "
+                       "(mapped and just-triangulated points it observes) into each of its neighbours"}
+    with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+        ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
+        for name, fwd in (("with_forward", True), ("without_forward", False)):
+            steps = [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                          mps=s.get("mps"), **({"fwd_mps": s["fwd_mps"], "fwd_skip": s["fwd_skip"]} if fwd else {}))
+                     for s in w["steps"]]
+            with ctx.plan(steps, new=(new_ids, [w["frames"][i] for i in new_ids])) as plan:
+                for _ in range(3):
+                    plan.run(stream)
+                torch.cuda.synchronize()
+                res = plan.results(stream)
+                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                for k in range(reps):
+                    flush.zero_()
+                    e0[k].record(stream)
+                    plan.run(stream)
+                    e1[k].record(stream)
+                torch.cuda.synchronize()
+                ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
+                out[name] = {"ms_per_step": ms, "keyframes_per_s": len(new_ids) / (ms / 1e3),
+                             "kernels_per_run": plan.info()["kernels_per_run"],
+                             "forward_candidates": int(len(res.fwd)), "forward_comparisons": int(res.n_comparisons_fwd),
+                             "forward_map_points": int(sum(s["fwd_mps"]["n"] * len(s["nbrs"]) for s in w["steps"])) if fwd else 0}
     return out
 
 
