@@ -575,6 +575,7 @@ def run_forward(tm, stream, flush, device, reps, seed):
                              "kernels_per_run": plan.info()["kernels_per_run"],
                              "forward_candidates": int(len(res.fwd)), "forward_comparisons": int(res.n_comparisons_fwd),
                              "forward_map_points": int(sum(s["fwd_mps"]["n"] * len(s["nbrs"]) for s in w["steps"])) if fwd else 0}
+            ctx.remove_keyframes(new_ids)  # the plan's new keyframes stay stored after it
     return out
 
 
