@@ -115,6 +115,12 @@ typedef struct {
                                else >= 16.  Worth it for dense nodes (~64 and more); each
                                call with it on runs one more kernel.  TM_MODE_PER_PAIR
                                ignores it.                                                   */
+    /* ORB-family variants (0 = off, the defaults): */
+    float epipole_px;       /* drop a candidate whose squared distance to the epipole (the
+                               new keyframe's centre projected into the neighbour) is below
+                               epipole_px^2 * 1.2^level_T (ORB-SLAM uses 10; monocular)      */
+    int32_t rot_mode;       /* rotation bins: 0 = 30 bins of 12 degrees, floor(rot / 12);
+                               1 = ORB-family round(rot * (1/30)), bins 0..12 used          */
 } tm_search_params;
 
 typedef struct {

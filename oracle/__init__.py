@@ -54,7 +54,8 @@ class _SearchParams(ctypes.Structure):
     _fields_ = [("hamming_max", ctypes.c_int32), ("ratio_num", ctypes.c_int32),
                 ("ratio_den", ctypes.c_int32), ("epi_chi2", ctypes.c_float),
                 ("epipolar", ctypes.c_int32), ("resolve", ctypes.c_int32),
-                ("rot_filter", ctypes.c_int32)]
+                ("rot_filter", ctypes.c_int32), ("epipole_px", ctypes.c_float),
+                ("rot_mode", ctypes.c_int32)]
 
 
 class _FuseParams(ctypes.Structure):
@@ -71,6 +72,8 @@ class SearchParams:
     epipolar: bool = True
     resolve: bool = True
     rot_filter: bool = True
+    epipole_px: float = 0.0   # ORB-family epipole rejection radius at level 0 (0 = off)
+    rot_mode: int = 0         # 0: 30 bins of 12 degrees; 1: ORB-family round(rot / 30)
 
 
 @dataclass
@@ -103,6 +106,10 @@ def lib(path=None):
                                       ctypes.POINTER(_SearchParams), P, P, P,
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.orc_search_pair.restype = ctypes.c_int64
+        L.orc_epipole.argtypes = [ctypes.POINTER(_Camera), P, P, P]
+        L.orc_epipole.restype = None
+        L.orc_rot_bin_mode.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int]
+        L.orc_rot_bin_mode.restype = ctypes.c_int
         L.orc_fuse.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Keyframe),
                                ctypes.c_int32, P, P, P, P, P, P,
                                ctypes.POINTER(_FuseParams), P, P, P, ctypes.c_int64,
@@ -146,6 +153,21 @@ def _mask(m):
     return None if m is None else np.ascontiguousarray(m, np.uint8)
 
 
+def epipole(cam, Tq, Tt):
+    """The epipole in T (float32 pair): Q's camera centre projected into T."""
+    c = _cam(cam)
+    q = np.ascontiguousarray(Tq, np.float64).reshape(12)
+    t = np.ascontiguousarray(Tt, np.float64).reshape(12)
+    e = np.zeros(2, np.float32)
+    lib().orc_epipole(ctypes.byref(c), q.ctypes.data, t.ctypes.data, e.ctypes.data)
+    return e
+
+
+def rot_bin(angle_q, angle_t, mode=0):
+    """Rotation-histogram bin of a match under rot_mode `mode`."""
+    return int(lib().orc_rot_bin_mode(float(angle_q), float(angle_t), int(mode)))
+
+
 def search_pair(cam, Q, T, free_q=None, free_t=None, params=None):
     """Matches of one (Q, T) pair as an int32 array (k, 3) of (q_idx, t_idx, dist), sorted
     by q_idx, and the number of descriptor comparisons."""
@@ -154,7 +176,7 @@ def search_pair(cam, Q, T, free_q=None, free_t=None, params=None):
     q, t = _kf(Q, keep), _kf(T, keep)
     fq, ft = _mask(free_q), _mask(free_t)
     sp = _SearchParams(p.hamming_max, p.ratio_num, p.ratio_den, p.epi_chi2, int(p.epipolar),
-                       int(p.resolve), int(p.rot_filter))
+                       int(p.resolve), int(p.rot_filter), float(p.epipole_px), int(p.rot_mode))
     cap = max(1, min(q.n, t.n) if p.resolve else q.n)
     out = np.zeros((3, cap), np.int32)
     ncmp = ctypes.c_int64(0)

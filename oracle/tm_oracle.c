@@ -102,14 +102,37 @@ static int orc_epipolar_ok(const float F[9], float xq, float yq, float xt, float
     return num * num < thr * den;
 }
 
-/* Rotation-histogram bin of an accepted match: 30 bins of 12 degrees over the orientation
- * difference angle_Q - angle_T, wrapped into [0, 360). */
-static int orc_rot_bin(float angle_q, float angle_t) {
+/* Rotation-histogram bin of an accepted match over the orientation difference
+ * angle_Q - angle_T wrapped into [0, 360): mode 0, 30 bins of 12 degrees; mode 1, the
+ * ORB-family binning, the nearest integer of rot * (1/30) (float32 factor; halves away from
+ * zero), 30 folded to 0, so that only bins 0..12 occur. */
+int orc_rot_bin_mode(float angle_q, float angle_t, int mode) {
     float rot = angle_q - angle_t;
     if (rot < 0.0f) rot += 360.0f;
-    int bin = (int)floorf(rot / 12.0f);
+    int bin = mode == 1 ? (int)roundf(rot * (1.0f / 30.0f)) : (int)floorf(rot / 12.0f);
     if (bin >= ORC_BINS) bin = 0;
     return bin;
+}
+
+/* The epipole in T, the image of Q's camera centre: C_Q = -R_Q^T t_Q, C = R_T C_Q + t_T,
+ * e = (fx * (C_x / C_z) + cx, fy * (C_y / C_z) + cy), all float64, sums left to right,
+ * rounded to float32 at the end. */
+void orc_epipole(const orc_camera *cam, const double Tq[12], const double Tt[12], float e[2]) {
+    double cq[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+        double s = Tq[0 * 4 + k] * Tq[0 * 4 + 3];
+        s = s + Tq[1 * 4 + k] * Tq[1 * 4 + 3];
+        s = s + Tq[2 * 4 + k] * Tq[2 * 4 + 3];
+        cq[k] = -s;
+    }
+    for (int r = 0; r < 3; ++r) {
+        double s = Tt[r * 4 + 0] * cq[0];
+        s = s + Tt[r * 4 + 1] * cq[1];
+        s = s + Tt[r * 4 + 2] * cq[2];
+        c[r] = s + Tt[r * 4 + 3];
+    }
+    e[0] = (float)(cam->fx * (c[0] / c[2]) + cam->cx);
+    e[1] = (float)(cam->fy * (c[1] / c[2]) + cam->cy);
 }
 
 int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_keyframe *T,
@@ -121,6 +144,13 @@ int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_
     for (int l = 0; l < ORC_LEVELS; ++l) thr[l] = p->epi_chi2 * sigma2[l];
     float F[9];
     orc_fundamental(cam, Q->Tcw, T->Tcw, F);
+    /* ORB-family epipole rejection: a candidate whose squared distance to the epipole is
+     * below epipole_px^2 * scale(level) (float32, (dx*dx) + (dy*dy)) is dropped after its
+     * distance is computed, like a failed epipolar gate. */
+    float ep[2] = {0.0f, 0.0f}, thr_e[ORC_LEVELS];
+    const int use_ep = p->epipole_px > 0.0f;
+    if (use_ep) orc_epipole(cam, Q->Tcw, T->Tcw, ep);
+    for (int l = 0; l < ORC_LEVELS; ++l) thr_e[l] = (p->epipole_px * p->epipole_px) * scale[l];
 
     const int nq = Q->n, nt = T->n;
     int *acc_t = (int *)malloc(sizeof(int) * (size_t)(nq > 0 ? nq : 1));
@@ -145,6 +175,10 @@ int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_
                 !orc_epipolar_ok(F, Q->xy[2 * i], Q->xy[2 * i + 1], T->xy[2 * j],
                                  T->xy[2 * j + 1], thr[T->level[j]]))
                 continue;
+            if (use_ep) {
+                const float dx = ep[0] - T->xy[2 * j], dy = ep[1] - T->xy[2 * j + 1];
+                if (dx * dx + dy * dy < thr_e[T->level[j]]) continue;
+            }
             if (d < best) {
                 second = best;
                 best = d;
@@ -186,7 +220,7 @@ int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_
         int hist[ORC_BINS];
         memset(hist, 0, sizeof hist);
         for (int i = 0; i < nq; ++i)
-            if (acc_t[i] >= 0) hist[orc_rot_bin(Q->angle[i], T->angle[acc_t[i]])]++;
+            if (acc_t[i] >= 0) hist[orc_rot_bin_mode(Q->angle[i], T->angle[acc_t[i]], p->rot_mode)]++;
         int top[3] = {-1, -1, -1};
         for (int r = 0; r < 3; ++r) {
             int bestb = -1;
@@ -204,7 +238,7 @@ int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_
         }
         for (int i = 0; i < nq; ++i) {
             if (acc_t[i] < 0) continue;
-            int b = orc_rot_bin(Q->angle[i], T->angle[acc_t[i]]);
+            int b = orc_rot_bin_mode(Q->angle[i], T->angle[acc_t[i]], p->rot_mode);
             if (b != top[0] && b != top[1] && b != top[2]) acc_t[i] = -1;
         }
     }

@@ -55,6 +55,12 @@ typedef struct {
     int32_t epipolar;       /* 1: apply the epipolar gate                            */
     int32_t resolve;        /* 1: keep one match per target keypoint                  */
     int32_t rot_filter;     /* 1: apply the rotation-histogram filter                 */
+    /* ORB-family variants (off by default) */
+    float epipole_px;       /* > 0: drop a candidate whose squared distance to the epipole
+                               (Q's centre projected into T) is below
+                               epipole_px^2 * scale(level of the candidate)              */
+    int32_t rot_mode;       /* 0: 30 bins of 12 degrees, floor(rot / 12);
+                               1: ORB-family bins round(rot * (1/30)), 30 -> 0            */
 } orc_search_params;
 
 typedef struct {
@@ -62,6 +68,12 @@ typedef struct {
     int32_t hamming_max;    /* (50) */
     float radius_scale;     /* window half-width = radius_scale*scale[level] (3.0) */
 } orc_fuse_params;
+
+/* The epipole in T: Q's camera centre C_Q = -R_Q^T t_Q projected into T (float64, rounded
+ * to float32); +-inf or NaN when C_Q lies in T's principal plane. */
+void orc_epipole(const orc_camera *cam, const double Tcw_q[12], const double Tcw_t[12], float e[2]);
+/* Rotation bin of a match (rot_mode as in orc_search_params). */
+int orc_rot_bin_mode(float angle_q, float angle_t, int mode);
 
 /* F (float32, row-major 3x3) with x_Q^T F x_T = 0 for corresponding pixels. */
 void orc_fundamental(const orc_camera *cam, const double Tcw_q[12], const double Tcw_t[12],

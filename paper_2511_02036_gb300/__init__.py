@@ -169,11 +169,14 @@ class SearchParams:
     mode: int = TM_MODE_FUSED
     lanes_per_query: int = 0
     dense_min: int = 0      # tensor-core blocks for nodes with >= dense_min neighbour keypoints
+    epipole_px: float = 0.0  # ORB-family epipole rejection radius at level 0 (0 = off; ORB-SLAM: 10)
+    rot_mode: int = 0       # 0: 30 bins of 12 degrees; 1: ORB-family round(rot / 30)
 
     def struct(self):
         return L.tm_search_params(self.hamming_max, self.ratio_num, self.ratio_den, self.epi_chi2,
                                   int(self.epipolar), int(self.resolve), int(self.rot_filter),
-                                  int(self.mode), int(self.lanes_per_query), int(self.dense_min))
+                                  int(self.mode), int(self.lanes_per_query), int(self.dense_min),
+                                  float(self.epipole_px), int(self.rot_mode))
 
 
 @dataclass

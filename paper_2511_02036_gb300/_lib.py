@@ -50,7 +50,7 @@ class tm_search_params(ctypes.Structure):
     _fields_ = [("hamming_max", c_i32), ("ratio_num", c_i32), ("ratio_den", c_i32),
                 ("epi_chi2", c_f32), ("epipolar", c_i32), ("resolve", c_i32),
                 ("rot_filter", c_i32), ("mode", c_i32), ("lanes_per_query", c_i32),
-                ("dense_min", c_i32)]
+                ("dense_min", c_i32), ("epipole_px", c_f32), ("rot_mode", c_i32)]
 
 
 class tm_fuse_params(ctypes.Structure):

@@ -107,11 +107,38 @@ __device__ __forceinline__ bool epi_pass(const Line &l, float xt, float yt, floa
     return epi_pass_den(l, epi_den(l), xt, yt, thr);
 }
 
+// The epipole in T (ORB-family rejection): Q's camera centre C_Q = -R_Q^T t_Q, C = R_T C_Q +
+// t_T, e = (fx * (C_x / C_z) + cx, fy * (C_y / C_z) + cy), float64 with sums left to right,
+// rounded to float32 (+-inf or NaN when C_z = 0, which then rejects nothing).  One thread.
+__device__ void epipole_of(const CamConst &cam, const double *Tq, const double *Tt, float *e) {
+    double cq[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+        double s = dmul(Tq[0 * 4 + k], Tq[0 * 4 + 3]);
+        s = dadd(s, dmul(Tq[1 * 4 + k], Tq[1 * 4 + 3]));
+        s = dadd(s, dmul(Tq[2 * 4 + k], Tq[2 * 4 + 3]));
+        cq[k] = -s;
+    }
+    for (int r = 0; r < 3; ++r) {
+        double s = dmul(Tt[r * 4 + 0], cq[0]);
+        s = dadd(s, dmul(Tt[r * 4 + 1], cq[1]));
+        s = dadd(s, dmul(Tt[r * 4 + 2], cq[2]));
+        c[r] = dadd(s, Tt[r * 4 + 3]);
+    }
+    e[0] = __double2float_rn(dadd(dmul(cam.fx, __ddiv_rn(c[0], c[2])), cam.cx));
+    e[1] = __double2float_rn(dadd(dmul(cam.fy, __ddiv_rn(c[1], c[2])), cam.cy));
+}
+// Squared distance to the epipole below the level's threshold: the candidate is dropped.
+__device__ __forceinline__ bool near_epipole(const float *e, float xt, float yt, float thr) {
+    const float dx = fsub(e[0], xt), dy = fsub(e[1], yt);
+    return fadd(fmul(dx, dx), fmul(dy, dy)) < thr;
+}
+
 // Rotation bin: 30 bins of 12 degrees over angle_Q - angle_T wrapped into [0, 360).
-__device__ __forceinline__ int rot_bin(float aq, float at) {
+__device__ __forceinline__ int rot_bin(float aq, float at, int mode) {
     float rot = fsub(aq, at);
     if (rot < 0.0f) rot = fadd(rot, 360.0f);
-    int bin = (int)floorf(__fdiv_rn(rot, 12.0f));
+    // mode 1: the ORB-family binning, nearest integer of rot * (1/30) (halves away from zero)
+    int bin = mode == 1 ? (int)roundf(fmul(rot, 1.0f / 30.0f)) : (int)floorf(__fdiv_rn(rot, 12.0f));
     if (bin >= kBins || bin < 0) bin = 0;  // (< 0 only for angles outside [0, 360))
     return bin;
 }
@@ -710,6 +737,7 @@ __device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &
 __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
                                              const float *F, const float *thr, const uint32_t *tkey,
                                              const uint16_t *bst, const uint16_t *ep, const uint16_t *epos,
+                                             const float *epl, const float *thre,
                                              uint32_t *win, uint32_t *acc, uint2 *st, int g, const QLoad &q,
                                              uint32_t &cmp, uint32_t *dfail) {
     const int lane = (int)(threadIdx.x & 31u);
@@ -773,7 +801,8 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             const int lv = T.level[j0];
             ++cmp;
             const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
-            if (!epi || epi_pass(li, xt.x, xt.y, thr[lv])) bk = (d << 16) | (uint32_t)j0;
+            if ((!epi || epi_pass(li, xt.x, xt.y, thr[lv])) && !(thre && near_epipole(epl, xt.x, xt.y, thre[lv])))
+                bk = (d << 16) | (uint32_t)j0;
         }
         // segmented merge over the lanes of each query (suffix within the segment), as many
         // doubling steps as the round's longest segment needs
@@ -936,7 +965,7 @@ __device__ __forceinline__ void expand_half_row(unsigned char *tile, int r, int 
 __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ float F[9];
-    __shared__ float thr[kLevels];
+    __shared__ float thr[kLevels], thre[kLevels], epl[2];
     __shared__ uint32_t wtot[32];
     __shared__ uint32_t s_taddr, s_fail;
     __shared__ __align__(8) uint64_t bar, never;
@@ -997,16 +1026,18 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
         s_fail = 0u;
     }
     if (wid == 2) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid == 96 && A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, epl);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
+        thre[tid] = fmul(fmul(A.sp.epipole_px, A.sp.epipole_px), sc);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = s_taddr;
     const uint32_t tlane = tbase + ((uint32_t)((wid & 3) * 32) << 16);  // this warp's 32 lanes
-    const bool epi = A.sp.epipolar != 0;
+    const bool epi = A.sp.epipolar != 0, eprej = A.sp.epipole_px > 0.0f;
     uint32_t phase = 0;
     for (int rr = 0; rr < nrun; ++rr) {
         const int lo = runs[2 * rr], hi = runs[2 * rr + 1];
@@ -1083,7 +1114,8 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
                         if (half == 0) {
                             const float2 xy = T.xy[j];
                             const bool e = w.b == kNone || A.masks[w.b + T.orig[j]] != 0;
-                            col[row] = make_float4(xy.x, xy.y, e ? thr[T.level[j]] : -1.0f, 0.0f);
+                            const int lv = T.level[j];
+                            col[row] = make_float4(xy.x, xy.y, e ? thr[lv] : -1.0f, thre[lv]);
                         }
                     }
                     b_ready = ncol <= kDenseCols;
@@ -1121,7 +1153,8 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
                                         const int dot = (int)__int_as_float(v[k]);
                                         const uint32_t d = (uint32_t)(256 - dot) >> 1;
                                         const float4 cc = col[c];
-                                        if (cc.z >= 0.0f && (!epi || epi_pass_den(l, den, cc.x, cc.y, cc.z))) {
+                                        if (cc.z >= 0.0f && (!epi || epi_pass_den(l, den, cc.x, cc.y, cc.z)) &&
+                                            !(eprej && near_epipole(epl, cc.x, cc.y, cc.w))) {
                                             const uint32_t kk = (d << 16) | (uint32_t)(lo + n0 + c);
                                             sc = min(sc, max(bk, kk) >> 16);
                                             bk = min(bk, kk);
@@ -1173,7 +1206,7 @@ template <int kMaxT>
 __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ float F[9];
-    __shared__ float thr[kLevels];
+    __shared__ float thr[kLevels], thre[kLevels], epl[2];
     __shared__ uint2 qst[kMaxT / 32][32];  // per warp
     __shared__ uint32_t hist[32];
     __shared__ uint32_t wtot[32];
@@ -1213,9 +1246,11 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         bulk_prefetch_l2(w.qdesc, 32u * (uint32_t)nQ);
     }
     if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
+    if (tid == 64 && A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, epl);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
+        thre[tid] = fmul(fmul(A.sp.epipole_px, A.sp.epipole_px), sc);
     }
     if (tid < 32) hist[tid] = 0u;
     QLoad cur = {};
@@ -1271,7 +1306,8 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     for (int g = wid; g * 32 < nQ; g += nw) {
         QLoad nxt = {};
         if ((g + nw) * 32 < nQ) nxt = load_group(A, w, g + nw);
-        search_group(A, w, T, F, thr, tkey, bst, ep, epos, win, acc, qst[wid], g, cur, cmp, &sdfail);
+        search_group(A, w, T, F, thr, tkey, bst, ep, epos, epl, A.sp.epipole_px > 0.0f ? thre : nullptr, win, acc,
+                     qst[wid], g, cur, cmp, &sdfail);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
@@ -1303,7 +1339,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
             const uint32_t ac = acc[p], j = ac >> 16, d = ac & 0xFFFFu;
             const uint32_t io = w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p;
             if (!A.sp.resolve || win[j] == ((d << 16) | io)) {
-                bin = rot ? (uint32_t)rot_bin(w.qangle[p], T.angle[j]) : 0u;
+                bin = rot ? (uint32_t)rot_bin(w.qangle[p], T.angle[j], A.sp.rot_mode) : 0u;
                 fres[io] = pack_res(T.orig[j], d, bin);
             }
         }
@@ -1512,16 +1548,18 @@ __global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *
                                   const uint8_t *mq, const uint8_t *mt, int cap, SearchConst sp,
                                   CamConst cam, PairScratch scr, unsigned long long *ncmp) {
     __shared__ float F[9];
-    __shared__ float thr[kLevels];
+    __shared__ float thr[kLevels], thre[kLevels], epl[2];
     __shared__ unsigned long long s_cmp;
     const SlotLayout L = SlotLayout::make(cap);
     const KfView Q = KfView::at(qs, L), T = KfView::at(ts, L);
     const int nQ = Q.hdr->n, nT = T.hdr->n;
     if (threadIdx.x < 32) fundamental_lanes(cam, Q.hdr->Tcw, T.hdr->Tcw, F);
+    if (threadIdx.x == 32 && sp.epipole_px > 0.0f) epipole_of(cam, Q.hdr->Tcw, T.hdr->Tcw, epl);
     if (threadIdx.x == 0) s_cmp = 0ull;
     if (threadIdx.x < kLevels) {
         const float s = level_scale(threadIdx.x);
         thr[threadIdx.x] = fmul(sp.epi_chi2, fmul(s, s));
+        thre[threadIdx.x] = fmul(fmul(sp.epipole_px, sp.epipole_px), s);
     }
     __syncthreads();
     const int g = threadIdx.x / G, sub = threadIdx.x % G;
@@ -1543,9 +1581,10 @@ __global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *
                     if (mt && !mt[T.orig[j]]) continue;
                     ++my_cmp;
                     const uint32_t d = (uint32_t)hamming(q0, q1, T.desc[2 * j], T.desc[2 * j + 1]);
-                    if (sp.epipolar) {
+                    if (sp.epipolar || sp.epipole_px > 0.0f) {
                         const float2 xt = T.xy[j];
-                        if (!epi_pass(l, xt.x, xt.y, thr[T.level[j]])) continue;
+                        if (sp.epipolar && !epi_pass(l, xt.x, xt.y, thr[T.level[j]])) continue;
+                        if (sp.epipole_px > 0.0f && near_epipole(epl, xt.x, xt.y, thre[T.level[j]])) continue;
                     }
                     const uint32_t key = (d << 16) | (uint32_t)j;
                     if (key < bkey) { sec = min(sec, bkey >> 16); bkey = key; }
@@ -1594,7 +1633,7 @@ __global__ void pair_resolve_kernel(const unsigned char *qs, const unsigned char
     if (sp.resolve && scr.win[j] != ((d << 16) | io)) return;
     uint32_t bin = 0;
     if (sp.rot_filter) {
-        bin = (uint32_t)rot_bin(Q.angle[p], T.angle[j]);
+        bin = (uint32_t)rot_bin(Q.angle[p], T.angle[j], sp.rot_mode);
         atomicAdd(&scr.hist[bin], 1u);
     }
     scr.res[io] = pack_res(T.orig[j], d, bin);
@@ -1908,7 +1947,8 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     tm_search_params sp;
     tm_search_params_default(&sp);
     if (params) sp = *params;
-    if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0))
+    if (sp.hamming_max < 0 || sp.ratio_num < 0 || sp.ratio_den < 0 || !(sp.epi_chi2 >= 0) ||
+        !(sp.epipole_px >= 0.0f && sp.epipole_px < 1e6f) || (sp.rot_mode != 0 && sp.rot_mode != 1))
         return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad search parameters");
     const int l = sp.lanes_per_query ? sp.lanes_per_query : 1;
     if (!(l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
@@ -1965,6 +2005,8 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     sc.resolve = sp.resolve;
     sc.rot_filter = sp.rot_filter;
     sc.dense_min = 0;
+    sc.epipole_px = sp.epipole_px;
+    sc.rot_mode = sp.rot_mode;
     uint32_t *pair_offset = ps.running + 1;  // start of the output (always 0 here)
     if ((e = launch_pair_plain(slot_q, slot_t, q_free, t_free, q->n, t->n, kNoAllocMaxKp, sc, cc, ps,
                                reinterpret_cast<Out3 *>(out), pair_offset, ncmp, l, s)))

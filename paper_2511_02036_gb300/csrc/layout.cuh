@@ -199,6 +199,8 @@ struct SearchConst {
     float epi_chi2;
     int32_t epipolar, resolve, rot_filter;
     int32_t dense_min;            // dense node blocks (tensor cores) from this run length; 0 = off
+    float epipole_px;             // epipole rejection radius at level 0 (0 = off)
+    int32_t rot_mode;             // 0: 30 bins of 12 degrees; 1: round(rot / 30)
 };
 
 struct FuseConst {

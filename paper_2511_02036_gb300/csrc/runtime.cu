@@ -109,6 +109,8 @@ extern "C" void tm_search_params_default(tm_search_params *p) {
     p->mode = TM_MODE_FUSED;
     p->lanes_per_query = 0;
     p->dense_min = 0;
+    p->epipole_px = 0.0f;
+    p->rot_mode = 0;
 }
 
 extern "C" void tm_fuse_params_default(tm_fuse_params *p) {
@@ -503,6 +505,8 @@ static SearchConst to_const(const tm_search_params &p) {
     s.resolve = p.resolve;
     s.rot_filter = p.rot_filter;
     s.dense_min = p.mode == TM_MODE_FUSED ? p.dense_min : 0;
+    s.epipole_px = p.epipole_px;
+    s.rot_mode = p.rot_mode;
     return s;
 }
 
@@ -513,6 +517,9 @@ static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &
         return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
     if (sp.dense_min != 0 && sp.dense_min < 16)
         return fail(TM_ERR_INVALID_ARG, "dense_min must be 0 or >= 16 (got %d)", sp.dense_min);
+    if (!(sp.epipole_px >= 0.0f && sp.epipole_px < 1e6f))
+        return fail(TM_ERR_INVALID_ARG, "epipole_px must be in [0, 1e6)");
+    if (sp.rot_mode != 0 && sp.rot_mode != 1) return fail(TM_ERR_INVALID_ARG, "rot_mode must be 0 or 1");
     const int l = sp.lanes_per_query;
     if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
         return fail(TM_ERR_INVALID_ARG, "lanes_per_query must be 0, 1, 2, 4, 8, 16 or 32");

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def osp(sp):
     return O.SearchParams(sp.hamming_max, sp.ratio_num, sp.ratio_den, sp.epi_chi2, sp.epipolar,
-                          sp.resolve, sp.rot_filter)
+                          sp.resolve, sp.rot_filter, sp.epipole_px, sp.rot_mode)
 
 
 def load_step(tm, ctx, w, st):
@@ -59,16 +59,22 @@ def test_dense_blocks_match_oracle(tm, dense_step, dense_min):
 
 
 @pytest.mark.parametrize("variant", ["gates_off", "no_epipolar", "no_ratio", "no_resolve",
-                                     "no_rot", "loose_chi2"])
+                                     "no_rot", "loose_chi2", "orb_variants"])
 def test_dense_parameter_variants(tm, dense_step, variant):
     sp = {"gates_off": dict(hamming_max=256, ratio_num=0, epipolar=False, resolve=False, rot_filter=False),
           "no_epipolar": dict(epipolar=False),
           "no_ratio": dict(ratio_num=0),
           "no_resolve": dict(resolve=False),
           "no_rot": dict(rot_filter=False),
-          "loose_chi2": dict(epi_chi2=50.0)}[variant]
+          "loose_chi2": dict(epi_chi2=50.0),
+          "orb_variants": dict(rot_mode=1)}[variant]
     w = dense_step
     st = w["steps"][0]
+    if variant == "orb_variants":  # a radius that reaches into the image for most neighbours
+        sp["epipole_px"] = float(np.median([np.hypot(*(O.epipole(w["cam"], w["frames"][st["q"]]["Tcw"],
+                                                                   w["frames"][f]["Tcw"]) -
+                                                       np.array([w["cam"]["cx"], w["cam"]["cy"]])))
+                                            for f in st["nbrs"]]))
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         load_step(tm, ctx, w, st)
         check_step(tm, ctx, w, st, tm.SearchParams(dense_min=16, **sp))

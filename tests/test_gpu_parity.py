@@ -22,7 +22,7 @@ def tm():
 def osp(sp):
     """Oracle parameters of a binding SearchParams."""
     return O.SearchParams(sp.hamming_max, sp.ratio_num, sp.ratio_den, sp.epi_chi2, sp.epipolar,
-                          sp.resolve, sp.rot_filter)
+                          sp.resolve, sp.rot_filter, sp.epipole_px, sp.rot_mode)
 
 
 def ofp(fp):
@@ -60,7 +60,8 @@ def test_lanes_and_modes(tm, lanes, mode):
 
 
 @pytest.mark.parametrize("variant", ["gates_off", "no_ratio", "no_epipolar", "no_resolve",
-                                     "no_rot", "tight", "loose_chi2"])
+                                     "no_rot", "tight", "loose_chi2", "epipole_10", "epipole_half",
+                                     "orb_bins", "orb_all"])
 def test_parameter_variants(tm, variant):
     sp = {"gates_off": tm.SearchParams(hamming_max=256, ratio_num=0, epipolar=False, resolve=False,
                                        rot_filter=False),
@@ -69,8 +70,17 @@ def test_parameter_variants(tm, variant):
           "no_resolve": tm.SearchParams(resolve=False),
           "no_rot": tm.SearchParams(rot_filter=False),
           "tight": tm.SearchParams(hamming_max=30, ratio_num=1, ratio_den=2),
-          "loose_chi2": tm.SearchParams(epi_chi2=50.0)}[variant]
+          "loose_chi2": tm.SearchParams(epi_chi2=50.0),
+          "epipole_10": tm.SearchParams(epipole_px=10.0),
+          "epipole_half": tm.SearchParams(),
+          "orb_bins": tm.SearchParams(rot_mode=1),
+          "orb_all": tm.SearchParams(rot_mode=1, epipolar=False)}[variant]
     p = W.make_pair_cfg0(21, n_nodes=30)
+    if variant in ("epipole_half", "orb_all"):
+        # a radius reaching the image centre: the epipole of this lateral motion lies far
+        # outside the image, and about half of the image is rejected
+        e = O.epipole(p["cam"], p["Q"]["Tcw"], p["T"]["Tcw"])
+        sp.epipole_px = float(np.hypot(e[0] - p["cam"]["cx"], e[1] - p["cam"]["cy"]))
     rng = np.random.default_rng(3)
     fq = (rng.random(p["Q"]["n"]) < 0.9).astype(np.uint8)
     ft = (rng.random(p["T"]["n"]) < 0.9).astype(np.uint8)
@@ -213,3 +223,23 @@ def test_device_resident_inputs(tm):
         fg, _ = ctx.fuse(st["q"], mps)
         fe, _ = O.fuse_step(w["cam"], w["frames"], st)
         np.testing.assert_array_equal(fg, fe)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_orb_variants_step(tm, mode):
+    """ORB-family variants on a whole EuRoC-shaped step (batched and per-pair forms): epipole
+    rejection with a radius that removes matches, and the ORB rotation binning."""
+    w = W.make_cfg1(seed=1003)
+    st = w["steps"][0]
+    d = [np.hypot(*(O.epipole(w["cam"], w["frames"][st["q"]]["Tcw"], w["frames"][f]["Tcw"]) -
+                    np.array([w["cam"]["cx"], w["cam"]["cy"]]))) for f in st["nbrs"]]
+    px = float(np.median(d))  # reaches the image centre for half of the neighbours
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_step(tm, ctx, w, st)
+        for sp in (tm.SearchParams(epipole_px=px, mode=mode), tm.SearchParams(rot_mode=1, mode=mode),
+                   tm.SearchParams(epipole_px=px, rot_mode=1, mode=mode, lanes_per_query=4)):
+            got, ncmp = ctx.search(st["q"], st["nbrs"], st.get("q_free"), st.get("nbr_free"), sp)
+            exp, ecmp = O.search_step(w["cam"], w["frames"], st, osp(sp))
+            for g, e in zip(got, exp):
+                np.testing.assert_array_equal(g, e)
+            assert ncmp == ecmp

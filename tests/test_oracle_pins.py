@@ -3,6 +3,7 @@
 
 Runs on the CPU only."""
 
+import ctypes
 import json
 import os
 
@@ -414,3 +415,59 @@ def test_forward_fusion_skip_and_independence():
     allskip["fwd_skip"] = [np.ones(fw["n"], np.uint8) for _ in st["nbrs"]]
     r2, c2 = O.fuse_forward_step(w["cam"], w["frames"], allskip)
     assert c2 == 0 and all(len(x) == 0 for x in r2)
+
+
+def test_orb_rotation_bins_golden():
+    """ORB-family binning (rot_mode 1): nearest integer of rot * (1/30), halves away from zero,
+    values worked by hand at the rounding boundaries; mode 0 keeps 30 bins of 12 degrees."""
+    cases = [((15.0, 0.0), 1), ((14.99, 0.0), 0), ((45.0, 0.0), 2), ((44.9, 0.0), 1),
+             ((0.0, 15.0), 12), ((0.0, 0.01), 12), ((344.9, 0.0), 11), ((0.0, 0.0), 0),
+             ((100.0, 40.0), 2), ((40.0, 100.0), 10)]
+    for (aq, at), b in cases:
+        assert O.rot_bin(aq, at, 1) == b, (aq, at)
+    assert [O.rot_bin(a, 0.0, 0) for a in (0.0, 11.99, 12.0, 359.9)] == [0, 0, 1, 29]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_epipole_on_every_epipolar_line(seed):
+    """The epipole in T (Q's centre projected into T) is the common point of the epipolar
+    lines F^T x_Q of every query pixel: a * ex + b * ey + c = 0 up to float32 rounding."""
+    p = W.make_pair_cfg0(seed)
+    cam, Q, T = p["cam"], p["Q"], p["T"]
+    e = O.epipole(cam, Q["Tcw"], T["Tcw"]).astype(np.float64)
+    F = np.zeros(9, np.float32)
+    O.lib().orc_fundamental(ctypes.byref(O._cam(cam)), np.ascontiguousarray(Q["Tcw"], np.float64).ctypes.data,
+                            np.ascontiguousarray(T["Tcw"], np.float64).ctypes.data, F.ctypes.data)
+    F = F.astype(np.float64).reshape(3, 3)
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        xq = np.array([rng.uniform(0, cam["width"]), rng.uniform(0, cam["height"]), 1.0])
+        l = F.T @ xq
+        d = abs(l[0] * e[0] + l[1] * e[1] + l[2]) / np.hypot(l[0], l[1])
+        assert d < 1e-3 * max(1.0, np.hypot(*e) / 1000.0), d
+
+
+def test_epipole_rejection_invariants():
+    """With epipole rejection, no kept match targets a keypoint inside the rejection radius;
+    the comparison count is unchanged (the distance is computed before the check); a radius
+    covering the whole image keeps nothing; radius 0 is the default search."""
+    w = W.make_cfg1()
+    st = w["steps"][0]
+    cam = w["cam"]
+    Q = w["frames"][st["q"]]
+    scale = [1.2 ** l for l in range(8)]
+    for k, f in enumerate(st["nbrs"][:4]):
+        T = w["frames"][f]
+        ft = st["nbr_free"][k]
+        base, c0 = O.search_pair(cam, Q, T, st["q_free"], ft)
+        same, c1 = O.search_pair(cam, Q, T, st["q_free"], ft, O.SearchParams(epipole_px=0.0))
+        np.testing.assert_array_equal(base, same)
+        e = O.epipole(cam, Q["Tcw"], T["Tcw"])
+        for px in (30.0, 300.0):
+            m, c2 = O.search_pair(cam, Q, T, st["q_free"], ft, O.SearchParams(epipole_px=px))
+            assert c2 == c0
+            for _, t, _ in m:
+                dx = np.float32(e[0] - T["xy"][t, 0]); dy = np.float32(e[1] - T["xy"][t, 1])
+                assert dx * dx + dy * dy >= np.float32(px * px) * np.float32(scale[T["level"][t]])
+        m, _ = O.search_pair(cam, Q, T, st["q_free"], ft, O.SearchParams(epipole_px=1e5))
+        assert len(m) == 0
