@@ -218,6 +218,21 @@ typedef struct {
     int64_t fwd_skip_off;
 } tm_step;
 
+/* Triangulation of the search's matches and their acceptance as new map points (Sec. III,
+ * Map Point Creation: sufficient parallax, positive depth, low reprojection error, scale
+ * consistency), run on the GPU over the batch's match lists.  Float64: normalized
+ * coordinates (u - cx) / fx; world rays R^T (xn, yn, 1), kept iff 0 < cos(parallax) <
+ * cos_parallax_max; linear triangulation from the rows xn P_3 - P_1, yn P_3 - P_2 of both
+ * views (P = [R | t]) by least squares through the 3x3 normal equations (Cramer's rule);
+ * depth > 0 and reprojection error^2 <= chi2 * 1.44^level in each view; distance ratio to
+ * the two camera centres consistent with the scale ratio within ratio_factor. */
+typedef struct {
+    double cos_parallax_max;  /* (0.9998)                                                   */
+    double chi2;              /* (5.991)                                                    */
+    double ratio_factor;      /* (1.8 = 1.5 * 1.2)                                          */
+} tm_triangulation_params;
+void tm_triangulation_params_default(tm_triangulation_params *p);
+
 typedef struct {
     const uint8_t *masks;    /* host or device, mask_bytes bytes (may be NULL if unused)    */
     size_t mask_bytes;
@@ -230,6 +245,8 @@ typedef struct {
     int32_t n_new;
     const uint64_t *new_ids;          /* host [n_new]                                       */
     const tm_keyframe_view *new_kfs;  /* host [n_new]                                       */
+    /* NULL, or triangulate every match of the batch (results in tm_batch_result.points). */
+    const tm_triangulation_params *tri;
 } tm_batch_inputs;
 
 /* Results, host buffers.  Search matches of all steps, step-major then neighbour order:
@@ -248,6 +265,11 @@ typedef struct {
     tm_fuse_match *fwd; size_t fwd_cap; size_t n_fwd;
     int32_t *fwd_offsets;    /* [total pairs + 1]                                           */
     uint64_t n_comparisons_fwd;
+    /* With triangulation: per match (same order as matches) its point, float32 x, y, z in
+     * the world frame (0 when not accepted), and 1 when accepted as a new map point; both
+     * match_cap entries, required then. */
+    float *points;
+    uint8_t *point_ok;
 } tm_batch_result;
 
 /* One-shot: upload, one launch sequence, download.  TM_ERR_CAPACITY sets n_matches and

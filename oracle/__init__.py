@@ -77,6 +77,18 @@ class SearchParams:
 
 
 @dataclass
+class TriParams:
+    cos_parallax_max: float = 0.9998
+    chi2: float = 5.991
+    ratio_factor: float = 1.5 * 1.2
+
+
+class _TriParams(ctypes.Structure):
+    _fields_ = [("cos_parallax_max", ctypes.c_double), ("chi2", ctypes.c_double),
+                ("ratio_factor", ctypes.c_double)]
+
+
+@dataclass
 class FuseParams:
     chi2: float = 5.99
     hamming_max: int = 50
@@ -110,6 +122,10 @@ def lib(path=None):
         L.orc_epipole.restype = None
         L.orc_rot_bin_mode.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int]
         L.orc_rot_bin_mode.restype = ctypes.c_int
+        L.orc_triangulate.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Keyframe),
+                                      ctypes.POINTER(_Keyframe), ctypes.c_int64, P, P,
+                                      ctypes.POINTER(_TriParams), P, P]
+        L.orc_triangulate.restype = None
         L.orc_fuse.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Keyframe),
                                ctypes.c_int32, P, P, P, P, P, P,
                                ctypes.POINTER(_FuseParams), P, P, P, ctypes.c_int64,
@@ -166,6 +182,22 @@ def epipole(cam, Tq, Tt):
 def rot_bin(angle_q, angle_t, mode=0):
     """Rotation-histogram bin of a match under rot_mode `mode`."""
     return int(lib().orc_rot_bin_mode(float(angle_q), float(angle_t), int(mode)))
+
+
+def triangulate(cam, Q, T, matches, params=None):
+    """Triangulation of a pair's matches (k, 3) int32 (q_idx, t_idx, dist) and their
+    acceptance as new map points: float32 (k, 3) points (0 where rejected) and uint8 (k,) flags."""
+    p = params or TriParams()
+    keep = []
+    q, t = _kf(Q, keep), _kf(T, keep)
+    m = np.ascontiguousarray(np.asarray(matches, np.int32).reshape(-1, 3))
+    qi, ti = np.ascontiguousarray(m[:, 0]), np.ascontiguousarray(m[:, 1])
+    xyz = np.zeros((len(m), 3), np.float32)
+    ok = np.zeros(len(m), np.uint8)
+    tp = _TriParams(p.cos_parallax_max, p.chi2, p.ratio_factor)
+    lib().orc_triangulate(ctypes.byref(_cam(cam)), ctypes.byref(q), ctypes.byref(t), len(m),
+                          qi.ctypes.data, ti.ctypes.data, ctypes.byref(tp), xyz.ctypes.data, ok.ctypes.data)
+    return xyz, ok
 
 
 def search_pair(cam, Q, T, free_q=None, free_t=None, params=None):

@@ -75,6 +75,19 @@ void orc_epipole(const orc_camera *cam, const double Tcw_q[12], const double Tcw
 /* Rotation bin of a match (rot_mode as in orc_search_params). */
 int orc_rot_bin_mode(float angle_q, float angle_t, int mode);
 
+/* Triangulation of matches and their acceptance as new map points (Sec. III, Map Point
+ * Creation: sufficient parallax, positive depth, low reprojection error, scale consistency). */
+typedef struct {
+    double cos_parallax_max;  /* accept only 0 < cos(angle between the rays) < this (0.9998) */
+    double chi2;              /* reprojection error^2 <= chi2 * sigma^2(level), each view (5.991) */
+    double ratio_factor;      /* scale consistency factor (1.5 * 1.2)                       */
+} orc_tri_params;
+/* For n matches (q_idx[k] of Q, t_idx[k] of T): xyz[3k..3k+2] the triangulated point
+ * (float32; 0 when rejected), ok[k] = 1 when every constraint holds. */
+void orc_triangulate(const orc_camera *cam, const orc_keyframe *Q, const orc_keyframe *T,
+                     int64_t n, const int32_t *q_idx, const int32_t *t_idx,
+                     const orc_tri_params *p, float *xyz, uint8_t *ok);
+
 /* F (float32, row-major 3x3) with x_Q^T F x_T = 0 for corresponding pixels. */
 void orc_fundamental(const orc_camera *cam, const double Tcw_q[12], const double Tcw_t[12],
                      float F[9]);

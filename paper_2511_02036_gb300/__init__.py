@@ -180,6 +180,17 @@ class SearchParams:
 
 
 @dataclass
+class TriParams:
+    """Triangulation of the matches and their acceptance as new map points."""
+    cos_parallax_max: float = 0.9998
+    chi2: float = 5.991
+    ratio_factor: float = 1.5 * 1.2
+
+    def struct(self):
+        return L.tm_triangulation_params(self.cos_parallax_max, self.chi2, self.ratio_factor)
+
+
+@dataclass
 class FuseParams:
     chi2: float = 5.99
     hamming_max: int = 50
@@ -324,7 +335,7 @@ class BatchResult:
     fwd_mp_begin, in the neighbour's keypoints)."""
 
     def __init__(self, matches, pair_offsets, fuse, fuse_offsets, ncmp_search, ncmp_fuse,
-                 fwd=None, fwd_offsets=None, ncmp_fwd=0):
+                 fwd=None, fwd_offsets=None, ncmp_fwd=0, points=None, point_ok=None):
         self.matches = matches
         self.pair_offsets = pair_offsets
         self.fuse = fuse
@@ -335,6 +346,8 @@ class BatchResult:
         self.n_comparisons_search = ncmp_search
         self.n_comparisons_fuse = ncmp_fuse
         self.n_comparisons_fwd = ncmp_fwd
+        self.points = points        # (n_matches, 3) float32 with triangulation, else None
+        self.point_ok = point_ok    # (n_matches,) uint8: accepted as a new map point
 
     @property
     def fwds(self):
@@ -358,7 +371,7 @@ class BatchResult:
         return self._fuses
 
 
-def _result_struct(match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0):
+def _result_struct(match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0, tri=False):
     m = np.zeros((max(1, match_cap), 3), np.int32)
     po = np.zeros(n_pairs + 1, np.int32)
     f = np.zeros((max(1, fuse_cap), 3), np.int32)
@@ -369,14 +382,21 @@ def _result_struct(match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0):
     r.matches, r.match_cap, r.pair_offsets = m.ctypes.data, match_cap, po.ctypes.data
     r.fuse, r.fuse_cap, r.fuse_offsets = f.ctypes.data, fuse_cap, fo.ctypes.data
     r.fwd, r.fwd_cap, r.fwd_offsets = w.ctypes.data, fwd_cap, wo.ctypes.data
-    return r, (m, po, f, fo, w, wo)
+    pt = ok = None
+    if tri:
+        pt = np.zeros((max(1, match_cap), 3), np.float32)
+        ok = np.zeros(max(1, match_cap), np.uint8)
+        r.points, r.point_ok = pt.ctypes.data, ok.ctypes.data
+    return r, (m, po, f, fo, w, wo, pt, ok)
 
 
 def _collect(r, bufs):
-    m, po, f, fo, w, wo = bufs
-    return BatchResult(m[:r.n_matches].copy(), po.copy(), f[:r.n_fuse].copy(), fo.copy(),
+    m, po, f, fo, w, wo, pt, ok = bufs
+    n = r.n_matches
+    return BatchResult(m[:n].copy(), po.copy(), f[:r.n_fuse].copy(), fo.copy(),
                        int(r.n_comparisons_search), int(r.n_comparisons_fuse),
-                       w[:r.n_fwd].copy(), wo.copy(), int(r.n_comparisons_fwd))
+                       w[:r.n_fwd].copy(), wo.copy(), int(r.n_comparisons_fwd),
+                       None if pt is None else pt[:n].copy(), None if ok is None else ok[:n].copy())
 
 
 def _fwd_cap(steps):
@@ -417,7 +437,7 @@ class _ResultBuffers:
     available, so that the results come back by DMA) and grown as needed."""
 
     def __init__(self):
-        self.m = self.po = self.f = self.fo = self.w = self.wo = None
+        self.m = self.po = self.f = self.fo = self.w = self.wo = self.pt = self.ok = None
 
     @staticmethod
     def _grow(a, n, width):
@@ -431,7 +451,7 @@ class _ResultBuffers:
         except Exception:  # no torch or no CUDA runtime: pageable memory
             return np.empty((n, width) if width else (n,), np.int32)
 
-    def struct(self, match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0):
+    def struct(self, match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0, tri=False):
         self.m = self._grow(self.m, max(1, match_cap), 3)
         self.po = self._grow(self.po, n_pairs + 1, 0)
         self.f = self._grow(self.f, max(1, fuse_cap), 3)
@@ -442,7 +462,22 @@ class _ResultBuffers:
         r.matches, r.match_cap, r.pair_offsets = self.m.ctypes.data, match_cap, self.po.ctypes.data
         r.fuse, r.fuse_cap, r.fuse_offsets = self.f.ctypes.data, fuse_cap, self.fo.ctypes.data
         r.fwd, r.fwd_cap, r.fwd_offsets = self.w.ctypes.data, fwd_cap, self.wo.ctypes.data
-        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1], self.w, self.wo[:n_pairs + 1])
+        pt = ok = None
+        if tri:
+            self.pt = self._grow_f(self.pt, max(1, match_cap))
+            self.ok = self._grow_u8(self.ok, max(1, match_cap))
+            pt, ok = self.pt, self.ok
+            r.points, r.point_ok = pt.ctypes.data, ok.ctypes.data
+        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1], self.w, self.wo[:n_pairs + 1],
+                   pt, ok)
+
+    @staticmethod
+    def _grow_f(a, n):
+        return a if a is not None and a.shape[0] >= n else np.empty((max(n, 1024), 3), np.float32)
+
+    @staticmethod
+    def _grow_u8(a, n):
+        return a if a is not None and a.shape[0] >= n else np.empty(max(n, 1024), np.uint8)
 
 
 class Context:
@@ -584,20 +619,25 @@ class Context:
         keep.append(st)
         return st, inp, keep
 
-    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None):
+    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None, tri=None):
         """One-shot batch (tm_batch_run).  Without masks/mps the steps carry their own
         q_free / nbr_free / mps and are packed here.  new = (ids, keyframes) entering the
         store with the batch: a list of keyframe dicts, or one packed dict (see
-        keyframe_views_packed)."""
+        keyframe_views_packed).  tri = TriParams(): triangulate every match (res.points,
+        res.point_ok)."""
         sp = sp or SearchParams()
         st, inp, keep = self._inputs(steps, masks, mps, new)
+        if tri is not None:
+            ts = tri.struct()
+            keep.append(ts)
+            inp.tri = ctypes.addressof(ts)
         mc, fc = _result_caps(steps, self.sizes, sp.resolve)
         if masks is not None or mps is not None:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
         if self._res is None:
             self._res = _ResultBuffers()
         n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
-        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps))
+        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps), tri is not None)
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
             check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
@@ -614,8 +654,8 @@ class Context:
         L.TM_DEBUG_STARVE_WAITS (bounded device waits run out)."""
         check(tm_debug_set(self.handle, int(what), int(value)))  # noqa: F821
 
-    def plan(self, steps, masks=None, mps=None, sp=None, fp=None, new=None):
-        return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams(), new)
+    def plan(self, steps, masks=None, mps=None, sp=None, fp=None, new=None, tri=None):
+        return Plan(self, steps, masks, mps, sp or SearchParams(), fp or FuseParams(), new, tri)
 
     def server(self, **cfg):
         return Server(self, **cfg)
@@ -624,9 +664,14 @@ class Context:
 class Plan:
     """A prepared batch (tm_plan): inputs resident on the GPU, launch captured in a graph."""
 
-    def __init__(self, ctx, steps, masks, mps, sp, fp, new=None):
+    def __init__(self, ctx, steps, masks, mps, sp, fp, new=None, tri=None):
         self.ctx = ctx
         st, inp, self._keep = ctx._inputs(steps, masks, mps, new)
+        self.tri = tri is not None
+        if tri is not None:
+            ts = tri.struct()
+            self._keep.append(ts)
+            inp.tri = ctypes.addressof(ts)
         self.caps = _result_caps(steps, ctx.sizes, sp.resolve)
         if mps is not None:
             self.caps = (self.caps[0], max(self.caps[1], int(mps["n"])))
@@ -645,7 +690,7 @@ class Plan:
         check(fn(self.handle, _stream(stream)))
 
     def results(self, stream=None):
-        r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps, self.fwd_cap)
+        r, bufs = _result_struct(self.caps[0], self.n_pairs, self.caps[1], self.n_steps, self.fwd_cap, self.tri)
         check(tm_plan_results(self.handle, ctypes.byref(r), _stream(stream)))  # noqa: F821
         return _collect(r, bufs)
 

@@ -74,9 +74,14 @@ class tm_step(ctypes.Structure):
                 ("fwd_skip_off", c_i64)]
 
 
+class tm_triangulation_params(ctypes.Structure):
+    _fields_ = [("cos_parallax_max", ctypes.c_double), ("chi2", ctypes.c_double),
+                ("ratio_factor", ctypes.c_double)]
+
+
 class tm_batch_inputs(ctypes.Structure):
     _fields_ = [("masks", c_p), ("mask_bytes", c_sz), ("mps", tm_mappoint_view),
-                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p)]
+                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p), ("tri", c_p)]
 
 
 class tm_batch_result(ctypes.Structure):
@@ -84,7 +89,8 @@ class tm_batch_result(ctypes.Structure):
                 ("pair_offsets", c_p), ("fuse", c_p), ("fuse_cap", c_sz), ("n_fuse", c_sz),
                 ("fuse_offsets", c_p), ("n_comparisons_search", c_u64),
                 ("n_comparisons_fuse", c_u64), ("fwd", c_p), ("fwd_cap", c_sz), ("n_fwd", c_sz),
-                ("fwd_offsets", c_p), ("n_comparisons_fwd", c_u64)]
+                ("fwd_offsets", c_p), ("n_comparisons_fwd", c_u64), ("points", c_p),
+                ("point_ok", c_p)]
 
 
 class tm_server_config(ctypes.Structure):
@@ -109,6 +115,7 @@ SIGNATURES = {
     "tm_last_error": (ctypes.c_char_p, []),
     "tm_search_params_default": (None, [P(tm_search_params)]),
     "tm_fuse_params_default": (None, [P(tm_fuse_params)]),
+    "tm_triangulation_params_default": (None, [P(tm_triangulation_params)]),
     "tm_ctx_create": (c_i32, [c_i32, P(tm_camera), c_i32, c_sz, P(c_p)]),
     "tm_ctx_destroy": (c_i32, [c_p]),
     "tm_store_get_stats": (c_i32, [c_p, P(tm_store_stats)]),

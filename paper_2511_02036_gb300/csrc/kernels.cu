@@ -1464,6 +1464,150 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     }
 }
 
+// ---------------------------------------------------------------- triangulation (Map Point Creation)
+//
+// One CTA per pair, a thread per match of the pair's compacted list: parallax of the two
+// viewing rays, linear least-squares triangulation (3x3 normal equations, Cramer's rule),
+// depth and reprojection error in both views, scale consistency (Sec. III's constraints).
+// Float64 in a fixed order (products, then sums left to right), the point rounded to float32.
+
+struct TriView {
+    double R[9], t[3], O[3];
+};
+
+__device__ __forceinline__ double det3(const double *m) {
+    const double a = dmul(m[0], dsub(dmul(m[4], m[8]), dmul(m[5], m[7])));
+    const double b = dmul(m[1], dsub(dmul(m[3], m[8]), dmul(m[5], m[6])));
+    const double c = dmul(m[2], dsub(dmul(m[3], m[7]), dmul(m[4], m[6])));
+    return dadd(dsub(a, b), c);
+}
+
+// depth and reprojection test of X in one view
+__device__ __forceinline__ bool tri_view_ok(const CamConst &cam, const TriView &v, const double *X, double u,
+                                            double vv, double thr) {
+    double c[3];
+    for (int r = 0; r < 3; ++r) {
+        double s = dmul(v.R[r * 3 + 0], X[0]);
+        s = dadd(s, dmul(v.R[r * 3 + 1], X[1]));
+        s = dadd(s, dmul(v.R[r * 3 + 2], X[2]));
+        c[r] = dadd(s, v.t[r]);
+    }
+    if (!(c[2] > 0.0)) return false;
+    const double eu = dsub(dadd(dmul(cam.fx, __ddiv_rn(c[0], c[2])), cam.cx), u);
+    const double ev = dsub(dadd(dmul(cam.fy, __ddiv_rn(c[1], c[2])), cam.cy), vv);
+    return dadd(dmul(eu, eu), dmul(ev, ev)) <= thr;
+}
+
+__global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
+    __shared__ TriView V[2];
+    __shared__ double sig2[kLevels], scl[kLevels];
+    const uint32_t i = blockIdx.x;  // search item, logical order
+    const uint32_t o0 = A.offsets[i], o1 = A.offsets[i + 1];
+    if (o0 == o1) return;
+    const WorkItem w = A.items[i];
+    const KfView Q = KfView::at(w.q, A.L), T = KfView::at(w.t, A.L);
+    const int tid = threadIdx.x;
+    if (tid < 2) {
+        const double *P = tid == 0 ? Q.hdr->Tcw : T.hdr->Tcw;
+        TriView &v = V[tid];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) v.R[r * 3 + c] = P[r * 4 + c];
+            v.t[r] = P[r * 4 + 3];
+        }
+        for (int k = 0; k < 3; ++k) {
+            double s = dmul(v.R[0 * 3 + k], v.t[0]);
+            s = dadd(s, dmul(v.R[1 * 3 + k], v.t[1]));
+            s = dadd(s, dmul(v.R[2 * 3 + k], v.t[2]));
+            v.O[k] = -s;
+        }
+    }
+    if (tid < kLevels) {
+        const float sc = level_scale(tid);
+        scl[tid] = (double)sc;
+        sig2[tid] = (double)fmul(sc, sc);
+    }
+    __syncthreads();
+    const CamConst &cam = A.cam;
+    for (uint32_t k = o0 + (uint32_t)tid; k < o1; k += blockDim.x) {
+        const Out3 m = A.dense[k];
+        const int pq = Q.pos[m.a], pt = T.pos[m.b];  // (q_idx, t_idx, dist) in caller order
+        const float2 xq = Q.xy[pq], xt = T.xy[pt];
+        const int lev[2] = {Q.level[pq], T.level[pt]};
+        const double u[2] = {(double)xq.x, (double)xt.x}, vv[2] = {(double)xq.y, (double)xt.y};
+        double xn[2], yn[2], ray[2][3], rn[2];
+        for (int s = 0; s < 2; ++s) {
+            xn[s] = __ddiv_rn(dsub(u[s], cam.cx), cam.fx);
+            yn[s] = __ddiv_rn(dsub(vv[s], cam.cy), cam.fy);
+            for (int c = 0; c < 3; ++c) {
+                double r = dmul(V[s].R[0 * 3 + c], xn[s]);
+                r = dadd(r, dmul(V[s].R[1 * 3 + c], yn[s]));
+                ray[s][c] = dadd(r, V[s].R[2 * 3 + c]);
+            }
+            rn[s] = __dsqrt_rn(dadd(dadd(dmul(ray[s][0], ray[s][0]), dmul(ray[s][1], ray[s][1])),
+                                    dmul(ray[s][2], ray[s][2])));
+        }
+        float3 out = make_float3(0.0f, 0.0f, 0.0f);
+        uint8_t ok = 0;
+        const double dotr = dadd(dadd(dmul(ray[0][0], ray[1][0]), dmul(ray[0][1], ray[1][1])), dmul(ray[0][2], ray[1][2]));
+        const double cosp = __ddiv_rn(dotr, dmul(rn[0], rn[1]));
+        if (cosp > 0.0 && cosp < A.tri_cos_max) {
+            double Am[4][4];
+            for (int s = 0; s < 2; ++s)
+                for (int c = 0; c < 4; ++c) {
+                    const double p3 = c < 3 ? V[s].R[2 * 3 + c] : V[s].t[2];
+                    const double p1 = c < 3 ? V[s].R[0 * 3 + c] : V[s].t[0];
+                    const double p2 = c < 3 ? V[s].R[1 * 3 + c] : V[s].t[1];
+                    Am[2 * s][c] = dsub(dmul(xn[s], p3), p1);
+                    Am[2 * s + 1][c] = dsub(dmul(yn[s], p3), p2);
+                }
+            double N[9], g[3];
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) {
+                    double sm = dmul(Am[0][r], Am[0][c]);
+                    for (int q = 1; q < 4; ++q) sm = dadd(sm, dmul(Am[q][r], Am[q][c]));
+                    N[r * 3 + c] = sm;
+                }
+                double sm = dmul(Am[0][r], -Am[0][3]);
+                for (int q = 1; q < 4; ++q) sm = dadd(sm, dmul(Am[q][r], -Am[q][3]));
+                g[r] = sm;
+            }
+            const double det = det3(N);
+            if (det != 0.0) {
+                double X[3];
+                for (int c = 0; c < 3; ++c) {
+                    double M[9];
+                    for (int q = 0; q < 9; ++q) M[q] = N[q];
+                    for (int r = 0; r < 3; ++r) M[r * 3 + c] = g[r];
+                    X[c] = __ddiv_rn(det3(M), det);
+                }
+                bool good = tri_view_ok(cam, V[0], X, u[0], vv[0], dmul(A.tri_chi2, sig2[lev[0]])) &&
+                            tri_view_ok(cam, V[1], X, u[1], vv[1], dmul(A.tri_chi2, sig2[lev[1]]));
+                if (good) {
+                    double d[2];
+                    for (int s = 0; s < 2; ++s) {
+                        const double dx = dsub(X[0], V[s].O[0]), dy = dsub(X[1], V[s].O[1]), dz = dsub(X[2], V[s].O[2]);
+                        d[s] = __dsqrt_rn(dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)));
+                    }
+                    good = d[0] != 0.0 && d[1] != 0.0;
+                    if (good) {
+                        const double ratio_dist = __ddiv_rn(d[1], d[0]);
+                        const double ratio_octave = __ddiv_rn(scl[lev[0]], scl[lev[1]]);
+                        good = !(dmul(ratio_dist, A.tri_ratio) < ratio_octave || ratio_dist > dmul(ratio_octave, A.tri_ratio));
+                    }
+                }
+                if (good) {
+                    out = make_float3(__double2float_rn(X[0]), __double2float_rn(X[1]), __double2float_rn(X[2]));
+                    ok = 1;
+                }
+            }
+        }
+        A.points[3 * (size_t)k] = out.x;
+        A.points[3 * (size_t)k + 1] = out.y;
+        A.points[3 * (size_t)k + 2] = out.z;
+        A.point_ok[k] = ok;
+    }
+}
+
 // Per-item counts -> offsets, and the per-item regions gathered into the dense output.  Every
 // CTA scans the counts itself (a few thousand words, read from L2), segment by segment, so
 // that no CTA waits for another; CTA 0 publishes the offsets, the comparison totals (search,
@@ -1792,6 +1936,12 @@ cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio) {
     cudaError_t e = cudaFuncSetAttribute(fuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return launch_prio(fuse_kernel, dim3(blocks), dim3(kFuseChunk), smem, s, prio, a);
+}
+
+cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s) {
+    if (!a.triangulate || a.n_search == 0) return cudaSuccess;
+    tri_kernel<<<a.n_search, 128, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {

@@ -28,6 +28,9 @@ size_t dense_smem_bytes();
 cudaError_t launch_dense(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
+// Triangulation of every match of the batch (a.triangulate; after the copy kernel: reads the
+// offsets and the dense matches).
+cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s);
 
 // Plain per-pair form: every stage of one pair is its own launch, with global scratch.
 struct PairScratch {

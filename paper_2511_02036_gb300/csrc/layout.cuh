@@ -265,6 +265,10 @@ struct BatchArgs {
     long long wait_limit;         // bound of a bulk-copy wait, SM clock cycles
     uint32_t starve;              // test hook: after the copies, await a barrier nothing arrives
                                   // at, so that the bounded wait runs out
+    int32_t triangulate;          // 1: tri_kernel over the match lists
+    double tri_cos_max, tri_chi2, tri_ratio;
+    float *points;                // [matches][3] triangulated points (triangulate)
+    uint8_t *point_ok;            // [matches] accepted as new map points
     uint2 *dres;                  // [sum of nq over search items] per-query (best key, second) of
                                   // dense queries, at WorkItem::c + position
     uint32_t dsplit;              // dense kernel CTAs per search item

@@ -113,6 +113,13 @@ extern "C" void tm_search_params_default(tm_search_params *p) {
     p->rot_mode = 0;
 }
 
+extern "C" void tm_triangulation_params_default(tm_triangulation_params *p) {
+    if (!p) return;
+    p->cos_parallax_max = 0.9998;
+    p->chi2 = 5.991;
+    p->ratio_factor = 1.5 * 1.2;
+}
+
 extern "C" void tm_fuse_params_default(tm_fuse_params *p) {
     if (!p) return;
     p->chi2 = 5.99f;
@@ -458,7 +465,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &points, &point_ok})
         b->release();
     h_stage.release();
     h_out.release();
@@ -538,6 +545,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if (n_steps < 0 || (n_steps > 0 && !steps)) return fail(TM_ERR_INVALID_ARG, "bad steps");
     const size_t mask_bytes = in ? in->mask_bytes : 0;
     const tm_mappoint_view mps = in ? in->mps : tm_mappoint_view{};
+    const tm_triangulation_params *tri = in ? in->tri : nullptr;
+    if (tri && !(tri->cos_parallax_max > 0.0 && tri->cos_parallax_max <= 1.0 && tri->chi2 >= 0.0 &&
+                 tri->ratio_factor >= 1.0))
+        return fail(TM_ERR_INVALID_ARG, "bad triangulation parameters");
     if (mask_bytes && !in->masks) return fail(TM_ERR_INVALID_ARG, "masks is null");
     if (mps.n < 0) return fail(TM_ERR_INVALID_ARG, "negative map point count");
     if (mps.n > 0 && (!mps.pos || !mps.normal || !mps.desc || !mps.min_dist || !mps.max_dist))
@@ -720,6 +731,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     }
     B.step_pair_begin[n_steps] = B.n_pairs;
     B.n_search_items = (uint32_t)items.size();
+    B.search_pad = pad;
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
         B.step_fuse_item[k] = (int)items.size();
@@ -813,7 +825,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (sp.dense_min > 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))))
+        (sp.dense_min > 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))) ||
+        (tri && ((e = B.points.reserve(std::max<size_t>(1, B.search_pad) * 12)) ||
+                 (e = B.point_ok.reserve(std::max<size_t>(1, B.search_pad))))))
         return cuda_fail(e, "batch buffers");
     if (B.pointers() != before && (B.graph || B.graph_timed)) {
         if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -889,6 +903,12 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.starve = c->starve;
     A.sn = B.smem_n;
     A.dres = static_cast<uint2 *>(B.dres.p);
+    A.triangulate = tri ? 1 : 0;
+    A.tri_cos_max = tri ? tri->cos_parallax_max : 0.0;
+    A.tri_chi2 = tri ? tri->chi2 : 0.0;
+    A.tri_ratio = tri ? tri->ratio_factor : 0.0;
+    A.points = static_cast<float *>(B.points.p);
+    A.point_ok = static_cast<uint8_t *>(B.point_ok.p);
     // dense kernel: at most one wave of three CTAs per SM over the pairs (a CTA takes every
     // dsplit-th dense run of its pair)
     A.dsplit = (uint32_t)std::max(1, std::min(64, 3 * c->num_sms / (int)nsi));
@@ -900,7 +920,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p};
+            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, points.p,
+            point_ok.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -972,6 +993,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     // copy: about one warp per item (32 per CTA), at most one CTA per SM
     if ((e = launch_copy(B.args, (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_items + 31) / 32, c->num_sms)), s)))
         return cuda_fail(e, "copy kernel");
+    if ((e = launch_tri(B.args, s))) return cuda_fail(e, "triangulation kernel");
     if ((e = mark(4, s))) return cuda_fail(e, "event");
     return TM_OK;
 }
@@ -1032,6 +1054,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
     }
     if ((e = cudaMemcpyAsync(offs + B.n_items, scr.running, 4, cudaMemcpyDeviceToDevice, s)))
         return cuda_fail(e, "plain total");
+    if ((e = launch_tri(B.args, s))) return cuda_fail(e, "triangulation kernel");
     return TM_OK;
 }
 
@@ -1061,6 +1084,8 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
     r->n_comparisons_search = hc[0];
     r->n_comparisons_fuse = hc[1];
     r->n_comparisons_fwd = hc[2];
+    if (B.args.triangulate && (!r->points || !r->point_ok))
+        return fail(TM_ERR_INVALID_ARG, "triangulation needs points and point_ok result buffers");
     if (search_total > r->match_cap || nf > r->fuse_cap || (nw && (!r->fwd || nw > r->fwd_cap)))
         return fail(TM_ERR_CAPACITY, "result buffers too small: %u matches (cap %zu), %zu fusion candidates (cap %zu), "
                     "%zu forward-fusion candidates (cap %zu)", search_total, r->match_cap, nf, r->fuse_cap, nw,
@@ -1088,6 +1113,10 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
         return cuda_fail(e, "fusion download");
     if (nw && (e = cudaMemcpyAsync(r->fwd, d + bwd_end, nw * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "forward fusion download");
+    if (B.args.triangulate && search_total &&
+        ((e = cudaMemcpyAsync(r->points, B.points.p, (size_t)search_total * 12, cudaMemcpyDefault, s)) ||
+         (e = cudaMemcpyAsync(r->point_ok, B.point_ok.p, search_total, cudaMemcpyDefault, s))))
+        return cuda_fail(e, "points download");
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(e, "results");
     return TM_OK;
 }
@@ -1427,11 +1456,15 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         // search (when there are pairs), fuse (when there are map points), copy, ingest (when
         // keyframes enter with the batch)
         P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
-                             1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0);
+                             1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0) +
+                             (P->B.n_search_items && P->B.args.triangulate ? 1 : 0);
     } else {
-        P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0);
+        P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0) +
+                             (P->B.n_search_items && P->B.args.triangulate ? 1 : 0);
         for (int k = 0; k < P->B.n_steps; ++k)
             if (P->B.step_fuse_item[k] != P->B.step_fuse_item[k + 1]) P->kernels_per_run += 2;
+        for (int p = 0; P->B.any_fwd && p < P->B.n_pairs; ++p)
+            if (P->B.pair_fwd_item[p] != P->B.pair_fwd_item[p + 1]) P->kernels_per_run += 2;
         P->B.lanes = spd.lanes_per_query ? spd.lanes_per_query : 1;
     }
     if (st) {

@@ -49,7 +49,7 @@ struct IngestStage {
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres;
+        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, points, point_ok;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -60,6 +60,7 @@ struct BatchBuf {
     std::vector<int> step_pair_begin, step_fuse_item, slots;
     std::vector<int> pair_fwd_item;  // [pairs + 1] first forward-fusion item of each pair
     uint32_t n_bwd_items = 0;        // fusion items into the new keyframes
+    uint32_t search_pad = 0;         // padded output entries of the search items
     bool any_fwd = false;            // some step asks for forward fusion
     uint32_t n_items = 0, n_search_items = 0, total_pad = 0;
     uint32_t res_total = 0, t_total = 0, fsn = 16;

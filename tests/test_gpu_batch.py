@@ -396,3 +396,50 @@ def test_forward_fusion_plan_and_mixed_steps(tm):
                 e = efw[p] if k not in (1, 3) else np.zeros((0, 3), np.int32)
                 np.testing.assert_array_equal(r.fwds[p], e)
                 p += 1
+
+
+def check_points(w, res, exp_pairs, params=None):
+    p = 0
+    for st in w["steps"]:
+        for f in st["nbrs"]:
+            xyz, ok = O.triangulate(w["cam"], w["frames"][st["q"]], w["frames"][f], exp_pairs[p], params)
+            a, b = res.pair_offsets[p], res.pair_offsets[p + 1]
+            np.testing.assert_array_equal(res.points[a:b], xyz)
+            np.testing.assert_array_equal(res.point_ok[a:b], ok)
+            p += 1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_triangulation_batch(tm, small_batch, mode):
+    """Triangulation and acceptance of every match on the GPU (float64, fixed order) equals the
+    oracle's bit for bit: points (float32) and accepted flags, batched and per-pair forms."""
+    w = small_batch
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        res = ctx.batch_run(steps_of(w), sp=tm.SearchParams(mode=mode), tri=tm.TriParams())
+        assert_same(res, exp)
+        assert res.point_ok.sum() > 100
+        check_points(w, res, exp[0])
+        tight = tm.TriParams(cos_parallax_max=0.999, chi2=2.0)
+        res2 = ctx.batch_run(steps_of(w), sp=tm.SearchParams(mode=mode), tri=tight)
+        check_points(w, res2, exp[0], O.TriParams(0.999, 2.0))
+        assert res2.point_ok.sum() < res.point_ok.sum()
+
+
+def test_triangulation_plan_new_keyframes(tm, small_batch):
+    """In a plan whose new keyframes enter the store with the batch (their slots are written by
+    the batch's own ingest before the triangulation reads them)."""
+    w = small_batch
+    exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
+        with ctx.plan(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids]), tri=tm.TriParams()) as plan:
+            assert plan.info()["kernels_per_run"] == 5  # ingest, search, fuse, copy, triangulation
+            for _ in range(2):
+                plan.run()
+                r = plan.results()
+                assert_same(r, exp)
+                check_points(w, r, exp[0])

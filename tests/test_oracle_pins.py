@@ -471,3 +471,42 @@ def test_epipole_rejection_invariants():
                 assert dx * dx + dy * dy >= np.float32(px * px) * np.float32(scale[T["level"][t]])
         m, _ = O.search_pair(cam, Q, T, st["q_free"], ft, O.SearchParams(epipole_px=1e5))
         assert len(m) == 0
+
+
+def test_triangulation_recovers_exact_points():
+    """Noise-free planted correspondences: every planted match is accepted and its
+    triangulated point is the planted world point (float32 pixels, float64 solve)."""
+    p = W.make_pair_cfg0(5, noise_px=0.0)
+    m, _ = O.search_pair(p["cam"], p["Q"], p["T"])
+    xyz, ok = O.triangulate(p["cam"], p["Q"], p["T"], m)
+    wq, wt = p["Q"]["wp"], p["T"]["wp"]
+    planted = np.array([wq[a] >= 0 and wq[a] == wt[b] for a, b, _ in m])
+    assert planted.sum() > 80
+    assert ok[planted].all()
+    err = np.linalg.norm(xyz[planted].astype(np.float64) - p["points"][wq[m[planted, 0]]], axis=1)
+    depth = p["points"][wq[m[planted, 0]], 2]
+    assert (err < 1e-3 * depth).all(), err.max()
+    assert not xyz[ok == 0].any()
+
+
+def test_triangulation_rejects_pure_rotation_and_scale_jumps():
+    """No baseline (pure rotation): every ray pair is parallel, nothing is accepted.  A target
+    keypoint moved four pyramid levels up breaks the scale consistency (1.2^4 > 1.8); one level
+    keeps it."""
+    p = W.make_pair_cfg0(6, noise_px=0.0, baseline=0.0)
+    m, _ = O.search_pair(p["cam"], p["Q"], p["T"], params=O.SearchParams(epipolar=False))
+    assert len(m) > 50
+    _, ok = O.triangulate(p["cam"], p["Q"], p["T"], m)
+    assert ok.sum() == 0
+    p = W.make_pair_cfg0(7, noise_px=0.0)
+    m, _ = O.search_pair(p["cam"], p["Q"], p["T"])
+    _, ok0 = O.triangulate(p["cam"], p["Q"], p["T"], m)
+    low = [k for k, (a, b, _) in enumerate(m) if ok0[k] and p["T"]["level"][b] <= 3]
+    assert len(low) > 20
+    for dl, expect in ((4, 0), (1, 1)):
+        T = dict(p["T"])
+        T["level"] = p["T"]["level"].copy()
+        for k in low:
+            T["level"][m[k, 1]] += dl
+        _, ok = O.triangulate(p["cam"], p["Q"], T, m)
+        assert (ok[low] == expect).all(), (dl, ok[low])
