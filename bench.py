@@ -550,14 +550,17 @@ def run_forward(tm, stream, flush, device, reps, seed):
     new_ids = [s["q"] for s in w["steps"]]
     old_ids = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
     out = {"workload": "cfg2 + forward fusion: the same 64 steps; per step its new keyframe's map points "
-                       "(mapped and just-triangulated points it observes) into each of its neighbours"}
+                       "(mapped and just-triangulated points it observes) into each of its neighbours; "
+                       "and the same with every match triangulated and checked on the GPU"}
     with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
         ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
-        for name, fwd in (("with_forward", True), ("without_forward", False)):
+        for name, fwd, tri in (("with_forward", True, False), ("without_forward", False, False),
+                               ("with_forward_and_triangulation", True, True)):
             steps = [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
                           mps=s.get("mps"), **({"fwd_mps": s["fwd_mps"], "fwd_skip": s["fwd_skip"]} if fwd else {}))
                      for s in w["steps"]]
-            with ctx.plan(steps, new=(new_ids, [w["frames"][i] for i in new_ids])) as plan:
+            with ctx.plan(steps, new=(new_ids, [w["frames"][i] for i in new_ids]),
+                          tri=tm.TriParams() if tri else None) as plan:
                 for _ in range(3):
                     plan.run(stream)
                 torch.cuda.synchronize()
@@ -575,6 +578,9 @@ def run_forward(tm, stream, flush, device, reps, seed):
                              "kernels_per_run": plan.info()["kernels_per_run"],
                              "forward_candidates": int(len(res.fwd)), "forward_comparisons": int(res.n_comparisons_fwd),
                              "forward_map_points": int(sum(s["fwd_mps"]["n"] * len(s["nbrs"]) for s in w["steps"])) if fwd else 0}
+                if tri:
+                    out[name]["triangulated_matches"] = int(len(res.matches))
+                    out[name]["accepted_new_points"] = int(res.point_ok.sum())
             ctx.remove_keyframes(new_ids)  # the plan's new keyframes stay stored after it
     return out
 
