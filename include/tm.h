@@ -298,7 +298,8 @@ tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t 
  * CUDA events recorded inside its graph (all zero otherwise).  The search kernel (one CTA per
  * pair: all of Sec. IV-C) runs beside the store branch (ingest -> fusion): ms[0] search kernel
  * (between events recorded right before and after it on its stream), ms[1] ingest, ms[2]
- * fusion kernel, ms[3] offsets + copy after both branches, ms[4] the dense-block kernel that
+ * fusion kernel, ms[3] offsets + copy after both branches (and the triangulation kernel
+ * when the batch triangulates), ms[4] the dense-block kernel that
  * precedes the search kernel (dense_min > 0; else 0).  Waits for the run to finish. */
 #define TM_PLAN_STAGES 5
 tm_status tm_plan_stage_times(tm_plan *plan, float ms[TM_PLAN_STAGES]);
