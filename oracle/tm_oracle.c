@@ -344,52 +344,45 @@ int64_t orc_fuse(const orc_camera *cam, const orc_keyframe *T, int32_t n, const 
  * Map Point Creation after the search (Sec. III): each match is triangulated and kept as a
  * new map point only if the two views see it with sufficient parallax, in front of both
  * cameras, with a low reprojection error in each view, and at consistent scales.  The paper
- * gives the constraints, not their formulas; the readings (all float64, sums left to right):
+ * gives the constraints, not their formulas; the readings, all float32 (a pose's R and t
+ * rounded from float64, its centre O = -R^T t formed in float64 and rounded; dot products
+ * (x*x' + y*y') + z*z'):
  *   normalized coordinates  xn = (u - cx) / fx, yn = (v - cy) / fy;
  *   rays in the world frame r = R^T (xn, yn, 1); parallax cos = (r1.r2) / (|r1| |r2|),
  *     kept iff 0 < cos < cos_parallax_max;
- *   linear triangulation: with P = [R | t] each view gives the rows xn P_3 - P_1 and
- *     yn P_3 - P_2 of A (4 x 4); X solves the least-squares problem A_{:,0:3} X = -A_{:,3}
- *     through its normal equations (A3^T A3) X = A3^T b, by Cramer's rule (det 0: rejected);
+ *   the point: the midpoint of the common perpendicular of the rays O1 + s r1, O2 + t r2:
+ *     w = O1 - O2, a = r1.r1, b = r1.r2, c = r2.r2, d = r1.w, e = r2.w, den = a c - b b
+ *     (rejected if not > 0), s = (b e - c d) / den, t = (a e - b d) / den,
+ *     X = ((O1 + s r1) + (O2 + t r2)) * 0.5;
  *   depth z = R_3 X + t_3 > 0 in both views;
  *   reprojection (fx x/z + cx - u)^2 + (fy y/z + cy - v)^2 <= chi2 * sigma^2(level), each view;
- *   scale: d_i = |X - O_i| (O = -R^T t), ratio_dist = d2 / d1, ratio_octave = s(l1) / s(l2);
+ *   scale: d_i = |X - O_i|, ratio_dist = d2 / d1, ratio_octave = s(l1) / s(l2);
  *     rejected if ratio_dist * f < ratio_octave or ratio_dist > ratio_octave * f. */
-static double orc_det3(const double m[9]) {
-    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
-           m[2] * (m[3] * m[7] - m[4] * m[6]);
-}
-
-/* One view: R (row-major 3x3), t, its camera centre O, and the pixel's normalized
- * coordinates and world ray. */
-typedef struct { double R[9], t[3], O[3]; } orc_view;
+typedef struct { float R[9], t[3], O[3]; } orc_view;
 
 static void orc_view_of(const double Tcw[12], orc_view *v) {
     for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) v->R[r * 3 + c] = Tcw[r * 4 + c];
-        v->t[r] = Tcw[r * 4 + 3];
+        for (int c = 0; c < 3; ++c) v->R[r * 3 + c] = (float)Tcw[r * 4 + c];
+        v->t[r] = (float)Tcw[r * 4 + 3];
     }
     for (int k = 0; k < 3; ++k) {
-        double s = v->R[0 * 3 + k] * v->t[0];
-        s = s + v->R[1 * 3 + k] * v->t[1];
-        s = s + v->R[2 * 3 + k] * v->t[2];
-        v->O[k] = -s;
+        double s = Tcw[0 * 4 + k] * Tcw[0 * 4 + 3];
+        s = s + Tcw[1 * 4 + k] * Tcw[1 * 4 + 3];
+        s = s + Tcw[2 * 4 + k] * Tcw[2 * 4 + 3];
+        v->O[k] = (float)(-s);
     }
 }
 
+static float orc_dot3(const float *a, const float *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
 /* depth and reprojection test of X in one view */
-static int orc_view_ok(const orc_camera *cam, const orc_view *v, const double X[3], double u,
-                       double vv, double thr) {
-    double c[3];
-    for (int r = 0; r < 3; ++r) {
-        double s = v->R[r * 3 + 0] * X[0];
-        s = s + v->R[r * 3 + 1] * X[1];
-        s = s + v->R[r * 3 + 2] * X[2];
-        c[r] = s + v->t[r];
-    }
-    if (!(c[2] > 0.0)) return 0;
-    const double eu = (cam->fx * (c[0] / c[2]) + cam->cx) - u;
-    const double ev = (cam->fy * (c[1] / c[2]) + cam->cy) - vv;
+static int orc_view_ok(const orc_camera *cam, const orc_view *v, const float X[3], float u, float vv,
+                       float thr) {
+    float c[3];
+    for (int r = 0; r < 3; ++r) c[r] = ((v->R[r * 3 + 0] * X[0] + v->R[r * 3 + 1] * X[1]) + v->R[r * 3 + 2] * X[2]) + v->t[r];
+    if (!(c[2] > 0.0f)) return 0;
+    const float eu = ((float)cam->fx * (c[0] / c[2]) + (float)cam->cx) - u;
+    const float ev = ((float)cam->fy * (c[1] / c[2]) + (float)cam->cy) - vv;
     return eu * eu + ev * ev <= thr;
 }
 
@@ -401,70 +394,47 @@ void orc_triangulate(const orc_camera *cam, const orc_keyframe *Q, const orc_key
     orc_view V[2];
     orc_view_of(Q->Tcw, &V[0]);
     orc_view_of(T->Tcw, &V[1]);
+    const float fx = (float)cam->fx, fy = (float)cam->fy, cx = (float)cam->cx, cy = (float)cam->cy;
+    const float cos_max = (float)p->cos_parallax_max, chi2 = (float)p->chi2, f = (float)p->ratio_factor;
     for (int64_t k = 0; k < n; ++k) {
         const orc_keyframe *kf[2] = {Q, T};
         const int idx[2] = {q_idx[k], t_idx[k]};
-        double u[2], vv[2], xn[2], yn[2], ray[2][3], rn[2];
+        float u[2], vv[2], ray[2][3];
         int lev[2];
         for (int s = 0; s < 2; ++s) {
             u[s] = kf[s]->xy[2 * idx[s]];
             vv[s] = kf[s]->xy[2 * idx[s] + 1];
             lev[s] = kf[s]->level[idx[s]];
-            xn[s] = (u[s] - cam->cx) / cam->fx;
-            yn[s] = (vv[s] - cam->cy) / cam->fy;
-            for (int c = 0; c < 3; ++c) {
-                double r = V[s].R[0 * 3 + c] * xn[s];
-                r = r + V[s].R[1 * 3 + c] * yn[s];
-                ray[s][c] = r + V[s].R[2 * 3 + c];
-            }
-            rn[s] = sqrt(ray[s][0] * ray[s][0] + ray[s][1] * ray[s][1] + ray[s][2] * ray[s][2]);
+            const float xn = (u[s] - cx) / fx, yn = (vv[s] - cy) / fy;
+            for (int c = 0; c < 3; ++c)
+                ray[s][c] = (V[s].R[0 * 3 + c] * xn + V[s].R[1 * 3 + c] * yn) + V[s].R[2 * 3 + c];
         }
         xyz[3 * k] = xyz[3 * k + 1] = xyz[3 * k + 2] = 0.0f;
         ok[k] = 0;
-        const double cosp = (ray[0][0] * ray[1][0] + ray[0][1] * ray[1][1] + ray[0][2] * ray[1][2]) / (rn[0] * rn[1]);
-        if (!(cosp > 0.0 && cosp < p->cos_parallax_max)) continue;
-        /* rows xn P_3 - P_1, yn P_3 - P_2 of each view, P = [R | t] */
-        double A[4][4];
-        for (int s = 0; s < 2; ++s)
-            for (int c = 0; c < 4; ++c) {
-                const double p3 = c < 3 ? V[s].R[2 * 3 + c] : V[s].t[2];
-                const double p1 = c < 3 ? V[s].R[0 * 3 + c] : V[s].t[0];
-                const double p2 = c < 3 ? V[s].R[1 * 3 + c] : V[s].t[1];
-                A[2 * s][c] = xn[s] * p3 - p1;
-                A[2 * s + 1][c] = yn[s] * p3 - p2;
-            }
-        double N[9], g[3];
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) {
-                double s = A[0][r] * A[0][c];
-                for (int q = 1; q < 4; ++q) s = s + A[q][r] * A[q][c];
-                N[r * 3 + c] = s;
-            }
-            double s = A[0][r] * -A[0][3];
-            for (int q = 1; q < 4; ++q) s = s + A[q][r] * -A[q][3];
-            g[r] = s;
-        }
-        const double det = orc_det3(N);
-        if (det == 0.0) continue;
-        double X[3];
-        for (int c = 0; c < 3; ++c) {
-            double M[9];
-            for (int q = 0; q < 9; ++q) M[q] = N[q];
-            for (int r = 0; r < 3; ++r) M[r * 3 + c] = g[r];
-            X[c] = orc_det3(M) / det;
-        }
-        if (!orc_view_ok(cam, &V[0], X, u[0], vv[0], p->chi2 * (double)sigma2[lev[0]])) continue;
-        if (!orc_view_ok(cam, &V[1], X, u[1], vv[1], p->chi2 * (double)sigma2[lev[1]])) continue;
-        double d[2];
+        const float a = orc_dot3(ray[0], ray[0]), b = orc_dot3(ray[0], ray[1]), c2 = orc_dot3(ray[1], ray[1]);
+        const float cosp = b / (sqrtf(a) * sqrtf(c2));
+        if (!(cosp > 0.0f && cosp < cos_max)) continue;
+        float w[3];
+        for (int q = 0; q < 3; ++q) w[q] = V[0].O[q] - V[1].O[q];
+        const float d = orc_dot3(ray[0], w), e = orc_dot3(ray[1], w);
+        const float den = a * c2 - b * b;
+        if (!(den > 0.0f)) continue;
+        const float s1 = (b * e - c2 * d) / den, s2 = (a * e - b * d) / den;
+        float X[3];
+        for (int q = 0; q < 3; ++q) X[q] = ((V[0].O[q] + s1 * ray[0][q]) + (V[1].O[q] + s2 * ray[1][q])) * 0.5f;
+        if (!orc_view_ok(cam, &V[0], X, u[0], vv[0], chi2 * sigma2[lev[0]])) continue;
+        if (!orc_view_ok(cam, &V[1], X, u[1], vv[1], chi2 * sigma2[lev[1]])) continue;
+        float dist[2];
         for (int s = 0; s < 2; ++s) {
-            const double dx = X[0] - V[s].O[0], dy = X[1] - V[s].O[1], dz = X[2] - V[s].O[2];
-            d[s] = sqrt(dx * dx + dy * dy + dz * dz);
+            float dv[3];
+            for (int q = 0; q < 3; ++q) dv[q] = X[q] - V[s].O[q];
+            dist[s] = sqrtf(orc_dot3(dv, dv));
         }
-        if (d[0] == 0.0 || d[1] == 0.0) continue;
-        const double ratio_dist = d[1] / d[0];
-        const double ratio_octave = (double)scale[lev[0]] / (double)scale[lev[1]];
-        if (ratio_dist * p->ratio_factor < ratio_octave || ratio_dist > ratio_octave * p->ratio_factor) continue;
-        for (int c = 0; c < 3; ++c) xyz[3 * k + c] = (float)X[c];
+        if (dist[0] == 0.0f || dist[1] == 0.0f) continue;
+        const float ratio_dist = dist[1] / dist[0];
+        const float ratio_octave = scale[lev[0]] / scale[lev[1]];
+        if (ratio_dist * f < ratio_octave || ratio_dist > ratio_octave * f) continue;
+        for (int q = 0; q < 3; ++q) xyz[3 * k + q] = X[q];
         ok[k] = 1;
     }
 }

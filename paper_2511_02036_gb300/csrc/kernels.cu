@@ -1467,40 +1467,36 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
 // ---------------------------------------------------------------- triangulation (Map Point Creation)
 //
 // One CTA per pair, a thread per match of the pair's compacted list: parallax of the two
-// viewing rays, linear least-squares triangulation (3x3 normal equations, Cramer's rule),
-// depth and reprojection error in both views, scale consistency (Sec. III's constraints).
-// Float64 in a fixed order (products, then sums left to right), the point rounded to float32.
+// viewing rays, the point as the midpoint of the rays' common perpendicular, depth and
+// reprojection error in both views, scale consistency (Sec. III's constraints).  Float32 in a
+// fixed order (dot products (x x' + y y') + z z'; this part's float64 rate is a small fraction
+// of its float32 rate); the pose's R, t rounded from float64, its centre O = -R^T t formed in
+// float64 and rounded.
 
 struct TriView {
-    double R[9], t[3], O[3];
+    float R[9], t[3], O[3];
 };
 
-__device__ __forceinline__ double det3(const double *m) {
-    const double a = dmul(m[0], dsub(dmul(m[4], m[8]), dmul(m[5], m[7])));
-    const double b = dmul(m[1], dsub(dmul(m[3], m[8]), dmul(m[5], m[6])));
-    const double c = dmul(m[2], dsub(dmul(m[3], m[7]), dmul(m[4], m[6])));
-    return dadd(dsub(a, b), c);
+__device__ __forceinline__ float dot3f(const float *a, const float *b) {
+    return fadd(fadd(fmul(a[0], b[0]), fmul(a[1], b[1])), fmul(a[2], b[2]));
 }
 
 // depth and reprojection test of X in one view
-__device__ __forceinline__ bool tri_view_ok(const CamConst &cam, const TriView &v, const double *X, double u,
-                                            double vv, double thr) {
-    double c[3];
-    for (int r = 0; r < 3; ++r) {
-        double s = dmul(v.R[r * 3 + 0], X[0]);
-        s = dadd(s, dmul(v.R[r * 3 + 1], X[1]));
-        s = dadd(s, dmul(v.R[r * 3 + 2], X[2]));
-        c[r] = dadd(s, v.t[r]);
-    }
-    if (!(c[2] > 0.0)) return false;
-    const double eu = dsub(dadd(dmul(cam.fx, __ddiv_rn(c[0], c[2])), cam.cx), u);
-    const double ev = dsub(dadd(dmul(cam.fy, __ddiv_rn(c[1], c[2])), cam.cy), vv);
-    return dadd(dmul(eu, eu), dmul(ev, ev)) <= thr;
+__device__ __forceinline__ bool tri_view_ok(const TriView &v, const float *X, float fx, float fy, float cx,
+                                            float cy, float u, float vv, float thr) {
+    float c[3];
+    for (int r = 0; r < 3; ++r)
+        c[r] = fadd(fadd(fadd(fmul(v.R[r * 3 + 0], X[0]), fmul(v.R[r * 3 + 1], X[1])), fmul(v.R[r * 3 + 2], X[2])),
+                    v.t[r]);
+    if (!(c[2] > 0.0f)) return false;
+    const float eu = fsub(fadd(fmul(fx, __fdiv_rn(c[0], c[2])), cx), u);
+    const float ev = fsub(fadd(fmul(fy, __fdiv_rn(c[1], c[2])), cy), vv);
+    return fadd(fmul(eu, eu), fmul(ev, ev)) <= thr;
 }
 
 __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
     __shared__ TriView V[2];
-    __shared__ double sig2[kLevels], scl[kLevels];
+    __shared__ float sig2[kLevels], scl[kLevels];
     const uint32_t i = blockIdx.x;  // search item, logical order
     const uint32_t o0 = A.offsets[i], o1 = A.offsets[i + 1];
     if (o0 == o1) return;
@@ -1511,92 +1507,71 @@ __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
         const double *P = tid == 0 ? Q.hdr->Tcw : T.hdr->Tcw;
         TriView &v = V[tid];
         for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) v.R[r * 3 + c] = P[r * 4 + c];
-            v.t[r] = P[r * 4 + 3];
+            for (int c = 0; c < 3; ++c) v.R[r * 3 + c] = __double2float_rn(P[r * 4 + c]);
+            v.t[r] = __double2float_rn(P[r * 4 + 3]);
         }
         for (int k = 0; k < 3; ++k) {
-            double s = dmul(v.R[0 * 3 + k], v.t[0]);
-            s = dadd(s, dmul(v.R[1 * 3 + k], v.t[1]));
-            s = dadd(s, dmul(v.R[2 * 3 + k], v.t[2]));
-            v.O[k] = -s;
+            double s = dmul(P[0 * 4 + k], P[0 * 4 + 3]);
+            s = dadd(s, dmul(P[1 * 4 + k], P[1 * 4 + 3]));
+            s = dadd(s, dmul(P[2 * 4 + k], P[2 * 4 + 3]));
+            v.O[k] = __double2float_rn(-s);
         }
     }
     if (tid < kLevels) {
         const float sc = level_scale(tid);
-        scl[tid] = (double)sc;
-        sig2[tid] = (double)fmul(sc, sc);
+        scl[tid] = sc;
+        sig2[tid] = fmul(sc, sc);
     }
     __syncthreads();
-    const CamConst &cam = A.cam;
+    const float fx = __double2float_rn(A.cam.fx), fy = __double2float_rn(A.cam.fy);
+    const float cx = __double2float_rn(A.cam.cx), cy = __double2float_rn(A.cam.cy);
+    const float cos_max = __double2float_rn(A.tri_cos_max), chi2 = __double2float_rn(A.tri_chi2);
+    const float fr = __double2float_rn(A.tri_ratio);
     for (uint32_t k = o0 + (uint32_t)tid; k < o1; k += blockDim.x) {
         const Out3 m = A.dense[k];
         const int pq = Q.pos[m.a], pt = T.pos[m.b];  // (q_idx, t_idx, dist) in caller order
         const float2 xq = Q.xy[pq], xt = T.xy[pt];
         const int lev[2] = {Q.level[pq], T.level[pt]};
-        const double u[2] = {(double)xq.x, (double)xt.x}, vv[2] = {(double)xq.y, (double)xt.y};
-        double xn[2], yn[2], ray[2][3], rn[2];
+        const float u[2] = {xq.x, xt.x}, vv[2] = {xq.y, xt.y};
+        float ray[2][3];
         for (int s = 0; s < 2; ++s) {
-            xn[s] = __ddiv_rn(dsub(u[s], cam.cx), cam.fx);
-            yn[s] = __ddiv_rn(dsub(vv[s], cam.cy), cam.fy);
-            for (int c = 0; c < 3; ++c) {
-                double r = dmul(V[s].R[0 * 3 + c], xn[s]);
-                r = dadd(r, dmul(V[s].R[1 * 3 + c], yn[s]));
-                ray[s][c] = dadd(r, V[s].R[2 * 3 + c]);
-            }
-            rn[s] = __dsqrt_rn(dadd(dadd(dmul(ray[s][0], ray[s][0]), dmul(ray[s][1], ray[s][1])),
-                                    dmul(ray[s][2], ray[s][2])));
+            const float xn = __fdiv_rn(fsub(u[s], cx), fx), yn = __fdiv_rn(fsub(vv[s], cy), fy);
+            for (int c = 0; c < 3; ++c)
+                ray[s][c] = fadd(fadd(fmul(V[s].R[0 * 3 + c], xn), fmul(V[s].R[1 * 3 + c], yn)), V[s].R[2 * 3 + c]);
         }
         float3 out = make_float3(0.0f, 0.0f, 0.0f);
         uint8_t ok = 0;
-        const double dotr = dadd(dadd(dmul(ray[0][0], ray[1][0]), dmul(ray[0][1], ray[1][1])), dmul(ray[0][2], ray[1][2]));
-        const double cosp = __ddiv_rn(dotr, dmul(rn[0], rn[1]));
-        if (cosp > 0.0 && cosp < A.tri_cos_max) {
-            double Am[4][4];
-            for (int s = 0; s < 2; ++s)
-                for (int c = 0; c < 4; ++c) {
-                    const double p3 = c < 3 ? V[s].R[2 * 3 + c] : V[s].t[2];
-                    const double p1 = c < 3 ? V[s].R[0 * 3 + c] : V[s].t[0];
-                    const double p2 = c < 3 ? V[s].R[1 * 3 + c] : V[s].t[1];
-                    Am[2 * s][c] = dsub(dmul(xn[s], p3), p1);
-                    Am[2 * s + 1][c] = dsub(dmul(yn[s], p3), p2);
-                }
-            double N[9], g[3];
-            for (int r = 0; r < 3; ++r) {
-                for (int c = 0; c < 3; ++c) {
-                    double sm = dmul(Am[0][r], Am[0][c]);
-                    for (int q = 1; q < 4; ++q) sm = dadd(sm, dmul(Am[q][r], Am[q][c]));
-                    N[r * 3 + c] = sm;
-                }
-                double sm = dmul(Am[0][r], -Am[0][3]);
-                for (int q = 1; q < 4; ++q) sm = dadd(sm, dmul(Am[q][r], -Am[q][3]));
-                g[r] = sm;
-            }
-            const double det = det3(N);
-            if (det != 0.0) {
-                double X[3];
-                for (int c = 0; c < 3; ++c) {
-                    double M[9];
-                    for (int q = 0; q < 9; ++q) M[q] = N[q];
-                    for (int r = 0; r < 3; ++r) M[r * 3 + c] = g[r];
-                    X[c] = __ddiv_rn(det3(M), det);
-                }
-                bool good = tri_view_ok(cam, V[0], X, u[0], vv[0], dmul(A.tri_chi2, sig2[lev[0]])) &&
-                            tri_view_ok(cam, V[1], X, u[1], vv[1], dmul(A.tri_chi2, sig2[lev[1]]));
+        const float a = dot3f(ray[0], ray[0]), b = dot3f(ray[0], ray[1]), c2 = dot3f(ray[1], ray[1]);
+        const float cosp = __fdiv_rn(b, fmul(__fsqrt_rn(a), __fsqrt_rn(c2)));
+        if (cosp > 0.0f && cosp < cos_max) {
+            float wv[3];
+            for (int q = 0; q < 3; ++q) wv[q] = fsub(V[0].O[q], V[1].O[q]);
+            const float d = dot3f(ray[0], wv), e = dot3f(ray[1], wv);
+            const float den = fsub(fmul(a, c2), fmul(b, b));
+            if (den > 0.0f) {
+                const float s1 = __fdiv_rn(fsub(fmul(b, e), fmul(c2, d)), den);
+                const float s2 = __fdiv_rn(fsub(fmul(a, e), fmul(b, d)), den);
+                float X[3];
+                for (int q = 0; q < 3; ++q)
+                    X[q] = fmul(fadd(fadd(V[0].O[q], fmul(s1, ray[0][q])), fadd(V[1].O[q], fmul(s2, ray[1][q]))), 0.5f);
+                bool good = tri_view_ok(V[0], X, fx, fy, cx, cy, u[0], vv[0], fmul(chi2, sig2[lev[0]])) &&
+                            tri_view_ok(V[1], X, fx, fy, cx, cy, u[1], vv[1], fmul(chi2, sig2[lev[1]]));
                 if (good) {
-                    double d[2];
+                    float dist[2];
                     for (int s = 0; s < 2; ++s) {
-                        const double dx = dsub(X[0], V[s].O[0]), dy = dsub(X[1], V[s].O[1]), dz = dsub(X[2], V[s].O[2]);
-                        d[s] = __dsqrt_rn(dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)));
+                        float dv[3];
+                        for (int q = 0; q < 3; ++q) dv[q] = fsub(X[q], V[s].O[q]);
+                        dist[s] = __fsqrt_rn(dot3f(dv, dv));
                     }
-                    good = d[0] != 0.0 && d[1] != 0.0;
+                    good = dist[0] != 0.0f && dist[1] != 0.0f;
                     if (good) {
-                        const double ratio_dist = __ddiv_rn(d[1], d[0]);
-                        const double ratio_octave = __ddiv_rn(scl[lev[0]], scl[lev[1]]);
-                        good = !(dmul(ratio_dist, A.tri_ratio) < ratio_octave || ratio_dist > dmul(ratio_octave, A.tri_ratio));
+                        const float ratio_dist = __fdiv_rn(dist[1], dist[0]);
+                        const float ratio_octave = __fdiv_rn(scl[lev[0]], scl[lev[1]]);
+                        good = !(fmul(ratio_dist, fr) < ratio_octave || ratio_dist > fmul(ratio_octave, fr));
                     }
                 }
                 if (good) {
-                    out = make_float3(__double2float_rn(X[0]), __double2float_rn(X[1]), __double2float_rn(X[2]));
+                    out = make_float3(X[0], X[1], X[2]);
                     ok = 1;
                 }
             }
