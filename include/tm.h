@@ -220,12 +220,11 @@ typedef struct {
 
 /* Triangulation of the search's matches and their acceptance as new map points (Sec. III,
  * Map Point Creation: sufficient parallax, positive depth, low reprojection error, scale
- * consistency), run on the GPU over the batch's match lists.  Float64: normalized
+ * consistency), run on the GPU over the batch's match lists.  Float32: normalized
  * coordinates (u - cx) / fx; world rays R^T (xn, yn, 1), kept iff 0 < cos(parallax) <
- * cos_parallax_max; linear triangulation from the rows xn P_3 - P_1, yn P_3 - P_2 of both
- * views (P = [R | t]) by least squares through the 3x3 normal equations (Cramer's rule);
- * depth > 0 and reprojection error^2 <= chi2 * 1.44^level in each view; distance ratio to
- * the two camera centres consistent with the scale ratio within ratio_factor. */
+ * cos_parallax_max; the point is the midpoint of the rays' common perpendicular; depth > 0
+ * and reprojection error^2 <= chi2 * 1.44^level in each view; distance ratio to the two
+ * camera centres consistent with the scale ratio within ratio_factor. */
 typedef struct {
     double cos_parallax_max;  /* (0.9998)                                                   */
     double chi2;              /* (5.991)                                                    */
