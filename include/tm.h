@@ -172,6 +172,26 @@ tm_status tm_store_remove_keyframes(tm_ctx *ctx, int32_t n, const uint64_t *kf_i
 /* Number of keypoints of a stored keyframe, or TM_ERR_NOT_FOUND. */
 tm_status tm_store_keyframe_size(tm_ctx *ctx, uint64_t kf_id, int32_t *n);
 
+/* ---------------------------------------------------------------------------- keyframe culling (Sec. IV-F)
+ * Host-side observation counters: per map point, the number of keyframe observations at each
+ * pyramid level (the paper keeps culling on the CPU and replaces the walk over each map point's
+ * observation list by this array).  A map point of a keyframe, observed at level L there, counts
+ * as redundant when at least th_obs other keyframes observe it at a level <= L + 1; the
+ * keyframe is redundant when more than ratio * n of its n map points are (ORB-SLAM: th_obs 3,
+ * ratio 0.9).  Map point ids 0 .. max_mps-1; a keyframe observes a map point at most once, and
+ * its own observations are among the counts. */
+typedef struct tm_obs_counter tm_obs_counter;
+tm_status tm_obs_create(int32_t max_mps, tm_obs_counter **out);
+tm_status tm_obs_destroy(tm_obs_counter *c);
+/* Adds n observations (map point mp[k] seen at keypoint level level[k]).  TM_ERR_CAPACITY if a
+ * counter would pass 65535 (the entries before it are added). */
+tm_status tm_obs_add(tm_obs_counter *c, int32_t n, const int32_t *mp, const uint8_t *level);
+/* Removes n observations; all or nothing (TM_ERR_NOT_FOUND when one has nothing to remove). */
+tm_status tm_obs_remove(tm_obs_counter *c, int32_t n, const int32_t *mp, const uint8_t *level);
+/* The redundancy test of one keyframe from its observations (its map points and their levels). */
+tm_status tm_obs_redundant(tm_obs_counter *c, int32_t n, const int32_t *mp, const uint8_t *level,
+                           int32_t th_obs, float ratio, int32_t *n_redundant, int32_t *is_redundant);
+
 /* ---------------------------------------------------------------------------- search (Sec. IV-C)
  * Correspondence search of stored keyframe `kf` against stored neighbours nbrs[0..n_nbrs).
  *   q_free    [n_Q] or NULL   1 = the keypoint has no map point yet (eligible)     host/device

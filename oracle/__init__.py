@@ -282,3 +282,18 @@ def fuse_forward_step(cam, frames, step, params=None):
         res.append(r)
         ncmp += c
     return res, ncmp
+
+
+def culling_redundant(observations, kf, th_obs=3, ratio=0.9):
+    """Keyframe culling's redundancy test (Sec. IV-F) by walking observation lists, the
+    definition the counter array replaces.  observations: {map point: [(keyframe, level)]};
+    kf: the keyframe tested.  A map point of kf, observed by kf at level L, is redundant when at
+    least th_obs other keyframes observe it at a level <= L + 1; kf is redundant when more than
+    ratio * (its number of map points) are.  Returns (number redundant, redundant)."""
+    own = [(m, lv) for m, obs in observations.items() for (k, lv) in obs if k == kf]
+    red = 0
+    for m, lv in own:
+        n = sum(1 for (k, l2) in observations[m] if k != kf and l2 <= lv + 1)
+        if n >= th_obs:
+            red += 1
+    return red, red > ratio * len(own)

@@ -480,6 +480,50 @@ class _ResultBuffers:
         return a if a is not None and a.shape[0] >= n else np.empty(max(n, 1024), np.uint8)
 
 
+class ObsCounter:
+    """Keyframe-culling observation counters (tm_obs_*, host-side): per map point the number of
+    keyframe observations at each pyramid level."""
+
+    def __init__(self, max_mps):
+        h = ctypes.c_void_p()
+        check(tm_obs_create(int(max_mps), ctypes.byref(h)))  # noqa: F821
+        self.handle = h
+
+    @staticmethod
+    def _arrays(mp, level):
+        mp = np.ascontiguousarray(mp, np.int32)
+        level = np.ascontiguousarray(level, np.uint8)
+        assert mp.shape == level.shape
+        return mp, level
+
+    def add(self, mp, level):
+        mp, level = self._arrays(mp, level)
+        check(tm_obs_add(self.handle, len(mp), mp.ctypes.data, level.ctypes.data))  # noqa: F821
+
+    def remove(self, mp, level):
+        mp, level = self._arrays(mp, level)
+        check(tm_obs_remove(self.handle, len(mp), mp.ctypes.data, level.ctypes.data))  # noqa: F821
+
+    def redundant(self, mp, level, th_obs=3, ratio=0.9):
+        """(number of redundant map points, keyframe redundant) for a keyframe's observations."""
+        mp, level = self._arrays(mp, level)
+        nr, red = ctypes.c_int32(), ctypes.c_int32()
+        check(tm_obs_redundant(self.handle, len(mp), mp.ctypes.data, level.ctypes.data,  # noqa: F821
+                               int(th_obs), float(ratio), ctypes.byref(nr), ctypes.byref(red)))
+        return nr.value, bool(red.value)
+
+    def close(self):
+        if self.handle:
+            check(tm_obs_destroy(self.handle))  # noqa: F821
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Context:
     """A tm_ctx: one GPU, one camera, a keyframe store of max_kp-keypoint slots."""
 

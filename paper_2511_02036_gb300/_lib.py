@@ -123,6 +123,11 @@ SIGNATURES = {
     "tm_store_add_keyframes": (c_i32, [c_p, c_i32, c_p, P(tm_keyframe_view), c_p]),
     "tm_store_remove_keyframe": (c_i32, [c_p, c_u64]),
     "tm_store_remove_keyframes": (c_i32, [c_p, c_i32, c_p]),
+    "tm_obs_create": (c_i32, [c_i32, P(c_p)]),
+    "tm_obs_destroy": (c_i32, [c_p]),
+    "tm_obs_add": (c_i32, [c_p, c_i32, c_p, c_p]),
+    "tm_obs_remove": (c_i32, [c_p, c_i32, c_p, c_p]),
+    "tm_obs_redundant": (c_i32, [c_p, c_i32, c_p, c_p, c_i32, c_f32, P(c_i32), P(c_i32)]),
     "tm_store_keyframe_size": (c_i32, [c_p, c_u64, P(c_i32)]),
     "tm_search_triangulation": (c_i32, [c_p, c_u64, c_p, c_i32, P(tm_search_params), c_p, c_p,
                                         c_p, c_sz, P(c_sz), c_p, P(c_u64), c_p]),

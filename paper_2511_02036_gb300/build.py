@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtm.so")
-SOURCES = ["kernels.cu", "runtime.cu", "server.cu"]
+SOURCES = ["kernels.cu", "runtime.cu", "server.cu", "culling.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false and -ffp-contract=off: no contraction anywhere (device and host code), so every
 # floating-point gate is the plain round-to-nearest evaluation of its stated expression.
