@@ -121,6 +121,9 @@ typedef struct {
                                epipole_px^2 * 1.2^level_T (ORB-SLAM uses 10; monocular)      */
     int32_t rot_mode;       /* rotation bins: 0 = 30 bins of 12 degrees, floor(rot / 12);
                                1 = ORB-family round(rot * (1/30)), bins 0..12 used          */
+    float baseline_min_ratio; /* skip a pair whose baseline (distance between the camera
+                               centres) over the neighbour's median scene depth is below
+                               this (tm_step.nbr_median_depth; ORB-SLAM: 0.01)             */
 } tm_search_params;
 
 typedef struct {
@@ -236,6 +239,9 @@ typedef struct {
     int32_t fwd_mp_begin;
     int32_t fwd_mp_count;
     int64_t fwd_skip_off;
+    /* host [n_nbrs] or NULL: each neighbour's median scene depth, for the pair-baseline skip
+     * (a depth <= 0 never skips) */
+    const float *nbr_median_depth;
 } tm_step;
 
 /* Triangulation of the search's matches and their acceptance as new map points (Sec. III,

@@ -55,7 +55,8 @@ class _SearchParams(ctypes.Structure):
                 ("ratio_den", ctypes.c_int32), ("epi_chi2", ctypes.c_float),
                 ("epipolar", ctypes.c_int32), ("resolve", ctypes.c_int32),
                 ("rot_filter", ctypes.c_int32), ("epipole_px", ctypes.c_float),
-                ("rot_mode", ctypes.c_int32)]
+                ("rot_mode", ctypes.c_int32), ("baseline_min_ratio", ctypes.c_float),
+                ("t_median_depth", ctypes.c_float)]
 
 
 class _FuseParams(ctypes.Structure):
@@ -74,6 +75,7 @@ class SearchParams:
     rot_filter: bool = True
     epipole_px: float = 0.0   # ORB-family epipole rejection radius at level 0 (0 = off)
     rot_mode: int = 0         # 0: 30 bins of 12 degrees; 1: ORB-family round(rot / 30)
+    baseline_min_ratio: float = 0.0  # ORB-family pair skip: baseline / median depth below this
 
 
 @dataclass
@@ -200,15 +202,17 @@ def triangulate(cam, Q, T, matches, params=None):
     return xyz, ok
 
 
-def search_pair(cam, Q, T, free_q=None, free_t=None, params=None):
+def search_pair(cam, Q, T, free_q=None, free_t=None, params=None, t_median_depth=0.0):
     """Matches of one (Q, T) pair as an int32 array (k, 3) of (q_idx, t_idx, dist), sorted
-    by q_idx, and the number of descriptor comparisons."""
+    by q_idx, and the number of descriptor comparisons.  t_median_depth: T's median scene
+    depth for the pair-baseline skip (0 = unknown)."""
     p = params or SearchParams()
     keep = []
     q, t = _kf(Q, keep), _kf(T, keep)
     fq, ft = _mask(free_q), _mask(free_t)
     sp = _SearchParams(p.hamming_max, p.ratio_num, p.ratio_den, p.epi_chi2, int(p.epipolar),
-                       int(p.resolve), int(p.rot_filter), float(p.epipole_px), int(p.rot_mode))
+                       int(p.resolve), int(p.rot_filter), float(p.epipole_px), int(p.rot_mode),
+                       float(p.baseline_min_ratio), float(t_median_depth))
     cap = max(1, min(q.n, t.n) if p.resolve else q.n)
     out = np.zeros((3, cap), np.int32)
     ncmp = ctypes.c_int64(0)
@@ -251,9 +255,10 @@ def search_step(cam, frames, step, params=None):
     total number of comparisons."""
     Q = frames[step["q"]]
     res, ncmp = [], 0
+    md = step.get("nbr_median_depth")
     for k, f in enumerate(step["nbrs"]):
         ft = None if step.get("nbr_free") is None else step["nbr_free"][k]
-        m, c = search_pair(cam, Q, frames[f], step.get("q_free"), ft, params)
+        m, c = search_pair(cam, Q, frames[f], step.get("q_free"), ft, params, 0.0 if md is None else float(md[k]))
         res.append(m)
         ncmp += c
     return res, ncmp

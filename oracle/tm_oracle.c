@@ -142,6 +142,26 @@ int64_t orc_search_pair(const orc_camera *cam, const orc_keyframe *Q, const orc_
     float scale[ORC_LEVELS], sigma2[ORC_LEVELS], thr[ORC_LEVELS];
     orc_scales(scale, sigma2);
     for (int l = 0; l < ORC_LEVELS; ++l) thr[l] = p->epi_chi2 * sigma2[l];
+    /* ORB-family pair-baseline skip: with the neighbour's median scene depth known, a pair
+     * whose baseline |C_Q - C_T| (camera centres C = -R^T t, float64) is below
+     * baseline_min_ratio * depth (as baseline / depth < ratio, float64) is not searched. */
+    if (p->baseline_min_ratio > 0.0f && p->t_median_depth > 0.0f) {
+        double c[2][3];
+        const double *P[2] = {Q->Tcw, T->Tcw};
+        for (int v = 0; v < 2; ++v)
+            for (int k = 0; k < 3; ++k) {
+                double s = P[v][0 * 4 + k] * P[v][0 * 4 + 3];
+                s = s + P[v][1 * 4 + k] * P[v][1 * 4 + 3];
+                s = s + P[v][2 * 4 + k] * P[v][2 * 4 + 3];
+                c[v][k] = -s;
+            }
+        const double dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
+        const double base = sqrt(dx * dx + dy * dy + dz * dz);
+        if (base / (double)p->t_median_depth < (double)p->baseline_min_ratio) {
+            if (n_comparisons) *n_comparisons = 0;
+            return 0;
+        }
+    }
     float F[9];
     orc_fundamental(cam, Q->Tcw, T->Tcw, F);
     /* ORB-family epipole rejection: a candidate whose squared distance to the epipole is

@@ -61,6 +61,9 @@ typedef struct {
                                epipole_px^2 * scale(level of the candidate)              */
     int32_t rot_mode;       /* 0: 30 bins of 12 degrees, floor(rot / 12);
                                1: ORB-family bins round(rot * (1/30)), 30 -> 0            */
+    float baseline_min_ratio; /* > 0: skip the pair when |C_Q - C_T| / t_median_depth is
+                               below it (t_median_depth > 0 only)                          */
+    float t_median_depth;   /* the neighbour's median scene depth (0 = unknown)            */
 } orc_search_params;
 
 typedef struct {

@@ -171,12 +171,13 @@ class SearchParams:
     dense_min: int = 0      # tensor-core blocks for nodes with >= dense_min neighbour keypoints
     epipole_px: float = 0.0  # ORB-family epipole rejection radius at level 0 (0 = off; ORB-SLAM: 10)
     rot_mode: int = 0       # 0: 30 bins of 12 degrees; 1: ORB-family round(rot / 30)
+    baseline_min_ratio: float = 0.0  # skip pairs with baseline / median depth below (ORB-SLAM: 0.01)
 
     def struct(self):
         return L.tm_search_params(self.hamming_max, self.ratio_num, self.ratio_den, self.epi_chi2,
                                   int(self.epipolar), int(self.resolve), int(self.rot_filter),
                                   int(self.mode), int(self.lanes_per_query), int(self.dense_min),
-                                  float(self.epipole_px), int(self.rot_mode))
+                                  float(self.epipole_px), int(self.rot_mode), float(self.baseline_min_ratio))
 
 
 @dataclass
@@ -218,6 +219,7 @@ class StepTable:
     fwd_mp_begin: np.ndarray = None
     fwd_mp_count: np.ndarray = None
     fwd_skip_off: np.ndarray = None
+    nbr_median_depth: np.ndarray = None  # per neighbour, aligned with nbr_ids (float32)
 
     @classmethod
     def from_steps(cls, steps):
@@ -254,6 +256,11 @@ class StepTable:
         arr["fwd_mp_begin"][:n] = 0 if self.fwd_mp_begin is None else self.fwd_mp_begin
         arr["fwd_mp_count"][:n] = 0 if self.fwd_mp_count is None else self.fwd_mp_count
         arr["fwd_skip_off"][:n] = -1 if self.fwd_skip_off is None else self.fwd_skip_off
+        if self.nbr_median_depth is not None:
+            md = np.ascontiguousarray(self.nbr_median_depth, np.float32)
+            assert len(md) == len(nbrs)
+            keep.append(md)
+            arr["nbr_median_depth"][:n] = np.where(cnt > 0, md.ctypes.data + 4 * off, 0)
         keep.append(arr)
         return arr
 
@@ -284,6 +291,11 @@ def pack_batch(steps, kf_sizes):
         st[k].q_free_off = -1
         st[k].nbr_free_off = -1
         st[k].fwd_skip_off = -1
+        if s.get("nbr_median_depth") is not None:
+            md = np.ascontiguousarray(s["nbr_median_depth"], np.float32)
+            assert len(md) == len(nb)
+            keep.append(md)
+            st[k].nbr_median_depth = md.ctypes.data
         if s.get("q_free") is not None:
             st[k].q_free_off = moff
             masks.append(np.asarray(s["q_free"], np.uint8))
@@ -645,6 +657,10 @@ class Context:
             arr["fwd_mp_begin"][:n] = np.fromiter((s.get("fwd_mp_begin", 0) for s in steps), np.int64, n)
             arr["fwd_mp_count"][:n] = np.fromiter((s.get("fwd_mp_count", 0) for s in steps), np.int64, n)
             arr["fwd_skip_off"][:n] = np.fromiter((s.get("fwd_skip_off", -1) for s in steps), np.int64, n)
+            mds = [None if s.get("nbr_median_depth") is None else np.ascontiguousarray(s["nbr_median_depth"], np.float32)
+                   for s in steps]
+            keep.extend(m for m in mds if m is not None)
+            arr["nbr_median_depth"][:n] = [0 if m is None else m.ctypes.data for m in mds]
             st = arr.ctypes.data
             keep.append(arr)
         inp = L.tm_batch_inputs()

@@ -50,7 +50,8 @@ class tm_search_params(ctypes.Structure):
     _fields_ = [("hamming_max", c_i32), ("ratio_num", c_i32), ("ratio_den", c_i32),
                 ("epi_chi2", c_f32), ("epipolar", c_i32), ("resolve", c_i32),
                 ("rot_filter", c_i32), ("mode", c_i32), ("lanes_per_query", c_i32),
-                ("dense_min", c_i32), ("epipole_px", c_f32), ("rot_mode", c_i32)]
+                ("dense_min", c_i32), ("epipole_px", c_f32), ("rot_mode", c_i32),
+                ("baseline_min_ratio", c_f32)]
 
 
 class tm_fuse_params(ctypes.Structure):
@@ -71,7 +72,7 @@ class tm_step(ctypes.Structure):
     _fields_ = [("kf_id", c_u64), ("nbr_ids", c_p), ("n_nbrs", c_i32),
                 ("q_free_off", c_i64), ("nbr_free_off", c_i64), ("mp_begin", c_i32),
                 ("mp_count", c_i32), ("fwd_mp_begin", c_i32), ("fwd_mp_count", c_i32),
-                ("fwd_skip_off", c_i64)]
+                ("fwd_skip_off", c_i64), ("nbr_median_depth", c_p)]
 
 
 class tm_triangulation_params(ctypes.Structure):

@@ -127,6 +127,24 @@ __device__ void epipole_of(const CamConst &cam, const double *Tq, const double *
     e[0] = __double2float_rn(dadd(dmul(cam.fx, __ddiv_rn(c[0], c[2])), cam.cx));
     e[1] = __double2float_rn(dadd(dmul(cam.fy, __ddiv_rn(c[1], c[2])), cam.cy));
 }
+// ORB-family pair-baseline skip: with T's median scene depth known (> 0), the pair is not
+// searched when |C_Q - C_T| / depth < min_ratio (camera centres C = -R^T t; float64, sums
+// left to right).  One thread.
+__device__ bool pair_skipped(const double *Tq, const double *Tt, float depth, float min_ratio) {
+    if (!(min_ratio > 0.0f && depth > 0.0f)) return false;
+    double c[2][3];
+    const double *P[2] = {Tq, Tt};
+    for (int v = 0; v < 2; ++v)
+        for (int k = 0; k < 3; ++k) {
+            double s = dmul(P[v][0 * 4 + k], P[v][0 * 4 + 3]);
+            s = dadd(s, dmul(P[v][1 * 4 + k], P[v][1 * 4 + 3]));
+            s = dadd(s, dmul(P[v][2 * 4 + k], P[v][2 * 4 + 3]));
+            c[v][k] = -s;
+        }
+    const double dx = dsub(c[0][0], c[1][0]), dy = dsub(c[0][1], c[1][1]), dz = dsub(c[0][2], c[1][2]);
+    const double base = __dsqrt_rn(dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)));
+    return __ddiv_rn(base, (double)depth) < (double)min_ratio;
+}
 // Squared distance to the epipole below the level's threshold: the candidate is dropped.
 __device__ __forceinline__ bool near_epipole(const float *e, float xt, float yt, float thr) {
     const float dx = fsub(e[0], xt), dy = fsub(e[1], yt);
@@ -979,6 +997,12 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
     const int row = tid & (kDenseRows - 1), half = tid / kDenseRows;  // warps 4-7: second half
     const uint32_t splits = A.dsplit, item = blockIdx.x / splits, split = blockIdx.x % splits;
     const WorkItem w = A.items[item];
+    if (A.sp.baseline_min_ratio > 0.0f) {  // (uniform) a skipped pair needs no dense blocks
+        __shared__ bool s_skip;
+        if (threadIdx.x == 0) s_skip = pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio);
+        __syncthreads();
+        if (s_skip) return;
+    }
     const KfView T = KfView::at(w.t, A.L);
     const int nQ = (int)w.nq, nT = (int)w.nt, dmin = A.sp.dense_min;
     for (int j0 = 0; j0 < nT; j0 += kDenseScan * kDenseThreads) {
@@ -1216,6 +1240,18 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
     const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
     const WorkItem w = A.sitems[blockIdx.x];
     const uint32_t i = w.idx;
+    if (A.sp.baseline_min_ratio > 0.0f) {  // (uniform) pair-baseline skip
+        __shared__ bool s_skip;
+        if (threadIdx.x == 0) s_skip = pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio);
+        __syncthreads();
+        if (s_skip) {
+            if (threadIdx.x == 0) {
+                A.counts[i] = 0u;
+                A.item_cmp[i] = 0u;
+            }
+            return;
+        }
+    }
     const SearchStage S = SearchStage::make(A.sn);
     uint32_t *tkey = reinterpret_cast<uint32_t *>(ssm + S.tkey);
     uint16_t *bst = reinterpret_cast<uint16_t *>(ssm + S.bst);
@@ -1665,15 +1701,17 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
 template <int G>
 __global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *ts,
                                   const uint8_t *mq, const uint8_t *mt, int cap, SearchConst sp,
-                                  CamConst cam, PairScratch scr, unsigned long long *ncmp) {
+                                  CamConst cam, PairScratch scr, unsigned long long *ncmp, float mdepth) {
     __shared__ float F[9];
     __shared__ float thr[kLevels], thre[kLevels], epl[2];
     __shared__ unsigned long long s_cmp;
+    __shared__ bool s_skip;
     const SlotLayout L = SlotLayout::make(cap);
     const KfView Q = KfView::at(qs, L), T = KfView::at(ts, L);
     const int nQ = Q.hdr->n, nT = T.hdr->n;
     if (threadIdx.x < 32) fundamental_lanes(cam, Q.hdr->Tcw, T.hdr->Tcw, F);
     if (threadIdx.x == 32 && sp.epipole_px > 0.0f) epipole_of(cam, Q.hdr->Tcw, T.hdr->Tcw, epl);
+    if (threadIdx.x == 64) s_skip = pair_skipped(Q.hdr->Tcw, T.hdr->Tcw, mdepth, sp.baseline_min_ratio);
     if (threadIdx.x == 0) s_cmp = 0ull;
     if (threadIdx.x < kLevels) {
         const float s = level_scale(threadIdx.x);
@@ -1688,7 +1726,7 @@ __global__ void pair_match_kernel(const unsigned char *qs, const unsigned char *
     if (p < nQ) {
         const uint32_t io = Q.orig[p];
         if (sub == 0) scr.res[io] = kNone;
-        if (!mq || mq[io]) {
+        if (!s_skip && (!mq || mq[io])) {
             const uint32_t nd = Q.node[p];
             const int lo = lower_bound_u32(T.node, nT, nd);
             const int hi = (lo < nT && T.node[lo] == nd) ? upper_bound_u32(T.node, lo, nT, nd) : lo;
@@ -1942,7 +1980,7 @@ cudaError_t launch_pair_plain(const unsigned char *q, const unsigned char *t, co
                               const uint8_t *mt, int nq, int nt, int cap, const SearchConst &sp,
                               const CamConst &cam, const PairScratch &scr, Out3 *dense,
                               uint32_t *pair_offset, unsigned long long *ncmp, int lanes,
-                              cudaStream_t s) {
+                              cudaStream_t s, float t_median_depth) {
     cudaError_t e;
     if (nt > 0 && (e = cudaMemsetAsync(scr.win, 0xFF, size_t(nt) * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(scr.hist, 0, 128, s)) != cudaSuccess) return e;
@@ -1951,12 +1989,12 @@ cudaError_t launch_pair_plain(const unsigned char *q, const unsigned char *t, co
         const int per = threads / lanes;
         const int grid = (nq + per - 1) / per;
         switch (lanes) {
-            case 1: pair_match_kernel<1><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
-            case 2: pair_match_kernel<2><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
-            case 4: pair_match_kernel<4><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
-            case 8: pair_match_kernel<8><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
-            case 16: pair_match_kernel<16><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
-            default: pair_match_kernel<32><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp); break;
+            case 1: pair_match_kernel<1><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
+            case 2: pair_match_kernel<2><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
+            case 4: pair_match_kernel<4><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
+            case 8: pair_match_kernel<8><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
+            case 16: pair_match_kernel<16><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
+            default: pair_match_kernel<32><<<grid, threads, 0, s>>>(q, t, mq, mt, cap, sp, cam, scr, ncmp, t_median_depth); break;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         pair_resolve_kernel<<<(nq + 255) / 256, 256, 0, s>>>(q, t, cap, sp, scr);
@@ -2132,6 +2170,7 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     sc.dense_min = 0;
     sc.epipole_px = sp.epipole_px;
     sc.rot_mode = sp.rot_mode;
+    sc.baseline_min_ratio = 0.0f;  // (no median scene depth here)
     uint32_t *pair_offset = ps.running + 1;  // start of the output (always 0 here)
     if ((e = launch_pair_plain(slot_q, slot_t, q_free, t_free, q->n, t->n, kNoAllocMaxKp, sc, cc, ps,
                                reinterpret_cast<Out3 *>(out), pair_offset, ncmp, l, s)))

@@ -47,7 +47,7 @@ cudaError_t launch_pair_plain(const unsigned char *q, const unsigned char *t, co
                               const uint8_t *mt, int nq, int nt, int cap, const SearchConst &sp,
                               const CamConst &cam, const PairScratch &scr, Out3 *dense,
                               uint32_t *pair_offset, unsigned long long *ncmp, int lanes,
-                              cudaStream_t s);
+                              cudaStream_t s, float t_median_depth = 0.0f);
 // Plain fusion: one thread per map point, then an ordered compaction appended at *running;
 // offset_out[0] receives the start.
 cudaError_t launch_fuse_plain(const unsigned char *t, int cap, const float *pos,

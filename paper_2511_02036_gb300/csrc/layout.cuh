@@ -150,6 +150,7 @@ struct WorkItem {
                              //   bytes (forward fusion), or kNone: the batch's mp_skip
     const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
                              // keyframe entering with the batch)
+    float mdepth;            // search: T's median scene depth (0 = unknown; pair-baseline skip)
 };
 
 constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;
@@ -201,6 +202,7 @@ struct SearchConst {
     int32_t dense_min;            // dense node blocks (tensor cores) from this run length; 0 = off
     float epipole_px;             // epipole rejection radius at level 0 (0 = off)
     int32_t rot_mode;             // 0: 30 bins of 12 degrees; 1: round(rot / 30)
+    float baseline_min_ratio;     // pair skip: baseline / median depth below this (0 = off)
 };
 
 struct FuseConst {

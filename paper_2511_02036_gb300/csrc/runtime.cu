@@ -111,6 +111,7 @@ extern "C" void tm_search_params_default(tm_search_params *p) {
     p->dense_min = 0;
     p->epipole_px = 0.0f;
     p->rot_mode = 0;
+    p->baseline_min_ratio = 0.0f;
 }
 
 extern "C" void tm_triangulation_params_default(tm_triangulation_params *p) {
@@ -514,6 +515,7 @@ static SearchConst to_const(const tm_search_params &p) {
     s.dense_min = p.mode == TM_MODE_FUSED ? p.dense_min : 0;
     s.epipole_px = p.epipole_px;
     s.rot_mode = p.rot_mode;
+    s.baseline_min_ratio = p.baseline_min_ratio;
     return s;
 }
 
@@ -527,6 +529,8 @@ static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &
     if (!(sp.epipole_px >= 0.0f && sp.epipole_px < 1e6f))
         return fail(TM_ERR_INVALID_ARG, "epipole_px must be in [0, 1e6)");
     if (sp.rot_mode != 0 && sp.rot_mode != 1) return fail(TM_ERR_INVALID_ARG, "rot_mode must be 0 or 1");
+    if (!(sp.baseline_min_ratio >= 0.0f && sp.baseline_min_ratio < 1e6f))
+        return fail(TM_ERR_INVALID_ARG, "baseline_min_ratio must be in [0, 1e6)");
     const int l = sp.lanes_per_query;
     if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
         return fail(TM_ERR_INVALID_ARG, "lanes_per_query must be 0, 1, 2, 4, 8, 16 or 32");
@@ -702,6 +706,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
                 ? reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) +
                                                    sizeof(IngestJob) * (size_t)tn->second + offsetof(IngestJob, Tcw))
                 : reinterpret_cast<const double *>(c->slots[ts].ptr + offsetof(KfHeader, Tcw));
+            w.mdepth = S.nbr_median_depth ? S.nbr_median_depth[j] : 0.0f;
             w.qdesc = qv.desc;
             w.qxy = qv.xy;
             w.qnode = qv.node;
@@ -1021,7 +1026,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
         const uint8_t *mq = w.a == kNone ? nullptr : B.args.masks + w.a;
         const uint8_t *mt = w.b == kNone ? nullptr : B.args.masks + w.b;
         if ((e = launch_pair_plain(w.q, w.t, mq, mt, qn, tn, c->cap, sp, c->camc, scr, B.args.dense,
-                                   offs + i, ncmp, lanes, s)))
+                                   offs + i, ncmp, lanes, s, w.mdepth)))
             return cuda_fail(e, "plain pair");
     }
     for (int k = 0; k < B.n_steps; ++k) {

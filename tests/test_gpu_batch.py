@@ -443,3 +443,39 @@ def test_triangulation_plan_new_keyframes(tm, small_batch):
                 r = plan.results()
                 assert_same(r, exp)
                 check_points(w, r, exp[0])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pair_baseline_skip_batch(tm, small_batch, mode):
+    """ORB-family pair-baseline skip: per neighbour a median scene depth chosen so that every
+    other pair falls below the ratio; skipped pairs are empty and cost no comparisons, the
+    others equal the oracle's."""
+    w = small_batch
+    steps = []
+    ow = dict(w)
+    ow["steps"] = []
+    for s in w["steps"]:
+        cq = W.camera_center(w["frames"][s["q"]]["Tcw"])
+        md = []
+        for k, f in enumerate(s["nbrs"]):
+            base = float(np.linalg.norm(cq - W.camera_center(w["frames"][f]["Tcw"])))
+            md.append(base / 0.01 * (1.5 if k % 2 == 0 else 0.5))
+        s2 = dict(s)
+        s2["nbr_median_depth"] = np.array(md, np.float32)
+        ow["steps"].append(s2)
+        steps.append(dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                          mps=s.get("mps"), nbr_median_depth=s2["nbr_median_depth"]))
+    sp = tm.SearchParams(baseline_min_ratio=0.01, mode=mode)
+    osp = O.SearchParams(baseline_min_ratio=0.01)
+    exp, ecmp = [], 0
+    for st in ow["steps"]:
+        r, c = O.search_step(w["cam"], w["frames"], st, osp)
+        exp.extend(r)
+        ecmp += c
+    assert sum(len(e) == 0 for e in exp) >= len(exp) // 2 - 1
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        res = ctx.batch_run(steps, sp=sp)
+        for g, e in zip(res.pairs, exp):
+            np.testing.assert_array_equal(g, e)
+        assert res.n_comparisons_search == ecmp

@@ -510,3 +510,18 @@ def test_triangulation_rejects_pure_rotation_and_scale_jumps():
             T["level"][m[k, 1]] += dl
         _, ok = O.triangulate(p["cam"], p["Q"], T, m)
         assert (ok[low] == expect).all(), (dl, ok[low])
+
+
+def test_pair_baseline_skip():
+    """ORB-family pair skip: with T's median scene depth d known, the pair is not searched when
+    baseline / d < ratio (the cfg0 baseline is 0.3 m: skipped for d = 40 m at ratio 0.01, kept
+    for d = 20 m with the same matches as without the rule; unknown depth never skips)."""
+    p = W.make_pair_cfg0(3)
+    base, c0 = O.search_pair(p["cam"], p["Q"], p["T"])
+    sp = O.SearchParams(baseline_min_ratio=0.01)
+    m, c = O.search_pair(p["cam"], p["Q"], p["T"], params=sp, t_median_depth=40.0)
+    assert len(m) == 0 and c == 0
+    for d in (20.0, 0.0):
+        m, c = O.search_pair(p["cam"], p["Q"], p["T"], params=sp, t_median_depth=d)
+        np.testing.assert_array_equal(m, base)
+        assert c == c0
