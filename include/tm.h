@@ -195,6 +195,67 @@ tm_status tm_obs_remove(tm_obs_counter *c, int32_t n, const int32_t *mp, const u
 tm_status tm_obs_redundant(tm_obs_counter *c, int32_t n, const int32_t *mp, const uint8_t *level,
                            int32_t th_obs, float ratio, int32_t *n_redundant, int32_t *is_redundant);
 
+/* ---------------------------------------------------------------------------- fuse-apply (Sec. IV-D)
+ * The sequential stage after the parallel fusion search.  The search lists candidate duplicate
+ * pairs (a map point, a keypoint of a target keyframe) from one state of the map; this stage
+ * merges them one at a time in the caller's order (ORB-SLAM's local mapping: the new keyframe's
+ * points into each neighbour, neighbour by neighbour, then the neighbours' points into the new
+ * keyframe), re-checking every candidate against the map as it stands at that moment.
+ *
+ * A host-side map: per keyframe a keypoint -> map point table and each keypoint's pyramid level;
+ * per map point its observations (keyframe, keypoint), whether it is live, and the point that
+ * replaced it; and the culling counters (per map point and level, as tm_obs_*), updated
+ * whenever an observation is added, moved or erased.  Applying candidate (m, T, j):
+ *   - skipped if m is no longer live (replaced by an earlier candidate) or T already observes m;
+ *   - else, if keypoint j of T has no map point, T observes m at j;
+ *   - else, with p the point at j: the one with more observations survives (a tie keeps m),
+ *     and the other is replaced: each of its observations (K, i) moves to the survivor, unless
+ *     K already observes the survivor, in which case keypoint i of K loses its map point; the
+ *     replaced point is no longer live and records the survivor.
+ * Map point ids 0 .. max_mps-1 (a point exists from its first observation); keyframe ids are the
+ * caller's (the store's, for one).  Every call validates all its arguments before it changes
+ * anything: on an error the map is unchanged.  Calls on one map are serialised by a lock. */
+typedef struct tm_map tm_map;
+typedef struct {
+    int32_t added;                /* keypoint had no map point: observation added             */
+    int32_t merged_into_existing; /* the keypoint's point had more observations: m replaced   */
+    int32_t replaced_existing;    /* m had as many or more: the keypoint's point replaced     */
+    int32_t skipped_dead;         /* m was replaced by an earlier candidate                   */
+    int32_t skipped_observed;     /* the target already observes m                           */
+} tm_fuse_apply_stats;
+tm_status tm_map_create(int32_t max_mps, tm_map **out);
+tm_status tm_map_destroy(tm_map *m);
+/* A keyframe of n_kp keypoints, level[n_kp] (0 .. TM_LEVELS-1; NULL: all 0), none with a map
+ * point.  TM_ERR_EXISTS if the id is in the map. */
+tm_status tm_map_add_keyframe(tm_map *m, uint64_t kf_id, int32_t n_kp, const uint8_t *level);
+/* Erases the keyframe and all its observations (keyframe culling).  Points left without an
+ * observation stay live.  TM_ERR_NOT_FOUND. */
+tm_status tm_map_remove_keyframe(tm_map *m, uint64_t kf_id);
+/* Keyframe kf_id observes map point mp[k] at keypoint kp[k] (points created by triangulation,
+ * or seen by tracking).  TM_ERR_INVALID_ARG if a keypoint is out of range or already has a map
+ * point, the keyframe already observes the point, a point is given twice, or it was replaced. */
+tm_status tm_map_add_observations(tm_map *m, uint64_t kf_id, int32_t n, const int32_t *kp,
+                                  const int32_t *mp);
+/* Applies n candidates of one target keyframe kf_id in order: cand[k].kp_idx is a keypoint of
+ * the target, and the map point is mp_ids[cand[k].mp_idx] (mp_ids[n_ids]: the batch's map point
+ * ids, as tm_fuse and tm_batch_run index them) or, with mp_ids NULL, cand[k].mp_idx itself.
+ * dist is not read.  TM_ERR_INVALID_ARG if an index is out of range or a point never existed.
+ * stats (may be NULL) receives this call's counts. */
+tm_status tm_map_fuse_apply(tm_map *m, uint64_t kf_id, int32_t n, const tm_fuse_match *cand,
+                            const int32_t *mp_ids, int32_t n_ids, tm_fuse_apply_stats *stats);
+/* out[n_kp]: the map point of each keypoint of the keyframe, -1 for none.  n_kp must equal the
+ * keyframe's keypoint count. */
+tm_status tm_map_keyframe_points(tm_map *m, uint64_t kf_id, int32_t n_kp, int32_t *out);
+/* Per map point mp[k]: live[k] (1 live, 0 replaced, -1 never existed), current[k] (the live
+ * point it now stands for, following replacements; -1 if it never existed) and n_obs[k] (its
+ * number of observations; 0 once replaced).  Any output may be NULL. */
+tm_status tm_map_point_info(tm_map *m, int32_t n, const int32_t *mp, int32_t *live,
+                            int32_t *current, int32_t *n_obs);
+/* Keyframe culling's redundancy test (as tm_obs_redundant) of keyframe kf_id over its map
+ * points, read from the map's own counters. */
+tm_status tm_map_redundant(tm_map *m, uint64_t kf_id, int32_t th_obs, float ratio,
+                           int32_t *n_redundant, int32_t *is_redundant);
+
 /* ---------------------------------------------------------------------------- search (Sec. IV-C)
  * Correspondence search of stored keyframe `kf` against stored neighbours nbrs[0..n_nbrs).
  *   q_free    [n_Q] or NULL   1 = the keypoint has no map point yet (eligible)     host/device

@@ -302,3 +302,80 @@ def culling_redundant(observations, kf, th_obs=3, ratio=0.9):
         if n >= th_obs:
             red += 1
     return red, red > ratio * len(own)
+
+
+class FuseMap:
+    """The sequential fuse-apply stage (Sec. IV-D: duplicate pairs are found in parallel and
+    merged afterwards, one at a time, keeping the original sequential logic; Sec. II: of two
+    duplicate points one is kept and takes over the observations, the other is discarded).
+    Plain dictionaries: keyframe -> list (keypoint -> map point or None), map point ->
+    {keyframe: keypoint}.
+
+    Readings (the paper gives the stage, not its rule): which point survives follows ORB-SLAM,
+    the system the paper restructures: the one with more observations, a tie keeping the point
+    being fused; a keyframe that already observes the survivor drops the replaced point's
+    keypoint link; a candidate whose point was replaced earlier, or whose target already
+    observes it, is skipped."""
+
+    def __init__(self):
+        self.kp = {}         # keyframe -> [map point or None] per keypoint
+        self.level = {}      # keyframe -> [level] per keypoint
+        self.obs = {}        # live map point -> {keyframe: keypoint}
+        self.replaced = {}   # replaced map point -> the point that replaced it
+
+    def add_keyframe(self, k, n_kp, level=None):
+        assert k not in self.kp
+        self.kp[k] = [None] * n_kp
+        self.level[k] = [0] * n_kp if level is None else [int(x) for x in level]
+
+    def remove_keyframe(self, k):
+        for m in self.kp.pop(k):
+            if m is not None:
+                del self.obs[m][k]
+        del self.level[k]
+
+    def observe(self, k, j, m):
+        assert self.kp[k][j] is None and m not in self.replaced and k not in self.obs.get(m, {})
+        self.obs.setdefault(m, {})[k] = j
+        self.kp[k][j] = m
+
+    def _replace(self, a, b):
+        """a is discarded: each of its observations goes to b, unless that keyframe observes b."""
+        for k, j in self.obs.pop(a).items():
+            if k in self.obs[b]:
+                self.kp[k][j] = None
+            else:
+                self.obs[b][k] = j
+                self.kp[k][j] = b
+        self.replaced[a] = b
+
+    def fuse(self, k, cands):
+        """Applies candidates [(map point, keypoint of k)] in order; returns the counts."""
+        st = dict(added=0, merged_into_existing=0, replaced_existing=0, skipped_dead=0, skipped_observed=0)
+        for m, j in cands:
+            if m in self.replaced:
+                st["skipped_dead"] += 1
+            elif k in self.obs[m]:
+                st["skipped_observed"] += 1
+            elif self.kp[k][j] is None:
+                self.observe(k, j, m)
+                st["added"] += 1
+            else:
+                p = self.kp[k][j]
+                if len(self.obs[p]) > len(self.obs[m]):
+                    self._replace(m, p)
+                    st["merged_into_existing"] += 1
+                else:
+                    self._replace(p, m)
+                    st["replaced_existing"] += 1
+        return st
+
+    def current(self, m):
+        """The live point m stands for, following replacements (None if it never existed)."""
+        while m in self.replaced:
+            m = self.replaced[m]
+        return m if m in self.obs else None
+
+    def observations(self):
+        """{map point: [(keyframe, level)]} for culling_redundant."""
+        return {m: [(k, self.level[k][j]) for k, j in o.items()] for m, o in self.obs.items()}

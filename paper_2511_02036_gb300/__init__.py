@@ -536,6 +536,73 @@ class ObsCounter:
         self.close()
 
 
+class Map:
+    """The host-side map of the fuse-apply stage (tm_map_*): per keyframe a keypoint -> map point
+    table and keypoint levels, per map point its observations, and the culling counters.  The
+    fusion search (GPU) lists candidates; fuse_apply merges them in order (Sec. IV-D)."""
+
+    def __init__(self, max_mps):
+        h = ctypes.c_void_p()
+        check(tm_map_create(int(max_mps), ctypes.byref(h)))  # noqa: F821
+        self.handle = h
+
+    def add_keyframe(self, kf_id, n_kp, level=None):
+        lv = None if level is None else np.ascontiguousarray(level, np.uint8)
+        assert lv is None or len(lv) == n_kp
+        check(tm_map_add_keyframe(self.handle, int(kf_id), int(n_kp), _ptr(lv)))  # noqa: F821
+
+    def remove_keyframe(self, kf_id):
+        check(tm_map_remove_keyframe(self.handle, int(kf_id)))  # noqa: F821
+
+    def add_observations(self, kf_id, kp, mp):
+        kp = np.ascontiguousarray(kp, np.int32)
+        mp = np.ascontiguousarray(mp, np.int32)
+        assert kp.shape == mp.shape
+        check(tm_map_add_observations(self.handle, int(kf_id), len(kp), kp.ctypes.data,  # noqa: F821
+                                      mp.ctypes.data))
+
+    def fuse_apply(self, kf_id, cands, mp_ids=None):
+        """cands: int32 (k, 3) (mp_idx, kp_idx, dist) rows as tm_fuse / batch results give them;
+        mp_ids: the batch's map point ids (None: mp_idx is the id).  Returns the call's counts."""
+        c = np.ascontiguousarray(np.asarray(cands, np.int32).reshape(-1, 3))
+        ids = None if mp_ids is None else np.ascontiguousarray(mp_ids, np.int32)
+        st = L.tm_fuse_apply_stats()
+        check(tm_map_fuse_apply(self.handle, int(kf_id), len(c), c.ctypes.data if len(c) else None,  # noqa: F821
+                                _ptr(ids), 0 if ids is None else len(ids), ctypes.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in L.tm_fuse_apply_stats._fields_}
+
+    def keyframe_points(self, kf_id, n_kp):
+        out = np.zeros(max(1, n_kp), np.int32)
+        check(tm_map_keyframe_points(self.handle, int(kf_id), int(n_kp), out.ctypes.data))  # noqa: F821
+        return out[:n_kp]
+
+    def point_info(self, mps):
+        """(live, current, n_obs) per map point: live 1 / 0 replaced / -1 never existed."""
+        mp = np.ascontiguousarray(mps, np.int32)
+        n = len(mp)
+        live, cur, nobs = (np.zeros(max(1, n), np.int32) for _ in range(3))
+        check(tm_map_point_info(self.handle, n, mp.ctypes.data, live.ctypes.data, cur.ctypes.data,  # noqa: F821
+                                nobs.ctypes.data))
+        return live[:n], cur[:n], nobs[:n]
+
+    def redundant(self, kf_id, th_obs=3, ratio=0.9):
+        nr, red = ctypes.c_int32(), ctypes.c_int32()
+        check(tm_map_redundant(self.handle, int(kf_id), int(th_obs), float(ratio),  # noqa: F821
+                               ctypes.byref(nr), ctypes.byref(red)))
+        return nr.value, bool(red.value)
+
+    def close(self):
+        if self.handle:
+            check(tm_map_destroy(self.handle))  # noqa: F821
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Context:
     """A tm_ctx: one GPU, one camera, a keyframe store of max_kp-keypoint slots."""
 

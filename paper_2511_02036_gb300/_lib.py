@@ -100,6 +100,11 @@ class tm_server_config(ctypes.Structure):
                 ("search", tm_search_params), ("fuse", tm_fuse_params)]
 
 
+class tm_fuse_apply_stats(ctypes.Structure):
+    _fields_ = [("added", c_i32), ("merged_into_existing", c_i32), ("replaced_existing", c_i32),
+                ("skipped_dead", c_i32), ("skipped_observed", c_i32)]
+
+
 class tm_request(ctypes.Structure):
     _fields_ = [("kf_id", c_u64), ("kf", tm_keyframe_view), ("nbr_ids", c_p), ("n_nbrs", c_i32),
                 ("q_free", c_p), ("nbr_free", c_p), ("mps", tm_mappoint_view)]
@@ -129,6 +134,15 @@ SIGNATURES = {
     "tm_obs_add": (c_i32, [c_p, c_i32, c_p, c_p]),
     "tm_obs_remove": (c_i32, [c_p, c_i32, c_p, c_p]),
     "tm_obs_redundant": (c_i32, [c_p, c_i32, c_p, c_p, c_i32, c_f32, P(c_i32), P(c_i32)]),
+    "tm_map_create": (c_i32, [c_i32, P(c_p)]),
+    "tm_map_destroy": (c_i32, [c_p]),
+    "tm_map_add_keyframe": (c_i32, [c_p, c_u64, c_i32, c_p]),
+    "tm_map_remove_keyframe": (c_i32, [c_p, c_u64]),
+    "tm_map_add_observations": (c_i32, [c_p, c_u64, c_i32, c_p, c_p]),
+    "tm_map_fuse_apply": (c_i32, [c_p, c_u64, c_i32, c_p, c_p, c_i32, P(tm_fuse_apply_stats)]),
+    "tm_map_keyframe_points": (c_i32, [c_p, c_u64, c_i32, c_p]),
+    "tm_map_point_info": (c_i32, [c_p, c_i32, c_p, c_p, c_p, c_p]),
+    "tm_map_redundant": (c_i32, [c_p, c_u64, c_i32, c_f32, P(c_i32), P(c_i32)]),
     "tm_store_keyframe_size": (c_i32, [c_p, c_u64, P(c_i32)]),
     "tm_search_triangulation": (c_i32, [c_p, c_u64, c_p, c_i32, P(tm_search_params), c_p, c_p,
                                         c_p, c_sz, P(c_sz), c_p, P(c_u64), c_p]),

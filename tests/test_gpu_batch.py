@@ -398,6 +398,69 @@ def test_forward_fusion_plan_and_mixed_steps(tm):
                 p += 1
 
 
+def test_fuse_apply_consumes_batch_lists(tm):
+    """The GPU's fusion lists feed the sequential fuse-apply (Sec. IV-D) in ORB-SLAM's order: the
+    new keyframe's map points into each neighbour in turn, then the neighbours' map points into
+    the new keyframe.  The library's host map after the GPU lists equals the oracle's map after
+    the oracle's lists.  The map's starting observations are drawn at random (a valid state)."""
+    w = W.make_cfg2(seed=2202, n_steps=1, forward=True)
+    st = w["steps"][0]
+    efw, _ = oracle_forward(w)
+    efu = oracle_results(w)[1][0]
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        res = ctx.batch_run(forward_steps(w))
+    q, nbrs = st["q"], list(st["nbrs"])
+    nf, nb = int(st["fwd_mps"]["n"]), int(st["mps"]["n"])
+    fwd_ids = np.arange(nf, dtype=np.int32)
+    bwd_ids = np.arange(nf, nf + nb, dtype=np.int32)
+    rng = np.random.default_rng(2202)
+    fm = O.FuseMap()
+    for k in [q] + nbrs:
+        fm.add_keyframe(k, w["frames"][k]["n"], w["frames"][k]["level"])
+    triples = []
+
+    def observe(k, m):
+        free = [j for j, x in enumerate(fm.kp[k]) if x is None]
+        if free and k not in fm.obs.get(m, {}):
+            j = int(rng.choice(free))
+            fm.observe(k, j, m)
+            triples.append((k, j, m))
+    for i in range(nf):
+        observe(q, int(fwd_ids[i]))
+        for n, k in enumerate(nbrs):
+            if st["fwd_skip"][n][i]:
+                observe(k, int(fwd_ids[i]))
+    for i in range(nb):
+        for k in rng.choice(nbrs, size=int(rng.integers(1, 3)), replace=False):
+            observe(int(k), int(bwd_ids[i]))
+        for k in rng.permutation(nbrs):  # every candidate's point must exist
+            if int(bwd_ids[i]) not in fm.obs:
+                observe(int(k), int(bwd_ids[i]))
+    assert all(m in fm.obs for m in range(nf + nb))
+    with tm.Map(nf + nb) as mp:
+        for k in [q] + nbrs:
+            mp.add_keyframe(k, w["frames"][k]["n"], w["frames"][k]["level"])
+            t = [(j, m) for (kk, j, m) in triples if kk == k]
+            mp.add_observations(k, [j for j, _ in t], [m for _, m in t])
+        totals = {}
+        for n, k in enumerate(nbrs):
+            est = fm.fuse(k, [(int(fwd_ids[a]), int(j)) for a, j, _ in efw[n]])
+            assert mp.fuse_apply(k, res.fwds[n], fwd_ids) == est
+            for f, v in est.items():
+                totals[f] = totals.get(f, 0) + v
+        est = fm.fuse(q, [(int(bwd_ids[a]), int(j)) for a, j, _ in efu])
+        assert mp.fuse_apply(q, res.fuses[0], bwd_ids) == est
+        assert totals["added"] > 0 and est["added"] + est["replaced_existing"] + est["merged_into_existing"] > 0
+        for k in [q] + nbrs:
+            np.testing.assert_array_equal(mp.keyframe_points(k, w["frames"][k]["n"]),
+                                          [-1 if x is None else x for x in fm.kp[k]])
+        live, cur, nobs = mp.point_info(np.arange(nf + nb))
+        for m in range(nf + nb):
+            c = fm.current(m)
+            assert cur[m] == (-1 if c is None else c) and nobs[m] == len(fm.obs.get(m, {}))
+
+
 def check_points(w, res, exp_pairs, params=None):
     p = 0
     for st in w["steps"]:
@@ -411,7 +474,7 @@ def check_points(w, res, exp_pairs, params=None):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_triangulation_batch(tm, small_batch, mode):
-    """Triangulation and acceptance of every match on the GPU (float64, fixed order) equals the
+    """Triangulation and acceptance of every match on the GPU (float32, fixed order) equals the
     oracle's bit for bit: points (float32) and accepted flags, batched and per-pair forms."""
     w = small_batch
     exp = oracle_results(w)
