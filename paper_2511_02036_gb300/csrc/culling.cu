@@ -89,14 +89,12 @@ extern "C" tm_status tm_obs_remove(tm_obs_counter *c, int32_t n, const int32_t *
     tm_status st = check_obs(c, n, mp, level);
     if (st) return st;
     std::lock_guard<std::mutex> lk(c->mu);
-    // all or nothing: every removal must have an observation to remove
-    std::vector<uint32_t> need;
+    // all or nothing: every removal must have an observation to remove (counted per counter,
+    // so that a counter named several times needs as many observations)
+    std::unordered_map<size_t, uint32_t> need;
     for (int32_t k = 0; k < n; ++k) {
         const size_t e = (size_t)mp[k] * TM_LEVELS + level[k];
-        uint32_t earlier = 0;
-        for (int32_t q = 0; q < k; ++q)
-            if (mp[q] == mp[k] && level[q] == level[k]) ++earlier;
-        if (c->counts[e] <= earlier)
+        if (c->counts[e] <= need[e]++)
             return fail(TM_ERR_NOT_FOUND, "tm_obs_remove: no observation of map point %d at level %d to remove",
                         mp[k], level[k]);
     }
@@ -259,6 +257,7 @@ extern "C" tm_status tm_map_add_observations(tm_map *m, uint64_t kf_id, int32_t 
                     (unsigned long long)kf_id);
     MapKeyframe &k = it->second;
     const int32_t n_kp = (int32_t)k.kp_mp.size();
+    std::unordered_map<int32_t, int32_t> seen_kp, seen_mp;  // first entry naming each
     for (int32_t e = 0; e < n; ++e) {
         if (kp[e] < 0 || kp[e] >= n_kp || mp[e] < 0 || mp[e] >= m->max_mps)
             return fail(TM_ERR_INVALID_ARG, "tm_map_add_observations: entry %d (keypoint %d, map point %d) "
@@ -271,10 +270,10 @@ extern "C" tm_status tm_map_add_observations(tm_map *m, uint64_t kf_id, int32_t 
         if (m->observed_at(mp[e], kf_id) >= 0)
             return fail(TM_ERR_INVALID_ARG, "tm_map_add_observations: keyframe already observes map point %d",
                         mp[e]);
-        for (int32_t f = 0; f < e; ++f)
-            if (kp[f] == kp[e] || mp[f] == mp[e])
-                return fail(TM_ERR_INVALID_ARG, "tm_map_add_observations: entries %d and %d share a keypoint "
-                            "or a map point", f, e);
+        const auto a = seen_kp.emplace(kp[e], e), b = seen_mp.emplace(mp[e], e);
+        if (!a.second || !b.second)
+            return fail(TM_ERR_INVALID_ARG, "tm_map_add_observations: entries %d and %d share a keypoint "
+                        "or a map point", !a.second ? a.first->second : b.first->second, e);
     }
     for (int32_t e = 0; e < n; ++e) m->observe(mp[e], kf_id, k, kp[e]);
     return TM_OK;

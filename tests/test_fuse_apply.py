@@ -234,3 +234,26 @@ def test_errors_leave_the_map_unchanged(tm):
         assert e.value.status == tm.TM_ERR_INVALID_ARG
         assert mp.fuse_apply(T, np.zeros((0, 3), np.int32)) == dict(
             added=0, merged_into_existing=0, replaced_existing=0, skipped_dead=0, skipped_observed=0)
+
+
+def test_add_observations_all_or_nothing(tm):
+    with tm.Map(100) as mp:
+        mp.add_keyframe(1, 4)
+        mp.add_keyframe(2, 4)
+        for kp, pts in (([0, 1], [20, 20]),      # one point at two keypoints of a keyframe
+                        ([0, 1, 0], [5, 6, 7]),  # one keypoint twice
+                        ([0, 4], [5, 6])):       # keypoint out of range
+            with pytest.raises(tm.TMError) as e:
+                mp.add_observations(1, kp, pts)
+            assert e.value.status == tm.TM_ERR_INVALID_ARG
+            np.testing.assert_array_equal(mp.keyframe_points(1, 4), [-1] * 4)
+            assert mp.point_info([5, 6, 7, 20])[0].tolist() == [-1] * 4
+        mp.add_observations(1, [3, 0], [20, 21])
+        mp.add_observations(2, [0], [20])
+        np.testing.assert_array_equal(mp.keyframe_points(1, 4), [21, -1, -1, 20])
+        assert mp.point_info([20, 21])[2].tolist() == [2, 1]
+        mp.remove_keyframe(1)                        # culling erases its observations
+        assert mp.point_info([20, 21])[2].tolist() == [1, 0]
+        assert mp.point_info([20, 21])[0].tolist() == [1, 1]  # points stay live
+        with pytest.raises(tm.TMError):
+            mp.keyframe_points(1, 4)
