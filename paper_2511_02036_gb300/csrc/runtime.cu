@@ -680,7 +680,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     };
     for (int k = 0; k < n_steps; ++k) {
         const tm_step &S = steps[k];
-        int qs;
+        int qs = -1;
         if ((st = slot_of(S.kf_id, qs))) return st;
         const int nq = c->slots[qs].n;
         if (S.n_nbrs < 0 || (S.n_nbrs > 0 && !S.nbr_ids)) return fail(TM_ERR_INVALID_ARG, "step %d: bad neighbours", k);
@@ -692,7 +692,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         const QView qv = qview_of(qs);
         unsigned char *qptr = c->slots[qs].ptr;
         for (int j = 0; j < S.n_nbrs; ++j) {
-            int ts;
+            int ts = -1;
             if ((st = slot_of(S.nbr_ids[j], ts))) return st;
             const int nt = c->slots[ts].n;
             if (S.nbr_free_off >= 0 && toff + (size_t)nt > mask_bytes)
