@@ -173,6 +173,15 @@ class SearchParams:
     rot_mode: int = 0       # 0: 30 bins of 12 degrees; 1: ORB-family round(rot / 30)
     baseline_min_ratio: float = 0.0  # skip pairs with baseline / median depth below (ORB-SLAM: 0.01)
 
+    @classmethod
+    def orb_family(cls, coarse=False, **kw):
+        """The ORB-family variants together: epipole rejection at 10 px (scaled by the level),
+        rotation bins round(rot / 30), pair-baseline skip below 1 % of the neighbour's median
+        depth (the steps must carry that depth).  coarse=True is the family's coarse mode: the
+        epipolar-line test is dropped, the epipole rejection kept."""
+        kw = dict(dict(epipole_px=10.0, rot_mode=1, baseline_min_ratio=0.01, epipolar=not coarse), **kw)
+        return cls(**kw)
+
     def struct(self):
         return L.tm_search_params(self.hamming_max, self.ratio_num, self.ratio_den, self.epi_chi2,
                                   int(self.epipolar), int(self.resolve), int(self.rot_filter),

@@ -88,6 +88,13 @@ def test_parameter_defaults(lib):
     for k, _ in L.tm_search_params._fields_:
         if k != "epi_chi2":
             assert getattr(s, k) == getattr(p, k), k
+    # the ORB-family preset and its coarse mode differ from the defaults only where stated
+    o, oc = tm.SearchParams.orb_family().struct(), tm.SearchParams.orb_family(coarse=True, mode=1).struct()
+    assert (o.epipole_px, o.rot_mode, o.epipolar) == (10.0, 1, 1) and abs(o.baseline_min_ratio - 0.01) < 1e-9
+    assert (oc.epipolar, oc.epipole_px, oc.rot_mode, oc.mode) == (0, 10.0, 1, 1)
+    for k, _ in L.tm_search_params._fields_:
+        if k not in ("epi_chi2", "epipole_px", "rot_mode", "baseline_min_ratio"):
+            assert getattr(o, k) == getattr(p, k), k
 
 
 def test_null_arguments_rejected(lib):

@@ -74,7 +74,7 @@ def test_parameter_variants(tm, variant):
           "epipole_10": tm.SearchParams(epipole_px=10.0),
           "epipole_half": tm.SearchParams(),
           "orb_bins": tm.SearchParams(rot_mode=1),
-          "orb_all": tm.SearchParams(rot_mode=1, epipolar=False)}[variant]
+          "orb_all": tm.SearchParams.orb_family(coarse=True, baseline_min_ratio=0.0)}[variant]
     p = W.make_pair_cfg0(21, n_nodes=30)
     if variant in ("epipole_half", "orb_all"):
         # a radius reaching the image centre: the epipole of this lateral motion lies far
