@@ -413,7 +413,7 @@ def run_mine(args, rank, world, local_rank):
                                 "kernels-only graph"},
            "warm_l2": {"ms_per_step": float(warm.mean()), "value": len(new_ids) / (float(warm.mean()) / 1e3),
                        "unit": "keyframes/s", "note": "same replays back to back without the L2 flush"},
-           "roofline": roof, "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
+           "device": torch.cuda.get_device_name(dev), "roofline": roof, "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
            "wall_s_timed_region": t_wall}
 
     # ---------------------------------------------------------------- plain per-pair form

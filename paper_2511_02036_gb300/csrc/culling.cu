@@ -302,6 +302,7 @@ extern "C" tm_status tm_map_fuse_apply(tm_map *m, uint64_t kf_id, int32_t n, con
         if (p < 0 || p >= m->max_mps || m->mps[p].state == MP_NONE)
             return fail(TM_ERR_INVALID_ARG, "tm_map_fuse_apply: candidate %d: map point %d does not exist", e, p);
     }
+    Range range("tm_map_fuse_apply");
     tm_fuse_apply_stats st = {0, 0, 0, 0, 0};
     for (int32_t e = 0; e < n; ++e) {
         const int32_t j = cand[e].kp_idx;

@@ -383,6 +383,7 @@ extern "C" tm_status tm_store_add_keyframes(tm_ctx *c, int32_t n, const uint64_t
                                             const tm_keyframe_view *kfs, void *stream) {
     if (!c || n < 0 || (n > 0 && (!ids || !kfs))) return fail(TM_ERR_INVALID_ARG, "tm_store_add_keyframes: bad arguments");
     if (n == 0) return TM_OK;
+    Range range("tm_store_add_keyframes");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);
@@ -1228,9 +1229,14 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
 static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
                                   const tm_batch_inputs *in, const tm_search_params &sp,
                                   const tm_fuse_params &fp, tm_batch_result *res, cudaStream_t s) {
+    Range range("tm_batch_run");
     BatchBuf &B = c->batch;
     B.early_fork = sp.mode != TM_MODE_PER_PAIR;  // one-shot: nothing of this enqueue is captured
-    tm_status st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
+    tm_status st;
+    {
+        Range r("prepare_batch (work list, uploads)");
+        st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
+    }
     B.early_fork = false;
     if (st) {
         // copies of the caller's arrays may be in flight: done before the call returns
@@ -1251,7 +1257,10 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
         }
         st = enqueue_fused(c, B, th, ln, s);
     }
-    if (!st) st = fetch_results(c, B, res, s);
+    if (!st) {
+        Range r("fetch_results (downloads, wait)");
+        st = fetch_results(c, B, res, s);
+    }
     if (st) {
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(s);
@@ -1287,6 +1296,7 @@ extern "C" tm_status tm_search_triangulation(tm_ctx *c, uint64_t kf, const uint6
     tm_search_params_default(&sp);
     tm_fuse_params_default(&fp);
     if (params) sp = *params;
+    Range range("tm_search_triangulation");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     auto it = c->ids.find(kf);
@@ -1349,6 +1359,7 @@ extern "C" tm_status tm_fuse(tm_ctx *c, uint64_t kf, const tm_mappoint_view *mps
     tm_search_params_default(&sp);
     tm_fuse_params_default(&fp);
     if (params) fp = *params;
+    Range range("tm_fuse");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     tm_step st{};
@@ -1491,6 +1502,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
 }
 
 static tm_status plan_run(tm_plan *P, void *stream, bool timed) {
+    Range range(timed ? "tm_plan_run_timed" : "tm_plan_run");
     if (!P) return fail(TM_ERR_INVALID_ARG, "tm_plan_run: null plan");
     tm_ctx *c = P->ctx;
     cudaSetDevice(c->device);

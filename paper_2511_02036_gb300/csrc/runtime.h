@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <mutex>
@@ -14,6 +15,15 @@
 #include "tm.h"
 
 namespace tmap {
+
+// A host-side NVTX range over a scope: the library's calls and their stages appear on the
+// timeline of a profiler attached to the process (with none attached a push costs a few ns).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 struct DevBuf {
     void *p = nullptr;

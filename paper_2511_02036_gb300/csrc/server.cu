@@ -91,6 +91,7 @@ namespace {
 
 // Distribute the results of a finished flight to its requests.
 void retire(tm_server *S, Flight &F) {
+    Range range("tm_server retire (results to requests)");
     tm_ctx *c = S->ctx;
     tm_batch_result r{};
     r.matches = F.h_matches.data();
@@ -128,6 +129,7 @@ void retire(tm_server *S, Flight &F) {
 // Pack up to max_batch_requests pending requests into flight F and launch it.
 // Returns false when nothing could be admitted (store full or queue empty).
 bool admit(tm_server *S, Flight &F) {
+    Range range("tm_server admit + launch");
     tm_ctx *c = S->ctx;
     std::vector<Req *> take;
     {
