@@ -409,7 +409,9 @@ tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
  * Continuous batching.  A host thread admits submitted requests in arrival order as
  * in-flight batch slots and store memory allow, ingests their keyframes, and launches
  * each batch's search + fuse while earlier batches are still on the GPU (a ring of
- * streams).  A request's neighbours must be stored or belong to earlier requests. */
+ * streams).  A request's neighbours must be stored or belong to earlier requests.  A request
+ * may also carry its new keyframe's own map points for forward fusion into each neighbour
+ * (Sec. IV-D), and the server may triangulate every match (Sec. III), as tm_batch_run does. */
 typedef struct {
     int32_t max_batch_requests;   /* requests per launch (64)                               */
     int32_t max_inflight_batches; /* batches on the GPU at once (3)                         */
@@ -417,6 +419,8 @@ typedef struct {
     int32_t evict_after;          /* keep only the newest N keyframes of the stream, 0 = no */
     tm_search_params search;
     tm_fuse_params fuse;
+    int32_t triangulate;          /* 1: triangulate and check every match (tri below)       */
+    tm_triangulation_params tri;
 } tm_server_config;
 
 typedef struct {
@@ -427,6 +431,10 @@ typedef struct {
     const uint8_t *q_free;        /* [n] or NULL, copied                                    */
     const uint8_t *nbr_free;      /* [sum n_T] or NULL, copied                              */
     tm_mappoint_view mps;         /* fused into kf_id; copied (host arrays)                 */
+    tm_mappoint_view fwd_mps;     /* kf_id's own map points, fused into every neighbour;
+                                     copied; n = 0 for none (its skip array is not read)     */
+    const uint8_t *fwd_skip;      /* [n_nbrs][fwd_mps.n] or NULL: 1 = that neighbour already
+                                     observes the point (not fused into it); copied          */
 } tm_request;
 
 typedef struct {
@@ -434,6 +442,7 @@ typedef struct {
     tm_status status;
     int32_t n_matches, n_fuse;
     double t_submit, t_admit, t_done; /* seconds, monotonic clock                           */
+    int32_t n_fwd;                /* forward-fusion candidates                              */
 } tm_request_info;
 
 void tm_server_config_default(tm_server_config *c);
@@ -447,6 +456,13 @@ tm_status tm_server_poll(tm_server *srv, uint64_t ticket, double timeout_s,
  * [n_nbrs+1], fuse [n_fuse], then forgets the ticket. */
 tm_status tm_server_take(tm_server *srv, uint64_t ticket, tm_match *matches,
                          int32_t *pair_offsets, tm_fuse_match *fuse);
+/* The same with the forward-fusion and triangulation results: fwd [n_fwd] with fwd_offsets
+ * [n_nbrs + 1] (per neighbour, as pair_offsets), points [n_matches][3] float and point_ok
+ * [n_matches] (only with triangulate in the configuration; else not written).  Any output may
+ * be NULL. */
+tm_status tm_server_take_ex(tm_server *srv, uint64_t ticket, tm_match *matches,
+                            int32_t *pair_offsets, tm_fuse_match *fuse, tm_fuse_match *fwd,
+                            int32_t *fwd_offsets, float *points, uint8_t *point_ok);
 /* Drains the queue, stops the thread, frees the server. */
 tm_status tm_server_stop(tm_server *srv);
 

@@ -859,7 +859,7 @@ class Server:
     """Continuous-batching server (tm_server_*)."""
 
     def __init__(self, ctx, max_batch_requests=64, max_inflight_batches=3, queue_capacity=1 << 16,
-                 evict_after=0, sp=None, fp=None):
+                 evict_after=0, sp=None, fp=None, tri=None):
         self.ctx = ctx
         c = L.tm_server_config()
         tm_server_config_default(ctypes.byref(c))  # noqa: F821
@@ -869,12 +869,17 @@ class Server:
             c.search = sp.struct()
         if fp is not None:
             c.fuse = fp.struct()
+        if tri is not None:  # triangulate every match (TriParams)
+            c.triangulate, c.tri = 1, tri.struct()
+        self.triangulate = tri is not None
         h = ctypes.c_void_p()
         check(tm_server_start(ctx.handle, ctypes.byref(c), ctypes.byref(h)))  # noqa: F821
         self.handle = h
         self.meta = {}
 
-    def submit(self, kf_id, kf, nbrs, q_free=None, nbr_free=None, mps=None):
+    def submit(self, kf_id, kf, nbrs, q_free=None, nbr_free=None, mps=None, fwd_mps=None, fwd_skip=None):
+        """fwd_mps: the new keyframe's own map points, fused into every neighbour; fwd_skip: per
+        neighbour a byte per forward map point (1 = that neighbour already observes it)."""
         keep = []
         r = L.tm_request()
         r.kf_id = int(kf_id)
@@ -887,6 +892,13 @@ class Server:
         nf = _host(nbr_free, np.uint8)
         r.q_free, r.nbr_free = _ptr(qf), _ptr(nf)
         r.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
+        r.fwd_mps = mappoint_view(fwd_mps if fwd_mps is not None and fwd_mps["n"] else None, keep)
+        if fwd_skip is not None and r.fwd_mps.n:
+            fs = np.ascontiguousarray(np.concatenate([np.asarray(x, np.uint8).reshape(-1) for x in fwd_skip])
+                                      if isinstance(fwd_skip, (list, tuple)) else np.asarray(fwd_skip, np.uint8))
+            assert fs.size == len(nb) * r.fwd_mps.n
+            keep.append(fs)
+            r.fwd_skip = fs.ctypes.data
         t = ctypes.c_uint64()
         check(tm_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))  # noqa: F821
         self.meta[t.value] = (len(nb),)
@@ -911,6 +923,26 @@ class Server:
         f = np.zeros((max(1, info["n_fuse"]), 3), np.int32)
         check(tm_server_take(self.handle, ticket, m.ctypes.data, po.ctypes.data, f.ctypes.data))  # noqa: F821
         return _split(m[:info["n_matches"]], po), f[:info["n_fuse"]], info
+
+    def take_ex(self, ticket):
+        """Waits for the request; returns a dict: pairs (per neighbour), fuse, fwds (per
+        neighbour), points and point_ok (None unless the server triangulates), info."""
+        info = self.poll(ticket, timeout=600.0)
+        if not info["done"]:
+            raise TMError(TM_ERR_TIMEOUT, "request %d not done" % ticket)
+        n_nbrs = self.meta.pop(ticket)[0]
+        nm = info["n_matches"]
+        m = np.zeros((max(1, nm), 3), np.int32)
+        po = np.zeros(n_nbrs + 1, np.int32)
+        f = np.zeros((max(1, info["n_fuse"]), 3), np.int32)
+        fw = np.zeros((max(1, info["n_fwd"]), 3), np.int32)
+        fo = np.zeros(n_nbrs + 1, np.int32)
+        pts = np.zeros((max(1, nm), 3), np.float32) if self.triangulate else None
+        ok = np.zeros(max(1, nm), np.uint8) if self.triangulate else None
+        check(tm_server_take_ex(self.handle, ticket, m.ctypes.data, po.ctypes.data, f.ctypes.data,  # noqa: F821
+                                fw.ctypes.data, fo.ctypes.data, _ptr(pts), _ptr(ok)))
+        return dict(pairs=_split(m[:nm], po), fuse=f[:info["n_fuse"]], fwds=_split(fw[:info["n_fwd"]], fo),
+                    points=None if pts is None else pts[:nm], point_ok=None if ok is None else ok[:nm], info=info)
 
     def close(self):
         if self.handle:

@@ -97,7 +97,8 @@ class tm_batch_result(ctypes.Structure):
 class tm_server_config(ctypes.Structure):
     _fields_ = [("max_batch_requests", c_i32), ("max_inflight_batches", c_i32),
                 ("queue_capacity", c_i32), ("evict_after", c_i32),
-                ("search", tm_search_params), ("fuse", tm_fuse_params)]
+                ("search", tm_search_params), ("fuse", tm_fuse_params),
+                ("triangulate", c_i32), ("tri", tm_triangulation_params)]
 
 
 class tm_fuse_apply_stats(ctypes.Structure):
@@ -107,12 +108,13 @@ class tm_fuse_apply_stats(ctypes.Structure):
 
 class tm_request(ctypes.Structure):
     _fields_ = [("kf_id", c_u64), ("kf", tm_keyframe_view), ("nbr_ids", c_p), ("n_nbrs", c_i32),
-                ("q_free", c_p), ("nbr_free", c_p), ("mps", tm_mappoint_view)]
+                ("q_free", c_p), ("nbr_free", c_p), ("mps", tm_mappoint_view),
+                ("fwd_mps", tm_mappoint_view), ("fwd_skip", c_p)]
 
 
 class tm_request_info(ctypes.Structure):
     _fields_ = [("done", c_i32), ("status", c_i32), ("n_matches", c_i32), ("n_fuse", c_i32),
-                ("t_submit", c_f64), ("t_admit", c_f64), ("t_done", c_f64)]
+                ("t_submit", c_f64), ("t_admit", c_f64), ("t_done", c_f64), ("n_fwd", c_i32)]
 
 
 P = ctypes.POINTER
@@ -164,6 +166,7 @@ SIGNATURES = {
     "tm_server_submit": (c_i32, [c_p, P(tm_request), P(c_u64)]),
     "tm_server_poll": (c_i32, [c_p, c_u64, c_f64, P(tm_request_info)]),
     "tm_server_take": (c_i32, [c_p, c_u64, c_p, c_p, c_p]),
+    "tm_server_take_ex": (c_i32, [c_p, c_u64, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "tm_server_stop": (c_i32, [c_p]),
     "tm_now": (c_f64, []),
     "tm_search_pair_noalloc": (c_i32, [P(tm_camera), P(tm_keyframe_view), P(tm_keyframe_view),

@@ -37,12 +37,19 @@ struct Req {
     int n_mps = 0;
     std::vector<float> pos, normal, mind, maxd;
     std::vector<uint8_t> mdesc, skip;
+    int n_fwd = 0;  // the new keyframe's own map points, fused into every neighbour
+    std::vector<float> fpos, fnormal, fmind, fmaxd;
+    std::vector<uint8_t> fdesc, fskip;
     // results
     bool done = false;
     tm_status status = TM_OK;
     std::vector<tm_match> matches;
     std::vector<int32_t> pair_offsets;
     std::vector<tm_fuse_match> fuse;
+    std::vector<tm_fuse_match> fwd;
+    std::vector<int32_t> fwd_offsets;
+    std::vector<float> points;
+    std::vector<uint8_t> point_ok;
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
@@ -55,8 +62,10 @@ struct Flight {
     std::vector<int> new_slots;
     bool busy = false;
     std::vector<tm_match> h_matches;
-    std::vector<tm_fuse_match> h_fuse;
-    std::vector<int32_t> h_pair_off, h_fuse_off;
+    std::vector<tm_fuse_match> h_fuse, h_fwd;
+    std::vector<int32_t> h_pair_off, h_fuse_off, h_fwd_off;
+    std::vector<float> h_points;
+    std::vector<uint8_t> h_point_ok;
 };
 
 }  // namespace
@@ -85,6 +94,8 @@ extern "C" void tm_server_config_default(tm_server_config *c) {
     c->evict_after = 0;
     tm_search_params_default(&c->search);
     tm_fuse_params_default(&c->fuse);
+    c->triangulate = 0;
+    tm_triangulation_params_default(&c->tri);
 }
 
 namespace {
@@ -100,6 +111,14 @@ void retire(tm_server *S, Flight &F) {
     r.fuse_cap = F.h_fuse.size();
     r.pair_offsets = F.h_pair_off.data();
     r.fuse_offsets = F.h_fuse_off.data();
+    r.fwd = F.h_fwd.data();
+    r.fwd_cap = F.h_fwd.size();
+    r.fwd_offsets = F.h_fwd_off.data();
+    const bool tri = S->cfg.triangulate != 0;
+    if (tri) {
+        r.points = F.h_points.data();
+        r.point_ok = F.h_point_ok.data();
+    }
     tm_status st = fetch_results(c, F.B, &r, F.stream);
     const double now = tm_now();
     {
@@ -117,6 +136,15 @@ void retire(tm_server *S, Flight &F) {
             q->pair_offsets.resize(p1 - p0 + 1);
             for (int p = p0; p <= p1; ++p) q->pair_offsets[p - p0] = F.h_pair_off[p] - base;
             q->fuse.assign(F.h_fuse.begin() + F.h_fuse_off[k], F.h_fuse.begin() + F.h_fuse_off[k + 1]);
+            const int fb = F.h_fwd_off[p0];
+            q->fwd.assign(F.h_fwd.begin() + fb, F.h_fwd.begin() + F.h_fwd_off[p1]);
+            q->fwd_offsets.resize(p1 - p0 + 1);
+            for (int p = p0; p <= p1; ++p) q->fwd_offsets[p - p0] = F.h_fwd_off[p] - fb;
+            if (tri) {
+                const int me = F.h_pair_off[p1];
+                q->points.assign(F.h_points.begin() + 3 * (size_t)base, F.h_points.begin() + 3 * (size_t)me);
+                q->point_ok.assign(F.h_point_ok.begin() + base, F.h_point_ok.begin() + me);
+            }
         }
         q->t_done = now;
         q->done = true;
@@ -226,7 +254,7 @@ bool admit(tm_server *S, Flight &F) {
             std::vector<tm_step> steps(ok.size());
             std::vector<uint8_t> masks;
             size_t nm = 0;
-            for (Req *q : ok) nm += (size_t)q->n_mps;
+            for (Req *q : ok) nm += (size_t)q->n_mps + (size_t)q->n_fwd;
             std::vector<float> pos(3 * nm), normal(3 * nm), mind(nm), maxd(nm);
             std::vector<uint8_t> mdesc(32 * nm), skip(nm);
             size_t mo = 0;
@@ -261,6 +289,24 @@ bool admit(tm_server *S, Flight &F) {
                     }
                 }
                 mo += (size_t)q->n_mps;
+                // forward fusion: the request's own map points, after its backward ones (their
+                // skip flags stay 0: the per-neighbour skip bytes decide)
+                s.fwd_mp_begin = (int)mo;
+                s.fwd_mp_count = q->n_fwd;
+                s.fwd_skip_off = -1;
+                if (q->n_fwd) {
+                    const size_t f = (size_t)q->n_fwd;
+                    memcpy(&pos[3 * mo], q->fpos.data(), 12 * f);
+                    memcpy(&normal[3 * mo], q->fnormal.data(), 12 * f);
+                    memcpy(&mind[mo], q->fmind.data(), 4 * f);
+                    memcpy(&maxd[mo], q->fmaxd.data(), 4 * f);
+                    memcpy(&mdesc[32 * mo], q->fdesc.data(), 32 * f);
+                    if (!q->fskip.empty()) {
+                        s.fwd_skip_off = (int64_t)masks.size();
+                        masks.insert(masks.end(), q->fskip.begin(), q->fskip.end());
+                    }
+                }
+                mo += (size_t)q->n_fwd;
             }
             tm_batch_inputs in{};
             in.masks = masks.empty() ? nullptr : masks.data();
@@ -272,6 +318,7 @@ bool admit(tm_server *S, Flight &F) {
             in.mps.min_dist = mind.data();
             in.mps.max_dist = maxd.data();
             in.mps.skip = any_skip ? skip.data() : nullptr;
+            in.tri = S->cfg.triangulate ? &S->cfg.tri : nullptr;
             tm_status st = prepare_batch(c, F.B, steps.data(), (int)steps.size(), &in, S->cfg.search,
                                          S->cfg.fuse, F.stream);
             if (!st) {
@@ -313,6 +360,12 @@ bool admit(tm_server *S, Flight &F) {
     F.h_fuse.resize(pad);
     F.h_pair_off.resize(F.B.n_pairs + 1);
     F.h_fuse_off.resize(F.B.n_steps + 1);
+    F.h_fwd.resize(pad);
+    F.h_fwd_off.resize(F.B.n_pairs + 1);
+    if (S->cfg.triangulate) {
+        F.h_points.resize(3 * pad);
+        F.h_point_ok.resize(pad);
+    }
     return true;
 }
 
@@ -390,9 +443,11 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
     if (v.n > 0 && (!v.desc || !v.xy || !v.angle || !v.level || !v.node))
         return fail(TM_ERR_INVALID_ARG, "tm_server_submit: null keyframe array");
     if (r->n_nbrs < 0 || (r->n_nbrs > 0 && !r->nbr_ids)) return fail(TM_ERR_INVALID_ARG, "tm_server_submit: bad neighbours");
-    const tm_mappoint_view &m = r->mps;
+    const tm_mappoint_view &m = r->mps, &fm = r->fwd_mps;
     if (m.n < 0 || (m.n > 0 && (!m.pos || !m.normal || !m.desc || !m.min_dist || !m.max_dist)))
         return fail(TM_ERR_INVALID_ARG, "tm_server_submit: bad map points");
+    if (fm.n < 0 || (fm.n > 0 && (!fm.pos || !fm.normal || !fm.desc || !fm.min_dist || !fm.max_dist)))
+        return fail(TM_ERR_INVALID_ARG, "tm_server_submit: bad forward map points");
     auto q = std::make_unique<Req>();
     q->kf_id = r->kf_id;
     q->n = v.n;
@@ -435,6 +490,16 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
         q->maxd.assign(m.max_dist, m.max_dist + nm);
         if (m.skip) q->skip.assign(m.skip, m.skip + nm);
     }
+    q->n_fwd = fm.n;
+    const size_t nf = (size_t)fm.n;
+    if (nf) {
+        q->fpos.assign(fm.pos, fm.pos + 3 * nf);
+        q->fnormal.assign(fm.normal, fm.normal + 3 * nf);
+        q->fdesc.assign(fm.desc, fm.desc + 32 * nf);
+        q->fmind.assign(fm.min_dist, fm.min_dist + nf);
+        q->fmaxd.assign(fm.max_dist, fm.max_dist + nf);
+        if (r->fwd_skip) q->fskip.assign(r->fwd_skip, r->fwd_skip + nf * (size_t)r->n_nbrs);
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     if ((int)S->pending.size() >= S->cfg.queue_capacity) return fail(TM_ERR_BUSY, "server queue full");
     if (S->stopping) return fail(TM_ERR_BUSY, "server stopping");
@@ -459,6 +524,7 @@ extern "C" tm_status tm_server_poll(tm_server *S, uint64_t ticket, double timeou
     info->status = q->status;
     info->n_matches = (int32_t)q->matches.size();
     info->n_fuse = (int32_t)q->fuse.size();
+    info->n_fwd = (int32_t)q->fwd.size();
     info->t_submit = q->t_submit;
     info->t_admit = q->t_admit;
     info->t_done = q->t_done;
@@ -468,6 +534,12 @@ extern "C" tm_status tm_server_poll(tm_server *S, uint64_t ticket, double timeou
 
 extern "C" tm_status tm_server_take(tm_server *S, uint64_t ticket, tm_match *matches,
                                     int32_t *pair_offsets, tm_fuse_match *fuse) {
+    return tm_server_take_ex(S, ticket, matches, pair_offsets, fuse, nullptr, nullptr, nullptr, nullptr);
+}
+
+extern "C" tm_status tm_server_take_ex(tm_server *S, uint64_t ticket, tm_match *matches,
+                                       int32_t *pair_offsets, tm_fuse_match *fuse, tm_fuse_match *fwd,
+                                       int32_t *fwd_offsets, float *points, uint8_t *point_ok) {
     if (!S) return fail(TM_ERR_INVALID_ARG, "tm_server_take: null server");
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
@@ -482,6 +554,11 @@ extern "C" tm_status tm_server_take(tm_server *S, uint64_t ticket, tm_match *mat
     if (matches && !q->matches.empty()) memcpy(matches, q->matches.data(), q->matches.size() * sizeof(tm_match));
     if (pair_offsets) memcpy(pair_offsets, q->pair_offsets.data(), q->pair_offsets.size() * sizeof(int32_t));
     if (fuse && !q->fuse.empty()) memcpy(fuse, q->fuse.data(), q->fuse.size() * sizeof(tm_fuse_match));
+    if (fwd && !q->fwd.empty()) memcpy(fwd, q->fwd.data(), q->fwd.size() * sizeof(tm_fuse_match));
+    if (fwd_offsets && !q->fwd_offsets.empty())
+        memcpy(fwd_offsets, q->fwd_offsets.data(), q->fwd_offsets.size() * sizeof(int32_t));
+    if (points && !q->points.empty()) memcpy(points, q->points.data(), q->points.size() * sizeof(float));
+    if (point_ok && !q->point_ok.empty()) memcpy(point_ok, q->point_ok.data(), q->point_ok.size());
     S->reqs.erase(it);
     return TM_OK;
 }

@@ -96,3 +96,45 @@ def test_request_errors(tm, stream):
             # the same keyframe id again -> EXISTS
             t1 = srv.submit(s0["q"], w["frames"][s0["q"]], [])
             assert srv.poll(t1, timeout=60.0)["status"] == tm.TM_ERR_EXISTS
+
+
+@pytest.mark.parametrize("batch,skip", [(8, True), (1, False)])
+def test_forward_fusion_and_triangulation_served(tm, batch, skip):
+    """Requests carrying their new keyframe's own map points (forward fusion into every
+    neighbour, with or without per-neighbour skip bytes), served with triangulation on: every
+    output equals the oracle's (search, both fusion directions, points and acceptance)."""
+    w = W.make_cfg2(seed=4200, n_steps=6, forward=True)
+    old = sorted(set(i for s in w["steps"] for i in s["nbrs"]) - set(s["q"] for s in w["steps"]))
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        with ctx.server(max_batch_requests=batch, max_inflight_batches=2, tri=tm.TriParams()) as srv:
+            tickets = [srv.submit(st["q"], w["frames"][st["q"]], st["nbrs"], st["q_free"], st["nbr_free"],
+                                  st["mps"], fwd_mps=st["fwd_mps"], fwd_skip=st["fwd_skip"] if skip else None)
+                       for st in w["steps"]]
+            n_fwd = n_ok = 0
+            for st, t in zip(w["steps"], tickets):
+                r = srv.take_ex(t)
+                assert r["info"]["status"] == 0
+                exp, _ = O.search_step(w["cam"], w["frames"], st)
+                assert len(r["pairs"]) == len(exp)
+                for g, e in zip(r["pairs"], exp):
+                    np.testing.assert_array_equal(g, e)
+                fe, _ = O.fuse_step(w["cam"], w["frames"], st)
+                np.testing.assert_array_equal(r["fuse"], fe)
+                s2 = dict(st)
+                if not skip:
+                    s2["fwd_skip"] = None
+                efw, _ = O.fuse_forward_step(w["cam"], w["frames"], s2)
+                assert len(r["fwds"]) == len(efw)
+                for g, e in zip(r["fwds"], efw):
+                    np.testing.assert_array_equal(g, e)
+                    n_fwd += len(e)
+                off = 0
+                for f, e in zip(st["nbrs"], exp):
+                    xyz, ok = O.triangulate(w["cam"], w["frames"][st["q"]], w["frames"][f], e)
+                    np.testing.assert_array_equal(r["points"][off:off + len(e)], xyz)
+                    np.testing.assert_array_equal(r["point_ok"][off:off + len(e)], ok)
+                    off += len(e)
+                    n_ok += int(ok.sum())
+                assert off == len(r["points"])
+            assert n_fwd > 50 and n_ok > 50
