@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--seed", type=int, default=2000)
@@ -69,14 +69,20 @@ class Clocks:
         self.index = index  # nvidia-smi -i accepts an index or a GPU UUID
         self.proc = None
         self.lines = []
+        self.skip = 0  # readings taken before the timed region
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # the first reading marks the start of sampling: the timed region starts after it
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)
+            self.skip = len(self.lines)
         except OSError:
             self.proc = None
 
@@ -95,7 +101,7 @@ class Clocks:
         self.th.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:] or self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
