@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--seed", type=int, default=2000)
@@ -257,7 +257,9 @@ def run_reference(args, rank, world):
     from gen import workloads as W
     import oracle as O
     w = W.make_cfg2(seed=args.seed)
-    per = 4  # local-mapping steps (keyframes) per timed step: a bounded sample of the batch
+    # local-mapping steps (keyframes) per timed step: a bounded sample of the batch, about 800
+    # oracle steps in all (half a minute on one core) whatever K is, and at least one per step
+    per = max(1, min(4, 800 // max(1, args.steps)))
     for _ in range(args.warmup):
         oracle_sample(w, 0.0, t_limit=1)
     t0 = time.perf_counter()
