@@ -404,6 +404,12 @@ tm_status tm_plan_destroy(tm_plan *plan);
 #define TM_DEBUG_WAIT_LIMIT 1
 #define TM_DEBUG_STARVE_WAITS 2
 tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
+/* Bounds-checking builds (compiled with -DTM_DEBUG_BOUNDS; the normal build sets *enabled = 0
+ * and *site = 0): every index the kernels take from data (bucket tables, grid lists, match and
+ * query lists) is checked against its array; *site is the first failed check (0 = none), and
+ * the failed index was clamped into range.  reset = 1 clears it after reading.  Reads the
+ * current device's status. */
+tm_status tm_debug_bounds(int32_t reset, uint32_t *site, int32_t *enabled);
 
 /* ---------------------------------------------------------------------------- serving
  * Continuous batching.  A host thread admits submitted requests in arrival order as

@@ -156,6 +156,7 @@ SIGNATURES = {
                                P(tm_fuse_params), P(c_p)]),
     "tm_plan_run": (c_i32, [c_p, c_p]),
     "tm_debug_set": (c_i32, [c_p, c_i32, ctypes.c_int64]),
+    "tm_debug_bounds": (c_i32, [c_i32, P(ctypes.c_uint32), P(c_i32)]),
     "tm_plan_run_timed": (c_i32, [c_p, c_p]),
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),

@@ -19,6 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtm.so")
+# the bounds-checking variant (-DTM_DEBUG_BOUNDS): for tests, loaded through TM_LIBRARY
+LIB_BOUNDS = os.path.join(PKG, "libtm_bounds.so")
 SOURCES = ["kernels.cu", "runtime.cu", "server.cu", "culling.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false and -ffp-contract=off: no contraction anywhere (device and host code), so every
@@ -42,17 +44,22 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False):
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, bounds=False):
+    """Compiles the library (bounds=True: the bounds-checking variant, objects and library
+    apart from the normal build's)."""
+    out_dir = os.path.join(OUT_DIR, "bounds") if bounds else OUT_DIR
+    lib = LIB_BOUNDS if bounds else LIB
+    extra = ["-DTM_DEBUG_BOUNDS"] if bounds else []
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "tm.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -64,11 +71,11 @@ def build(force=False, verbose=False):
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

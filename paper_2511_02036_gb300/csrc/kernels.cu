@@ -22,9 +22,31 @@
 
 namespace tmap {
 
+// Bounds-checking build (-DTM_DEBUG_BOUNDS): every index that comes from data (bucket tables,
+// grid lists, match lists, query lists) is checked against the array it indexes before use;
+// the first failed check records its site here and the index is clamped into range, so that
+// the run completes and the host reads the site (tm_debug_bounds).  In the normal build the
+// check is the identity.
+#ifdef TM_DEBUG_BOUNDS
+__device__ unsigned int g_bounds_site;
+#endif
+
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int guard(int i, int n, unsigned site) {
+#ifdef TM_DEBUG_BOUNDS
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_bounds_site, 0u, site);
+        return n > 0 ? (i < 0 ? 0 : n - 1) : 0;
+    }
+#else
+    (void)n;
+    (void)site;
+#endif
+    return i;
+}
 
 // ------------------------------------------------------------------------- arithmetic
 
@@ -442,7 +464,7 @@ __global__ void __maxnreg__(40) ingest_kernel(IngestArgs A) {
     uint16_t *pos = reinterpret_cast<uint16_t *>(base + L.pos);
     uint8_t *level = base + L.level;
     for (int p = tid; p < n; p += bs) {
-        const uint32_t o = ord[p];
+        const uint32_t o = (uint32_t)guard(ord[p], n, 19);
         const uint32_t s = job.src + o;
         const uint4 d0 = A.desc[2 * s], d1 = A.desc[2 * s + 1];
         const float2 v = A.xy[s];
@@ -634,7 +656,7 @@ __device__ __forceinline__ MapPoint load_mp(const float *pos, const float *norma
     return q;
 }
 
-__device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &cam,
+__device__ __forceinline__ uint32_t fuse_one(const KfView &T, int nT, const CamConst &cam,
                                              const FuseConst &fp, const FuseK &K,
                                              const MapPoint &q, uint32_t &cmp) {
     const float X = q.X, Y = q.Y, Z = q.Z;
@@ -668,9 +690,9 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, const CamConst &ca
     uint32_t best = kNone;  // (dist << 16) | caller keypoint index
     for (int cy = cy0; cy <= cy1; ++cy) {
         const int c0 = cy * kGridCols + cx0, c1 = cy * kGridCols + cx1;
-        const int k0 = T.grid_start[c0], k1 = T.grid_start[c1 + 1];
+        const int k0 = T.grid_start[c0], k1 = guard(T.grid_start[c1 + 1], nT + 1, 11);
         for (int k = k0; k < k1; ++k) {
-            const int j = T.grid_items[k];
+            const int j = guard(T.grid_items[k], nT, 12);
             const int lv = T.level[j];
             if (lv != pl && lv != pl - 1) continue;
             const float2 xt = T.xy[j];
@@ -769,7 +791,8 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     const uint32_t key = w.qraw ? node_key(nk) : nk;
     const uint32_t b = key >> (32 - kBucketBits);
     int lo = bst[b];
-    const int be = bst[b + 1];
+    const int be = guard(bst[b + 1], (int)w.nt + 1, 1);
+    lo = guard(lo, be + 1, 2);
     while (lo < be && tkey[lo] < key) ++lo;
     int hi = lo;
     while (hi < be && tkey[hi] == key) ++hi;
@@ -809,10 +832,10 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
         li.b = __shfl_sync(kFull, l.b, i);
         li.c = __shfl_sync(kFull, l.c, i);
         const bool valid = k < total;
-        const int j0 = valid ? (int)epos[e0] : 0;
+        const int j0 = valid ? guard((int)epos[guard(e0, (int)w.nt, 3)], (int)w.nt, 4) : 0;
         uint32_t bk = kNone, sc = 0xFFFFu;
         if (valid) {
-            const int pq = p0 + i;
+            const int pq = guard(p0 + i, (int)w.nq, 5);
             const uint4 a0 = w.qdesc[2 * pq], a1 = w.qdesc[2 * pq + 1];
             const uint4 t0 = T.desc[2 * j0], t1 = T.desc[2 * j0 + 1];
             const float2 xt = T.xy[j0];
@@ -849,7 +872,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             if (ok && A.sp.ratio_num != 0 && v.y != 0xFFFFu)
                 ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * v.y;
             if (ok) {
-                const uint32_t j = v.x & 0xFFFFu;
+                const uint32_t j = (uint32_t)guard((int)(v.x & 0xFFFFu), (int)w.nt, 6);
                 a = (j << 16) | best;
                 if (A.sp.resolve) atomicMin(&win[j], (best << 16) | io);
             }
@@ -1119,7 +1142,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
             const int rows = min(qn - head, kDenseRows);
             if (rows == 0) break;  // every position scanned and every listed query done
             const bool mine = row < rows;
-            const int p = mine ? (int)qlist[head + row] : 0;
+            const int p = mine ? guard((int)qlist[head + row], (int)w.nq, 18) : 0;
             Line l{};
             float den = 0.0f;
             uint32_t bk = kNone, sc = 0xFFFFu;
@@ -1371,9 +1394,9 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         const int e = e0 + tid;
         uint32_t bin = kNone;
         if (e < na) {
-            const int p = alist[e];
-            const uint32_t ac = acc[p], j = ac >> 16, d = ac & 0xFFFFu;
-            const uint32_t io = w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p;
+            const int p = guard(alist[e], nQ, 7);
+            const uint32_t ac = acc[p], j = (uint32_t)guard((int)(ac >> 16), nT, 8), d = ac & 0xFFFFu;
+            const uint32_t io = (uint32_t)guard(w.qorig ? (int)w.qorig[p] : p, nQ, 9);
             if (!A.sp.resolve || win[j] == ((d << 16) | io)) {
                 bin = rot ? (uint32_t)rot_bin(w.qangle[p], T.angle[j], A.sp.rot_mode) : 0u;
                 fres[io] = pack_res(T.orig[j], d, bin);
@@ -1414,7 +1437,7 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
         const unsigned m = __ballot_sync(kFull, f);
         if (f) {
-            const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+            const uint32_t pos = (uint32_t)guard((int)(base + __popc(m & ((1u << lane) - 1u))), min(nQ, nT), 10);
             A.padded[w.out_off + pos] = Out3{q, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
         }
         base += __popc(m);
@@ -1489,11 +1512,12 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     T.orig = reinterpret_cast<const uint16_t *>(fsm + FS.orig);
     T.level = fsm + FS.level;
     uint32_t cmp = 0, r = kNone;
-    if (have) r = fuse_one(T, A.cam, A.fp, K, mp, cmp);
+    if (have) r = fuse_one(T, nT, A.cam, A.fp, K, mp, cmp);
     warp_count(cmp, &scmp);
     uint32_t tot;
     const uint32_t pos = block_scan_flag(r != kNone, wtot, tot);
-    if (r != kNone) A.padded[w.out_off + pos] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
+    if (r != kNone)
+        A.padded[w.out_off + (uint32_t)guard((int)pos, (int)w.b, 13)] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
     if (tid == 0) {
         A.counts[item] = tot;
         A.item_cmp[item] = scmp;
@@ -1565,7 +1589,9 @@ __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
     const float fr = __double2float_rn(A.tri_ratio);
     for (uint32_t k = o0 + (uint32_t)tid; k < o1; k += blockDim.x) {
         const Out3 m = A.dense[k];
-        const int pq = Q.pos[m.a], pt = T.pos[m.b];  // (q_idx, t_idx, dist) in caller order
+        // (q_idx, t_idx, dist) in caller order
+        const int pq = guard(Q.pos[guard(m.a, (int)w.nq, 14)], (int)w.nq, 15);
+        const int pt = guard(T.pos[guard(m.b, (int)w.nt, 16)], (int)w.nt, 17);
         const float2 xq = Q.xy[pq], xt = T.xy[pt];
         const int lev[2] = {Q.level[pq], T.level[pt]};
         const float u[2] = {xq.x, xt.x}, vv[2] = {xq.y, xt.y};
@@ -1839,7 +1865,7 @@ __global__ void fuse_plain_kernel(const unsigned char *ts, int cap, const float 
     if (m < n) {
         uint32_t r = kNone;
         if (!(skip && skip[m]))
-            r = fuse_one(T, cam, fp, K, load_mp(pos + 3 * (size_t)m, normal + 3 * (size_t)m,
+            r = fuse_one(T, T.hdr->n, cam, fp, K, load_mp(pos + 3 * (size_t)m, normal + 3 * (size_t)m,
                                                 desc + 2 * (size_t)m, mn[m], mx[m]), cmp);
         res[m] = r;
     }
@@ -1955,6 +1981,23 @@ cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s) {
     if (!a.triangulate || a.n_search == 0) return cudaSuccess;
     tri_kernel<<<a.n_search, 128, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t debug_bounds(bool reset, uint32_t *site, bool *enabled) {
+#ifdef TM_DEBUG_BOUNDS
+    *enabled = true;
+    cudaError_t e = cudaMemcpyFromSymbol(site, g_bounds_site, sizeof(uint32_t));
+    if (e == cudaSuccess && reset) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_bounds_site, &zero, sizeof zero);
+    }
+    return e;
+#else
+    (void)reset;
+    *enabled = false;
+    *site = 0u;
+    return cudaSuccess;
+#endif
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {

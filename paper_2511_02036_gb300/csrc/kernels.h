@@ -28,6 +28,9 @@ size_t dense_smem_bytes();
 cudaError_t launch_dense(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
+// Bounds-checking build: the first failed index check's site (0: none), optionally reset;
+// enabled = false and site = 0 in the normal build.
+cudaError_t debug_bounds(bool reset, uint32_t *site, bool *enabled);
 // Triangulation of every match of the batch (a.triangulate; after the copy kernel: reads the
 // offsets and the dense matches).
 cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s);

@@ -1396,6 +1396,14 @@ struct tm_plan {
     bool timed_last = false;  // the last run was tm_plan_run_timed
 };
 
+extern "C" tm_status tm_debug_bounds(int32_t reset, uint32_t *site, int32_t *enabled) {
+    if (!site || !enabled) return fail(TM_ERR_INVALID_ARG, "tm_debug_bounds: null argument");
+    bool en = false;
+    cudaError_t e = debug_bounds(reset != 0, site, &en);
+    *enabled = en ? 1 : 0;
+    return e == cudaSuccess ? TM_OK : cuda_fail(e, "bounds status");
+}
+
 extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
     if (!c) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: null context");
     std::lock_guard<std::mutex> lk(c->mu);

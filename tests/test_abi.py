@@ -206,3 +206,10 @@ def test_pack_batch_forward_fusion_ranges():
     assert list(masks[15:21]) == [1, 0, 0, 0, 0, 1] and len(masks) == 21
     assert mps["n"] == 12 and mps["pos"][7, 0] == 2.0 and mps["pos"][10, 0] == 3.0
     assert tm._fwd_cap(steps) == 3 * 2
+
+
+def test_normal_build_has_no_bounds_checks(lib):
+    """tm_debug_bounds in the normal build: checks off, nothing recorded (no GPU call)."""
+    site, en = ctypes.c_uint32(7), ctypes.c_int32(7)
+    assert lib.tm_debug_bounds(1, ctypes.byref(site), ctypes.byref(en)) == 0
+    assert (site.value, en.value) == (0, 0)

@@ -1,0 +1,91 @@
+"""The bounds-checking build (-DTM_DEBUG_BOUNDS): every index the kernels take from data is
+checked against its array and the first failure is recorded.  Small workloads through every
+kernel (ingest in the store and inside a batch, search in both forms, dense tensor-core blocks,
+backward and forward fusion, triangulation, copy) must leave no failed check and give the
+oracle's results.  Runs in a child process that loads the variant through TM_LIBRARY."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SCRIPT = r'''
+import ctypes
+import numpy as np
+import paper_2511_02036_gb300 as tm
+import oracle as O
+from gen import workloads as W
+
+def site():
+    s, en = ctypes.c_uint32(), ctypes.c_int32()
+    tm.check(tm._clib.tm_debug_bounds(0, ctypes.byref(s), ctypes.byref(en)))
+    return s.value, en.value
+
+assert tm.LIB_PATH.endswith("libtm_bounds.so"), tm.LIB_PATH
+assert site() == (0, 1), site()
+
+def check_pairs(got, exp):
+    assert len(got) == len(exp)
+    for g, e in zip(got, exp):
+        np.testing.assert_array_equal(g, e)
+
+w = W.make_cfg2(seed=2150, n_steps=4, forward=True)
+old = sorted(set(i for s in w["steps"] for i in s["nbrs"]) - set(s["q"] for s in w["steps"]))
+new = [s["q"] for s in w["steps"]]
+exp_pairs = [p for st in w["steps"] for p in O.search_step(w["cam"], w["frames"], st)[0]]
+exp_fuse = [O.fuse_step(w["cam"], w["frames"], st)[0] for st in w["steps"]]
+exp_fwd = [p for st in w["steps"] for p in O.fuse_forward_step(w["cam"], w["frames"], st)[0]]
+steps = [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s["q_free"], nbr_free=s["nbr_free"], mps=s["mps"],
+              fwd_mps=s["fwd_mps"], fwd_skip=s["fwd_skip"]) for s in w["steps"]]
+with tm.Context(w["cam"], max_kp=2048) as ctx:
+    ctx.add_keyframes(old, [w["frames"][i] for i in old])
+    for mode, with_new in ((tm.TM_MODE_FUSED, True), (tm.TM_MODE_FUSED, False), (tm.TM_MODE_PER_PAIR, False)):
+        kw = dict(new=(new, [w["frames"][i] for i in new])) if with_new else {}
+        if not with_new and not all(i in ctx.sizes for i in new):
+            ctx.add_keyframes(new, [w["frames"][i] for i in new])
+        res = ctx.batch_run(steps, sp=tm.SearchParams(mode=mode), tri=tm.TriParams(), **kw)
+        check_pairs(res.pairs, exp_pairs)
+        check_pairs(res.fuses, exp_fuse)
+        check_pairs(res.fwds, exp_fwd)
+        p = 0
+        for st in w["steps"]:
+            for f in st["nbrs"]:
+                xyz, ok = O.triangulate(w["cam"], w["frames"][st["q"]], w["frames"][f], exp_pairs[p])
+                a, b = res.pair_offsets[p], res.pair_offsets[p + 1]
+                np.testing.assert_array_equal(res.points[a:b], xyz)
+                np.testing.assert_array_equal(res.point_ok[a:b], ok)
+                p += 1
+        if with_new:
+            ctx.remove_keyframes(new)
+        assert site() == (0, 1), (mode, with_new, site())
+
+d = W.make_cfg3b(n_nbrs=4)
+st = d["steps"][0]
+ids = [st["q"]] + list(st["nbrs"])
+with tm.Context(d["cam"], max_kp=2048) as ctx:
+    ctx.add_keyframes(ids, [d["frames"][i] for i in ids])
+    for dmin in (16, 64):
+        got, ncmp = ctx.search(st["q"], st["nbrs"], st.get("q_free"), st.get("nbr_free"), tm.SearchParams(dense_min=dmin))
+        exp, ecmp = O.search_step(d["cam"], d["frames"], st)
+        check_pairs(got, exp)
+        assert ncmp == ecmp
+assert site() == (0, 1), site()
+print("bounds clean")
+'''
+
+
+def test_bounds_checked_build_runs_clean():
+    import __graft_entry__ as g
+    g.build()
+    sys.path.insert(0, os.path.join(ROOT, "paper_2511_02036_gb300"))
+    import build as B
+    lib = B.build(bounds=True)
+    env = dict(os.environ, TM_LIBRARY=lib)
+    r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, (r.stdout + r.stderr)[-4000:]
+    assert "bounds clean" in r.stdout
