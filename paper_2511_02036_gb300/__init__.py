@@ -124,22 +124,34 @@ def keyframe_views(kfs, keep):
     return v
 
 
+_KF_PACKED = (("desc", np.uint8), ("xy", np.float32), ("angle", np.float32), ("level", np.uint8),
+              ("node", np.uint32))
+_KF_PACKED_ELT = np.array([32, 8, 4, 1, 4], np.int64)  # bytes per keypoint of each array
+_KF_PACKED_COL = [_KF_DT.fields[name][1] // 8 for name, _ in _KF_PACKED]
+
+
 def keyframe_views_packed(packed, keep):
     """tm_keyframe_view records for keyframes packed one after another in one array per field:
     packed = dict(n=[counts], desc (N, 32), xy (N, 2), angle (N,), level (N,), node (N,),
     Tcw (k, 12) or (k, 3, 4)); numpy arrays or torch tensors (host or device)."""
     n = np.asarray(packed["n"], np.int64).reshape(-1)
     k = len(n)
-    start = np.concatenate([[0], np.cumsum(n)[:-1]]) if k else np.zeros(0, np.int64)
     v = np.zeros(max(1, k), _KF_DT)
-    v["n"][:k] = n
-    for name, dt, elt in (("desc", np.uint8, 32), ("xy", np.float32, 8), ("angle", np.float32, 4),
-                          ("level", np.uint8, 1), ("node", np.uint32, 4)):
-        a = _host(packed[name], dt)
-        keep.append(a)
-        v[name][:k] = np.where(n > 0, (_ptr(a) or 0) + elt * start, 0)
-    if k:
-        v["Tcw"][:k] = np.asarray(packed["Tcw"], np.float64).reshape(k, 12)
+    if not k:
+        return v
+    start = np.cumsum(n) - n
+    # the records as rows of 64-bit words: the five pointer columns in one broadcast, the pose
+    # written whole (a few array operations whatever the number of keyframes)
+    words = v.view(np.int64).reshape(len(v), _KF_DT.itemsize // 8)
+    arrs = [_host(packed[name], dt) for name, dt in _KF_PACKED]
+    keep.extend(arrs)
+    base = np.array([_ptr(a) or 0 for a in arrs], np.int64)
+    cols = base + start[:, None] * _KF_PACKED_ELT
+    cols[n == 0] = 0
+    words[:, _KF_PACKED_COL] = cols
+    t0 = _KF_DT.fields["Tcw"][1] // 8
+    words[:, t0:t0 + 12] = np.ascontiguousarray(packed["Tcw"], np.float64).reshape(k, 12).view(np.int64)
+    v["n"] = n
     keep.append(v)
     return v
 
