@@ -347,10 +347,23 @@ tm_status tmap::validate_view(tm_ctx *c, const tm_keyframe_view &v) {
         return fail(TM_ERR_INVALID_ARG, "keyframe has %d keypoints, capacity %d", v.n, c->cap);
     if (v.n > 0 && (!v.desc || !v.xy || !v.angle || !v.level || !v.node))
         return fail(TM_ERR_INVALID_ARG, "keyframe arrays must be non-null");
-    if (v.n > 0 && !is_device_ptr(v.level))
-        for (int i = 0; i < v.n; ++i)
-            if (v.level[i] >= TM_LEVELS)
-                return fail(TM_ERR_INVALID_ARG, "keypoint %d has level %d >= %d", i, v.level[i], TM_LEVELS);
+    if (v.n > 0 && !is_device_ptr(v.level)) {
+        // levels 0..7 use the low three bits only: or the bytes together 8 at a time, and
+        // look for the offending keypoint only if some byte has a higher bit set
+        static_assert(TM_LEVELS == 8, "the level check assumes 8 levels");
+        uint64_t any = 0;
+        int i = 0;
+        for (; i + 8 <= v.n; i += 8) {
+            uint64_t w;
+            memcpy(&w, v.level + i, 8);
+            any |= w;
+        }
+        for (; i < v.n; ++i) any |= v.level[i];
+        if (any & 0xF8F8F8F8F8F8F8F8ull)
+            for (i = 0; i < v.n; ++i)
+                if (v.level[i] >= TM_LEVELS)
+                    return fail(TM_ERR_INVALID_ARG, "keypoint %d has level %d >= %d", i, v.level[i], TM_LEVELS);
+    }
     return TM_OK;
 }
 
@@ -627,12 +640,14 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     // pose of a keyframe as the search kernel reads it: from the slot header, or from the
     // ingest job of a keyframe entering with this batch (so that the search need not wait for
     // its ingest)
-    std::unordered_map<int, int> new_index;
-    for (size_t k = 0; k < new_slots.size(); ++k) new_index[new_slots[k]] = (int)k;
+    // slot -> position among the keyframes entering with this batch, -1 for stored ones
+    std::vector<int> &new_index = B.new_index;
+    new_index.assign(c->slots.size(), -1);
+    for (size_t k = 0; k < new_slots.size(); ++k) new_index[(size_t)new_slots[k]] = (int)k;
     auto pose_of = [&](int slot) -> const double * {
-        auto it = new_index.find(slot);
-        const unsigned char *p = it != new_index.end()
-            ? reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) + sizeof(IngestJob) * (size_t)it->second +
+        const int ni = new_index[(size_t)slot];
+        const unsigned char *p = ni >= 0
+            ? reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) + sizeof(IngestJob) * (size_t)ni +
                   offsetof(IngestJob, Tcw)
             : c->slots[slot].ptr + offsetof(KfHeader, Tcw);
         return reinterpret_cast<const double *>(p);
@@ -644,10 +659,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     struct QView { const uint4 *desc; const float2 *xy; const uint32_t *node; const uint16_t *orig;
                    const float *angle; uint32_t raw; };
     auto qview_of = [&](int slot) -> QView {
-        auto it = new_index.find(slot);
-        if (it != new_index.end()) {
+        const int ni = new_index[(size_t)slot];
+        if (ni >= 0) {
             const IngestArgs &a = B.ingest_args;
-            const uint32_t src = B.ingest.src[(size_t)it->second];
+            const uint32_t src = B.ingest.src[(size_t)ni];
             return QView{a.desc + 2 * (size_t)src, a.xy + src, a.node + src, nullptr, a.angle + src, 1u};
         }
         const unsigned char *b = c->slots[slot].ptr;
@@ -702,11 +717,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.q = qptr;
             w.t = c->slots[ts].ptr;
             w.pq = pq;
-            const auto tn = new_index.find(ts);
-            w.pt = tn != new_index.end()
-                ? reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(B.ingest_args.jobs) +
-                                                   sizeof(IngestJob) * (size_t)tn->second + offsetof(IngestJob, Tcw))
-                : reinterpret_cast<const double *>(c->slots[ts].ptr + offsetof(KfHeader, Tcw));
+            const bool t_new = new_index[(size_t)ts] >= 0;
+            w.pt = pose_of(ts);
             w.mdepth = S.nbr_median_depth ? S.nbr_median_depth[j] : 0.0f;
             w.qdesc = qv.desc;
             w.qxy = qv.xy;
@@ -714,7 +726,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.qorig = qv.orig;
             w.qangle = qv.angle;
             w.qraw = qv.raw;
-            B.nbr_new |= tn != new_index.end();
+            B.nbr_new |= t_new;
             w.kind = kItemSearch;
             w.out_off = pad;
             w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;

@@ -68,6 +68,7 @@ struct BatchBuf {
     std::vector<WorkItem> h_items;
     std::vector<int> item_nq, item_nt;
     std::vector<int> step_pair_begin, step_fuse_item, slots;
+    std::vector<int> new_index;    // slot -> position among the new keyframes, -1 (work list)
     std::vector<int> pair_fwd_item;  // [pairs + 1] first forward-fusion item of each pair
     uint32_t n_bwd_items = 0;        // fusion items into the new keyframes
     uint32_t search_pad = 0;         // padded output entries of the search items
