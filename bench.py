@@ -469,12 +469,16 @@ def run_mine(args, rank, world, local_rank):
                      node=pin(np.concatenate([f["node"] for f in fr]).view(np.int32)),
                      Tcw=np.stack([np.asarray(f["Tcw"], np.float64).reshape(12) for f in fr]))
         # bytes copied in per step: masks, map-point arrays, the new keyframes' arrays
-        # (desc 32 + xy 8 + angle 4 + level 1 + node 4 = 49 B per keypoint), the work list
+        # (desc 32 + xy 8 + angle 4 + level 1 + node 4 = 49 B per keypoint), the work list (the
+        # library's 128-byte work records: every item, and the search items once more in launch
+        # order) and the new keyframes' ingest and gather records (112 + 48 B each)
+        n_pairs = sum(len(s["nbrs"]) for s in steps)
+        n_items = n_pairs + sum((s["mps"]["n"] + 255) // 256 for s in steps)
         h2d = (int(masks.nbytes) + sum(int(v.nbytes) for v in mps.values() if isinstance(v, np.ndarray))
-               + sum(w["frames"][i]["n"] for i in new_ids) * 49)
-        n_items = sum(len(s["nbrs"]) for s in steps) + sum((s["mps"]["n"] + 255) // 256 for s in steps)
-        h2d += n_items * 44
-        d2h = 4 * (n_items + 1) + 16 + OUT_BYTES * (len(res.matches) + len(res.fuse))
+               + sum(w["frames"][i]["n"] for i in new_ids) * 49
+               + (n_items + n_pairs) * 128 + len(new_ids) * (112 + 48))
+        # out: item offsets, comparison totals (3 x 8 B) and the status word, the results
+        d2h = 4 * (n_items + 1) + 24 + 4 + OUT_BYTES * (len(res.matches) + len(res.fuse))
 
         # the step table as columns (how a producer of batches hands it over; built once here
         # because every timed step runs the same batch)
