@@ -1,12 +1,17 @@
-"""Oracle for the correspondence search (Sec. IV-C) and fusion search (Sec. IV-D).
+"""Oracle for the correspondence search (Sec. IV-C), the fusion search (Sec. IV-D), the
+triangulation checks of Map Point Creation (Sec. III), the keyframe-culling redundancy test
+(Sec. IV-F) and the sequential fuse-apply stage (Sec. IV-D).
 
 TEST INFRASTRUCTURE ONLY.  A plain, slow, obviously-correct CPU definition (C, in
-`tm_oracle.c`) plus this ctypes wrapper.  Only the tests, the smoke check and the benchmark's
-CPU-baseline / reference arm load it; the library never does, and it shares no code with the
-CUDA path.
+`tm_oracle.c`; the culling test and the fuse-apply map in plain Python below) plus this ctypes
+wrapper.  Only the tests, the smoke check and the benchmark's CPU-baseline / reference arm
+load it; the library never does, and it shares no code with the CUDA path.
 
-Parity pins: see tests/test_oracle_pins.py (brute force, closed forms, planted geometry,
-hand-worked golden cases under tests/golden/).
+Parity pins: tests/test_oracle_pins.py (brute force, closed forms, planted geometry,
+hand-worked golden cases under tests/golden/), tests/test_oracle_mutations.py (planted
+mistakes caught), tests/test_fuse_apply.py (a hand-worked fuse-apply and culling case, the
+map's consistency invariants).  Unpinned beyond hand-worked cases: the exact 3:5 ratio tie and
+the rotation-bin boundaries (readings, not facts of the paper).
 """
 
 from __future__ import annotations
