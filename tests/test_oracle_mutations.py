@@ -1,13 +1,14 @@
 """The oracle's pins must catch plausible mistakes: each mutation below plants one bug in a
-copy of the oracle's C source (on the CPU), and at least one pin must then fail."""
+copy of the oracle's C source (on the CPU), or in its fuse-apply map, and at least one pin
+must then fail."""
 
 import os
 import shutil
-import tempfile
 
 import pytest
 
 import oracle as O
+from tests import test_fuse_apply as FA
 from tests import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(O.__file__), "tm_oracle.c")
@@ -44,6 +45,18 @@ MUTATIONS = [
     ("fuse ignores skip", "if (skip && skip[m]) continue;", ""),
     ("fuse u uses fy", "float u = fx * x + cx, v = fy * y + cy;", "float u = fy * x + cy, v = fy * y + cy;"),
     ("search ignores target mask", "if (free_t && !free_t[j]) continue;", ""),
+    ("ORB bins floored", "(int)roundf(rot * (1.0f / 30.0f))", "(int)floorf(rot * (1.0f / 30.0f))"),
+    ("epipole from the centre's mirror", "        cq[k] = -s;", "        cq[k] = s;"),
+    ("epipole x uses cy", "e[0] = (float)(cam->fx * (c[0] / c[2]) + cam->cx);",
+     "e[0] = (float)(cam->fx * (c[0] / c[2]) + cam->cy);"),
+    ("baseline skip inverted", "if (base / (double)p->t_median_depth < (double)p->baseline_min_ratio) {",
+     "if (base / (double)p->t_median_depth > (double)p->baseline_min_ratio) {"),
+    ("midpoint parameter sign", "const float s1 = (b * e - c2 * d) / den", "const float s1 = (c2 * d - b * e) / den"),
+    ("parallax bound dropped", "if (!(cosp > 0.0f && cosp < cos_max)) continue;", "if (!(cosp > 0.0f)) continue;"),
+    ("reprojection in one view only",
+     "        if (!orc_view_ok(cam, &V[1], X, u[1], vv[1], chi2 * sigma2[lev[1]])) continue;\n", ""),
+    ("scale consistency dropped",
+     "if (ratio_dist * f < ratio_octave || ratio_dist > ratio_octave * f) continue;", ""),
 ]
 
 PINS = [
@@ -51,13 +64,19 @@ PINS = [
     lambda: P.test_hamming_argmin_brute_force(0), lambda: P.test_node_buckets_brute_force(1),
     lambda: P.test_fundamental_epipolar_constraint(0), lambda: P.test_epipolar_gate_geometric(0),
     lambda: P.test_planted_recovery(0), P.test_step_invariants,
-    lambda: P.test_fuse_gates_geometric(0), P.test_fuse_planted,
+    lambda: P.test_fuse_gates_geometric(0), P.test_fuse_planted, P.test_forward_fusion_skip_and_independence,
+    P.test_orb_rotation_bins_golden, lambda: P.test_epipole_on_every_epipolar_line(0),
+    P.test_epipole_rejection_invariants, P.test_triangulation_recovers_exact_points,
+    P.test_triangulation_rejects_pure_rotation_and_scale_jumps, P.test_pair_baseline_skip,
+    P.test_triangulation_parallax_bound_alone, P.test_triangulation_point_behind_second_view,
 ]
 
 
 @pytest.fixture(scope="module")
 def workdir():
-    d = tempfile.mkdtemp(prefix="orc_mut_")
+    # the mutated copies are built beside the oracle, in its (git-ignored) build folder
+    d = os.path.join(os.path.dirname(O.__file__), "_build", "mutations_%d" % os.getpid())
+    os.makedirs(d, exist_ok=True)
     yield d
     O.use_library(None)
     shutil.rmtree(d, ignore_errors=True)
@@ -83,3 +102,59 @@ def test_mutation_is_caught(workdir, name, old, new):
     finally:
         O.use_library(None)
     assert failed, "no pin caught: " + name
+
+
+# Mistakes planted in the fuse-apply map (plain Python), each a subclass overriding one step.
+class _TieToExisting(O.FuseMap):
+    def fuse(self, k, cands):  # a tie keeps the point already at the keypoint
+        st = dict(added=0, merged_into_existing=0, replaced_existing=0, skipped_dead=0, skipped_observed=0)
+        for m, j in cands:
+            if m in self.replaced:
+                st["skipped_dead"] += 1
+            elif k in self.obs[m]:
+                st["skipped_observed"] += 1
+            elif self.kp[k][j] is None:
+                self.observe(k, j, m)
+                st["added"] += 1
+            elif len(self.obs[self.kp[k][j]]) >= len(self.obs[m]):
+                self._replace(m, self.kp[k][j])
+                st["merged_into_existing"] += 1
+            else:
+                self._replace(self.kp[k][j], m)
+                st["replaced_existing"] += 1
+        return st
+
+
+class _NoErase(O.FuseMap):
+    def _replace(self, a, b):  # a keyframe that already sees b keeps its link to a
+        for k, j in self.obs.pop(a).items():
+            if k not in self.obs[b]:
+                self.obs[b][k] = j
+                self.kp[k][j] = b
+        self.replaced[a] = b
+
+
+class _NoDeadSkip(O.FuseMap):
+    def fuse(self, k, cands):  # a replaced point stands for its survivor instead of being skipped
+        st = dict(added=0, merged_into_existing=0, replaced_existing=0, skipped_dead=0, skipped_observed=0)
+        for m, j in cands:
+            m = self.current(m)
+            if k in self.obs[m]:
+                st["skipped_observed"] += 1
+            elif self.kp[k][j] is None:
+                self.observe(k, j, m)
+                st["added"] += 1
+            elif len(self.obs[self.kp[k][j]]) > len(self.obs[m]):
+                self._replace(m, self.kp[k][j])
+                st["merged_into_existing"] += 1
+            else:
+                self._replace(self.kp[k][j], m)
+                st["replaced_existing"] += 1
+        return st
+
+
+@pytest.mark.parametrize("cls", [_TieToExisting, _NoErase, _NoDeadSkip], ids=lambda c: c.__name__)
+def test_fuse_apply_mutation_is_caught(monkeypatch, cls):
+    monkeypatch.setattr(O, "FuseMap", cls)
+    with pytest.raises(AssertionError):
+        FA.test_oracle_worked_case()

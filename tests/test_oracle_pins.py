@@ -431,20 +431,26 @@ def test_orb_rotation_bins_golden():
 @pytest.mark.parametrize("seed", range(3))
 def test_epipole_on_every_epipolar_line(seed):
     """The epipole in T (Q's centre projected into T) is the common point of the epipolar
-    lines F^T x_Q of every query pixel: a * ex + b * ey + c = 0 up to float32 rounding."""
+    lines F^T x_Q of every query pixel: a * ex + b * ey + c = 0 up to float32 rounding.  On a
+    pair whose new keyframe sits at the origin, and on pairs of a trajectory where neither
+    camera does (so that the sign and origin of Q's centre matter)."""
     p = W.make_pair_cfg0(seed)
-    cam, Q, T = p["cam"], p["Q"], p["T"]
-    e = O.epipole(cam, Q["Tcw"], T["Tcw"]).astype(np.float64)
-    F = np.zeros(9, np.float32)
-    O.lib().orc_fundamental(ctypes.byref(O._cam(cam)), np.ascontiguousarray(Q["Tcw"], np.float64).ctypes.data,
-                            np.ascontiguousarray(T["Tcw"], np.float64).ctypes.data, F.ctypes.data)
-    F = F.astype(np.float64).reshape(3, 3)
+    pairs = [(p["cam"], p["Q"], p["T"])]
+    w = W.make_cfg1(seed=1000 + seed)
+    st = w["steps"][0]
+    pairs += [(w["cam"], w["frames"][st["q"]], w["frames"][f]) for f in st["nbrs"][:3]]
     rng = np.random.default_rng(seed)
-    for _ in range(20):
-        xq = np.array([rng.uniform(0, cam["width"]), rng.uniform(0, cam["height"]), 1.0])
-        l = F.T @ xq
-        d = abs(l[0] * e[0] + l[1] * e[1] + l[2]) / np.hypot(l[0], l[1])
-        assert d < 1e-3 * max(1.0, np.hypot(*e) / 1000.0), d
+    for cam, Q, T in pairs:
+        e = O.epipole(cam, Q["Tcw"], T["Tcw"]).astype(np.float64)
+        F = np.zeros(9, np.float32)
+        O.lib().orc_fundamental(ctypes.byref(O._cam(cam)), np.ascontiguousarray(Q["Tcw"], np.float64).ctypes.data,
+                                np.ascontiguousarray(T["Tcw"], np.float64).ctypes.data, F.ctypes.data)
+        F = F.astype(np.float64).reshape(3, 3)
+        for _ in range(20):
+            xq = np.array([rng.uniform(0, cam["width"]), rng.uniform(0, cam["height"]), 1.0])
+            l = F.T @ xq
+            d = abs(l[0] * e[0] + l[1] * e[1] + l[2]) / np.hypot(l[0], l[1])
+            assert d < 1e-3 * max(1.0, np.hypot(*e) / 1000.0), d
 
 
 def test_epipole_rejection_invariants():
@@ -510,6 +516,53 @@ def test_triangulation_rejects_pure_rotation_and_scale_jumps():
             T["level"][m[k, 1]] += dl
         _, ok = O.triangulate(p["cam"], p["Q"], T, m)
         assert (ok[low] == expect).all(), (dl, ok[low])
+
+
+def _frame_at(centre, points, cam, level=0):
+    """A keyframe with identity rotation at `centre` whose keypoints are the exact projections
+    of `points` (world, float64); other keypoint fields are unused by triangulation."""
+    c = np.asarray(centre, np.float64)
+    Tcw = np.hstack([np.eye(3), -c[:, None]]).reshape(12)
+    rel = np.asarray(points, np.float64) - c
+    xy = np.stack([cam["fx"] * rel[:, 0] / rel[:, 2] + cam["cx"], cam["fy"] * rel[:, 1] / rel[:, 2] + cam["cy"]], 1)
+    n = len(rel)
+    return dict(n=n, xy=xy.astype(np.float32), level=np.full(n, level, np.uint8), Tcw=Tcw,
+                desc=np.zeros((n, 32), np.uint8), angle=np.zeros(n, np.float32), node=np.zeros(n, np.uint32))
+
+
+CAM_PIN = dict(width=640, height=480, fx=450.0, fy=450.0, cx=320.0, cy=240.0)
+
+
+def test_triangulation_parallax_bound_alone():
+    """Noise-free points 17-25 m away seen from two centres 0.3 m apart: the rays meet at the
+    point, but their angle (0.7-1.0 degrees) is below the default parallax bound
+    (cos 0.9998, 1.15 degrees), so nothing is accepted; with the bound at cos 0.99999
+    (0.26 degrees) every point is accepted and recovered."""
+    X = np.array([[0.1, 0.05, 20.0], [-0.5, 0.3, 17.0], [0.8, -0.4, 25.0], [0.0, 0.0, 18.0]])
+    Q, T = _frame_at([0, 0, 0], X, CAM_PIN), _frame_at([0.3, 0, 0], X, CAM_PIN)
+    ang = [np.degrees(np.arccos(np.dot(x, x - [0.3, 0, 0]) / np.linalg.norm(x) / np.linalg.norm(x - [0.3, 0, 0])))
+           for x in X]
+    assert all(0.6 < a < 1.14 for a in ang), ang
+    m = np.array([[k, k, 0] for k in range(len(X))], np.int32)
+    _, ok = O.triangulate(CAM_PIN, Q, T, m)
+    assert ok.sum() == 0
+    xyz, ok = O.triangulate(CAM_PIN, Q, T, m, O.TriParams(cos_parallax_max=0.99999))
+    assert ok.all()
+    assert (np.linalg.norm(xyz.astype(np.float64) - X, axis=1) < 0.01 * X[:, 2]).all()
+
+
+def test_triangulation_point_behind_second_view():
+    """Both lines pass through X = (0, 0, 5) exactly, X is in front of the first camera, and
+    the second camera sits at (1, 0, 10) looking along +z, so X lies behind it: rejected
+    (positive depth is required in both views).  The same point seen from (1, 0, 0), in front
+    of both cameras, is accepted and recovered."""
+    X = np.array([[0.0, 0.0, 5.0]])
+    Q = _frame_at([0, 0, 0], X, CAM_PIN)
+    m = np.array([[0, 0, 0]], np.int32)
+    _, ok = O.triangulate(CAM_PIN, Q, _frame_at([1, 0, 10], X, CAM_PIN), m)
+    assert ok[0] == 0
+    xyz, ok = O.triangulate(CAM_PIN, Q, _frame_at([1, 0, 0], X, CAM_PIN), m)
+    assert ok[0] == 1 and np.linalg.norm(xyz[0] - X[0]) < 1e-3
 
 
 def test_pair_baseline_skip():
