@@ -5,8 +5,8 @@ import ctypes
 import glob
 import os
 import re
+import shutil
 import subprocess
-import tempfile
 
 import numpy as np
 
@@ -59,12 +59,17 @@ def test_struct_layout_matches_c(lib):
         for f, _ in getattr(L, s)._fields_:
             lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
     lines.append("return 0;}")
-    with tempfile.TemporaryDirectory() as d:
+    # the probe program is built in the tests' own (git-ignored) build folder
+    d = os.path.join(ROOT, "tests", "_build", "abi_%d" % os.getpid())
+    os.makedirs(d, exist_ok=True)
+    try:
         c = os.path.join(d, "abi.c")
         open(c, "w").write("\n".join(lines))
         exe = os.path.join(d, "abi")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
     got = dict(ln.split() for ln in out.splitlines())
     for s in structs:
         T = getattr(L, s)

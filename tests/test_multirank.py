@@ -5,6 +5,7 @@ The reference arm runs on rank 0 alone."""
 
 import io
 import os
+import shutil
 import socket
 import sys
 from contextlib import redirect_stdout
@@ -54,11 +55,20 @@ def _rank_main(rank, world, port, out_dir):
         D.destroy_process_group()
 
 
-def test_two_ranks_gloo(tmp_path):
+@pytest.fixture
+def out_dir():
+    # the ranks' results go to the tests' own (git-ignored) build folder
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "ranks_%d" % os.getpid())
+    os.makedirs(d, exist_ok=True)
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def test_two_ranks_gloo(out_dir):
     world = 2
-    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
-    r0 = np.load(tmp_path / "r0.npy")
-    r1 = np.load(tmp_path / "r1.npy")
+    mp.spawn(_rank_main, args=(world, _free_port(), out_dir), nprocs=world, join=True)
+    r0 = np.load(os.path.join(out_dir, "r0.npy"))
+    r1 = np.load(os.path.join(out_dir, "r1.npy"))
     # both ranks agree on the slowest time and the job throughput
     assert r0[1] == r1[1] == 2.0
     assert r0[0] == r1[0] == pytest.approx(64 * world / 2.0)
