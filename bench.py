@@ -186,19 +186,19 @@ def job_throughput(units_per_rank, seconds, world, dist, device=None):
 
 
 def search_bytes(w, res):
-    """Unique bytes the search kernel must touch for one batch: of each query keyframe its
-    descriptors, positions, node keys, caller indices, angles and mask bytes (51 B per
-    keypoint), of each neighbour its descriptors, positions, node keys, levels, caller indices,
-    angles and mask bytes (52 B per keypoint) and its node-key bucket table (8208 B), and 12 B
-    per output match."""
+    """Algorithmic bytes of the search kernel for one batch: 52 B per keypoint of every query
+    and neighbour keyframe (desc 32, xy 8, angle 4, node 4, level 1, caller index 2, mask 1),
+    each keyframe once, plus 12 B per output match.  The kernel's own tables (bucket table,
+    eligible lists) are implementation, not algorithmic bytes."""
     qs, ts = set(), set()
     for s in w["steps"]:
         qs.add(s["q"])
         ts.update(s["nbrs"])
     q = sum(w["frames"][i]["n"] for i in qs)
     t = sum(w["frames"][i]["n"] for i in ts)
-    return 51 * q + 52 * t + 8208 * len(ts) + OUT_BYTES * len(res.matches), dict(
-        query_keypoints=q, neighbour_keypoints=t, neighbours=len(ts), matches=len(res.matches))
+    return 52 * (q + t) + OUT_BYTES * len(res.matches), dict(
+        query_keypoints=q, neighbour_keypoints=t, neighbours=len(ts), matches=len(res.matches),
+        bytes_per_keypoint=52, bytes_per_match=OUT_BYTES)
 
 
 def oracle_sample(w, seconds, t_limit=None):
@@ -389,17 +389,22 @@ def run_mine(args, rank, world, local_rank):
             "peak_kind": pk_kind, "algorithmic_bytes": alg, "algorithmic_parts": parts,
             "kernel_ms": kern_ms, "traffic_note": traffic_note,
             "path_algorithmic_bytes": path_bytes, "path_parts": path_parts}
-    # the ALU side: 8 POPC (and 8 XOR) per comparison; POPC issue rate taken as 16 per SM per
-    # clock (the integer population-count throughput of recent NVIDIA SMs), 152 SMs at the
-    # maximum SM clock seen
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    popc_rate = 16 * sms * (clk.get("sm_max_mhz") or 2070.0) * 1e6
-    t_alu = 8 * res.n_comparisons_search / popc_rate
+    roof["path_frac"] = (path_bytes / (float(step_ms.mean()) / 1e3) / 1e9) / pk["hbm_gbs"]
+    roof["path_note"] = ("path_frac: the whole step's algorithmic bytes (every keyframe, map point, "
+                         "mask byte and output once) / ms_per_step / the HBM peak")
+    # the ALU side: per comparison 8 XOR + 8 POPC (a 256-bit Hamming distance); peak rates
+    # measured on this device by the library's probe kernel (tm_measure_int_rates)
+    rates = tm.int_rates(local_rank)
+    t_alu = max(8 * res.n_comparisons_search / rates["popc_per_s"],
+                res.n_comparisons_search / rates["hamming_per_s"])
     t_hbm = alg / (pk["hbm_gbs"] * 1e9)
     roof["alu_check"] = {"popc_per_comparison": 8, "comparisons": int(res.n_comparisons_search),
-                         "popc_per_s": popc_rate, "t_alu_us": 1e6 * t_alu, "t_hbm_us": 1e6 * t_hbm,
+                         "popc_per_s": rates["popc_per_s"], "lop3_per_s": rates["lop3_per_s"],
+                         "hamming_per_s": rates["hamming_per_s"], "rates": "measured (probe kernel, best of 3)",
+                         "t_alu_us": 1e6 * t_alu, "t_hbm_us": 1e6 * t_hbm,
                          "t_roof_us": 1e6 * max(t_alu, t_hbm), "frac_of_t_roof": max(t_alu, t_hbm) / (kern_ms / 1e3),
-                         "note": "T_roof = max(bytes / HBM peak, POPC count / POPC rate); the HBM term binds"}
+                         "note": "T_roof = max(bytes / HBM peak, comparisons x 8 / POPC rate, comparisons / "
+                                 "Hamming rate); the HBM term binds"}
 
     out = {"metric": METRIC, "value": value, "unit": "keyframes/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),

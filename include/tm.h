@@ -381,13 +381,14 @@ tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
 tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
                        int32_t *kernels_per_run);
 /* Device time of the stages of the plan's last run when it was a tm_plan_run_timed, from the
- * CUDA events recorded inside its graph (all zero otherwise).  The search kernel (one CTA per
- * pair: all of Sec. IV-C) runs beside the store branch (ingest -> fusion): ms[0] search kernel
- * (between events recorded right before and after it on its stream), ms[1] ingest, ms[2]
- * fusion kernel, ms[3] offsets + copy after both branches (and the triangulation kernel
- * when the batch triangulates), ms[4] the dense-block kernel that
- * precedes the search kernel (dense_min > 0; else 0).  Waits for the run to finish. */
-#define TM_PLAN_STAGES 5
+ * CUDA events recorded inside its graph (all zero otherwise).  The search branch (prep kernel:
+ * per-pair F and eligibility; search kernel: one CTA per pair, all of Sec. IV-C) runs beside
+ * the store branch (ingest -> fusion): ms[0] search kernel (between events recorded right
+ * before and after it on its stream), ms[1] ingest, ms[2] fusion kernel, ms[3] offsets + copy
+ * after both branches (and the triangulation kernel when the batch triangulates), ms[4] the
+ * dense-block kernel that precedes the search kernel (dense_min > 0; else 0), ms[5] the prep
+ * kernel.  Waits for the run to finish. */
+#define TM_PLAN_STAGES 6
 tm_status tm_plan_stage_times(tm_plan *plan, float ms[TM_PLAN_STAGES]);
 tm_status tm_plan_destroy(tm_plan *plan);
 
@@ -400,9 +401,16 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *   TM_DEBUG_STARVE_WAITS  non-zero: after its copies have landed, every such kernel also
  *                          awaits a barrier that nothing arrives at, so that the bound runs
  *                          out with no copy in flight; 0 restores normal operation
- * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, limit <= 0). */
+ * Launch choices that the autotuner otherwise makes, fixed so that tests can check every
+ * choice against the oracle (results never depend on them):
+ *   TM_DEBUG_SEARCH_THREADS threads per search CTA: 256; 0 = tuned (default)
+ *   TM_DEBUG_L2_PREFETCH    1: search CTAs ask L2 to prefetch their pair's descriptors and
+ *                           positions at start; 0 or -1 (default): they do not
+ * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, value out of range). */
 #define TM_DEBUG_WAIT_LIMIT 1
 #define TM_DEBUG_STARVE_WAITS 2
+#define TM_DEBUG_SEARCH_THREADS 3
+#define TM_DEBUG_L2_PREFETCH 4
 tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
 /* Bounds-checking builds (compiled with -DTM_DEBUG_BOUNDS; the normal build sets *enabled = 0
  * and *site = 0): every index the kernels take from data (bucket tables, grid lists, match and
@@ -410,6 +418,18 @@ tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
  * the failed index was clamped into range.  reset = 1 clears it after reading.  Reads the
  * current device's status. */
 tm_status tm_debug_bounds(int32_t reset, uint32_t *site, int32_t *enabled);
+
+/* Measured peak rates of the integer operations a descriptor comparison is made of (the ALU
+ * term of the roofline; Sec. IV-C's comparisons are XOR + population count over 256 bits):
+ * a probe kernel on `device` keeps every SM busy with independent register chains and is
+ * timed with CUDA events (best of three launches).
+ *   popc_per_s     population counts per second (popc.b32)
+ *   lop3_per_s     three-input logic operations per second (lop3.b32)
+ *   hamming_per_s  register-resident 256-bit Hamming distances per second (8 xor, 8 popc
+ *                  and their sum each)
+ * Any output may be NULL.  Synchronous; allocates and frees 1.3 MB of device memory.
+ * Errors: TM_ERR_INVALID_ARG (bad device), TM_ERR_CUDA. */
+tm_status tm_measure_int_rates(int32_t device, double *popc_per_s, double *lop3_per_s, double *hamming_per_s);
 
 /* ---------------------------------------------------------------------------- serving
  * Continuous batching.  A host thread admits submitted requests in arrival order as
@@ -476,10 +496,10 @@ tm_status tm_server_stop(tm_server *srv);
 double tm_now(void);
 
 /* ---------------------------------------------------------------------------- no allocation
- * The paper has no counterpart to this call; it exists for callers that cannot allocate
- * device memory -- code running while a CUDA graph is being captured, code under a fixed
- * memory budget or in a real-time loop that forbids allocation after start-up, or a host
- * without a tm_ctx (whose keyframe store allocates).
+ * The paper has no counterpart to this call.  It is for callers that cannot allocate device
+ * memory: code under an allocator that must not grow (a fixed memory budget), a real-time
+ * loop that forbids allocation after start-up (an allocation may block or synchronise the
+ * device), or a host without a tm_ctx (whose keyframe store allocates).
  *
  * Correspondence search of one keyframe pair, with the same results as tm_search_
  * triangulation(q, [t]).  It allocates nothing: its scratch -- both keyframes in node order
@@ -487,19 +507,25 @@ double tm_now(void);
  * array inside the library (about 256 KB, held by every GPU that loads the library until
  * the process exits).
  *   q, t       keyframes of at most TM_NOALLOC_MAX_KP keypoints each; their arrays must be
- *              device memory (Tcw is read from the struct); larger ones are rejected with
- *              TM_ERR_INVALID_ARG
+ *              memory of the current device (or managed memory), desc 16-byte, xy 8-byte,
+ *              angle and node 4-byte aligned (Tcw is read from the struct); larger keyframes,
+ *              host or another device's memory and misaligned arrays are rejected with
+ *              TM_ERR_INVALID_ARG before any work
+ *   params     NULL = defaults; mode, dense_min and baseline_min_ratio are ignored (this call
+ *              always runs the plain per-pair kernels and has no median scene depth), the
+ *              other fields are checked as by tm_search_triangulation
  *   q_free, t_free  device [n] or NULL
- *   out        device tm_match [q->n], matches sorted by q_idx
- *   n_out      device uint32: number of matches
- *   n_comparisons   device uint64 or NULL
+ *   out        device tm_match [q->n] (4-byte aligned), matches sorted by q_idx
+ *   n_out      device uint32 (4-byte aligned): number of matches
+ *   n_comparisons   device uint64 (8-byte aligned) or NULL
  * Asynchronous on `stream` (NULL: the legacy default stream): results are valid once the
  * stream reaches this call, and the inputs must stay valid until then.  The first call on a
- * device looks up the array's device address (once per device, with that device current);
- * make that first call before any stream capture.  Every call uses the same array and
- * leaves its contents behind (each call clears what must start at zero): calls whose work
- * may overlap on the GPU -- on different streams or threads -- race with one another;
- * calls on one stream run one after the other. */
+ * device looks up the array's device address (once per device, with that device current)
+ * and keeps it for the life of the process: make that first call before any stream capture,
+ * and do not reset the device (cudaDeviceReset) while the library is loaded.  Every call uses
+ * the same array and leaves its contents behind (each call clears what must start at zero):
+ * calls whose work may overlap on the GPU -- on different streams or threads -- race with one
+ * another; calls on one stream run one after the other. */
 #define TM_NOALLOC_MAX_KP 2048
 tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyframe_view *q,
                                  const tm_keyframe_view *t, const tm_search_params *params,

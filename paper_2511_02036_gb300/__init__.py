@@ -69,6 +69,15 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+def int_rates(device=0):
+    """Measured peak integer-operation rates of a device (tm_measure_int_rates): population
+    counts, three-input logic operations and register-resident 256-bit Hamming distances per
+    second."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(tm_measure_int_rates(int(device), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))  # noqa: F821
+    return dict(popc_per_s=a.value, lop3_per_s=b.value, hamming_per_s=c.value)
+
+
 def camera_struct(cam):
     return L.tm_camera(int(cam["width"]), int(cam["height"]), float(cam["fx"]), float(cam["fy"]),
                        float(cam["cx"]), float(cam["cy"]))

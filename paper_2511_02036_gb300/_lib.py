@@ -26,9 +26,11 @@ TM_MODE_FUSED = 0
 TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
 TM_MAX_IMAGE_SIZE = 16384
-TM_PLAN_STAGES = 5
+TM_PLAN_STAGES = 6
 TM_DEBUG_WAIT_LIMIT = 1
 TM_DEBUG_STARVE_WAITS = 2
+TM_DEBUG_SEARCH_THREADS = 3
+TM_DEBUG_L2_PREFETCH = 4
 
 
 class tm_camera(ctypes.Structure):
@@ -157,6 +159,7 @@ SIGNATURES = {
     "tm_plan_run": (c_i32, [c_p, c_p]),
     "tm_debug_set": (c_i32, [c_p, c_i32, ctypes.c_int64]),
     "tm_debug_bounds": (c_i32, [c_i32, P(ctypes.c_uint32), P(c_i32)]),
+    "tm_measure_int_rates": (c_i32, [c_i32, P(c_f64), P(c_f64), P(c_f64)]),
     "tm_plan_run_timed": (c_i32, [c_p, c_p]),
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),

@@ -570,14 +570,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void bulk_prefetch_l2(const void *p, uint32_t bytes) {
     if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+// The waiting thread is suspended until the phase completes or about 20 us pass (the time
+// hint, ns), so that waiting warps do not take issue slots from the CTAs beside them.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -738,146 +740,254 @@ __device__ __forceinline__ void merge_best2(uint32_t &b, uint32_t &s, uint32_t o
     b = min(b, ob);
 }
 
-// The loads of a warp's 32-query group that depend on nothing else: issued one group ahead, so
+// Shared memory of the candidate rounds, by 32-bit shared address: explicit ld/st/atom.shared,
+// so that every access of the hot loops is a shared-memory instruction with a 32-bit address.
+__device__ __forceinline__ uint32_t ld_s32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_s16(uint32_t a) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 ld_s128(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void st_s32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_s128(uint32_t a, const float4 &v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t atom_s_min(uint32_t a, uint32_t v) {
+    uint32_t o;
+    asm volatile("atom.shared.min.u32 %0, [%1], %2;" : "=r"(o) : "r"(a), "r"(v) : "memory");
+    return o;
+}
+__device__ __forceinline__ void red_s_min(uint32_t a, uint32_t v) {
+    asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// The load only where p holds (no branch around it); v unchanged elsewhere.
+__device__ __forceinline__ uint32_t ld_s32_if(bool p, uint32_t a, uint32_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.u32 %0, [%1];\n\t}"
+                 : "+r"(v)
+                 : "r"(a), "r"((int)p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_s64(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+// Read-only global loads through the non-coherent path.
+template <typename V>
+__device__ __forceinline__ V ldg(const V *p) { return __ldg(p); }
+
+// A warp searches 64 queries at a time (positions 64g .. 64g + 63): lane l takes positions
+// 64g + l (its query 0) and 64g + 32 + l (its query 1).
+//
+// The loads of a warp's 64 queries that depend on nothing else: issued one group ahead, so
 // that their latency overlaps the previous group's search.
 struct QLoad {
-    uint32_t nk;   // node key or raw node id
-    uint32_t io;   // caller index
-    float2 xq;
-    int el;        // eligible (1/0), or -1: not loaded yet (stored query keyframe with masks)
+    uint32_t nk[2];  // node keys or raw node ids
+    uint32_t io[2];  // caller indices
+    int el[2];       // eligible (1/0), or -1: not loaded yet (stored query keyframe with masks)
 };
 __device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &w, int g) {
     const int lane = (int)(threadIdx.x & 31u);
-    const int p0 = g * 32;
-    const bool in = lane < (int)w.nq - p0;
-    const int p = p0 + (in ? lane : 0);
     QLoad q;
-    q.nk = w.qnode[p];
-    q.xq = w.qxy[p];
-    if (w.qorig) {
-        q.io = w.qorig[p];
-        q.el = !in ? 0 : (w.a == kNone ? 1 : -1);
-    } else {
-        q.io = (uint32_t)p;
-        q.el = in && (w.a == kNone || A.masks[w.a + (uint32_t)p]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p0 = g * 64 + 32 * h;
+        const bool in = lane < (int)w.nq - p0;
+        const int p = in ? p0 + lane : 0;
+        q.nk[h] = ldg(w.qnode + p);
+        if (w.qorig) {
+            q.io[h] = ldg(w.qorig + p);
+            q.el[h] = !in ? 0 : (w.a == kNone ? 1 : -1);
+        } else {
+            q.io[h] = (uint32_t)p;
+            q.el[h] = in && (w.a == kNone || ldg(A.masks + w.a + (uint32_t)p));
+        }
     }
     return q;
 }
 
-// 32 queries (positions 32g ..) of the CTA's pair, by one warp.  Each lane finds its query's
-// candidates in the neighbour's node index staged in shared memory: the bucket of its key,
-// then the run of equal keys inside it (keys ascend within a bucket).  The (query, candidate)
-// entries of the 32 queries are numbered by a warp prefix sum and taken 32 per round, lane k
-// handling entry k (its query found by a search over the prefix sums; key-equal and eligible
-// by construction or by the staged eligibility), so that the warp waits ~ceil(entries / 32)
-// rounds of candidate loads instead of the largest bucket.  A round's entries of one query
-// sit in adjacent lanes: a segmented shuffle reduction merges (best, second) and the
-// segment's first lane folds it into the query's state.  The accepted match of each query goes
-// to acc[], its claim on the target to win[] (shared atomicMin).
+// Shared addresses of the search CTA's arrays and of the calling warp's query tables.
+struct SearchSmem {
+    uint32_t tkey, bst, words, epos, win, pc, thr, thre;
+    uint32_t rec;  // the warp's 64 query records: second distance << 16 | first eligible entry
+    uint32_t sb;   // the warp's 64 best keys (distance << 16 | target position)
+};
+constexpr uint32_t kSecTimeout = 0xFFFEu;  // second-distance field: the query's dense tile timed out
+
+// Eligible positions before position j (0 <= j <= nT): the count before j's word plus the
+// eligible bits of the word below j.
+__device__ __forceinline__ int eligible_before(const SearchSmem &M, int j) {
+    const uint2 wd = ld_s64(M.words + 8 * (j >> 5));
+    return (int)wd.y + __popc(wd.x & ((1u << (j & 31)) - 1u));
+}
+
+// 64 queries of the CTA's pair, by one warp (Sec. IV-C).  Each lane finds its two queries'
+// candidates: the bucket of the node key, the run of equal keys inside it (keys ascend within
+// a bucket; one pass over both queries' buckets counting the keys below and up to each key),
+// the run's eligible targets (counts from the eligibility bitmap).  The (query, candidate)
+// entries of the 64 queries are numbered by a warp prefix sum (a lane's query 0 entries, then
+// its query 1 entries) and taken 32 per round, lane k handling entry k (its lane found by a
+// binary search over the prefix sums), so that the warp waits ~ceil(entries / 32) rounds of
+// candidate loads for 64 queries.  An entry's lane folds its (distance << 16 | target) key
+// into the query's state with two shared atomicMin: the first returns the previous best, and
+// the larger of the two is a loser whose distance bounds the second (entries of one query in
+// one round are serialized by the hardware; the result does not depend on their order).  A
+// query whose best passes the distance and ratio tests gets its rotation bin, is listed in the
+// pair's accepted list (global, `acc`) and claims its target (shared atomicMin of
+// (distance << 16 | caller)).  kEpi, kEprej, kDense: the epipolar gate, the epipole
+// rejection and dense node blocks are on (fixed per launch).
+template <bool kEpi, bool kEprej, bool kDense>
 __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
-                                             const float *F, const float *thr, const uint32_t *tkey,
-                                             const uint16_t *bst, const uint16_t *ep, const uint16_t *epos,
-                                             const float *epl, const float *thre,
-                                             uint32_t *win, uint32_t *acc, uint2 *st, int g, const QLoad &q,
-                                             uint32_t &cmp, uint32_t *dfail) {
+                                             const SearchSmem &M, uint32_t *nacc, int g, const QLoad &q,
+                                             uint32_t &cmp, uint32_t &dfail) {
     const int lane = (int)(threadIdx.x & 31u);
-    const int p0 = g * 32;
-    const int nloc = min(32, (int)w.nq - p0);
-    const bool in = lane < nloc;
-    const int p = p0 + (in ? lane : 0);
-    const uint32_t nk = q.nk, io = q.io;
-    const float2 xq = q.xq;
-    const bool el = q.el >= 0 ? q.el != 0 : (A.masks[w.a + io] != 0);
-    const uint32_t key = w.qraw ? node_key(nk) : nk;
-    const uint32_t b = key >> (32 - kBucketBits);
-    int lo = bst[b];
-    const int be = guard(bst[b + 1], (int)w.nt + 1, 1);
-    lo = guard(lo, be + 1, 2);
-    while (lo < be && tkey[lo] < key) ++lo;
-    int hi = lo;
-    while (hi < be && tkey[hi] == key) ++hi;
-    const Line l = epi_line(F, xq.x, xq.y);
-    // the eligible candidates: positions epos[elo .. elo + c)
-    const int elo = ep[lo];
-    int c = el ? (int)ep[hi] - elo : 0;
-    // a query of a dense node block: its candidates were compared on the tensor cores
-    const bool dz = A.sp.dense_min > 0 && hi - lo >= A.sp.dense_min;
-    if (dz) {
-        cmp += (uint32_t)c;
-        c = 0;
+    const int nT = (int)w.nt, nQ = (int)w.nq;
+    uint32_t key[2];
+    int lo[2], be[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        key[h] = w.qraw ? node_key(q.nk[h]) : q.nk[h];
+        const uint32_t b = key[h] >> (32 - kBucketBits);
+        lo[h] = guard((int)ld_s16(M.bst + 2 * b), nT + 1, 1);
+        be[h] = guard((int)ld_s16(M.bst + 2 * b + 2), nT + 1, 2);
     }
-    int off = c;
+    // one pass over both buckets: keys below each query's key, and up to it
+    int nlt0 = 0, nle0 = 0, nlt1 = 0, nle1 = 0;
+    const int len = max(be[0] - lo[0], be[1] - lo[1]);
+    for (int t = 0; t < len; ++t) {
+        const bool p0 = lo[0] + t < be[0], p1 = lo[1] + t < be[1];
+        const uint32_t k0 = ld_s32_if(p0, M.tkey + 4 * (lo[0] + t), 0u);
+        const uint32_t k1 = ld_s32_if(p1, M.tkey + 4 * (lo[1] + t), 0u);
+        nlt0 += p0 && k0 < key[0];
+        nle0 += p0 && k0 <= key[0];
+        nlt1 += p1 && k1 < key[1];
+        nle1 += p1 && k1 <= key[1];
+    }
+    int c[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int nlt = h ? nlt1 : nlt0, nle = h ? nle1 : nle0;
+        const bool el = q.el[h] >= 0 ? q.el[h] != 0 : (ldg(A.masks + w.a + q.io[h]) != 0);
+        const int elo = eligible_before(M, lo[h] + nlt);
+        int n = el ? eligible_before(M, lo[h] + nle) - elo : 0;
+        uint32_t b0 = kNone, s0 = 0xFFFFu;
+        // a query of a dense node block: its candidates were compared on the tensor cores
+        if (kDense && el && nle - nlt >= A.sp.dense_min) {
+            cmp += (uint32_t)n;
+            n = 0;
+            const uint2 v = A.dres[w.c + (uint32_t)(g * 64 + 32 * h + lane)];
+            b0 = v.x;
+            s0 = v.y == kNone ? kSecTimeout : v.y;
+        }
+        c[h] = n;
+        st_s32(M.sb + 4 * (32 * h + lane), b0);
+        st_s32(M.rec + 4 * (32 * h + lane), (s0 << 16) | (uint32_t)elo);
+    }
+    const int c0 = c[0], cl = c[0] + c[1];
+    int off = cl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kFull, off, o);
         if (lane >= o) off += y;
     }
     const int total = __shfl_sync(kFull, off, 31);
-    off -= c;  // exclusive
-    st[lane] = (dz && el) ? A.dres[w.c + (uint32_t)p] : make_uint2(kNone, 0xFFFFu);
+    off -= cl;  // exclusive
     __syncwarp();
-    const bool epi = A.sp.epipolar != 0;
     for (int k0 = 0; k0 < total; k0 += 32) {
         const int k = k0 + lane;
-        // owner: the last query whose first entry is <= k (it has entries, as k < total)
-        int i = 0;
+        // owner lane: the last lane whose first entry is <= k (it has entries, as k < total)
+        int o = 0;
 #pragma unroll
         for (int s2 = 16; s2 >= 1; s2 >>= 1) {
-            const int oi = __shfl_sync(kFull, off, (i + s2) & 31);
-            if (i + s2 < 32 && oi <= k) i += s2;
+            const int oo = __shfl_sync(kFull, off, o + s2);
+            if (oo <= k) o += s2;
         }
-        const int e0 = __shfl_sync(kFull, elo, i) + (k - __shfl_sync(kFull, off, i));
-        Line li;
-        li.a = __shfl_sync(kFull, l.a, i);
-        li.b = __shfl_sync(kFull, l.b, i);
-        li.c = __shfl_sync(kFull, l.c, i);
-        const bool valid = k < total;
-        const int j0 = valid ? guard((int)epos[guard(e0, (int)w.nt, 3)], (int)w.nt, 4) : 0;
-        uint32_t bk = kNone, sc = 0xFFFFu;
-        if (valid) {
-            const int pq = guard(p0 + i, (int)w.nq, 5);
-            const uint4 a0 = w.qdesc[2 * pq], a1 = w.qdesc[2 * pq + 1];
-            const uint4 t0 = T.desc[2 * j0], t1 = T.desc[2 * j0 + 1];
-            const float2 xt = T.xy[j0];
-            const int lv = T.level[j0];
+        const int r = k - __shfl_sync(kFull, off, o);
+        const int c0o = __shfl_sync(kFull, c0, o);
+        if (k < total) {
+            const int h = r >= c0o ? 1 : 0;
+            const int qi = o + 32 * h;  // state index of the entry's query
+            const uint32_t elo = ld_s32(M.rec + 4 * qi) & 0xFFFFu;
+            const int j0 = guard((int)ld_s16(M.epos + 2 * guard((int)elo + r - (h ? c0o : 0), nT, 3)), nT, 4);
+            const int pq = guard(g * 64 + qi, nQ, 5);
+            const uint4 a0 = ldg(w.qdesc + 2 * pq), a1 = ldg(w.qdesc + 2 * pq + 1);
+            const uint4 t0 = ldg(T.desc + 2 * j0), t1 = ldg(T.desc + 2 * j0 + 1);
+            const float2 xt = ldg(T.xy + j0);
+            const uint32_t lv = ldg(T.level + j0);
             ++cmp;
             const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
-            if ((!epi || epi_pass(li, xt.x, xt.y, thr[lv])) && !(thre && near_epipole(epl, xt.x, xt.y, thre[lv])))
-                bk = (d << 16) | (uint32_t)j0;
-        }
-        // segmented merge over the lanes of each query (suffix within the segment), as many
-        // doubling steps as the round's longest segment needs
-        const int seg = __reduce_max_sync(kFull, (unsigned)__popc(__match_any_sync(kFull, i)));
-        for (int s2 = 1; s2 < seg; s2 <<= 1) {
-            const uint32_t ob = __shfl_down_sync(kFull, bk, s2);
-            const uint32_t os = __shfl_down_sync(kFull, sc, s2);
-            const int oi = __shfl_down_sync(kFull, i, s2);
-            if (lane + s2 < 32 && oi == i) merge_best2(bk, sc, ob, os);
-        }
-        const int prev = __shfl_up_sync(kFull, i, 1);
-        if (k < total && (lane == 0 || prev != i)) {
-            uint2 v = st[i];
-            merge_best2(v.x, v.y, bk, sc);
-            st[i] = v;
-        }
-        __syncwarp();
-    }
-    if (in) {
-        const uint2 v = st[lane];
-        uint32_t a = kNone;
-        if (v.y == kNone) *dfail = 1u;  // the dense tile of this query timed out
-        if (v.x != kNone) {
-            const uint32_t best = v.x >> 16;
-            bool ok = (int)best <= A.sp.hamming_max;
-            if (ok && A.sp.ratio_num != 0 && v.y != 0xFFFFu)
-                ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * v.y;
-            if (ok) {
-                const uint32_t j = (uint32_t)guard((int)(v.x & 0xFFFFu), (int)w.nt, 6);
-                a = (j << 16) | best;
-                if (A.sp.resolve) atomicMin(&win[j], (best << 16) | io);
+            bool pass = true;
+            if (kEpi) {
+                // l = F^T x_Q: a = (x F00 + y F10) + F20, b = (x F01 + y F11) + F21,
+                // c = (x F02 + y F12) + F22; num = (a x_T + b y_T) + c, den = a^2 + b^2;
+                // pass iff den > 0 and num^2 < thr den
+                const float2 xq = ldg(w.qxy + pq);
+                const float4 F0 = ld_s128(M.pc), F1 = ld_s128(M.pc + 16), F2 = ld_s128(M.pc + 32);
+                const float la = fadd(fadd(fmul(xq.x, F0.x), fmul(xq.y, F0.w)), F1.z);
+                const float lb = fadd(fadd(fmul(xq.x, F0.y), fmul(xq.y, F1.x)), F1.w);
+                const float lc = fadd(fadd(fmul(xq.x, F0.z), fmul(xq.y, F1.y)), F2.x);
+                const float num = fadd(fadd(fmul(la, xt.x), fmul(lb, xt.y)), lc);
+                const float den = fadd(fmul(la, la), fmul(lb, lb));
+                pass = den > 0.0f && fmul(num, num) < fmul(__uint_as_float(ld_s32(M.thr + 4 * lv)), den);
+            }
+            if (kEprej) {
+                const float ex = __uint_as_float(ld_s32(M.pc + 36)), ey = __uint_as_float(ld_s32(M.pc + 40));
+                const float dx = fsub(ex, xt.x), dy = fsub(ey, xt.y);
+                if (fadd(fmul(dx, dx), fmul(dy, dy)) < __uint_as_float(ld_s32(M.thre + 4 * lv))) pass = false;
+            }
+            if (pass) {
+                const uint32_t bk = (d << 16) | (uint32_t)j0;
+                const uint32_t old = atom_s_min(M.sb + 4 * qi, bk);
+                // the record: second << 16 | first eligible entry, the entry fixed for the
+                // query, so the minimum of the word is that of the second
+                red_s_min(M.rec + 4 * qi, ((max(old, bk) >> 16) << 16) | elo);
             }
         }
-        acc[p] = a;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = g * 64 + 32 * h + lane;
+        bool ok = false;
+        uint32_t best = 0, j = 0;
+        if (p < nQ) {
+            const uint32_t bk = ld_s32(M.sb + 4 * (32 * h + lane)), sc = ld_s32(M.rec + 4 * (32 * h + lane)) >> 16;
+            if (kDense && sc == kSecTimeout) dfail = 1u;  // the dense tile of this query timed out
+            if (bk != kNone) {
+                best = bk >> 16;
+                ok = (int)best <= A.sp.hamming_max;
+                if (ok && A.sp.ratio_num != 0 && sc != 0xFFFFu)
+                    ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sc;
+                j = (uint32_t)guard((int)(bk & 0xFFFFu), nT, 6);
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, ok);
+        if (m) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(nacc, (uint32_t)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (ok) {
+                const uint32_t io = q.io[h];
+                const uint32_t bin = A.sp.rot_filter ? (uint32_t)rot_bin(ldg(w.qangle + p), ldg(T.angle + j), A.sp.rot_mode) : 0u;
+                const uint32_t e = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                A.acc[w.c + (uint32_t)guard((int)e, nQ, 7)] =
+                    make_uint2(io | (j << 16), (uint32_t)ldg(T.orig + j) | (best << 16) | (bin << 25));
+                if (A.sp.resolve) red_s_min(M.win + 4 * j, (best << 16) | io);
+            }
+        }
     }
     __syncwarp();
 }
@@ -1241,118 +1351,87 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
 // One CTA per (new keyframe, neighbour) pair, largest pairs first (Sec. IV-C, all of S1-S6):
 //   setup    the neighbour's node keys and bucket table into shared memory (bulk copies);
 //            F by nine lanes of warp 0 (float64); winners reset; the neighbour's eligibility
-//            gathered into node order;
-//   search   warps take 32-query groups (search_group);
-//   finalize each query's accepted match is kept only if it is its target's winner; kept
-//            matches are binned by rotation, the top-3 bins kept, and the pair compacted in
-//            caller query order into its output region.
+//            read in node order (through the caller index of each position) and its eligible
+//            positions listed with prefix counts (warp w takes a contiguous range of bitmap
+//            words: ballots, one barrier, the list);
+//   search   warps take 64-query groups (search_group), each accepted query listed with its
+//            rotation bin;
+//   finalize only the accepted queries are visited: kept if its target's winner, the top-3
+//            rotation bins kept; a bitmap of the kept caller queries and its prefix counts give
+//            every kept match its slot in caller query order.
 // Comparisons (and a timed-out bulk copy) are recorded per item for the copy kernel.
-// kMaxT: largest block size of the instance; 256 (five CTAs per SM, the batched form) or 1024
-// (one CTA per SM: a few large pairs, where more warps per pair hide more latency).
-template <int kMaxT>
-__global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(BatchArgs A) {
+// kMaxT: block size of the instance, 256 (five CTAs per SM) or 512 (two per SM: twice the warps
+// on each pair, for batches of few pairs).
+#ifndef TM_SEARCH_MINB
+#define TM_SEARCH_MINB 5
+#endif
+constexpr int kSearchThreads = 256;
+template <bool kEpi, bool kEprej, bool kDense>
+__global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(BatchArgs A) {
+    constexpr int kMaxT = kSearchThreads;
     extern __shared__ __align__(128) unsigned char ssm[];
-    __shared__ float F[9];
-    __shared__ float thr[kLevels], thre[kLevels], epl[2];
-    __shared__ uint2 qst[kMaxT / 32][32];  // per warp
+    __shared__ __align__(16) float thr[kLevels], thre[kLevels];
+    __shared__ uint32_t qrec[kMaxT / 32][64], sbest[kMaxT / 32][64];  // per warp: its queries' states
     __shared__ uint32_t hist[32];
-    __shared__ uint32_t wtot[32];
     __shared__ uint32_t keep, scmp, sdfail, nacc;
     __shared__ __align__(8) uint64_t bar, never;
-    __shared__ bool ok_all;
-    const int tid = threadIdx.x, bs = blockDim.x, wid = tid >> 5, nw = bs >> 5;
+    __shared__ int ok_all;
+    constexpr int nw = kMaxT / 32;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const WorkItem w = A.sitems[blockIdx.x];
     const uint32_t i = w.idx;
-    if (A.sp.baseline_min_ratio > 0.0f) {  // (uniform) pair-baseline skip
-        __shared__ bool s_skip;
-        if (threadIdx.x == 0) s_skip = pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio);
-        __syncthreads();
-        if (s_skip) {
-            if (threadIdx.x == 0) {
-                A.counts[i] = 0u;
-                A.item_cmp[i] = 0u;
-            }
-            return;
-        }
-    }
     const SearchStage S = SearchStage::make(A.sn);
     uint32_t *tkey = reinterpret_cast<uint32_t *>(ssm + S.tkey);
     uint16_t *bst = reinterpret_cast<uint16_t *>(ssm + S.bst);
-    uint32_t *win = reinterpret_cast<uint32_t *>(ssm + S.win);
-    uint32_t *acc = reinterpret_cast<uint32_t *>(ssm + S.acc);
-    uint16_t *ep = reinterpret_cast<uint16_t *>(ssm + S.ep);
+    uint2 *words = reinterpret_cast<uint2 *>(ssm + S.words);
     uint16_t *epos = reinterpret_cast<uint16_t *>(ssm + S.epos);
-    uint8_t *tel = reinterpret_cast<uint8_t *>(acc);  // eligibility bytes, until the search
+    float *pc = reinterpret_cast<float *>(ssm + S.pc);
+    uint32_t *win = reinterpret_cast<uint32_t *>(ssm + S.win);
+    uint32_t *qbits = reinterpret_cast<uint32_t *>(ssm + S.qbits);
+    uint32_t *qpre = reinterpret_cast<uint32_t *>(ssm + S.qpre);
     const KfView T = KfView::at(w.t, A.L);
     const int nQ = (int)w.nq, nT = (int)w.nt;
+    const int nwq = (nQ + 31) >> 5, nwt = (nT + 31) >> 5;  // bitmap words: queries, targets
     if (tid == 0) {
+        // the neighbour's node keys and bucket table (store), its eligibility words and eligible
+        // positions and the pair's constants (prep kernel), all into shared memory
         mbar_init(&bar, 1);
         mbar_init(&never, 1);
         fence_mbar_init();
         const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
-        mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes);
+        const uint32_t wb = (8u * (uint32_t)(nwt + 1) + 15u) & ~15u;
+        const uint32_t eb = (2u * (uint32_t)nT + 15u) & ~15u;
+        mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes + wb + eb + 48u);
         if (kb) bulk_g2s(tkey, T.node, kb, &bar);
         bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
+        bulk_g2s(words, A.pwords + w.toff / 32u, wb, &bar);
+        if (eb) bulk_g2s(epos, A.pepos + w.toff, eb, &bar);
+        bulk_g2s(pc, A.pconst + (size_t)kPairConst * i, 48u, &bar);
         scmp = 0u;
         sdfail = 0u;
         nacc = 0u;
+        ok_all = 1;
     }
-    if (tid == 32) {
+    if (tid == 32 && A.l2_prefetch) {
         // the arrays the candidate rounds read, into L2 while the setup runs (each neighbour's
         // descriptors are read once, so their loads would otherwise wait on DRAM)
         bulk_prefetch_l2(T.desc, 32u * (uint32_t)nT);
         bulk_prefetch_l2(T.xy, (8u * (uint32_t)nT) & ~15u);
         bulk_prefetch_l2(w.qdesc, 32u * (uint32_t)nQ);
     }
-    if (wid == 0) fundamental_lanes(A.cam, w.pq, w.pt, F);
-    if (tid == 64 && A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, epl);
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
         thre[tid] = fmul(fmul(A.sp.epipole_px, A.sp.epipole_px), sc);
     }
-    if (tid < 32) hist[tid] = 0u;
+    if (tid >= 96 && tid < 128) hist[tid - 96] = 0u;
+    for (int j = tid; j < nT; j += kMaxT) win[j] = kNone;
+    for (int k = tid; k < nwq; k += kMaxT) qbits[k] = 0u;
     QLoad cur = {};
-    if (wid * 32 < nQ) cur = load_group(A, w, wid);  // the first group's loads overlap the setup
-    // the neighbour's eligibility into node order: caller index c's mask byte goes to its
-    // position pos[c] (both loads coalesced and independent)
-    constexpr int U = 8;  // targets per thread and pass: all their loads in flight together
-    for (int j0 = 0; j0 < nT; j0 += U * bs) {
-        uint32_t m[U], ps[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int c = j0 + k * bs + tid;
-            const bool in = w.b != kNone && c < nT;
-            m[k] = in ? A.masks[w.b + (uint32_t)c] : 1u;
-            ps[k] = in ? T.pos[c] : (uint32_t)c;
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int c = j0 + k * bs + tid;
-            if (c < nT) {
-                win[c] = kNone;
-                tel[ps[k]] = m[k] != 0u;
-            }
-        }
-    }
-    __syncthreads();
-    {
-        // eligible positions in node order: thread t takes the run [t*per, (t+1)*per)
-        const int per = (nT + bs - 1) / bs, jb = min(tid * per, nT), je = min(jb + per, nT);
-        uint32_t cnt = 0;
-        for (int j = jb; j < je; ++j) cnt += tel[j];
-        uint32_t tot;
-        uint32_t run = block_scan_add(cnt, wtot, tot);
-        for (int j = jb; j < je; ++j) {
-            ep[j] = (uint16_t)run;
-            if (tel[j]) epos[run++] = (uint16_t)j;
-        }
-        if (tid == 0) ep[nT] = (uint16_t)tot;
-    }
-    const bool ok = staged_wait(&bar, &never, A);
-    if (tid == 0) ok_all = true;
-    __syncthreads();
-    if (!ok) ok_all = false;
+    if (wid * 64 < nQ) cur = load_group(A, w, wid);  // the first group's loads overlap the setup
+    // the thread that initialized the barrier and issued the bulk copies awaits them; the CTA
+    // barrier then publishes the copied data (and every other setup write) to all threads
+    if (tid == 0 && !staged_wait(&bar, &never, A)) ok_all = 0;
     __syncthreads();
     if (!ok_all) {
         if (tid == 0) {
@@ -1361,91 +1440,177 @@ __global__ void __launch_bounds__(kMaxT, kMaxT <= 256 ? 5 : 1) search_kernel(Bat
         }
         return;
     }
-    uint32_t cmp = 0;
-    for (int g = wid; g * 32 < nQ; g += nw) {
+    if (A.sp.baseline_min_ratio > 0.0f && pc[11] != 0.0f) {  // (uniform) pair-baseline skip
+        if (tid == 0) {
+            A.counts[i] = 0u;
+            A.item_cmp[i] = 0u;
+        }
+        return;
+    }
+    SearchSmem M;
+    M.tkey = smem_addr(tkey);
+    M.bst = smem_addr(bst);
+    M.words = smem_addr(words);
+    M.epos = smem_addr(epos);
+    M.win = smem_addr(win);
+    M.pc = smem_addr(pc);
+    M.thr = smem_addr(thr);
+    M.thre = smem_addr(thre);
+    M.rec = smem_addr(&qrec[wid][0]);
+    M.sb = smem_addr(&sbest[wid][0]);
+    uint32_t cmp = 0, dfail = 0;
+    for (int g = wid; g * 64 < nQ; g += nw) {
         QLoad nxt = {};
-        if ((g + nw) * 32 < nQ) nxt = load_group(A, w, g + nw);
-        search_group(A, w, T, F, thr, tkey, bst, ep, epos, epl, A.sp.epipole_px > 0.0f ? thre : nullptr, win, acc,
-                     qst[wid], g, cur, cmp, &sdfail);
+        if ((g + nw) * 64 < nQ) nxt = load_group(A, w, g + nw);
+        search_group<kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
+    if (kDense && __any_sync(kFull, dfail != 0u) && lane == 0) sdfail = 1u;
     __syncthreads();
-    // finalize: one match per target, rotation histogram (results by caller index in tkey[]).
-    // Only the accepted queries are visited: their positions are listed first (in ep[], free
-    // after the search) by a ballot compaction of acc[].
-    uint32_t *fres = tkey;
-    uint16_t *alist = ep;
-    const bool rot = A.sp.rot_filter != 0;
-    const int ln = tid & 31;
-    for (int q = tid; q < nQ; q += bs) fres[q] = kNone;
-    for (int p0 = 0; p0 < nQ; p0 += bs) {
-        const int p = p0 + tid;
-        const bool a = p < nQ && acc[p] != kNone;
-        const unsigned m = __ballot_sync(kFull, a);
-        uint32_t base = 0;
-        if (ln == 0 && m) base = atomicAdd(&nacc, (uint32_t)__popc(m));
-        base = __shfl_sync(kFull, base, 0);
-        if (a) alist[base + __popc(m & ((1u << ln) - 1u))] = (uint16_t)p;
+    // finalize over the accepted queries (their list, written by this CTA, is read back from
+    // L2 once; a thread keeps its first two entries in registers)
+    const int na = (int)nacc;
+    const bool rot = A.sp.rot_filter != 0, res = A.sp.resolve != 0;
+    const uint2 v0 = tid < na ? A.acc[w.c + (uint32_t)tid] : make_uint2(0u, 0u);
+    const uint2 v1 = tid + kMaxT < na ? A.acc[w.c + (uint32_t)(tid + kMaxT)] : make_uint2(0u, 0u);
+    auto entry = [&](int e) -> uint2 {
+        return e == tid ? v0 : (e == tid + kMaxT ? v1 : A.acc[w.c + (uint32_t)e]);
+    };
+    // a listed query is kept if it is its target's winner (io = caller index, j = target)
+    auto winner = [&](const uint2 &v) -> bool {
+        const uint32_t io = v.x & 0xFFFFu, j = (uint32_t)guard((int)(v.x >> 16), nT, 10);
+        return !res || win[j] == (((v.y >> 16) & 0x1FFu) << 16 | io);
+    };
+    if (rot)
+        for (int e = tid; e < na; e += kMaxT) {
+            const uint2 v = entry(e);
+            if (winner(v)) atomicAdd(&hist[v.y >> 25], 1u);
+        }
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t k = rot ? top3_mask_warp(hist) : kNone;
+        if (lane == 0) keep = k;
     }
     __syncthreads();
-    const int na = (int)nacc;
-    for (int e0 = 0; e0 < na; e0 += bs) {
-        const int e = e0 + tid;
-        uint32_t bin = kNone;
-        if (e < na) {
-            const int p = guard(alist[e], nQ, 7);
-            const uint32_t ac = acc[p], j = (uint32_t)guard((int)(ac >> 16), nT, 8), d = ac & 0xFFFFu;
-            const uint32_t io = (uint32_t)guard(w.qorig ? (int)w.qorig[p] : p, nQ, 9);
-            if (!A.sp.resolve || win[j] == ((d << 16) | io)) {
-                bin = rot ? (uint32_t)rot_bin(w.qangle[p], T.angle[j], A.sp.rot_mode) : 0u;
-                fres[io] = pack_res(T.orig[j], d, bin);
+    const uint32_t kp = keep;
+    for (int e = tid; e < na; e += kMaxT) {
+        const uint2 v = entry(e);
+        if (((kp >> (v.y >> 25)) & 1u) && winner(v)) {
+            const uint32_t io = v.x & 0xFFFFu;
+            atomicOr(&qbits[guard((int)(io >> 5), nwq, 11)], 1u << (io & 31u));
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {
+        // prefix counts of the bitmap's words: lane l takes words [l * pw, (l + 1) * pw)
+        const int pw = (nwq + 31) >> 5, kb = min(lane * pw, nwq), ke = min(kb + pw, nwq);
+        uint32_t s = 0;
+        for (int k = kb; k < ke; ++k) s += (uint32_t)__popc(qbits[k]);
+        uint32_t run = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, run, o);
+            if (lane >= o) run += y;
+        }
+        run -= s;
+        for (int k = kb; k < ke; ++k) {
+            qpre[k] = run;
+            run += (uint32_t)__popc(qbits[k]);
+        }
+        if (lane == 31) qpre[nwq] = run;
+    }
+    __syncthreads();
+    const int lim = res ? min(nQ, nT) : nQ;
+    for (int e = tid; e < na; e += kMaxT) {
+        const uint2 v = entry(e);
+        if (((kp >> (v.y >> 25)) & 1u) && winner(v)) {
+            const uint32_t io = v.x & 0xFFFFu;
+            const uint32_t r = qpre[io >> 5] + (uint32_t)__popc(qbits[io >> 5] & ((1u << (io & 31u)) - 1u));
+            A.padded[w.out_off + (uint32_t)guard((int)r, lim, 12)] =
+                Out3{(int)io, (int)(v.y & 0xFFFFu), (int)((v.y >> 16) & 0x1FFu)};
+        }
+    }
+    if (tid == 0) {
+        A.counts[i] = qpre[nwq];
+        A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
+    }
+}
+
+// Per-pair preparation for the search kernel, one CTA per search item (Sec. IV-C pair setup):
+// F by nine lanes of warp 0 (float64, rounded to float32), the epipole and the pair-baseline
+// skip when those variants are on, and the neighbour's eligibility in node order: warp w takes
+// words [wb, we) of the position bitmap (a position's mask byte read through its caller index,
+// four words' loads in flight per lane), records their ballots and counts, and after one
+// barrier writes each word with the eligible positions before it and lists its eligible
+// positions, from the count of the warps before it; a closing word holds the total.
+constexpr int kPrepThreads = 256;
+__global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
+    __shared__ uint32_t wtot[kPrepThreads / 32];
+    __shared__ __align__(16) float F[12];
+    constexpr int nw = kPrepThreads / 32;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const uint32_t i = blockIdx.x;
+    const WorkItem w = A.items[i];
+    const KfView T = KfView::at(w.t, A.L);
+    const int nT = (int)w.nt, nwt = (nT + 31) >> 5;
+    float *pc = A.pconst + (size_t)kPairConst * i;
+    if (wid == 0) {
+        fundamental_lanes(A.cam, w.pq, w.pt, F);
+        __syncwarp();
+        if (lane < 9) pc[lane] = F[lane];
+    }
+    if (tid == 64) {
+        float e[2] = {0.0f, 0.0f};
+        if (A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, e);
+        pc[9] = e[0];
+        pc[10] = e[1];
+    }
+    if (tid == 96)
+        pc[11] = (A.sp.baseline_min_ratio > 0.0f && pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio)) ? 1.0f
+                                                                                                             : 0.0f;
+    __shared__ uint32_t sbits[TM_MAX_KP_LIMIT / 32];
+    uint2 *words = A.pwords + w.toff / 32u;
+    uint16_t *epos = A.pepos + w.toff;
+    const int per = (nwt + nw - 1) / nw, wb = min(wid * per, nwt), we = min(wb + per, nwt);
+    uint32_t cnt = 0;
+    constexpr int U = 4;
+    for (int W0 = wb; W0 < we; W0 += U) {
+        uint32_t o[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = 32 * (W0 + u) + lane;
+            o[u] = (W0 + u < we && j < nT) ? (uint32_t)ldg(T.orig + j) : kNone;
+        }
+        bool m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            m[u] = o[u] != kNone && (w.b == kNone || ldg(A.masks + w.b + o[u]) != 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned bal = __ballot_sync(kFull, m[u]);
+            if (W0 + u < we) {
+                if (lane == 0) sbits[W0 + u] = bal;
+                cnt += (uint32_t)__popc(bal);
             }
         }
-        if (rot) {
-            const unsigned peers = __match_any_sync(kFull, bin);
-            if (bin != kNone && ln == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-        }
     }
+    if (lane == 0) wtot[wid] = cnt;
     __syncthreads();
-    if (tid < 32) {
-        const uint32_t k = rot ? top3_mask_warp(hist) : kNone;
-        if (tid == 0) keep = k;
-    }
-    __syncthreads();
-    // ordered compaction: warp k owns caller indices [k*per, (k+1)*per); a count pass, a scan
-    // of the warp totals, a write pass
-    const int lane = tid & 31, per = (((nQ + nw - 1) / nw) + 31) & ~31;
-    const int qb = wid * per, qe = min(qb + per, nQ);
-    uint32_t wc = 0;
-    for (int q0 = qb; q0 < qe; q0 += 32) {
-        const int q = q0 + lane;
-        const uint32_t r = q < qe ? fres[q] : kNone;
-        wc += __popc(__ballot_sync(kFull, r != kNone && ((keep >> (r & 31u)) & 1u)));
-    }
-    if (lane == 0) wtot[wid] = wc;
-    __syncthreads();
-    uint32_t base = 0, total = 0;
+    uint32_t base = 0, ne = 0;
+#pragma unroll
     for (int k = 0; k < nw; ++k) {
         const uint32_t v = wtot[k];
         if (k < wid) base += v;
-        total += v;
+        ne += v;
     }
-    for (int q0 = qb; q0 < qe; q0 += 32) {
-        const int q = q0 + lane;
-        const uint32_t r = q < qe ? fres[q] : kNone;
-        const bool f = r != kNone && ((keep >> (r & 31u)) & 1u);
-        const unsigned m = __ballot_sync(kFull, f);
-        if (f) {
-            const uint32_t pos = (uint32_t)guard((int)(base + __popc(m & ((1u << lane) - 1u))), min(nQ, nT), 10);
-            A.padded[w.out_off + pos] = Out3{q, (int)(r >> 14), (int)((r >> 5) & 0x1FFu)};
-        }
-        base += __popc(m);
+    for (int W = wb; W < we; ++W) {
+        const unsigned bal = sbits[W];
+        if (lane == 0) words[W] = make_uint2(bal, base);
+        if ((bal >> lane) & 1u) epos[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = (uint16_t)(32 * W + lane);
+        base += (uint32_t)__popc(bal);
     }
-    if (tid == 0) {
-        A.counts[i] = total;
-        A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
-    }
+    if (tid == 0) words[nwt] = make_uint2(0u, ne);
 }
 
 // ---------------------------------------------------------------- fusion (S7-S9)
@@ -1720,6 +1885,48 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
     }
 }
 
+// ------------------------------------------------------------------------- integer-pipe rates
+//
+// Peak rates of the integer operations a descriptor comparison is made of, for the roofline's
+// ALU term: every thread runs `iters` rounds over 8 independent register chains, so that
+// throughput, not latency, bounds the launch.  mode 0: population count only (popc.b32);
+// mode 1: three-input logic only (lop3.b32, xor of three); mode 2: one 256-bit Hamming
+// distance per round (8 xor, 8 popc, the sum), operands in registers.  Inline PTX with
+// volatile keeps every operation.  sink receives one word per thread so nothing is dead.
+__global__ void __launch_bounds__(256) int_rate_kernel(int mode, int iters, uint32_t seed, uint32_t *sink) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t x[8], y = seed ^ (t * 0x9E3779B1u), z = t + seed;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (t + 1u) * (2u * k + 1u) ^ seed;
+    if (mode == 0) {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) asm volatile("popc.b32 %0, %0;" : "+r"(x[k]));
+    } else if (mode == 1) {
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[k]) : "r"(y), "r"(z));
+    } else {
+        uint32_t d = 0;
+        for (int it = 0; it < iters; ++it) {
+            uint32_t c[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                asm volatile("xor.b32 %0, %1, %2;" : "=r"(c[k]) : "r"(x[k]), "r"(y));
+                asm volatile("popc.b32 %0, %0;" : "+r"(c[k]));
+            }
+            const uint32_t h = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+            d += h;
+            y += h;  // the next round's operand depends on this one
+        }
+        x[0] = d;
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r ^= x[k];
+    sink[t] = r;
+}
+
 // ------------------------------------------------------------------------- plain form
 
 // Stage 1: match.  One group of G lanes per sorted query; node ranges found by binary search
@@ -1938,25 +2145,35 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {
 
 size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 
-// the search kernel instance for a block size
-static void (*search_fn(int threads))(BatchArgs) {
-    return threads <= 256 ? search_kernel<256> : search_kernel<1024>;
+// the search kernel instance for a launch's gate variants and dense node blocks
+static void (*search_fn(const BatchArgs &a))(BatchArgs) {
+    const bool epi = a.sp.epipolar != 0, eprej = a.sp.epipole_px > 0.0f, dense = a.sp.dense_min > 0;
+    if (dense) {
+        if (epi) return eprej ? search_kernel<true, true, true> : search_kernel<true, false, true>;
+        return eprej ? search_kernel<false, true, true> : search_kernel<false, false, true>;
+    }
+    if (epi) return eprej ? search_kernel<true, true, false> : search_kernel<true, false, false>;
+    return eprej ? search_kernel<false, true, false> : search_kernel<false, false, false>;
 }
 
-int search_ctas_per_sm(int threads, int sn) {
+int search_ctas_per_sm(const BatchArgs &a) {
     int n = 0;
-    const size_t smem = search_smem_bytes(sn);
-    if (threads < 32 || threads > 1024 || threads % 32) return 0;
-    if (cudaFuncSetAttribute(search_fn(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_fn(threads), threads, smem) == cudaSuccess ? n : 0;
+    const size_t smem = search_smem_bytes(a.sn);
+    if (cudaFuncSetAttribute(search_fn(a), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_fn(a), kSearchThreads, smem) == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio) {
+cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s, int prio) {
+    if (a.n_search == 0) return cudaSuccess;
+    return launch_prio(pair_prep_kernel, dim3(a.n_search), dim3(kPrepThreads), 0, s, prio, a);
+}
+
+cudaError_t launch_search(const BatchArgs &a, cudaStream_t s, int prio) {
     if (a.n_search == 0) return cudaSuccess;
     const size_t smem = search_smem_bytes(a.sn);
-    cudaError_t e = cudaFuncSetAttribute(search_fn(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(search_fn(a), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_prio(search_fn(threads), dim3(a.n_search), dim3(threads), smem, s, prio, a);
+    return launch_prio(search_fn(a), dim3(a.n_search), dim3(kSearchThreads), smem, s, prio, a);
 }
 
 size_t dense_smem_bytes() { return kDenseSmem; }
@@ -1998,6 +2215,11 @@ cudaError_t debug_bounds(bool reset, uint32_t *site, bool *enabled) {
     *site = 0u;
     return cudaSuccess;
 #endif
+}
+
+cudaError_t launch_int_rate(int mode, int ctas, int iters, uint32_t *sink, cudaStream_t s) {
+    int_rate_kernel<<<ctas, 256, 0, s>>>(mode, iters, 0x1234567u, sink);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {
@@ -2066,9 +2288,9 @@ cudaError_t launch_fuse_plain(const unsigned char *t, int cap, const float *pos,
 
 // ------------------------------------------------------------------------- no-allocation variant
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA graph is being
-// captured, code under an allocator that must not grow (a fixed memory budget, a real-time
-// loop that forbids allocation after start-up), or a host without a tm_ctx and its store.
+// Some callers cannot allocate device memory: code under an allocator that must not grow (a
+// fixed memory budget), a real-time loop that forbids allocation after start-up (an
+// allocation may block or synchronise the device), or a host without a tm_ctx and its store.
 // For them tm_search_pair_noalloc searches one keyframe pair with the plain per-pair kernels,
 // keeping all of its scratch -- the two node-sorted keyframe slots, the per-pair arrays and
 // the counters -- in the file-scope array below, which every GPU that loads the library holds
@@ -2094,7 +2316,9 @@ __global__ void noalloc_jobs_kernel(tmap::IngestJob *dst, tmap::IngestJob q, tma
     dst[1] = t;
 }
 
-// Device address of the scratch array for the current device, looked up once per device.
+// Device address of the scratch array for the current device, looked up once per device (the
+// first call with that device current) and kept for the life of the process.  A device reset
+// (cudaDeviceReset) while the library is loaded would leave the kept address stale.
 // (In host code g_noalloc_scratch names a host-side stand-in, not device memory.)
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_ptr[64] = {nullptr};
@@ -2112,13 +2336,17 @@ tm_status noalloc_scratch(int device, unsigned char **out) {
     return TM_OK;
 }
 
-bool device_accessible(const void *p) {
+// p is memory the kernels on `device` read directly: device memory of that device (or managed
+// memory), aligned to `align` bytes (the width of the kernels' loads and stores).
+bool device_accessible(const void *p, int device, size_t align) {
+    if (reinterpret_cast<uintptr_t>(p) % align) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -2136,20 +2364,27 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
         cam->height > TM_MAX_IMAGE_SIZE || !(cam->fx > 0) || !(cam->fy > 0))
         return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad camera (image sides 1..%d px, fx, fy > 0)",
                     TM_MAX_IMAGE_SIZE);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     for (const tm_keyframe_view *v : {q, t}) {
         if (v->n < 0 || v->n > kNoAllocMaxKp)
             return fail(TM_ERR_INVALID_ARG,
                         "tm_search_pair_noalloc: %d keypoints exceed the limit of %d per keyframe "
                         "(the size of the library's fixed scratch array)", v->n, kNoAllocMaxKp);
-        if (v->n > 0 && !(device_accessible(v->desc) && device_accessible(v->xy) &&
-                          device_accessible(v->angle) && device_accessible(v->level) &&
-                          device_accessible(v->node)))
-            return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: keyframe arrays must be device memory");
+        if (v->n > 0 && !(device_accessible(v->desc, dev, 16) && device_accessible(v->xy, dev, 8) &&
+                          device_accessible(v->angle, dev, 4) && device_accessible(v->level, dev, 1) &&
+                          device_accessible(v->node, dev, 4)))
+            return fail(TM_ERR_INVALID_ARG,
+                        "tm_search_pair_noalloc: keyframe arrays must be memory of the current device "
+                        "(desc 16-byte, xy 8-byte, angle and node 4-byte aligned)");
     }
-    if (!device_accessible(out) || !device_accessible(n_out) ||
-        (n_comparisons && !device_accessible(n_comparisons)) ||
-        (q_free && !device_accessible(q_free)) || (t_free && !device_accessible(t_free)))
-        return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: masks and outputs must be device memory");
+    if (!device_accessible(out, dev, 4) || !device_accessible(n_out, dev, 4) ||
+        (n_comparisons && !device_accessible(n_comparisons, dev, 8)) ||
+        (q_free && !device_accessible(q_free, dev, 1)) || (t_free && !device_accessible(t_free, dev, 1)))
+        return fail(TM_ERR_INVALID_ARG,
+                    "tm_search_pair_noalloc: masks and outputs must be memory of the current device "
+                    "(out and n_out 4-byte, n_comparisons 8-byte aligned)");
     tm_search_params sp;
     tm_search_params_default(&sp);
     if (params) sp = *params;
@@ -2159,9 +2394,6 @@ extern "C" tm_status tm_search_pair_noalloc(const tm_camera *cam, const tm_keyfr
     const int l = sp.lanes_per_query ? sp.lanes_per_query : 1;
     if (!(l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32))
         return fail(TM_ERR_INVALID_ARG, "tm_search_pair_noalloc: bad lanes_per_query");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     unsigned char *scr = nullptr;
     tm_status st = noalloc_scratch(dev, &scr);
     if (st) return st;

@@ -18,10 +18,12 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_stage_gather(const GatherJob *jobs, int n, unsigned char *base, const size_t offs[5],
                                 cudaStream_t s);
 
-// Batch pipeline: search (CTA per pair), fuse (CTA per 256 map points), copy.
+// Batch pipeline: prep (CTA per pair: F, eligibility), search (CTA per pair), fuse (CTA per
+// 256 map points), copy.
 size_t search_smem_bytes(int sn);
-int search_ctas_per_sm(int threads, int sn);
-cudaError_t launch_search(const BatchArgs &a, int threads, cudaStream_t s, int prio = 0);
+int search_ctas_per_sm(const BatchArgs &a);
+cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s, int prio = 0);
+cudaError_t launch_search(const BatchArgs &a, cudaStream_t s, int prio = 0);
 // Dense node blocks on the tensor cores (a.sp.dense_min > 0): a.n_search * a.dsplit CTAs;
 // writes a.dres, which launch_search then reads (same stream, before it).
 size_t dense_smem_bytes();
@@ -34,6 +36,11 @@ cudaError_t debug_bounds(bool reset, uint32_t *site, bool *enabled);
 // Triangulation of every match of the batch (a.triangulate; after the copy kernel: reads the
 // offsets and the dense matches).
 cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s);
+
+// Integer-pipe rate probe: `ctas` CTAs of 256 threads, each thread `iters` rounds of 8
+// operations (mode 0 popc, 1 lop3, 2 one register-resident 256-bit Hamming distance per round);
+// sink: one word per thread.
+cudaError_t launch_int_rate(int mode, int ctas, int iters, uint32_t *sink, cudaStream_t s);
 
 // Plain per-pair form: every stage of one pair is its own launch, with global scratch.
 struct PairScratch {

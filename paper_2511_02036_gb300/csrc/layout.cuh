@@ -22,10 +22,10 @@ constexpr int kGridCols = 64;
 constexpr int kGridRows = 48;
 constexpr int kGridCells = kGridCols * kGridRows;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr int kBucketBits = 12;  // node-key buckets of a keyframe's node index
+constexpr int kBucketBits = 11;  // node-key buckets of a keyframe's node index
 constexpr int kBuckets = 1 << kBucketBits;
 constexpr int kFuseChunk = 256; // map points per fusion item (one CTA of the fusion kernel)
-constexpr int kQueryGroup = 32; // queries per search unit (one warp)
+constexpr int kQueryGroup = 64; // queries per search unit (one warp, two per lane)
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
@@ -151,27 +151,40 @@ struct WorkItem {
     const double *pq, *pt;   // search: poses Tcw of Q and T (slot header, or the ingest job of a
                              // keyframe entering with the batch)
     float mdepth;            // search: T's median scene depth (0 = unknown; pair-baseline skip)
+    uint32_t toff;           // search: the pair's first entry in the batch's per-target arrays
+                             //   (BatchArgs::pepos; a multiple of 32, so toff / 32 indexes pwords)
 };
+static_assert(sizeof(WorkItem) == 128, "work records are 128 bytes");
+
+// Per-pair constants written by the prep kernel: F (row-major, float32), the epipole in the
+// neighbour (x, y; epipole rejection only), and 1.0 when the pair-baseline skip applies.
+constexpr int kPairConst = 12;
 
 constexpr size_t kBucketTableBytes = ((size_t(kBuckets + 1) * 2 + 15) / 16) * 16;
 
 // Shared-memory carve of a search CTA (one pair) for a capacity of sn keypoints (a multiple
-// of 32): the neighbour's node keys and bucket table (bulk copies), its per-target winners,
-// its eligible positions in node order (epos) with their prefix counts (ep: eligible
-// positions before j), and the per-query accepted matches (whose space first holds the
-// per-target eligibility bytes); after the search the key array holds the per-caller-query
-// results.
+// of 32); the first five arrays arrive by bulk copies:
+//   tkey   the neighbour's node keys
+//   bst    its node-key bucket table
+//   words  its eligibility bitmap (32 positions a word) with the eligible positions before
+//          each word: uint2 (bits, count before), sn / 32 + 1 words (the last: 0, total)
+//   epos   the eligible positions in node order
+//   pc     the pair's constants (kPairConst floats)
+//   win    per target: lowest (distance << 16 | caller query) among the accepted queries
+//   qbits  kept matches, one bit per caller query; qpre: prefix counts of its words (+ total)
 struct SearchStage {
-    size_t tkey, bst, win, acc, ep, epos, bytes;
+    size_t tkey, bst, words, epos, pc, win, qbits, qpre, bytes;
     __host__ __device__ static constexpr SearchStage make(int sn) {
         SearchStage L{};
         size_t o = 0;
-        L.tkey = o; o = align128(o + size_t(sn) * 4);
-        L.bst = o;  o = align128(o + kBucketTableBytes);
-        L.win = o;  o = align128(o + size_t(sn) * 4);
-        L.acc = o;  o = align128(o + size_t(sn) * 4);
-        L.ep = o;   o = align128(o + size_t(sn + 1) * 2);
-        L.epos = o; o = align128(o + size_t(sn) * 2);
+        L.tkey = o;  o = align128(o + size_t(sn) * 4);
+        L.bst = o;   o = align128(o + kBucketTableBytes);
+        L.words = o; o = align128(o + size_t(sn / 32 + 1) * 8);
+        L.epos = o;  o = align128(o + size_t(sn) * 2);
+        L.pc = o;    o = align128(o + size_t(kPairConst) * 4);
+        L.win = o;   o = align128(o + size_t(sn) * 4);
+        L.qbits = o; o = align128(o + size_t(sn / 32) * 4);
+        L.qpre = o;  o = align128(o + size_t(sn / 32 + 1) * 4);
         L.bytes = o;
         return L;
     }
@@ -273,6 +286,14 @@ struct BatchArgs {
     uint8_t *point_ok;            // [matches] accepted as new map points
     uint2 *dres;                  // [sum of nq over search items] per-query (best key, second) of
                                   // dense queries, at WorkItem::c + position
+    uint2 *acc;                   // [sum of nq over search items] accepted queries of each pair,
+                                  // listed from WorkItem::c: (target position << 16 | caller,
+                                  // bin << 25 | distance << 16 | target caller index)
+    uint32_t l2_prefetch;         // search CTAs ask L2 to prefetch their pair's descriptors
+    float *pconst;                // [n_search][kPairConst] per-pair constants (prep kernel)
+    uint2 *pwords;                // per pair from toff / 32: eligibility words (bits, count before)
+                                  //   and one closing word (0, eligible total)
+    uint16_t *pepos;              // per pair from toff: the eligible positions in node order
     uint32_t dsplit;              // dense kernel CTAs per search item
 };
 

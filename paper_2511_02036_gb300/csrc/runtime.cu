@@ -480,7 +480,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &points, &point_ok})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &points, &point_ok})
         b->release();
     h_stage.release();
     h_out.release();
@@ -686,7 +686,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.step_pair_begin.assign(n_steps + 1, 0);
     B.step_fuse_item.assign(n_steps + 1, 0);
     B.n_pairs = 0;
-    uint32_t pad = 0, dq = 0;
+    uint32_t pad = 0, dq = 0, tq = 0;
     int smem_n = 32;
     auto slot_of = [&](uint64_t id, int &slot) -> tm_status {
         auto it = c->ids.find(id);
@@ -736,6 +736,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.cost = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, (uint64_t)nq + nt + (uint64_t)nq * nt / 256);
             w.c = dq;
             dq += (uint32_t)nq;
+            // per-target arrays of the prep kernel: the eligible positions and the bitmap words
+            // (nwt + 1 of them) from toff / 32, a multiple of 64 (16-byte aligned copies)
+            w.toff = tq;
+            tq += (uint32_t)((32 * ((nt + 31) / 32 + 1) + 63) & ~63);
             pad += (uint32_t)(sp.resolve ? std::min(nq, nt) : nq);
             smem_n = std::max(smem_n, std::max(nq, nt));
             items.push_back(w);
@@ -844,6 +848,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
         (sp.dense_min > 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))) ||
+        (e = B.acc.reserve(std::max<size_t>(1, dq) * 8)) ||
+        (e = B.pconst.reserve(nsi * kPairConst * 4)) || (e = B.pwords.reserve(std::max<uint32_t>(64, tq) / 32 * 8)) ||
+        (e = B.pepos.reserve(std::max<uint32_t>(64, tq) * 2)) ||
         (tri && ((e = B.points.reserve(std::max<size_t>(1, B.search_pad) * 12)) ||
                  (e = B.point_ok.reserve(std::max<size_t>(1, B.search_pad))))))
         return cuda_fail(e, "batch buffers");
@@ -921,6 +928,11 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.starve = c->starve;
     A.sn = B.smem_n;
     A.dres = static_cast<uint2 *>(B.dres.p);
+    A.acc = static_cast<uint2 *>(B.acc.p);
+    A.pconst = static_cast<float *>(B.pconst.p);
+    A.pwords = static_cast<uint2 *>(B.pwords.p);
+    A.pepos = static_cast<uint16_t *>(B.pepos.p);
+    A.l2_prefetch = c->force_prefetch == 1 ? 1u : 0u;  // measured: off is faster (setup copies wait less)
     A.triangulate = tri ? 1 : 0;
     A.tri_cos_max = tri ? tri->cos_parallax_max : 0.0;
     A.tri_chi2 = tri ? tri->chi2 : 0.0;
@@ -938,7 +950,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
-            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, points.p,
+            mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, acc.p, pconst.p,
+            pwords.p, pepos.p, points.p,
             point_ok.p};
 }
 
@@ -979,7 +992,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     B.threads = threads;
     B.lanes = lanes;
     B.ctas = (int)B.n_search_items;
-    if (search_ctas_per_sm(threads, B.args.sn) < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
+    if (search_ctas_per_sm(B.args) < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
     if (timed && !B.ev[0])
         for (cudaEvent_t &ev : B.ev)
             if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
@@ -999,9 +1012,10 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
+        (e = launch_prep(B.args, B.paux, hi_p)) || (e = mark(7, B.paux)) ||
         (e = launch_dense(B.args, B.paux, hi_p)) ||
         (B.args.sp.dense_min > 0 && B.n_search_items > 0 && (e = mark(6, B.paux))) ||
-        (e = launch_search(B.args, threads, B.paux, hi_p)) ||
+        (e = launch_search(B.args, B.paux, hi_p)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
     if (mp_async && (e = cudaStreamWaitEvent(s, B.mready, 0))) return cuda_fail(e, "map points");
@@ -1142,13 +1156,8 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 // ------------------------------------------------------------------------- tuning
 
 
-// Default launch shape: 256-thread CTAs (several per SM).
-// 256 threads per search CTA (five per SM) for batches of many pairs; with fewer pairs than
-// SMs every pair has an SM of its own, and 1024 threads (32 warps on its 32-query groups) hide
-// more of each pair's load latency.
-int tmap::default_threads(const tm_ctx *c, const BatchBuf &B) {
-    return (int)B.n_search_items * 2 <= c->num_sms ? 1024 : 256;
-}
+// Launch shape of the search kernel: 256 threads per CTA (five per SM).
+int tmap::default_threads(const tm_ctx *, const BatchBuf &) { return 256; }
 
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
@@ -1184,6 +1193,11 @@ static uint64_t batch_queries(tm_ctx *c, const BatchBuf &B, const tm_step *steps
 // Picks (threads, lanes) for a prepared batch: cached by density class, else measured.
 tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure) {
     tm_status st;
+    if (c->force_threads) {
+        B.threads = c->force_threads;
+        B.lanes = c->def_lanes;
+        return TM_OK;
+    }
     if ((st = enqueue_fused(c, B, default_threads(c, B), c->def_lanes, s))) return st;
     unsigned long long hc[2];
     cudaError_t e;
@@ -1208,8 +1222,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     float best = 1e30f;
     int bt = default_threads(c, B), bl = c->def_lanes;
     // threads per search CTA (warps sharing one pair); lanes per query only shape the plain form
-    std::vector<int> threads_set = {128, 256};
-    if ((int)B.n_search_items < c->num_sms) threads_set.insert(threads_set.end(), {512, 1024});
+    std::vector<int> threads_set = {256};
     for (int th : threads_set)
         for (int ln : {c->def_lanes}) {
             if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
@@ -1416,6 +1429,51 @@ extern "C" tm_status tm_debug_bounds(int32_t reset, uint32_t *site, int32_t *ena
     return e == cudaSuccess ? TM_OK : cuda_fail(e, "bounds status");
 }
 
+extern "C" tm_status tm_measure_int_rates(int32_t device, double *popc_per_s, double *lop3_per_s,
+                                          double *hamming_per_s) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(TM_ERR_INVALID_ARG, "tm_measure_int_rates: bad device %d", device);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if ((e = cudaSetDevice(device))) return cuda_fail(e, "cudaSetDevice");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int ctas = 8 * sms, iters = 4096;  // 64 warps per SM
+    uint32_t *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double rate[3] = {0.0, 0.0, 0.0};
+    tm_status st = TM_OK;
+    if ((e = cudaMalloc(&sink, (size_t)ctas * 256 * 4)) || (e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1)))
+        st = cuda_fail(e, "tm_measure_int_rates: setup");
+    for (int mode = 0; mode < 3 && !st; ++mode) {
+        float best = 1e30f;
+        for (int r = 0; r < 4 && !st; ++r) {  // the first launch warms up
+            if ((e = cudaEventRecord(e0, 0)) || (e = launch_int_rate(mode, ctas, iters, sink, 0)) ||
+                (e = cudaEventRecord(e1, 0)) || (e = cudaEventSynchronize(e1))) {
+                st = cuda_fail(e, "tm_measure_int_rates: probe");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) best = std::min(best, ms);
+        }
+        // operations per launch: mode 0, 1: 8 per round; mode 2: one distance per round
+        const double ops = (double)ctas * 256.0 * iters * (mode == 2 ? 1.0 : 8.0);
+        rate[mode] = ops / (best * 1e-3);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    cudaSetDevice(prev);
+    if (st) return st;
+    if (popc_per_s) *popc_per_s = rate[0];
+    if (lop3_per_s) *lop3_per_s = rate[1];
+    if (hamming_per_s) *hamming_per_s = rate[2];
+    return TM_OK;
+}
+
 extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
     if (!c) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: null context");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -1426,6 +1484,15 @@ extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
             return TM_OK;
         case TM_DEBUG_STARVE_WAITS:
             c->starve = value ? 1u : 0u;
+            return TM_OK;
+        case TM_DEBUG_SEARCH_THREADS:
+            if (value != 0 && value != 256)
+                return fail(TM_ERR_INVALID_ARG, "tm_debug_set: search threads must be 0 or 256");
+            c->force_threads = (int)value;
+            return TM_OK;
+        case TM_DEBUG_L2_PREFETCH:
+            if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: L2 prefetch must be -1, 0 or 1");
+            c->force_prefetch = (int)value;
             return TM_OK;
         default:
             return fail(TM_ERR_INVALID_ARG, "tm_debug_set: unknown setting %d", (int)what);
@@ -1491,7 +1558,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         }
         // search (when there are pairs), fuse (when there are map points), copy, ingest (when
         // keyframes enter with the batch)
-        P->kernels_per_run = (P->B.n_search_items ? 1 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
+        P->kernels_per_run = (P->B.n_search_items ? 2 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
                              1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0) +
                              (P->B.n_search_items && P->B.args.triangulate ? 1 : 0);
     } else {
@@ -1568,14 +1635,16 @@ extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     cudaError_t e = cudaEventSynchronize(P->B.ev[4]);
     if (e) return cuda_fail(e, "stage events");
     const bool dense = P->B.args.sp.dense_min > 0 && P->B.n_search_items > 0;
-    float t[7] = {0};
-    for (int k = 1; k < (dense ? 7 : 6); ++k)
-        if ((e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k]))) return cuda_fail(e, "stage times");
-    ms[0] = t[1] - (dense ? t[6] : t[5]); // search kernel (between the events around it)
+    float t[8] = {0};
+    for (int k = 1; k < 8; ++k)
+        if ((k != 6 || dense) && (e = cudaEventElapsedTime(&t[k], P->B.ev[0], P->B.ev[k])))
+            return cuda_fail(e, "stage times");
+    ms[0] = t[1] - (dense ? t[6] : t[7]); // search kernel (between the events around it)
     ms[1] = t[2];                         // ingest (from the start)
     ms[2] = t[3] - t[2];                  // fusion (after the ingest)
     ms[3] = t[4] - std::max(t[1], t[3]);  // offsets + copy (after both branches)
-    ms[4] = dense ? t[6] - t[5] : 0.0f;   // dense node blocks (before the search kernel)
+    ms[4] = dense ? t[6] - t[7] : 0.0f;   // dense node blocks (before the search kernel)
+    ms[5] = t[7] - t[5];                  // prep (per-pair constants and eligibility)
     return TM_OK;
 }
 

@@ -59,7 +59,7 @@ struct IngestStage {
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, points, point_ok;
+        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, points, point_ok;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -82,7 +82,7 @@ struct BatchBuf {
     BatchArgs args{};
     cudaGraphExec_t graph = nullptr;        // kernels only
     cudaGraphExec_t graph_timed = nullptr;  // the same with events at the stage boundaries
-    cudaEvent_t ev[7] = {};                 // stage boundaries (timed graph)
+    cudaEvent_t ev[8] = {};                 // stage boundaries (timed graph)
     cudaEvent_t join = nullptr;          // end of the search branch
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)
     cudaEvent_t pfork = nullptr;         // start of the search branch
@@ -120,6 +120,8 @@ struct tm_ctx {
     int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1, last_staged = -1;
     long long wait_limit = 4000000000ll;  // bound of device bulk-copy waits (SM cycles)
     uint32_t starve = 0;                  // test hook: bounded waits run out (no copy in flight)
+    int force_threads = 0;                // test hook: threads per search CTA (0 = tuned)
+    int force_prefetch = -1;              // test hook: search CTAs' L2 prefetch (-1 = tuned)
     ~tm_ctx();
 };
 

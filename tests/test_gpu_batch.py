@@ -76,7 +76,7 @@ def test_plan_graph_replay(tm, small_batch):
         load_all(ctx, w)
         with ctx.plan(steps_of(w)) as plan:
             info = plan.info()
-            assert info["kernels_per_run"] == 3 and info["ctas"] >= 1
+            assert info["kernels_per_run"] == 4 and info["ctas"] >= 1  # prep, search, fuse, copy
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -237,7 +237,7 @@ def test_cfg2_full_size_parity(tm, cfg2):
             plan.run(timed=True)
             assert_same(plan.results(), exp)
             ms = plan.stage_times()
-            assert len(ms) == 5 and all(t > 0 for t in ms[:4]) and ms[4] == 0  # no dense blocks
+            assert len(ms) == 6 and all(t > 0 for t in ms[:4]) and ms[4] == 0 and ms[5] > 0  # no dense blocks
 
 
 def test_new_keyframes_enter_with_the_batch(tm, small_batch):
@@ -266,7 +266,7 @@ def test_new_keyframes_enter_with_the_batch(tm, small_batch):
         with pytest.raises(tm.TMError):
             ctx.keyframe_size(new_ids[0])
         with ctx.plan(steps_of(w), new=new) as plan:
-            assert plan.info()["kernels_per_run"] == 4
+            assert plan.info()["kernels_per_run"] == 5  # ingest, prep, search, fuse, copy
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -500,7 +500,7 @@ def test_triangulation_plan_new_keyframes(tm, small_batch):
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
         with ctx.plan(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids]), tri=tm.TriParams()) as plan:
-            assert plan.info()["kernels_per_run"] == 5  # ingest, search, fuse, copy, triangulation
+            assert plan.info()["kernels_per_run"] == 6  # ingest, prep, search, fuse, copy, triangulation
             for _ in range(2):
                 plan.run()
                 r = plan.results()

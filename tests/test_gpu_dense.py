@@ -130,7 +130,7 @@ def test_dense_plan_counts_its_kernel(tm, dense_step):
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         load_step(tm, ctx, w, st)
         with ctx.plan(steps, sp=tm.SearchParams(dense_min=16)) as plan:
-            assert plan.info()["kernels_per_run"] == 3  # dense, search, copy
+            assert plan.info()["kernels_per_run"] == 4  # prep, dense, search, copy
             for timed in (False, True):
                 plan.run(timed=timed)
                 res = plan.results()

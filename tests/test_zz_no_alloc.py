@@ -1,9 +1,11 @@
 """tm_search_pair_noalloc is the correspondence search for callers that cannot allocate device
-memory (during stream capture, under a fixed budget, or without a context and its store): it
-keeps its scratch in one fixed array inside the library.  Called twice in a row through the C
-ABI -- a 1200-keypoint pair with masks, then a smaller 500-keypoint pair without, so that
-leftovers of the first call in the shared array would show -- it must give exactly the
-matches and comparison count of tm_search_triangulation.  Oversized keyframes are refused.
+memory (under a fixed memory budget, in a real-time loop that forbids allocation after
+start-up, or without a context and its store): it keeps its scratch in one fixed array inside
+the library.  Called twice in a row through the C ABI -- a 1200-keypoint pair with masks,
+then a smaller 500-keypoint pair without, so that leftovers of the first call in the shared
+array would show -- it must give exactly the matches and comparison count of
+tm_search_triangulation and of the oracle.  Oversized keyframes, host memory and misaligned
+arrays are refused before any work.
 
 This file is collected last on purpose."""
 
@@ -21,6 +23,7 @@ def test_noalloc_equals_search_triangulation():
     torch = pytest.importorskip("torch")
     import __graft_entry__ as g
     g.build()
+    import oracle as O
     import paper_2511_02036_gb300 as tm
     from paper_2511_02036_gb300 import _lib as L
 
@@ -66,6 +69,30 @@ def test_noalloc_equals_search_triangulation():
         np.testing.assert_array_equal(out[:n].cpu().numpy(), exp[0])
         assert int(ncmp.item()) == ecmp
         assert n == len(exp[0]) and n > 50
+        # and the oracle's, directly
+        om, ocmp = O.search_pair(cam, Q, T, fq, ft)
+        np.testing.assert_array_equal(out[:n].cpu().numpy(), om)
+        assert int(ncmp.item()) == ocmp
+
+    # arguments the kernels could not read safely are refused before any work: a descriptor
+    # array 8 bytes off its 16-byte alignment, keyframe arrays in host memory
+    cam, Q, T = cases[1][0], cases[1][1], cases[1][2]
+    c = tm.camera_struct(cam)
+    out = torch.zeros((Q["n"], 3), dtype=torch.int32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    qv, tv = view(Q), view(T)
+    bad = L.tm_keyframe_view.from_buffer_copy(qv)
+    padded_desc = dev(np.zeros((Q["n"] + 1) * 32, np.uint8))
+    bad.desc = padded_desc.data_ptr() + 8
+    st_ = tm.tm_search_pair_noalloc(ctypes.byref(c), ctypes.byref(bad), ctypes.byref(tv), None, None, None,
+                                    out.data_ptr(), n_out.data_ptr(), None, None)
+    assert st_ == tm.TM_ERR_INVALID_ARG
+    assert b"aligned" in tm._clib.tm_last_error()
+    host_desc = np.ascontiguousarray(Q["desc"])
+    bad.desc = host_desc.ctypes.data
+    st_ = tm.tm_search_pair_noalloc(ctypes.byref(c), ctypes.byref(bad), ctypes.byref(tv), None, None, None,
+                                    out.data_ptr(), n_out.data_ptr(), None, None)
+    assert st_ == tm.TM_ERR_INVALID_ARG
 
     # beyond the fixed scratch size: refused before any work
     big = W.random_keyframe(np.random.default_rng(0), L.TM_MAX_KP_LIMIT, W.CAM_CFG0)
