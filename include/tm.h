@@ -112,7 +112,7 @@ typedef struct {
                                keypoints of the neighbour is compared with all of them on
                                the tensor cores (descriptors as +-1 fp8 vectors, Hamming =
                                (256 - dot) / 2, exact); same results.  0 = off (default),
-                               else >= 16.  Worth it for dense nodes (~64 and more); each
+                               -1 = the autotuner's choice (plans), else >= 16.  Worth it for dense nodes (~64 and more); each
                                call with it on runs one more kernel.  TM_MODE_PER_PAIR
                                ignores it.                                                   */
     /* ORB-family variants (0 = off, the defaults): */
@@ -380,6 +380,22 @@ tm_status tm_plan_results(tm_plan *plan, tm_batch_result *res, void *stream);
  * parameter as given), search CTAs (one per pair), kernels per run. */
 tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t *ctas,
                        int32_t *kernels_per_run);
+/* Launch choices of a plan's fused form, made by the autotuner when the plan was created
+ * (measured once per batch regime and cached per context, and in the file named by the
+ * TM_TUNE_CACHE environment variable when set) or fixed by tm_debug_set.  Results never depend
+ * on them.  For a plain per-pair plan every field is 0. */
+typedef struct {
+    int32_t queries_per_warp; /* queries a search warp takes at a time: 32 or 64                 */
+    int32_t persistent;       /* 1: resident search CTAs take pairs from a work counter          */
+    int32_t l2_prefetch;      /* 1: search CTAs prefetch their pair's descriptors into L2        */
+    int32_t branch_priority;  /* CTAs placed first when SMs free up: 0 search, 1 store branch    */
+    int32_t dense_min;        /* dense node blocks on the tensor cores from this run length; 0 off */
+    int32_t dense_split;      /* dense kernel CTAs per pair (0 when off)                         */
+    int32_t search_ctas;      /* CTAs of the search launch                                       */
+    int32_t tuned;            /* 1: chosen by the tuner (measured or cached); 0: defaults        */
+} tm_plan_tuning;
+tm_status tm_plan_get_tuning(tm_plan *plan, tm_plan_tuning *out);
+
 /* Device time of the stages of the plan's last run when it was a tm_plan_run_timed, from the
  * CUDA events recorded inside its graph (all zero otherwise).  The search branch (prep kernel:
  * per-pair F and eligibility; search kernel: one CTA per pair, all of Sec. IV-C) runs beside
@@ -406,11 +422,21 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *   TM_DEBUG_SEARCH_THREADS threads per search CTA: 256; 0 = tuned (default)
  *   TM_DEBUG_L2_PREFETCH    1: search CTAs ask L2 to prefetch their pair's descriptors and
  *                           positions at start; 0 or -1 (default): they do not
+ *   TM_DEBUG_BRANCH_PRIORITY which branch of a batch the scheduler serves first: 0 the search
+ *                           branch, 1 the store branch (ingest, fusion), 2 neither; -1 = tuned
+ *                           (default)
+ *   TM_DEBUG_QUERIES_PER_LANE search warps take 32 (1) or 64 (2) queries at a time; 0 = tuned
+ *                           (default)
+ *   TM_DEBUG_PERSISTENT     1: resident search CTAs take pairs from a work counter; 0: one CTA
+ *                           per pair; -1 = tuned (default)
  * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, value out of range). */
 #define TM_DEBUG_WAIT_LIMIT 1
 #define TM_DEBUG_STARVE_WAITS 2
 #define TM_DEBUG_SEARCH_THREADS 3
 #define TM_DEBUG_L2_PREFETCH 4
+#define TM_DEBUG_BRANCH_PRIORITY 5
+#define TM_DEBUG_QUERIES_PER_LANE 6
+#define TM_DEBUG_PERSISTENT 7
 tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
 /* Bounds-checking builds (compiled with -DTM_DEBUG_BOUNDS; the normal build sets *enabled = 0
  * and *site = 0): every index the kernels take from data (bucket tables, grid lists, match and

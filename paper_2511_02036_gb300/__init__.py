@@ -808,7 +808,9 @@ class Context:
 
     def debug_set(self, what, value):
         """Test hooks of the context (tm_debug_set): L.TM_DEBUG_WAIT_LIMIT (SM cycles),
-        L.TM_DEBUG_STARVE_WAITS (bounded device waits run out)."""
+        L.TM_DEBUG_STARVE_WAITS (bounded device waits run out), and launch choices otherwise
+        left to the autotuner (L.TM_DEBUG_QUERIES_PER_LANE, L.TM_DEBUG_PERSISTENT,
+        L.TM_DEBUG_L2_PREFETCH, L.TM_DEBUG_BRANCH_PRIORITY)."""
         check(tm_debug_set(self.handle, int(what), int(value)))  # noqa: F821
 
     def plan(self, steps, masks=None, mps=None, sp=None, fp=None, new=None, tri=None):
@@ -857,9 +859,15 @@ class Plan:
                            ctypes.byref(d)))
         return dict(threads=a.value, lanes=b.value, ctas=c.value, kernels_per_run=d.value)
 
+    def tuning(self):
+        """The launch choices of the plan's fused form (tm_plan_get_tuning) as a dict."""
+        t = L.tm_plan_tuning()
+        check(tm_plan_get_tuning(self.handle, ctypes.byref(t)))  # noqa: F821
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
     def stage_times(self):
-        """(search kernel, ingest, fusion, offsets + copy, dense blocks) device milliseconds of
-        the last run if it was timed (run(timed=True)); zeros otherwise."""
+        """(search kernel, ingest, fusion, offsets + copy, dense blocks, prep) device
+        milliseconds of the last run if it was timed (run(timed=True)); zeros otherwise."""
         ms = np.zeros(L.TM_PLAN_STAGES, np.float32)
         check(tm_plan_stage_times(self.handle, ms.ctypes.data))  # noqa: F821
         return tuple(float(x) for x in ms)

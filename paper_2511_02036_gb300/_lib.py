@@ -31,6 +31,9 @@ TM_DEBUG_WAIT_LIMIT = 1
 TM_DEBUG_STARVE_WAITS = 2
 TM_DEBUG_SEARCH_THREADS = 3
 TM_DEBUG_L2_PREFETCH = 4
+TM_DEBUG_BRANCH_PRIORITY = 5
+TM_DEBUG_QUERIES_PER_LANE = 6
+TM_DEBUG_PERSISTENT = 7
 
 
 class tm_camera(ctypes.Structure):
@@ -103,6 +106,12 @@ class tm_server_config(ctypes.Structure):
                 ("triangulate", c_i32), ("tri", tm_triangulation_params)]
 
 
+class tm_plan_tuning(ctypes.Structure):
+    _fields_ = [("queries_per_warp", c_i32), ("persistent", c_i32), ("l2_prefetch", c_i32),
+                ("branch_priority", c_i32), ("dense_min", c_i32), ("dense_split", c_i32),
+                ("search_ctas", c_i32), ("tuned", c_i32)]
+
+
 class tm_fuse_apply_stats(ctypes.Structure):
     _fields_ = [("added", c_i32), ("merged_into_existing", c_i32), ("replaced_existing", c_i32),
                 ("skipped_dead", c_i32), ("skipped_observed", c_i32)]
@@ -164,6 +173,7 @@ SIGNATURES = {
     "tm_plan_results": (c_i32, [c_p, P(tm_batch_result), c_p]),
     "tm_plan_info": (c_i32, [c_p, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
     "tm_plan_stage_times": (c_i32, [c_p, c_p]),
+    "tm_plan_get_tuning": (c_i32, [c_p, P(tm_plan_tuning)]),
     "tm_plan_destroy": (c_i32, [c_p]),
     "tm_server_config_default": (None, [P(tm_server_config)]),
     "tm_server_start": (c_i32, [c_p, P(tm_server_config), P(c_p)]),

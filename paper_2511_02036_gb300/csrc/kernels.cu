@@ -15,6 +15,7 @@
 // Floating point: every gate is evaluated with explicit round-to-nearest intrinsics in the
 // order stated next to it (no contraction, IEEE division and square root), so that a
 // decision equals the one of a plain float32 evaluation of the same expression.
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -789,22 +790,24 @@ __device__ __forceinline__ uint2 ld_s64(uint32_t a) {
 template <typename V>
 __device__ __forceinline__ V ldg(const V *p) { return __ldg(p); }
 
-// A warp searches 64 queries at a time (positions 64g .. 64g + 63): lane l takes positions
-// 64g + l (its query 0) and 64g + 32 + l (its query 1).
+// A warp searches 32 Q queries at a time (a group, Q = 1 or 2 queries per lane): lane l
+// takes positions 32 Q g + l (its query 0) and, with Q = 2, 32 Q g + 32 + l (its query 1).
 //
-// The loads of a warp's 64 queries that depend on nothing else: issued one group ahead, so
-// that their latency overlaps the previous group's search.
+// The loads of a warp's group that depend on nothing else: issued one group ahead, so that
+// their latency overlaps the previous group's search.
+template <int Q>
 struct QLoad {
-    uint32_t nk[2];  // node keys or raw node ids
-    uint32_t io[2];  // caller indices
-    int el[2];       // eligible (1/0), or -1: not loaded yet (stored query keyframe with masks)
+    uint32_t nk[Q];  // node keys or raw node ids
+    uint32_t io[Q];  // caller indices
+    int el[Q];       // eligible (1/0), or -1: not loaded yet (stored query keyframe with masks)
 };
-__device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &w, int g) {
+template <int Q>
+__device__ __forceinline__ QLoad<Q> load_group(const BatchArgs &A, const WorkItem &w, int g) {
     const int lane = (int)(threadIdx.x & 31u);
-    QLoad q;
+    QLoad<Q> q;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int p0 = g * 64 + 32 * h;
+    for (int h = 0; h < Q; ++h) {
+        const int p0 = g * 32 * Q + 32 * h;
         const bool in = lane < (int)w.nq - p0;
         const int p = in ? p0 + lane : 0;
         q.nk[h] = ldg(w.qnode + p);
@@ -822,8 +825,8 @@ __device__ __forceinline__ QLoad load_group(const BatchArgs &A, const WorkItem &
 // Shared addresses of the search CTA's arrays and of the calling warp's query tables.
 struct SearchSmem {
     uint32_t tkey, bst, words, epos, win, pc, thr, thre;
-    uint32_t rec;  // the warp's 64 query records: second distance << 16 | first eligible entry
-    uint32_t sb;   // the warp's 64 best keys (distance << 16 | target position)
+    uint32_t rec;  // the warp's query records: second distance << 16 | first eligible entry
+    uint32_t sb;   // the warp's best keys (distance << 16 | target position)
 };
 constexpr uint32_t kSecTimeout = 0xFFFEu;  // second-distance field: the query's dense tile timed out
 
@@ -834,14 +837,14 @@ __device__ __forceinline__ int eligible_before(const SearchSmem &M, int j) {
     return (int)wd.y + __popc(wd.x & ((1u << (j & 31)) - 1u));
 }
 
-// 64 queries of the CTA's pair, by one warp (Sec. IV-C).  Each lane finds its two queries'
-// candidates: the bucket of the node key, the run of equal keys inside it (keys ascend within
-// a bucket; one pass over both queries' buckets counting the keys below and up to each key),
-// the run's eligible targets (counts from the eligibility bitmap).  The (query, candidate)
-// entries of the 64 queries are numbered by a warp prefix sum (a lane's query 0 entries, then
-// its query 1 entries) and taken 32 per round, lane k handling entry k (its lane found by a
-// binary search over the prefix sums), so that the warp waits ~ceil(entries / 32) rounds of
-// candidate loads for 64 queries.  An entry's lane folds its (distance << 16 | target) key
+// One group (32 Q queries) of the CTA's pair, by one warp (Sec. IV-C).  Each lane finds its
+// queries' candidates: the bucket of the node key, the run of equal keys inside it (keys
+// ascend within a bucket; one pass over the lane's buckets counting the keys below and up to
+// each key), the run's eligible targets (counts from the eligibility bitmap).  The (query,
+// candidate) entries of the group are numbered by a warp prefix sum (a lane's query 0 entries,
+// then its query 1 entries) and taken 32 per round, lane k handling entry k (its lane found by
+// a binary search over the prefix sums), so that the warp waits ~ceil(entries / 32) rounds of
+// candidate loads for the group.  An entry's lane folds its (distance << 16 | target) key
 // into the query's state with two shared atomicMin: the first returns the previous best, and
 // the larger of the two is a loser whose distance bounds the second (entries of one query in
 // one round are serialized by the hardware; the result does not depend on their order).  A
@@ -849,46 +852,54 @@ __device__ __forceinline__ int eligible_before(const SearchSmem &M, int j) {
 // pair's accepted list (global, `acc`) and claims its target (shared atomicMin of
 // (distance << 16 | caller)).  kEpi, kEprej, kDense: the epipolar gate, the epipole
 // rejection and dense node blocks are on (fixed per launch).
-template <bool kEpi, bool kEprej, bool kDense>
+template <int Q, bool kEpi, bool kEprej, bool kDense>
 __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
-                                             const SearchSmem &M, uint32_t *nacc, int g, const QLoad &q,
+                                             const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
                                              uint32_t &cmp, uint32_t &dfail) {
     const int lane = (int)(threadIdx.x & 31u);
     const int nT = (int)w.nt, nQ = (int)w.nq;
-    uint32_t key[2];
-    int lo[2], be[2];
+    uint32_t key[Q];
+    int lo[Q], be[Q];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < Q; ++h) {
         key[h] = w.qraw ? node_key(q.nk[h]) : q.nk[h];
         const uint32_t b = key[h] >> (32 - kBucketBits);
         lo[h] = guard((int)ld_s16(M.bst + 2 * b), nT + 1, 1);
         be[h] = guard((int)ld_s16(M.bst + 2 * b + 2), nT + 1, 2);
     }
-    // one pass over both buckets: keys below each query's key, and up to it
-    int nlt0 = 0, nle0 = 0, nlt1 = 0, nle1 = 0;
-    const int len = max(be[0] - lo[0], be[1] - lo[1]);
-    for (int t = 0; t < len; ++t) {
-        const bool p0 = lo[0] + t < be[0], p1 = lo[1] + t < be[1];
-        const uint32_t k0 = ld_s32_if(p0, M.tkey + 4 * (lo[0] + t), 0u);
-        const uint32_t k1 = ld_s32_if(p1, M.tkey + 4 * (lo[1] + t), 0u);
-        nlt0 += p0 && k0 < key[0];
-        nle0 += p0 && k0 <= key[0];
-        nlt1 += p1 && k1 < key[1];
-        nle1 += p1 && k1 <= key[1];
-    }
-    int c[2];
+    // one pass over the lane's buckets: keys below each query's key, and up to it
+    int nlt[Q], nle[Q], len = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int nlt = h ? nlt1 : nlt0, nle = h ? nle1 : nle0;
+    for (int h = 0; h < Q; ++h) {
+        nlt[h] = nle[h] = 0;
+        len = max(len, be[h] - lo[h]);
+    }
+    for (int t = 0; t < len; ++t) {
+        bool pt[Q];
+        uint32_t kt[Q];
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            pt[h] = lo[h] + t < be[h];
+            kt[h] = ld_s32_if(pt[h], M.tkey + 4 * (lo[h] + t), 0u);
+        }
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            nlt[h] += pt[h] && kt[h] < key[h];
+            nle[h] += pt[h] && kt[h] <= key[h];
+        }
+    }
+    int c[Q];
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
         const bool el = q.el[h] >= 0 ? q.el[h] != 0 : (ldg(A.masks + w.a + q.io[h]) != 0);
-        const int elo = eligible_before(M, lo[h] + nlt);
-        int n = el ? eligible_before(M, lo[h] + nle) - elo : 0;
+        const int elo = eligible_before(M, lo[h] + nlt[h]);
+        int n = el ? eligible_before(M, lo[h] + nle[h]) - elo : 0;
         uint32_t b0 = kNone, s0 = 0xFFFFu;
         // a query of a dense node block: its candidates were compared on the tensor cores
-        if (kDense && el && nle - nlt >= A.sp.dense_min) {
+        if (kDense && el && nle[h] - nlt[h] >= A.sp.dense_min) {
             cmp += (uint32_t)n;
             n = 0;
-            const uint2 v = A.dres[w.c + (uint32_t)(g * 64 + 32 * h + lane)];
+            const uint2 v = A.dres[w.c + (uint32_t)(g * 32 * Q + 32 * h + lane)];
             b0 = v.x;
             s0 = v.y == kNone ? kSecTimeout : v.y;
         }
@@ -896,7 +907,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
         st_s32(M.sb + 4 * (32 * h + lane), b0);
         st_s32(M.rec + 4 * (32 * h + lane), (s0 << 16) | (uint32_t)elo);
     }
-    const int c0 = c[0], cl = c[0] + c[1];
+    const int c0 = c[0], cl = Q > 1 ? c[0] + c[Q - 1] : c[0];
     int off = cl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -916,13 +927,13 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             if (oo <= k) o += s2;
         }
         const int r = k - __shfl_sync(kFull, off, o);
-        const int c0o = __shfl_sync(kFull, c0, o);
+        const int c0o = Q > 1 ? __shfl_sync(kFull, c0, o) : 0x7FFFFFFF;
         if (k < total) {
             const int h = r >= c0o ? 1 : 0;
             const int qi = o + 32 * h;  // state index of the entry's query
             const uint32_t elo = ld_s32(M.rec + 4 * qi) & 0xFFFFu;
             const int j0 = guard((int)ld_s16(M.epos + 2 * guard((int)elo + r - (h ? c0o : 0), nT, 3)), nT, 4);
-            const int pq = guard(g * 64 + qi, nQ, 5);
+            const int pq = guard(g * 32 * Q + qi, nQ, 5);
             const uint4 a0 = ldg(w.qdesc + 2 * pq), a1 = ldg(w.qdesc + 2 * pq + 1);
             const uint4 t0 = ldg(T.desc + 2 * j0), t1 = ldg(T.desc + 2 * j0 + 1);
             const float2 xt = ldg(T.xy + j0);
@@ -959,8 +970,8 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     }
     __syncwarp();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int p = g * 64 + 32 * h + lane;
+    for (int h = 0; h < Q; ++h) {
+        const int p = g * 32 * Q + 32 * h + lane;
         bool ok = false;
         uint32_t best = 0, j = 0;
         if (p < nQ) {
@@ -1366,19 +1377,22 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
 #define TM_SEARCH_MINB 5
 #endif
 constexpr int kSearchThreads = 256;
-template <bool kEpi, bool kEprej, bool kDense>
-__global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(BatchArgs A) {
+// The pair in slot `slot` of the launch order.  parity: phase of the CTA's bulk-copy barrier for
+// this pair (the CTA's pairs alternate); first: the CTA's first pair (initializes the barriers).
+// Returns 1 when a bounded wait ran out (the CTA stops).
+template <int Q, bool kEpi, bool kEprej, bool kDense>
+__device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, uint32_t parity, bool first) {
     constexpr int kMaxT = kSearchThreads;
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ __align__(16) float thr[kLevels], thre[kLevels];
-    __shared__ uint32_t qrec[kMaxT / 32][64], sbest[kMaxT / 32][64];  // per warp: its queries' states
+    __shared__ uint32_t qrec[kMaxT / 32][32 * Q], sbest[kMaxT / 32][32 * Q];  // per warp: its queries' states
     __shared__ uint32_t hist[32];
     __shared__ uint32_t keep, scmp, sdfail, nacc;
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ int ok_all;
     constexpr int nw = kMaxT / 32;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const WorkItem w = A.sitems[blockIdx.x];
+    const WorkItem w = A.sitems[slot];
     const uint32_t i = w.idx;
     const SearchStage S = SearchStage::make(A.sn);
     uint32_t *tkey = reinterpret_cast<uint32_t *>(ssm + S.tkey);
@@ -1395,9 +1409,11 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
     if (tid == 0) {
         // the neighbour's node keys and bucket table (store), its eligibility words and eligible
         // positions and the pair's constants (prep kernel), all into shared memory
-        mbar_init(&bar, 1);
-        mbar_init(&never, 1);
-        fence_mbar_init();
+        if (first) {
+            mbar_init(&bar, 1);
+            mbar_init(&never, 1);
+            fence_mbar_init();
+        }
         const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
         const uint32_t wb = (8u * (uint32_t)(nwt + 1) + 15u) & ~15u;
         const uint32_t eb = (2u * (uint32_t)nT + 15u) & ~15u;
@@ -1427,25 +1443,29 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
     if (tid >= 96 && tid < 128) hist[tid - 96] = 0u;
     for (int j = tid; j < nT; j += kMaxT) win[j] = kNone;
     for (int k = tid; k < nwq; k += kMaxT) qbits[k] = 0u;
-    QLoad cur = {};
-    if (wid * 64 < nQ) cur = load_group(A, w, wid);  // the first group's loads overlap the setup
+    QLoad<Q> cur = {};
+    if (wid * 32 * Q < nQ) cur = load_group<Q>(A, w, wid);  // the first group's loads overlap the setup
     // the thread that initialized the barrier and issued the bulk copies awaits them; the CTA
     // barrier then publishes the copied data (and every other setup write) to all threads
-    if (tid == 0 && !staged_wait(&bar, &never, A)) ok_all = 0;
+    if (tid == 0) {
+        bool ok = mbar_wait_bounded(&bar, parity, A.wait_limit);
+        if (ok && A.starve) ok = mbar_wait_bounded(&never, 0, A.wait_limit);
+        if (!ok) ok_all = 0;
+    }
     __syncthreads();
     if (!ok_all) {
         if (tid == 0) {
             A.counts[i] = 0u;
             A.item_cmp[i] = kItemTimeout;
         }
-        return;
+        return 1;
     }
     if (A.sp.baseline_min_ratio > 0.0f && pc[11] != 0.0f) {  // (uniform) pair-baseline skip
         if (tid == 0) {
             A.counts[i] = 0u;
             A.item_cmp[i] = 0u;
         }
-        return;
+        return 0;
     }
     SearchSmem M;
     M.tkey = smem_addr(tkey);
@@ -1459,10 +1479,10 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
     M.rec = smem_addr(&qrec[wid][0]);
     M.sb = smem_addr(&sbest[wid][0]);
     uint32_t cmp = 0, dfail = 0;
-    for (int g = wid; g * 64 < nQ; g += nw) {
-        QLoad nxt = {};
-        if ((g + nw) * 64 < nQ) nxt = load_group(A, w, g + nw);
-        search_group<kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
+    for (int g = wid; g * 32 * Q < nQ; g += nw) {
+        QLoad<Q> nxt = {};
+        if ((g + nw) * 32 * Q < nQ) nxt = load_group<Q>(A, w, g + nw);
+        search_group<Q, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
@@ -1535,44 +1555,67 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
         A.counts[i] = qpre[nwq];
         A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
     }
+    return 0;
 }
 
-// Per-pair preparation for the search kernel, one CTA per search item (Sec. IV-C pair setup):
-// F by nine lanes of warp 0 (float64, rounded to float32), the epipole and the pair-baseline
-// skip when those variants are on, and the neighbour's eligibility in node order: warp w takes
-// words [wb, we) of the position bitmap (a position's mask byte read through its caller index,
-// four words' loads in flight per lane), records their ballots and counts, and after one
-// barrier writes each word with the eligible positions before it and lists its eligible
-// positions, from the count of the warps before it; a closing word holds the total.
+// The search kernel: one CTA per pair (grid = pairs), or, kPersist, CTAs that stay resident
+// and take pairs in launch order (largest first) from the batch's work counter until none is
+// left (the copy kernel resets the counter for the next run).
+template <int Q, bool kEpi, bool kEprej, bool kDense, bool kPersist>
+__global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(BatchArgs A) {
+    __shared__ uint32_t s_slot;
+    if (!kPersist) {
+        search_pair<Q, kEpi, kEprej, kDense>(A, blockIdx.x, 0u, true);
+        return;
+    }
+    for (uint32_t it = 0;; ++it) {
+        if (threadIdx.x == 0) s_slot = atomicAdd(A.work, 1u);
+        __syncthreads();
+        const uint32_t slot = s_slot;
+        if (slot >= A.n_search) return;
+        if (search_pair<Q, kEpi, kEprej, kDense>(A, slot, it & 1u, it == 0)) return;
+    }
+}
+
+// Per-pair preparation for the search kernel, one CTA per search item (Sec. IV-C pair setup).
+// Warp 0: F by its nine lanes (float64, rounded to float32), then the epipole and the
+// pair-baseline skip when those variants are on.  Warps 1 .. 7, meanwhile, the neighbour's
+// eligibility in node order: each takes words [wb, we) of the position bitmap (a position's
+// mask byte read through its caller index, four words' loads in flight per lane), records
+// their ballots and counts, and after a barrier of these warps only writes each word with the
+// eligible positions before it and lists its eligible positions, from the count of the warps
+// before it; a closing word holds the total.
 constexpr int kPrepThreads = 256;
 __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
-    __shared__ uint32_t wtot[kPrepThreads / 32];
+    constexpr int nw = kPrepThreads / 32 - 1;  // eligibility warps (1 .. 7)
+    __shared__ uint32_t wtot[nw];
     __shared__ __align__(16) float F[12];
-    constexpr int nw = kPrepThreads / 32;
+    __shared__ uint32_t sbits[TM_MAX_KP_LIMIT / 32];
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const uint32_t i = blockIdx.x;
     const WorkItem w = A.items[i];
-    const KfView T = KfView::at(w.t, A.L);
-    const int nT = (int)w.nt, nwt = (nT + 31) >> 5;
     float *pc = A.pconst + (size_t)kPairConst * i;
     if (wid == 0) {
         fundamental_lanes(A.cam, w.pq, w.pt, F);
         __syncwarp();
         if (lane < 9) pc[lane] = F[lane];
+        if (lane == 0) {
+            float e[2] = {0.0f, 0.0f};
+            if (A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, e);
+            pc[9] = e[0];
+            pc[10] = e[1];
+        }
+        if (lane == 1)
+            pc[11] = (A.sp.baseline_min_ratio > 0.0f && pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio))
+                         ? 1.0f : 0.0f;
+        return;
     }
-    if (tid == 64) {
-        float e[2] = {0.0f, 0.0f};
-        if (A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, e);
-        pc[9] = e[0];
-        pc[10] = e[1];
-    }
-    if (tid == 96)
-        pc[11] = (A.sp.baseline_min_ratio > 0.0f && pair_skipped(w.pq, w.pt, w.mdepth, A.sp.baseline_min_ratio)) ? 1.0f
-                                                                                                             : 0.0f;
-    __shared__ uint32_t sbits[TM_MAX_KP_LIMIT / 32];
+    const KfView T = KfView::at(w.t, A.L);
+    const int nT = (int)w.nt, nwt = (nT + 31) >> 5;
+    const int ew = wid - 1;  // eligibility warp index
     uint2 *words = A.pwords + w.toff / 32u;
     uint16_t *epos = A.pepos + w.toff;
-    const int per = (nwt + nw - 1) / nw, wb = min(wid * per, nwt), we = min(wb + per, nwt);
+    const int per = (nwt + nw - 1) / nw, wb = min(ew * per, nwt), we = min(wb + per, nwt);
     uint32_t cnt = 0;
     constexpr int U = 4;
     for (int W0 = wb; W0 < we; W0 += U) {
@@ -1595,13 +1638,13 @@ __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
             }
         }
     }
-    if (lane == 0) wtot[wid] = cnt;
-    __syncthreads();
+    if (lane == 0) wtot[ew] = cnt;
+    asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");  // warps 1 .. 7 only
     uint32_t base = 0, ne = 0;
 #pragma unroll
     for (int k = 0; k < nw; ++k) {
         const uint32_t v = wtot[k];
-        if (k < wid) base += v;
+        if (k < ew) base += v;
         ne += v;
     }
     for (int W = wb; W < we; ++W) {
@@ -1610,7 +1653,7 @@ __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
         if ((bal >> lane) & 1u) epos[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = (uint16_t)(32 * W + lane);
         base += (uint32_t)__popc(bal);
     }
-    if (tid == 0) words[nwt] = make_uint2(0u, ne);
+    if (tid == 32) words[nwt] = make_uint2(0u, ne);
 }
 
 // ---------------------------------------------------------------- fusion (S7-S9)
@@ -1881,6 +1924,7 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
             A.ncmp[2] = f;
             A.counters[2] = sflags ? kStatusTimeout : 0u;
             A.offsets[A.n_items] = base;
+            if (A.work) *A.work = 0u;  // the persistent search of the next run starts over
         }
     }
 }
@@ -2145,15 +2189,32 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {
 
 size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 
-// the search kernel instance for a launch's gate variants and dense node blocks
+// The search kernel instance for a launch: the group size (1 or 2 queries per lane) and the
+// persistent form exist for the gate configurations of the default search (epipolar gate on
+// or off, no epipole rejection, no dense blocks); any other configuration runs 64-query groups,
+// one CTA per pair (search_form reports the form a launch gets).
+static bool search_variants(const BatchArgs &a) { return !(a.sp.epipole_px > 0.0f) && !(a.sp.dense_min > 0); }
 static void (*search_fn(const BatchArgs &a))(BatchArgs) {
     const bool epi = a.sp.epipolar != 0, eprej = a.sp.epipole_px > 0.0f, dense = a.sp.dense_min > 0;
-    if (dense) {
-        if (epi) return eprej ? search_kernel<true, true, true> : search_kernel<true, false, true>;
-        return eprej ? search_kernel<false, true, true> : search_kernel<false, false, true>;
+    if (search_variants(a)) {
+        if (a.qpl == 1)
+            return a.persist ? (epi ? search_kernel<1, true, false, false, true> : search_kernel<1, false, false, false, true>)
+                             : (epi ? search_kernel<1, true, false, false, false> : search_kernel<1, false, false, false, false>);
+        return a.persist ? (epi ? search_kernel<2, true, false, false, true> : search_kernel<2, false, false, false, true>)
+                         : (epi ? search_kernel<2, true, false, false, false> : search_kernel<2, false, false, false, false>);
     }
-    if (epi) return eprej ? search_kernel<true, true, false> : search_kernel<true, false, false>;
-    return eprej ? search_kernel<false, true, false> : search_kernel<false, false, false>;
+    if (dense) {
+        if (epi) return eprej ? search_kernel<2, true, true, true, false> : search_kernel<2, true, false, true, false>;
+        return eprej ? search_kernel<2, false, true, true, false> : search_kernel<2, false, false, true, false>;
+    }
+    return epi ? search_kernel<2, true, true, false, false> : search_kernel<2, false, true, false, false>;
+}
+
+void search_form(BatchArgs &a) {
+    if (!search_variants(a)) {
+        a.qpl = 2;
+        a.persist = 0;
+    }
 }
 
 int search_ctas_per_sm(const BatchArgs &a) {
@@ -2168,12 +2229,13 @@ cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s, int prio) {
     return launch_prio(pair_prep_kernel, dim3(a.n_search), dim3(kPrepThreads), 0, s, prio, a);
 }
 
-cudaError_t launch_search(const BatchArgs &a, cudaStream_t s, int prio) {
+cudaError_t launch_search(const BatchArgs &a, int ctas, cudaStream_t s, int prio) {
     if (a.n_search == 0) return cudaSuccess;
     const size_t smem = search_smem_bytes(a.sn);
     cudaError_t e = cudaFuncSetAttribute(search_fn(a), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_prio(search_fn(a), dim3(a.n_search), dim3(kSearchThreads), smem, s, prio, a);
+    const uint32_t grid = a.persist ? (uint32_t)std::max(1, std::min(ctas, (int)a.n_search)) : a.n_search;
+    return launch_prio(search_fn(a), dim3(grid), dim3(kSearchThreads), smem, s, prio, a);
 }
 
 size_t dense_smem_bytes() { return kDenseSmem; }

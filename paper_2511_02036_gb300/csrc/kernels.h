@@ -23,7 +23,11 @@ cudaError_t launch_stage_gather(const GatherJob *jobs, int n, unsigned char *bas
 size_t search_smem_bytes(int sn);
 int search_ctas_per_sm(const BatchArgs &a);
 cudaError_t launch_prep(const BatchArgs &a, cudaStream_t s, int prio = 0);
-cudaError_t launch_search(const BatchArgs &a, cudaStream_t s, int prio = 0);
+// The form a search launch gets: a.qpl and a.persist reset to 2 and 0 for the gate
+// configurations that only have that form.
+void search_form(BatchArgs &a);
+// ctas: CTAs of a persistent launch (a.persist; one per pair otherwise)
+cudaError_t launch_search(const BatchArgs &a, int ctas, cudaStream_t s, int prio = 0);
 // Dense node blocks on the tensor cores (a.sp.dense_min > 0): a.n_search * a.dsplit CTAs;
 // writes a.dres, which launch_search then reads (same stream, before it).
 size_t dense_smem_bytes();

@@ -290,6 +290,9 @@ struct BatchArgs {
                                   // listed from WorkItem::c: (target position << 16 | caller,
                                   // bin << 25 | distance << 16 | target caller index)
     uint32_t l2_prefetch;         // search CTAs ask L2 to prefetch their pair's descriptors
+    uint32_t qpl;                 // search: queries per lane of a warp's group (1 or 2)
+    uint32_t persist;             // search: resident CTAs take pairs from *work (else CTA per pair)
+    uint32_t *work;               // next pair of the persistent search (reset by the copy kernel)
     float *pconst;                // [n_search][kPairConst] per-pair constants (prep kernel)
     uint2 *pwords;                // per pair from toff / 32: eligibility words (bits, count before)
                                   //   and one closing word (0, eligible total)

@@ -480,7 +480,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &points, &point_ok})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok})
         b->release();
     h_stage.release();
     h_out.release();
@@ -538,8 +538,8 @@ static tm_status check_params(const tm_search_params &sp, const tm_fuse_params &
         return fail(TM_ERR_INVALID_ARG, "bad search parameters");
     if (sp.mode != TM_MODE_FUSED && sp.mode != TM_MODE_PER_PAIR)
         return fail(TM_ERR_INVALID_ARG, "bad search mode %d", sp.mode);
-    if (sp.dense_min != 0 && sp.dense_min < 16)
-        return fail(TM_ERR_INVALID_ARG, "dense_min must be 0 or >= 16 (got %d)", sp.dense_min);
+    if (sp.dense_min != 0 && sp.dense_min != -1 && sp.dense_min < 16)
+        return fail(TM_ERR_INVALID_ARG, "dense_min must be 0, -1 (tuned) or >= 16 (got %d)", sp.dense_min);
     if (!(sp.epipole_px >= 0.0f && sp.epipole_px < 1e6f))
         return fail(TM_ERR_INVALID_ARG, "epipole_px must be in [0, 1e6)");
     if (sp.rot_mode != 0 && sp.rot_mode != 1) return fail(TM_ERR_INVALID_ARG, "rot_mode must be 0 or 1");
@@ -847,7 +847,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (sp.dense_min > 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))) ||
+        (sp.dense_min != 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))) ||
+        (e = B.work.reserve(16)) ||
         (e = B.acc.reserve(std::max<size_t>(1, dq) * 8)) ||
         (e = B.pconst.reserve(nsi * kPairConst * 4)) || (e = B.pwords.reserve(std::max<uint32_t>(64, tq) / 32 * 8)) ||
         (e = B.pepos.reserve(std::max<uint32_t>(64, tq) * 2)) ||
@@ -932,7 +933,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.pconst = static_cast<float *>(B.pconst.p);
     A.pwords = static_cast<uint2 *>(B.pwords.p);
     A.pepos = static_cast<uint16_t *>(B.pepos.p);
-    A.l2_prefetch = c->force_prefetch == 1 ? 1u : 0u;  // measured: off is faster (setup copies wait less)
+    A.work = static_cast<uint32_t *>(B.work.p);
+    if ((e = cudaMemsetAsync(B.work.p, 0, 4, s))) return cuda_fail(e, "work counter");
     A.triangulate = tri ? 1 : 0;
     A.tri_cos_max = tri ? tri->cos_parallax_max : 0.0;
     A.tri_chi2 = tri ? tri->chi2 : 0.0;
@@ -941,7 +943,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.point_ok = static_cast<uint8_t *>(B.point_ok.p);
     // dense kernel: at most one wave of three CTAs per SM over the pairs (a CTA takes every
     // dsplit-th dense run of its pair)
-    A.dsplit = (uint32_t)std::max(1, std::min(64, 3 * c->num_sms / (int)nsi));
+    B.dsplit_base = (uint32_t)std::max(1, std::min(64, 3 * c->num_sms / (int)nsi));
+    A.dsplit = B.dsplit_base;
+    B.user_dense_min = sp.dense_min;
     B.sp = sp;
     B.fp = fp;
     rollback.armed = false;
@@ -951,7 +955,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
 std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, acc.p, pconst.p,
-            pwords.p, pepos.p, points.p,
+            pwords.p, pepos.p, work.p, points.p,
             point_ok.p};
 }
 
@@ -991,8 +995,17 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     cudaError_t e;
     B.threads = threads;
     B.lanes = lanes;
-    B.ctas = (int)B.n_search_items;
-    if (search_ctas_per_sm(B.args) < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
+    // the launch choices in effect: the tuner's (B.knobs) unless a test hook fixes one
+    BatchArgs &KA = B.args;
+    KA.qpl = (uint32_t)(c->force_qpl ? c->force_qpl : B.knobs.qpl);
+    KA.persist = (uint32_t)(c->force_persist >= 0 ? c->force_persist : B.knobs.persist);
+    KA.l2_prefetch = (uint32_t)(c->force_prefetch >= 0 ? c->force_prefetch : B.knobs.prefetch);
+    if (B.user_dense_min < 0) KA.sp.dense_min = B.knobs.dense_min;
+    KA.dsplit = std::max(1u, B.dsplit_base / (uint32_t)std::max(1, B.knobs.dsplit_div));
+    search_form(KA);
+    const int per_sm = search_ctas_per_sm(KA);
+    if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
+    B.ctas = KA.persist ? std::min((int)B.n_search_items, per_sm * c->num_sms) : (int)B.n_search_items;
     if (timed && !B.ev[0])
         for (cudaEvent_t &ev : B.ev)
             if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
@@ -1003,23 +1016,29 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     // when SMs free up (priorities within the device's range; `hi` is numerically lowest)
     int lo_p = 0, hi_p = 0;
     if ((e = cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p))) return cuda_fail(e, "priorities");
+    // which branch's CTAs the scheduler places first when SMs free up: the store branch
+    // (ingest -> fusion) or the search branch
+    int sp_ = hi_p, st_ = lo_p;
+    const int bprio = c->branch_prio >= 0 ? c->branch_prio : B.knobs.bprio;
+    if (bprio == 1) std::swap(sp_, st_);
+    if (bprio == 2) sp_ = st_ = 0;
     if ((e = mark(0, s))) return cuda_fail(e, "event");
     const bool after_ingest = B.n_new > 0 && B.nbr_new;
     const bool forked = B.forked, mp_async = B.mp_async;  // set by prepare_batch, for this enqueue only
     B.forked = B.mp_async = false;
     if (!after_ingest && !forked && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
-    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, lo_p))) return cuda_fail(e, "ingest kernel");
+    if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, st_))) return cuda_fail(e, "ingest kernel");
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
-        (e = launch_prep(B.args, B.paux, hi_p)) || (e = mark(7, B.paux)) ||
-        (e = launch_dense(B.args, B.paux, hi_p)) ||
+        (e = launch_prep(B.args, B.paux, sp_)) || (e = mark(7, B.paux)) ||
+        (e = launch_dense(B.args, B.paux, sp_)) ||
         (B.args.sp.dense_min > 0 && B.n_search_items > 0 && (e = mark(6, B.paux))) ||
-        (e = launch_search(B.args, B.paux, hi_p)) ||
+        (e = launch_search(B.args, B.ctas, B.paux, sp_)) ||
         (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
         return cuda_fail(e, "search kernel");
     if (mp_async && (e = cudaStreamWaitEvent(s, B.mready, 0))) return cuda_fail(e, "map points");
-    if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, lo_p))) || (e = mark(3, s)) ||
+    if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, st_))) || (e = mark(3, s)) ||
         (e = cudaStreamWaitEvent(s, B.join, 0)))
         return cuda_fail(e, "fusion kernel");
     // copy: about one warp per item (32 per CTA), at most one CTA per SM
@@ -1162,8 +1181,11 @@ int tmap::default_threads(const tm_ctx *, const BatchBuf &) { return 256; }
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int key, th, ln;
-    while (fscanf(f, "%d %d %d", &key, &th, &ln) == 3) c->tuned[key] = {th, ln};
+    int key;
+    Knobs k;
+    while (fscanf(f, "%d %d %d %d %d %d %d", &key, &k.qpl, &k.persist, &k.prefetch, &k.bprio, &k.dense_min,
+                  &k.dsplit_div) == 7)
+        if ((k.qpl == 1 || k.qpl == 2) && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
     fclose(f);
 }
 
@@ -1172,7 +1194,10 @@ static void save_tuning(tm_ctx *c) {
     if (!path) return;
     FILE *f = fopen(path, "w");
     if (!f) return;
-    for (auto &kv : c->tuned) fprintf(f, "%d %d %d\n", kv.first, kv.second.first, kv.second.second);
+    for (auto &kv : c->tuned_knobs) {
+        const Knobs &k = kv.second;
+        fprintf(f, "%d %d %d %d %d %d %d\n", kv.first, k.qpl, k.persist, k.prefetch, k.bprio, k.dense_min, k.dsplit_div);
+    }
     fclose(f);
 }
 
@@ -1190,62 +1215,85 @@ static uint64_t batch_queries(tm_ctx *c, const BatchBuf &B, const tm_step *steps
     return q;
 }
 
-// Picks (threads, lanes) for a prepared batch: cached by density class, else measured.
+// Picks the launch choices of a prepared batch (B.knobs): cached by batch regime, else measured
+// by coordinate descent (each choice in turn, the others held at the best so far; a choice is
+// timed over three enqueues after a warm-up).  The regime: density class (comparisons per query
+// of a first run), pairs fewer than SMs, dense blocks left to the tuner.  Results never depend
+// on the choices.
 tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure) {
     tm_status st;
-    if (c->force_threads) {
-        B.threads = c->force_threads;
-        B.lanes = c->def_lanes;
-        return TM_OK;
-    }
-    if ((st = enqueue_fused(c, B, default_threads(c, B), c->def_lanes, s))) return st;
+    B.threads = 256;
+    B.lanes = c->def_lanes;
+    B.knobs = Knobs{};
+    B.tuned = false;
+    if ((st = enqueue_fused(c, B, 256, c->def_lanes, s))) return st;
     unsigned long long hc[2];
     cudaError_t e;
     if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "tuning");
-    // density class, and whether the pairs are fewer than the SMs (the block size choices differ)
-    const int key = density_key(hc[0], batch_queries(c, B, steps)) * 2 + ((int)B.n_search_items < c->num_sms ? 1 : 0);
-    auto it = c->tuned.find(key);
-    if (it != c->tuned.end()) {
-        B.threads = it->second.first;
-        B.lanes = it->second.second;
+    const bool dense_auto = B.user_dense_min < 0 && B.n_search_items > 0;
+    const int key = (density_key(hc[0], batch_queries(c, B, steps)) * 2 +
+                     ((int)B.n_search_items < c->num_sms ? 1 : 0)) * 2 + (dense_auto ? 1 : 0);
+    auto it = c->tuned_knobs.find(key);
+    if (it != c->tuned_knobs.end()) {
+        B.knobs = it->second;
+        B.tuned = true;
         return TM_OK;
     }
-    if (!measure) {
-        B.threads = default_threads(c, B);
-        B.lanes = c->def_lanes;
-        return TM_OK;
-    }
+    if (!measure) return TM_OK;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int bt = default_threads(c, B), bl = c->def_lanes;
-    // threads per search CTA (warps sharing one pair); lanes per query only shape the plain form
-    std::vector<int> threads_set = {256};
-    for (int th : threads_set)
-        for (int ln : {c->def_lanes}) {
-            if ((st = enqueue_fused(c, B, th, ln, s))) break;  // warm-up
-            float tot = 0.0f;
-            for (int r = 0; r < 3; ++r) {
-                cudaEventRecord(e0, s);
-                if ((st = enqueue_fused(c, B, th, ln, s))) break;
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                tot += ms;
-            }
-            if (st) break;
-            if (tot < best) { best = tot; bt = th; bl = ln; }
+    auto time_of = [&](const Knobs &k, float &ms) -> tm_status {
+        B.knobs = k;
+        tm_status r = enqueue_fused(c, B, 256, c->def_lanes, s);  // warm-up
+        ms = 0.0f;
+        for (int rep = 0; rep < 3 && !r; ++rep) {
+            cudaEventRecord(e0, s);
+            if ((r = enqueue_fused(c, B, 256, c->def_lanes, s))) break;
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms += t;
         }
+        return r;
+    };
+    Knobs best{};
+    float tbest = 0.0f;
+    st = time_of(best, tbest);
+    const bool both_branches = B.n_search_items > 0 && (B.n_new > 0 || B.n_items > B.n_search_items);
+    for (int knob = 0; knob < 6 && !st; ++knob) {
+        std::vector<Knobs> alts;
+        Knobs k = best;
+        switch (knob) {
+            case 0: if (!c->force_qpl) { k.qpl = best.qpl == 2 ? 1 : 2; alts.push_back(k); } break;
+            case 1: if (c->force_persist < 0) { k.persist = !best.persist; alts.push_back(k); } break;
+            case 2: if (c->force_prefetch < 0) { k.prefetch = !best.prefetch; alts.push_back(k); } break;
+            case 3: if (c->branch_prio < 0 && both_branches) { k.bprio = !best.bprio; alts.push_back(k); } break;
+            case 4:
+                if (dense_auto)
+                    for (int dm : {64, 32, 128})
+                        if (dm != best.dense_min) { k.dense_min = dm; alts.push_back(k); }
+                break;
+            case 5: if (best.dense_min > 0 && B.dsplit_base > 1) { k.dsplit_div = 2; alts.push_back(k); } break;
+        }
+        for (const Knobs &a : alts) {
+            float t = 0.0f;
+            if ((st = time_of(a, t))) break;
+            if (t < tbest) {
+                tbest = t;
+                best = a;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
-    c->tuned[key] = {bt, bl};
+    B.knobs = best;
+    B.tuned = true;
+    c->tuned_knobs[key] = best;
     save_tuning(c);
-    B.threads = bt;
-    B.lanes = bl;
     return TM_OK;
 }
 
@@ -1274,12 +1322,8 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     } else {
         int th = default_threads(c, B), ln = c->def_lanes;
         if (sp.lanes_per_query) ln = sp.lanes_per_query;
-        else if (c->last_staged == 1 && (c->last_threads > 256) == (th > 256)) {
-            // the last tuned plan's choice, if it was made for the same regime (pairs below
-            // or above the SM count)
-            th = c->last_threads;
-            ln = c->last_lanes;
-        }
+        // the last tuned plan's launch choices (one-shot batches are not measured)
+        B.knobs = c->last_staged == 1 ? c->last_knobs : Knobs{};
         st = enqueue_fused(c, B, th, ln, s);
     }
     if (!st) {
@@ -1490,6 +1534,19 @@ extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
                 return fail(TM_ERR_INVALID_ARG, "tm_debug_set: search threads must be 0 or 256");
             c->force_threads = (int)value;
             return TM_OK;
+        case TM_DEBUG_BRANCH_PRIORITY:
+            if (value < -1 || value > 2)
+                return fail(TM_ERR_INVALID_ARG, "tm_debug_set: branch priority must be -1, 0, 1 or 2");
+            c->branch_prio = (int)value;
+            return TM_OK;
+        case TM_DEBUG_QUERIES_PER_LANE:
+            if (value < 0 || value > 2) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: queries per lane must be 0, 1 or 2");
+            c->force_qpl = (int)value;
+            return TM_OK;
+        case TM_DEBUG_PERSISTENT:
+            if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: persistent must be -1, 0 or 1");
+            c->force_persist = (int)value;
+            return TM_OK;
         case TM_DEBUG_L2_PREFETCH:
             if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: L2 prefetch must be -1, 0 or 1");
             c->force_prefetch = (int)value;
@@ -1526,6 +1583,7 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
             if (!st) {
                 c->last_threads = P->B.threads;
                 c->last_lanes = P->B.lanes;
+                c->last_knobs = P->B.knobs;
                 c->last_staged = 1;
             }
         }
@@ -1624,6 +1682,21 @@ extern "C" tm_status tm_plan_info(tm_plan *P, int32_t *threads, int32_t *lanes, 
     if (lanes) *lanes = P->B.lanes;
     if (ctas) *ctas = P->B.ctas;
     if (kernels) *kernels = P->kernels_per_run;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_plan_get_tuning(tm_plan *P, tm_plan_tuning *out) {
+    if (!P || !out) return fail(TM_ERR_INVALID_ARG, "tm_plan_get_tuning: null argument");
+    const BatchArgs &A = P->B.args;
+    const bool fused = P->B.sp.mode != TM_MODE_PER_PAIR;
+    out->queries_per_warp = fused ? 32 * (int)A.qpl : 0;
+    out->persistent = fused ? (int)A.persist : 0;
+    out->l2_prefetch = fused ? (int)A.l2_prefetch : 0;
+    out->branch_priority = fused ? (P->ctx->branch_prio >= 0 ? P->ctx->branch_prio : P->B.knobs.bprio) : 0;
+    out->dense_min = fused && A.sp.dense_min > 0 ? A.sp.dense_min : 0;
+    out->dense_split = out->dense_min > 0 ? (int)A.dsplit : 0;
+    out->search_ctas = fused ? P->B.ctas : 0;
+    out->tuned = P->B.tuned ? 1 : 0;
     return TM_OK;
 }
 

@@ -56,10 +56,20 @@ struct IngestStage {
     void release() { dev.release(); host.release(); }
 };
 
+// Launch choices of a batch's fused form that the autotuner makes (results never depend on
+// them): queries per lane of a search warp's group (1: 32-query groups, 2: 64), persistent
+// search CTAs, the L2 prefetch of a pair's descriptors, which branch the scheduler serves
+// first (0 search, 1 store), dense node blocks from this run length (0 = off; only when the
+// caller asks for the tuner's choice, dense_min -1), the dense kernel's split divisor.
+struct Knobs {
+    int qpl = 2, persist = 0, prefetch = 0, bprio = 0, dense_min = 0, dsplit_div = 1;
+};
+
 // Device and staging buffers of one batch, plus what the host needs to read its results.
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
-        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, points, point_ok;
+        counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, work, points,
+        point_ok;
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -77,6 +87,10 @@ struct BatchBuf {
     uint32_t res_total = 0, t_total = 0, fsn = 16;
     int n_steps = 0, n_pairs = 0, smem_n = 32;
     int threads = 256, lanes = 1, ctas = 0;
+    Knobs knobs;                   // the fused form's launch choices (tune_batch)
+    bool tuned = false;            // knobs measured or cached by the tuner
+    int user_dense_min = 0;        // the caller's dense_min (-1: the tuner's choice)
+    uint32_t dsplit_base = 1;      // dense kernel CTAs per pair before the tuner's divisor
     tm_search_params sp{};
     tm_fuse_params fp{};
     BatchArgs args{};
@@ -117,11 +131,16 @@ struct tm_ctx {
     tmap::BatchBuf batch;
     tmap::DevBuf mask_scratch;
     std::map<int, std::pair<int, int>> tuned;
+    std::map<int, tmap::Knobs> tuned_knobs;
+    tmap::Knobs last_knobs;
     int def_threads = 256, def_lanes = 1, last_threads = 256, last_lanes = 1, last_staged = -1;
     long long wait_limit = 4000000000ll;  // bound of device bulk-copy waits (SM cycles)
     uint32_t starve = 0;                  // test hook: bounded waits run out (no copy in flight)
     int force_threads = 0;                // test hook: threads per search CTA (0 = tuned)
     int force_prefetch = -1;              // test hook: search CTAs' L2 prefetch (-1 = tuned)
+    int branch_prio = -1;                 // test hook: 0 search branch first, 1 store, 2 equal, -1 tuned
+    int force_qpl = 0;                    // test hook: queries per lane of a search group (0 = tuned)
+    int force_persist = -1;               // test hook: persistent search CTAs (-1 = tuned)
     ~tm_ctx();
 };
 

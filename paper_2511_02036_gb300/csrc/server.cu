@@ -324,10 +324,8 @@ bool admit(tm_server *S, Flight &F) {
             if (!st) {
                 int th = default_threads(c, F.B), ln = c->def_lanes;
                 if (S->cfg.search.lanes_per_query) ln = S->cfg.search.lanes_per_query;
-                else if (c->last_staged == 1 && (c->last_threads > 256) == (th > 256)) {
-                    th = c->last_threads;
-                    ln = c->last_lanes;
-                }
+                // the last tuned plan's launch choices (served requests are not measured)
+                F.B.knobs = c->last_staged == 1 ? c->last_knobs : Knobs{};
                 st = S->cfg.search.mode == TM_MODE_PER_PAIR ? enqueue_plain(c, F.B, ln, F.stream)
                                                             : enqueue_fused(c, F.B, th, ln, F.stream);
             }
