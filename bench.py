@@ -47,12 +47,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--seed", type=int, default=2000)
-    ap.add_argument("--serve-kf", type=int, default=600, help="keyframes of the serving stream (0: skip)")
+    ap.add_argument("--serve-kf", type=int, default=3000, help="keyframes of the serving stream (0: skip)")
+    ap.add_argument("--serve-kf-20", type=int, default=600,
+                    help="keyframes served at 20/s (the stream's first ones; 3000 take 150 s)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-node (tensor-core) workload")
     ap.add_argument("--no-forward", action="store_true", help="skip the step with forward-direction fusion")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-step configurations (cfg0, cfg1, cfg3)")
     return ap.parse_args()
 
 
@@ -517,9 +520,13 @@ def run_mine(args, rank, world, local_rank):
     if not args.no_forward and rank == 0:
         out["forward_fusion"] = run_forward(tm, stream, flush, local_rank, max(3, args.steps // 2), args.seed)
 
+    # ---------------------------------------------------------------- single-step configurations
+    if not args.no_configs and rank == 0:
+        out["configs"] = run_configs(tm, stream, flush, local_rank, max(20, args.steps), min(2.0, args.cpu_seconds / 4))
+
     # ---------------------------------------------------------------- serving
     if args.serve_kf > 0 and rank == 0:
-        out["serving"] = run_serving(tm, args.serve_kf, local_rank)
+        out["serving"] = run_serving(tm, args.serve_kf, local_rank, args.serve_kf_20)
 
     # ---------------------------------------------------------------- oracle on host cores
     if rank == 0:
@@ -656,23 +663,107 @@ def run_forward(tm, stream, flush, device, reps, seed):
     return out
 
 
-def run_serving(tm, n_kf, device):
-    """Continuous batching under Poisson arrivals at 20, 100 and 500 keyframes/s on a stream
-    of n_kf keyframes (cfg4 model), and the plain per-pair form served one request at a
-    time at 500 keyframes/s."""
+def time_plan(plan, stream, flush, reps):
+    """Device milliseconds of `reps` replays of a plan, each after an L2 flush, timed by
+    CUDA events on the launching stream."""
+    import torch
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        e0[k].record(stream)
+        plan.run(stream)
+        e1[k].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
+
+
+def config_workloads():
+    """The single-step configurations: (name, description, workload in the step format)."""
+    from gen import workloads as W
+    p = W.make_pair_cfg0(0)
+    cfg0 = dict(cam=p["cam"], frames=[p["Q"], p["T"]], steps=[dict(q=0, nbrs=[1])])
+    return [("cfg0", "single pair: 640x480 f=450, 500 keypoints, 200 planted correspondences, "
+                     "0.3 m baseline, 5 deg yaw, 1000 BoW nodes, no masks, no fusion", cfg0),
+            ("cfg1", "EuRoC-shaped step: 752x480 f=458, new keyframe + 10 neighbours, 1200 keypoints, "
+                     "40% shared points, masks, ~6000 map points fused", W.make_cfg1()),
+            ("cfg3", "TUM-VI-shaped step: 512x512 f=190, new keyframe + 20 neighbours, 1500 keypoints, "
+                     "50% shared, flip 0.08, 10000 BoW nodes, masks, map points fused", W.make_cfg3())]
+
+
+def run_configs(tm, stream, flush, device, reps, cpu_seconds):
+    """cfg0, cfg1 and cfg3, one step each: the fused plan (new keyframe ingested in the step,
+    search, fusion: one graph) against the plain per-pair form (neighbours and new keyframe
+    already stored), both checked against the oracle element by element, and the oracle on
+    one host core and on all of them."""
+    import oracle as O
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    out = {}
+    for name, desc, w in config_workloads():
+        st = w["steps"][0]
+        exp_pairs, ecs = O.search_step(w["cam"], w["frames"], st)
+        exp_fuse, ecf = O.fuse_step(w["cam"], w["frames"], st)
+        steps = [dict(kf_id=st["q"], nbrs=st["nbrs"], q_free=st.get("q_free"), nbr_free=st.get("nbr_free"),
+                      mps=st.get("mps"))]
+        row = {"workload": desc, "pairs": len(st["nbrs"]), "comparisons_per_step": int(ecs + ecf),
+               "map_points": int(st["mps"]["n"]) if st.get("mps") is not None else 0}
+        with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+            ctx.add_keyframes(list(st["nbrs"]), [w["frames"][i] for i in st["nbrs"]])
+            for form, kw in (("batched", dict(new=([st["q"]], [w["frames"][st["q"]]]))),
+                             ("plain", dict(sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR)))):
+                with ctx.plan(steps, **kw) as plan:
+                    for _ in range(3):
+                        plan.run(stream)
+                    res = plan.results(stream)
+                    # parity with the oracle, element by element, for this form
+                    assert len(res.pairs) == len(exp_pairs)
+                    for g, e in zip(res.pairs, exp_pairs):
+                        assert np.array_equal(g, e), (name, form)
+                    assert np.array_equal(res.fuses[0], exp_fuse), (name, form)
+                    assert res.n_comparisons_search == ecs and res.n_comparisons_fuse == ecf
+                    ms = time_plan(plan, stream, flush, reps)
+                    row[form] = {"keyframes_per_s": 1e3 / float(ms.mean()), "ms_per_step": float(ms.mean()),
+                                 "gcomparisons_per_s": (ecs + ecf) / (float(ms.mean()) / 1e3) / 1e9,
+                                 "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                                 "kernels_per_run": plan.info()["kernels_per_run"], "parity": "oracle, bit-exact"}
+        row["batched"]["note"] = "includes the new keyframe's ingest into the store"
+        row["plain"]["note"] = "new keyframe already stored; one launch sequence per pair"
+        n, cmp, el = oracle_sample(w, cpu_seconds)
+        row["oracle_1_core"] = {"keyframes_per_s": n / el, "gcomparisons_per_s": cmp / el / 1e9,
+                                "sample": "%d repetitions of the step, %.1f s" % (n, el)}
+        n, cmp, el = oracle_sample_threads(w, cpu_seconds, threads)
+        row["oracle_all_cores"] = {"keyframes_per_s": n / el, "gcomparisons_per_s": cmp / el / 1e9, "cores": threads,
+                                   "sample": "%d repetitions of the step on %d threads, %.1f s" % (n, threads, el)}
+        out[name] = row
+    return out
+
+
+def run_serving(tm, n_kf, device, rate20_kf):
+    """Continuous batching on the cfg4 stream (n_kf keyframes along a 10-minute trajectory,
+    752x480, 1000-2000 keypoints, 5-20 neighbours; store budget 5000 keyframe slots):
+    Poisson arrivals at 20, 100 and 500 keyframes/s, every request at once (the served
+    ceiling), a tight store (64 slots, the oldest keyframes evicted) at 500/s showing
+    admission by memory, and the plain per-pair form served one request at a time at 500/s
+    and at once.  The 20/s rate serves the stream's first rate20_kf keyframes (its full
+    length takes n_kf / 20 seconds of wall time)."""
     from gen import workloads as W
     w = W.make_stream_cfg4(seed=4000, n_kf=n_kf, duration_s=600.0 * n_kf / 3000.0)
-    out = {"keyframes": n_kf, "stream": "cfg4 model: 752x480, 1000-2000 keypoints, 5-20 neighbours"}
+    out = {"keyframes": n_kf, "stream": "cfg4: 752x480 f=458, 1000-2000 keypoints, 5-20 neighbours, "
+                                        "10-minute trajectory, masks, map points fused"}
+    with tm.Context(w["cam"], max_kp=2048, device=device) as probe:
+        slot = probe.stats()["slot_bytes"]
+    out["store_budget"] = {"slots": 5000, "slot_bytes": slot, "bytes": 5000 * slot}
 
-    def serve(rate, **cfg):
+    def serve(rate, n=None, slots=5000, **cfg):
+        n = n or n_kf
         rng = np.random.default_rng(7)
-        arr = np.cumsum(rng.exponential(1.0 / rate, n_kf))
-        with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+        arr = np.cumsum(rng.exponential(1.0 / rate, n)) if rate else np.zeros(n)
+        with tm.Context(w["cam"], max_kp=2048, budget=slots * slot, device=device) as ctx:
             with ctx.server(**cfg) as srv:
                 t0 = time.perf_counter()
                 t0_lib = tm.tm_now()
                 tickets = []
-                for k, st in enumerate(w["steps"]):
+                for k, st in enumerate(w["steps"][:n]):
                     while time.perf_counter() - t0 < arr[k]:
                         time.sleep(1e-4)
                     tickets.append(srv.submit(st["q"], w["frames"][st["q"]], st["nbrs"], st["q_free"],
@@ -684,17 +775,23 @@ def run_serving(tm, n_kf, device):
                     lat.append(info["t_done"] - info["t_submit"])
                     done = max(done, info["t_done"])
                     srv.take(t)
+                stats = srv.stats()
         lat = np.array(lat) * 1e3
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_ms": float(lat.max()), "offered_kf_per_s": rate,
-                "served_kf_per_s": n_kf / (done - t0_lib)}
+        return {"keyframes": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "offered_kf_per_s": rate if rate else "all at once",
+                "served_kf_per_s": n / (done - t0_lib), "server": stats}
 
-    for rate in (20, 100, 500):
-        if rate == 20 and n_kf > 600:
-            continue
-        out["continuous_batching_%d" % rate] = serve(rate, max_batch_requests=64, max_inflight_batches=3)
-    out["plain_per_pair_500"] = serve(500, max_batch_requests=1, max_inflight_batches=1,
-                                      sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR))
+    batched = dict(max_batch_requests=64, max_inflight_batches=3)
+    out["continuous_batching_20"] = serve(20, n=min(n_kf, rate20_kf), **batched)
+    for rate in (100, 500):
+        out["continuous_batching_%d" % rate] = serve(rate, **batched)
+    out["continuous_batching_all_at_once"] = serve(0, **batched)
+    tight = serve(500, slots=64, evict_after=40, **batched)
+    tight["note"] = "store budget 64 slots, evict_after 40: requests wait for slots as batches retire"
+    out["continuous_batching_500_tight_store"] = tight
+    plain = dict(max_batch_requests=1, max_inflight_batches=1, sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR))
+    out["plain_per_pair_500"] = serve(500, **plain)
+    out["plain_per_pair_all_at_once"] = serve(0, **plain)
     return out
 
 

@@ -360,8 +360,8 @@ class Sequence:
         tracked[mq] = rng.random(int(mq.sum())) < tracked_frac
         tracked_wp = np.unique(q_wp[tracked])
         q_free = (~tracked).astype(np.uint8)
-        nbr_has, obs_w, obs_f, obs_j, clutter, nbr_mapped_w, nbr_w = [], [], [], [], [], [], []
-        for f in nbrs:
+        nbr_has, obs_w, obs_k, obs_j, clutter, nbr_mapped_w, nbr_w = [], [], [], [], [], [], []
+        for k_nb, f in enumerate(nbrs):
             fr = self.frames[f]
             w = fr["wp"]
             has = np.zeros(fr["n"], bool)
@@ -370,12 +370,12 @@ class Sequence:
             has[sel] = True
             nbr_mapped_w.append(w[sel])
             nbr_w.append(w[w >= 0])
-            obs_w.append(w[sel]); obs_f.append(np.full(len(sel), f)); obs_j.append(sel)
+            obs_w.append(w[sel]); obs_k.append(np.full(len(sel), k_nb)); obs_j.append(sel)
             clutter.append(np.nonzero(w < 0)[0])
             nbr_has.append(has)
         nn = len(nbrs)
         obs_w = np.concatenate(obs_w) if nn else np.zeros(0, np.int64)
-        obs_f = np.concatenate(obs_f) if nn else np.zeros(0, np.int64)
+        obs_k = np.concatenate(obs_k) if nn else np.zeros(0, np.int64)  # index into nbrs
         obs_j = np.concatenate(obs_j) if nn else np.zeros(0, np.int64)
         uw, first = np.unique(obs_w, return_index=True)
         n_pool = len(uw)
@@ -386,20 +386,27 @@ class Sequence:
         if clutter_mp_frac is not None:
             frac = clutter_mp_frac
         centers = {f: camera_center(self.frames[f]["Tcw"]) for f in nbrs}
+        carr = np.array([centers[f] for f in nbrs]).reshape(nn, 3)
         # pool map points
         pos_p = self.pts[uw] + rng.normal(0, 0.005, (n_pool, 3))
-        ref_f, ref_j = obs_f[first], obs_j[first]
-        desc_p = np.stack([self.frames[f]["desc"][j] for f, j in zip(ref_f, ref_j)]) \
-            if n_pool else np.zeros((0, DESC_BYTES), np.uint8)
+        ref_k, ref_j = obs_k[first], obs_j[first]
+        # each pool point's reference keypoint (its first observing neighbour), gathered per
+        # neighbour
+        desc_p = np.zeros((n_pool, DESC_BYTES), np.uint8)
+        lvl_ref = np.zeros(n_pool, np.int64)
+        for k_nb in np.unique(ref_k):
+            m = ref_k == k_nb
+            fr = self.frames[nbrs[k_nb]]
+            desc_p[m] = fr["desc"][ref_j[m]]
+            lvl_ref[m] = fr["level"][ref_j[m]]
         slot = np.searchsorted(uw, obs_w)
-        cobs = np.stack([centers[f] for f in obs_f]) if len(obs_f) else np.zeros((0, 3))
+        cobs = carr[obs_k] if len(obs_k) else np.zeros((0, 3))
         v = pos_p[slot] - cobs
         v /= np.linalg.norm(v, axis=1)[:, None]
         acc = np.zeros((n_pool, 3))
         np.add.at(acc, slot, v)
         nrm_p = acc / np.linalg.norm(acc, axis=1)[:, None] if n_pool else acc
-        cref = np.stack([centers[f] for f in ref_f]) if n_pool else np.zeros((0, 3))
-        lvl_ref = np.array([self.frames[f]["level"][j] for f, j in zip(ref_f, ref_j)], np.int64)
+        cref = carr[ref_k] if n_pool else np.zeros((0, 3))
         maxd_p = np.linalg.norm(pos_p - cref, axis=1) * SCALE_FACTOR ** lvl_ref
         skip_p = np.isin(uw, tracked_wp).astype(np.uint8)
         # single-view map points lifted from neighbour clutter

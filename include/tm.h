@@ -515,6 +515,22 @@ tm_status tm_server_take(tm_server *srv, uint64_t ticket, tm_match *matches,
 tm_status tm_server_take_ex(tm_server *srv, uint64_t ticket, tm_match *matches,
                             int32_t *pair_offsets, tm_fuse_match *fuse, tm_fuse_match *fwd,
                             int32_t *fwd_offsets, float *points, uint8_t *point_ok);
+/* Counters of a server since its start (admission by memory and eviction made visible).
+ *   submitted, admitted, completed, failed   requests (failed: completed with an error)
+ *   batches                                  launches of a batch (search + fusion)
+ *   deferrals                                admission rounds that left requests waiting
+ *                                            for a store slot (admission by memory)
+ *   evicted                                  keyframes the server removed (evict_after)
+ *   peak_pending                             most requests queued at once
+ *   peak_inflight                            most batches on the GPU at once
+ *   peak_store_slots                         most keyframe slots in use at once (whole store)
+ *   store_slot_limit                         slots the context's budget allows (-1: free memory
+ *                                            decides) */
+typedef struct {
+    int64_t submitted, admitted, completed, failed, batches, deferrals, evicted;
+    int32_t peak_pending, peak_inflight, peak_store_slots, store_slot_limit;
+} tm_server_stats;
+tm_status tm_server_get_stats(tm_server *srv, tm_server_stats *out);
 /* Drains the queue, stops the thread, frees the server. */
 tm_status tm_server_stop(tm_server *srv);
 

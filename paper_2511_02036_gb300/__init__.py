@@ -941,6 +941,15 @@ class Server:
             check(st)
         return {f: getattr(info, f) for f, _ in info._fields_}
 
+    def stats(self):
+        """The server's counters since its start (tm_server_get_stats) as a dict: requests
+        submitted / admitted / completed / failed, batches, admission rounds that waited for
+        store memory (deferrals), keyframes evicted, and the peaks of the queue, of the batches
+        in flight and of the store's occupied slots, beside the budget's slot limit."""
+        st = L.tm_server_stats()
+        check(tm_server_get_stats(self.handle, ctypes.byref(st)))  # noqa: F821
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
     def take(self, ticket):
         """Waits for the request and returns (per-pair match arrays, fusion array, info)."""
         info = self.poll(ticket, timeout=600.0)

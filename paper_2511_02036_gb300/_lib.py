@@ -128,6 +128,13 @@ class tm_request_info(ctypes.Structure):
                 ("t_submit", c_f64), ("t_admit", c_f64), ("t_done", c_f64), ("n_fwd", c_i32)]
 
 
+class tm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("batches", ctypes.c_int64), ("deferrals", ctypes.c_int64),
+                ("evicted", ctypes.c_int64), ("peak_pending", c_i32), ("peak_inflight", c_i32),
+                ("peak_store_slots", c_i32), ("store_slot_limit", c_i32)]
+
+
 P = ctypes.POINTER
 # name -> (restype, argtypes)
 SIGNATURES = {
@@ -182,6 +189,7 @@ SIGNATURES = {
     "tm_server_take": (c_i32, [c_p, c_u64, c_p, c_p, c_p]),
     "tm_server_take_ex": (c_i32, [c_p, c_u64, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "tm_server_stop": (c_i32, [c_p]),
+    "tm_server_get_stats": (c_i32, [c_p, P(tm_server_stats)]),
     "tm_now": (c_f64, []),
     "tm_search_pair_noalloc": (c_i32, [P(tm_camera), P(tm_keyframe_view), P(tm_keyframe_view),
                                        P(tm_search_params), c_p, c_p, c_p, c_p, c_p, c_p]),

@@ -111,6 +111,47 @@ __device__ __noinline__ void fundamental_lanes(const CamConst &cam, const double
     if (lane < 9) Fout[lane] = __double2float_rn(F);
 }
 
+// The same F for three pairs at once: lanes 9 k .. 9 k + 8 take pair k (k = 0, 1, 2; lanes
+// 27 .. 31 repeat pair 2's first lanes and write nothing), each lane one entry, with the
+// operation order of fundamental_lanes.  Tq[k], Tt[k]: the poses of pair k (null: no pair k,
+// its lanes idle); lane 9 k + e writes Fout[k][e].
+__device__ __noinline__ void fundamental_lanes3(const CamConst &cam, const double *const *Tq, const double *const *Tt,
+                                                float (*Fout)[12]) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int k = lane < 27 ? lane / 9 : 2, e = lane < 27 ? lane % 9 : lane - 27, r = e / 3, c = e % 3;
+    const int gb = 9 * k;  // the group's first lane
+    const double *tq = Tq[k] ? Tq[k] : Tq[0], *tt = Tt[k] ? Tt[k] : Tt[0];
+    double R = dmul(tq[r * 4 + 0], tt[c * 4 + 0]);
+    R = dadd(R, dmul(tq[r * 4 + 1], tt[c * 4 + 1]));
+    R = dadd(R, dmul(tq[r * 4 + 2], tt[c * 4 + 2]));
+    const double Rr0 = __shfl_sync(kFull, R, gb + 3 * r), Rr1 = __shfl_sync(kFull, R, gb + 3 * r + 1),
+                 Rr2 = __shfl_sync(kFull, R, gb + 3 * r + 2);
+    double s = dmul(Rr0, tt[0 * 4 + 3]);
+    s = dadd(s, dmul(Rr1, tt[1 * 4 + 3]));
+    s = dadd(s, dmul(Rr2, tt[2 * 4 + 3]));
+    const double tr = dsub(tq[r * 4 + 3], s);
+    const double t0 = __shfl_sync(kFull, tr, gb + 0), t1 = __shfl_sync(kFull, tr, gb + 3),
+                 t2 = __shfl_sync(kFull, tr, gb + 6);
+    const double tx[9] = {0.0, -t2, t1, t2, 0.0, -t0, -t1, t0, 0.0};
+    const double Kinv[9] = {cam.kinv[0], 0.0, cam.kinv[1], 0.0, cam.kinv[2], cam.kinv[3], 0.0, 0.0, 1.0};
+    double Am = dmul(Kinv[0 * 3 + r], tx[0 * 3 + c]);
+    Am = dadd(Am, dmul(Kinv[1 * 3 + r], tx[1 * 3 + c]));
+    Am = dadd(Am, dmul(Kinv[2 * 3 + r], tx[2 * 3 + c]));
+    const double Ar0 = __shfl_sync(kFull, Am, gb + 3 * r), Ar1 = __shfl_sync(kFull, Am, gb + 3 * r + 1),
+                 Ar2 = __shfl_sync(kFull, Am, gb + 3 * r + 2);
+    const double R0c = __shfl_sync(kFull, R, gb + c), R1c = __shfl_sync(kFull, R, gb + 3 + c),
+                 R2c = __shfl_sync(kFull, R, gb + 6 + c);
+    double B = dmul(Ar0, R0c);
+    B = dadd(B, dmul(Ar1, R1c));
+    B = dadd(B, dmul(Ar2, R2c));
+    const double Br0 = __shfl_sync(kFull, B, gb + 3 * r), Br1 = __shfl_sync(kFull, B, gb + 3 * r + 1),
+                 Br2 = __shfl_sync(kFull, B, gb + 3 * r + 2);
+    double F = dmul(Br0, Kinv[0 * 3 + c]);
+    F = dadd(F, dmul(Br1, Kinv[1 * 3 + c]));
+    F = dadd(F, dmul(Br2, Kinv[2 * 3 + c]));
+    if (lane < 27 && Tq[k]) Fout[k][e] = __double2float_rn(F);
+}
+
 // Epipolar line of a query in the target image: l = F^T x_Q = (a, b, c).
 struct Line { float a, b, c; };
 __device__ __forceinline__ Line epi_line(const float *F, float xq, float yq) {
@@ -1578,8 +1619,9 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
 }
 
 // Per-pair preparation for the search kernel, one CTA per search item (Sec. IV-C pair setup).
-// Warp 0: F by its nine lanes (float64, rounded to float32), then the epipole and the
-// pair-baseline skip when those variants are on.  Warps 1 .. 7, meanwhile, the neighbour's
+// Warp 0: in every third CTA, F of that CTA's pair and the next two (float64, rounded to
+// float32; nine lanes a pair, since this part's float64 pipe is narrow), then the epipole and
+// the pair-baseline skip when those variants are on.  Warps 1 .. 7, meanwhile, the neighbour's
 // eligibility in node order: each takes words [wb, we) of the position bitmap (a position's
 // mask byte read through its caller index, four words' loads in flight per lane), records
 // their ballots and counts, and after a barrier of these warps only writes each word with the
@@ -1589,16 +1631,27 @@ constexpr int kPrepThreads = 256;
 __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
     constexpr int nw = kPrepThreads / 32 - 1;  // eligibility warps (1 .. 7)
     __shared__ uint32_t wtot[nw];
-    __shared__ __align__(16) float F[12];
+    __shared__ float F3[3][12];
     __shared__ uint32_t sbits[TM_MAX_KP_LIMIT / 32];
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const uint32_t i = blockIdx.x;
     const WorkItem w = A.items[i];
     float *pc = A.pconst + (size_t)kPairConst * i;
     if (wid == 0) {
-        fundamental_lanes(A.cam, w.pq, w.pt, F);
-        __syncwarp();
-        if (lane < 9) pc[lane] = F[lane];
+        // F of pairs 3 (i / 3) .. 3 (i / 3) + 2 by the first CTA of each three (one warp, 27 lanes)
+        if (i % 3 == 0) {
+            const double *tq[3], *tt[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const bool have = i + k < A.n_search;
+                tq[k] = have ? A.items[i + k].pq : nullptr;
+                tt[k] = have ? A.items[i + k].pt : nullptr;
+            }
+            fundamental_lanes3(A.cam, tq, tt, F3);
+            __syncwarp();
+            if (lane < 27 && i + lane / 9 < A.n_search)
+                A.pconst[(size_t)kPairConst * (i + lane / 9) + lane % 9] = F3[lane / 9][lane % 9];
+        }
         if (lane == 0) {
             float e[2] = {0.0f, 0.0f};
             if (A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, e);

@@ -84,6 +84,7 @@ struct tm_server {
     uint64_t next_ticket = 1;
     cudaEvent_t last_ingest = nullptr;
     tm_status thread_error = TM_OK;
+    tm_server_stats stats{};  // under mu
 };
 
 extern "C" void tm_server_config_default(tm_server_config *c) {
@@ -148,6 +149,8 @@ void retire(tm_server *S, Flight &F) {
         }
         q->t_done = now;
         q->done = true;
+        S->stats.completed++;
+        if (st) S->stats.failed++;
     }
     F.reqs.clear();
     F.busy = false;
@@ -173,6 +176,8 @@ bool admit(tm_server *S, Flight &F) {
     std::vector<tm_keyframe_view> views;
     std::vector<uint64_t> ids;
     std::vector<Req *> failed, deferred;
+    int64_t evicted = 0;
+    int slots_in_use = 0;
     {
         std::lock_guard<std::mutex> lk(c->mu);
         cudaSetDevice(c->device);
@@ -185,6 +190,7 @@ bool admit(tm_server *S, Flight &F) {
                     if (c->slots[it->second].refs > 0) break;
                     c->free_slots.push_back(it->second);
                     c->ids.erase(it);
+                    ++evicted;
                 }
                 S->history.pop_front();
             }
@@ -339,6 +345,7 @@ bool admit(tm_server *S, Flight &F) {
                 cudaEventRecord(F.done, F.stream);
             }
         }
+        slots_in_use = (int)(c->slots.size() - c->free_slots.size());
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -349,6 +356,19 @@ bool admit(tm_server *S, Flight &F) {
         }
         for (Req *q : ok) q->t_admit = now;
         if (!failed.empty()) S->cv_done.notify_all();
+        tm_server_stats &sx = S->stats;
+        sx.admitted += (int64_t)ok.size();
+        sx.failed += (int64_t)failed.size();
+        sx.completed += (int64_t)failed.size();
+        sx.deferrals += deferred.empty() ? 0 : 1;
+        sx.evicted += evicted;
+        sx.batches += ok.empty() ? 0 : 1;
+        sx.peak_store_slots = std::max(sx.peak_store_slots, slots_in_use);
+        if (!ok.empty()) {
+            int infl = 1;
+            for (Flight &G : S->ring) infl += (&G != &F && G.busy) ? 1 : 0;
+            sx.peak_inflight = std::max(sx.peak_inflight, infl);
+        }
     }
     if (ok.empty()) return !failed.empty();
     F.reqs = ok;
@@ -390,6 +410,8 @@ void server_loop(tm_server *S) {
                 q->status = TM_ERR_NO_MEMORY;
                 q->done = true;
                 q->t_done = tm_now();
+                S->stats.completed++;
+                S->stats.failed++;
             }
             S->pending.clear();
             S->cv_done.notify_all();
@@ -506,7 +528,20 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
     *ticket = q->ticket;
     S->pending.push_back(q.get());
     S->reqs[q->ticket] = std::move(q);
+    S->stats.submitted++;
+    S->stats.peak_pending = std::max(S->stats.peak_pending, (int32_t)S->pending.size());
     S->cv_work.notify_one();
+    return TM_OK;
+}
+
+extern "C" tm_status tm_server_get_stats(tm_server *S, tm_server_stats *out) {
+    if (!S || !out) return fail(TM_ERR_INVALID_ARG, "tm_server_get_stats: null argument");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        *out = S->stats;
+    }
+    tm_ctx *c = S->ctx;
+    out->store_slot_limit = c->budget ? (int32_t)std::min<size_t>(c->budget / c->slot_bytes, INT32_MAX) : -1;
     return TM_OK;
 }
 

@@ -53,7 +53,7 @@ def test_struct_layout_matches_c(lib):
     structs = ["tm_camera", "tm_keyframe_view", "tm_mappoint_view", "tm_search_params",
                "tm_fuse_params", "tm_match", "tm_store_stats", "tm_step", "tm_batch_inputs",
                "tm_batch_result", "tm_server_config", "tm_request", "tm_request_info", "tm_fuse_apply_stats",
-               "tm_plan_tuning"]
+               "tm_plan_tuning", "tm_server_stats"]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tm.h"', "int main(void){"]
     for s in structs:
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))

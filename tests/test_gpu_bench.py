@@ -40,3 +40,11 @@ def test_bench_json_line():
     c = d["clocks"]
     assert "sm_mhz" in c and "sm_max_mhz" in c and isinstance(c["reasons"], list)
     assert d["gpu_launches"] >= 5
+    cf = d["configs"]
+    for name in ("cfg0", "cfg1", "cfg3"):
+        for form in ("batched", "plain"):
+            r = cf[name][form]
+            assert r["keyframes_per_s"] > 0 and r["p99_ms"] >= r["p50_ms"] > 0
+            assert r["parity"] == "oracle, bit-exact"
+        assert cf[name]["oracle_1_core"]["keyframes_per_s"] > 0
+        assert cf[name]["oracle_all_cores"]["cores"] >= 1

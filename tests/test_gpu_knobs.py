@@ -1,0 +1,162 @@
+"""Parity under every launch choice the autotuner can make: queries per warp group (32 or
+64), the persistent work-queue search, the L2 prefetch of a pair's descriptors, the branch
+priority, and the dense-block split.  Each choice is forced through tm_debug_set on a fresh
+context; the fused batch's results must equal the oracle's bit-exactly whatever it is, and
+tm_plan_get_tuning must report the choice in effect."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_02036_gb300 as tm
+    return tm
+
+
+def osp(sp):
+    return O.SearchParams(sp.hamming_max, sp.ratio_num, sp.ratio_den, sp.epi_chi2, sp.epipolar,
+                          sp.resolve, sp.rot_filter, sp.epipole_px, sp.rot_mode)
+
+
+def steps_of(w):
+    return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                 mps=s.get("mps")) for s in w["steps"]]
+
+
+def expected(w, sp=None):
+    pairs, fuses, cs, cf = [], [], 0, 0
+    for st in w["steps"]:
+        r, c = O.search_step(w["cam"], w["frames"], st, osp(sp) if sp is not None else None)
+        pairs.extend(r)
+        cs += c
+        f, c2 = O.fuse_step(w["cam"], w["frames"], st)
+        fuses.append(f)
+        cf += c2
+    return pairs, fuses, cs, cf
+
+
+def assert_same(res, exp):
+    pairs, fuses, cs, cf = exp
+    assert len(res.pairs) == len(pairs) and len(res.fuses) == len(fuses)
+    for g, e in zip(res.pairs, pairs):
+        np.testing.assert_array_equal(g, e)
+    for g, e in zip(res.fuses, fuses):
+        np.testing.assert_array_equal(g, e)
+    assert res.n_comparisons_search == cs
+    assert res.n_comparisons_fuse == cf
+
+
+def load_all(ctx, w):
+    ids = sorted(set(i for s in w["steps"] for i in [s["q"]] + s["nbrs"]))
+    ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
+
+
+@pytest.fixture(scope="module")
+def batch():
+    # several tiles of queries per pair and a ragged last group (600..2000 keypoints)
+    w = W.make_cfg2(seed=2200, n_steps=5)
+    return w, expected(w)
+
+
+def force(tm, ctx, qpl=None, persist=None, prefetch=None, bprio=None):
+    from paper_2511_02036_gb300 import _lib as L
+    if qpl is not None:
+        ctx.debug_set(L.TM_DEBUG_QUERIES_PER_LANE, qpl)
+    if persist is not None:
+        ctx.debug_set(L.TM_DEBUG_PERSISTENT, persist)
+    if prefetch is not None:
+        ctx.debug_set(L.TM_DEBUG_L2_PREFETCH, prefetch)
+    if bprio is not None:
+        ctx.debug_set(L.TM_DEBUG_BRANCH_PRIORITY, bprio)
+
+
+@pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))))
+def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
+    w, exp = batch
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        force(tm, ctx, qpl=qpl, persist=persist, prefetch=prefetch)
+        with ctx.plan(steps_of(w)) as plan:
+            t = plan.tuning()
+            assert t["queries_per_warp"] == 32 * qpl
+            assert t["persistent"] == persist and t["l2_prefetch"] == prefetch
+            if persist:
+                assert 1 <= t["search_ctas"] <= sum(len(s["nbrs"]) for s in w["steps"])
+            for _ in range(2):  # the replay resets the persistent work counter
+                plan.run()
+                assert_same(plan.results(), exp)
+        # the one-shot batch takes the same forced choices
+        assert_same(ctx.batch_run(steps_of(w)), exp)
+
+
+@pytest.mark.parametrize("bprio", [0, 1, 2])
+def test_branch_priority_matches_oracle(tm, batch, bprio):
+    w, exp = batch
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        force(tm, ctx, bprio=bprio)
+        with ctx.plan(steps_of(w)) as plan:
+            assert plan.tuning()["branch_priority"] == bprio
+            plan.run()
+            assert_same(plan.results(), exp)
+
+
+@pytest.mark.parametrize("qpl", [1, 2])
+def test_variant_gates_ignore_persistent(tm, qpl):
+    """With the epipole rejection on, the search takes its general instance: the persistent
+    request is set aside (reported as 0), the results still equal the oracle's."""
+    w = W.make_cfg2(seed=2201, n_steps=3)
+    sp = tm.SearchParams(epipole_px=12.0)
+    exp = expected(w, sp)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        force(tm, ctx, qpl=qpl, persist=1)
+        with ctx.plan(steps_of(w), sp=sp) as plan:
+            t = plan.tuning()
+            assert t["persistent"] == 0
+            plan.run()
+            assert_same(plan.results(), exp)
+
+
+@pytest.mark.parametrize("dense_min", [16, 100])
+@pytest.mark.parametrize("qpl", [1, 2])
+def test_dense_split_matches_oracle(tm, qpl, dense_min):
+    """Dense node blocks (tensor cores) beside the candidate rounds under each group width:
+    dense_min 16 sends nearly every block to the tensor cores, 100 splits pairs between both."""
+    w = W.make_cfg3b(seed=3510, n_nbrs=6)
+    sp = tm.SearchParams(dense_min=dense_min)
+    exp = expected(w, sp)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        force(tm, ctx, qpl=qpl, persist=1)
+        with ctx.plan(steps_of(w), sp=sp) as plan:
+            t = plan.tuning()
+            assert t["dense_min"] == dense_min and t["dense_split"] >= 1 and t["persistent"] == 0
+            plan.run()
+            assert_same(plan.results(), exp)
+
+
+def test_tuned_choice_matches_oracle(tm, batch):
+    """The tuner's own choice (measured on this device) and its cached reuse."""
+    w, exp = batch
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        with ctx.plan(steps_of(w)) as plan:
+            t = plan.tuning()
+            assert t["tuned"] == 1 and t["queries_per_warp"] in (32, 64)
+            plan.run()
+            assert_same(plan.results(), exp)
+        with ctx.plan(steps_of(w)) as plan:
+            assert plan.tuning() == t
+            plan.run()
+            assert_same(plan.results(), exp)

@@ -64,17 +64,28 @@ def test_stream_matches_oracle(tm, stream, batch, inflight, rate):
     assert np.all(lat > 0)
 
 
-def test_admission_by_memory_with_eviction(tm, stream):
+@pytest.mark.parametrize("batch", [2, 8])
+def test_admission_by_memory_with_eviction(tm, stream, batch):
     """A store that holds only 24 keyframes: the server evicts the oldest (neighbours reach
-    back at most 20) and every request still completes correctly."""
+    back at most 20) and every request still completes correctly.  With batches of 8 the
+    store cannot take a whole batch once 21 keyframes are kept: requests wait for slots
+    (deferrals), and the counters show it."""
     w = stream
     with tm.Context(w["cam"], max_kp=2048) as probe:
         slot = probe.stats()["slot_bytes"]
     with tm.Context(w["cam"], max_kp=2048, budget=24 * slot) as ctx:
-        with ctx.server(max_batch_requests=2, max_inflight_batches=2, evict_after=21) as srv:
+        with ctx.server(max_batch_requests=batch, max_inflight_batches=2, evict_after=21) as srv:
             tickets = submit_all(srv, w)
             check_against_oracle(srv, w, tickets)
+            s = srv.stats()
         assert ctx.stats()["slots_used"] <= 24
+    n = len(w["steps"])
+    assert s["submitted"] == s["admitted"] == s["completed"] == n and s["failed"] == 0
+    assert s["store_slot_limit"] == 24 and 21 <= s["peak_store_slots"] <= 24
+    assert s["evicted"] >= n - 24 and 1 <= s["peak_inflight"] <= 2
+    assert n / batch <= s["batches"] <= n
+    if batch == 8:
+        assert s["deferrals"] > 0
 
 
 def test_request_errors(tm, stream):

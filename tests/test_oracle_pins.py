@@ -481,7 +481,8 @@ def test_epipole_rejection_invariants():
 
 def test_triangulation_recovers_exact_points():
     """Noise-free planted correspondences: every planted match is accepted and its
-    triangulated point is the planted world point (float32 pixels, float64 solve)."""
+    triangulated point is the planted world point (float32 throughout: rays from float32
+    pixels and poses, the float32 closed-form midpoint of the two rays)."""
     p = W.make_pair_cfg0(5, noise_px=0.0)
     m, _ = O.search_pair(p["cam"], p["Q"], p["T"])
     xyz, ok = O.triangulate(p["cam"], p["Q"], p["T"], m)
