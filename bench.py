@@ -742,8 +742,8 @@ def run_serving(tm, n_kf, device, rate20_kf):
     """Continuous batching on the cfg4 stream (n_kf keyframes along a 10-minute trajectory,
     752x480, 1000-2000 keypoints, 5-20 neighbours; store budget 5000 keyframe slots):
     Poisson arrivals at 20, 100 and 500 keyframes/s, every request at once (the served
-    ceiling), a tight store (64 slots, the oldest keyframes evicted) at 500/s showing
-    admission by memory, and the plain per-pair form served one request at a time at 500/s
+    ceiling), a tight store (64 slots, the oldest keyframes evicted) at 500/s and at once,
+    showing admission by memory, and the plain per-pair form served one request at a time at 500/s
     and at once.  The 20/s rate serves the stream's first rate20_kf keyframes (its full
     length takes n_kf / 20 seconds of wall time)."""
     from gen import workloads as W
@@ -786,9 +786,12 @@ def run_serving(tm, n_kf, device, rate20_kf):
     for rate in (100, 500):
         out["continuous_batching_%d" % rate] = serve(rate, **batched)
     out["continuous_batching_all_at_once"] = serve(0, **batched)
-    tight = serve(500, slots=64, evict_after=40, **batched)
-    tight["note"] = "store budget 64 slots, evict_after 40: requests wait for slots as batches retire"
-    out["continuous_batching_500_tight_store"] = tight
+    for name, rate in (("continuous_batching_500_tight_store", 500), ("continuous_batching_all_at_once_tight_store", 0)):
+        tight = serve(rate, slots=64, evict_after=40, **batched)
+        tight["note"] = ("store budget 64 slots, the server keeps the newest 40 of its keyframes: a batch "
+                         "takes only the slots that are free, the rest of the queue waits for slots as "
+                         "earlier batches retire and their keyframes can be evicted (server.deferrals)")
+        out[name] = tight
     plain = dict(max_batch_requests=1, max_inflight_batches=1, sp=tm.SearchParams(mode=tm.TM_MODE_PER_PAIR))
     out["plain_per_pair_500"] = serve(500, **plain)
     out["plain_per_pair_all_at_once"] = serve(0, **plain)

@@ -364,6 +364,10 @@ typedef struct {
 tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
                        const tm_batch_inputs *in, const tm_search_params *sp,
                        const tm_fuse_params *fp, tm_batch_result *res, void *stream);
+/* Host wall time of the phases of the context's last tm_batch_run, in microseconds: us[0]
+ * the work list and the uploads (prepare), us[1] the launches, us[2] waiting for the GPU and
+ * the result counts, us[3] the result downloads.  Zeros before the first call. */
+tm_status tm_batch_last_host_times(tm_ctx *ctx, double us[4]);
 
 /* Prepared batch: uploads the inputs once and captures the launch in a CUDA graph; each
  * tm_plan_run replays it (asynchronous on `stream`, results stay on the device until

@@ -806,6 +806,13 @@ class Context:
             raise
         return _collect(r, bufs)
 
+    def last_host_times(self):
+        """Host microseconds of the phases of the last batch_run (tm_batch_last_host_times):
+        dict(prepare, launch, wait, download)."""
+        us = np.zeros(4, np.float64)
+        check(tm_batch_last_host_times(self.handle, us.ctypes.data))  # noqa: F821
+        return dict(zip(("prepare", "launch", "wait", "download"), us.tolist()))
+
     def debug_set(self, what, value):
         """Test hooks of the context (tm_debug_set): L.TM_DEBUG_WAIT_LIMIT (SM cycles),
         L.TM_DEBUG_STARVE_WAITS (bounded device waits run out), and launch choices otherwise

@@ -170,6 +170,7 @@ SIGNATURES = {
                         P(c_sz), P(c_u64), c_p]),
     "tm_batch_run": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                              P(tm_fuse_params), P(tm_batch_result), c_p]),
+    "tm_batch_last_host_times": (c_i32, [c_p, c_p]),
     "tm_plan_create": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                                P(tm_fuse_params), P(c_p)]),
     "tm_plan_run": (c_i32, [c_p, c_p]),

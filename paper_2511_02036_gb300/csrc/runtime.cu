@@ -1111,7 +1111,6 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
 
 // Download results of the last run of B into r (host offsets; matches host or device).
 tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s) {
-    (void)c;
     cudaError_t e;
     const size_t nio = (size_t)B.n_items + 1;
     if ((e = B.h_out.reserve((nio + 2) * 4 + 48))) return cuda_fail(e, "pinned results");
@@ -1123,6 +1122,7 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
         (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
+    c->t_counts = tm_now();
     if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
         return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory or a tensor-core product did not complete in time");
     const uint32_t search_total = ho[B.n_search_items];
@@ -1306,11 +1306,14 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
     BatchBuf &B = c->batch;
     B.early_fork = sp.mode != TM_MODE_PER_PAIR;  // one-shot: nothing of this enqueue is captured
     tm_status st;
+    const double t0 = tm_now();
+    c->t_counts = 0;
     {
         Range r("prepare_batch (work list, uploads)");
         st = prepare_batch(c, B, steps, n_steps, in, sp, fp, s);
     }
     B.early_fork = false;
+    const double t1 = tm_now();
     if (st) {
         // copies of the caller's arrays may be in flight: done before the call returns
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
@@ -1326,16 +1329,29 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
         B.knobs = c->last_staged == 1 ? c->last_knobs : Knobs{};
         st = enqueue_fused(c, B, th, ln, s);
     }
+    const double t2 = tm_now();
     if (!st) {
         Range r("fetch_results (downloads, wait)");
         st = fetch_results(c, B, res, s);
     }
+    const double t3 = tm_now(), tc = c->t_counts > 0 ? c->t_counts : t3;
+    c->host_us[0] = 1e6 * (t1 - t0);
+    c->host_us[1] = 1e6 * (t2 - t1);
+    c->host_us[2] = 1e6 * (tc - t2);
+    c->host_us[3] = 1e6 * (t3 - tc);
     if (st) {
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(s);
         drop_new_keyframes(c, B, in);
     }
     return st;
+}
+
+extern "C" tm_status tm_batch_last_host_times(tm_ctx *c, double us[4]) {
+    if (!c || !us) return fail(TM_ERR_INVALID_ARG, "tm_batch_last_host_times: null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (int k = 0; k < 4; ++k) us[k] = c->host_us[k];
+    return TM_OK;
 }
 
 extern "C" tm_status tm_batch_run(tm_ctx *c, const tm_step *steps, int32_t n_steps,

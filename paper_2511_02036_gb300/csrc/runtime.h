@@ -141,6 +141,11 @@ struct tm_ctx {
     int branch_prio = -1;                 // test hook: 0 search branch first, 1 store, 2 equal, -1 tuned
     int force_qpl = 0;                    // test hook: queries per lane of a search group (0 = tuned)
     int force_persist = -1;               // test hook: persistent search CTAs (-1 = tuned)
+    // host time of the phases of the last one-shot batch (tm_batch_last_host_times), in
+    // microseconds: work list + uploads, launches, wait for the GPU and the result counts,
+    // result downloads; t_counts marks the end of the third phase
+    double host_us[4] = {0, 0, 0, 0};
+    double t_counts = 0;
     ~tm_ctx();
 };
 
