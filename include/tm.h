@@ -319,6 +319,21 @@ typedef struct {
 } tm_triangulation_params;
 void tm_triangulation_params_default(tm_triangulation_params *p);
 
+/* Keyframes packed one after another, one array per field: keyframe i's keypoints are rows
+ * n[0] + ... + n[i-1] onward of every array.  The same data as an array of tm_keyframe_view
+ * (Sec. IV-B), in a form whose arrays are classified (host, page-locked host, device) and
+ * moved once for all keyframes rather than once per keyframe.  Arrays: host or device, each
+ * array wholly in one kind of memory. */
+typedef struct {
+    const int32_t *n;       /* host [count] keypoints per keyframe                           */
+    const uint8_t *desc;    /* [sum n][32]                                                    */
+    const float *xy;        /* [sum n][2]                                                     */
+    const float *angle;     /* [sum n]                                                        */
+    const uint8_t *level;   /* [sum n]                                                        */
+    const uint32_t *node;   /* [sum n]                                                        */
+    const double *Tcw;      /* host [count][12], row-major 3x4 per keyframe                   */
+} tm_keyframes_packed;
+
 typedef struct {
     const uint8_t *masks;    /* host or device, mask_bytes bytes (may be NULL if unused)    */
     size_t mask_bytes;
@@ -330,9 +345,12 @@ typedef struct {
      * keyframe entry + search + fusion.  Arrays: host or device. */
     int32_t n_new;
     const uint64_t *new_ids;          /* host [n_new]                                       */
-    const tm_keyframe_view *new_kfs;  /* host [n_new]                                       */
+    const tm_keyframe_view *new_kfs;  /* host [n_new], or NULL with new_packed below          */
     /* NULL, or triangulate every match of the batch (results in tm_batch_result.points). */
     const tm_triangulation_params *tri;
+    /* The new keyframes packed (count = n_new), in place of new_kfs (which is then NULL);
+     * NULL when new_kfs is used. */
+    const tm_keyframes_packed *new_packed;
 } tm_batch_inputs;
 
 /* Results, host buffers.  Search matches of all steps, step-major then neighbour order:

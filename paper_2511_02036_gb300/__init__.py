@@ -165,6 +165,21 @@ def keyframe_views_packed(packed, keep):
     return v
 
 
+def keyframes_packed(packed, keep):
+    """tm_keyframes_packed of keyframes packed one after another (the dict form that
+    keyframe_views_packed takes): six pointers and the counts, whatever the number of
+    keyframes."""
+    n = np.ascontiguousarray(packed["n"], np.int32).reshape(-1)
+    tcw = np.ascontiguousarray(packed["Tcw"], np.float64).reshape(len(n), 12)
+    arrs = [_host(packed[name], dt) for name, dt in _KF_PACKED]
+    keep.extend(arrs + [n, tcw])
+    p = L.tm_keyframes_packed()
+    p.n, p.Tcw = n.ctypes.data, tcw.ctypes.data
+    p.desc, p.xy, p.angle, p.level, p.node = (_ptr(a) for a in arrs)
+    keep.append(p)
+    return p, n
+
+
 def mappoint_view(mps, keep):
     v = L.tm_mappoint_view()
     if mps is None:
@@ -269,7 +284,18 @@ class StepTable:
 
     def records(self, keep):
         """tm_step records (numpy structured array, C layout); the arrays they point into are
-        appended to keep."""
+        appended to keep.  Built at the table's first use and kept with it: a table is read
+        once, so build a new one for new steps rather than changing its columns in place."""
+        cached = self.__dict__.get("_records")
+        if cached is not None:
+            keep.extend(cached)
+            return cached[-1]
+        mark = len(keep)
+        arr = self._build_records(keep)
+        self.__dict__["_records"] = list(keep[mark:])
+        return arr
+
+    def _build_records(self, keep):
         n = len(self.kf_id)
         arr = np.zeros(max(1, n), _STEP_DT)
         cnt = np.asarray(self.n_nbrs, np.int64)
@@ -480,6 +506,7 @@ class _ResultBuffers:
 
     def __init__(self):
         self.m = self.po = self.f = self.fo = self.w = self.wo = self.pt = self.ok = None
+        self._last = None  # (capacities, result struct, views) of the previous call
 
     @staticmethod
     def _grow(a, n, width):
@@ -494,6 +521,9 @@ class _ResultBuffers:
             return np.empty((n, width) if width else (n,), np.int32)
 
     def struct(self, match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0, tri=False):
+        key = (match_cap, n_pairs, fuse_cap, n_steps, fwd_cap, tri)
+        if self._last is not None and self._last[0] == key:
+            return self._last[1], self._last[2]
         self.m = self._grow(self.m, max(1, match_cap), 3)
         self.po = self._grow(self.po, n_pairs + 1, 0)
         self.f = self._grow(self.f, max(1, fuse_cap), 3)
@@ -510,8 +540,9 @@ class _ResultBuffers:
             self.ok = self._grow_u8(self.ok, max(1, match_cap))
             pt, ok = self.pt, self.ok
             r.points, r.point_ok = pt.ctypes.data, ok.ctypes.data
-        return r, (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1], self.w, self.wo[:n_pairs + 1],
-                   pt, ok)
+        bufs = (self.m, self.po[:n_pairs + 1], self.f, self.fo[:n_steps + 1], self.w, self.wo[:n_pairs + 1], pt, ok)
+        self._last = (key, r, bufs)
+        return r, bufs
 
     @staticmethod
     def _grow_f(a, n):
@@ -768,11 +799,18 @@ class Context:
         if new is not None:
             ids, kfs = new
             idarr = np.ascontiguousarray(ids, np.uint64)
-            views = keyframe_views_packed(kfs, keep) if isinstance(kfs, dict) else keyframe_views(kfs, keep)
-            for i, n in zip(idarr.tolist(), views["n"][:len(idarr)].tolist()):
-                self.sizes[i] = n
             keep.append(idarr)
-            inp.n_new, inp.new_ids, inp.new_kfs = len(idarr), idarr.ctypes.data, views.ctypes.data
+            inp.n_new, inp.new_ids = len(idarr), idarr.ctypes.data
+            if isinstance(kfs, dict):
+                # packed keyframes: one record of six arrays (tm_keyframes_packed)
+                pk, counts = keyframes_packed(kfs, keep)
+                assert len(counts) == len(idarr)
+                inp.new_packed = ctypes.addressof(pk)
+            else:
+                views = keyframe_views(kfs, keep)
+                counts = views["n"][:len(idarr)]
+                inp.new_kfs = views.ctypes.data
+            self.sizes.update(zip(idarr.tolist(), counts.tolist()))
         keep.append(st)
         return st, inp, keep
 

@@ -85,9 +85,14 @@ class tm_triangulation_params(ctypes.Structure):
                 ("ratio_factor", ctypes.c_double)]
 
 
+class tm_keyframes_packed(ctypes.Structure):
+    _fields_ = [("n", c_p), ("desc", c_p), ("xy", c_p), ("angle", c_p), ("level", c_p), ("node", c_p),
+                ("Tcw", c_p)]
+
+
 class tm_batch_inputs(ctypes.Structure):
     _fields_ = [("masks", c_p), ("mask_bytes", c_sz), ("mps", tm_mappoint_view),
-                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p), ("tri", c_p)]
+                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p), ("tri", c_p), ("new_packed", c_p)]
 
 
 class tm_batch_result(ctypes.Structure):

@@ -232,8 +232,74 @@ tm_status tmap::alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got) {
 
 // Stage keyframes (host or device arrays) into the ingest buffers on stream s.  Slots must
 // already be reserved.  The caller synchronizes before the staging buffers are reused.
+tm_status tmap::classify_packed(tm_ctx *c, const tm_keyframes_packed &p, int n, std::vector<tm_keyframe_view> &views,
+                                PackedSource &src) {
+    if (n > 0 && (!p.n || !p.Tcw)) return fail(TM_ERR_INVALID_ARG, "packed keyframes: null counts or poses");
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        if (p.n[k] < 0 || p.n[k] > c->cap)
+            return fail(TM_ERR_INVALID_ARG, "packed keyframe %d has %d keypoints, capacity %d", k, p.n[k], c->cap);
+        total += (size_t)p.n[k];
+    }
+    src = PackedSource{};
+    src.total = total;
+    const void *arr[5] = {p.desc, p.xy, p.angle, p.node, p.level};
+    if (total) {
+        for (int q = 0; q < 5; ++q) {
+            if (!arr[q]) return fail(TM_ERR_INVALID_ARG, "packed keyframes: null keypoint array");
+            cudaPointerAttributes at;
+            int kind = 3;
+            const void *dp = arr[q];
+            if (cudaPointerGetAttributes(&at, arr[q]) != cudaSuccess) {
+                cudaGetLastError();
+            } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+                if (at.type == cudaMemoryTypeDevice && at.device != c->device)
+                    return fail(TM_ERR_INVALID_ARG, "packed keyframes: array on device %d, context on %d", at.device, c->device);
+                kind = 1;
+            } else if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+                kind = 2;
+                dp = at.devicePointer;
+            }
+            if (q > 0 && kind != src.kind)
+                return fail(TM_ERR_INVALID_ARG, "packed keyframes: arrays in different kinds of memory");
+            src.kind = kind;
+            src.src[q] = static_cast<const unsigned char *>(dp);
+        }
+        if (src.kind != 1) {
+            // levels 0..7 use the low three bits only (one pass over all keyframes' levels)
+            uint64_t any = 0;
+            size_t i = 0;
+            for (; i + 8 <= total; i += 8) {
+                uint64_t w;
+                memcpy(&w, p.level + i, 8);
+                any |= w;
+            }
+            for (; i < total; ++i) any |= p.level[i];
+            if (any & 0xF8F8F8F8F8F8F8F8ull)
+                for (i = 0; i < total; ++i)
+                    if (p.level[i] >= TM_LEVELS)
+                        return fail(TM_ERR_INVALID_ARG, "packed keypoint %zu has level %d >= %d", i, p.level[i], TM_LEVELS);
+        }
+    }
+    views.resize((size_t)n);
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        tm_keyframe_view &v = views[k];
+        v.n = p.n[k];
+        const bool any = v.n > 0;
+        v.desc = any ? p.desc + 32 * off : nullptr;
+        v.xy = any ? p.xy + 2 * off : nullptr;
+        v.angle = any ? p.angle + off : nullptr;
+        v.level = any ? p.level + off : nullptr;
+        v.node = any ? p.node + off : nullptr;
+        memcpy(v.Tcw, p.Tcw + 12 * (size_t)k, sizeof v.Tcw);
+        off += (size_t)v.n;
+    }
+    return TM_OK;
+}
+
 tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
-                             const int *slots, cudaStream_t s, IngestArgs &a) {
+                             const int *slots, cudaStream_t s, IngestArgs &a, const PackedSource *pk) {
     size_t total = 0;
     for (int k = 0; k < n; ++k) total += (size_t)kfs[k].n;
     const size_t N = (total + 31) & ~size_t(31);
@@ -258,6 +324,10 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
         st.src[k] = (uint32_t)off;
         jobs[k].n = v.n;
         for (int q = 0; q < 12; ++q) jobs[k].Tcw[q] = v.Tcw[q];
+        if (pk) {  // packed: the arrays move once for all keyframes, below
+            off += m;
+            continue;
+        }
         const void *pd[5] = {pinned_device_ptr(v.desc), pinned_device_ptr(v.xy), pinned_device_ptr(v.angle),
                              pinned_device_ptr(v.node), pinned_device_ptr(v.level)};
         if (m && pd[0] && pd[1] && pd[2] && pd[3] && pd[4]) {
@@ -284,6 +354,29 @@ tm_status tmap::stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyfram
             }
         }
         off += m;
+    }
+    if (pk && pk->total) {
+        // the packed arrays are laid out as the staging area is (keyframes in order)
+        const size_t T = pk->total;
+        const size_t o5[5] = {o_desc, o_xy, o_ang, o_node, o_lvl}, e5[5] = {32, 8, 4, 4, 1};
+        if (pk->kind == 1) {
+            for (int q = 0; q < 5; ++q)
+                if ((e = cudaMemcpyAsync(d + o5[q], pk->src[q], T * e5[q], cudaMemcpyDeviceToDevice, s)))
+                    return cuda_fail(e, "ingest copy");
+        } else if (pk->kind == 2) {
+            // page-locked: read by the gather kernel in chunks of 1024 keypoints
+            constexpr size_t kChunk = 1024;
+            for (size_t o = 0; o < T; o += kChunk) {
+                GatherJob g;
+                for (int q = 0; q < 5; ++q) g.src[q] = pk->src[q] + o * e5[q];
+                g.dst = (uint32_t)o;
+                g.n = (uint32_t)std::min(kChunk, T - o);
+                gather.push_back(g);
+            }
+        } else {
+            for (int q = 0; q < 5; ++q) memcpy(h + o5[q], pk->src[q], T * e5[q]);
+            st.host_ranges.push_back({0, T});
+        }
     }
     // one transfer of everything staged on the host (contiguous runs merged per array)
     auto flush = [&](size_t base, size_t elt) -> cudaError_t {
@@ -600,11 +693,16 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.n_new = 0;
     std::vector<int> new_slots;
     const int n_new = in ? in->n_new : 0;
-    if (n_new < 0 || (n_new > 0 && (!in->new_ids || !in->new_kfs)))
+    if (n_new < 0 || (n_new > 0 && (!in->new_ids || (!in->new_kfs && !in->new_packed))))
         return fail(TM_ERR_INVALID_ARG, "bad new keyframes");
+    std::vector<tm_keyframe_view> packed_views;
+    PackedSource packed_src;
+    const bool packed = n_new > 0 && !in->new_kfs;
+    if (packed && (st = classify_packed(c, *in->new_packed, n_new, packed_views, packed_src))) return st;
+    const tm_keyframe_view *new_kfs = packed ? packed_views.data() : (in ? in->new_kfs : nullptr);
     if (n_new > 0) {
         for (int k = 0; k < n_new; ++k) {
-            if ((st = validate_view(c, in->new_kfs[k]))) return st;
+            if (!packed && (st = validate_view(c, new_kfs[k]))) return st;
             if (c->ids.count(in->new_ids[k]))
                 return fail(TM_ERR_EXISTS, "keyframe %llu already stored", (unsigned long long)in->new_ids[k]);
             for (int q = 0; q < k; ++q)
@@ -612,13 +710,14 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
                     return fail(TM_ERR_EXISTS, "keyframe %llu given twice", (unsigned long long)in->new_ids[k]);
         }
         if ((st = alloc_slots_locked(c, n_new, new_slots))) return st;
-        if ((st = stage_ingest(c, B.ingest, n_new, in->new_kfs, new_slots.data(), s, B.ingest_args))) {
+        if ((st = stage_ingest(c, B.ingest, n_new, new_kfs, new_slots.data(), s, B.ingest_args,
+                               packed ? &packed_src : nullptr))) {
             for (int sl : new_slots) c->free_slots.push_back(sl);
             return st;
         }
         for (int k = 0; k < n_new; ++k) {
             Slot &sl = c->slots[new_slots[k]];
-            sl.n = in->new_kfs[k].n;
+            sl.n = new_kfs[k].n;
             sl.refs = 0;
             sl.id = in->new_ids[k];
             c->ids[in->new_ids[k]] = new_slots[k];

@@ -156,12 +156,22 @@ tm_status cuda_fail(cudaError_t e, const char *what);
 bool is_device_ptr(const void *p);
 cudaStream_t pick_stream(tm_ctx *c, void *s);
 tm_status validate_view(tm_ctx *c, const tm_keyframe_view &v);
+// Where the five arrays of a packed keyframe set live, classified once for all its keyframes.
+struct PackedSource {
+    int kind = 0;                       // 1 device, 2 page-locked host, 3 pageable host
+    const unsigned char *src[5] = {};   // desc, xy, angle, node, level (kind 2: device-mapped)
+    size_t total = 0;                   // keypoints of all keyframes
+};
+// Checks a packed keyframe set of n keyframes (counts, null arrays, levels, one kind of memory
+// per set) and gives its per-keyframe views (pointers into the packed arrays) and its source.
+tm_status classify_packed(tm_ctx *c, const tm_keyframes_packed &p, int n, std::vector<tm_keyframe_view> &views,
+                          PackedSource &src);
 // Reserves n store slots (all or nothing) within the budget; caller holds c->mu.
 tm_status alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got);
 // Copies keyframes (host or device arrays) into staging buffers on stream s and fills the
 // ingest kernel's arguments; enqueue_ingest also launches it.
 tm_status stage_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
-                       const int *slots, cudaStream_t s, IngestArgs &args);
+                       const int *slots, cudaStream_t s, IngestArgs &args, const PackedSource *pk = nullptr);
 tm_status enqueue_ingest(tm_ctx *c, IngestStage &st, int n, const tm_keyframe_view *kfs,
                          const int *slots, cudaStream_t s);
 tm_status store_add(tm_ctx *c, int n, const uint64_t *ids, const tm_keyframe_view *kfs,

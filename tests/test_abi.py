@@ -53,7 +53,7 @@ def test_struct_layout_matches_c(lib):
     structs = ["tm_camera", "tm_keyframe_view", "tm_mappoint_view", "tm_search_params",
                "tm_fuse_params", "tm_match", "tm_store_stats", "tm_step", "tm_batch_inputs",
                "tm_batch_result", "tm_server_config", "tm_request", "tm_request_info", "tm_fuse_apply_stats",
-               "tm_plan_tuning", "tm_server_stats"]
+               "tm_plan_tuning", "tm_server_stats", "tm_keyframes_packed"]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tm.h"', "int main(void){"]
     for s in structs:
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
@@ -173,6 +173,37 @@ def test_packed_keyframe_views():
         else:
             assert c.desc is None or c.desc == 0
         off += n
+
+
+def test_packed_keyframes_record():
+    """keyframes_packed: one tm_keyframes_packed record pointing at the packed arrays (counts
+    and poses converted to int32 / float64), and batch inputs that carry it instead of views."""
+    import paper_2511_02036_gb300 as tm
+    from paper_2511_02036_gb300 import _lib as L
+    rng = np.random.default_rng(1)
+    ns = [4, 0, 2]
+    N = sum(ns)
+    packed = dict(n=ns, desc=rng.integers(0, 255, (N, 32), dtype=np.uint8), xy=rng.random((N, 2), np.float32),
+                  angle=rng.random(N, np.float32), level=rng.integers(0, 8, N, dtype=np.uint8),
+                  node=rng.integers(0, 99, N, dtype=np.uint32), Tcw=rng.random((3, 3, 4)))
+    keep = []
+    p, counts = tm.keyframes_packed(packed, keep)
+    assert list(counts) == ns and counts.dtype == np.int32
+    assert list((ctypes.c_int32 * 3).from_address(p.n)) == ns
+    assert list((ctypes.c_double * 36).from_address(p.Tcw)) == list(packed["Tcw"].reshape(36))
+    assert (p.desc, p.xy, p.angle, p.level, p.node) == tuple(packed[k].ctypes.data for k in
+                                                             ("desc", "xy", "angle", "level", "node"))
+
+    class FakeCtx(tm.Context):
+        def __init__(self):
+            self.sizes, self._res, self.max_kp = {}, None, 2048
+    ctx = FakeCtx()
+    st, inp, keep2 = ctx._inputs([dict(kf_id=1, nbrs=[])], masks=np.zeros(1, np.uint8),
+                                 mps=dict(n=0), new=([10, 11, 12], packed))
+    assert inp.n_new == 3 and not inp.new_kfs and inp.new_packed
+    rec = L.tm_keyframes_packed.from_address(inp.new_packed)
+    assert rec.desc == packed["desc"].ctypes.data and list((ctypes.c_int32 * 3).from_address(rec.n)) == ns
+    assert ctx.sizes == {10: 4, 11: 0, 12: 2}
 
 
 def test_step_table_records_match_step_dicts():

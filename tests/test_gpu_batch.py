@@ -328,6 +328,57 @@ def test_pinned_host_inputs(tm, small_batch):
                 ctx.remove_keyframe(i)
 
 
+@pytest.mark.parametrize("kind", ["pageable", "pinned", "device"])
+def test_packed_new_keyframes(tm, small_batch, kind):
+    """The new keyframes as one packed record (tm_keyframes_packed) in pageable host,
+    page-locked host and device memory: one-shot batches and a plan give the oracle's results;
+    a packed set whose arrays sit in different kinds of memory, a level above 7 and a count
+    above the capacity are refused before any work, and the store is left as it was."""
+    torch = pytest.importorskip("torch")
+    w = small_batch
+    exp = oracle_results(w)
+    new_ids = [s["q"] for s in w["steps"]]
+    fr = [w["frames"][i] for i in new_ids]
+    cat = lambda k: np.ascontiguousarray(np.concatenate([f[k] for f in fr]))  # noqa: E731
+    host = dict(desc=cat("desc"), xy=cat("xy"), angle=cat("angle"), level=cat("level"), node=cat("node"))
+    put = {"pageable": lambda a: a, "pinned": lambda a: torch.from_numpy(a).pin_memory(),
+           "device": lambda a: torch.from_numpy(a).cuda()}[kind]
+    packed = {k: put(v) for k, v in host.items()}
+    packed["n"] = [f["n"] for f in fr]
+    packed["Tcw"] = np.stack([np.asarray(f["Tcw"], np.float64).reshape(12) for f in fr])
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in w["steps"] for i in s["nbrs"]))
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        used = ctx.stats()["slots_used"]
+        for _ in range(2):
+            assert_same(ctx.batch_run(steps_of(w), new=(new_ids, packed)), exp)
+            ctx.remove_keyframes(new_ids)
+        with ctx.plan(steps_of(w), new=(new_ids, packed)) as plan:
+            plan.run()
+            assert_same(plan.results(), exp)
+        ctx.remove_keyframes(new_ids)
+        bad = []
+        mixed = dict(packed)
+        mixed["level"] = torch.from_numpy(host["level"]).cuda() if kind != "device" else host["level"]
+        bad.append(mixed)
+        if kind != "device":
+            lv = dict(packed)
+            lv_arr = host["level"].copy()
+            lv_arr[len(lv_arr) // 2] = 8
+            lv["level"] = put(lv_arr)
+            bad.append(lv)
+        big = dict(packed)
+        big["n"] = list(packed["n"])
+        big["n"][0] = 4096
+        bad.append(big)
+        for b in bad:
+            with pytest.raises(tm.TMError) as e:
+                ctx.batch_run(steps_of(w), new=(new_ids, b))
+            assert e.value.status == tm.TM_ERR_INVALID_ARG
+            assert ctx.stats()["slots_used"] == used
+        assert_same(ctx.batch_run(steps_of(w), new=(new_ids, packed)), exp)
+
+
 def forward_steps(w, skip=True):
     return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
                  mps=s.get("mps"), fwd_mps=s["fwd_mps"], fwd_skip=s["fwd_skip"] if skip else None)
