@@ -844,6 +844,51 @@ class Context:
             raise
         return _collect(r, bufs)
 
+    def batch_begin(self, steps, masks=None, mps=None, sp=None, fp=None, new=None, tri=None):
+        """Asynchronous batch_run (tm_batch_begin): enqueues the batch and returns a ticket for
+        batch_finish.  The input arrays must stay alive and unchanged until then (the context
+        keeps references to them); at most L.TM_BATCH_INFLIGHT batches are in flight."""
+        sp = sp or SearchParams()
+        st, inp, keep = self._inputs(steps, masks, mps, new)
+        if tri is not None:
+            ts = tri.struct()
+            keep.append(ts)
+            inp.tri = ctypes.addressof(ts)
+        mc, fc = _result_caps(steps, self.sizes, sp.resolve)
+        if masks is not None or mps is not None:
+            fc = max(fc, int(mps["n"]) if mps is not None else 0)
+        n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
+        sps, fps = sp.struct(), (fp or FuseParams()).struct()
+        keep.extend([sps, fps])
+        t = ctypes.c_uint64()
+        try:
+            check(tm_batch_begin(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
+                                 ctypes.byref(fps), ctypes.byref(t)))
+        except TMError:
+            if new is not None:
+                for i in new[0]:
+                    self.sizes.pop(int(i), None)
+            raise
+        if not hasattr(self, "_inflight"):
+            self._inflight = {}
+        self._inflight[t.value] = (keep, (mc, n_pairs, fc, len(steps), _fwd_cap(steps), tri is not None),
+                                   None if new is None else list(new[0]))
+        return t.value
+
+    def batch_finish(self, ticket):
+        """Waits for a batch begun by batch_begin and returns its BatchResult."""
+        keep, caps, new_ids = self._inflight.pop(ticket)
+        if self._res is None:
+            self._res = _ResultBuffers()
+        r, bufs = self._res.struct(*caps)
+        try:
+            check(tm_batch_finish(self.handle, ticket, ctypes.byref(r)))  # noqa: F821
+        except TMError:
+            for i in new_ids or []:
+                self.sizes.pop(int(i), None)
+            raise
+        return _collect(r, bufs)
+
     def last_host_times(self):
         """Host microseconds of the phases of the last batch_run (tm_batch_last_host_times):
         dict(prepare, launch, wait, download)."""

@@ -27,6 +27,7 @@ TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
 TM_MAX_IMAGE_SIZE = 16384
 TM_PLAN_STAGES = 6
+TM_BATCH_INFLIGHT = 2
 TM_DEBUG_WAIT_LIMIT = 1
 TM_DEBUG_STARVE_WAITS = 2
 TM_DEBUG_SEARCH_THREADS = 3
@@ -176,6 +177,9 @@ SIGNATURES = {
     "tm_batch_run": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                              P(tm_fuse_params), P(tm_batch_result), c_p]),
     "tm_batch_last_host_times": (c_i32, [c_p, c_p]),
+    "tm_batch_begin": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
+                               P(tm_fuse_params), P(c_u64)]),
+    "tm_batch_finish": (c_i32, [c_p, c_u64, P(tm_batch_result)]),
     "tm_plan_create": (c_i32, [c_p, c_p, c_i32, P(tm_batch_inputs), P(tm_search_params),
                                P(tm_fuse_params), P(c_p)]),
     "tm_plan_run": (c_i32, [c_p, c_p]),

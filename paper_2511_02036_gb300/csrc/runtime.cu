@@ -170,6 +170,13 @@ extern "C" tm_status tm_ctx_create(int device, const tm_camera *cam, int32_t max
 tm_ctx::~tm_ctx() {
     cudaSetDevice(device);
     if (stream) cudaStreamSynchronize(stream);
+    for (AsyncBatch &a : async) {
+        if (a.s) cudaStreamSynchronize(a.s);
+        if (a.B.mcopy) cudaStreamSynchronize(a.B.mcopy);
+        a.B.release();
+        if (a.ingested) cudaEventDestroy(a.ingested);
+        if (a.s) cudaStreamDestroy(a.s);
+    }
     batch.release();
     for (void *p : chunks) cudaFree(p);
     if (stream) cudaStreamDestroy(stream);
@@ -1127,6 +1134,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     B.forked = B.mp_async = false;
     if (!after_ingest && !forked && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s, st_))) return cuda_fail(e, "ingest kernel");
+    if (B.ingest_done && (e = cudaEventRecord(B.ingest_done, s))) return cuda_fail(e, "event");
     if ((e = mark(2, s))) return cuda_fail(e, "event");
     if (after_ingest && (e = cudaEventRecord(B.pfork, s))) return cuda_fail(e, "search branch");
     if ((e = cudaStreamWaitEvent(B.paux, B.pfork, 0)) || (e = mark(5, B.paux)) ||
@@ -1157,6 +1165,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
         return cuda_fail(e, "plain scratch");
     PairScratch scr = pair_scratch_at(B.scratch.p, c->cap);
     if (B.n_new > 0 && (e = launch_ingest(B.ingest_args, s))) return cuda_fail(e, "ingest kernel");
+    if (B.ingest_done && (e = cudaEventRecord(B.ingest_done, s))) return cuda_fail(e, "event");
     uint32_t *res = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(B.scratch.p) + scr_bytes);
     if ((e = cudaMemsetAsync(scr.running, 0, 8, s)) || (e = cudaMemsetAsync(B.ncmp.p, 0, 24, s)))
         return cuda_fail(e, "reset");
@@ -1443,6 +1452,94 @@ static tm_status run_batch_locked(tm_ctx *c, const tm_step *steps, int n_steps,
         cudaStreamSynchronize(s);
         drop_new_keyframes(c, B, in);
     }
+    return st;
+}
+
+extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_steps,
+                                    const tm_batch_inputs *in, const tm_search_params *sp,
+                                    const tm_fuse_params *fp, uint64_t *ticket) {
+    if (!c || !ticket) return fail(TM_ERR_INVALID_ARG, "tm_batch_begin: null argument");
+    tm_search_params spd;
+    tm_fuse_params fpd;
+    tm_search_params_default(&spd);
+    tm_fuse_params_default(&fpd);
+    if (sp) spd = *sp;
+    if (fp) fpd = *fp;
+    Range range("tm_batch_begin");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    int k = -1;
+    for (int q = 0; q < TM_BATCH_INFLIGHT; ++q)
+        if (!c->async[q].ticket) { k = q; break; }
+    if (k < 0) return fail(TM_ERR_BUSY, "tm_batch_begin: %d batches already in flight", TM_BATCH_INFLIGHT);
+    tm_ctx::AsyncBatch &a = c->async[k];
+    cudaError_t e;
+    if (!a.s && ((e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking)) ||
+                 (e = cudaEventCreateWithFlags(&a.ingested, cudaEventDisableTiming))))
+        return cuda_fail(e, "async batch stream");
+    // after the ingest of the batch begun before this one (its keyframes may be neighbours here)
+    if (c->async_last >= 0 && c->async[c->async_last].ticket &&
+        (e = cudaStreamWaitEvent(a.s, c->async[c->async_last].ingested, 0)))
+        return cuda_fail(e, "async batch order");
+    BatchBuf &B = a.B;
+    B.early_fork = spd.mode != TM_MODE_PER_PAIR;
+    tm_status st = prepare_batch(c, B, steps, n_steps, in, spd, fpd, a.s);
+    B.early_fork = false;
+    if (!st) {
+        B.ingest_done = a.ingested;
+        if (spd.mode == TM_MODE_PER_PAIR) {
+            st = enqueue_plain(c, B, spd.lanes_per_query ? spd.lanes_per_query : 1, a.s);
+        } else {
+            int ln = c->def_lanes;
+            if (spd.lanes_per_query) ln = spd.lanes_per_query;
+            B.knobs = c->last_staged == 1 ? c->last_knobs : Knobs{};
+            st = enqueue_fused(c, B, default_threads(c, B), ln, a.s);
+        }
+        B.ingest_done = nullptr;
+        if (st) drop_new_keyframes(c, B, in);
+    }
+    if (st) {
+        if (B.mcopy) cudaStreamSynchronize(B.mcopy);
+        cudaStreamSynchronize(a.s);
+        return st;
+    }
+    for (int sl : B.slots) c->slots[sl].refs++;
+    a.new_ids.assign(in && in->n_new > 0 ? in->new_ids : nullptr, in && in->n_new > 0 ? in->new_ids + in->n_new : nullptr);
+    a.ticket = c->async_next++;
+    c->async_last = k;
+    *ticket = a.ticket;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_batch_finish(tm_ctx *c, uint64_t ticket, tm_batch_result *res) {
+    if (!c || !res) return fail(TM_ERR_INVALID_ARG, "tm_batch_finish: null argument");
+    Range range("tm_batch_finish");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    int k = -1;
+    for (int q = 0; q < TM_BATCH_INFLIGHT; ++q)
+        if (ticket && c->async[q].ticket == ticket) { k = q; break; }
+    if (k < 0) return fail(TM_ERR_NOT_FOUND, "tm_batch_finish: unknown ticket %llu", (unsigned long long)ticket);
+    tm_ctx::AsyncBatch &a = c->async[k];
+    BatchBuf &B = a.B;
+    tm_status st = fetch_results(c, B, res, a.s);
+    if (st) {
+        if (B.mcopy) cudaStreamSynchronize(B.mcopy);
+        cudaStreamSynchronize(a.s);
+    }
+    for (int sl : B.slots) c->slots[sl].refs--;
+    if (st && B.n_new > 0) {
+        for (uint64_t id : a.new_ids) {
+            auto it = c->ids.find(id);
+            // (a keyframe that a batch begun later reads stays stored: its slot is in use)
+            if (it == c->ids.end() || c->slots[it->second].refs > 0) continue;
+            c->free_slots.push_back(it->second);
+            c->ids.erase(it);
+        }
+    }
+    B.n_new = 0;
+    a.new_ids.clear();
+    a.ticket = 0;
     return st;
 }
 

@@ -100,6 +100,7 @@ struct BatchBuf {
     cudaEvent_t join = nullptr;          // end of the search branch
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)
     cudaEvent_t pfork = nullptr;         // start of the search branch
+    cudaEvent_t ingest_done = nullptr;   // if set: recorded after the batch's ingest (async batches)
     // one-shot batches (early_fork): the search branch forks right after the work list and the
     // masks are uploaded, and the map points are copied on mcopy, which the fusion kernel
     // awaits (mready); forked / mp_async say that prepare_batch did so for the next enqueue
@@ -146,6 +147,17 @@ struct tm_ctx {
     // result downloads; t_counts marks the end of the third phase
     double host_us[4] = {0, 0, 0, 0};
     double t_counts = 0;
+    // asynchronous one-shot batches (tm_batch_begin / tm_batch_finish): each on its own stream
+    struct AsyncBatch {
+        tmap::BatchBuf B;
+        cudaStream_t s = nullptr;
+        cudaEvent_t ingested = nullptr;   // after the batch's ingest (or its start)
+        uint64_t ticket = 0;              // 0: free
+        std::vector<uint64_t> new_ids;    // the keyframes it stores (taken out again on failure)
+    };
+    AsyncBatch async[TM_BATCH_INFLIGHT];
+    uint64_t async_next = 1;
+    int async_last = -1;                  // the slot begun last
     ~tm_ctx();
 };
 

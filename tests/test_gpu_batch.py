@@ -379,6 +379,50 @@ def test_packed_new_keyframes(tm, small_batch, kind):
         assert_same(ctx.batch_run(steps_of(w), new=(new_ids, packed)), exp)
 
 
+def test_async_batches(tm, small_batch):
+    """tm_batch_begin / tm_batch_finish: two batches in flight at once, the second using as
+    neighbour a keyframe that the first stores; finished in reverse order, each equal to the
+    oracle.  A third begin is refused while two are in flight, the keyframes they use cannot be
+    removed, an unknown ticket is refused, and a pipelined loop (begin k + 1, then finish k)
+    gives the oracle's results at every step."""
+    from paper_2511_02036_gb300 import _lib as L
+    w = small_batch
+    st = w["steps"]
+    nb1 = st[1]["nbrs"][0]  # stored by the first batch, read by the second
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in st for i in s["nbrs"]) - {nb1})
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        s0, s1 = steps_of(dict(w, steps=st[:1])), steps_of(dict(w, steps=st[1:2]))
+        t0 = ctx.batch_begin(s0, new=([st[0]["q"], nb1], [w["frames"][st[0]["q"]], w["frames"][nb1]]))
+        t1 = ctx.batch_begin(s1, new=([st[1]["q"]], [w["frames"][st[1]["q"]]]))
+        with pytest.raises(tm.TMError) as e:
+            ctx.batch_begin(steps_of(dict(w, steps=st[2:3])))
+        assert e.value.status == tm.TM_ERR_BUSY
+        with pytest.raises(tm.TMError) as e:
+            ctx.remove_keyframe(st[1]["nbrs"][1])
+        assert e.value.status == tm.TM_ERR_BUSY
+        r1 = ctx.batch_finish(t1)
+        r0 = ctx.batch_finish(t0)
+        for res, part in ((r0, st[:1]), (r1, st[1:2])):
+            assert_same(res, oracle_results(dict(w, steps=part)))
+        r = L.tm_batch_result()
+        assert tm.tm_batch_finish(ctx.handle, t0, ctypes.byref(r)) == tm.TM_ERR_NOT_FOUND  # finished already
+        # pipelined: begin step k + 1 before finishing step k (all remaining steps, two id sets)
+        ctx.remove_keyframes([st[0]["q"], st[1]["q"]])
+        rest = st[2:]
+        prev = None
+        got = []
+        for k, s in enumerate(rest):
+            t = ctx.batch_begin(steps_of(dict(w, steps=[s])), new=([s["q"]], [w["frames"][s["q"]]]))
+            if prev is not None:
+                got.append(ctx.batch_finish(prev))
+            prev = t
+        got.append(ctx.batch_finish(prev))
+        for res, s in zip(got, rest):
+            assert_same(res, oracle_results(dict(w, steps=[s])))
+        assert L.TM_BATCH_INFLIGHT == 2
+
+
 def forward_steps(w, skip=True):
     return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
                  mps=s.get("mps"), fwd_mps=s["fwd_mps"], fwd_skip=s["fwd_skip"] if skip else None)

@@ -48,3 +48,4 @@ def test_bench_json_line():
             assert r["parity"] == "oracle, bit-exact"
         assert cf[name]["oracle_1_core"]["keyframes_per_s"] > 0
         assert cf[name]["oracle_all_cores"]["cores"] >= 1
+    assert d["e2e"]["serial"]["value"] > 0 and d["e2e"]["serial"]["unit"] == d["unit"]
