@@ -651,7 +651,7 @@ __device__ __forceinline__ bool staged_wait(uint64_t *bar, uint64_t *never, cons
 //            pair, with the neighbour's node index, the winners, the accepted matches and the
 //            results in shared memory.  It reads a new keyframe from its staged arrays, so it
 //            runs beside the ingest.
-//   store    ingest_kernel, then fuse_kernel (CTA per 256 map points of a step: projection
+//   store    ingest_kernel, then fuse_kernel (CTA per 512 map points of a step: projection
 //            gates, grid window in the staged target, best Hamming).
 //   copy     per-item counts -> offsets, per-item regions -> dense output, comparison totals.
 
@@ -683,8 +683,7 @@ __device__ __forceinline__ uint32_t top3_mask_warp(const uint32_t *hist) {
     return mask;
 }
 
-// Fusion of one map point into keyframe T (Sec. IV-D).  Returns the packed
-// (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
+// A map point as the fusion reads it (Sec. IV-D's map-point data).
 struct MapPoint {
     float X, Y, Z, nx, ny, nz, mind, maxd;
     uint4 d0, d1;
@@ -700,26 +699,33 @@ __device__ __forceinline__ MapPoint load_mp(const float *pos, const float *norma
     return q;
 }
 
-__device__ __forceinline__ uint32_t fuse_one(const KfView &T, int nT, const CamConst &cam,
-                                             const FuseConst &fp, const FuseK &K,
-                                             const MapPoint &q, uint32_t &cmp) {
-    const float X = q.X, Y = q.Y, Z = q.Z;
-    const float nx = q.nx, ny = q.ny, nz = q.nz;
-    const uint4 m0 = q.d0, m1 = q.d1;
-    const float mind = q.mind, maxd = q.maxd;
+// Where a map point projects into the target (Sec. IV-D's gates before the window): pixel
+// (u, v), window half-size r and pyramid level pl, and the grid cells of the window packed as
+// cx0 | cx1 << 8 | cy0 << 16 | cy1 << 24.
+struct FuseProj {
+    float u, v, r;
+    int pl;
+    uint32_t cells;
+};
+// The projection gates of one map point: in front of the camera, inside the image, within its
+// scale-invariance distance range, viewing angle below 60 degrees; then its predicted level
+// and window.  False when a gate rejects it.
+__device__ __forceinline__ bool fuse_project(const CamConst &cam, const FuseConst &fp, const FuseK &K,
+                                             float X, float Y, float Z, float nx, float ny, float nz,
+                                             float mind, float maxd, FuseProj &P) {
     const float xc = fadd(fadd(fadd(fmul(K.R[0], X), fmul(K.R[1], Y)), fmul(K.R[2], Z)), K.t[0]);
     const float yc = fadd(fadd(fadd(fmul(K.R[3], X), fmul(K.R[4], Y)), fmul(K.R[5], Z)), K.t[1]);
     const float zc = fadd(fadd(fadd(fmul(K.R[6], X), fmul(K.R[7], Y)), fmul(K.R[8], Z)), K.t[2]);
-    if (!(zc > 0.0f)) return kNone;
+    if (!(zc > 0.0f)) return false;
     const float x = __fdiv_rn(xc, zc), y = __fdiv_rn(yc, zc);
     const float u = fadd(fmul(float(cam.fx), x), float(cam.cx));
     const float v = fadd(fmul(float(cam.fy), y), float(cam.cy));
-    if (!(u >= 0.0f && u < float(cam.width) && v >= 0.0f && v < float(cam.height))) return kNone;
+    if (!(u >= 0.0f && u < float(cam.width) && v >= 0.0f && v < float(cam.height))) return false;
     const float pox = fsub(X, K.O[0]), poy = fsub(Y, K.O[1]), poz = fsub(Z, K.O[2]);
     const float dist = __fsqrt_rn(fadd(fadd(fmul(pox, pox), fmul(poy, poy)), fmul(poz, poz)));
-    if (dist < mind || dist > maxd) return kNone;
+    if (dist < mind || dist > maxd) return false;
     const float cosv = fadd(fadd(fmul(pox, nx), fmul(poy, ny)), fmul(poz, nz));
-    if (cosv < fmul(0.5f, dist)) return kNone;
+    if (cosv < fmul(0.5f, dist)) return false;
     int pl = kLevels - 1;
     for (int l = 0; l < kLevels; ++l)
         if (fmul(dist, K.scale[l]) >= maxd) { pl = l; break; }
@@ -731,6 +737,25 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, int nT, const CamC
     const int cx1 = grid_cell(fadd(fadd(u, r), 0.01f), cam.cell_w_inv, kGridCols);
     const int cy0 = grid_cell(fsub(fsub(v, r), 0.01f), cam.cell_h_inv, kGridRows);
     const int cy1 = grid_cell(fadd(fadd(v, r), 0.01f), cam.cell_h_inv, kGridRows);
+    P.u = u;
+    P.v = v;
+    P.r = r;
+    P.pl = pl;
+    P.cells = (uint32_t)cx0 | (uint32_t)cx1 << 8 | (uint32_t)cy0 << 16 | (uint32_t)cy1 << 24;
+    return true;
+}
+
+// The window search of a projected map point (descriptor m0 m1): every keypoint of the window's
+// cells at level pl or pl - 1 within r of (u, v) on both axes and inside the reprojection
+// gate is compared; returns the packed (distance << 16 | caller keypoint) of the best one
+// under hamming_max, or kNone; adds the window comparisons to cmp.
+__device__ __forceinline__ uint32_t fuse_window(const KfView &T, int nT, const FuseConst &fp, const FuseK &K,
+                                                const FuseProj &P, const uint4 &m0, const uint4 &m1,
+                                                uint32_t &cmp) {
+    const float u = P.u, v = P.v, r = P.r;
+    const int pl = P.pl;
+    const int cx0 = (int)(P.cells & 0xFFu), cx1 = (int)((P.cells >> 8) & 0xFFu);
+    const int cy0 = (int)((P.cells >> 16) & 0xFFu), cy1 = (int)(P.cells >> 24);
     uint32_t best = kNone;  // (dist << 16) | caller keypoint index
     for (int cy = cy0; cy <= cy1; ++cy) {
         const int c0 = cy * kGridCols + cx0, c1 = cy * kGridCols + cx1;
@@ -750,6 +775,16 @@ __device__ __forceinline__ uint32_t fuse_one(const KfView &T, int nT, const CamC
     }
     if (best == kNone || (int)(best >> 16) > fp.hamming_max) return kNone;
     return best;
+}
+
+// Fusion of one map point into keyframe T (Sec. IV-D): projection gates, then the window.
+// Returns the packed (distance << 16 | keypoint) or kNone; adds window comparisons to cmp.
+__device__ __forceinline__ uint32_t fuse_one(const KfView &T, int nT, const CamConst &cam,
+                                             const FuseConst &fp, const FuseK &K,
+                                             const MapPoint &q, uint32_t &cmp) {
+    FuseProj P;
+    if (!fuse_project(cam, fp, K, q.X, q.Y, q.Z, q.nx, q.ny, q.nz, q.mind, q.maxd, P)) return kNone;
+    return fuse_window(T, nT, fp, K, P, q.d0, q.d1, cmp);
 }
 
 // Pose-derived constants of a fusion target: R, t in float32 and the camera centre
@@ -1711,11 +1746,17 @@ __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
 
 // ---------------------------------------------------------------- fusion (S7-S9)
 
-// One fusion item (up to 256 map points of a step) per CTA.  The target keyframe's grid
-// index, positions, caller indices and levels are bulk-copied into shared memory; each
-// thread projects one map point, walks the grid window in shared memory and reads the
-// descriptors of the keypoints that pass the reprojection gate; ordered compaction.
-__global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
+// One fusion item (up to kFuseChunk map points of a step) per CTA of 256 threads, thread t
+// taking map points kFusePer t .. kFusePer t + kFusePer - 1 of the item.  The target keyframe's grid index,
+// positions, caller indices and levels are bulk-copied into shared memory while each thread
+// loads its two map points and runs their projection gates (which need only the target's
+// pose); then each thread walks its map points' windows in shared memory and reads the
+// descriptors of the keypoints that pass the reprojection gate; ordered compaction (map
+// point order).
+constexpr int kFuseThreads = 256;
+constexpr int kFusePer = kFuseChunk / kFuseThreads;
+static_assert(kFusePer * kFuseThreads == kFuseChunk, "whole map points per thread");
+__global__ void __launch_bounds__(kFuseThreads) fuse_kernel(BatchArgs A) {
     extern __shared__ __align__(128) unsigned char fsm[];
     __shared__ FuseK K;
     __shared__ __align__(8) uint64_t bar, never;
@@ -1746,14 +1787,36 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
         scmp = 0u;
     }
     fuse_setup(Tg.hdr, A.fp.chi2, K);
-    const uint32_t m = w.a + (uint32_t)tid;
-    const bool have = tid < (int)w.b &&
-                      !(w.skip != kNone ? A.masks[w.skip + (uint32_t)tid] != 0 : (A.mp_skip && A.mp_skip[m]));
-    // the map point's loads overlap the staging
-    const uint32_t mc = tid < (int)w.b ? m : w.a;  // (a valid index for the speculative loads)
-    const MapPoint mp = load_mp(A.mp_pos + 3 * (size_t)mc, A.mp_normal + 3 * (size_t)mc,
-                                A.mp_desc + 2 * (size_t)mc, A.mp_min[mc], A.mp_max[mc]);
-    __syncthreads();
+    // the thread's map points: their loads overlap the staging
+    bool have[kFusePer];
+    float X[kFusePer], Y[kFusePer], Z[kFusePer], nx[kFusePer], ny[kFusePer], nz[kFusePer], mn[kFusePer],
+        mx[kFusePer];
+#pragma unroll
+    for (int h = 0; h < kFusePer; ++h) {
+        const uint32_t k = (uint32_t)(kFusePer * tid + h), m = w.a + k;
+        have[h] = k < w.b && !(w.skip != kNone ? A.masks[w.skip + k] != 0 : (A.mp_skip && A.mp_skip[m]));
+        const uint32_t mc = k < w.b ? m : w.a;  // (a valid index for the speculative loads)
+        X[h] = A.mp_pos[3 * (size_t)mc];
+        Y[h] = A.mp_pos[3 * (size_t)mc + 1];
+        Z[h] = A.mp_pos[3 * (size_t)mc + 2];
+        nx[h] = A.mp_normal[3 * (size_t)mc];
+        ny[h] = A.mp_normal[3 * (size_t)mc + 1];
+        nz[h] = A.mp_normal[3 * (size_t)mc + 2];
+        mn[h] = A.mp_min[mc];
+        mx[h] = A.mp_max[mc];
+    }
+    __syncthreads();  // K
+    FuseProj P[kFusePer];
+    bool pr[kFusePer];
+    uint4 d[kFusePer][2];
+#pragma unroll
+    for (int h = 0; h < kFusePer; ++h) {
+        pr[h] = have[h] && fuse_project(A.cam, A.fp, K, X[h], Y[h], Z[h], nx[h], ny[h], nz[h], mn[h], mx[h], P[h]);
+        // the descriptor only of a map point that passed the gates
+        const uint32_t mc = w.a + (uint32_t)(kFusePer * tid + h);
+        d[h][0] = pr[h] ? A.mp_desc[2 * (size_t)mc] : make_uint4(0u, 0u, 0u, 0u);
+        d[h][1] = pr[h] ? A.mp_desc[2 * (size_t)mc + 1] : make_uint4(0u, 0u, 0u, 0u);
+    }
     const bool ok = staged_wait(&bar, &never, A);
     if (tid == 0) ok_all = true;
     __syncthreads();
@@ -1772,13 +1835,23 @@ __global__ void __launch_bounds__(256) fuse_kernel(BatchArgs A) {
     T.grid_items = reinterpret_cast<const uint16_t *>(fsm + FS.gitems);
     T.orig = reinterpret_cast<const uint16_t *>(fsm + FS.orig);
     T.level = fsm + FS.level;
-    uint32_t cmp = 0, r = kNone;
-    if (have) r = fuse_one(T, nT, A.cam, A.fp, K, mp, cmp);
+    uint32_t cmp = 0, r[kFusePer], nfound = 0;
+#pragma unroll
+    for (int h = 0; h < kFusePer; ++h) {
+        r[h] = pr[h] ? fuse_window(T, nT, A.fp, K, P[h], d[h][0], d[h][1], cmp) : kNone;
+        nfound += r[h] != kNone ? 1u : 0u;
+    }
     warp_count(cmp, &scmp);
     uint32_t tot;
-    const uint32_t pos = block_scan_flag(r != kNone, wtot, tot);
-    if (r != kNone)
-        A.padded[w.out_off + (uint32_t)guard((int)pos, (int)w.b, 13)] = Out3{(int)(m - w.c), (int)(r & 0xFFFFu), (int)(r >> 16)};
+    uint32_t pos = block_scan_add(nfound, wtot, tot);
+#pragma unroll
+    for (int h = 0; h < kFusePer; ++h)
+        if (r[h] != kNone) {
+            const uint32_t m = w.a + (uint32_t)(kFusePer * tid + h);
+            A.padded[w.out_off + (uint32_t)guard((int)pos, (int)w.b, 13)] =
+                Out3{(int)(m - w.c), (int)(r[h] & 0xFFFFu), (int)(r[h] >> 16)};
+            ++pos;
+        }
     if (tid == 0) {
         A.counts[item] = tot;
         A.item_cmp[item] = scmp;
@@ -1907,13 +1980,16 @@ __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
 }
 
 // Per-item counts -> offsets, and the per-item regions gathered into the dense output.  Every
-// CTA scans the counts itself (a few thousand words, read from L2), segment by segment, so
-// that no CTA waits for another; CTA 0 publishes the offsets, the comparison totals (search,
-// fusion) and the status of the run.  Warps copy items.
+// CTA scans the counts itself (a few thousand words, read from L2 once into registers, kept
+// with their offsets in shared memory), segment by segment, so that no CTA waits for another;
+// CTA 0 publishes the offsets, the comparison totals (search, fusion) and the status of the
+// run.  Warps copy items as 32-bit words (an output record is three words), so that a warp's
+// loads and stores are contiguous.
 constexpr int kCopyThreads = 1024;
-constexpr int kCopySeg = 8192;  // items per scan segment (offsets held in shared memory)
+constexpr int kCopyPer = 4;                          // counts per thread and segment
+constexpr int kCopySeg = kCopyPer * kCopyThreads;    // items per scan segment
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
-    __shared__ uint32_t offs[kCopySeg];
+    __shared__ uint32_t offs[kCopySeg], cnts[kCopySeg];
     __shared__ uint32_t wtot[32];
     const int tid = threadIdx.x, bs = blockDim.x;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nw = bs >> 5;
@@ -1923,32 +1999,59 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
     uint32_t base = 0;
     unsigned long long cs = 0, cf = 0, cw = 0;  // comparisons: search, fusion, forward fusion (CTA 0)
     uint32_t flags = 0;
+    static_assert(sizeof(Out3) == 12, "three words per output record");
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(A.padded);
+    uint32_t *dw = reinterpret_cast<uint32_t *>(A.dense);
     for (uint32_t s0 = 0; s0 < A.n_items; s0 += kCopySeg) {
         const uint32_t ns = min((uint32_t)kCopySeg, A.n_items - s0);
-        const uint32_t per = (ns + bs - 1) / bs, cb = min(tid * per, ns), ce = min(cb + per, ns);
-        uint32_t sum = 0;
-        for (uint32_t k = cb; k < ce; ++k) sum += A.counts[s0 + k];
+        // thread t takes items cb .. cb + kCopyPer - 1 of the segment (contiguous, so that the
+        // prefix sum runs in item order)
+        const uint32_t cb = (uint32_t)tid * kCopyPer;
+        uint32_t c[kCopyPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kCopyPer; ++q) {
+            c[q] = cb + q < ns ? __ldg(A.counts + s0 + cb + q) : 0u;
+            sum += c[q];
+        }
         if (blockIdx.x == 0)
-            for (uint32_t k = cb; k < ce; ++k) {
-                const uint32_t v = A.item_cmp[s0 + k];
+#pragma unroll
+            for (int q = 0; q < kCopyPer; ++q) {
+                const uint32_t k = s0 + cb + q;
+                if (cb + q >= ns) break;
+                const uint32_t v = A.item_cmp[k];
                 flags |= v & kItemTimeout;
-                if (s0 + k < A.n_search) cs += v & ~kItemTimeout;
-                else if (s0 + k < A.n_search + A.n_bwd) cf += v & ~kItemTimeout;
+                if (k < A.n_search) cs += v & ~kItemTimeout;
+                else if (k < A.n_search + A.n_bwd) cf += v & ~kItemTimeout;
                 else cw += v & ~kItemTimeout;
             }
         uint32_t total;
         uint32_t run = block_scan_add(sum, wtot, total) + base;
-        for (uint32_t k = cb; k < ce; ++k) {
-            offs[k] = run;
-            run += A.counts[s0 + k];
-        }
+#pragma unroll
+        for (int q = 0; q < kCopyPer; ++q)
+            if (cb + q < ns) {
+                offs[cb + q] = run;
+                cnts[cb + q] = c[q];
+                run += c[q];
+            }
         __syncthreads();
         if (blockIdx.x == 0)
             for (uint32_t k = tid; k < ns; k += bs) A.offsets[s0 + k] = offs[k];
         for (uint32_t k = gw; k < ns; k += gws) {
-            const uint32_t i = s0 + k;
-            const uint32_t cnt = A.counts[i], dst = offs[k], src = A.items[i].out_off;
-            for (uint32_t e = lane; e < cnt; e += 32) A.dense[dst + e] = A.padded[src + e];
+            const uint32_t words = 3u * cnts[k], dst = 3u * offs[k], src = 3u * A.items[s0 + k].out_off;
+            // four loads of each lane in flight before its stores
+            for (uint32_t e0 = 0; e0 < words; e0 += 128) {
+                uint32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t e = e0 + 32u * q + lane;
+                    v[q] = e < words ? __ldg(pw + src + e) : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t e = e0 + 32u * q + lane;
+                    if (e < words) dw[dst + e] = v[q];
+                }
+            }
         }
         base += total;
         __syncthreads();
@@ -2306,7 +2409,7 @@ cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio) {
     const size_t smem = FuseStage::make((int)a.fsn).bytes;
     cudaError_t e = cudaFuncSetAttribute(fuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_prio(fuse_kernel, dim3(blocks), dim3(kFuseChunk), smem, s, prio, a);
+    return launch_prio(fuse_kernel, dim3(blocks), dim3(kFuseThreads), smem, s, prio, a);
 }
 
 cudaError_t launch_tri(const BatchArgs &a, cudaStream_t s) {

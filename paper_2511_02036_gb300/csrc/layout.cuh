@@ -24,7 +24,7 @@ constexpr int kGridCells = kGridCols * kGridRows;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kBucketBits = 11;  // node-key buckets of a keyframe's node index
 constexpr int kBuckets = 1 << kBucketBits;
-constexpr int kFuseChunk = 256; // map points per fusion item (one CTA of the fusion kernel)
+constexpr int kFuseChunk = 512; // map points per fusion item (one CTA of the fusion kernel, two per thread)
 constexpr int kQueryGroup = 64; // queries per search unit (one warp, two per lane)
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
