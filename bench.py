@@ -597,60 +597,56 @@ def dense_comparisons(w, st, dmin):
 
 
 def run_dense(tm, stream, flush, device, reps):
-    """cfg3b: the TUM-VI-shaped step (new keyframe + 20 neighbours, 1500 keypoints, 16 BoW
-    nodes, so ~94 x 94 same-node blocks): search with the dense blocks on the tensor cores
-    (dense_min 64) against the candidate rounds (dense_min 0), same results required."""
+    """Dense node blocks on the tensor cores against the candidate rounds, same results
+    required: the batched workload (64 TUM-VI-shaped steps of cfg3b's model -- new keyframe +
+    20 neighbours, 1500 keypoints, 16 BoW nodes, so ~94 x 94 same-node blocks -- 1280 pairs
+    in one plan, search only) and the single cfg3b step."""
     import torch
     from gen import workloads as W
-    w = W.make_cfg3b()
-    st = w["steps"][0]
-    steps = [dict(kf_id=st["q"], nbrs=st["nbrs"], q_free=st.get("q_free"), nbr_free=st.get("nbr_free"))]
-    out = {"workload": "cfg3b: TUM-VI-shaped step, 512x512 f=190, new keyframe + 20 neighbours, 1500 keypoints, 16 BoW nodes, masks",
-           "dense_min": 64}
-    with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
-        ids = [st["q"]] + list(st["nbrs"])
-        ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
-        results = {}
-        for name, dmin in (("tensor_cores", 64), ("candidate_rounds", 0)):
-            with ctx.plan(steps, sp=tm.SearchParams(dense_min=dmin)) as plan:
-                for _ in range(3):
-                    plan.run(stream)
-                torch.cuda.synchronize()
-                res = plan.results(stream)
-                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
-                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
-                for k in range(reps):
-                    flush.zero_()
-                    e0[k].record(stream)
-                    plan.run(stream)
-                    e1[k].record(stream)
-                torch.cuda.synchronize()
-                ms = float(np.mean([a.elapsed_time(b) for a, b in zip(e0, e1)]))
-                stage = []
-                for _ in range(reps):
-                    flush.zero_()
-                    plan.run(stream, timed=True)
-                    stage.append(plan.stage_times())
-                stage = np.array(stage).mean(axis=0)
-                results[name] = res
-                out[name] = {"ms_per_step": ms, "keyframes_per_s": 1e3 / ms,
-                             "gcomparisons_per_s": res.n_comparisons_search / (ms / 1e3) / 1e9,
-                             "search_kernel_ms": float(stage[0]), "dense_kernel_ms": float(stage[4]),
-                             "kernels_per_run": plan.info()["kernels_per_run"]}
-        a, b = results["tensor_cores"], results["candidate_rounds"]
-        assert np.array_equal(a.matches, b.matches) and a.n_comparisons_search == b.n_comparisons_search
-        ncmp_dense = dense_comparisons(w, st, 64)
-        pk, pk_kind = peaks()
-        fp8_peak = 2.0 * pk["bf16_tflops"]  # dense fp8 = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
-        dms = out["tensor_cores"]["dense_kernel_ms"]
-        flops = 2.0 * 256 * ncmp_dense  # one 256-long +-1 dot product per (query, candidate)
-        out["comparisons"] = a.n_comparisons_search
-        out["dense_comparisons"] = ncmp_dense
-        out["speedup"] = out["candidate_rounds"]["ms_per_step"] / out["tensor_cores"]["ms_per_step"]
-        out["roofline"] = {"bound": "tensor", "kernel": "dense_kernel", "achieved": flops / (dms / 1e3) / 1e12,
-                           "peak": fp8_peak, "unit": "TFLOP/s", "frac": flops / (dms / 1e3) / 1e12 / fp8_peak,
-                           "peak_kind": pk_kind + " bf16 burst x 2 (fp8/bf16 nominal ratio)",
-                           "algorithmic_flops": flops, "traffic": None}
+    out = {"dense_min": 64}
+    for name, w in (("batched", W.make_cfg3b_batch()), ("single_step", W.make_cfg3b())):
+        steps = [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"))
+                 for s in w["steps"]]
+        row = {"workload": ("64 steps x (new keyframe + 20 neighbours), 512x512 f=190, 1500 keypoints, "
+                            "16 BoW nodes, masks; 1280 pairs" if name == "batched" else
+                            "cfg3b: one step, new keyframe + 20 neighbours, 1500 keypoints, 16 BoW nodes, masks")}
+        with tm.Context(w["cam"], max_kp=2048, device=device) as ctx:
+            ids = sorted(set(i for s in w["steps"] for i in [s["q"]] + list(s["nbrs"])))
+            ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
+            results = {}
+            for form, dmin in (("tensor_cores", 64), ("candidate_rounds", 0)):
+                with ctx.plan(steps, sp=tm.SearchParams(dense_min=dmin)) as plan:
+                    for _ in range(3):
+                        plan.run(stream)
+                    torch.cuda.synchronize()
+                    res = plan.results(stream)
+                    ms = time_plan(plan, stream, flush, reps)
+                    stage = []
+                    for _ in range(reps):
+                        flush.zero_()
+                        plan.run(stream, timed=True)
+                        stage.append(plan.stage_times())
+                    stage = np.array(stage).mean(axis=0)
+                    results[form] = res
+                    row[form] = {"ms_per_step": float(ms.mean()), "keyframes_per_s": len(steps) / (float(ms.mean()) / 1e3),
+                                 "gcomparisons_per_s": res.n_comparisons_search / (float(ms.mean()) / 1e3) / 1e9,
+                                 "search_kernel_ms": float(stage[0]), "dense_kernel_ms": float(stage[4]),
+                                 "kernels_per_run": plan.info()["kernels_per_run"]}
+            a, b = results["tensor_cores"], results["candidate_rounds"]
+            assert np.array_equal(a.matches, b.matches) and a.n_comparisons_search == b.n_comparisons_search
+            ncmp_dense = sum(dense_comparisons(w, st, 64) for st in w["steps"])
+            pk, pk_kind = peaks()
+            fp8_peak = 2.0 * pk["bf16_tflops"]  # dense fp8 = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
+            dms = row["tensor_cores"]["dense_kernel_ms"]
+            flops = 2.0 * 256 * ncmp_dense  # one 256-long +-1 dot product per (query, candidate)
+            row["comparisons"] = a.n_comparisons_search
+            row["dense_comparisons"] = ncmp_dense
+            row["speedup"] = row["candidate_rounds"]["ms_per_step"] / row["tensor_cores"]["ms_per_step"]
+            row["roofline"] = {"bound": "tensor", "kernel": "dense_kernel", "achieved": flops / (dms / 1e3) / 1e12,
+                               "peak": fp8_peak, "unit": "TFLOP/s", "frac": flops / (dms / 1e3) / 1e12 / fp8_peak,
+                               "peak_kind": pk_kind + " bf16 burst x 2 (fp8/bf16 nominal ratio)",
+                               "algorithmic_flops": flops, "traffic": None}
+        out[name] = row
     return out
 
 

@@ -508,6 +508,27 @@ def make_cfg2(seed=2000, n_steps=64, nbr_range=(5, 20), kp_range=(600, 2000),
     return dict(cam=CAM_EUROC, frames=frames, steps=steps)
 
 
+def make_cfg3b_batch(seed=3600, n_steps=64, n_nbrs=20, n_kp=1500, n_nodes=16, with_masks=True):
+    """Independent cfg3b-model local-mapping steps (TUM-VI camera, new keyframe + n_nbrs
+    neighbours, n_kp keypoints, 50 % shared points, flip rate 0.08, n_nodes BoW nodes, so that
+    every node is a dense block of ~n_kp / n_nodes keypoints), as one batch.  Frames of all
+    steps are numbered consecutively in one `frames` list."""
+    rng = np.random.default_rng(seed)
+    frames, steps = [], []
+    for s in range(n_steps):
+        sub = np.random.default_rng(int(rng.integers(1 << 62)))
+        poses = trajectory(n_nbrs + 1, 0.125, heading0=sub.uniform(0, 360))
+        seq = Sequence(sub, CAM_TUMVI, poses, np.full(n_nbrs + 1, n_kp), 0.5, 0.08, n_nodes)
+        q = n_nbrs
+        st = seq.step(q, list(range(q - 1, -1, -1)), with_masks=with_masks)
+        base = len(frames)
+        frames.extend(seq.frames)
+        st["q"] += base
+        st["nbrs"] = [b + base for b in st["nbrs"]]
+        steps.append(st)
+    return dict(cam=CAM_TUMVI, frames=frames, steps=steps)
+
+
 def make_stream_cfg4(seed=4000, n_kf=3000, kp_range=(1000, 2000), nbr_range=(5, 20),
                      duration_s=600.0, with_masks=True, rate_hz=None):
     """A keyframe stream along one long trajectory.  Keyframe k's neighbours are the

@@ -1007,7 +1007,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
         if (k < total) {
             const int h = r >= c0o ? 1 : 0;
             const int qi = o + 32 * h;  // state index of the entry's query
-            const uint32_t elo = ld_s32(M.rec + 4 * qi) & 0xFFFFu;
+            const uint32_t rw = ld_s32(M.rec + 4 * qi), elo = rw & 0xFFFFu;
             const int j0 = guard((int)ld_s16(M.epos + 2 * guard((int)elo + r - (h ? c0o : 0), nT, 3)), nT, 4);
             const int pq = guard(g * 32 * Q + qi, nQ, 5);
             const uint4 a0 = ldg(w.qdesc + 2 * pq), a1 = ldg(w.qdesc + 2 * pq + 1);
@@ -1016,8 +1016,10 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             const uint32_t lv = ldg(T.level + j0);
             ++cmp;
             const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
-            bool pass = true;
-            if (kEpi) {
+            // an entry farther than the query's second (as read at the round's start: the
+            // second only decreases) changes neither its best nor its second: no gates needed
+            bool pass = d <= (rw >> 16);
+            if (kEpi && pass) {
                 // l = F^T x_Q: a = (x F00 + y F10) + F20, b = (x F01 + y F11) + F21,
                 // c = (x F02 + y F12) + F22; num = (a x_T + b y_T) + c, den = a^2 + b^2;
                 // pass iff den > 0 and num^2 < thr den
@@ -1030,7 +1032,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
                 const float den = fadd(fmul(la, la), fmul(lb, lb));
                 pass = den > 0.0f && fmul(num, num) < fmul(__uint_as_float(ld_s32(M.thr + 4 * lv)), den);
             }
-            if (kEprej) {
+            if (kEprej && pass) {
                 const float ex = __uint_as_float(ld_s32(M.pc + 36)), ey = __uint_as_float(ld_s32(M.pc + 40));
                 const float dx = fsub(ex, xt.x), dy = fsub(ey, xt.y);
                 if (fadd(fmul(dx, dx), fmul(dy, dy)) < __uint_as_float(ld_s32(M.thre + 4 * lv))) pass = false;
@@ -1269,8 +1271,13 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
         fence_mbar_init();
         s_fail = 0u;
     }
-    if (wid == 2) fundamental_lanes(A.cam, w.pq, w.pt, F);
-    if (tid == 96 && A.sp.epipole_px > 0.0f) epipole_of(A.cam, w.pq, w.pt, epl);
+    // F and the epipole of the pair, as the prep kernel (which runs before this kernel) left them
+    const float *pc = A.pconst + (size_t)kPairConst * w.idx;
+    if (tid < 9) F[tid] = pc[tid];
+    if (tid == 96 && A.sp.epipole_px > 0.0f) {
+        epl[0] = pc[9];
+        epl[1] = pc[10];
+    }
     if (tid < kLevels) {
         const float sc = level_scale(tid);
         thr[tid] = fmul(A.sp.epi_chi2, fmul(sc, sc));
@@ -1288,28 +1295,35 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
         const uint32_t key = T.node[lo];
         const int ncol = hi - lo;
         bool b_ready = false;  // B operand of a one-tile run, kept over its query tiles
-        // the node's eligible queries in ascending position: qlist[head .. qn) (uniform counts)
-        int scan = 0, head = 0, qn = 0;
+        // the node's eligible queries in ascending position: qlist[head .. qn) (uniform counts).
+        // A stored query keyframe is in node-key order: the key's bucket bounds the scan.
+        int scan = 0, head = 0, qn = 0, qend = nQ;
+        if (!w.qraw) {
+            const KfView Qv = KfView::at(w.q, A.L);
+            const uint32_t b = key >> (32 - kBucketBits);
+            scan = min((int)Qv.bstart[b], nQ);
+            qend = min((int)Qv.bstart[b + 1], nQ);
+        }
         for (;;) {
-            if (qn - head < kDenseRows && scan < nQ) {
+            if (qn - head < kDenseRows && scan < qend) {
                 const int rest = qn - head;  // < 128: at most one entry per thread to move
                 const uint16_t v = tid < rest ? qlist[head + tid] : (uint16_t)0;
                 __syncthreads();
                 if (tid < rest) qlist[tid] = v;
                 qn = rest;
                 head = 0;
-                while (qn < kDenseRows && scan < nQ) {
+                while (qn < kDenseRows && scan < qend) {
                     uint32_t nk[kDenseScan];
 #pragma unroll
                     for (int u = 0; u < kDenseScan; ++u) {
                         const int p = scan + u * kDenseThreads + tid;
-                        nk[u] = p < nQ ? w.qnode[p] : 0u;
+                        nk[u] = p < qend ? w.qnode[p] : 0u;
                     }
                     unsigned m[kDenseScan];
 #pragma unroll
                     for (int u = 0; u < kDenseScan; ++u) {
                         const int p = scan + u * kDenseThreads + tid;
-                        bool f = p < nQ && (w.qraw ? node_key(nk[u]) : nk[u]) == key;
+                        bool f = p < qend && (w.qraw ? node_key(nk[u]) : nk[u]) == key;
                         if (f && w.a != kNone)
                             f = A.masks[w.a + (w.qorig ? (uint32_t)w.qorig[p] : (uint32_t)p)] != 0;
                         m[u] = __ballot_sync(kFull, f);
@@ -1393,9 +1407,11 @@ __global__ void __launch_bounds__(kDenseThreads, 3) dense_kernel(BatchArgs A) {
 #pragma unroll
                                 for (int k = 0; k < 16; ++k) {
                                     const int c = c0 + k;
-                                    if (c < nc) {
-                                        const int dot = (int)__int_as_float(v[k]);
-                                        const uint32_t d = (uint32_t)(256 - dot) >> 1;
+                                    const int dot = (int)__int_as_float(v[k]);
+                                    const uint32_t d = (uint32_t)(256 - dot) >> 1;
+                                    // an entry farther than the query's current second changes
+                                    // neither its best nor its second: its gates are not needed
+                                    if (c < nc && d <= sc) {
                                         const float4 cc = col[c];
                                         if (cc.z >= 0.0f && (!epi || epi_pass_den(l, den, cc.x, cc.y, cc.z)) &&
                                             !(eprej && near_epipole(epl, cc.x, cc.y, cc.w))) {

@@ -167,3 +167,27 @@ def test_dense_min_validation(tm, dense_step):
         with pytest.raises(tm.TMError) as e:
             ctx.search(st["q"], st["nbrs"], params=tm.SearchParams(dense_min=8))
         assert e.value.status == tm.TM_ERR_INVALID_ARG
+
+
+def test_dense_batch_matches_oracle(tm):
+    """Several cfg3b-model steps as one plan (the batched dense workload's model, fewer steps):
+    dense blocks on the tensor cores for every pair of the batch, results equal the oracle's
+    pair by pair, and the candidate rounds' (dense_min 0) too."""
+    w = W.make_cfg3b_batch(seed=3610, n_steps=3, n_nbrs=8)
+    steps = [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"))
+             for s in w["steps"]]
+    exp, ecmp = [], 0
+    for st in w["steps"]:
+        r, c = O.search_step(w["cam"], w["frames"], st)
+        exp.extend(r)
+        ecmp += c
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        ids = sorted(set(i for s in w["steps"] for i in [s["q"]] + list(s["nbrs"])))
+        ctx.add_keyframes(ids, [w["frames"][i] for i in ids])
+        for dmin in (64, 0):
+            with ctx.plan(steps, sp=tm.SearchParams(dense_min=dmin)) as plan:
+                plan.run()
+                res = plan.results()
+            assert len(res.pairs) == len(exp) and res.n_comparisons_search == ecmp
+            for g, e in zip(res.pairs, exp):
+                np.testing.assert_array_equal(g, e)
