@@ -432,6 +432,8 @@ typedef struct {
     int32_t dense_split;      /* dense kernel CTAs per pair (0 when off)                         */
     int32_t search_ctas;      /* CTAs of the search launch                                       */
     int32_t tuned;            /* 1: chosen by the tuner (measured or cached); 0: defaults        */
+    int32_t per_lane;         /* 1: each lane walks its own queries' candidates (per-lane form);
+                                 0: a warp's candidates spread over its lanes in rounds          */
 } tm_plan_tuning;
 tm_status tm_plan_get_tuning(tm_plan *plan, tm_plan_tuning *out);
 
@@ -464,8 +466,9 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *   TM_DEBUG_BRANCH_PRIORITY which branch of a batch the scheduler serves first: 0 the search
  *                           branch, 1 the store branch (ingest, fusion), 2 neither; -1 = tuned
  *                           (default)
- *   TM_DEBUG_QUERIES_PER_LANE search warps take 32 (1) or 64 (2) queries at a time; 0 = tuned
- *                           (default)
+ *   TM_DEBUG_QUERIES_PER_LANE search warps take 32 (1) or 64 (2) queries at a time with their
+ *                           candidates spread over the lanes in rounds, or 64 with each lane
+ *                           walking its own two queries' candidates (3); 0 = tuned (default)
  *   TM_DEBUG_PERSISTENT     1: resident search CTAs take pairs from a work counter; 0: one CTA
  *                           per pair; -1 = tuned (default)
  * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, value out of range). */

@@ -115,7 +115,7 @@ class tm_server_config(ctypes.Structure):
 class tm_plan_tuning(ctypes.Structure):
     _fields_ = [("queries_per_warp", c_i32), ("persistent", c_i32), ("l2_prefetch", c_i32),
                 ("branch_priority", c_i32), ("dense_min", c_i32), ("dense_split", c_i32),
-                ("search_ctas", c_i32), ("tuned", c_i32)]
+                ("search_ctas", c_i32), ("tuned", c_i32), ("per_lane", c_i32)]
 
 
 class tm_fuse_apply_stats(ctypes.Structure):

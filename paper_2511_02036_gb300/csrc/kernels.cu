@@ -1082,6 +1082,132 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
 }
 
 
+// The same group (64 queries, two per lane) in the per-lane form: after the same bucket
+// lookups, each lane walks its own queries' candidates itself, in eligible-list order (both
+// queries' candidates interleaved, for two independent load chains), keeping each query's
+// (best key, second distance) in registers -- no prefix sums, no owner search, no shared
+// atomics, at the price of lanes that idle while the lane with most candidates finishes.
+// The state of a query is the same minimum over its candidates as in the rounds.  Default
+// gates only (epipolar gate on or off, no epipole rejection, no dense blocks).
+template <bool kEpi>
+__device__ __forceinline__ void search_group_lane(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                                  const SearchSmem &M, uint32_t *nacc, int g, const QLoad<2> &q,
+                                                  uint32_t &cmp) {
+    constexpr int Q = 2;
+    const int lane = (int)(threadIdx.x & 31u);
+    const int nT = (int)w.nt, nQ = (int)w.nq;
+    uint32_t key[Q];
+    int lo[Q], be[Q];
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        key[h] = w.qraw ? node_key(q.nk[h]) : q.nk[h];
+        const uint32_t b = key[h] >> (32 - kBucketBits);
+        lo[h] = guard((int)ld_s16(M.bst + 2 * b), nT + 1, 1);
+        be[h] = guard((int)ld_s16(M.bst + 2 * b + 2), nT + 1, 2);
+    }
+    int nlt[Q], nle[Q], len = 0;
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        nlt[h] = nle[h] = 0;
+        len = max(len, be[h] - lo[h]);
+    }
+    for (int t = 0; t < len; ++t) {
+        bool pt[Q];
+        uint32_t kt[Q];
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            pt[h] = lo[h] + t < be[h];
+            kt[h] = ld_s32_if(pt[h], M.tkey + 4 * (lo[h] + t), 0u);
+        }
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            nlt[h] += pt[h] && kt[h] < key[h];
+            nle[h] += pt[h] && kt[h] <= key[h];
+        }
+    }
+    int c[Q], elo[Q];
+    uint32_t bk[Q], sc[Q];
+    float la[Q], lb[Q], lc[Q];
+    uint4 a0[Q], a1[Q];
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const bool el = q.el[h] >= 0 ? q.el[h] != 0 : (ldg(A.masks + w.a + q.io[h]) != 0);
+        elo[h] = eligible_before(M, lo[h] + nlt[h]);
+        c[h] = el ? eligible_before(M, lo[h] + nle[h]) - elo[h] : 0;
+        bk[h] = kNone;
+        sc[h] = 0xFFFFu;
+        la[h] = lb[h] = lc[h] = 0.0f;
+        a0[h] = a1[h] = make_uint4(0u, 0u, 0u, 0u);
+        if (c[h] > 0) {
+            const int pq = guard(g * 32 * Q + 32 * h + lane, nQ, 5);
+            a0[h] = ldg(w.qdesc + 2 * pq);
+            a1[h] = ldg(w.qdesc + 2 * pq + 1);
+            if (kEpi) {
+                // l = F^T x_Q, the same expression as in the rounds
+                const float2 xq = ldg(w.qxy + pq);
+                const float4 F0 = ld_s128(M.pc), F1 = ld_s128(M.pc + 16), F2 = ld_s128(M.pc + 32);
+                la[h] = fadd(fadd(fmul(xq.x, F0.x), fmul(xq.y, F0.w)), F1.z);
+                lb[h] = fadd(fadd(fmul(xq.x, F0.y), fmul(xq.y, F1.x)), F1.w);
+                lc[h] = fadd(fadd(fmul(xq.x, F0.z), fmul(xq.y, F1.y)), F2.x);
+            }
+        }
+    }
+    const int cm = max(c[0], c[1]);
+    for (int t = 0; t < cm; ++t) {
+#pragma unroll
+        for (int h = 0; h < Q; ++h) {
+            if (t < c[h]) {
+                const int j0 = guard((int)ld_s16(M.epos + 2 * guard(elo[h] + t, nT, 3)), nT, 4);
+                const uint4 t0 = ldg(T.desc + 2 * j0), t1 = ldg(T.desc + 2 * j0 + 1);
+                const float2 xt = ldg(T.xy + j0);
+                const uint32_t lv = ldg(T.level + j0);
+                ++cmp;
+                const uint32_t d = (uint32_t)hamming(a0[h], a1[h], t0, t1);
+                // an entry farther than the query's second changes neither its best nor second
+                bool pass = d <= sc[h];
+                if (kEpi && pass) {
+                    const float num = fadd(fadd(fmul(la[h], xt.x), fmul(lb[h], xt.y)), lc[h]);
+                    const float den = fadd(fmul(la[h], la[h]), fmul(lb[h], lb[h]));
+                    pass = den > 0.0f && fmul(num, num) < fmul(__uint_as_float(ld_s32(M.thr + 4 * lv)), den);
+                }
+                if (pass) {
+                    const uint32_t kk = (d << 16) | (uint32_t)j0;
+                    sc[h] = min(sc[h], max(bk[h], kk) >> 16);
+                    bk[h] = min(bk[h], kk);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const int p = g * 32 * Q + 32 * h + lane;
+        bool ok = false;
+        uint32_t best = 0, j = 0;
+        if (p < nQ && bk[h] != kNone) {
+            best = bk[h] >> 16;
+            ok = (int)best <= A.sp.hamming_max;
+            if (ok && A.sp.ratio_num != 0 && sc[h] != 0xFFFFu)
+                ok = (long long)A.sp.ratio_den * best < (long long)A.sp.ratio_num * sc[h];
+            j = (uint32_t)guard((int)(bk[h] & 0xFFFFu), nT, 6);
+        }
+        const unsigned m = __ballot_sync(kFull, ok);
+        if (m) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(nacc, (uint32_t)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (ok) {
+                const uint32_t io = q.io[h];
+                const uint32_t bin = A.sp.rot_filter ? (uint32_t)rot_bin(ldg(w.qangle + p), ldg(T.angle + j), A.sp.rot_mode) : 0u;
+                const uint32_t e = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                A.acc[w.c + (uint32_t)guard((int)e, nQ, 7)] =
+                    make_uint2(io | (j << 16), (uint32_t)ldg(T.orig + j) | (best << 16) | (bin << 25));
+                if (A.sp.resolve) red_s_min(M.win + 4 * j, (best << 16) | io);
+            }
+        }
+    }
+}
+
+
 // ---------------------------------------------------------------- dense node blocks (S3b)
 //
 // A query whose BoW node holds at least dense_min keypoints of the neighbour belongs to a
@@ -1475,9 +1601,12 @@ constexpr int kSearchThreads = 256;
 template <int Q, bool kEpi, bool kEprej, bool kDense>
 __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, uint32_t parity, bool first) {
     constexpr int kMaxT = kSearchThreads;
+    constexpr bool kLane = Q == 3;            // the per-lane form (two queries per lane)
+    constexpr int QL = kLane ? 2 : Q;         // queries per lane of a group
+    static_assert(!kLane || (!kEprej && !kDense), "the per-lane form runs the default gates");
     extern __shared__ __align__(128) unsigned char ssm[];
     __shared__ __align__(16) float thr[kLevels], thre[kLevels];
-    __shared__ uint32_t qrec[kMaxT / 32][32 * Q], sbest[kMaxT / 32][32 * Q];  // per warp: its queries' states
+    __shared__ uint32_t qrec[kMaxT / 32][32 * QL], sbest[kMaxT / 32][32 * QL];  // per warp: its queries' states
     __shared__ uint32_t hist[32];
     __shared__ uint32_t keep, scmp, sdfail, nacc;
     __shared__ __align__(8) uint64_t bar, never;
@@ -1535,8 +1664,8 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     if (tid >= 96 && tid < 128) hist[tid - 96] = 0u;
     for (int j = tid; j < nT; j += kMaxT) win[j] = kNone;
     for (int k = tid; k < nwq; k += kMaxT) qbits[k] = 0u;
-    QLoad<Q> cur = {};
-    if (wid * 32 * Q < nQ) cur = load_group<Q>(A, w, wid);  // the first group's loads overlap the setup
+    QLoad<QL> cur = {};
+    if (wid * 32 * QL < nQ) cur = load_group<QL>(A, w, wid);  // the first group's loads overlap the setup
     // the thread that initialized the barrier and issued the bulk copies awaits them; the CTA
     // barrier then publishes the copied data (and every other setup write) to all threads
     if (tid == 0) {
@@ -1571,10 +1700,13 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     M.rec = smem_addr(&qrec[wid][0]);
     M.sb = smem_addr(&sbest[wid][0]);
     uint32_t cmp = 0, dfail = 0;
-    for (int g = wid; g * 32 * Q < nQ; g += nw) {
-        QLoad<Q> nxt = {};
-        if ((g + nw) * 32 * Q < nQ) nxt = load_group<Q>(A, w, g + nw);
-        search_group<Q, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
+    for (int g = wid; g * 32 * QL < nQ; g += nw) {
+        QLoad<QL> nxt = {};
+        if ((g + nw) * 32 * QL < nQ) nxt = load_group<QL>(A, w, g + nw);
+        if constexpr (kLane)
+            search_group_lane<kEpi>(A, w, T, M, &nacc, g, cur, cmp);
+        else
+            search_group<QL, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
@@ -2361,14 +2493,17 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s, int prio) {
 
 size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 
-// The search kernel instance for a launch: the group size (1 or 2 queries per lane) and the
-// persistent form exist for the gate configurations of the default search (epipolar gate on
+// The search kernel instance for a launch: the group form (rounds with 1 or 2 queries per lane,
+// or 3: the per-lane form) and the persistent form exist for the gate configurations of the
+// default search (epipolar gate on
 // or off, no epipole rejection, no dense blocks); any other configuration runs 64-query groups,
 // one CTA per pair (search_form reports the form a launch gets).
 static bool search_variants(const BatchArgs &a) { return !(a.sp.epipole_px > 0.0f) && !(a.sp.dense_min > 0); }
 static void (*search_fn(const BatchArgs &a))(BatchArgs) {
     const bool epi = a.sp.epipolar != 0, eprej = a.sp.epipole_px > 0.0f, dense = a.sp.dense_min > 0;
     if (search_variants(a)) {
+        if (a.qpl == 3 && !a.persist)
+            return epi ? search_kernel<3, true, false, false, false> : search_kernel<3, false, false, false, false>;
         if (a.qpl == 1)
             return a.persist ? (epi ? search_kernel<1, true, false, false, true> : search_kernel<1, false, false, false, true>)
                              : (epi ? search_kernel<1, true, false, false, false> : search_kernel<1, false, false, false, false>);
@@ -2387,6 +2522,7 @@ void search_form(BatchArgs &a) {
         a.qpl = 2;
         a.persist = 0;
     }
+    if (a.qpl == 3) a.persist = 0;  // the per-lane form has no persistent instance
 }
 
 int search_ctas_per_sm(const BatchArgs &a) {

@@ -1293,7 +1293,7 @@ void tmap::load_tuning(tm_ctx *c, const char *path) {
     Knobs k;
     while (fscanf(f, "%d %d %d %d %d %d %d", &key, &k.qpl, &k.persist, &k.prefetch, &k.bprio, &k.dense_min,
                   &k.dsplit_div) == 7)
-        if ((k.qpl == 1 || k.qpl == 2) && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
+        if (k.qpl >= 1 && k.qpl <= 3 && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
     fclose(f);
 }
 
@@ -1375,7 +1375,11 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         std::vector<Knobs> alts;
         Knobs k = best;
         switch (knob) {
-            case 0: if (!c->force_qpl) { k.qpl = best.qpl == 2 ? 1 : 2; alts.push_back(k); } break;
+            case 0:
+                if (!c->force_qpl)
+                    for (int qf : {2, 1, 3})
+                        if (qf != best.qpl) { k.qpl = qf; alts.push_back(k); }
+                break;
             case 1: if (c->force_persist < 0) { k.persist = !best.persist; alts.push_back(k); } break;
             case 2: if (c->force_prefetch < 0) { k.prefetch = !best.prefetch; alts.push_back(k); } break;
             case 3: if (c->branch_prio < 0 && both_branches) { k.bprio = !best.bprio; alts.push_back(k); } break;
@@ -1752,7 +1756,7 @@ extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
             c->branch_prio = (int)value;
             return TM_OK;
         case TM_DEBUG_QUERIES_PER_LANE:
-            if (value < 0 || value > 2) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: queries per lane must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: group form must be 0, 1, 2 or 3");
             c->force_qpl = (int)value;
             return TM_OK;
         case TM_DEBUG_PERSISTENT:
@@ -1901,7 +1905,8 @@ extern "C" tm_status tm_plan_get_tuning(tm_plan *P, tm_plan_tuning *out) {
     if (!P || !out) return fail(TM_ERR_INVALID_ARG, "tm_plan_get_tuning: null argument");
     const BatchArgs &A = P->B.args;
     const bool fused = P->B.sp.mode != TM_MODE_PER_PAIR;
-    out->queries_per_warp = fused ? 32 * (int)A.qpl : 0;
+    out->queries_per_warp = fused ? 32 * (int)(A.qpl == 3 ? 2 : A.qpl) : 0;
+    out->per_lane = fused && A.qpl == 3 ? 1 : 0;
     out->persistent = fused ? (int)A.persist : 0;
     out->l2_prefetch = fused ? (int)A.l2_prefetch : 0;
     out->branch_priority = fused ? (P->ctx->branch_prio >= 0 ? P->ctx->branch_prio : P->B.knobs.bprio) : 0;

@@ -80,7 +80,7 @@ def force(tm, ctx, qpl=None, persist=None, prefetch=None, bprio=None):
         ctx.debug_set(L.TM_DEBUG_BRANCH_PRIORITY, bprio)
 
 
-@pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))))
+@pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))) + [(3, 0, 0), (3, 0, 1)])
 def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
     w, exp = batch
     with tm.Context(w["cam"], max_kp=2048) as ctx:
@@ -88,7 +88,7 @@ def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
         force(tm, ctx, qpl=qpl, persist=persist, prefetch=prefetch)
         with ctx.plan(steps_of(w)) as plan:
             t = plan.tuning()
-            assert t["queries_per_warp"] == 32 * qpl
+            assert t["queries_per_warp"] == 32 * min(qpl, 2) and t["per_lane"] == (qpl == 3)
             assert t["persistent"] == persist and t["l2_prefetch"] == prefetch
             if persist:
                 assert 1 <= t["search_ctas"] <= sum(len(s["nbrs"]) for s in w["steps"])
@@ -111,10 +111,11 @@ def test_branch_priority_matches_oracle(tm, batch, bprio):
             assert_same(plan.results(), exp)
 
 
-@pytest.mark.parametrize("qpl", [1, 2])
+@pytest.mark.parametrize("qpl", [1, 2, 3])
 def test_variant_gates_ignore_persistent(tm, qpl):
-    """With the epipole rejection on, the search takes its general instance: the persistent
-    request is set aside (reported as 0), the results still equal the oracle's."""
+    """With the epipole rejection on, the search takes its general instance (rounds, 64-query
+    groups): the persistent and per-lane requests are set aside (reported as 0), the results
+    still equal the oracle's."""
     w = W.make_cfg2(seed=2201, n_steps=3)
     sp = tm.SearchParams(epipole_px=12.0)
     exp = expected(w, sp)
@@ -123,9 +124,24 @@ def test_variant_gates_ignore_persistent(tm, qpl):
         force(tm, ctx, qpl=qpl, persist=1)
         with ctx.plan(steps_of(w), sp=sp) as plan:
             t = plan.tuning()
-            assert t["persistent"] == 0
+            assert t["persistent"] == 0 and t["per_lane"] == 0
             plan.run()
             assert_same(plan.results(), exp)
+
+
+def test_per_lane_form_without_epipolar_gate(tm, batch):
+    """The per-lane form's instance without the epipolar gate."""
+    w = batch[0]
+    sp = tm.SearchParams(epipolar=False)
+    exp = expected(w, sp)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        force(tm, ctx, qpl=3)
+        with ctx.plan(steps_of(w), sp=sp) as plan:
+            assert plan.tuning()["per_lane"] == 1
+            plan.run()
+            assert_same(plan.results(), exp)
+        assert_same(ctx.batch_run(steps_of(w), sp=sp), exp)
 
 
 @pytest.mark.parametrize("dense_min", [16, 100])
@@ -153,7 +169,7 @@ def test_tuned_choice_matches_oracle(tm, batch):
         load_all(ctx, w)
         with ctx.plan(steps_of(w)) as plan:
             t = plan.tuning()
-            assert t["tuned"] == 1 and t["queries_per_warp"] in (32, 64)
+            assert t["tuned"] == 1 and t["queries_per_warp"] in (32, 64) and t["per_lane"] in (0, 1)
             plan.run()
             assert_same(plan.results(), exp)
         with ctx.plan(steps_of(w)) as plan:
