@@ -631,7 +631,7 @@ def run_dense(tm, stream, flush, device, reps):
                     row[form] = {"ms_per_step": float(ms.mean()), "keyframes_per_s": len(steps) / (float(ms.mean()) / 1e3),
                                  "gcomparisons_per_s": res.n_comparisons_search / (float(ms.mean()) / 1e3) / 1e9,
                                  "search_kernel_ms": float(stage[0]), "dense_kernel_ms": float(stage[4]),
-                                 "kernels_per_run": plan.info()["kernels_per_run"]}
+                                 "kernels_per_run": plan.info()["kernels_per_run"], "tuning": plan.tuning()}
             a, b = results["tensor_cores"], results["candidate_rounds"]
             assert np.array_equal(a.matches, b.matches) and a.n_comparisons_search == b.n_comparisons_search
             ncmp_dense = sum(dense_comparisons(w, st, 64) for st in w["steps"])
