@@ -6,7 +6,7 @@ A step is one pass of the whole hot path over one batch: the 64 new keyframes of
 64-step EuRoC-shaped batch (5..20 neighbours and 600..2000 keypoints per frame, uneven)
 enter the device-resident store (grouping by BoW node + projection grid), then every
 (new keyframe, neighbour) pair is searched and every step's map points are fused: one replay
-of a CUDA graph of four kernels.  Inputs are synthetic (seeded generator), all
+of a CUDA graph of five kernels.  Inputs are synthetic (seeded generator), all
 resident in HBM before the timed region; the L2 is flushed (256 MB written) before each
 timed step because the batch (~95 MB) fits in L2.  Prints one JSON line.
 
