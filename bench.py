@@ -510,22 +510,25 @@ def run_mine(args, rank, world, local_rank):
         serial_value, serial_el = job_throughput(len(new_ids) * ke, time.perf_counter() - t0, world, dist, dev)
         assert np.array_equal(r.matches, res.matches) and np.array_equal(r.fuse, res.fuse)
 
-        # pipelined: the batch of step k + 1 is begun (marshalled, uploaded, launched) before
-        # the results of step k are taken; consecutive steps store their new keyframes under
-        # two id sets, so that a step's keyframes are removed once its results are in
-        ids2 = [new_ids, [i + (1 << 40) for i in new_ids]]
-        tables = [table, tm.StepTable.from_steps([dict(st, kf_id=i) for st, i in zip(off_steps, ids2[1])])]
+        # pipelined: the batches of steps k + 1 and k + 2 are begun (marshalled, uploaded,
+        # launched) before the results of step k are taken, so that the host prepares while
+        # earlier batches transfer and run; consecutive steps store their new keyframes under
+        # three id sets, so that a step's keyframes are removed once its results are in
+        depth = 3
+        ids2 = [[i + (j << 40) for i in new_ids] for j in range(depth)]
+        tables = [table] + [tm.StepTable.from_steps([dict(st, kf_id=i) for st, i in zip(off_steps, ids2[j])])
+                            for j in range(1, depth)]
 
         def pipelined(n):
-            prev, last = None, None
-            for k in range(n + 1):
-                t = None
+            inflight, last = [], None
+            for k in range(n + depth - 1):
                 if k < n:
-                    t = (ctx.batch_begin(tables[k % 2], masks=h_masks, mps=h_mps, new=(ids2[k % 2], h_new)), k % 2)
-                if prev is not None:
-                    last = ctx.batch_finish(prev[0])
-                    ctx.remove_keyframes(ids2[prev[1]])
-                prev = t
+                    inflight.append((ctx.batch_begin(tables[k % depth], masks=h_masks, mps=h_mps,
+                                                     new=(ids2[k % depth], h_new)), k % depth))
+                if len(inflight) == depth or (k >= n and inflight):
+                    t, j = inflight.pop(0)
+                    last = ctx.batch_finish(t)
+                    ctx.remove_keyframes(ids2[j])
             return last
 
         pipelined(max(2, args.warmup))
@@ -538,9 +541,9 @@ def run_mine(args, rank, world, local_rank):
         out["e2e"] = {"value": e2e_value, "unit": "keyframes/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "ms_per_step": 1e3 * el / ke,
-                      "api": "Context.batch_begin / batch_finish -> tm_batch_begin / tm_batch_finish, two "
-                             "batches in flight (step k + 1 begun before step k's results are taken; step "
-                             "table as columns; pinned host buffers: new keyframes, masks, map points in; "
+                      "api": "Context.batch_begin / batch_finish -> tm_batch_begin / tm_batch_finish, three "
+                             "batches in flight (steps k + 1 and k + 2 begun before step k's results are taken; "
+                             "step table as columns; pinned host buffers: new keyframes, masks, map points in; "
                              "matches and fusion candidates out) + Context.remove_keyframes of each step's "
                              "64 new keyframes once its results are in",
                       "link": "inputs cross the host link at about 205 GB/s on this GB300 (copy engine and SM "

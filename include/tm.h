@@ -387,21 +387,22 @@ tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
  * uploads, ingest of its new keyframes, launches) on a stream of its own and returns a ticket
  * without waiting; tm_batch_finish waits for that batch and copies its results, with
  * tm_batch_run's result rules.  At most TM_BATCH_INFLIGHT batches of a context are in flight
- * (TM_ERR_BUSY beyond).  A batch's GPU work starts after the ingest of the batch begun before
+ * (TM_ERR_BUSY beyond); each slot keeps its device buffers once used.  A batch's GPU work starts after the ingest of the batch begun before
  * it, so a neighbour may be a keyframe that an earlier in-flight batch stores; their copies
  * and kernels otherwise overlap.  The caller's input arrays (host or device) must stay valid
  * and unchanged until tm_batch_finish returns; keyframes used by an in-flight batch cannot be
  * removed (TM_ERR_BUSY).  If tm_batch_finish reports an error, the batch's new keyframes are
  * taken out of the store again, except those that a batch still in flight reads.  Tickets are
  * finished in any order; an unknown ticket is TM_ERR_NOT_FOUND. */
-#define TM_BATCH_INFLIGHT 2
+#define TM_BATCH_INFLIGHT 4
 tm_status tm_batch_begin(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
                          const tm_batch_inputs *in, const tm_search_params *sp,
                          const tm_fuse_params *fp, uint64_t *ticket);
 tm_status tm_batch_finish(tm_ctx *ctx, uint64_t ticket, tm_batch_result *res);
 /* Host wall time of the phases of the context's last tm_batch_run, in microseconds: us[0]
  * the work list and the uploads (prepare), us[1] the launches, us[2] waiting for the GPU and
- * the result counts, us[3] the result downloads.  Zeros before the first call. */
+ * the result counts, us[3] the result downloads; after a tm_batch_finish, its own wait (us[2])
+ * and downloads (us[3]) with us[0] = us[1] = 0.  Zeros before the first call. */
 tm_status tm_batch_last_host_times(tm_ctx *ctx, double us[4]);
 
 /* Prepared batch: uploads the inputs once and captures the launch in a CUDA graph; each

@@ -282,6 +282,22 @@ class StepTable:
     def __len__(self):
         return len(self.kf_id)
 
+    def _cached(self, name, make):
+        v = self.__dict__.get(name)
+        if v is None:
+            v = make()
+            self.__dict__[name] = v
+        return v
+
+    def n_pairs(self):
+        """Neighbour pairs of all steps (read at first use, like the records)."""
+        return self._cached("_n_pairs", lambda: int(np.sum(np.asarray(self.n_nbrs, np.int64))))
+
+    def lists(self):
+        """(kf ids, neighbour counts) as Python lists (read at first use)."""
+        return self._cached("_lists", lambda: (np.asarray(self.kf_id, np.uint64).tolist(),
+                                                 np.asarray(self.n_nbrs, np.int64).tolist()))
+
     def records(self, keep):
         """tm_step records (numpy structured array, C layout); the arrays they point into are
         appended to keep.  Built at the table's first use and kept with it: a table is read
@@ -472,7 +488,8 @@ def _fwd_cap(steps):
     if isinstance(steps, StepTable):
         if steps.fwd_mp_count is None:
             return 0
-        return int((np.asarray(steps.fwd_mp_count, np.int64) * np.asarray(steps.n_nbrs, np.int64)).sum())
+        return steps._cached("_fwd_cap", lambda: int((np.asarray(steps.fwd_mp_count, np.int64) *
+                                                      np.asarray(steps.n_nbrs, np.int64)).sum()))
     tot = 0
     for s in steps:
         c = s.get("fwd_mp_count")
@@ -488,9 +505,11 @@ def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
     g = kf_sizes.get
     if isinstance(steps, StepTable):
         # per step only: at most n_Q matches per pair (the looser bound; no lookup per pair)
-        nq = np.fromiter((g(int(k), default) for k in steps.kf_id.tolist()), np.int64, len(steps))
-        mc = int((nq * np.asarray(steps.n_nbrs, np.int64)).sum())
-        return mc, 0 if steps.mp_count is None else int(np.asarray(steps.mp_count, np.int64).sum())
+        kf, nn = steps.lists()
+        mc = sum(g(k, default) * n for k, n in zip(kf, nn))
+        fc = steps._cached("_mp_total", lambda: 0 if steps.mp_count is None else
+                           int(np.asarray(steps.mp_count, np.int64).sum()))
+        return mc, fc
     nq = np.fromiter((g(int(s["kf_id"]), default) for s in steps), np.int64, len(steps))
     cnt = np.fromiter((len(s["nbrs"]) for s in steps), np.int64, len(steps))
     nt = np.fromiter((g(int(t), default) for s in steps for t in s["nbrs"]), np.int64, int(cnt.sum()))
@@ -831,7 +850,7 @@ class Context:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
         if self._res is None:
             self._res = _ResultBuffers()
-        n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
+        n_pairs = steps.n_pairs() if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
         r, bufs = self._res.struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps), tri is not None)
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
@@ -857,7 +876,7 @@ class Context:
         mc, fc = _result_caps(steps, self.sizes, sp.resolve)
         if masks is not None or mps is not None:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
-        n_pairs = int(np.sum(steps.n_nbrs)) if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
+        n_pairs = steps.n_pairs() if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         keep.extend([sps, fps])
         t = ctypes.c_uint64()

@@ -27,7 +27,7 @@ TM_MODE_PER_PAIR = 1
 TM_MAX_KP_LIMIT = 8192
 TM_MAX_IMAGE_SIZE = 16384
 TM_PLAN_STAGES = 6
-TM_BATCH_INFLIGHT = 2
+TM_BATCH_INFLIGHT = 4
 TM_DEBUG_WAIT_LIMIT = 1
 TM_DEBUG_STARVE_WAITS = 2
 TM_DEBUG_SEARCH_THREADS = 3

@@ -928,11 +928,13 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.total_pad = pad;
     B.smem_n = (smem_n + 31) & ~31;
     B.slots = slots_used;
-    // search CTAs take the pairs largest first
+    // search CTAs take the pairs largest first (ties in item order): one 64-bit key per pair,
+    // (~cost << 32 | index), sorted ascending
+    std::vector<uint64_t> okey(B.n_search_items);
+    for (size_t i = 0; i < okey.size(); ++i) okey[i] = ((uint64_t)(~items[i].cost) << 32) | (uint64_t)i;
+    std::sort(okey.begin(), okey.end());
     std::vector<uint32_t> order(B.n_search_items);
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t x, uint32_t y) { return items[x].cost > items[y].cost; });
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)(okey[i] & 0xFFFFFFFFu);
     // fusion stage: the largest target of the batch (new keyframes, and neighbours for
     // forward fusion)
     int fuse_n = 0;
@@ -1481,14 +1483,20 @@ extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_s
     if (!a.s && ((e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking)) ||
                  (e = cudaEventCreateWithFlags(&a.ingested, cudaEventDisableTiming))))
         return cuda_fail(e, "async batch stream");
-    // after the ingest of the batch begun before this one (its keyframes may be neighbours here)
-    if (c->async_last >= 0 && c->async[c->async_last].ticket &&
-        (e = cudaStreamWaitEvent(a.s, c->async[c->async_last].ingested, 0)))
-        return cuda_fail(e, "async batch order");
     BatchBuf &B = a.B;
+    // this batch's uploads (its own buffers) start at once; its kernels wait for the ingest of
+    // the batch begun before it (whose keyframes may be neighbours here)
     B.early_fork = spd.mode != TM_MODE_PER_PAIR;
     tm_status st = prepare_batch(c, B, steps, n_steps, in, spd, fpd, a.s);
     B.early_fork = false;
+    const bool prepared = !st;  // (its new keyframes are then stored: taken out on failure)
+    if (!st && c->async_last >= 0 && c->async[c->async_last].ticket) {
+        // both branches: the stream's (ingest, fusion, copy) and the search branch, which a
+        // one-shot batch forks early
+        const cudaEvent_t prev = c->async[c->async_last].ingested;
+        if ((e = cudaStreamWaitEvent(a.s, prev, 0)) || (B.paux && (e = cudaStreamWaitEvent(B.paux, prev, 0))))
+            st = cuda_fail(e, "async batch order");
+    }
     if (!st) {
         B.ingest_done = a.ingested;
         if (spd.mode == TM_MODE_PER_PAIR) {
@@ -1500,11 +1508,12 @@ extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_s
             st = enqueue_fused(c, B, default_threads(c, B), ln, a.s);
         }
         B.ingest_done = nullptr;
-        if (st) drop_new_keyframes(c, B, in);
     }
     if (st) {
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(a.s);
+        if (B.paux) cudaStreamSynchronize(B.paux);
+        if (prepared) drop_new_keyframes(c, B, in);
         return st;
     }
     for (int sl : B.slots) c->slots[sl].refs++;
@@ -1526,7 +1535,13 @@ extern "C" tm_status tm_batch_finish(tm_ctx *c, uint64_t ticket, tm_batch_result
     if (k < 0) return fail(TM_ERR_NOT_FOUND, "tm_batch_finish: unknown ticket %llu", (unsigned long long)ticket);
     tm_ctx::AsyncBatch &a = c->async[k];
     BatchBuf &B = a.B;
+    const double t0 = tm_now();
+    c->t_counts = 0;
     tm_status st = fetch_results(c, B, res, a.s);
+    const double t1 = tm_now(), tc = c->t_counts > 0 ? c->t_counts : t1;
+    c->host_us[0] = c->host_us[1] = 0.0;
+    c->host_us[2] = 1e6 * (tc - t0);
+    c->host_us[3] = 1e6 * (t1 - tc);
     if (st) {
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(a.s);

@@ -113,6 +113,83 @@ struct BatchBuf {
 
 }  // namespace tmap
 
+namespace tmap {
+// Keyframe id -> store slot: open addressing with linear probing (the store's hottest host
+// lookup: one per pair and step of every batch).  The subset of std::unordered_map's
+// interface the library uses: find / end / count / erase / operator[] / size.
+class IdMap {
+  public:
+    struct Entry {
+        uint64_t first;
+        int second;
+        uint8_t state;  // 0 empty, 1 full, 2 erased
+    };
+    using iterator = Entry *;
+    IdMap() { rehash(64); }
+    iterator end() const { return nullptr; }
+    size_t size() const { return n_; }
+    iterator find(uint64_t k) const {
+        size_t i = hash(k) & mask_;
+        for (;;) {
+            Entry &e = tab_[i];
+            if (e.state == 0) return nullptr;
+            if (e.state == 1 && e.first == k) return &e;
+            i = (i + 1) & mask_;
+        }
+    }
+    size_t count(uint64_t k) const { return find(k) ? 1 : 0; }
+    int &operator[](uint64_t k) {
+        if (Entry *e = find(k)) return e->second;
+        if (2 * (used_ + 1) > tab_.size()) rehash(2 * n_ + 2 > tab_.size() / 2 ? 2 * tab_.size() : tab_.size());
+        size_t i = hash(k) & mask_;
+        while (tab_[i].state == 1) i = (i + 1) & mask_;
+        if (tab_[i].state == 0) ++used_;
+        tab_[i] = Entry{k, 0, 1};
+        ++n_;
+        return tab_[i].second;
+    }
+    void erase(iterator it) {
+        if (!it || it->state != 1) return;
+        it->state = 2;
+        --n_;
+    }
+    size_t erase(uint64_t k) {
+        iterator it = find(k);
+        if (!it) return 0;
+        erase(it);
+        return 1;
+    }
+
+  private:
+    static size_t hash(uint64_t k) {  // splitmix64 finaliser
+        k ^= k >> 30;
+        k *= 0xbf58476d1ce4e5b9ull;
+        k ^= k >> 27;
+        k *= 0x94d049bb133111ebull;
+        k ^= k >> 31;
+        return (size_t)k;
+    }
+    // table of `cap` entries (a power of two) holding the live entries; erased ones are dropped
+    void rehash(size_t cap) {
+        std::vector<Entry> old;
+        old.swap(tab_);
+        tab_.assign(cap, Entry{0, 0, 0});
+        mask_ = cap - 1;
+        n_ = used_ = 0;
+        for (const Entry &e : old)
+            if (e.state == 1) {
+                size_t i = hash(e.first) & mask_;
+                while (tab_[i].state != 0) i = (i + 1) & mask_;
+                tab_[i] = e;
+                ++n_;
+                ++used_;
+            }
+    }
+    mutable std::vector<Entry> tab_;  // (find hands out pointers to entries)
+    size_t mask_ = 0, n_ = 0, used_ = 0;  // used_: full and erased entries (probe length)
+};
+}  // namespace tmap
+
 struct tm_ctx {
     int device = 0;
     tm_camera cam{};
@@ -123,7 +200,7 @@ struct tm_ctx {
     size_t max_smem = 0;  // opt-in shared memory per block
     tmap::CamConst camc{};
     std::mutex mu;
-    std::unordered_map<uint64_t, int> ids;
+    tmap::IdMap ids;
     std::vector<tmap::Slot> slots;
     std::vector<int> free_slots;
     std::vector<void *> chunks;

@@ -380,11 +380,11 @@ def test_packed_new_keyframes(tm, small_batch, kind):
 
 
 def test_async_batches(tm, small_batch):
-    """tm_batch_begin / tm_batch_finish: two batches in flight at once, the second using as
-    neighbour a keyframe that the first stores; finished in reverse order, each equal to the
-    oracle.  A third begin is refused while two are in flight, the keyframes they use cannot be
-    removed, an unknown ticket is refused, and a pipelined loop (begin k + 1, then finish k)
-    gives the oracle's results at every step."""
+    """tm_batch_begin / tm_batch_finish: batches in flight at once, the second using as
+    neighbour a keyframe that the first stores; finished out of order, each equal to the
+    oracle.  A begin beyond TM_BATCH_INFLIGHT is refused, the keyframes in-flight batches use
+    cannot be removed, an unknown ticket is refused, and a pipelined loop (begin k + 1, then
+    finish k) gives the oracle's results at every step."""
     from paper_2511_02036_gb300 import _lib as L
     w = small_batch
     st = w["steps"]
@@ -395,9 +395,15 @@ def test_async_batches(tm, small_batch):
         s0, s1 = steps_of(dict(w, steps=st[:1])), steps_of(dict(w, steps=st[1:2]))
         t0 = ctx.batch_begin(s0, new=([st[0]["q"], nb1], [w["frames"][st[0]["q"]], w["frames"][nb1]]))
         t1 = ctx.batch_begin(s1, new=([st[1]["q"]], [w["frames"][st[1]["q"]]]))
+        # fill the remaining slots with searches of already stored keyframes, then one more
+        extra = [ctx.batch_begin(steps_of(dict(w, steps=st[1:2])), sp=tm.SearchParams())
+                 for _ in range(L.TM_BATCH_INFLIGHT - 2)]
         with pytest.raises(tm.TMError) as e:
             ctx.batch_begin(steps_of(dict(w, steps=st[2:3])))
         assert e.value.status == tm.TM_ERR_BUSY
+        exp1 = oracle_results(dict(w, steps=st[1:2]))
+        for t in extra:
+            assert_same(ctx.batch_finish(t), exp1)
         with pytest.raises(tm.TMError) as e:
             ctx.remove_keyframe(st[1]["nbrs"][1])
         assert e.value.status == tm.TM_ERR_BUSY
@@ -420,7 +426,7 @@ def test_async_batches(tm, small_batch):
         got.append(ctx.batch_finish(prev))
         for res, s in zip(got, rest):
             assert_same(res, oracle_results(dict(w, steps=[s])))
-        assert L.TM_BATCH_INFLIGHT == 2
+        assert L.TM_BATCH_INFLIGHT == 4
 
 
 def forward_steps(w, skip=True):
