@@ -530,6 +530,9 @@ typedef struct {
                                      copied; n = 0 for none (its skip array is not read)     */
     const uint8_t *fwd_skip;      /* [n_nbrs][fwd_mps.n] or NULL: 1 = that neighbour already
                                      observes the point (not fused into it); copied          */
+    size_t nbr_free_bytes;        /* length of nbr_free (the neighbours' keypoints), or 0: the
+                                     server looks the neighbours' sizes up (under the context's
+                                     lock, which a batch being launched holds)                */
 } tm_request;
 
 typedef struct {

@@ -1029,6 +1029,8 @@ class Server:
             nbr_free = np.concatenate([np.asarray(m, np.uint8) for m in nbr_free]) if len(nbr_free) else None
         nf = _host(nbr_free, np.uint8)
         r.q_free, r.nbr_free = _ptr(qf), _ptr(nf)
+        if nf is not None:
+            r.nbr_free_bytes = int(nf.numel()) if hasattr(nf, "numel") else int(nf.size)
         r.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
         r.fwd_mps = mappoint_view(fwd_mps if fwd_mps is not None and fwd_mps["n"] else None, keep)
         if fwd_skip is not None and r.fwd_mps.n:

@@ -126,7 +126,7 @@ class tm_fuse_apply_stats(ctypes.Structure):
 class tm_request(ctypes.Structure):
     _fields_ = [("kf_id", c_u64), ("kf", tm_keyframe_view), ("nbr_ids", c_p), ("n_nbrs", c_i32),
                 ("q_free", c_p), ("nbr_free", c_p), ("mps", tm_mappoint_view),
-                ("fwd_mps", tm_mappoint_view), ("fwd_skip", c_p)]
+                ("fwd_mps", tm_mappoint_view), ("fwd_skip", c_p), ("nbr_free_bytes", c_sz)]
 
 
 class tm_request_info(ctypes.Structure):

@@ -78,6 +78,9 @@ struct tm_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Req *> pending;
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+    // keyframe id -> (keypoints, requests holding it) of the requests not yet taken: a
+    // neighbour that is not stored yet may be the keyframe of an earlier request
+    std::unordered_map<uint64_t, std::pair<int, int>> req_kf;
     std::vector<Flight> ring;
     std::deque<uint64_t> history;  // keyframes stored by this server, oldest first
     bool stopping = false;
@@ -199,6 +202,13 @@ bool admit(tm_server *S, Flight &F) {
         std::vector<int> slots;
         std::unordered_map<uint64_t, int> batch_ids;
         for (Req *q : take) {
+            // once a request waits for store memory, the later ones wait too (arrival order):
+            // they are checked when they are taken, so that a neighbour that is a waiting
+            // request's keyframe is not taken for a missing one
+            if (!deferred.empty()) {
+                deferred.push_back(q);
+                continue;
+            }
             tm_keyframe_view v{};
             v.n = q->n;
             v.desc = q->desc.data();
@@ -209,16 +219,22 @@ bool admit(tm_server *S, Flight &F) {
             memcpy(v.Tcw, q->Tcw, sizeof v.Tcw);
             tm_status st = validate_view(c, v);
             if (!st && (c->ids.count(q->kf_id) || batch_ids.count(q->kf_id))) st = TM_ERR_EXISTS;
+            size_t nbr_kp = 0;  // the neighbours' keypoints: the length nbr_free must have
             if (!st)
-                for (uint64_t nb : q->nbrs)
-                    if (!c->ids.count(nb) && !batch_ids.count(nb)) { st = TM_ERR_NOT_FOUND; break; }
+                for (uint64_t nb : q->nbrs) {
+                    auto it = c->ids.find(nb);
+                    if (it != c->ids.end()) {
+                        nbr_kp += (size_t)c->slots[it->second].n;
+                    } else {
+                        auto bt = batch_ids.find(nb);
+                        if (bt == batch_ids.end()) { st = TM_ERR_NOT_FOUND; break; }
+                        nbr_kp += (size_t)views[(size_t)bt->second].n;
+                    }
+                }
+            if (!st && !q->nbr_free.empty() && q->nbr_free.size() != nbr_kp) st = TM_ERR_INVALID_ARG;
             if (st) {
                 q->status = st;
                 failed.push_back(q);
-                continue;
-            }
-            if (!deferred.empty()) {  // keep arrival order once something had to wait
-                deferred.push_back(q);
                 continue;
             }
             // admission by memory: a store slot for the new keyframe
@@ -480,9 +496,11 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
     q->node.assign(v.node, v.node + n);
     q->nbrs.assign(r->nbr_ids, r->nbr_ids + r->n_nbrs);
     if (r->q_free) q->q_free.assign(r->q_free, r->q_free + n);
-    if (r->nbr_free) {
-        // neighbour sizes are known only once they are stored: take what the caller says
-        // is the concatenation length (sum of neighbour keypoint counts)
+    if (r->nbr_free && r->nbr_free_bytes) {
+        q->nbr_free.assign(r->nbr_free, r->nbr_free + r->nbr_free_bytes);
+    } else if (r->nbr_free) {
+        // the concatenation length (sum of the neighbours' keypoint counts) from their sizes:
+        // stored keyframes, or the keyframes of earlier requests
         size_t tot = 0;
         {
             std::lock_guard<std::mutex> lk(S->ctx->mu);
@@ -491,10 +509,9 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
                 if (it != S->ctx->ids.end()) tot += (size_t)S->ctx->slots[it->second].n;
                 else {
                     std::lock_guard<std::mutex> lk2(S->mu);
-                    bool found = false;
-                    for (auto &kv : S->reqs)
-                        if (kv.second->kf_id == nb) { tot += (size_t)kv.second->n; found = true; break; }
-                    if (!found) return fail(TM_ERR_NOT_FOUND, "neighbour %llu unknown", (unsigned long long)nb);
+                    auto rk = S->req_kf.find(nb);
+                    if (rk == S->req_kf.end()) return fail(TM_ERR_NOT_FOUND, "neighbour %llu unknown", (unsigned long long)nb);
+                    tot += (size_t)rk->second.first;
                 }
             }
         }
@@ -527,6 +544,11 @@ extern "C" tm_status tm_server_submit(tm_server *S, const tm_request *r, uint64_
     q->t_submit = tm_now();
     *ticket = q->ticket;
     S->pending.push_back(q.get());
+    {
+        auto &e = S->req_kf[q->kf_id];
+        e.first = q->n;
+        ++e.second;
+    }
     S->reqs[q->ticket] = std::move(q);
     S->stats.submitted++;
     S->stats.peak_pending = std::max(S->stats.peak_pending, (int32_t)S->pending.size());
@@ -579,9 +601,14 @@ extern "C" tm_status tm_server_take_ex(tm_server *S, uint64_t ticket, tm_match *
     if (it == S->reqs.end()) return fail(TM_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
     Req *q = it->second.get();
     if (!q->done) return fail(TM_ERR_BUSY, "request %llu not done", (unsigned long long)ticket);
+    auto forget = [&]() {
+        auto rk = S->req_kf.find(q->kf_id);
+        if (rk != S->req_kf.end() && --rk->second.second <= 0) S->req_kf.erase(rk);
+        S->reqs.erase(it);
+    };
     if (q->status) {
         tm_status s = q->status;
-        S->reqs.erase(it);
+        forget();
         return fail(s, "request failed with status %d", s);
     }
     if (matches && !q->matches.empty()) memcpy(matches, q->matches.data(), q->matches.size() * sizeof(tm_match));
@@ -592,7 +619,7 @@ extern "C" tm_status tm_server_take_ex(tm_server *S, uint64_t ticket, tm_match *
         memcpy(fwd_offsets, q->fwd_offsets.data(), q->fwd_offsets.size() * sizeof(int32_t));
     if (points && !q->points.empty()) memcpy(points, q->points.data(), q->points.size() * sizeof(float));
     if (point_ok && !q->point_ok.empty()) memcpy(point_ok, q->point_ok.data(), q->point_ok.size());
-    S->reqs.erase(it);
+    forget();
     return TM_OK;
 }
 

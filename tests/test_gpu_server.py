@@ -106,6 +106,18 @@ def test_request_errors(tm, stream):
             # the same keyframe id again -> EXISTS
             t1 = srv.submit(s0["q"], w["frames"][s0["q"]], [])
             assert srv.poll(t1, timeout=60.0)["status"] == tm.TM_ERR_EXISTS
+            # neighbour masks shorter than the neighbours' keypoints -> INVALID_ARG for that
+            # request alone; the next request (same neighbours, full masks) is served
+            s1 = w["steps"][1]
+            short = np.concatenate([np.asarray(m, np.uint8) for m in s1["nbr_free"]])[:-1]
+            t2 = srv.submit(s1["q"], w["frames"][s1["q"]], s1["nbrs"], s1["q_free"], short, s1["mps"])
+            assert srv.poll(t2, timeout=60.0)["status"] == tm.TM_ERR_INVALID_ARG
+            t3 = srv.submit(s1["q"], w["frames"][s1["q"]], s1["nbrs"], s1["q_free"], s1["nbr_free"], s1["mps"])
+            pairs, fuse, info = srv.take(t3)
+            assert info["status"] == 0
+            exp, _ = O.search_step(w["cam"], w["frames"], s1)
+            for g, e in zip(pairs, exp):
+                np.testing.assert_array_equal(g, e)
 
 
 @pytest.mark.parametrize("batch,skip", [(8, True), (1, False)])
