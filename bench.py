@@ -794,6 +794,7 @@ def run_serving(tm, n_kf, device, rate20_kf):
         rng = np.random.default_rng(7)
         arr = np.cumsum(rng.exponential(1.0 / rate, n)) if rate else np.zeros(n)
         with tm.Context(w["cam"], max_kp=2048, budget=slots * slot, device=device) as ctx:
+            ctx.reserve(min(slots, n + 64))  # the store's slots allocated before serving starts
             with ctx.server(**cfg) as srv:
                 t0 = time.perf_counter()
                 t0_lib = tm.tm_now()

@@ -164,6 +164,11 @@ tm_status tm_store_get_stats(tm_ctx *ctx, tm_store_stats *out);
  * stored, TM_ERR_NO_MEMORY if no slot fits the budget (nothing is stored then). */
 tm_status tm_store_add_keyframe(tm_ctx *ctx, uint64_t kf_id, const tm_keyframe_view *kf,
                                 void *stream);
+/* Makes sure at least n_slots keyframe slots are allocated and free (one allocation for the
+ * missing ones, within the memory budget), so that later additions -- a server's admissions
+ * among them -- allocate no device memory.  TM_ERR_NO_MEMORY if the budget or the free
+ * memory cannot hold them (the slots that could be allocated stay reserved). */
+tm_status tm_store_reserve(tm_ctx *ctx, int32_t n_slots);
 /* The same for n keyframes in one transfer and one launch; all or nothing. */
 tm_status tm_store_add_keyframes(tm_ctx *ctx, int32_t n, const uint64_t *kf_ids,
                                  const tm_keyframe_view *kfs, void *stream);

@@ -736,6 +736,10 @@ class Context:
         for i in ids.tolist():
             self.sizes.pop(i, None)
 
+    def reserve(self, n_slots):
+        """Allocates keyframe slots ahead (tm_store_reserve): later additions allocate nothing."""
+        check(tm_store_reserve(self.handle, int(n_slots)))  # noqa: F821
+
     def keyframe_size(self, kf_id):
         n = ctypes.c_int32()
         check(tm_store_keyframe_size(self.handle, int(kf_id), ctypes.byref(n)))  # noqa: F821

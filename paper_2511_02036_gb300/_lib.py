@@ -150,6 +150,7 @@ SIGNATURES = {
     "tm_triangulation_params_default": (None, [P(tm_triangulation_params)]),
     "tm_ctx_create": (c_i32, [c_i32, P(tm_camera), c_i32, c_sz, P(c_p)]),
     "tm_ctx_destroy": (c_i32, [c_p]),
+    "tm_store_reserve": (c_i32, [c_p, c_i32]),
     "tm_store_get_stats": (c_i32, [c_p, P(tm_store_stats)]),
     "tm_store_add_keyframe": (c_i32, [c_p, c_u64, P(tm_keyframe_view), c_p]),
     "tm_store_add_keyframes": (c_i32, [c_p, c_i32, c_p, P(tm_keyframe_view), c_p]),

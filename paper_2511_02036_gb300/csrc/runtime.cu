@@ -206,8 +206,10 @@ tm_status tmap::alloc_slots_locked(tm_ctx *c, int n, std::vector<int> &got) {
         size_t max_slots = c->budget ? c->budget / c->slot_bytes : (size_t)-1;
         size_t have = c->slots.size();
         if (have >= max_slots) break;
-        size_t want = std::min<size_t>(32, max_slots - have);
-        want = std::max<size_t>(want, (size_t)(n - (int)got.size()) < want ? (size_t)(n - (int)got.size()) : want);
+        // chunks grow with the store (32, then as many as are held, at most 1024 slots), so
+        // that a growing store allocates device memory a few times, not every 32 keyframes
+        size_t want = std::min<size_t>(std::min<size_t>(std::max<size_t>(32, have), 1024), max_slots - have);
+        want = std::max<size_t>(want, std::min<size_t>((size_t)(n - (int)got.size()), max_slots - have));
         size_t bytes = want * c->slot_bytes;
         if (!c->budget) {
             size_t fr = 0, tot = 0;
@@ -506,6 +508,38 @@ extern "C" tm_status tm_store_add_keyframes(tm_ctx *c, int32_t n, const uint64_t
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "ingest");
     return TM_OK;
+}
+
+extern "C" tm_status tm_store_reserve(tm_ctx *c, int32_t n_slots) {
+    if (!c || n_slots < 0) return fail(TM_ERR_INVALID_ARG, "tm_store_reserve: bad arguments");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    const size_t free_now = c->free_slots.size();
+    if ((size_t)n_slots <= free_now) return TM_OK;
+    // allocate the missing slots in one chunk (within the budget), keeping them free
+    const size_t max_slots = c->budget ? c->budget / c->slot_bytes : (size_t)-1;
+    const size_t want = std::min<size_t>((size_t)n_slots - free_now, max_slots - std::min(max_slots, c->slots.size()));
+    if (want == 0) return fail(TM_ERR_NO_MEMORY, "tm_store_reserve: budget holds %zu slots", c->slots.size());
+    if (!c->budget) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < want * c->slot_bytes + (size_t(1) << 30))
+            return fail(TM_ERR_NO_MEMORY, "tm_store_reserve: not enough free device memory");
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, want * c->slot_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TM_ERR_NO_MEMORY, "tm_store_reserve: allocation of %zu slots failed", want);
+    }
+    c->chunks.push_back(p);
+    for (size_t k = 0; k < want; ++k) {
+        Slot sl;
+        sl.ptr = static_cast<unsigned char *>(p) + k * c->slot_bytes;
+        c->slots.push_back(sl);
+        c->free_slots.push_back((int)c->slots.size() - 1);
+    }
+    std::sort(c->free_slots.begin(), c->free_slots.end(), std::greater<int>());
+    return (size_t)n_slots <= c->free_slots.size() ? TM_OK
+                                                   : fail(TM_ERR_NO_MEMORY, "tm_store_reserve: budget reached");
 }
 
 extern "C" tm_status tm_store_add_keyframe(tm_ctx *c, uint64_t id, const tm_keyframe_view *kf,

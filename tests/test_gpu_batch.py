@@ -214,6 +214,34 @@ def test_memory_budget_admission(tm):
         assert ctx.stats()["slots_used"] == 3
 
 
+def test_store_reserve(tm):
+    """tm_store_reserve allocates slots ahead within the budget (one allocation); later
+    additions take them without growing the store; beyond the budget it reports NO_MEMORY and
+    keeps what fits."""
+    cam = W.CAM_CFG0
+    rng = np.random.default_rng(2)
+    with tm.Context(cam, max_kp=512) as probe:
+        slot = probe.stats()["slot_bytes"]
+    with tm.Context(cam, max_kp=512, budget=10 * slot) as ctx:
+        ctx.reserve(8)
+        st = ctx.stats()
+        assert st["bytes_reserved"] == 8 * slot and st["slots_used"] == 0
+        ctx.reserve(4)  # already free: nothing allocated
+        assert ctx.stats()["bytes_reserved"] == 8 * slot
+        for k in range(8):
+            ctx.add_keyframe(k, W.random_keyframe(rng, 100, cam))
+        assert ctx.stats()["bytes_reserved"] == 8 * slot
+        with pytest.raises(tm.TMError) as e:
+            ctx.reserve(5)
+        assert e.value.status == tm.TM_ERR_NO_MEMORY
+        assert ctx.stats()["bytes_reserved"] == 10 * slot
+        for k in range(8, 10):
+            ctx.add_keyframe(k, W.random_keyframe(rng, 100, cam))
+        with pytest.raises(tm.TMError) as e:
+            ctx.add_keyframe(10, W.random_keyframe(rng, 100, cam))
+        assert e.value.status == tm.TM_ERR_NO_MEMORY
+
+
 @pytest.fixture(scope="module")
 def cfg2():
     return W.make_cfg2()
