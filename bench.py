@@ -332,6 +332,7 @@ def run_mine(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     plan = ctx.plan(off_steps, masks=d_masks, mps=d_mps, new=(new_ids, d_new))
     info = plan.info()
+    tuning = plan.tuning()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -480,13 +481,16 @@ def run_mine(args, rank, world, local_rank):
                      Tcw=np.stack([np.asarray(f["Tcw"], np.float64).reshape(12) for f in fr]))
         # bytes copied in per step: masks, map-point arrays, the new keyframes' arrays
         # (desc 32 + xy 8 + angle 4 + level 1 + node 4 = 49 B per keypoint), the work list (the
-        # library's 128-byte work records: every item, and the search items once more in launch
-        # order) and the new keyframes' ingest and gather records (112 + 48 B each)
+        # library's 128-byte work records: every item, and the search's launch entries once
+        # more), the new keyframes' ingest records (112 B each) and the gather records of their
+        # packed arrays (48 B per 1024 keypoints)
         n_pairs = sum(len(s["nbrs"]) for s in steps)
-        n_items = n_pairs + sum((s["mps"]["n"] + 255) // 256 for s in steps)
+        n_items = n_pairs + sum((s["mps"]["n"] + 511) // 512 for s in steps)
+        n_units = tuning["search_units"]  # launch entries of the search (split pairs twice)
         h2d = (int(masks.nbytes) + sum(int(v.nbytes) for v in mps.values() if isinstance(v, np.ndarray))
                + sum(w["frames"][i]["n"] for i in new_ids) * 49
-               + (n_items + n_pairs) * 128 + len(new_ids) * (112 + 48))
+               + (n_items + n_units) * 128 + len(new_ids) * 112
+               + 48 * ((sum(w["frames"][i]["n"] for i in new_ids) + 1023) // 1024))
         # out: item offsets, comparison totals (3 x 8 B) and the status word, the results
         d2h = 4 * (n_items + 1) + 24 + 4 + OUT_BYTES * (len(res.matches) + len(res.fuse))
 

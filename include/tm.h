@@ -440,6 +440,7 @@ typedef struct {
     int32_t tuned;            /* 1: chosen by the tuner (measured or cached); 0: defaults        */
     int32_t per_lane;         /* 1: each lane walks its own queries' candidates (per-lane form);
                                  0: a warp's candidates spread over its lanes in rounds          */
+    int32_t search_units;     /* search launch entries: pairs, a split pair counted twice        */
 } tm_plan_tuning;
 tm_status tm_plan_get_tuning(tm_plan *plan, tm_plan_tuning *out);
 
@@ -477,6 +478,10 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *                           walking its own two queries' candidates (3); 0 = tuned (default)
  *   TM_DEBUG_PERSISTENT     1: resident search CTAs take pairs from a work counter; 0: one CTA
  *                           per pair; -1 = tuned (default)
+ *   TM_DEBUG_SPLIT_MIN      in batches of fewer pairs than SMs, pairs with at least this many
+ *                           query keypoints are searched by two CTAs, each half of the queries,
+ *                           the last to finish finalizing the pair (default 768; 0 = never; a
+ *                           negative value -n splits pairs of n or more in any batch)
  * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, value out of range). */
 #define TM_DEBUG_WAIT_LIMIT 1
 #define TM_DEBUG_STARVE_WAITS 2
@@ -485,6 +490,7 @@ tm_status tm_plan_destroy(tm_plan *plan);
 #define TM_DEBUG_BRANCH_PRIORITY 5
 #define TM_DEBUG_QUERIES_PER_LANE 6
 #define TM_DEBUG_PERSISTENT 7
+#define TM_DEBUG_SPLIT_MIN 8
 tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
 /* Bounds-checking builds (compiled with -DTM_DEBUG_BOUNDS; the normal build sets *enabled = 0
  * and *site = 0): every index the kernels take from data (bucket tables, grid lists, match and

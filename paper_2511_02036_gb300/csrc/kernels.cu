@@ -928,10 +928,12 @@ __device__ __forceinline__ int eligible_before(const SearchSmem &M, int j) {
 // pair's accepted list (global, `acc`) and claims its target (shared atomicMin of
 // (distance << 16 | caller)).  kEpi, kEprej, kDense: the epipolar gate, the epipole
 // rejection and dense node blocks are on (fixed per launch).
+// wing: the pair's per-target winners in global memory when the pair is split over two CTAs
+// (else null: in shared memory); the accepted queries are listed from acc[c + abase].
 template <int Q, bool kEpi, bool kEprej, bool kDense>
 __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
                                              const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
-                                             uint32_t &cmp, uint32_t &dfail) {
+                                             uint32_t &cmp, uint32_t &dfail, uint32_t *wing, uint32_t abase) {
     const int lane = (int)(threadIdx.x & 31u);
     const int nT = (int)w.nt, nQ = (int)w.nq;
     uint32_t key[Q];
@@ -1072,9 +1074,12 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
                 const uint32_t io = q.io[h];
                 const uint32_t bin = A.sp.rot_filter ? (uint32_t)rot_bin(ldg(w.qangle + p), ldg(T.angle + j), A.sp.rot_mode) : 0u;
                 const uint32_t e = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                A.acc[w.c + (uint32_t)guard((int)e, nQ, 7)] =
+                A.acc[w.c + (uint32_t)guard((int)(abase + e), nQ, 7)] =
                     make_uint2(io | (j << 16), (uint32_t)ldg(T.orig + j) | (best << 16) | (bin << 25));
-                if (A.sp.resolve) red_s_min(M.win + 4 * j, (best << 16) | io);
+                if (A.sp.resolve) {
+                    if (wing) atomicMin(wing + j, (best << 16) | io);
+                    else red_s_min(M.win + 4 * j, (best << 16) | io);
+                }
             }
         }
     }
@@ -1092,7 +1097,7 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
 template <bool kEpi>
 __device__ __forceinline__ void search_group_lane(const BatchArgs &A, const WorkItem &w, const KfView &T,
                                                   const SearchSmem &M, uint32_t *nacc, int g, const QLoad<2> &q,
-                                                  uint32_t &cmp) {
+                                                  uint32_t &cmp, uint32_t *wing, uint32_t abase) {
     constexpr int Q = 2;
     const int lane = (int)(threadIdx.x & 31u);
     const int nT = (int)w.nt, nQ = (int)w.nq;
@@ -1199,9 +1204,12 @@ __device__ __forceinline__ void search_group_lane(const BatchArgs &A, const Work
                 const uint32_t io = q.io[h];
                 const uint32_t bin = A.sp.rot_filter ? (uint32_t)rot_bin(ldg(w.qangle + p), ldg(T.angle + j), A.sp.rot_mode) : 0u;
                 const uint32_t e = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                A.acc[w.c + (uint32_t)guard((int)e, nQ, 7)] =
+                A.acc[w.c + (uint32_t)guard((int)(abase + e), nQ, 7)] =
                     make_uint2(io | (j << 16), (uint32_t)ldg(T.orig + j) | (best << 16) | (bin << 25));
-                if (A.sp.resolve) red_s_min(M.win + 4 * j, (best << 16) | io);
+                if (A.sp.resolve) {
+                    if (wing) atomicMin(wing + j, (best << 16) | io);
+                    else red_s_min(M.win + 4 * j, (best << 16) | io);
+                }
             }
         }
     }
@@ -1608,7 +1616,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     __shared__ __align__(16) float thr[kLevels], thre[kLevels];
     __shared__ uint32_t qrec[kMaxT / 32][32 * QL], sbest[kMaxT / 32][32 * QL];  // per warp: its queries' states
     __shared__ uint32_t hist[32];
-    __shared__ uint32_t keep, scmp, sdfail, nacc;
+    __shared__ uint32_t keep, scmp, sdfail, nacc, s_last;
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ int ok_all;
     constexpr int nw = kMaxT / 32;
@@ -1627,6 +1635,12 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     const KfView T = KfView::at(w.t, A.L);
     const int nQ = (int)w.nq, nT = (int)w.nt;
     const int nwq = (nQ + 31) >> 5, nwt = (nT + 31) >> 5;  // bitmap words: queries, targets
+    // a split pair: this CTA takes part `part` of its query groups; the winners are global
+    const int parts = (int)(w.step >> 8) > 1 ? 2 : 1, part = parts > 1 ? (int)(w.step & 0xFFu) & 1 : 0;
+    const int ngroups = (nQ + 32 * QL - 1) / (32 * QL), gpp = (ngroups + parts - 1) / parts;
+    const int g0 = min(part * gpp, ngroups), g1 = min(g0 + gpp, ngroups);
+    uint32_t *wing = parts > 1 ? A.pwin + w.toff : nullptr;
+    const uint32_t abase = (uint32_t)(g0 * 32 * QL);
     if (tid == 0) {
         // the neighbour's node keys and bucket table (store), its eligibility words and eligible
         // positions and the pair's constants (prep kernel), all into shared memory
@@ -1662,10 +1676,11 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
         thre[tid] = fmul(fmul(A.sp.epipole_px, A.sp.epipole_px), sc);
     }
     if (tid >= 96 && tid < 128) hist[tid - 96] = 0u;
-    for (int j = tid; j < nT; j += kMaxT) win[j] = kNone;
+    if (parts == 1)
+        for (int j = tid; j < nT; j += kMaxT) win[j] = kNone;
     for (int k = tid; k < nwq; k += kMaxT) qbits[k] = 0u;
     QLoad<QL> cur = {};
-    if (wid * 32 * QL < nQ) cur = load_group<QL>(A, w, wid);  // the first group's loads overlap the setup
+    if (g0 + wid < g1) cur = load_group<QL>(A, w, g0 + wid);  // the first group's loads overlap the setup
     // the thread that initialized the barrier and issued the bulk copies awaits them; the CTA
     // barrier then publishes the copied data (and every other setup write) to all threads
     if (tid == 0) {
@@ -1677,7 +1692,15 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     if (!ok_all) {
         if (tid == 0) {
             A.counts[i] = 0u;
-            A.item_cmp[i] = kItemTimeout;
+            if (parts > 1) {
+                // the other part still counts this one in, and finds the pair failed
+                A.pacc[2 * i + part] = 0u;
+                atomicOr(A.item_cmp + i, kItemTimeout);
+                __threadfence();
+                atomicAdd(A.pdone + i, 1u);
+            } else {
+                A.item_cmp[i] = kItemTimeout;
+            }
         }
         return 1;
     }
@@ -1700,31 +1723,56 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     M.rec = smem_addr(&qrec[wid][0]);
     M.sb = smem_addr(&sbest[wid][0]);
     uint32_t cmp = 0, dfail = 0;
-    for (int g = wid; g * 32 * QL < nQ; g += nw) {
+    for (int g = g0 + wid; g < g1; g += nw) {
         QLoad<QL> nxt = {};
-        if ((g + nw) * 32 * QL < nQ) nxt = load_group<QL>(A, w, g + nw);
+        if (g + nw < g1) nxt = load_group<QL>(A, w, g + nw);
         if constexpr (kLane)
-            search_group_lane<kEpi>(A, w, T, M, &nacc, g, cur, cmp);
+            search_group_lane<kEpi>(A, w, T, M, &nacc, g, cur, cmp, wing, abase);
         else
-            search_group<QL, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail);
+            search_group<QL, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail, wing, abase);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
     if (kDense && __any_sync(kFull, dfail != 0u) && lane == 0) sdfail = 1u;
+    if (parts > 1) __threadfence();  // (uniform) this thread's list entries and winners, device-wide
     __syncthreads();
+    if (parts > 1) {
+        // publish this part (its accepted list, winners, comparisons), then count it in: the
+        // part that completes the count finalizes the pair (no CTA waits for another)
+        if (tid == 0) {
+            A.pacc[2 * i + part] = nacc;
+            atomicAdd(A.item_cmp + i, scmp);
+            if (sdfail) atomicOr(A.item_cmp + i, kItemTimeout);
+            __threadfence();
+            s_last = atomicAdd(A.pdone + i, 1u) == (uint32_t)(parts - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (!s_last) return 0;
+        __threadfence();
+    }
     // finalize over the accepted queries (their list, written by this CTA, is read back from
     // L2 once; a thread keeps its first two entries in registers)
-    const int na = (int)nacc;
+    // a split pair's lists: part 0's entries, then part 1's (read through L2: another CTA
+    // wrote them)
+    const int na0 = parts > 1 ? (int)__ldcg(A.pacc + 2 * i) : (int)nacc;
+    const int na = parts > 1 ? na0 + (int)__ldcg(A.pacc + 2 * i + 1) : na0;
+    const uint32_t abase1 = (uint32_t)(min(gpp, ngroups) * 32 * QL);
     const bool rot = A.sp.rot_filter != 0, res = A.sp.resolve != 0;
-    const uint2 v0 = tid < na ? A.acc[w.c + (uint32_t)tid] : make_uint2(0u, 0u);
-    const uint2 v1 = tid + kMaxT < na ? A.acc[w.c + (uint32_t)(tid + kMaxT)] : make_uint2(0u, 0u);
+    auto load_entry = [&](int e) -> uint2 {
+        if (parts == 1) return A.acc[w.c + (uint32_t)e];
+        const uint32_t o = e < na0 ? (uint32_t)e : abase1 + (uint32_t)(e - na0);
+        return __ldcg(A.acc + w.c + (uint32_t)guard((int)o, nQ, 20));
+    };
+    const uint2 v0 = tid < na ? load_entry(tid) : make_uint2(0u, 0u);
+    const uint2 v1 = tid + kMaxT < na ? load_entry(tid + kMaxT) : make_uint2(0u, 0u);
     auto entry = [&](int e) -> uint2 {
-        return e == tid ? v0 : (e == tid + kMaxT ? v1 : A.acc[w.c + (uint32_t)e]);
+        return e == tid ? v0 : (e == tid + kMaxT ? v1 : load_entry(e));
     };
     // a listed query is kept if it is its target's winner (io = caller index, j = target)
     auto winner = [&](const uint2 &v) -> bool {
         const uint32_t io = v.x & 0xFFFFu, j = (uint32_t)guard((int)(v.x >> 16), nT, 10);
-        return !res || win[j] == (((v.y >> 16) & 0x1FFu) << 16 | io);
+        const uint32_t wv = parts > 1 ? __ldcg(wing + j) : win[j];
+        return !res || wv == (((v.y >> 16) & 0x1FFu) << 16 | io);
     };
     if (rot)
         for (int e = tid; e < na; e += kMaxT) {
@@ -1777,7 +1825,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     }
     if (tid == 0) {
         A.counts[i] = qpre[nwq];
-        A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
+        if (parts == 1) A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
     }
     return 0;
 }
@@ -1796,7 +1844,7 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
         if (threadIdx.x == 0) s_slot = atomicAdd(A.work, 1u);
         __syncthreads();
         const uint32_t slot = s_slot;
-        if (slot >= A.n_search) return;
+        if (slot >= A.n_units) return;
         if (search_pair<Q, kEpi, kEprej, kDense>(A, slot, it & 1u, it == 0)) return;
     }
 }
@@ -1849,6 +1897,15 @@ __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
     const KfView T = KfView::at(w.t, A.L);
     const int nT = (int)w.nt, nwt = (nT + 31) >> 5;
     const int ew = wid - 1;  // eligibility warp index
+    if ((w.step >> 8) > 1) {
+        // a split pair: its global winners, its completion count and its comparison count
+        // start over at every run
+        for (int j = tid - 32; j < nT; j += kPrepThreads - 32) A.pwin[w.toff + (uint32_t)j] = kNone;
+        if (tid == 32) {
+            A.pdone[i] = 0u;
+            A.item_cmp[i] = 0u;
+        }
+    }
     uint2 *words = A.pwords + w.toff / 32u;
     uint16_t *epos = A.pepos + w.toff;
     const int per = (nwt + nw - 1) / nw, wb = min(ew * per, nwt), we = min(wb + per, nwt);
@@ -2542,7 +2599,7 @@ cudaError_t launch_search(const BatchArgs &a, int ctas, cudaStream_t s, int prio
     const size_t smem = search_smem_bytes(a.sn);
     cudaError_t e = cudaFuncSetAttribute(search_fn(a), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint32_t grid = a.persist ? (uint32_t)std::max(1, std::min(ctas, (int)a.n_search)) : a.n_search;
+    const uint32_t grid = a.persist ? (uint32_t)std::max(1, std::min(ctas, (int)a.n_units)) : a.n_units;
     return launch_prio(search_fn(a), dim3(grid), dim3(kSearchThreads), smem, s, prio, a);
 }
 

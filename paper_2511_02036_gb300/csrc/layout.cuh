@@ -297,6 +297,14 @@ struct BatchArgs {
     uint2 *pwords;                // per pair from toff / 32: eligibility words (bits, count before)
                                   //   and one closing word (0, eligible total)
     uint16_t *pepos;              // per pair from toff: the eligible positions in node order
+    // split pairs (a pair's query groups over two search CTAs; WorkItem::step = part | parts << 8
+    // for search items): the per-target winners of a split pair live in pwin from toff (the
+    // prep kernel resets them), each part's accepted count in pacc[2 idx + part], and the last
+    // part to finish (pdone[idx], counted by atomics) finalizes the pair
+    uint32_t *pwin;
+    uint32_t *pacc;
+    uint32_t *pdone;
+    uint32_t n_units;             // search launch entries (pairs, split pairs twice)
     uint32_t dsplit;              // dense kernel CTAs per search item
 };
 

@@ -614,7 +614,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok, &pwin, &pacc, &pdone})
         b->release();
     h_stage.release();
     h_out.release();
@@ -818,6 +818,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.item_nt.clear();
     size_t n_pairs_max = 0;
     for (int k = 0; k < n_steps; ++k) n_pairs_max += (size_t)std::max(0, steps[k].n_nbrs);
+    // split_min > 0: split in batches of fewer pairs than SMs; < 0: split whatever the batch
+    const bool split = c->split_min < 0 || (c->split_min > 0 && n_pairs_max < (size_t)c->num_sms);
     items.reserve(n_pairs_max + 64);
     B.item_nq.reserve(n_pairs_max);
     B.item_nt.reserve(n_pairs_max);
@@ -868,6 +870,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             w.qraw = qv.raw;
             B.nbr_new |= t_new;
             w.kind = kItemSearch;
+            // pairs with many queries are split over two search CTAs (part | parts << 8) when the
+            // batch's pairs are fewer than the SMs (a full batch fills the GPU unsplit, and
+            // there the split's second setup and global winners cost more than they gain)
+            w.step = (split && nq >= std::abs(c->split_min)) ? 2u << 8 : 1u << 8;
             w.out_off = pad;
             w.a = S.q_free_off >= 0 ? (uint32_t)S.q_free_off : kNone;
             w.b = S.nbr_free_off >= 0 ? (uint32_t)toff : kNone;
@@ -967,8 +973,15 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     std::vector<uint64_t> okey(B.n_search_items);
     for (size_t i = 0; i < okey.size(); ++i) okey[i] = ((uint64_t)(~items[i].cost) << 32) | (uint64_t)i;
     std::sort(okey.begin(), okey.end());
-    std::vector<uint32_t> order(B.n_search_items);
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)(okey[i] & 0xFFFFFFFFu);
+    // launch entries: a split pair twice (parts 0 and 1, adjacent)
+    std::vector<uint32_t> order;
+    order.reserve(2 * okey.size());
+    for (size_t i = 0; i < okey.size(); ++i) {
+        const uint32_t it = (uint32_t)(okey[i] & 0xFFFFFFFFu);
+        order.push_back(it);
+        if ((items[it].step >> 8) > 1) order.push_back(it | 0x80000000u);  // part 1
+    }
+    B.n_units = (uint32_t)order.size();
     // fusion stage: the largest target of the batch (new keyframes, and neighbours for
     // forward fusion)
     int fuse_n = 0;
@@ -977,9 +990,9 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     // device buffers
     const size_t ni = std::max<size_t>(1, items.size());
     const size_t nm = std::max<int>(1, mps.n);
-    const size_t nsi = std::max<size_t>(1, B.n_search_items);
+    const size_t nsi = std::max<size_t>(1, B.n_search_items), nun = std::max<size_t>(1, B.n_units);
     cudaError_t e;
-    if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nsi * sizeof(WorkItem))) ||
+    if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nun * sizeof(WorkItem))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
         (e = B.offsets.reserve((ni + 1) * 4)) ||
         (e = B.ncmp.reserve(24)) || (e = B.counters.reserve(16)) ||
@@ -994,6 +1007,8 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.acc.reserve(std::max<size_t>(1, dq) * 8)) ||
         (e = B.pconst.reserve(nsi * kPairConst * 4)) || (e = B.pwords.reserve(std::max<uint32_t>(64, tq) / 32 * 8)) ||
         (e = B.pepos.reserve(std::max<uint32_t>(64, tq) * 2)) ||
+        (e = B.pwin.reserve(std::max<uint32_t>(64, tq) * 4)) || (e = B.pacc.reserve(nsi * 8)) ||
+        (e = B.pdone.reserve(nsi * 4)) ||
         (tri && ((e = B.points.reserve(std::max<size_t>(1, B.search_pad) * 12)) ||
                  (e = B.point_ok.reserve(std::max<size_t>(1, B.search_pad))))))
         return cuda_fail(e, "batch buffers");
@@ -1011,7 +1026,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     unsigned char *h = static_cast<unsigned char *>(B.h_stage.p);
     if (!items.empty()) memcpy(h, items.data(), items.size() * sizeof(WorkItem));
     WorkItem *hs = reinterpret_cast<WorkItem *>(h + o_order);
-    for (size_t k = 0; k < order.size(); ++k) hs[k] = items[order[k]];
+    for (size_t k = 0; k < order.size(); ++k) {
+        hs[k] = items[order[k] & 0x7FFFFFFFu];
+        if (order[k] & 0x80000000u) hs[k].step |= 1u;  // part 1 of a split pair
+    }
     if (!items.empty() &&
         (e = cudaMemcpyAsync(B.items.p, h, order.empty() ? items.size() * sizeof(WorkItem) : stage, cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "work list upload");
@@ -1075,6 +1093,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.pconst = static_cast<float *>(B.pconst.p);
     A.pwords = static_cast<uint2 *>(B.pwords.p);
     A.pepos = static_cast<uint16_t *>(B.pepos.p);
+    A.pwin = static_cast<uint32_t *>(B.pwin.p);
+    A.pacc = static_cast<uint32_t *>(B.pacc.p);
+    A.pdone = static_cast<uint32_t *>(B.pdone.p);
+    A.n_units = B.n_units;
     A.work = static_cast<uint32_t *>(B.work.p);
     if ((e = cudaMemsetAsync(B.work.p, 0, 4, s))) return cuda_fail(e, "work counter");
     A.triangulate = tri ? 1 : 0;
@@ -1098,7 +1120,7 @@ std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, acc.p, pconst.p,
             pwords.p, pepos.p, work.p, points.p,
-            point_ok.p};
+            point_ok.p, pwin.p, pacc.p, pdone.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -1147,7 +1169,7 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     search_form(KA);
     const int per_sm = search_ctas_per_sm(KA);
     if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
-    B.ctas = KA.persist ? std::min((int)B.n_search_items, per_sm * c->num_sms) : (int)B.n_search_items;
+    B.ctas = KA.persist ? std::min((int)B.n_units, per_sm * c->num_sms) : (int)B.n_units;
     if (timed && !B.ev[0])
         for (cudaEvent_t &ev : B.ev)
             if ((e = cudaEventCreate(&ev))) return cuda_fail(e, "events");
@@ -1812,6 +1834,11 @@ extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
             if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: persistent must be -1, 0 or 1");
             c->force_persist = (int)value;
             return TM_OK;
+        case TM_DEBUG_SPLIT_MIN:
+            if (value < -TM_MAX_KP_LIMIT || value > TM_MAX_KP_LIMIT)
+                return fail(TM_ERR_INVALID_ARG, "tm_debug_set: split threshold out of range");
+            c->split_min = (int)value;
+            return TM_OK;
         case TM_DEBUG_L2_PREFETCH:
             if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: L2 prefetch must be -1, 0 or 1");
             c->force_prefetch = (int)value;
@@ -1963,6 +1990,7 @@ extern "C" tm_status tm_plan_get_tuning(tm_plan *P, tm_plan_tuning *out) {
     out->dense_split = out->dense_min > 0 ? (int)A.dsplit : 0;
     out->search_ctas = fused ? P->B.ctas : 0;
     out->tuned = P->B.tuned ? 1 : 0;
+    out->search_units = fused ? (int)P->B.n_units : 0;
     return TM_OK;
 }
 

@@ -69,7 +69,8 @@ struct Knobs {
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
         counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, work, points,
-        point_ok;
+        point_ok, pwin, pacc, pdone;
+    uint32_t n_units = 0;          // search launch entries (split pairs twice)
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -219,6 +220,9 @@ struct tm_ctx {
     int branch_prio = -1;                 // test hook: 0 search branch first, 1 store, 2 equal, -1 tuned
     int force_qpl = 0;                    // test hook: queries per lane of a search group (0 = tuned)
     int force_persist = -1;               // test hook: persistent search CTAs (-1 = tuned)
+    int split_min = 768;                  // pairs with at least this many queries take two search
+                                          // CTAs in batches of fewer pairs than SMs; < 0: in any
+                                          // batch (from -split_min); 0: none (TM_DEBUG_SPLIT_MIN)
     // host time of the phases of the last one-shot batch (tm_batch_last_host_times), in
     // microseconds: work list + uploads, launches, wait for the GPU and the result counts,
     // result downloads; t_counts marks the end of the third phase

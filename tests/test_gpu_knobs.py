@@ -91,7 +91,7 @@ def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
             assert t["queries_per_warp"] == 32 * min(qpl, 2) and t["per_lane"] == (qpl == 3)
             assert t["persistent"] == persist and t["l2_prefetch"] == prefetch
             if persist:
-                assert 1 <= t["search_ctas"] <= sum(len(s["nbrs"]) for s in w["steps"])
+                assert 1 <= t["search_ctas"] <= t["search_units"]
             for _ in range(2):  # the replay resets the persistent work counter
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -127,6 +127,47 @@ def test_variant_gates_ignore_persistent(tm, qpl):
             assert t["persistent"] == 0 and t["per_lane"] == 0
             plan.run()
             assert_same(plan.results(), exp)
+
+
+@pytest.mark.parametrize("split_min,qpl,persist", [(0, 2, 0), (-1, 2, 0), (-1, 1, 1), (-1, 3, 0), (-700, 2, 1), (-2048, 2, 0),
+                                                    (768, 2, 0)])
+def test_split_pairs_match_oracle(tm, batch, split_min, qpl, persist):
+    """Pairs split over two search CTAs (each half of the query groups, winners in global
+    memory, the last to finish finalizing): never (0), every pair (-1), most, none in range,
+    and the default rule (768: only in batches of fewer pairs than SMs); under each group form
+    and with the persistent search; the replay resets the split pairs' state."""
+    from paper_2511_02036_gb300 import _lib as L
+    w, exp = batch
+    n_pairs = sum(len(s["nbrs"]) for s in w["steps"])
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        ctx.debug_set(L.TM_DEBUG_SPLIT_MIN, split_min)
+        force(tm, ctx, qpl=qpl, persist=persist)
+        with ctx.plan(steps_of(w)) as plan:
+            t = plan.tuning()
+            # a positive threshold splits only in batches of fewer pairs than SMs (152 here)
+            active = split_min < 0 or (split_min > 0 and n_pairs < 152)
+            n_split = sum(1 for s in w["steps"] for _ in s["nbrs"]
+                          if active and w["frames"][s["q"]]["n"] >= abs(split_min))
+            assert t["search_units"] == n_pairs + n_split
+            for _ in range(3):
+                plan.run()
+                assert_same(plan.results(), exp)
+        assert_same(ctx.batch_run(steps_of(w)), exp)
+
+
+def test_split_pairs_dense_and_gates(tm):
+    """Split pairs with dense node blocks and with the epipole rejection (general instance)."""
+    from paper_2511_02036_gb300 import _lib as L
+    w = W.make_cfg3b(seed=3520, n_nbrs=4)
+    for sp in (tm.SearchParams(dense_min=64), tm.SearchParams(epipole_px=10.0), tm.SearchParams(resolve=False)):
+        exp = expected(w, sp)
+        with tm.Context(w["cam"], max_kp=2048) as ctx:
+            load_all(ctx, w)
+            ctx.debug_set(L.TM_DEBUG_SPLIT_MIN, -1)
+            with ctx.plan(steps_of(w), sp=sp) as plan:
+                plan.run()
+                assert_same(plan.results(), exp)
 
 
 def test_per_lane_form_without_epipolar_gate(tm, batch):
