@@ -396,7 +396,8 @@ tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
  * it, so a neighbour may be a keyframe that an earlier in-flight batch stores; their copies
  * and kernels otherwise overlap.  The caller's input arrays (host or device) must stay valid
  * and unchanged until tm_batch_finish returns; keyframes used by an in-flight batch cannot be
- * removed (TM_ERR_BUSY).  If tm_batch_finish reports an error, the batch's new keyframes are
+ * removed (TM_ERR_BUSY), and the keyframes it stores may be read only by later batches begun
+ * with tm_batch_begin until it is finished (other calls that name them: TM_ERR_BUSY).  If tm_batch_finish reports an error, the batch's new keyframes are
  * taken out of the store again, except those that a batch still in flight reads.  Tickets are
  * finished in any order; an unknown ticket is TM_ERR_NOT_FOUND. */
 #define TM_BATCH_INFLIGHT 4
@@ -481,7 +482,9 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *   TM_DEBUG_SPLIT_MIN      in batches of fewer pairs than SMs, pairs with at least this many
  *                           query keypoints are searched by two CTAs, each half of the queries,
  *                           the last to finish finalizing the pair (default 768; 0 = never; a
- *                           negative value -n splits pairs of n or more in any batch)
+ *                           negative value -n splits pairs of n or more in any batch); fused
+ *                           batches with the default gates only (no epipole rejection, no
+ *                           dense blocks), and not with the persistent search
  * Errors: TM_ERR_INVALID_ARG (null context, unknown setting, value out of range). */
 #define TM_DEBUG_WAIT_LIMIT 1
 #define TM_DEBUG_STARVE_WAITS 2

@@ -1606,7 +1606,7 @@ constexpr int kSearchThreads = 256;
 // The pair in slot `slot` of the launch order.  parity: phase of the CTA's bulk-copy barrier for
 // this pair (the CTA's pairs alternate); first: the CTA's first pair (initializes the barriers).
 // Returns 1 when a bounded wait ran out (the CTA stops).
-template <int Q, bool kEpi, bool kEprej, bool kDense>
+template <int Q, bool kEpi, bool kEprej, bool kDense, bool kSplit>
 __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, uint32_t parity, bool first) {
     constexpr int kMaxT = kSearchThreads;
     constexpr bool kLane = Q == 3;            // the per-lane form (two queries per lane)
@@ -1636,7 +1636,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     const int nQ = (int)w.nq, nT = (int)w.nt;
     const int nwq = (nQ + 31) >> 5, nwt = (nT + 31) >> 5;  // bitmap words: queries, targets
     // a split pair: this CTA takes part `part` of its query groups; the winners are global
-    const int parts = (int)(w.step >> 8) > 1 ? 2 : 1, part = parts > 1 ? (int)(w.step & 0xFFu) & 1 : 0;
+    const int parts = kSplit && (int)(w.step >> 8) > 1 ? 2 : 1, part = parts > 1 ? (int)(w.step & 0xFFu) & 1 : 0;
     const int ngroups = (nQ + 32 * QL - 1) / (32 * QL), gpp = (ngroups + parts - 1) / parts;
     const int g0 = min(part * gpp, ngroups), g1 = min(g0 + gpp, ngroups);
     uint32_t *wing = parts > 1 ? A.pwin + w.toff : nullptr;
@@ -1833,11 +1833,11 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
 // The search kernel: one CTA per pair (grid = pairs), or, kPersist, CTAs that stay resident
 // and take pairs in launch order (largest first) from the batch's work counter until none is
 // left (the copy kernel resets the counter for the next run).
-template <int Q, bool kEpi, bool kEprej, bool kDense, bool kPersist>
+template <int Q, bool kEpi, bool kEprej, bool kDense, bool kPersist, bool kSplit = false>
 __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(BatchArgs A) {
     __shared__ uint32_t s_slot;
     if (!kPersist) {
-        search_pair<Q, kEpi, kEprej, kDense>(A, blockIdx.x, 0u, true);
+        search_pair<Q, kEpi, kEprej, kDense, kSplit>(A, blockIdx.x, 0u, true);
         return;
     }
     for (uint32_t it = 0;; ++it) {
@@ -1845,7 +1845,7 @@ __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(
         __syncthreads();
         const uint32_t slot = s_slot;
         if (slot >= A.n_units) return;
-        if (search_pair<Q, kEpi, kEprej, kDense>(A, slot, it & 1u, it == 0)) return;
+        if (search_pair<Q, kEpi, kEprej, kDense, kSplit>(A, slot, it & 1u, it == 0)) return;
     }
 }
 
@@ -2558,6 +2558,11 @@ size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 static bool search_variants(const BatchArgs &a) { return !(a.sp.epipole_px > 0.0f) && !(a.sp.dense_min > 0); }
 static void (*search_fn(const BatchArgs &a))(BatchArgs) {
     const bool epi = a.sp.epipolar != 0, eprej = a.sp.epipole_px > 0.0f, dense = a.sp.dense_min > 0;
+    if (search_variants(a) && a.n_units > a.n_search) {  // split pairs: their own instances
+        if (a.qpl == 3) return epi ? search_kernel<3, true, false, false, false, true> : search_kernel<3, false, false, false, false, true>;
+        if (a.qpl == 1) return epi ? search_kernel<1, true, false, false, false, true> : search_kernel<1, false, false, false, false, true>;
+        return epi ? search_kernel<2, true, false, false, false, true> : search_kernel<2, false, false, false, false, true>;
+    }
     if (search_variants(a)) {
         if (a.qpl == 3 && !a.persist)
             return epi ? search_kernel<3, true, false, false, false> : search_kernel<3, false, false, false, false>;
@@ -2580,6 +2585,7 @@ void search_form(BatchArgs &a) {
         a.persist = 0;
     }
     if (a.qpl == 3) a.persist = 0;  // the per-lane form has no persistent instance
+    if (a.n_units > a.n_search) a.persist = 0;  // nor do split pairs
 }
 
 int search_ctas_per_sm(const BatchArgs &a) {

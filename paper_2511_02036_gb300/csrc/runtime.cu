@@ -818,8 +818,10 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     B.item_nt.clear();
     size_t n_pairs_max = 0;
     for (int k = 0; k < n_steps; ++k) n_pairs_max += (size_t)std::max(0, steps[k].n_nbrs);
-    // split_min > 0: split in batches of fewer pairs than SMs; < 0: split whatever the batch
-    const bool split = c->split_min < 0 || (c->split_min > 0 && n_pairs_max < (size_t)c->num_sms);
+    // split_min > 0: split in batches of fewer pairs than SMs; < 0: split whatever the batch.
+    // Split pairs run the default gates (the epipole rejection and dense blocks: never split).
+    const bool split = (c->split_min < 0 || (c->split_min > 0 && n_pairs_max < (size_t)c->num_sms)) &&
+                       !(sp.epipole_px > 0.0f) && sp.dense_min == 0 && sp.mode != TM_MODE_PER_PAIR;
     items.reserve(n_pairs_max + 64);
     B.item_nq.reserve(n_pairs_max);
     B.item_nt.reserve(n_pairs_max);
@@ -834,6 +836,11 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         auto it = c->ids.find(id);
         if (it == c->ids.end()) return fail(TM_ERR_NOT_FOUND, "keyframe %llu not stored", (unsigned long long)id);
         slot = it->second;
+        // a keyframe an asynchronous batch is still storing: only later asynchronous batches,
+        // which wait for that ingest, may read it before the batch is finished
+        if (c->slots[slot].pending && !B.allow_pending)
+            return fail(TM_ERR_BUSY, "keyframe %llu is being stored by a batch in flight (tm_batch_finish it first)",
+                        (unsigned long long)id);
         return TM_OK;
     };
     for (int k = 0; k < n_steps; ++k) {
@@ -1543,8 +1550,10 @@ extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_s
     // this batch's uploads (its own buffers) start at once; its kernels wait for the ingest of
     // the batch begun before it (whose keyframes may be neighbours here)
     B.early_fork = spd.mode != TM_MODE_PER_PAIR;
+    B.allow_pending = true;
     tm_status st = prepare_batch(c, B, steps, n_steps, in, spd, fpd, a.s);
     B.early_fork = false;
+    B.allow_pending = false;
     const bool prepared = !st;  // (its new keyframes are then stored: taken out on failure)
     if (!st && c->async_last >= 0 && c->async[c->async_last].ticket) {
         // both branches: the stream's (ingest, fusion, copy) and the search branch, which a
@@ -1575,6 +1584,10 @@ extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_s
     for (int sl : B.slots) c->slots[sl].refs++;
     a.new_ids.assign(in && in->n_new > 0 ? in->new_ids : nullptr, in && in->n_new > 0 ? in->new_ids + in->n_new : nullptr);
     a.ticket = c->async_next++;
+    for (uint64_t id : a.new_ids) {
+        auto it = c->ids.find(id);
+        if (it != c->ids.end()) c->slots[it->second].pending = a.ticket;
+    }
     c->async_last = k;
     *ticket = a.ticket;
     return TM_OK;
@@ -1603,6 +1616,10 @@ extern "C" tm_status tm_batch_finish(tm_ctx *c, uint64_t ticket, tm_batch_result
         cudaStreamSynchronize(a.s);
     }
     for (int sl : B.slots) c->slots[sl].refs--;
+    for (uint64_t id : a.new_ids) {
+        auto it = c->ids.find(id);
+        if (it != c->ids.end() && c->slots[it->second].pending == ticket) c->slots[it->second].pending = 0;
+    }
     if (st && B.n_new > 0) {
         for (uint64_t id : a.new_ids) {
             auto it = c->ids.find(id);

@@ -45,6 +45,7 @@ struct Slot {
     int n = 0;
     int refs = 0;
     uint64_t id = 0;
+    uint64_t pending = 0;  // ticket of the asynchronous batch still ingesting it, or 0
 };
 
 // Staging area of keyframe ingest (device copy of the caller-order arrays + pinned mirror).
@@ -102,6 +103,8 @@ struct BatchBuf {
     cudaStream_t paux = nullptr;         // search branch (beside the ingest)
     cudaEvent_t pfork = nullptr;         // start of the search branch
     cudaEvent_t ingest_done = nullptr;   // if set: recorded after the batch's ingest (async batches)
+    bool allow_pending = false;          // may use keyframes that batches in flight still ingest
+                                         // (an asynchronous batch, ordered after them)
     // one-shot batches (early_fork): the search branch forks right after the work list and the
     // masks are uploaded, and the map points are copied on mcopy, which the fusion kernel
     // awaits (mready); forked / mp_async say that prepare_batch did so for the next enqueue

@@ -435,6 +435,14 @@ def test_async_batches(tm, small_batch):
         with pytest.raises(tm.TMError) as e:
             ctx.remove_keyframe(st[1]["nbrs"][1])
         assert e.value.status == tm.TM_ERR_BUSY
+        # keyframes that batches in flight are still storing: only later asynchronous batches
+        # (ordered after their ingest) may read them; other calls are refused until finished
+        with pytest.raises(tm.TMError) as e:
+            ctx.batch_run(s1)
+        assert e.value.status == tm.TM_ERR_BUSY
+        with pytest.raises(tm.TMError) as e:
+            ctx.search(st[1]["q"], st[1]["nbrs"])
+        assert e.value.status == tm.TM_ERR_BUSY
         r1 = ctx.batch_finish(t1)
         r0 = ctx.batch_finish(t0)
         for res, part in ((r0, st[:1]), (r1, st[1:2])):

@@ -82,9 +82,11 @@ def force(tm, ctx, qpl=None, persist=None, prefetch=None, bprio=None):
 
 @pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))) + [(3, 0, 0), (3, 0, 1)])
 def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
+    from paper_2511_02036_gb300 import _lib as L
     w, exp = batch
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         load_all(ctx, w)
+        ctx.debug_set(L.TM_DEBUG_SPLIT_MIN, 0)  # (split pairs have no persistent instance)
         force(tm, ctx, qpl=qpl, persist=persist, prefetch=prefetch)
         with ctx.plan(steps_of(w)) as plan:
             t = plan.tuning()
@@ -135,7 +137,8 @@ def test_split_pairs_match_oracle(tm, batch, split_min, qpl, persist):
     """Pairs split over two search CTAs (each half of the query groups, winners in global
     memory, the last to finish finalizing): never (0), every pair (-1), most, none in range,
     and the default rule (768: only in batches of fewer pairs than SMs); under each group form
-    and with the persistent search; the replay resets the split pairs' state."""
+    (a persistent request is set aside when pairs are split); the replay resets the split
+    pairs' state."""
     from paper_2511_02036_gb300 import _lib as L
     w, exp = batch
     n_pairs = sum(len(s["nbrs"]) for s in w["steps"])
@@ -157,7 +160,8 @@ def test_split_pairs_match_oracle(tm, batch, split_min, qpl, persist):
 
 
 def test_split_pairs_dense_and_gates(tm):
-    """Split pairs with dense node blocks and with the epipole rejection (general instance)."""
+    """Batches with dense node blocks or the epipole rejection are not split (their instances
+    have no split form) and still equal the oracle; without resolve a split batch does."""
     from paper_2511_02036_gb300 import _lib as L
     w = W.make_cfg3b(seed=3520, n_nbrs=4)
     for sp in (tm.SearchParams(dense_min=64), tm.SearchParams(epipole_px=10.0), tm.SearchParams(resolve=False)):
