@@ -523,6 +523,9 @@ def run_mine(args, rank, world, local_rank):
         tables = [table] + [tm.StepTable.from_steps([dict(st, kf_id=i) for st, i in zip(off_steps, ids2[j])])
                             for j in range(1, depth)]
 
+        # results as views into caller-owned pinned buffers, one set per batch in flight
+        outs = [tm.ResultBuffers() for _ in range(depth)]
+
         def pipelined(n):
             inflight, last = [], None
             for k in range(n + depth - 1):
@@ -531,7 +534,7 @@ def run_mine(args, rank, world, local_rank):
                                                      new=(ids2[k % depth], h_new)), k % depth))
                 if len(inflight) == depth or (k >= n and inflight):
                     t, j = inflight.pop(0)
-                    last = ctx.batch_finish(t)
+                    last = ctx.batch_finish(t, out=outs[j])
                     ctx.remove_keyframes(ids2[j])
             return last
 
@@ -548,7 +551,8 @@ def run_mine(args, rank, world, local_rank):
                       "api": "Context.batch_begin / batch_finish -> tm_batch_begin / tm_batch_finish, three "
                              "batches in flight (steps k + 1 and k + 2 begun before step k's results are taken; "
                              "step table as columns; pinned host buffers: new keyframes, masks, map points in; "
-                             "matches and fusion candidates out) + Context.remove_keyframes of each step's "
+                             "matches and fusion candidates out, into one caller-owned ResultBuffers per batch "
+                             "in flight, returned as views) + Context.remove_keyframes of each step's "
                              "64 new keyframes once its results are in",
                       "link": "inputs cross the host link at about 205 GB/s on this GB300 (copy engine and SM "
                               "loads alike): ~0.2 ms of the step's 40 MB",

@@ -474,13 +474,14 @@ def _result_struct(match_cap, n_pairs, fuse_cap, n_steps, fwd_cap=0, tri=False):
     return r, (m, po, f, fo, w, wo, pt, ok)
 
 
-def _collect(r, bufs):
+def _collect(r, bufs, copy=True):
     m, po, f, fo, w, wo, pt, ok = bufs
     n = r.n_matches
-    return BatchResult(m[:n].copy(), po.copy(), f[:r.n_fuse].copy(), fo.copy(),
+    c = (lambda a: a.copy()) if copy else (lambda a: a)
+    return BatchResult(c(m[:n]), c(po), c(f[:r.n_fuse]), c(fo),
                        int(r.n_comparisons_search), int(r.n_comparisons_fuse),
-                       w[:r.n_fwd].copy(), wo.copy(), int(r.n_comparisons_fwd),
-                       None if pt is None else pt[:n].copy(), None if ok is None else ok[:n].copy())
+                       c(w[:r.n_fwd]), c(wo), int(r.n_comparisons_fwd),
+                       None if pt is None else c(pt[:n]), None if ok is None else c(ok[:n]))
 
 
 def _fwd_cap(steps):
@@ -519,9 +520,12 @@ def _result_caps(steps, kf_sizes, resolve=True, default=TM_MAX_KP_LIMIT):
     return mc, fc
 
 
-class _ResultBuffers:
-    """Host result buffers of a context, reused across one-shot calls (pinned when torch is
-    available, so that the results come back by DMA) and grown as needed."""
+class ResultBuffers:
+    """Host result buffers (pinned when torch is available, so that the results come back by
+    DMA), grown as needed.  A context keeps one set for its one-shot calls and copies the
+    results out of it; a caller may own sets of its own instead and pass one as `out` to
+    Context.batch_run / batch_finish: the BatchResult's arrays are then views into that set,
+    with no copy, valid until the set is passed to another call (one set per batch in flight)."""
 
     def __init__(self):
         self.m = self.po = self.f = self.fo = self.w = self.wo = self.pt = self.ok = None
@@ -837,12 +841,13 @@ class Context:
         keep.append(st)
         return st, inp, keep
 
-    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None, tri=None):
+    def batch_run(self, steps, masks=None, mps=None, sp=None, fp=None, stream=None, new=None, tri=None,
+                  out=None):
         """One-shot batch (tm_batch_run).  Without masks/mps the steps carry their own
         q_free / nbr_free / mps and are packed here.  new = (ids, keyframes) entering the
         store with the batch: a list of keyframe dicts, or one packed dict (see
         keyframe_views_packed).  tri = TriParams(): triangulate every match (res.points,
-        res.point_ok)."""
+        res.point_ok).  out = a caller's ResultBuffers: the results as views into it."""
         sp = sp or SearchParams()
         st, inp, keep = self._inputs(steps, masks, mps, new)
         if tri is not None:
@@ -853,9 +858,9 @@ class Context:
         if masks is not None or mps is not None:
             fc = max(fc, int(mps["n"]) if mps is not None else 0)
         if self._res is None:
-            self._res = _ResultBuffers()
+            self._res = ResultBuffers()
         n_pairs = steps.n_pairs() if isinstance(steps, StepTable) else sum(len(s["nbrs"]) for s in steps)
-        r, bufs = self._res.struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps), tri is not None)
+        r, bufs = (out or self._res).struct(mc, n_pairs, fc, len(steps), _fwd_cap(steps), tri is not None)
         sps, fps = sp.struct(), (fp or FuseParams()).struct()
         try:
             check(tm_batch_run(self.handle, st, len(steps), ctypes.byref(inp), ctypes.byref(sps),  # noqa: F821
@@ -865,7 +870,7 @@ class Context:
                 for i in new[0]:
                     self.sizes.pop(int(i), None)
             raise
-        return _collect(r, bufs)
+        return _collect(r, bufs, copy=out is None)
 
     def batch_begin(self, steps, masks=None, mps=None, sp=None, fp=None, new=None, tri=None):
         """Asynchronous batch_run (tm_batch_begin): enqueues the batch and returns a ticket for
@@ -898,19 +903,20 @@ class Context:
                                    None if new is None else list(new[0]))
         return t.value
 
-    def batch_finish(self, ticket):
-        """Waits for a batch begun by batch_begin and returns its BatchResult."""
+    def batch_finish(self, ticket, out=None):
+        """Waits for a batch begun by batch_begin and returns its BatchResult (with out = a
+        caller's ResultBuffers: views into it)."""
         keep, caps, new_ids = self._inflight.pop(ticket)
         if self._res is None:
-            self._res = _ResultBuffers()
-        r, bufs = self._res.struct(*caps)
+            self._res = ResultBuffers()
+        r, bufs = (out or self._res).struct(*caps)
         try:
             check(tm_batch_finish(self.handle, ticket, ctypes.byref(r)))  # noqa: F821
         except TMError:
             for i in new_ids or []:
                 self.sizes.pop(int(i), None)
             raise
-        return _collect(r, bufs)
+        return _collect(r, bufs, copy=out is None)
 
     def last_host_times(self):
         """Host microseconds of the phases of the last batch_run (tm_batch_last_host_times):

@@ -412,7 +412,8 @@ def test_async_batches(tm, small_batch):
     neighbour a keyframe that the first stores; finished out of order, each equal to the
     oracle.  A begin beyond TM_BATCH_INFLIGHT is refused, the keyframes in-flight batches use
     cannot be removed, an unknown ticket is refused, and a pipelined loop (begin k + 1, then
-    finish k) gives the oracle's results at every step."""
+    finish k) gives the oracle's results at every step, also as views into two caller-owned
+    result buffer sets taken in turn (out=)."""
     from paper_2511_02036_gb300 import _lib as L
     w = small_batch
     st = w["steps"]
@@ -462,6 +463,29 @@ def test_async_batches(tm, small_batch):
         got.append(ctx.batch_finish(prev))
         for res, s in zip(got, rest):
             assert_same(res, oracle_results(dict(w, steps=[s])))
+        # the same loop with the results as views into caller-owned buffers, checked as each
+        # arrives (the set is written again two batches later)
+        ctx.remove_keyframes([s["q"] for s in rest])
+        outs = [tm.ResultBuffers(), tm.ResultBuffers()]
+        prev = None
+
+        def take(t, k):
+            res = ctx.batch_finish(t, out=outs[k % 2])
+            for a, b in ((res.matches, outs[k % 2].m), (res.fuse, outs[k % 2].f)):
+                assert len(a) == 0 or np.shares_memory(a, b)
+            assert_same(res, oracle_results(dict(w, steps=[rest[k]])))
+
+        for k, s in enumerate(rest):
+            t = ctx.batch_begin(steps_of(dict(w, steps=[s])), new=([s["q"]], [w["frames"][s["q"]]]))
+            if prev is not None:
+                take(prev, k - 1)
+            prev = t
+        take(prev, len(rest) - 1)
+        ctx.remove_keyframes([s["q"] for s in rest])
+        res = ctx.batch_run(steps_of(dict(w, steps=rest[:1])), new=([rest[0]["q"]], [w["frames"][rest[0]["q"]]]),
+                            out=outs[0])
+        assert len(res.matches) == 0 or np.shares_memory(res.matches, outs[0].m)
+        assert_same(res, oracle_results(dict(w, steps=rest[:1])))
         assert L.TM_BATCH_INFLIGHT == 4
 
 
