@@ -428,7 +428,9 @@ tm_status tm_plan_info(tm_plan *plan, int32_t *threads, int32_t *lanes, int32_t 
                        int32_t *kernels_per_run);
 /* Launch choices of a plan's fused form, made by the autotuner when the plan was created
  * (measured once per batch regime and cached per context, and in the file named by the
- * TM_TUNE_CACHE environment variable when set) or fixed by tm_debug_set.  Results never depend
+ * TM_TUNE_CACHE environment variable when set; a file whose first line names another key
+ * layout is ignored) or fixed by tm_debug_set.  The regime: comparisons per query, fewer pairs
+ * than SMs, dense blocks off / on / left to the tuner, epipole rejection.  Results never depend
  * on them.  For a plain per-pair plan every field is 0. */
 typedef struct {
     int32_t queries_per_warp; /* queries a search warp takes at a time: 32 or 64                 */

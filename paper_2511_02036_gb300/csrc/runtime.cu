@@ -1351,11 +1351,19 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
 // Launch shape of the search kernel: 256 threads per CTA (five per SM).
 int tmap::default_threads(const tm_ctx *, const BatchBuf &) { return 256; }
 
+// Layout of the regime keys in a tuning cache file (its first line).
+static constexpr int kTuneVersion = 2;
+
 void tmap::load_tuning(tm_ctx *c, const char *path) {
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int key;
+    int key, version = 0;
     Knobs k;
+    // (a file of another key layout is ignored: its choices would be taken for other regimes)
+    if (fscanf(f, "tm-tune %d", &version) != 1 || version != kTuneVersion) {
+        fclose(f);
+        return;
+    }
     while (fscanf(f, "%d %d %d %d %d %d %d", &key, &k.qpl, &k.persist, &k.prefetch, &k.bprio, &k.dense_min,
                   &k.dsplit_div) == 7)
         if (k.qpl >= 1 && k.qpl <= 3 && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
@@ -1367,6 +1375,7 @@ static void save_tuning(tm_ctx *c) {
     if (!path) return;
     FILE *f = fopen(path, "w");
     if (!f) return;
+    fprintf(f, "tm-tune %d\n", kTuneVersion);
     for (auto &kv : c->tuned_knobs) {
         const Knobs &k = kv.second;
         fprintf(f, "%d %d %d %d %d %d %d\n", kv.first, k.qpl, k.persist, k.prefetch, k.bprio, k.dense_min, k.dsplit_div);
@@ -1405,8 +1414,14 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     if ((e = cudaMemcpyAsync(hc, B.ncmp.p, 16, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "tuning");
     const bool dense_auto = B.user_dense_min < 0 && B.n_search_items > 0;
-    const int key = (density_key(hc[0], batch_queries(c, B, steps)) * 2 +
-                     ((int)B.n_search_items < c->num_sms ? 1 : 0)) * 2 + (dense_auto ? 1 : 0);
+    // dense blocks off, on at the caller's dense_min, or left to the tuner; epipole rejection:
+    // with dense blocks on or epipole rejection the search has one group form only, so such
+    // batches neither tune the form nor share choices with batches that have all of them
+    const int dense_mode = dense_auto ? 2 : (B.user_dense_min > 0 ? 1 : 0);
+    const bool epi_rej = B.sp.epipole_px > 0.0f;
+    const bool forms = dense_mode != 1 && !epi_rej;
+    const int key = (((density_key(hc[0], batch_queries(c, B, steps)) * 2 +
+                       ((int)B.n_search_items < c->num_sms ? 1 : 0)) * 3 + dense_mode) * 2) + (epi_rej ? 1 : 0);
     auto it = c->tuned_knobs.find(key);
     if (it != c->tuned_knobs.end()) {
         B.knobs = it->second;
@@ -1441,11 +1456,11 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         Knobs k = best;
         switch (knob) {
             case 0:
-                if (!c->force_qpl)
+                if (!c->force_qpl && forms)
                     for (int qf : {2, 1, 3})
                         if (qf != best.qpl) { k.qpl = qf; alts.push_back(k); }
                 break;
-            case 1: if (c->force_persist < 0) { k.persist = !best.persist; alts.push_back(k); } break;
+            case 1: if (c->force_persist < 0 && forms) { k.persist = !best.persist; alts.push_back(k); } break;
             case 2: if (c->force_prefetch < 0) { k.prefetch = !best.prefetch; alts.push_back(k); } break;
             case 3: if (c->branch_prio < 0 && both_branches) { k.bprio = !best.bprio; alts.push_back(k); } break;
             case 4:

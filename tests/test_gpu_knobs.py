@@ -221,3 +221,38 @@ def test_tuned_choice_matches_oracle(tm, batch):
             assert plan.tuning() == t
             plan.run()
             assert_same(plan.results(), exp)
+
+
+def test_tuning_cache_keyed_by_dense_mode(tm, tmp_path, monkeypatch):
+    """A tuning cache file (TM_TUNE_CACHE, first line its key layout) holding other choices for
+    batches with dense blocks on than for batches without: in one context a plan with dense
+    blocks and then one without each take their own regime's choices (dense blocks fix the
+    group form, so their choices must not reach a batch that has every form), and both equal
+    the oracle."""
+    w = W.make_cfg3b(seed=3510, n_nbrs=6)
+    lines = ["tm-tune 2"]
+    # key = ((density class x 2 + fewer pairs than SMs) x 3 + dense mode) x 2 + epipole rejection
+    for dk in range(-4, 41):
+        for few in (0, 1):
+            for dmode in range(3):
+                for epi in (0, 1):
+                    key = ((dk * 2 + few) * 3 + dmode) * 2 + epi
+                    # qpl, persistent, prefetch, branch priority, dense_min, dense split divisor
+                    kn = (1, 1, 0, 0, 0, 1) if dmode == 1 else (3, 0, 1, 0, 0, 1)
+                    lines.append(" ".join(str(v) for v in (key,) + kn))
+    path = tmp_path / "tune.txt"
+    path.write_text("\n".join(lines) + "\n")
+    monkeypatch.setenv("TM_TUNE_CACHE", str(path))
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        for dense_min in (64, 0):
+            sp = tm.SearchParams(dense_min=dense_min)
+            with ctx.plan(steps_of(w), sp=sp) as plan:
+                t = plan.tuning()
+                assert t["tuned"] == 1
+                if dense_min:
+                    assert t["dense_min"] == 64 and t["l2_prefetch"] == 0 and t["per_lane"] == 0
+                else:
+                    assert t["dense_min"] == 0 and t["l2_prefetch"] == 1 and t["per_lane"] == 1
+                plan.run()
+                assert_same(plan.results(), expected(w, sp))
