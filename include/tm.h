@@ -399,7 +399,10 @@ tm_status tm_batch_run(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
  * removed (TM_ERR_BUSY), and the keyframes it stores may be read only by later batches begun
  * with tm_batch_begin until it is finished (other calls that name them: TM_ERR_BUSY).  If tm_batch_finish reports an error, the batch's new keyframes are
  * taken out of the store again, except those that a batch still in flight reads.  Tickets are
- * finished in any order; an unknown ticket is TM_ERR_NOT_FOUND. */
+ * finished in any order; an unknown ticket (or one that another thread is finishing) is
+ * TM_ERR_NOT_FOUND.  tm_batch_finish waits for its batch and downloads the results without
+ * holding the context, so one thread may begin batches (or call anything else on the context)
+ * while another finishes earlier ones; the result buffers of concurrent finishes must differ. */
 #define TM_BATCH_INFLIGHT 4
 tm_status tm_batch_begin(tm_ctx *ctx, const tm_step *steps, int32_t n_steps,
                          const tm_batch_inputs *in, const tm_search_params *sp,

@@ -905,7 +905,8 @@ class Context:
 
     def batch_finish(self, ticket, out=None):
         """Waits for a batch begun by batch_begin and returns its BatchResult (with out = a
-        caller's ResultBuffers: views into it)."""
+        caller's ResultBuffers: views into it).  The wait does not hold the context: another
+        thread may begin batches meanwhile (finishes on several threads at once need out=)."""
         keep, caps, new_ids = self._inflight.pop(ticket)
         if self._res is None:
             self._res = ResultBuffers()

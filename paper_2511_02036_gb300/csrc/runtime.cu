@@ -1283,7 +1283,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
 }
 
 // Download results of the last run of B into r (host offsets; matches host or device).
-tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s) {
+tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s, double *t_counts) {
     cudaError_t e;
     const size_t nio = (size_t)B.n_items + 1;
     if ((e = B.h_out.reserve((nio + 2) * 4 + 48))) return cuda_fail(e, "pinned results");
@@ -1295,7 +1295,7 @@ tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaSt
         (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
-    c->t_counts = tm_now();
+    *(t_counts ? t_counts : &c->t_counts) = tm_now();
     if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
         return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory or a tensor-core product did not complete in time");
     const uint32_t search_total = ho[B.n_search_items];
@@ -1611,25 +1611,32 @@ extern "C" tm_status tm_batch_begin(tm_ctx *c, const tm_step *steps, int32_t n_s
 extern "C" tm_status tm_batch_finish(tm_ctx *c, uint64_t ticket, tm_batch_result *res) {
     if (!c || !res) return fail(TM_ERR_INVALID_ARG, "tm_batch_finish: null argument");
     Range range("tm_batch_finish");
-    std::lock_guard<std::mutex> lk(c->mu);
-    cudaSetDevice(c->device);
     int k = -1;
-    for (int q = 0; q < TM_BATCH_INFLIGHT; ++q)
-        if (ticket && c->async[q].ticket == ticket) { k = q; break; }
-    if (k < 0) return fail(TM_ERR_NOT_FOUND, "tm_batch_finish: unknown ticket %llu", (unsigned long long)ticket);
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (int q = 0; q < TM_BATCH_INFLIGHT; ++q)
+            if (ticket && c->async[q].ticket == ticket && !c->async[q].finishing) { k = q; break; }
+        if (k < 0) return fail(TM_ERR_NOT_FOUND, "tm_batch_finish: unknown ticket %llu", (unsigned long long)ticket);
+        c->async[k].finishing = true;
+    }
+    cudaSetDevice(c->device);
     tm_ctx::AsyncBatch &a = c->async[k];
     BatchBuf &B = a.B;
+    // the wait and the downloads use only the batch's own buffers and streams (its slot stays
+    // taken until the end of this call), so they run without the context's lock: other threads
+    // may begin batches, or finish other ones, meanwhile
     const double t0 = tm_now();
-    c->t_counts = 0;
-    tm_status st = fetch_results(c, B, res, a.s);
-    const double t1 = tm_now(), tc = c->t_counts > 0 ? c->t_counts : t1;
-    c->host_us[0] = c->host_us[1] = 0.0;
-    c->host_us[2] = 1e6 * (tc - t0);
-    c->host_us[3] = 1e6 * (t1 - tc);
+    double tcnt = 0;
+    tm_status st = fetch_results(c, B, res, a.s, &tcnt);
+    const double t1 = tm_now(), tc = tcnt > 0 ? tcnt : t1;
     if (st) {
         if (B.mcopy) cudaStreamSynchronize(B.mcopy);
         cudaStreamSynchronize(a.s);
     }
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->host_us[0] = c->host_us[1] = 0.0;
+    c->host_us[2] = 1e6 * (tc - t0);
+    c->host_us[3] = 1e6 * (t1 - tc);
     for (int sl : B.slots) c->slots[sl].refs--;
     for (uint64_t id : a.new_ids) {
         auto it = c->ids.find(id);
@@ -1647,6 +1654,7 @@ extern "C" tm_status tm_batch_finish(tm_ctx *c, uint64_t ticket, tm_batch_result
     B.n_new = 0;
     a.new_ids.clear();
     a.ticket = 0;
+    a.finishing = false;
     return st;
 }
 

@@ -237,6 +237,7 @@ struct tm_ctx {
         cudaStream_t s = nullptr;
         cudaEvent_t ingested = nullptr;   // after the batch's ingest (or its start)
         uint64_t ticket = 0;              // 0: free
+        bool finishing = false;           // a tm_batch_finish is waiting for it (without the lock)
         std::vector<uint64_t> new_ids;    // the keyframes it stores (taken out again on failure)
     };
     AsyncBatch async[TM_BATCH_INFLIGHT];
@@ -277,7 +278,8 @@ tm_status prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int n_step
                         const tm_fuse_params &fp, cudaStream_t s);
 tm_status enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed = false);
 tm_status enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s);
-tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s);
+// t_counts: where to note when the counts arrived (default: c->t_counts, under c's lock)
+tm_status fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s, double *t_counts = nullptr);
 tm_status tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStream_t s, bool measure);
 void load_tuning(tm_ctx *c, const char *path);
 // Threads per CTA used when no tuned value applies.

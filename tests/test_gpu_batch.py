@@ -489,6 +489,66 @@ def test_async_batches(tm, small_batch):
         assert L.TM_BATCH_INFLIGHT == 4
 
 
+def test_async_batches_two_threads(tm, small_batch):
+    """A producer thread begins batches (at most three in flight) while a consumer thread
+    finishes them in order, into its own result buffers, and removes their keyframes: every
+    batch equals the oracle (tm_batch_finish waits without holding the context)."""
+    import queue
+    import threading
+    w = small_batch
+    st = w["steps"]
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        old = sorted(set(i for s in st for i in s["nbrs"]))
+        ctx.add_keyframes(old, [w["frames"][i] for i in old])
+        exp = [oracle_results(dict(w, steps=[s])) for s in st]
+        # each batch stores its step's new keyframe under an id of its own round, not one of the
+        # stored ids
+        rounds, depth = 4, 3
+        outs = [tm.ResultBuffers() for _ in range(depth)]
+        sem, q, got, err = threading.Semaphore(depth), queue.Queue(), [], []
+
+        def consumer():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                t, k, nid = item
+                try:
+                    res = ctx.batch_finish(t, out=outs[k % depth])
+                    got.append((k, [a.copy() for a in res.pairs], [a.copy() for a in res.fuses],
+                                res.n_comparisons_search, res.n_comparisons_fuse))
+                    ctx.remove_keyframes([nid])
+                except BaseException as ex:  # noqa: BLE001
+                    err.append(ex)
+                sem.release()
+
+        th = threading.Thread(target=consumer)
+        th.start()
+        try:
+            n = 0
+            for r in range(rounds):
+                for s in st:
+                    sem.acquire()
+                    nid = s["q"] + ((r + 1) << 40)
+                    step = dict(kf_id=nid, nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
+                                mps=s.get("mps"))
+                    q.put((ctx.batch_begin([step], new=([nid], [w["frames"][s["q"]]])), n, nid))
+                    n += 1
+        finally:
+            q.put(None)
+            th.join()
+        assert not err, err
+        assert [k for k, *_ in got] == list(range(rounds * len(st)))
+        for k, pairs, fuses, cs, cf in got:
+            e_pairs, e_fuses, e_cs, e_cf = exp[k % len(st)]
+            assert len(pairs) == len(e_pairs) and len(fuses) == len(e_fuses)
+            for g, e in zip(pairs, e_pairs):
+                np.testing.assert_array_equal(g, e)
+            for g, e in zip(fuses, e_fuses):
+                np.testing.assert_array_equal(g, e)
+            assert cs == e_cs and cf == e_cf
+
+
 def forward_steps(w, skip=True):
     return [dict(kf_id=s["q"], nbrs=s["nbrs"], q_free=s.get("q_free"), nbr_free=s.get("nbr_free"),
                  mps=s.get("mps"), fwd_mps=s["fwd_mps"], fwd_skip=s["fwd_skip"] if skip else None)

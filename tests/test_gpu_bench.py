@@ -49,3 +49,4 @@ def test_bench_json_line():
         assert cf[name]["oracle_1_core"]["keyframes_per_s"] > 0
         assert cf[name]["oracle_all_cores"]["cores"] >= 1
     assert d["e2e"]["serial"]["value"] > 0 and d["e2e"]["serial"]["unit"] == d["unit"]
+    assert d["e2e"]["one_thread"]["value"] > 0 and d["e2e"]["one_thread"]["unit"] == d["unit"]
