@@ -447,6 +447,9 @@ typedef struct {
     int32_t per_lane;         /* 1: each lane walks its own queries' candidates (per-lane form);
                                  0: a warp's candidates spread over its lanes in rounds          */
     int32_t search_units;     /* search launch entries: pairs, a split pair counted twice        */
+    int32_t entry_form;       /* 1: the entry form -- a join pass lists every (query, candidate)
+                                 entry of the batch, one thread evaluates each, a finalize pass
+                                 per pair reads the queries' states (three launches)            */
 } tm_plan_tuning;
 tm_status tm_plan_get_tuning(tm_plan *plan, tm_plan_tuning *out);
 
@@ -481,7 +484,12 @@ tm_status tm_plan_destroy(tm_plan *plan);
  *                           (default)
  *   TM_DEBUG_QUERIES_PER_LANE search warps take 32 (1) or 64 (2) queries at a time with their
  *                           candidates spread over the lanes in rounds, or 64 with each lane
- *                           walking its own two queries' candidates (3); 0 = tuned (default)
+ *                           walking its own two queries' candidates (3); or the entry form (4:
+ *                           join, one thread per candidate entry, finalize; batches with the
+ *                           default gates only); 0 = tuned (default)
+ *   TM_DEBUG_ENTRY_CAP      entries the entry form's list holds (0 = four per query visit, at
+ *                           least 2^20, grown by the tuner to a batch's count; at most 2^26);
+ *                           a pair with entries past it is searched in rounds by its finalize
  *   TM_DEBUG_PERSISTENT     1: resident search CTAs take pairs from a work counter; 0: one CTA
  *                           per pair; -1 = tuned (default)
  *   TM_DEBUG_SPLIT_MIN      in batches of fewer pairs than SMs, pairs with at least this many
@@ -499,6 +507,7 @@ tm_status tm_plan_destroy(tm_plan *plan);
 #define TM_DEBUG_QUERIES_PER_LANE 6
 #define TM_DEBUG_PERSISTENT 7
 #define TM_DEBUG_SPLIT_MIN 8
+#define TM_DEBUG_ENTRY_CAP 9
 tm_status tm_debug_set(tm_ctx *ctx, int32_t what, int64_t value);
 /* Bounds-checking builds (compiled with -DTM_DEBUG_BOUNDS; the normal build sets *enabled = 0
  * and *site = 0): every index the kernels take from data (bucket tables, grid lists, match and

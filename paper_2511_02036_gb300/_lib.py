@@ -36,6 +36,7 @@ TM_DEBUG_BRANCH_PRIORITY = 5
 TM_DEBUG_QUERIES_PER_LANE = 6
 TM_DEBUG_PERSISTENT = 7
 TM_DEBUG_SPLIT_MIN = 8
+TM_DEBUG_ENTRY_CAP = 9
 
 
 class tm_camera(ctypes.Structure):
@@ -116,7 +117,8 @@ class tm_server_config(ctypes.Structure):
 class tm_plan_tuning(ctypes.Structure):
     _fields_ = [("queries_per_warp", c_i32), ("persistent", c_i32), ("l2_prefetch", c_i32),
                 ("branch_priority", c_i32), ("dense_min", c_i32), ("dense_split", c_i32),
-                ("search_ctas", c_i32), ("tuned", c_i32), ("per_lane", c_i32), ("search_units", c_i32)]
+                ("search_ctas", c_i32), ("tuned", c_i32), ("per_lane", c_i32), ("search_units", c_i32),
+                ("entry_form", c_i32)]
 
 
 class tm_fuse_apply_stats(ctypes.Structure):

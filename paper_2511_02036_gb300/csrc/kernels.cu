@@ -930,12 +930,15 @@ __device__ __forceinline__ int eligible_before(const SearchSmem &M, int j) {
 // rejection and dense node blocks are on (fixed per launch).
 // wing: the pair's per-target winners in global memory when the pair is split over two CTAs
 // (else null: in shared memory); the accepted queries are listed from acc[c + abase].
-template <int Q, bool kEpi, bool kEprej, bool kDense>
-__device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
-                                             const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
-                                             uint32_t &cmp, uint32_t &dfail, uint32_t *wing, uint32_t abase) {
+// The lookups of a group (the first part of search_group): per query of the lane, the count n
+// of its eligible candidates and its first eligible entry elo; a dense-block query's (best key,
+// second) from the tensor cores in b0 / s0 (its n then 0; else kNone / 0xFFFF).
+template <int Q, bool kDense>
+__device__ __forceinline__ void group_lookup(const BatchArgs &A, const WorkItem &w, const SearchSmem &M, int g,
+                                             const QLoad<Q> &q, uint32_t &cmp, int (&c)[Q], int (&elo_out)[Q],
+                                             uint32_t (&b0_out)[Q], uint32_t (&s0_out)[Q]) {
     const int lane = (int)(threadIdx.x & 31u);
-    const int nT = (int)w.nt, nQ = (int)w.nq;
+    const int nT = (int)w.nt;
     uint32_t key[Q];
     int lo[Q], be[Q];
 #pragma unroll
@@ -966,7 +969,6 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             nle[h] += pt[h] && kt[h] <= key[h];
         }
     }
-    int c[Q];
 #pragma unroll
     for (int h = 0; h < Q; ++h) {
         const bool el = q.el[h] >= 0 ? q.el[h] != 0 : (ldg(A.masks + w.a + q.io[h]) != 0);
@@ -982,8 +984,30 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
             s0 = v.y == kNone ? kSecTimeout : v.y;
         }
         c[h] = n;
-        st_s32(M.sb + 4 * (32 * h + lane), b0);
-        st_s32(M.rec + 4 * (32 * h + lane), (s0 << 16) | (uint32_t)elo);
+        elo_out[h] = elo;
+        b0_out[h] = b0;
+        s0_out[h] = s0;
+    }
+}
+
+template <int Q, bool kDense>
+__device__ __forceinline__ void group_results(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                              const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
+                                              uint32_t &dfail, uint32_t *wing, uint32_t abase);
+
+template <int Q, bool kEpi, bool kEprej, bool kDense>
+__device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                             const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
+                                             uint32_t &cmp, uint32_t &dfail, uint32_t *wing, uint32_t abase) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int nT = (int)w.nt, nQ = (int)w.nq;
+    int c[Q], elo[Q];
+    uint32_t b0[Q], s0[Q];
+    group_lookup<Q, kDense>(A, w, M, g, q, cmp, c, elo, b0, s0);
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        st_s32(M.sb + 4 * (32 * h + lane), b0[h]);
+        st_s32(M.rec + 4 * (32 * h + lane), (s0[h] << 16) | (uint32_t)elo[h]);
     }
     const int c0 = c[0], cl = Q > 1 ? c[0] + c[Q - 1] : c[0];
     int off = cl;
@@ -1049,6 +1073,18 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
         }
     }
     __syncwarp();
+    group_results<Q, kDense>(A, w, T, M, nacc, g, q, dfail, wing, abase);
+}
+
+// The results of a group (the last part of search_group), from its queries' states in M.sb /
+// M.rec: a query whose best passes the distance and ratio tests gets its rotation bin, is listed
+// in the pair's accepted list and claims its target.
+template <int Q, bool kDense>
+__device__ __forceinline__ void group_results(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                              const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
+                                              uint32_t &dfail, uint32_t *wing, uint32_t abase) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int nT = (int)w.nt, nQ = (int)w.nq;
 #pragma unroll
     for (int h = 0; h < Q; ++h) {
         const int p = g * 32 * Q + 32 * h + lane;
@@ -1086,6 +1122,123 @@ __device__ __forceinline__ void search_group(const BatchArgs &A, const WorkItem 
     __syncwarp();
 }
 
+// Entry form, join pass (Sec. IV-C candidate generation without the comparisons): the group's
+// lookups as in search_group; each query's state (best key, second) starts in dres at kNone /
+// 0xFFFF, and its candidates are appended to the batch's entry list (a warp prefix of the
+// lanes' counts, one atomicAdd a warp).  An entry past ent_cap is not written and flags the
+// pair (ovf), whose finalize then searches it in rounds.
+template <int Q>
+__device__ __forceinline__ void join_group(const BatchArgs &A, const WorkItem &w, const SearchSmem &M, int g,
+                                           const QLoad<Q> &q, uint32_t &cmp, uint32_t slot, bool &ovf) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int nQ = (int)w.nq, nT = (int)w.nt;
+    int c[Q], elo[Q];
+    uint32_t b0[Q], s0[Q];
+    group_lookup<Q, false>(A, w, M, g, q, cmp, c, elo, b0, s0);
+    int cl = 0;
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const int p = g * 32 * Q + 32 * h + lane;
+        if (p < nQ) A.dres[w.c + (uint32_t)p] = make_uint2(kNone, 0xFFFFu);
+        cl += c[h];
+    }
+    int off = cl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, off, o);
+        if (lane >= o) off += y;
+    }
+    const uint32_t total = (uint32_t)__shfl_sync(kFull, off, 31);
+    off -= cl;
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(A.nents, total);
+    base = __shfl_sync(kFull, base, 0);
+    cmp += (uint32_t)cl;
+    if ((uint64_t)base + total > A.ent_cap) ovf = true;
+    uint32_t e = base + (uint32_t)off;
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const uint32_t p = (uint32_t)(g * 32 * Q + 32 * h + lane);
+        for (int r = 0; r < c[h]; ++r, ++e) {
+            const uint32_t j = (uint32_t)guard((int)ld_s16(M.epos + 2 * guard(elo[h] + r, nT, 33)), nT, 34);
+            if (e < A.ent_cap) A.ents[e] = make_uint2(slot, (p << 16) | j);
+        }
+    }
+}
+
+// Entry form, finalize pass: the group's states as the entries left them, then its results as
+// in search_group.
+template <int Q>
+__device__ __forceinline__ void final_group(const BatchArgs &A, const WorkItem &w, const KfView &T,
+                                            const SearchSmem &M, uint32_t *nacc, int g, const QLoad<Q> &q,
+                                            uint32_t &dfail, uint32_t *wing, uint32_t abase) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int nQ = (int)w.nq;
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const int p = g * 32 * Q + 32 * h + lane;
+        const uint2 v = p < nQ ? A.dres[w.c + (uint32_t)p] : make_uint2(kNone, 0xFFFFu);
+        st_s32(M.sb + 4 * (32 * h + lane), v.x);
+        st_s32(M.rec + 4 * (32 * h + lane), v.y << 16);
+    }
+    __syncwarp();
+    group_results<Q, false>(A, w, T, M, nacc, g, q, dfail, wing, abase);
+}
+
+// Entry form, evaluation pass: one thread per (query, candidate) entry of the batch (a grid
+// stride over the list): Hamming distance, epipolar gate (the same float32 operations as the
+// rounds), and the query's state folded with two atomicMin as the rounds do in shared memory
+// (the first returns the previous best; the larger of the two bounds the second), so that the
+// states do not depend on the order in which the entries run.
+constexpr int kEvalThreads = 256;
+template <bool kEpi>
+__global__ void __launch_bounds__(kEvalThreads) eval_kernel(BatchArgs A) {
+    __shared__ float thr[kLevels];
+    if (threadIdx.x < kLevels) {
+        const float sc = level_scale((int)threadIdx.x);
+        thr[threadIdx.x] = fmul(A.sp.epi_chi2, fmul(sc, sc));
+    }
+    __syncthreads();
+    const uint32_t n = min(*A.nents, A.ent_cap);
+    for (uint32_t e = blockIdx.x * kEvalThreads + threadIdx.x; e < n; e += gridDim.x * kEvalThreads) {
+        const uint2 en = A.ents[e];
+        const WorkItem *wp = A.sitems + guard((int)en.x, (int)A.n_units, 30);
+        const uint32_t nq = wp->nq, nt = wp->nt, c = wp->c;
+        const KfView T = KfView::at(wp->t, A.L);
+        const int p = guard((int)(en.y >> 16), (int)nq, 31), j = guard((int)(en.y & 0xFFFFu), (int)nt, 32);
+        const uint4 *qd = wp->qdesc;
+        const uint4 a0 = ldg(qd + 2 * p), a1 = ldg(qd + 2 * p + 1);
+        const uint4 t0 = ldg(T.desc + 2 * j), t1 = ldg(T.desc + 2 * j + 1);
+        const float2 xt = ldg(T.xy + j);
+        const uint32_t lv = ldg(T.level + j);
+        const uint32_t d = (uint32_t)hamming(a0, a1, t0, t1);
+        uint32_t *st = reinterpret_cast<uint32_t *>(A.dres + c + (uint32_t)p);
+        // an entry farther than the query's second (read from L2; the second only decreases, so
+        // a stale read only costs work) changes neither its best nor its second: no gates and no
+        // atomics
+        if (d > __ldcg(st + 1)) continue;
+        bool pass = true;
+        if (kEpi) {
+            // l = F^T x_Q as in the rounds: a = (x F00 + y F10) + F20, b = (x F01 + y F11) + F21,
+            // c = (x F02 + y F12) + F22; num = (a x_T + b y_T) + c, den = a^2 + b^2;
+            // pass iff den > 0 and num^2 < thr den
+            const float2 xq = ldg(wp->qxy + p);
+            const float4 *pc = reinterpret_cast<const float4 *>(A.pconst + (size_t)kPairConst * wp->idx);
+            const float4 F0 = ldg(pc), F1 = ldg(pc + 1), F2 = ldg(pc + 2);
+            const float la = fadd(fadd(fmul(xq.x, F0.x), fmul(xq.y, F0.w)), F1.z);
+            const float lb = fadd(fadd(fmul(xq.x, F0.y), fmul(xq.y, F1.x)), F1.w);
+            const float lc = fadd(fadd(fmul(xq.x, F0.z), fmul(xq.y, F1.y)), F2.x);
+            const float num = fadd(fadd(fmul(la, xt.x), fmul(lb, xt.y)), lc);
+            const float den = fadd(fmul(la, la), fmul(lb, lb));
+            pass = den > 0.0f && fmul(num, num) < fmul(thr[guard((int)lv, kLevels, 35)], den);
+        }
+        if (pass) {
+            const uint32_t bk = (d << 16) | (uint32_t)j;
+            const uint32_t old = atomicMin(st, bk);
+            atomicMin(st + 1, max(old, bk) >> 16);
+        }
+    }
+}
 
 // The same group (64 queries, two per lane) in the per-lane form: after the same bucket
 // lookups, each lane walks its own queries' candidates itself, in eligible-list order (both
@@ -1606,7 +1759,11 @@ constexpr int kSearchThreads = 256;
 // The pair in slot `slot` of the launch order.  parity: phase of the CTA's bulk-copy barrier for
 // this pair (the CTA's pairs alternate); first: the CTA's first pair (initializes the barriers).
 // Returns 1 when a bounded wait ran out (the CTA stops).
-template <int Q, bool kEpi, bool kEprej, bool kDense, bool kSplit>
+// kForm: 0 the candidate rounds; 1 the entry form's join pass (the setup and the lookups, then
+// the pair's entries listed for the evaluation pass; no finalize); 2 its finalize pass (the
+// queries' states from the evaluation, then the results and finalize; a pair whose entries did
+// not all fit is searched in rounds here instead).
+template <int Q, bool kEpi, bool kEprej, bool kDense, bool kSplit, int kForm = 0>
 __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, uint32_t parity, bool first) {
     constexpr int kMaxT = kSearchThreads;
     constexpr bool kLane = Q == 3;            // the per-lane form (two queries per lane)
@@ -1616,7 +1773,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     __shared__ __align__(16) float thr[kLevels], thre[kLevels];
     __shared__ uint32_t qrec[kMaxT / 32][32 * QL], sbest[kMaxT / 32][32 * QL];  // per warp: its queries' states
     __shared__ uint32_t hist[32];
-    __shared__ uint32_t keep, scmp, sdfail, nacc, s_last;
+    __shared__ uint32_t keep, scmp, sdfail, nacc, s_last, sovf;
     __shared__ __align__(8) uint64_t bar, never;
     __shared__ int ok_all;
     constexpr int nw = kMaxT / 32;
@@ -1641,6 +1798,13 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     const int g0 = min(part * gpp, ngroups), g1 = min(g0 + gpp, ngroups);
     uint32_t *wing = parts > 1 ? A.pwin + w.toff : nullptr;
     const uint32_t abase = (uint32_t)(g0 * 32 * QL);
+    static_assert(kForm == 0 || (!kLane && !kDense && !kEprej), "the entry form runs the default gates");
+    if (kForm == 2 && (A.item_cmp[i] & kItemTimeout)) {  // (uniform) the join pass timed out
+        if (tid == 0) A.counts[i] = 0u;
+        return 0;
+    }
+    // the entry form's finalize of a pair whose entries all fit reads no staged tables
+    const bool rounds = kForm != 2 || A.povf[i] != 0u;
     if (tid == 0) {
         // the neighbour's node keys and bucket table (store), its eligibility words and eligible
         // positions and the pair's constants (prep kernel), all into shared memory
@@ -1649,21 +1813,24 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
             mbar_init(&never, 1);
             fence_mbar_init();
         }
-        const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
-        const uint32_t wb = (8u * (uint32_t)(nwt + 1) + 15u) & ~15u;
-        const uint32_t eb = (2u * (uint32_t)nT + 15u) & ~15u;
-        mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes + wb + eb + 48u);
-        if (kb) bulk_g2s(tkey, T.node, kb, &bar);
-        bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
-        bulk_g2s(words, A.pwords + w.toff / 32u, wb, &bar);
-        if (eb) bulk_g2s(epos, A.pepos + w.toff, eb, &bar);
-        bulk_g2s(pc, A.pconst + (size_t)kPairConst * i, 48u, &bar);
+        if (rounds) {
+            const uint32_t kb = (4u * (uint32_t)nT + 15u) & ~15u;
+            const uint32_t wb = (8u * (uint32_t)(nwt + 1) + 15u) & ~15u;
+            const uint32_t eb = (2u * (uint32_t)nT + 15u) & ~15u;
+            mbar_expect_tx(&bar, kb + (uint32_t)kBucketTableBytes + wb + eb + 48u);
+            if (kb) bulk_g2s(tkey, T.node, kb, &bar);
+            bulk_g2s(bst, T.bstart, (uint32_t)kBucketTableBytes, &bar);
+            bulk_g2s(words, A.pwords + w.toff / 32u, wb, &bar);
+            if (eb) bulk_g2s(epos, A.pepos + w.toff, eb, &bar);
+            bulk_g2s(pc, A.pconst + (size_t)kPairConst * i, 48u, &bar);
+        }
         scmp = 0u;
         sdfail = 0u;
         nacc = 0u;
+        sovf = 0u;
         ok_all = 1;
     }
-    if (tid == 32 && A.l2_prefetch) {
+    if (tid == 32 && A.l2_prefetch && kForm == 0) {
         // the arrays the candidate rounds read, into L2 while the setup runs (each neighbour's
         // descriptors are read once, so their loads would otherwise wait on DRAM)
         bulk_prefetch_l2(T.desc, 32u * (uint32_t)nT);
@@ -1683,7 +1850,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     if (g0 + wid < g1) cur = load_group<QL>(A, w, g0 + wid);  // the first group's loads overlap the setup
     // the thread that initialized the barrier and issued the bulk copies awaits them; the CTA
     // barrier then publishes the copied data (and every other setup write) to all threads
-    if (tid == 0) {
+    if (tid == 0 && rounds) {
         bool ok = mbar_wait_bounded(&bar, parity, A.wait_limit);
         if (ok && A.starve) ok = mbar_wait_bounded(&never, 0, A.wait_limit);
         if (!ok) ok_all = 0;
@@ -1692,7 +1859,11 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     if (!ok_all) {
         if (tid == 0) {
             A.counts[i] = 0u;
-            if (parts > 1) {
+            if (kForm == 1) {
+                // the finalize pass of the pair finds the flag and stops too
+                if (parts > 1) atomicOr(A.item_cmp + i, kItemTimeout);
+                else A.item_cmp[i] = kItemTimeout;
+            } else if (parts > 1) {
                 // the other part still counts this one in, and finds the pair failed
                 A.pacc[2 * i + part] = 0u;
                 atomicOr(A.item_cmp + i, kItemTimeout);
@@ -1704,7 +1875,8 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
         }
         return 1;
     }
-    if (A.sp.baseline_min_ratio > 0.0f && pc[11] != 0.0f) {  // (uniform) pair-baseline skip
+    if (A.sp.baseline_min_ratio > 0.0f &&
+        (rounds ? pc[11] : A.pconst[(size_t)kPairConst * i + 11]) != 0.0f) {  // (uniform) pair-baseline skip
         if (tid == 0) {
             A.counts[i] = 0u;
             A.item_cmp[i] = 0u;
@@ -1723,16 +1895,32 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     M.rec = smem_addr(&qrec[wid][0]);
     M.sb = smem_addr(&sbest[wid][0]);
     uint32_t cmp = 0, dfail = 0;
+    bool ovf = false;
     for (int g = g0 + wid; g < g1; g += nw) {
         QLoad<QL> nxt = {};
         if (g + nw < g1) nxt = load_group<QL>(A, w, g + nw);
         if constexpr (kLane)
             search_group_lane<kEpi>(A, w, T, M, &nacc, g, cur, cmp, wing, abase);
+        else if constexpr (kForm == 1)
+            join_group<QL>(A, w, M, g, cur, cmp, slot, ovf);
+        else if (kForm == 2 && !rounds)
+            final_group<QL>(A, w, T, M, &nacc, g, cur, dfail, wing, abase);
         else
             search_group<QL, kEpi, kEprej, kDense>(A, w, T, M, &nacc, g, cur, cmp, dfail, wing, abase);
         cur = nxt;
     }
     warp_count(cmp, &scmp);
+    if (kForm == 1) {
+        // the join pass ends here: the pair's comparisons (its entries) and overflow flag
+        if (ovf) sovf = 1u;
+        __syncthreads();
+        if (tid == 0) {
+            if (parts > 1) atomicAdd(A.item_cmp + i, scmp);
+            else A.item_cmp[i] = scmp;
+            if (sovf) A.povf[i] = 1u;
+        }
+        return 0;
+    }
     if (kDense && __any_sync(kFull, dfail != 0u) && lane == 0) sdfail = 1u;
     if (parts > 1) __threadfence();  // (uniform) this thread's list entries and winners, device-wide
     __syncthreads();
@@ -1741,7 +1929,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
         // part that completes the count finalizes the pair (no CTA waits for another)
         if (tid == 0) {
             A.pacc[2 * i + part] = nacc;
-            atomicAdd(A.item_cmp + i, scmp);
+            if (kForm == 0) atomicAdd(A.item_cmp + i, scmp);  // (the entry form's: by its join)
             if (sdfail) atomicOr(A.item_cmp + i, kItemTimeout);
             __threadfence();
             s_last = atomicAdd(A.pdone + i, 1u) == (uint32_t)(parts - 1) ? 1u : 0u;
@@ -1825,7 +2013,7 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
     }
     if (tid == 0) {
         A.counts[i] = qpre[nwq];
-        if (parts == 1) A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
+        if (parts == 1 && kForm == 0) A.item_cmp[i] = scmp | (sdfail ? kItemTimeout : 0u);
     }
     return 0;
 }
@@ -1833,11 +2021,12 @@ __device__ __forceinline__ int search_pair(const BatchArgs &A, uint32_t slot, ui
 // The search kernel: one CTA per pair (grid = pairs), or, kPersist, CTAs that stay resident
 // and take pairs in launch order (largest first) from the batch's work counter until none is
 // left (the copy kernel resets the counter for the next run).
-template <int Q, bool kEpi, bool kEprej, bool kDense, bool kPersist, bool kSplit = false>
+template <int Q, bool kEpi, bool kEprej, bool kDense, bool kPersist, bool kSplit = false, int kForm = 0>
 __global__ void __launch_bounds__(kSearchThreads, TM_SEARCH_MINB) search_kernel(BatchArgs A) {
     __shared__ uint32_t s_slot;
+    static_assert(kForm == 0 || !kPersist, "the entry form is not persistent");
     if (!kPersist) {
-        search_pair<Q, kEpi, kEprej, kDense, kSplit>(A, blockIdx.x, 0u, true);
+        search_pair<Q, kEpi, kEprej, kDense, kSplit, kForm>(A, blockIdx.x, 0u, true);
         return;
     }
     for (uint32_t it = 0;; ++it) {
@@ -1905,6 +2094,11 @@ __global__ void __launch_bounds__(kPrepThreads) pair_prep_kernel(BatchArgs A) {
             A.pdone[i] = 0u;
             A.item_cmp[i] = 0u;
         }
+    }
+    if (A.qpl == 4 && tid == 32) {
+        // entry form: the pair's overflow flag and the batch's entry count start over every run
+        A.povf[i] = 0u;
+        if (i == 0) *A.nents = 0u;
     }
     uint2 *words = A.pwords + w.toff / 32u;
     uint16_t *epos = A.pepos + w.toff;
@@ -2556,8 +2750,19 @@ size_t search_smem_bytes(int sn) { return SearchStage::make(sn).bytes; }
 // or off, no epipole rejection, no dense blocks); any other configuration runs 64-query groups,
 // one CTA per pair (search_form reports the form a launch gets).
 static bool search_variants(const BatchArgs &a) { return !(a.sp.epipole_px > 0.0f) && !(a.sp.dense_min > 0); }
+// The entry form's join (kForm 1) and finalize (kForm 2) instances.
+static void (*entry_fn(const BatchArgs &a, int form))(BatchArgs) {
+    const bool epi = a.sp.epipolar != 0, split = a.n_units > a.n_search;
+    if (form == 1)
+        return split ? (epi ? search_kernel<2, true, false, false, false, true, 1> : search_kernel<2, false, false, false, false, true, 1>)
+                     : (epi ? search_kernel<2, true, false, false, false, false, 1> : search_kernel<2, false, false, false, false, false, 1>);
+    return split ? (epi ? search_kernel<2, true, false, false, false, true, 2> : search_kernel<2, false, false, false, false, true, 2>)
+                 : (epi ? search_kernel<2, true, false, false, false, false, 2> : search_kernel<2, false, false, false, false, false, 2>);
+}
+
 static void (*search_fn(const BatchArgs &a))(BatchArgs) {
     const bool epi = a.sp.epipolar != 0, eprej = a.sp.epipole_px > 0.0f, dense = a.sp.dense_min > 0;
+    if (search_variants(a) && a.qpl == 4) return entry_fn(a, 2);
     if (search_variants(a) && a.n_units > a.n_search) {  // split pairs: their own instances
         if (a.qpl == 3) return epi ? search_kernel<3, true, false, false, false, true> : search_kernel<3, false, false, false, false, true>;
         if (a.qpl == 1) return epi ? search_kernel<1, true, false, false, false, true> : search_kernel<1, false, false, false, false, true>;
@@ -2584,7 +2789,7 @@ void search_form(BatchArgs &a) {
         a.qpl = 2;
         a.persist = 0;
     }
-    if (a.qpl == 3) a.persist = 0;  // the per-lane form has no persistent instance
+    if (a.qpl == 3 || a.qpl == 4) a.persist = 0;  // the per-lane and entry forms have no persistent instance
     if (a.n_units > a.n_search) a.persist = 0;  // nor do split pairs
 }
 
@@ -2605,6 +2810,23 @@ cudaError_t launch_search(const BatchArgs &a, int ctas, cudaStream_t s, int prio
     const size_t smem = search_smem_bytes(a.sn);
     cudaError_t e = cudaFuncSetAttribute(search_fn(a), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (a.qpl == 4 && search_variants(a)) {
+        // the entry form: join (one CTA per launch entry), evaluation (a grid stride over the
+        // entries, eight CTAs per SM), finalize (one CTA per launch entry)
+        void (*join)(BatchArgs) = entry_fn(a, 1), (*fin)(BatchArgs) = entry_fn(a, 2);
+        static int sms = 0;
+        if (!sms) {
+            int d = 0;
+            if ((e = cudaGetDevice(&d)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d)))
+                return e;
+        }
+        if ((e = cudaFuncSetAttribute(join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+            (e = launch_prio(join, dim3(a.n_units), dim3(kSearchThreads), smem, s, prio, a)))
+            return e;
+        void (*ev)(BatchArgs) = a.sp.epipolar ? eval_kernel<true> : eval_kernel<false>;
+        if ((e = launch_prio(ev, dim3(8 * sms), dim3(kEvalThreads), 0, s, prio, a))) return e;
+        return launch_prio(fin, dim3(a.n_units), dim3(kSearchThreads), smem, s, prio, a);
+    }
     const uint32_t grid = a.persist ? (uint32_t)std::max(1, std::min(ctas, (int)a.n_units)) : a.n_units;
     return launch_prio(search_fn(a), dim3(grid), dim3(kSearchThreads), smem, s, prio, a);
 }

@@ -306,6 +306,15 @@ struct BatchArgs {
     uint32_t *pdone;
     uint32_t n_units;             // search launch entries (pairs, split pairs twice)
     uint32_t dsplit;              // dense kernel CTAs per search item
+    // entry form (qpl 4): a join pass lists every (query, candidate) entry of the batch in ents
+    // (launch entry, query position << 16 | target position), counted by *nents (reset by the
+    // prep kernel); each entry is evaluated by its own thread, folding into its query's
+    // (best key, second) in dres; a finalize pass reads those.  Entries past ent_cap are not
+    // written and their pair is flagged in povf (its finalize searches it in rounds instead).
+    uint2 *ents;
+    uint32_t *nents;
+    uint32_t ent_cap;
+    uint32_t *povf;
 };
 
 }  // namespace tmap

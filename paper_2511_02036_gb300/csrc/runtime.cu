@@ -614,7 +614,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok, &pwin, &pacc, &pdone})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok, &pwin, &pacc, &pdone, &ents, &povf})
         b->release();
     h_stage.release();
     h_out.release();
@@ -994,6 +994,12 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     int fuse_n = 0;
     for (uint32_t i = B.n_search_items; i < items.size(); ++i) fuse_n = std::max(fuse_n, (int)items[i].nt);
     B.fsn = (uint32_t)std::max(16, (fuse_n + 15) & ~15);
+    // the entry form's list (batches whose search has every form): room for four candidates a
+    // query visit (at least 1 M), unless a test fixes it; the tuner grows it to a batch's count
+    const bool entry_ok = sp.mode != TM_MODE_PER_PAIR && !(sp.epipole_px > 0.0f) && sp.dense_min <= 0;
+    const uint32_t ent_cap = !entry_ok ? 0u
+        : c->entry_cap > 0 ? (uint32_t)std::min<long long>(c->entry_cap, kEntryCapMax)
+        : (uint32_t)std::min<size_t>(std::max<size_t>(B.ent_cap, std::max<size_t>(size_t(1) << 20, 4 * dq)), kEntryCapMax);
     // device buffers
     const size_t ni = std::max<size_t>(1, items.size());
     const size_t nm = std::max<int>(1, mps.n);
@@ -1009,16 +1015,18 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.mp_pos.reserve(nm * 12)) || (e = B.mp_normal.reserve(nm * 12)) ||
         (e = B.mp_desc.reserve(nm * 32)) || (e = B.mp_min.reserve(nm * 4)) ||
         (e = B.mp_max.reserve(nm * 4)) || (e = B.mp_skip.reserve(nm)) ||
-        (sp.dense_min != 0 && (e = B.dres.reserve(std::max<size_t>(1, dq) * 8))) ||
+        (e = B.dres.reserve(std::max<size_t>(1, dq) * 8)) ||
         (e = B.work.reserve(16)) ||
         (e = B.acc.reserve(std::max<size_t>(1, dq) * 8)) ||
         (e = B.pconst.reserve(nsi * kPairConst * 4)) || (e = B.pwords.reserve(std::max<uint32_t>(64, tq) / 32 * 8)) ||
         (e = B.pepos.reserve(std::max<uint32_t>(64, tq) * 2)) ||
         (e = B.pwin.reserve(std::max<uint32_t>(64, tq) * 4)) || (e = B.pacc.reserve(nsi * 8)) ||
-        (e = B.pdone.reserve(nsi * 4)) ||
+        (e = B.pdone.reserve(nsi * 4)) || (e = B.povf.reserve(nsi * 4)) ||
+        (entry_ok && (e = B.ents.reserve(size_t(ent_cap) * 8))) ||
         (tri && ((e = B.points.reserve(std::max<size_t>(1, B.search_pad) * 12)) ||
                  (e = B.point_ok.reserve(std::max<size_t>(1, B.search_pad))))))
         return cuda_fail(e, "batch buffers");
+    B.ent_cap = ent_cap;
     if (B.pointers() != before && (B.graph || B.graph_timed)) {
         if (B.graph) cudaGraphExecDestroy(B.graph);
         if (B.graph_timed) cudaGraphExecDestroy(B.graph_timed);
@@ -1127,7 +1135,7 @@ std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, acc.p, pconst.p,
             pwords.p, pepos.p, work.p, points.p,
-            point_ok.p, pwin.p, pacc.p, pdone.p};
+            point_ok.p, pwin.p, pacc.p, pdone.p, ents.p, povf.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).
@@ -1173,6 +1181,11 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
     KA.l2_prefetch = (uint32_t)(c->force_prefetch >= 0 ? c->force_prefetch : B.knobs.prefetch);
     if (B.user_dense_min < 0) KA.sp.dense_min = B.knobs.dense_min;
     KA.dsplit = std::max(1u, B.dsplit_base / (uint32_t)std::max(1, B.knobs.dsplit_div));
+    if (KA.qpl == 4 && !B.ent_cap) KA.qpl = 2;  // (the batch has no entry list)
+    KA.ents = static_cast<uint2 *>(B.ents.p);
+    KA.nents = static_cast<uint32_t *>(B.work.p) + 1;
+    KA.ent_cap = B.ent_cap;
+    KA.povf = static_cast<uint32_t *>(B.povf.p);
     search_form(KA);
     const int per_sm = search_ctas_per_sm(KA);
     if (per_sm < 1) return fail(TM_ERR_INVALID_ARG, "search kernel does not fit");
@@ -1366,7 +1379,7 @@ void tmap::load_tuning(tm_ctx *c, const char *path) {
     }
     while (fscanf(f, "%d %d %d %d %d %d %d", &key, &k.qpl, &k.persist, &k.prefetch, &k.bprio, &k.dense_min,
                   &k.dsplit_div) == 7)
-        if (k.qpl >= 1 && k.qpl <= 3 && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
+        if (k.qpl >= 1 && k.qpl <= 4 && k.dsplit_div >= 1) c->tuned_knobs[key] = k;
     fclose(f);
 }
 
@@ -1422,6 +1435,13 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     const bool forms = dense_mode != 1 && !epi_rej;
     const int key = (((density_key(hc[0], batch_queries(c, B, steps)) * 2 +
                        ((int)B.n_search_items < c->num_sms ? 1 : 0)) * 3 + dense_mode) * 2) + (epi_rej ? 1 : 0);
+    // the entry form's list: room for this batch's entries (its comparisons), so that a plan
+    // that takes the form never falls back to rounds
+    if (forms && B.ent_cap && !c->entry_cap && hc[0] > B.ent_cap) {
+        const size_t want = std::min<size_t>(size_t(hc[0] + hc[0] / 16), size_t(kEntryCapMax));
+        if ((e = B.ents.reserve(want * 8))) return cuda_fail(e, "entry list");
+        B.ent_cap = (uint32_t)want;
+    }
     auto it = c->tuned_knobs.find(key);
     if (it != c->tuned_knobs.end()) {
         B.knobs = it->second;
@@ -1457,7 +1477,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         switch (knob) {
             case 0:
                 if (!c->force_qpl && forms)
-                    for (int qf : {2, 1, 3})
+                    for (int qf : {2, 1, 3, 4})
                         if (qf != best.qpl) { k.qpl = qf; alts.push_back(k); }
                 break;
             case 1: if (c->force_persist < 0 && forms) { k.persist = !best.persist; alts.push_back(k); } break;
@@ -1867,8 +1887,12 @@ extern "C" tm_status tm_debug_set(tm_ctx *c, int32_t what, int64_t value) {
             c->branch_prio = (int)value;
             return TM_OK;
         case TM_DEBUG_QUERIES_PER_LANE:
-            if (value < 0 || value > 3) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: group form must be 0, 1, 2 or 3");
+            if (value < 0 || value > 4) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: group form must be 0 .. 4");
             c->force_qpl = (int)value;
+            return TM_OK;
+        case TM_DEBUG_ENTRY_CAP:
+            if (value < 0 || value > kEntryCapMax) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: entry capacity out of range");
+            c->entry_cap = value;
             return TM_OK;
         case TM_DEBUG_PERSISTENT:
             if (value < -1 || value > 1) return fail(TM_ERR_INVALID_ARG, "tm_debug_set: persistent must be -1, 0 or 1");
@@ -2021,8 +2045,9 @@ extern "C" tm_status tm_plan_get_tuning(tm_plan *P, tm_plan_tuning *out) {
     if (!P || !out) return fail(TM_ERR_INVALID_ARG, "tm_plan_get_tuning: null argument");
     const BatchArgs &A = P->B.args;
     const bool fused = P->B.sp.mode != TM_MODE_PER_PAIR;
-    out->queries_per_warp = fused ? 32 * (int)(A.qpl == 3 ? 2 : A.qpl) : 0;
+    out->queries_per_warp = fused ? 32 * (int)(A.qpl >= 3 ? 2 : A.qpl) : 0;
     out->per_lane = fused && A.qpl == 3 ? 1 : 0;
+    out->entry_form = fused && A.qpl == 4 ? 1 : 0;
     out->persistent = fused ? (int)A.persist : 0;
     out->l2_prefetch = fused ? (int)A.l2_prefetch : 0;
     out->branch_priority = fused ? (P->ctx->branch_prio >= 0 ? P->ctx->branch_prio : P->B.knobs.bprio) : 0;

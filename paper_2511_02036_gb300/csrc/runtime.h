@@ -16,6 +16,9 @@
 
 namespace tmap {
 
+// Largest entry list of the entry form (entries of 8 bytes: 512 MB).
+constexpr long long kEntryCapMax = 1LL << 26;
+
 // A host-side NVTX range over a scope: the library's calls and their stages appear on the
 // timeline of a profiler attached to the process (with none attached a push costs a few ns).
 struct Range {
@@ -70,8 +73,9 @@ struct Knobs {
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
         counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, work, points,
-        point_ok, pwin, pacc, pdone;
+        point_ok, pwin, pacc, pdone, ents, povf;
     uint32_t n_units = 0;          // search launch entries (split pairs twice)
+    uint32_t ent_cap = 0;          // entry form: capacity of ents (entries; 0 = form not prepared)
     PinBuf h_stage, h_out;
     IngestStage ingest;            // keyframes entering the store with this batch
     IngestArgs ingest_args{};
@@ -222,6 +226,8 @@ struct tm_ctx {
     int force_prefetch = -1;              // test hook: search CTAs' L2 prefetch (-1 = tuned)
     int branch_prio = -1;                 // test hook: 0 search branch first, 1 store, 2 equal, -1 tuned
     int force_qpl = 0;                    // test hook: queries per lane of a search group (0 = tuned)
+    long long entry_cap = 0;              // test hook: entry list capacity of the entry form (0 = sized
+                                          // from the batch; TM_DEBUG_ENTRY_CAP)
     int force_persist = -1;               // test hook: persistent search CTAs (-1 = tuned)
     int split_min = 768;                  // pairs with at least this many queries take two search
                                           // CTAs in batches of fewer pairs than SMs; < 0: in any

@@ -1,6 +1,6 @@
 """The bounds-checking build (-DTM_DEBUG_BOUNDS): every index the kernels take from data is
 checked against its array and the first failure is recorded.  Small workloads through every
-kernel (ingest in the store and inside a batch, search in both forms, dense tensor-core blocks,
+kernel (ingest in the store and inside a batch, search in both forms and the entry form, dense tensor-core blocks,
 backward and forward fusion, triangulation, copy) must leave no failed check and give the
 oracle's results.  Runs in a child process that loads the variant through TM_LIBRARY."""
 
@@ -62,6 +62,18 @@ with tm.Context(w["cam"], max_kp=2048) as ctx:
         if with_new:
             ctx.remove_keyframes(new)
         assert site() == (0, 1), (mode, with_new, site())
+    # the entry form (join, one thread per entry, finalize), its list sized from the batch and
+    # too small (the overflowing pairs searched in rounds by their finalize)
+    from paper_2511_02036_gb300 import _lib as L
+    ctx.remove_keyframes(new)  # (stored by the per-pair pass above)
+    ctx.debug_set(L.TM_DEBUG_QUERIES_PER_LANE, 4)
+    for cap in (0, 100):
+        ctx.debug_set(L.TM_DEBUG_ENTRY_CAP, cap)
+        res = ctx.batch_run(steps, new=(new, [w["frames"][i] for i in new]))
+        check_pairs(res.pairs, exp_pairs)
+        check_pairs(res.fuses, exp_fuse)
+        ctx.remove_keyframes(new)
+        assert site() == (0, 1), ("entry form", cap, site())
 
 d = W.make_cfg3b(n_nbrs=4)
 st = d["steps"][0]

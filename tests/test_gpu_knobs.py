@@ -80,7 +80,8 @@ def force(tm, ctx, qpl=None, persist=None, prefetch=None, bprio=None):
         ctx.debug_set(L.TM_DEBUG_BRANCH_PRIORITY, bprio)
 
 
-@pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))) + [(3, 0, 0), (3, 0, 1)])
+@pytest.mark.parametrize("qpl,persist,prefetch", list(itertools.product((1, 2), (0, 1), (0, 1))) +
+                         [(3, 0, 0), (3, 0, 1), (4, 0, 0)])
 def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
     from paper_2511_02036_gb300 import _lib as L
     w, exp = batch
@@ -91,6 +92,7 @@ def test_search_knobs_match_oracle(tm, batch, qpl, persist, prefetch):
         with ctx.plan(steps_of(w)) as plan:
             t = plan.tuning()
             assert t["queries_per_warp"] == 32 * min(qpl, 2) and t["per_lane"] == (qpl == 3)
+            assert t["entry_form"] == (qpl == 4)
             assert t["persistent"] == persist and t["l2_prefetch"] == prefetch
             if persist:
                 assert 1 <= t["search_ctas"] <= t["search_units"]
@@ -113,7 +115,7 @@ def test_branch_priority_matches_oracle(tm, batch, bprio):
             assert_same(plan.results(), exp)
 
 
-@pytest.mark.parametrize("qpl", [1, 2, 3])
+@pytest.mark.parametrize("qpl", [1, 2, 3, 4])
 def test_variant_gates_ignore_persistent(tm, qpl):
     """With the epipole rejection on, the search takes its general instance (rounds, 64-query
     groups): the persistent and per-lane requests are set aside (reported as 0), the results
@@ -126,13 +128,13 @@ def test_variant_gates_ignore_persistent(tm, qpl):
         force(tm, ctx, qpl=qpl, persist=1)
         with ctx.plan(steps_of(w), sp=sp) as plan:
             t = plan.tuning()
-            assert t["persistent"] == 0 and t["per_lane"] == 0
+            assert t["persistent"] == 0 and t["per_lane"] == 0 and t["entry_form"] == 0
             plan.run()
             assert_same(plan.results(), exp)
 
 
 @pytest.mark.parametrize("split_min,qpl,persist", [(0, 2, 0), (-1, 2, 0), (-1, 1, 1), (-1, 3, 0), (-700, 2, 1), (-2048, 2, 0),
-                                                    (768, 2, 0)])
+                                                    (768, 2, 0), (-1, 4, 0), (-700, 4, 0)])
 def test_split_pairs_match_oracle(tm, batch, split_min, qpl, persist):
     """Pairs split over two search CTAs (each half of the query groups, winners in global
     memory, the last to finish finalizing): never (0), every pair (-1), most, none in range,
@@ -256,3 +258,31 @@ def test_tuning_cache_keyed_by_dense_mode(tm, tmp_path, monkeypatch):
                     assert t["dense_min"] == 0 and t["l2_prefetch"] == 1 and t["per_lane"] == 1
                 plan.run()
                 assert_same(plan.results(), expected(w, sp))
+
+
+@pytest.mark.parametrize("cap,split_min", [(1, 0), (300, 0), (2000, -700), (0, 0)])
+@pytest.mark.parametrize("epipolar", [True, False])
+def test_entry_form_overflow_matches_oracle(tm, batch, cap, split_min, epipolar):
+    """The entry form with an entry list too small for the batch (1 or 300 entries: the pairs
+    whose entries did not fit are searched in rounds by their finalize, the others from the
+    list; 2000 with split pairs) and sized from the batch (0), with and without the epipolar
+    gate: equal to the oracle, replay after replay (the prep kernel resets the count and the
+    flags), and the one-shot batch too."""
+    from paper_2511_02036_gb300 import _lib as L
+    w = batch[0]
+    sp = tm.SearchParams(epipolar=epipolar)
+    exp = expected(w, sp)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        ctx.debug_set(L.TM_DEBUG_SPLIT_MIN, split_min)
+        ctx.debug_set(L.TM_DEBUG_ENTRY_CAP, cap)
+        force(tm, ctx, qpl=4)
+        with ctx.plan(steps_of(w), sp=sp) as plan:
+            assert plan.tuning()["entry_form"] == 1
+            for _ in range(3):
+                plan.run()
+                assert_same(plan.results(), exp)
+        assert_same(ctx.batch_run(steps_of(w), sp=sp), exp)
+    with pytest.raises(tm.TMError):
+        with tm.Context(w["cam"], max_kp=2048) as ctx:
+            ctx.debug_set(L.TM_DEBUG_ENTRY_CAP, -1)
