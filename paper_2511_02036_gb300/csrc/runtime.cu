@@ -1452,19 +1452,36 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // a choice is timed as the plan will run it: captured into a graph, replayed once to warm
+    // up, then the fastest of up to 16 replays (at least ~1 ms of them, so that a small
+    // batch's choices are told apart), each between events on the stream
     auto time_of = [&](const Knobs &k, float &ms) -> tm_status {
         B.knobs = k;
-        tm_status r = enqueue_fused(c, B, 256, c->def_lanes, s);  // warm-up
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (ce) return cuda_fail(ce, "tuning capture");
+        tm_status r = enqueue_fused(c, B, 256, c->def_lanes, c->capture_stream);
+        ce = cudaStreamEndCapture(c->capture_stream, &g);
+        if (!r && ce) r = cuda_fail(ce, "tuning capture");
+        if (!r && (ce = cudaGraphInstantiate(&x, g, 0))) r = cuda_fail(ce, "tuning graph");
+        if (g) cudaGraphDestroy(g);
+        if (r) return r;
         ms = 0.0f;
-        for (int rep = 0; rep < 3 && !r; ++rep) {
-            cudaEventRecord(e0, s);
-            if ((r = enqueue_fused(c, B, 256, c->def_lanes, s))) break;
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float t = 0.0f;
-            cudaEventElapsedTime(&t, e0, e1);
-            ms += t;
+        float t = 0.0f;
+        for (int rep = 0, reps = 2; rep < reps; ++rep) {
+            if ((ce = cudaEventRecord(e0, s)) || (ce = cudaGraphLaunch(x, s)) || (ce = cudaEventRecord(e1, s)) ||
+                (ce = cudaEventSynchronize(e1)) || (ce = cudaEventElapsedTime(&t, e0, e1))) {
+                r = cuda_fail(ce, "tuning replay");
+                break;
+            }
+            if (rep == 0) {  // the warm-up sets how many replays follow
+                reps = 1 + std::max(3, std::min(16, (int)std::ceil(1.0f / std::max(t, 1e-3f))));
+                continue;
+            }
+            ms = rep == 1 ? t : std::min(ms, t);
         }
+        cudaGraphExecDestroy(x);
         return r;
     };
     Knobs best{};
@@ -1972,7 +1989,9 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         }
         // search (when there are pairs), fuse (when there are map points), copy, ingest (when
         // keyframes enter with the batch)
-        P->kernels_per_run = (P->B.n_search_items ? 2 : 0) + (P->B.n_items > P->B.n_search_items ? 1 : 0) +
+        // (the entry form's search is three launches: join, evaluation, finalize)
+        P->kernels_per_run = (P->B.n_search_items ? (P->B.args.qpl == 4 ? 4 : 2) : 0) +
+                             (P->B.n_items > P->B.n_search_items ? 1 : 0) +
                              1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0) +
                              (P->B.n_search_items && P->B.args.triangulate ? 1 : 0);
     } else {
