@@ -76,7 +76,8 @@ def test_plan_graph_replay(tm, small_batch):
         load_all(ctx, w)
         with ctx.plan(steps_of(w)) as plan:
             info = plan.info()
-            assert info["kernels_per_run"] == 4 and info["ctas"] >= 1  # prep, search, fuse, copy
+            # prep, search (join, evaluation, finalize in the entry form), fuse, copy
+            assert info["kernels_per_run"] == 4 + 2 * plan.tuning()["entry_form"] and info["ctas"] >= 1
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -294,7 +295,8 @@ def test_new_keyframes_enter_with_the_batch(tm, small_batch):
         with pytest.raises(tm.TMError):
             ctx.keyframe_size(new_ids[0])
         with ctx.plan(steps_of(w), new=new) as plan:
-            assert plan.info()["kernels_per_run"] == 5  # ingest, prep, search, fuse, copy
+            # ingest, prep, search (three launches in the entry form), fuse, copy
+            assert plan.info()["kernels_per_run"] == 5 + 2 * plan.tuning()["entry_form"]
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -721,7 +723,8 @@ def test_triangulation_plan_new_keyframes(tm, small_batch):
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
         with ctx.plan(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids]), tri=tm.TriParams()) as plan:
-            assert plan.info()["kernels_per_run"] == 6  # ingest, prep, search, fuse, copy, triangulation
+            # ingest, prep, search (three launches in the entry form), fuse, copy, triangulation
+            assert plan.info()["kernels_per_run"] == 6 + 2 * plan.tuning()["entry_form"]
             for _ in range(2):
                 plan.run()
                 r = plan.results()
