@@ -457,8 +457,9 @@ tm_status tm_plan_get_tuning(tm_plan *plan, tm_plan_tuning *out);
  * CUDA events recorded inside its graph (all zero otherwise).  The search branch (prep kernel:
  * per-pair F and eligibility; search kernel: one CTA per pair, all of Sec. IV-C) runs beside
  * the store branch (ingest -> fusion): ms[0] search kernel (between events recorded right
- * before and after it on its stream), ms[1] ingest, ms[2] fusion kernel, ms[3] offsets + copy
- * after both branches (and the triangulation kernel when the batch triangulates), ms[4] the
+ * before and after it on its stream), ms[1] ingest, ms[2] fusion kernel, ms[3] from the later of
+ * the search and fusion kernels' ends to the end of the run: each branch's offsets + copy of its
+ * own records (and the triangulation kernel after the search's, when the batch triangulates), ms[4] the
  * dense-block kernel that precedes the search kernel (dense_min > 0; else 0), ms[5] the prep
  * kernel.  Waits for the run to finish. */
 #define TM_PLAN_STAGES 6

@@ -646,14 +646,15 @@ __device__ __forceinline__ bool staged_wait(uint64_t *bar, uint64_t *never, cons
 
 // ------------------------------------------------------------------------- batch pipeline
 //
-// A batch runs as two branches of a graph, joined before copy:
+// A batch runs as two branches of a graph, each ending with the compaction of its own records:
 //   search   search_kernel, one CTA per pair (largest first): everything of Sec. IV-C for the
 //            pair, with the neighbour's node index, the winners, the accepted matches and the
 //            results in shared memory.  It reads a new keyframe from its staged arrays, so it
-//            runs beside the ingest.
+//            runs beside the ingest.  Then copy_kernel over the search items.
 //   store    ingest_kernel, then fuse_kernel (CTA per 512 map points of a step: projection
-//            gates, grid window in the staged target, best Hamming).
-//   copy     per-item counts -> offsets, per-item regions -> dense output, comparison totals.
+//            gates, grid window in the staged target, best Hamming), then copy_kernel over the
+//            fusion items (per-item counts -> offsets, per-item regions -> dense output,
+//            comparison totals).
 
 struct FuseK {
     float R[9], t[3], O[3], scale[kLevels], thr[kLevels];
@@ -2291,7 +2292,8 @@ __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
     __shared__ TriView V[2];
     __shared__ float sig2[kLevels], scl[kLevels];
     const uint32_t i = blockIdx.x;  // search item, logical order
-    const uint32_t o0 = A.offsets[i], o1 = A.offsets[i + 1];
+    // (the search part's total follows the item offsets)
+    const uint32_t o0 = A.offsets[i], o1 = A.offsets[i + 1 < A.n_search ? i + 1 : A.n_items];
     if (o0 == o1) return;
     const WorkItem w = A.items[i];
     const KfView Q = KfView::at(w.q, A.L), T = KfView::at(w.t, A.L);
@@ -2378,16 +2380,22 @@ __global__ void __launch_bounds__(128) tri_kernel(BatchArgs A) {
     }
 }
 
-// Per-item counts -> offsets, and the per-item regions gathered into the dense output.  Every
-// CTA scans the counts itself (a few thousand words, read from L2 once into registers, kept
-// with their offsets in shared memory), segment by segment, so that no CTA waits for another;
-// CTA 0 publishes the offsets, the comparison totals (search, fusion) and the status of the
-// run.  Warps copy items as 32-bit words (an output record is three words), so that a warp's
-// loads and stores are contiguous.
+// Per-item counts -> offsets, and the per-item regions gathered into the dense output, for one
+// part of the batch's items: part 0 the search items [0, n_search), launched on the search
+// branch right after the search; part 1 the fusion items [n_search, n_items), on the store
+// branch right after the fusion, its records from dense record out0 on (a fixed base past the
+// search part's room), so that neither waits for the other branch.  Offsets are relative to
+// the part's base; offsets[n_items + part] is the part's total.  Every CTA scans the part's
+// counts itself (a few thousand words, read from L2 once into registers, kept with their
+// offsets in shared memory), segment by segment, so that no CTA waits for another; CTA 0
+// publishes the offsets, the part's comparison totals (search; fusion and forward fusion) and
+// its status word (counters[2 + part]).  Warps copy items as 32-bit words (an output record is
+// three words), so that a warp's loads and stores are contiguous.
 constexpr int kCopyThreads = 1024;
 constexpr int kCopyPer = 4;                          // counts per thread and segment
 constexpr int kCopySeg = kCopyPer * kCopyThreads;    // items per scan segment
-__global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A, uint32_t i0, uint32_t i1, uint32_t out0,
+                                                             uint32_t part) {
     __shared__ uint32_t offs[kCopySeg], cnts[kCopySeg];
     __shared__ uint32_t wtot[32];
     const int tid = threadIdx.x, bs = blockDim.x;
@@ -2400,9 +2408,9 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
     uint32_t flags = 0;
     static_assert(sizeof(Out3) == 12, "three words per output record");
     const uint32_t *pw = reinterpret_cast<const uint32_t *>(A.padded);
-    uint32_t *dw = reinterpret_cast<uint32_t *>(A.dense);
-    for (uint32_t s0 = 0; s0 < A.n_items; s0 += kCopySeg) {
-        const uint32_t ns = min((uint32_t)kCopySeg, A.n_items - s0);
+    uint32_t *dw = reinterpret_cast<uint32_t *>(A.dense + out0);
+    for (uint32_t s0 = i0; s0 < i1; s0 += kCopySeg) {
+        const uint32_t ns = min((uint32_t)kCopySeg, i1 - s0);
         // thread t takes items cb .. cb + kCopyPer - 1 of the segment (contiguous, so that the
         // prefix sum runs in item order)
         const uint32_t cb = (uint32_t)tid * kCopyPer;
@@ -2474,12 +2482,15 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A) {
         if (tid == 0) {
             unsigned long long a = 0, b = 0, f = 0;
             for (uint32_t q = 0; q < nw; ++q) { a += csum[0][q]; b += csum[1][q]; f += csum[2][q]; }
-            A.ncmp[0] = a;
-            A.ncmp[1] = b;
-            A.ncmp[2] = f;
-            A.counters[2] = sflags ? kStatusTimeout : 0u;
-            A.offsets[A.n_items] = base;
-            if (A.work) *A.work = 0u;  // the persistent search of the next run starts over
+            if (part == 0) {
+                A.ncmp[0] = a;
+                if (A.work) *A.work = 0u;  // the persistent search of the next run starts over
+            } else {
+                A.ncmp[1] = b;
+                A.ncmp[2] = f;
+            }
+            A.counters[2 + part] = sflags ? kStatusTimeout : 0u;
+            A.offsets[A.n_items + part] = base;
         }
     }
 }
@@ -2877,8 +2888,10 @@ cudaError_t launch_int_rate(int mode, int ctas, int iters, uint32_t *sink, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s) {
-    copy_kernel<<<ctas, kCopyThreads, 0, s>>>(a);
+cudaError_t launch_copy(const BatchArgs &a, int part, uint32_t out0, int ctas, cudaStream_t s) {
+    const uint32_t i0 = part == 0 ? 0u : a.n_search, i1 = part == 0 ? a.n_search : a.n_items;
+    if (i0 >= i1) return cudaSuccess;
+    copy_kernel<<<ctas, kCopyThreads, 0, s>>>(a, i0, i1, out0, (uint32_t)part);
     return cudaGetLastError();
 }
 

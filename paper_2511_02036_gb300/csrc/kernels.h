@@ -33,7 +33,8 @@ cudaError_t launch_search(const BatchArgs &a, int ctas, cudaStream_t s, int prio
 size_t dense_smem_bytes();
 cudaError_t launch_dense(const BatchArgs &a, cudaStream_t s, int prio = 0);
 cudaError_t launch_fuse(const BatchArgs &a, cudaStream_t s, int prio = 0);
-cudaError_t launch_copy(const BatchArgs &a, int ctas, cudaStream_t s);
+// Part 0: the search items' records from dense record 0; part 1: the fusion items' from out0.
+cudaError_t launch_copy(const BatchArgs &a, int part, uint32_t out0, int ctas, cudaStream_t s);
 // Bounds-checking build: the first failed index check's site (0: none), optionally reset;
 // enabled = false and site = 0 in the normal build.
 cudaError_t debug_bounds(bool reset, uint32_t *site, bool *enabled);

@@ -1007,7 +1007,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     cudaError_t e;
     if ((e = B.items.reserve(align128(ni * sizeof(WorkItem)) + nun * sizeof(WorkItem))) ||
         (e = B.counts.reserve(ni * 4)) || (e = B.item_cmp.reserve(ni * 4)) ||
-        (e = B.offsets.reserve((ni + 1) * 4)) ||
+        (e = B.offsets.reserve((ni + 2) * 4)) ||
         (e = B.ncmp.reserve(24)) || (e = B.counters.reserve(16)) ||
         (e = B.padded.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
         (e = B.dense.reserve(std::max<size_t>(1, pad) * sizeof(Out3))) ||
@@ -1166,10 +1166,12 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 //           from their staged arrays, so it runs beside their ingest (unless a neighbour enters
 //           with the batch: then it starts after the ingest);
 //   store:  ingest of new keyframes -> fusion (needs their grids), on s, at low priority;
-// joined before copy (offsets, dense output, comparison totals, status).  `threads` = threads
-// per search CTA.  With `timed`, events E0..E5 mark: start, search done, ingest done, fusion
-// done, copy done, search start (on the search branch, right before the kernel); E6 (with dense
-// node blocks) between the dense and the search kernel.
+// each branch then compacts its own records (offsets, dense output, comparison totals, status:
+// the search part from record 0, then the triangulation of its matches; the fusion part from
+// record search_pad), and the store branch awaits the search branch.  `threads` = threads per
+// search CTA.  With `timed`, events E0..E5 mark: start, search done, ingest done, fusion done,
+// both copies done, search start (on the search branch, right before the kernel); E6 (with
+// dense node blocks) between the dense and the search kernel.
 tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cudaStream_t s, bool timed) {
     cudaError_t e;
     B.threads = threads;
@@ -1219,17 +1221,21 @@ tm_status tmap::enqueue_fused(tm_ctx *c, BatchBuf &B, int threads, int lanes, cu
         (e = launch_prep(B.args, B.paux, sp_)) || (e = mark(7, B.paux)) ||
         (e = launch_dense(B.args, B.paux, sp_)) ||
         (B.args.sp.dense_min > 0 && B.n_search_items > 0 && (e = mark(6, B.paux))) ||
-        (e = launch_search(B.args, B.ctas, B.paux, sp_)) ||
-        (e = mark(1, B.paux)) || (e = cudaEventRecord(B.join, B.paux)))
+        (e = launch_search(B.args, B.ctas, B.paux, sp_)) || (e = mark(1, B.paux)))
         return cuda_fail(e, "search kernel");
+    // each branch compacts its own records (about one warp per item, 32 per CTA, at most one
+    // CTA per SM): the search part on the search branch (then the triangulation of its
+    // matches), the fusion part on the store branch, from record search_pad on
+    const uint32_t nfi = B.n_items - B.n_search_items;
+    auto copy_ctas = [&](uint32_t n) { return (int)std::max<uint32_t>(1, std::min<uint32_t>((n + 31) / 32, c->num_sms)); };
+    if ((e = launch_copy(B.args, 0, 0u, copy_ctas(B.n_search_items), B.paux)) || (e = launch_tri(B.args, B.paux)) ||
+        (e = cudaEventRecord(B.join, B.paux)))
+        return cuda_fail(e, "search copy");
     if (mp_async && (e = cudaStreamWaitEvent(s, B.mready, 0))) return cuda_fail(e, "map points");
-    if ((B.n_items > B.n_search_items && (e = launch_fuse(B.args, s, st_))) || (e = mark(3, s)) ||
+    if ((nfi && (e = launch_fuse(B.args, s, st_))) || (e = mark(3, s)) ||
+        (e = launch_copy(B.args, 1, (uint32_t)B.search_pad, copy_ctas(nfi), s)) ||
         (e = cudaStreamWaitEvent(s, B.join, 0)))
         return cuda_fail(e, "fusion kernel");
-    // copy: about one warp per item (32 per CTA), at most one CTA per SM
-    if ((e = launch_copy(B.args, (int)std::max<uint32_t>(1, std::min<uint32_t>((B.n_items + 31) / 32, c->num_sms)), s)))
-        return cuda_fail(e, "copy kernel");
-    if ((e = launch_tri(B.args, s))) return cuda_fail(e, "triangulation kernel");
     if ((e = mark(4, s))) return cuda_fail(e, "event");
     return TM_OK;
 }
@@ -1261,6 +1267,12 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
                                    offs + i, ncmp, lanes, s, w.mdepth)))
             return cuda_fail(e, "plain pair");
     }
+    // the search part's total; the fusion part's records from record search_pad on, its offsets
+    // relative to that (the layout of the fused form's two copies)
+    if ((e = cudaMemcpyAsync(offs + B.n_items, scr.running, 4, cudaMemcpyDeviceToDevice, s)) ||
+        (e = cudaMemsetAsync(scr.running, 0, 4, s)))
+        return cuda_fail(e, "plain search total");
+    Out3 *fdense = B.args.dense + B.search_pad;
     for (int k = 0; k < B.n_steps; ++k) {
         const int f0 = B.step_fuse_item[k], f1 = B.step_fuse_item[k + 1];
         if (f0 == f1) continue;
@@ -1272,7 +1284,7 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
                                    B.args.mp_normal + 3 * (size_t)begin, B.args.mp_desc + 2 * (size_t)begin,
                                    B.args.mp_min + begin, B.args.mp_max + begin,
                                    B.args.mp_skip ? B.args.mp_skip + begin : nullptr, (int)n, B.args.fp,
-                                   c->camc, res, B.args.dense, scr.running, offs + f0, ncmp + 1, s)))
+                                   c->camc, res, fdense, scr.running, offs + f0, ncmp + 1, s)))
             return cuda_fail(e, "plain fuse");
     }
     for (int p = 0; p < B.n_pairs && B.any_fwd; ++p) {  // forward fusion, pair by pair
@@ -1286,10 +1298,10 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
                                    B.args.mp_normal + 3 * (size_t)begin, B.args.mp_desc + 2 * (size_t)begin,
                                    B.args.mp_min + begin, B.args.mp_max + begin,
                                    w.skip != kNone ? B.args.masks + w.skip : nullptr, (int)n, B.args.fp,
-                                   c->camc, res, B.args.dense, scr.running, offs + f0, ncmp + 2, s)))
+                                   c->camc, res, fdense, scr.running, offs + f0, ncmp + 2, s)))
             return cuda_fail(e, "plain forward fuse");
     }
-    if ((e = cudaMemcpyAsync(offs + B.n_items, scr.running, 4, cudaMemcpyDeviceToDevice, s)))
+    if ((e = cudaMemcpyAsync(offs + B.n_items + 1, scr.running, 4, cudaMemcpyDeviceToDevice, s)))
         return cuda_fail(e, "plain total");
     if ((e = launch_tri(B.args, s))) return cuda_fail(e, "triangulation kernel");
     return TM_OK;
@@ -1298,57 +1310,64 @@ tm_status tmap::enqueue_plain(tm_ctx *c, BatchBuf &B, int lanes, cudaStream_t s)
 // Download results of the last run of B into r (host offsets; matches host or device).
 tm_status tmap::fetch_results(tm_ctx *c, BatchBuf &B, tm_batch_result *r, cudaStream_t s, double *t_counts) {
     cudaError_t e;
-    const size_t nio = (size_t)B.n_items + 1;
+    // item offsets, then the search part's total and the fusion part's (each part's offsets
+    // relative to its base: record 0, record search_pad)
+    const size_t nio = (size_t)B.n_items + 2;
     if ((e = B.h_out.reserve((nio + 2) * 4 + 48))) return cuda_fail(e, "pinned results");
     uint32_t *ho = static_cast<uint32_t *>(B.h_out.p);
     unsigned long long *hc = reinterpret_cast<unsigned long long *>(ho + ((nio + 1) & ~size_t(1)));
     uint32_t *hs = reinterpret_cast<uint32_t *>(hc + 3);
     if ((e = cudaMemcpyAsync(ho, B.offsets.p, nio * 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(hc, B.ncmp.p, 24, cudaMemcpyDeviceToHost, s)) ||
-        (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 4, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hs, static_cast<uint32_t *>(B.counters.p) + 2, 8, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "results");
     *(t_counts ? t_counts : &c->t_counts) = tm_now();
-    if (B.sp.mode != TM_MODE_PER_PAIR && (*hs & kStatusTimeout))
+    // (a part with no items launched no copy: its words are not this run's)
+    const bool has_s = B.n_search_items > 0, has_f = B.n_items > B.n_search_items;
+    const uint32_t status = (has_s ? hs[0] : 0u) | (has_f ? hs[1] : 0u);
+    if (B.sp.mode != TM_MODE_PER_PAIR && (status & kStatusTimeout))
         return fail(TM_ERR_TIMEOUT, "a bulk copy into shared memory or a tensor-core product did not complete in time");
-    const uint32_t search_total = ho[B.n_search_items];
-    const uint32_t bwd_end = ho[B.n_search_items + B.n_bwd_items];
-    const uint32_t total = ho[B.n_items];
-    const size_t nf = bwd_end - search_total, nw = total - bwd_end;
+    const uint32_t search_total = has_s ? ho[B.n_items] : 0u, fuse_total = has_f ? ho[B.n_items + 1] : 0u;
+    // offset of a fusion item in the fusion part (its end for n_items)
+    auto foff = [&](int k) -> uint32_t { return k < (int)B.n_items ? ho[k] : fuse_total; };
+    const uint32_t bwd_end = foff((int)(B.n_search_items + B.n_bwd_items));
+    const size_t nf = bwd_end, nw = fuse_total - bwd_end;
     r->n_matches = search_total;
     r->n_fuse = nf;
     r->n_fwd = nw;
-    r->n_comparisons_search = hc[0];
-    r->n_comparisons_fuse = hc[1];
-    r->n_comparisons_fwd = hc[2];
+    r->n_comparisons_search = has_s ? hc[0] : 0ull;
+    r->n_comparisons_fuse = has_f ? hc[1] : 0ull;
+    r->n_comparisons_fwd = has_f ? hc[2] : 0ull;
     if (B.args.triangulate && (!r->points || !r->point_ok))
         return fail(TM_ERR_INVALID_ARG, "triangulation needs points and point_ok result buffers");
     if (search_total > r->match_cap || nf > r->fuse_cap || (nw && (!r->fwd || nw > r->fwd_cap)))
         return fail(TM_ERR_CAPACITY, "result buffers too small: %u matches (cap %zu), %zu fusion candidates (cap %zu), "
                     "%zu forward-fusion candidates (cap %zu)", search_total, r->match_cap, nf, r->fuse_cap, nw,
                     r->fwd ? r->fwd_cap : (size_t)0);
-    if (r->pair_offsets)
-        for (int p = 0; p <= B.n_pairs; ++p) r->pair_offsets[p] = (int32_t)ho[p];
+    if (r->pair_offsets) {
+        for (int p = 0; p < B.n_pairs; ++p) r->pair_offsets[p] = (int32_t)ho[p];
+        r->pair_offsets[B.n_pairs] = (int32_t)search_total;
+    }
     if (r->fuse_offsets)
-        for (int k = 0; k <= B.n_steps; ++k)
-            r->fuse_offsets[k] = (int32_t)(ho[B.step_fuse_item[k]] - search_total);
+        for (int k = 0; k <= B.n_steps; ++k) r->fuse_offsets[k] = (int32_t)foff(B.step_fuse_item[k]);
     if (r->fuse_offsets && B.n_steps > 0) {
         // steps without map points start where the next step starts
         for (int k = B.n_steps - 1; k >= 0; --k)
             if (B.step_fuse_item[k] == B.step_fuse_item[k + 1]) r->fuse_offsets[k] = r->fuse_offsets[k + 1];
     }
     if (r->fwd_offsets) {
-        for (int p = 0; p <= B.n_pairs; ++p) r->fwd_offsets[p] = (int32_t)(ho[B.pair_fwd_item[p]] - bwd_end);
+        for (int p = 0; p <= B.n_pairs; ++p) r->fwd_offsets[p] = (int32_t)(foff(B.pair_fwd_item[p]) - bwd_end);
         // pairs without forward items start where the next pair starts
         for (int p = B.n_pairs - 1; p >= 0; --p)
             if (B.pair_fwd_item[p] == B.pair_fwd_item[p + 1]) r->fwd_offsets[p] = r->fwd_offsets[p + 1];
     }
-    const Out3 *d = static_cast<const Out3 *>(B.dense.p);
+    const Out3 *d = static_cast<const Out3 *>(B.dense.p), *df = d + B.search_pad;
     if (search_total && (e = cudaMemcpyAsync(r->matches, d, search_total * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "matches download");
-    if (nf && (e = cudaMemcpyAsync(r->fuse, d + search_total, nf * sizeof(Out3), cudaMemcpyDefault, s)))
+    if (nf && (e = cudaMemcpyAsync(r->fuse, df, nf * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "fusion download");
-    if (nw && (e = cudaMemcpyAsync(r->fwd, d + bwd_end, nw * sizeof(Out3), cudaMemcpyDefault, s)))
+    if (nw && (e = cudaMemcpyAsync(r->fwd, df + bwd_end, nw * sizeof(Out3), cudaMemcpyDefault, s)))
         return cuda_fail(e, "forward fusion download");
     if (B.args.triangulate && search_total &&
         ((e = cudaMemcpyAsync(r->points, B.points.p, (size_t)search_total * 12, cudaMemcpyDefault, s)) ||
@@ -1990,9 +2009,10 @@ extern "C" tm_status tm_plan_create(tm_ctx *c, const tm_step *steps, int32_t n_s
         // search (when there are pairs), fuse (when there are map points), copy, ingest (when
         // keyframes enter with the batch)
         // (the entry form's search is three launches: join, evaluation, finalize)
-        P->kernels_per_run = (P->B.n_search_items ? (P->B.args.qpl == 4 ? 4 : 2) : 0) +
-                             (P->B.n_items > P->B.n_search_items ? 1 : 0) +
-                             1 + (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0) +
+        // (each branch compacts its own records: a copy per part that has items)
+        P->kernels_per_run = (P->B.n_search_items ? (P->B.args.qpl == 4 ? 4 : 2) + 1 : 0) +
+                             (P->B.n_items > P->B.n_search_items ? 2 : 0) +
+                             (P->B.n_new ? 1 : 0) + (P->B.n_search_items && P->B.args.sp.dense_min > 0 ? 1 : 0) +
                              (P->B.n_search_items && P->B.args.triangulate ? 1 : 0);
     } else {
         P->kernels_per_run = 3 * (int)P->B.n_search_items + (P->B.n_new ? 1 : 0) +
@@ -2093,7 +2113,7 @@ extern "C" tm_status tm_plan_stage_times(tm_plan *P, float *ms) {
     ms[0] = t[1] - (dense ? t[6] : t[7]); // search kernel (between the events around it)
     ms[1] = t[2];                         // ingest (from the start)
     ms[2] = t[3] - t[2];                  // fusion (after the ingest)
-    ms[3] = t[4] - std::max(t[1], t[3]);  // offsets + copy (after both branches)
+    ms[3] = t[4] - std::max(t[1], t[3]);  // each branch's offsets + copy, after the later kernel
     ms[4] = dense ? t[6] - t[7] : 0.0f;   // dense node blocks (before the search kernel)
     ms[5] = t[7] - t[5];                  // prep (per-pair constants and eligibility)
     return TM_OK;

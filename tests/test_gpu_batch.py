@@ -76,8 +76,8 @@ def test_plan_graph_replay(tm, small_batch):
         load_all(ctx, w)
         with ctx.plan(steps_of(w)) as plan:
             info = plan.info()
-            # prep, search (join, evaluation, finalize in the entry form), fuse, copy
-            assert info["kernels_per_run"] == 4 + 2 * plan.tuning()["entry_form"] and info["ctas"] >= 1
+            # prep, search (join, evaluation, finalize in the entry form), its copy, fuse, its copy
+            assert info["kernels_per_run"] == 5 + 2 * plan.tuning()["entry_form"] and info["ctas"] >= 1
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -295,8 +295,8 @@ def test_new_keyframes_enter_with_the_batch(tm, small_batch):
         with pytest.raises(tm.TMError):
             ctx.keyframe_size(new_ids[0])
         with ctx.plan(steps_of(w), new=new) as plan:
-            # ingest, prep, search (three launches in the entry form), fuse, copy
-            assert plan.info()["kernels_per_run"] == 5 + 2 * plan.tuning()["entry_form"]
+            # ingest, prep, search (three launches in the entry form), its copy, fuse, its copy
+            assert plan.info()["kernels_per_run"] == 6 + 2 * plan.tuning()["entry_form"]
             for _ in range(3):
                 plan.run()
                 assert_same(plan.results(), exp)
@@ -723,8 +723,9 @@ def test_triangulation_plan_new_keyframes(tm, small_batch):
     with tm.Context(w["cam"], max_kp=2048) as ctx:
         ctx.add_keyframes(old_ids, [w["frames"][i] for i in old_ids])
         with ctx.plan(steps_of(w), new=(new_ids, [w["frames"][i] for i in new_ids]), tri=tm.TriParams()) as plan:
-            # ingest, prep, search (three launches in the entry form), fuse, copy, triangulation
-            assert plan.info()["kernels_per_run"] == 6 + 2 * plan.tuning()["entry_form"]
+            # ingest, prep, search (three launches in the entry form), its copy, triangulation, fuse,
+            # its copy
+            assert plan.info()["kernels_per_run"] == 7 + 2 * plan.tuning()["entry_form"]
             for _ in range(2):
                 plan.run()
                 r = plan.results()
