@@ -2420,6 +2420,17 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A, uint32_
             c[q] = cb + q < ns ? __ldg(A.counts + s0 + cb + q) : 0u;
             sum += c[q];
         }
+        // the warp's first item of the segment: its count, region and first 128 words, loaded
+        // before the scan so that their latency overlaps it
+        const bool have0 = gw < ns;
+        const uint32_t w0 = have0 ? 3u * __ldg(A.counts + s0 + gw) : 0u;
+        const uint32_t src0 = have0 ? 3u * A.items[s0 + gw].out_off : 0u;
+        uint32_t v0[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t e = 32u * q + lane;
+            v0[q] = e < w0 ? __ldg(pw + src0 + e) : 0u;
+        }
         if (blockIdx.x == 0)
 #pragma unroll
             for (int q = 0; q < kCopyPer; ++q) {
@@ -2444,9 +2455,18 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(BatchArgs A, uint32_
         if (blockIdx.x == 0)
             for (uint32_t k = tid; k < ns; k += bs) A.offsets[s0 + k] = offs[k];
         for (uint32_t k = gw; k < ns; k += gws) {
-            const uint32_t words = 3u * cnts[k], dst = 3u * offs[k], src = 3u * A.items[s0 + k].out_off;
+            const bool first = k == gw;
+            const uint32_t words = first ? w0 : 3u * cnts[k], dst = 3u * offs[k];
+            const uint32_t src = first ? src0 : 3u * A.items[s0 + k].out_off;
+            if (first) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t e = 32u * q + lane;
+                    if (e < words) dw[dst + e] = v0[q];
+                }
+            }
             // four loads of each lane in flight before its stores
-            for (uint32_t e0 = 0; e0 < words; e0 += 128) {
+            for (uint32_t e0 = first ? 128u : 0u; e0 < words; e0 += 128) {
                 uint32_t v[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
