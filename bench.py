@@ -470,7 +470,8 @@ def run_mine(args, rank, world, local_rank):
             ctx.remove_keyframe(i)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
         h_masks = pin(masks)
-        h_mps = {k: (pin(v) if isinstance(v, np.ndarray) else v) for k, v in mps.items()}
+        # the map points in one page-locked staging block (uploaded with one copy)
+        h_mps = tm.pack_mappoints(mps)
         # the new keyframes packed one after another, one pinned array per field (as a producer
         # streaming keyframes into a staging buffer would hand them over)
         fr = [w["frames"][i] for i in new_ids]
@@ -487,7 +488,7 @@ def run_mine(args, rank, world, local_rank):
         n_pairs = sum(len(s["nbrs"]) for s in steps)
         n_items = n_pairs + sum((s["mps"]["n"] + 511) // 512 for s in steps)
         n_units = tuning["search_units"]  # launch entries of the search (split pairs twice)
-        h2d = (int(masks.nbytes) + sum(int(v.nbytes) for v in mps.values() if isinstance(v, np.ndarray))
+        h2d = (int(masks.nbytes) + int(h_mps["block"].numel())
                + sum(w["frames"][i]["n"] for i in new_ids) * 49
                + (n_items + n_units) * 128 + len(new_ids) * 112
                + 48 * ((sum(w["frames"][i]["n"] for i in new_ids) + 1023) // 1024))
@@ -605,7 +606,8 @@ def run_mine(args, rank, world, local_rank):
                       "api": "Context.batch_begin / batch_finish -> tm_batch_begin / tm_batch_finish, three "
                              "batches in flight, begun by a producer thread and finished in order by a consumer "
                              "thread (step table as columns; pinned host buffers: new keyframes, masks, map "
-                             "points in; matches and fusion candidates out, into one caller-owned ResultBuffers "
+                             "points (one staging block, one copy) in; matches and fusion candidates out, into "
+                             "one caller-owned ResultBuffers "
                              "per batch in flight, returned as views) + Context.remove_keyframes of the new "
                              "keyframes of every 8 finished steps in one call (consumer)",
                       "link": "inputs cross the host link at about 205 GB/s on this GB300 (copy engine and SM "

@@ -356,6 +356,15 @@ typedef struct {
     /* The new keyframes packed (count = n_new), in place of new_kfs (which is then NULL);
      * NULL when new_kfs is used. */
     const tm_keyframes_packed *new_packed;
+    /* NULL, or one allocation (page-locked host or device memory) that holds every array of
+     * mps: the batch then uploads the block [mps_block, mps_block + mps_block_bytes) with one
+     * copy (a transfer costs a few microseconds besides its bytes) and reads the arrays at
+     * their offsets in it.  The offsets of pos, normal, min_dist and max_dist must be
+     * multiples of 4 bytes and that of desc a multiple of 16; an array outside the block or
+     * an offset off alignment is TM_ERR_INVALID_ARG.  The block must stay valid and unchanged
+     * like the arrays themselves. */
+    const void *mps_block;
+    uint64_t mps_block_bytes;
 } tm_batch_inputs;
 
 /* Results, host buffers.  Search matches of all steps, step-major then neighbour order:

@@ -180,6 +180,40 @@ def keyframes_packed(packed, keep):
     return p, n
 
 
+_MP_FIELDS = (("pos", np.float32, 3), ("normal", np.float32, 3), ("desc", np.uint8, 32),
+              ("min_dist", np.float32, 1), ("max_dist", np.float32, 1), ("skip", np.uint8, 1))
+
+
+def pack_mappoints(mps, pinned=True):
+    """The map points of a batch (dict: n, pos, normal, desc, min_dist, max_dist, optional
+    skip) copied into one buffer -- page-locked when pinned (torch), else a numpy array --
+    each array at a 16-byte aligned offset.  The returned dict holds views into the buffer
+    and "block", the buffer: a batch given it uploads its map points with one copy
+    (tm_batch_inputs.mps_block) instead of one copy an array."""
+    n = int(mps["n"])
+    parts = [(f, dt, w) for f, dt, w in _MP_FIELDS if f != "skip" or mps.get("skip") is not None]
+    offs, o = {}, 0
+    for f, dt, w in parts:
+        offs[f] = o
+        o = (o + n * w * np.dtype(dt).itemsize + 15) & ~15
+    total = max(16, o)
+    if pinned:
+        import torch
+        buf = torch.empty(total, dtype=torch.uint8).pin_memory()
+        raw = buf.numpy()
+    else:
+        buf = raw = np.zeros(total, np.uint8)
+    out = dict(n=n, block=buf)
+    for f, dt, w in parts:
+        x = mps[f]
+        a = np.asarray(x.cpu() if hasattr(x, "cpu") else x).astype(dt, copy=False).reshape(n, w) if n else \
+            np.zeros((0, w), dt)
+        v = raw[offs[f]:offs[f] + a.nbytes].view(dt).reshape((n, w) if w > 1 else (n,))
+        v[...] = a.reshape(v.shape)
+        out[f] = torch.from_numpy(v) if pinned else v
+    return out
+
+
 def mappoint_view(mps, keep):
     v = L.tm_mappoint_view()
     if mps is None:
@@ -823,6 +857,12 @@ class Context:
         inp.masks = _ptr(masks) if masks is not None and len(masks) else None
         inp.mask_bytes = 0 if masks is None else int(np.prod(masks.shape)) if isinstance(masks, np.ndarray) else masks.numel()
         inp.mps = mappoint_view(mps if mps is not None and mps["n"] else None, keep)
+        blk = mps.get("block") if isinstance(mps, dict) and mps["n"] else None
+        if blk is not None:
+            # one allocation holding every array (pack_mappoints): uploaded with one copy
+            keep.append(blk)
+            inp.mps_block = _ptr(blk)
+            inp.mps_block_bytes = int(blk.nbytes) if isinstance(blk, np.ndarray) else blk.numel() * blk.element_size()
         if new is not None:
             ids, kfs = new
             idarr = np.ascontiguousarray(ids, np.uint64)

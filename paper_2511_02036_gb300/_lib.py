@@ -95,7 +95,8 @@ class tm_keyframes_packed(ctypes.Structure):
 
 class tm_batch_inputs(ctypes.Structure):
     _fields_ = [("masks", c_p), ("mask_bytes", c_sz), ("mps", tm_mappoint_view),
-                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p), ("tri", c_p), ("new_packed", c_p)]
+                ("n_new", c_i32), ("new_ids", c_p), ("new_kfs", c_p), ("tri", c_p), ("new_packed", c_p),
+                ("mps_block", c_p), ("mps_block_bytes", c_u64)]
 
 
 class tm_batch_result(ctypes.Structure):

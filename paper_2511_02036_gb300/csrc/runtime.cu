@@ -614,7 +614,7 @@ void BatchBuf::release() {
     if (graph_timed) cudaGraphExecDestroy(graph_timed);
     graph = graph_timed = nullptr;
     for (DevBuf *b : {&items, &masks, &mp_pos, &mp_normal, &mp_desc, &mp_min, &mp_max,
-                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok, &pwin, &pacc, &pdone, &ents, &povf})
+                      &mp_skip, &padded, &counts, &item_cmp, &offsets, &ncmp, &counters, &dense, &scratch, &dres, &acc, &pconst, &pwords, &pepos, &work, &points, &point_ok, &pwin, &pacc, &pdone, &ents, &povf, &mp_block})
         b->release();
     h_stage.release();
     h_out.release();
@@ -706,6 +706,43 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     if (mps.n > 0 && (!mps.pos || !mps.normal || !mps.desc || !mps.min_dist || !mps.max_dist))
         return fail(TM_ERR_INVALID_ARG, "map point arrays must be non-null");
     std::vector<void *> before = B.pointers();
+    // map points in one caller block: the byte offset of each array in it (checked: inside the
+    // block, aligned as the kernels read it), so that the block is uploaded with one copy
+    const unsigned char *blk = in ? static_cast<const unsigned char *>(in->mps_block) : nullptr;
+    const uint64_t blk_bytes = in ? in->mps_block_bytes : 0;
+    uint64_t boff[6] = {0, 0, 0, 0, 0, 0};  // pos, normal, desc, min_dist, max_dist, skip
+    if (blk && mps.n > 0) {
+        const size_t m = (size_t)mps.n;
+        const void *ptr[6] = {mps.pos, mps.normal, mps.desc, mps.min_dist, mps.max_dist, mps.skip};
+        const size_t len[6] = {m * 12, m * 12, m * 32, m * 4, m * 4, m};
+        const unsigned align[6] = {4, 4, 16, 4, 4, 1};
+        for (int k = 0; k < 6; ++k) {
+            if (!ptr[k]) continue;
+            const unsigned char *p = static_cast<const unsigned char *>(ptr[k]);
+            if (p < blk || (uint64_t)(p - blk) > blk_bytes || len[k] > blk_bytes - (uint64_t)(p - blk) ||
+                (uint64_t)(p - blk) % align[k])
+                return fail(TM_ERR_INVALID_ARG, "map point array %d outside the block or off alignment", k);
+            boff[k] = (uint64_t)(p - blk);
+        }
+    } else {
+        blk = nullptr;
+    }
+    // the map points' upload: the block with one copy, or the six arrays
+    auto upload_mps = [&](cudaStream_t cs) -> cudaError_t {
+        const size_t m = (size_t)mps.n;
+        cudaError_t ce;
+        if (blk) {
+            if ((ce = B.mp_block.reserve(std::max<uint64_t>(16, blk_bytes)))) return ce;
+            return cudaMemcpyAsync(B.mp_block.p, blk, blk_bytes, cudaMemcpyDefault, cs);
+        }
+        if ((ce = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, cs)) ||
+            (ce = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, cs)) ||
+            (ce = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, cs)) ||
+            (ce = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, cs)) ||
+            (ce = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, cs)))
+            return ce;
+        return mps.skip ? cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, cs) : cudaSuccess;
+    };
     // a one-shot batch copies its map points first, on a stream of their own that only the
     // fusion kernel awaits, so that the copy runs under the host work below
     B.forked = B.mp_async = false;
@@ -719,13 +756,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
             return cuda_fail(e, "batch buffers");
         if ((e = cudaEventRecord(B.mpre, s)) || (e = cudaStreamWaitEvent(B.mcopy, B.mpre, 0)))
             return cuda_fail(e, "map point stream");
-        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, B.mcopy)) ||
-            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, B.mcopy)) ||
-            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, B.mcopy)) ||
-            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, B.mcopy)) ||
-            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, B.mcopy)) ||
-            (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, B.mcopy))) ||
-            (e = cudaEventRecord(B.mready, B.mcopy)))
+        if ((e = upload_mps(B.mcopy)) || (e = cudaEventRecord(B.mready, B.mcopy)))
             return cuda_fail(e, "map point upload");
         B.mp_async = mp_copied = true;
     }
@@ -1022,6 +1053,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         (e = B.pepos.reserve(std::max<uint32_t>(64, tq) * 2)) ||
         (e = B.pwin.reserve(std::max<uint32_t>(64, tq) * 4)) || (e = B.pacc.reserve(nsi * 8)) ||
         (e = B.pdone.reserve(nsi * 4)) || (e = B.povf.reserve(nsi * 4)) ||
+        (blk && (e = B.mp_block.reserve(std::max<uint64_t>(16, blk_bytes)))) ||
         (entry_ok && (e = B.ents.reserve(size_t(ent_cap) * 8))) ||
         (tri && ((e = B.points.reserve(std::max<size_t>(1, B.search_pad) * 12)) ||
                  (e = B.point_ok.reserve(std::max<size_t>(1, B.search_pad))))))
@@ -1060,17 +1092,7 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
         }
     }
     const cudaStream_t ms = s;
-    if (mps.n > 0 && !mp_copied) {
-        const size_t m = (size_t)mps.n;
-        if ((e = cudaMemcpyAsync(B.mp_pos.p, mps.pos, m * 12, cudaMemcpyDefault, ms)) ||
-            (e = cudaMemcpyAsync(B.mp_normal.p, mps.normal, m * 12, cudaMemcpyDefault, ms)) ||
-            (e = cudaMemcpyAsync(B.mp_desc.p, mps.desc, m * 32, cudaMemcpyDefault, ms)) ||
-            (e = cudaMemcpyAsync(B.mp_min.p, mps.min_dist, m * 4, cudaMemcpyDefault, ms)) ||
-            (e = cudaMemcpyAsync(B.mp_max.p, mps.max_dist, m * 4, cudaMemcpyDefault, ms)))
-            return cuda_fail(e, "map point upload");
-        if (mps.skip && (e = cudaMemcpyAsync(B.mp_skip.p, mps.skip, m, cudaMemcpyDefault, ms)))
-            return cuda_fail(e, "map point upload");
-    }
+    if (mps.n > 0 && !mp_copied && (e = upload_mps(ms))) return cuda_fail(e, "map point upload");
     BatchArgs &A = B.args;
     A.items = static_cast<const WorkItem *>(B.items.p);
     A.n_items = B.n_items;
@@ -1079,13 +1101,15 @@ tm_status tmap::prepare_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, int 
     A.sitems = reinterpret_cast<const WorkItem *>(static_cast<unsigned char *>(B.items.p) + align128(ni * sizeof(WorkItem)));
     A.counters = static_cast<uint32_t *>(B.counters.p);
     A.masks = static_cast<const uint8_t *>(B.masks.p);
-    A.mp_pos = static_cast<const float *>(B.mp_pos.p);
-    A.mp_normal = static_cast<const float *>(B.mp_normal.p);
-    A.mp_min = static_cast<const float *>(B.mp_min.p);
-    A.mp_max = static_cast<const float *>(B.mp_max.p);
+    const unsigned char *db = static_cast<const unsigned char *>(B.mp_block.p);
+    A.mp_pos = blk ? reinterpret_cast<const float *>(db + boff[0]) : static_cast<const float *>(B.mp_pos.p);
+    A.mp_normal = blk ? reinterpret_cast<const float *>(db + boff[1]) : static_cast<const float *>(B.mp_normal.p);
+    A.mp_min = blk ? reinterpret_cast<const float *>(db + boff[3]) : static_cast<const float *>(B.mp_min.p);
+    A.mp_max = blk ? reinterpret_cast<const float *>(db + boff[4]) : static_cast<const float *>(B.mp_max.p);
     A.n_mp = (uint32_t)std::max(0, mps.n);
-    A.mp_desc = static_cast<const uint4 *>(B.mp_desc.p);
-    A.mp_skip = (mps.n > 0 && mps.skip) ? static_cast<const uint8_t *>(B.mp_skip.p) : nullptr;
+    A.mp_desc = blk ? reinterpret_cast<const uint4 *>(db + boff[2]) : static_cast<const uint4 *>(B.mp_desc.p);
+    A.mp_skip = !(mps.n > 0 && mps.skip) ? nullptr
+        : blk ? db + boff[5] : static_cast<const uint8_t *>(B.mp_skip.p);
     A.padded = static_cast<Out3 *>(B.padded.p);
     A.counts = static_cast<uint32_t *>(B.counts.p);
     A.offsets = static_cast<uint32_t *>(B.offsets.p);
@@ -1135,7 +1159,7 @@ std::vector<void *> BatchBuf::pointers() const {
     return {items.p, masks.p, mp_pos.p, mp_normal.p, mp_desc.p, mp_min.p, mp_max.p,
             mp_skip.p, padded.p, counts.p, item_cmp.p, offsets.p, ncmp.p, counters.p, dense.p, dres.p, acc.p, pconst.p,
             pwords.p, pepos.p, work.p, points.p,
-            point_ok.p, pwin.p, pacc.p, pdone.p, ents.p, povf.p};
+            point_ok.p, pwin.p, pacc.p, pdone.p, ents.p, povf.p, mp_block.p};
 }
 
 // Takes the keyframes that entered the store with batch B out again (failed call).

@@ -73,7 +73,7 @@ struct Knobs {
 struct BatchBuf {
     DevBuf items, masks, mp_pos, mp_normal, mp_desc, mp_min, mp_max, mp_skip, padded,
         counts, item_cmp, offsets, ncmp, counters, dense, scratch, dres, acc, pconst, pwords, pepos, work, points,
-        point_ok, pwin, pacc, pdone, ents, povf;
+        point_ok, pwin, pacc, pdone, ents, povf, mp_block;
     uint32_t n_units = 0;          // search launch entries (split pairs twice)
     uint32_t ent_cap = 0;          // entry form: capacity of ents (entries; 0 = form not prepared)
     PinBuf h_stage, h_out;

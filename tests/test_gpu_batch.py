@@ -767,3 +767,60 @@ def test_pair_baseline_skip_batch(tm, small_batch, mode):
         for g, e in zip(res.pairs, exp):
             np.testing.assert_array_equal(g, e)
         assert res.n_comparisons_search == ecmp
+
+
+@pytest.mark.parametrize("kind", ["pinned", "device"])
+def test_mappoint_block(tm, small_batch, kind):
+    """The batch's map points in one staging block (pack_mappoints; tm_batch_inputs.mps_block:
+    one upload), page-locked host or device memory: one-shot, asynchronous and plan batches give
+    the oracle's results; a descriptor array off its 16-byte alignment in the block and an array
+    outside the block are refused before any work."""
+    torch = pytest.importorskip("torch")
+    w = small_batch
+    exp = oracle_results(w)
+    with tm.Context(w["cam"], max_kp=2048) as ctx:
+        load_all(ctx, w)
+        st_arr, masks, mps, _keep = tm.pack_batch(steps_of(w), ctx.sizes)
+        steps = [dict(kf_id=st_arr[k].kf_id, nbrs=w["steps"][k]["nbrs"], q_free_off=st_arr[k].q_free_off,
+                      nbr_free_off=st_arr[k].nbr_free_off, mp_begin=st_arr[k].mp_begin,
+                      mp_count=st_arr[k].mp_count) for k in range(len(w["steps"]))]
+        fields = ("pos", "normal", "desc", "min_dist", "max_dist", "skip")
+        blk = tm.pack_mappoints(mps, pinned=True)
+        if kind == "device":
+            # the same layout in device memory: views at the host block's offsets
+            dev_block = blk["block"].cuda()
+            dv = {}
+            for f in fields:
+                if f in blk:
+                    off = blk[f].data_ptr() - blk["block"].data_ptr()
+                    nb = blk[f].numel() * blk[f].element_size()
+                    dv[f] = dev_block[off:off + nb].view(blk[f].dtype).view(blk[f].shape)
+            blk = dict(n=blk["n"], block=dev_block, **dv)
+        d_masks = torch.from_numpy(np.ascontiguousarray(masks)).cuda()
+        assert_same(ctx.batch_run(steps, masks=d_masks, mps=blk), exp)
+        t = ctx.batch_begin(steps, masks=d_masks, mps=blk)
+        assert_same(ctx.batch_finish(t), exp)
+        with ctx.plan(steps, masks=d_masks, mps=blk) as plan:
+            plan.run()
+            assert_same(plan.results(), exp)
+        if kind == "pinned":
+            # desc 8 bytes into its slot: off the 16-byte alignment
+            n = int(mps["n"])
+            raw = blk["block"]
+            shifted = torch.empty(raw.numel() + 64, dtype=torch.uint8).pin_memory()
+            shifted[:raw.numel()] = raw
+            bad = dict(n=n, block=shifted)
+            for f in fields:
+                if f in blk:
+                    o = blk[f].data_ptr() - raw.data_ptr() + (8 if f == "desc" else 0)
+                    nb = blk[f].numel() * blk[f].element_size()
+                    bad[f] = shifted[o:o + nb].view(blk[f].dtype).view(blk[f].shape)
+            with pytest.raises(tm.TMError) as e:
+                ctx.batch_run(steps, masks=d_masks, mps=bad)
+            assert e.value.status == tm.TM_ERR_INVALID_ARG
+            # an array outside the block
+            outside = dict(blk, desc=torch.from_numpy(np.ascontiguousarray(mps["desc"])).pin_memory())
+            with pytest.raises(tm.TMError) as e:
+                ctx.batch_run(steps, masks=d_masks, mps=outside)
+            assert e.value.status == tm.TM_ERR_INVALID_ARG
+            assert_same(ctx.batch_run(steps, masks=d_masks, mps=blk), exp)
