@@ -1542,7 +1542,11 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
                 break;
             case 1: if (c->force_persist < 0 && forms) { k.persist = !best.persist; alts.push_back(k); } break;
             case 2: if (c->force_prefetch < 0) { k.prefetch = !best.prefetch; alts.push_back(k); } break;
-            case 3: if (c->branch_prio < 0 && both_branches) { k.bprio = !best.bprio; alts.push_back(k); } break;
+            case 3:
+                if (c->branch_prio < 0 && both_branches)
+                    for (int bp : {0, 1, 2})  // search first, store first, equal
+                        if (bp != best.bprio) { k.bprio = bp; alts.push_back(k); }
+                break;
             case 4:
                 if (dense_auto)
                     for (int dm : {64, 32, 128})
