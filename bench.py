@@ -419,7 +419,7 @@ def run_mine(args, rank, world, local_rank):
            "config": {"workload": WORKLOAD, "new_keyframes_per_step": len(new_ids),
                       "pairs": sum(len(s["nbrs"]) for s in steps), "map_points": int(mps["n"]),
                       "l2": "flushed before each timed step (256 MB written)",
-                      "launch": info, "parallelism": "replicas" if world == 1 else "dp%d" % world},
+                      "launch": dict(info, tuning=tuning), "parallelism": "replicas" if world == 1 else "dp%d" % world},
            "gcomparisons_per_s": gcomp,
            "comparisons_per_step": ncmp,
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

@@ -1496,8 +1496,15 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // a choice is timed as the plan will run it: captured into a graph, replayed once to warm
-    // up, then the fastest of up to 16 replays (at least ~1 ms of them, so that a small
-    // batch's choices are told apart), each between events on the stream
+    // up, then the median of up to 16 replays (at least ~1 ms of them, so that a small batch's
+    // choices are told apart), each between events on the stream and each after 256 MB
+    // written (L2 flushed: a batch's inputs are not in L2 when it runs)
+    void *flush = nullptr;
+    const size_t flush_bytes = size_t(256) << 20;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;  // (timed with a warm L2 then)
+    }
     auto time_of = [&](const Knobs &k, float &ms) -> tm_status {
         B.knobs = k;
         cudaGraph_t g = nullptr;
@@ -1512,8 +1519,10 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
         if (r) return r;
         ms = 0.0f;
         float t = 0.0f;
+        std::vector<float> ts;
         for (int rep = 0, reps = 2; rep < reps; ++rep) {
-            if ((ce = cudaEventRecord(e0, s)) || (ce = cudaGraphLaunch(x, s)) || (ce = cudaEventRecord(e1, s)) ||
+            if ((flush && (ce = cudaMemsetAsync(flush, rep & 0xFF, flush_bytes, s))) ||
+                (ce = cudaEventRecord(e0, s)) || (ce = cudaGraphLaunch(x, s)) || (ce = cudaEventRecord(e1, s)) ||
                 (ce = cudaEventSynchronize(e1)) || (ce = cudaEventElapsedTime(&t, e0, e1))) {
                 r = cuda_fail(ce, "tuning replay");
                 break;
@@ -1522,7 +1531,11 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
                 reps = 1 + std::max(3, std::min(16, (int)std::ceil(1.0f / std::max(t, 1e-3f))));
                 continue;
             }
-            ms = rep == 1 ? t : std::min(ms, t);
+            ts.push_back(t);
+        }
+        if (!ts.empty()) {
+            std::nth_element(ts.begin(), ts.begin() + ts.size() / 2, ts.end());
+            ms = ts[ts.size() / 2];
         }
         cudaGraphExecDestroy(x);
         return r;
@@ -1565,6 +1578,7 @@ tm_status tmap::tune_batch(tm_ctx *c, BatchBuf &B, const tm_step *steps, cudaStr
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (flush) cudaFree(flush);
     if (st) return st;
     B.knobs = best;
     B.tuned = true;

@@ -66,7 +66,9 @@ struct IngestStage {
 // first (0 search, 1 store), dense node blocks from this run length (0 = off; only when the
 // caller asks for the tuner's choice, dense_min -1), the dense kernel's split divisor.
 struct Knobs {
-    int qpl = 2, persist = 0, prefetch = 0, bprio = 0, dense_min = 0, dsplit_div = 1;
+    // (the store branch first by default: ingest -> fusion -> its copy is the batch's usual
+    // critical chain)
+    int qpl = 2, persist = 0, prefetch = 0, bprio = 1, dense_min = 0, dsplit_div = 1;
 };
 
 // Device and staging buffers of one batch, plus what the host needs to read its results.
