@@ -428,8 +428,9 @@ def run_mine(args, rank, world, local_rank):
                         "fuse": float(stage[:, 2].mean()), "copy": float(stage[:, 3].mean()),
                         "note": "from the plan's timed graph (an event node at each stage boundary "
                                 "adds a few us); the search kernel runs beside the store branch "
-                                "(ingest, then fuse); value and ms_per_step come from the "
-                                "kernels-only graph"},
+                                "(ingest, then fuse); copy = from the later of the search and fusion "
+                                "kernels' ends to the end of the run (each branch compacts its own "
+                                "records); value and ms_per_step come from the kernels-only graph"},
            "warm_l2": {"ms_per_step": float(warm.mean()), "value": len(new_ids) / (float(warm.mean()) / 1e3),
                        "unit": "keyframes/s", "note": "same replays back to back without the L2 flush"},
            "device": torch.cuda.get_device_name(dev), "roofline": roof, "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,

@@ -1026,8 +1026,10 @@ class Plan:
         return {f: getattr(t, f) for f, _ in t._fields_}
 
     def stage_times(self):
-        """(search kernel, ingest, fusion, offsets + copy, dense blocks, prep) device
-        milliseconds of the last run if it was timed (run(timed=True)); zeros otherwise."""
+        """(search kernel, ingest, fusion, tail, dense blocks, prep) device milliseconds of the
+        last run if it was timed (run(timed=True)); zeros otherwise.  The tail runs from the later
+        of the search and fusion kernels' ends to the end of the run (each branch's offsets +
+        copy of its own records, and the triangulation when on)."""
         ms = np.zeros(L.TM_PLAN_STAGES, np.float32)
         check(tm_plan_stage_times(self.handle, ms.ctypes.data))  # noqa: F821
         return tuple(float(x) for x in ms)
